@@ -1,0 +1,194 @@
+"""Seeded synthetic graph generators (inputs only).
+
+Both the CPU oracle and the CUDA path consume these graphs; this package holds none of the
+bridge method's arithmetic.  Graphs are undirected int32 COO edge lists in structure-of-arrays
+form (``u``, ``v``), normalised so that ``u < v`` except for self-loops in the test multigraphs.
+
+Named workloads (the sizes of the paper's dense-graph regime, Sec. 3 and Figs. 2-4):
+
+* ``small``: 8 Erdos-Renyi clusters of 256 vertices (p=0.5), a random inter-cluster tree of
+  7 edges, 40 pendant vertices and 20 inter-cluster edge pairs; seed 0.
+* ``mid``: 64 clusters of 512 vertices (p=0.3), a 63-edge cluster tree, 1,000 pendant paths of
+  length 1-8 and 500 extra inter-cluster edges; seed 1.
+* ``large``: one ER(65,536, 0.5) core with 256 pendant random recursive trees of 1-64
+  vertices and 128 two-edge vertices; seed 2 (about 1.07 G edges, 8.6 GB).
+* ``batched``/``served``: per-graph parameters from :func:`workload_spec`.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass, field, asdict
+
+import numpy as np
+
+from . import build as _build
+
+_lib = None
+
+
+class _Spec(ctypes.Structure):
+    _fields_ = [
+        ("seed", ctypes.c_uint64),
+        ("n_clusters", ctypes.c_int32),
+        ("core_vertices", ctypes.c_int32),
+        ("p", ctypes.c_double),
+        ("n_pendant", ctypes.c_int32),
+        ("n_paths", ctypes.c_int32),
+        ("path_min", ctypes.c_int32),
+        ("path_max", ctypes.c_int32),
+        ("n_extra_pairs", ctypes.c_int32),
+        ("n_extra", ctypes.c_int32),
+        ("n_trees", ctypes.c_int32),
+        ("tree_min", ctypes.c_int32),
+        ("tree_max", ctypes.c_int32),
+        ("n_two_edge", ctypes.c_int32),
+        ("shuffle", ctypes.c_int32),
+        ("relabel", ctypes.c_int32),
+    ]
+
+
+class _Graph(ctypes.Structure):
+    _fields_ = [
+        ("E", ctypes.c_int64),
+        ("V", ctypes.c_int32),
+        ("n_planted", ctypes.c_int64),
+        ("u", ctypes.POINTER(ctypes.c_int32)),
+        ("v", ctypes.POINTER(ctypes.c_int32)),
+        ("planted", ctypes.POINTER(ctypes.c_int32)),
+        ("n_er", ctypes.c_int64),
+    ]
+
+
+def _load():
+    global _lib
+    if _lib is None:
+        path = _build.build()
+        lib = ctypes.CDLL(path)
+        lib.gg_generate.restype = ctypes.POINTER(_Graph)
+        lib.gg_generate.argtypes = [ctypes.POINTER(_Spec)]
+        lib.gg_free.argtypes = [ctypes.POINTER(_Graph)]
+        lib.gg_workload_spec.restype = ctypes.c_int
+        lib.gg_workload_spec.argtypes = [ctypes.c_int, ctypes.c_uint64, ctypes.c_int64, ctypes.c_int32,
+                                         ctypes.c_int32, ctypes.c_double, ctypes.c_double,
+                                         ctypes.POINTER(_Spec)]
+        lib.gg_random_multigraph.argtypes = [ctypes.c_uint64, ctypes.c_int32, ctypes.c_int64,
+                                             ctypes.c_void_p, ctypes.c_void_p]
+        lib.gg_num_threads.restype = ctypes.c_int
+        _lib = lib
+    return _lib
+
+
+@dataclass
+class Spec:
+    seed: int = 0
+    n_clusters: int = 1
+    core_vertices: int = 64
+    p: float = 0.5
+    n_pendant: int = 0
+    n_paths: int = 0
+    path_min: int = 1
+    path_max: int = 1
+    n_extra_pairs: int = 0
+    n_extra: int = 0
+    n_trees: int = 0
+    tree_min: int = 1
+    tree_max: int = 1
+    n_two_edge: int = 0
+    shuffle: int = 1
+    relabel: int = 1
+
+    def _c(self) -> _Spec:
+        return _Spec(**asdict(self))
+
+
+@dataclass
+class Graph:
+    """An undirected edge list plus the bridges planted by construction.
+
+    ``planted`` holds the bridges the construction guarantees (pendant vertices, pendant paths
+    and trees, uncovered cluster-tree edges) as sorted (a<b) pairs, shape (n, 2).  Every planted
+    edge is a bridge of the graph; the converse holds when every cluster is 2-edge-connected.
+    """
+
+    u: np.ndarray
+    v: np.ndarray
+    V: int
+    planted: np.ndarray
+    spec: Spec | None = None
+    n_er: int = 0
+    _handle: object = field(default=None, repr=False)
+
+    @property
+    def E(self) -> int:
+        return int(self.u.shape[0])
+
+    def __del__(self):
+        h = getattr(self, "_handle", None)
+        if h is not None and _lib is not None:
+            self.u = self.v = None
+            _lib.gg_free(h)
+            self._handle = None
+
+
+def generate(spec: Spec) -> Graph:
+    """Generates the graph of ``spec``.  The edge arrays alias C-owned memory (no copy)."""
+    lib = _load()
+    cs = spec._c()
+    h = lib.gg_generate(ctypes.byref(cs))
+    if not h:
+        raise ValueError(f"invalid generator spec or out of memory: {spec}")
+    g = h.contents
+    E, V, npl = int(g.E), int(g.V), int(g.n_planted)
+    if E > 0:
+        u = np.ctypeslib.as_array(g.u, shape=(E,))
+        v = np.ctypeslib.as_array(g.v, shape=(E,))
+    else:
+        u = np.zeros(0, np.int32)
+        v = np.zeros(0, np.int32)
+    planted = np.ctypeslib.as_array(g.planted, shape=(max(npl, 1) * 2,))[: 2 * npl].reshape(npl, 2).copy()
+    return Graph(u=u, v=v, V=V, planted=planted, spec=spec, n_er=int(g.n_er), _handle=h)
+
+
+WORKLOADS = {
+    "small": Spec(seed=0, n_clusters=8, core_vertices=2048, p=0.5, n_pendant=40, n_extra_pairs=20),
+    "mid": Spec(seed=1, n_clusters=64, core_vertices=32768, p=0.3, n_paths=1000, path_min=1, path_max=8,
+                n_extra=500),
+    "large": Spec(seed=2, n_clusters=1, core_vertices=65536, p=0.5, n_trees=256, tree_min=1, tree_max=64,
+                  n_two_edge=128),
+}
+
+
+def workload(name: str, **overrides) -> Graph:
+    spec = Spec(**{**asdict(WORKLOADS[name]), **overrides})
+    return generate(spec)
+
+
+def workload_spec(kind: str, seed: int, index: int) -> Spec:
+    """Per-graph spec of the batched (V in [64, 4096], d in [0.1, 0.9]) or served
+    (V in [256, 65536], d in [0.05, 0.6]) workloads."""
+    lib = _load()
+    out = _Spec()
+    if kind == "batched":
+        rc = lib.gg_workload_spec(0, seed, index, 64, 6, 0.1, 0.9, ctypes.byref(out))
+    elif kind == "served":
+        rc = lib.gg_workload_spec(1, seed, index, 256, 8, 0.05, 0.6, ctypes.byref(out))
+    else:
+        raise ValueError(kind)
+    if rc != 0:
+        raise ValueError(kind)
+    return Spec(**{name: getattr(out, name) for name, _ in _Spec._fields_})
+
+
+def random_multigraph(seed: int, V: int, E: int):
+    """Seeded random multigraph with self-loops and duplicates kept (not normalised)."""
+    lib = _load()
+    u = np.empty(E, np.int32)
+    v = np.empty(E, np.int32)
+    if E:
+        lib.gg_random_multigraph(seed, V, E, u.ctypes.data, v.ctypes.data)
+    return u, v
+
+
+def num_threads() -> int:
+    return int(_load().gg_num_threads())

@@ -1,0 +1,117 @@
+"""CPU oracle for the sparse-certificate bridge method (TEST INFRASTRUCTURE ONLY).
+
+Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline / reference legs of
+``bench.py`` may import this package.  It shares no code with the CUDA path.
+
+Every function takes an undirected edge list as two int32 arrays ``u``, ``v`` and the vertex
+count ``V`` and returns bridges as an (n, 2) int32 array of (a < b) pairs sorted ascending.
+See ``oracle.c`` for the passage of the paper each function follows.
+
+Parity status: every function here is pinned by the ``-m "not gpu"`` tests (hand-derived
+fixtures, closed forms, brute force, planted bridges and certificate invariants); none is
+"parity unpinned".
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+
+from . import build as _build
+
+_lib = None
+_I32P = ctypes.c_void_p
+
+
+def _load():
+    global _lib
+    if _lib is None:
+        lib = ctypes.CDLL(_build.build())
+        for name in ("oracle_dfs_bridges", "oracle_chain_bridges", "oracle_brute_bridges"):
+            f = getattr(lib, name)
+            f.restype = ctypes.c_int64
+            f.argtypes = [_I32P, _I32P, ctypes.c_int64, ctypes.c_int32, _I32P]
+        lib.oracle_bridges.restype = ctypes.c_int64
+        lib.oracle_bridges.argtypes = [_I32P, _I32P, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32, _I32P]
+        lib.oracle_certificate.restype = ctypes.c_int64
+        lib.oracle_certificate.argtypes = [_I32P, _I32P, ctypes.c_int64, ctypes.c_int32, _I32P, _I32P]
+        lib.oracle_pipeline_cert.restype = ctypes.c_int64
+        lib.oracle_pipeline_cert.argtypes = [_I32P, _I32P, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32,
+                                             _I32P, _I32P, _I32P, _I32P]
+        lib.oracle_components.restype = ctypes.c_int32
+        lib.oracle_components.argtypes = [_I32P, _I32P, ctypes.c_int64, ctypes.c_int32, _I32P]
+        _lib = lib
+    return _lib
+
+
+def _edges(u, v):
+    u = np.ascontiguousarray(u, dtype=np.int32)
+    v = np.ascontiguousarray(v, dtype=np.int32)
+    if u.shape != v.shape or u.ndim != 1:
+        raise ValueError("u and v must be 1-D arrays of equal length")
+    return u, v
+
+
+def _check(rc):
+    if rc == -1:
+        raise ValueError("invalid input: vertex id outside [0, V) or negative size")
+    if rc == -2:
+        raise MemoryError("oracle allocation failed")
+    return rc
+
+
+def _bridge_call(name, u, v, V, *extra):
+    u, v = _edges(u, v)
+    out = np.empty(2 * max(V, 1), np.int32)
+    n = _check(getattr(_load(), name)(u.ctypes.data, v.ctypes.data, u.shape[0], V, *extra, out.ctypes.data))
+    return out[: 2 * n].reshape(n, 2).copy()
+
+
+def bridges(u, v, V: int, M: int = 1) -> np.ndarray:
+    """Sec. 3 end to end: M-way partition, certificates, merge phases, then Alg. 1 on X_0."""
+    return _bridge_call("oracle_bridges", u, v, V, M)
+
+
+def dfs_bridges(u, v, V: int) -> np.ndarray:
+    """Alg. 1 (iterative Tarjan disc/low) on the whole edge list."""
+    return _bridge_call("oracle_dfs_bridges", u, v, V)
+
+
+def chain_bridges(u, v, V: int) -> np.ndarray:
+    """Schmidt's chain decomposition on the whole edge list (independent of Alg. 1)."""
+    return _bridge_call("oracle_chain_bridges", u, v, V)
+
+
+def brute_bridges(u, v, V: int) -> np.ndarray:
+    """The definition: an edge is a bridge iff deleting it disconnects its ends (BFS)."""
+    return _bridge_call("oracle_brute_bridges", u, v, V)
+
+
+def certificate(u, v, V: int):
+    """Alg. 2 on the whole list: (edge ids of S, F-membership flags)."""
+    u, v = _edges(u, v)
+    ids = np.empty(max(2 * V, 1), np.int64)
+    f1 = np.empty(max(2 * V, 1), np.uint8)
+    k = _check(_load().oracle_certificate(u.ctypes.data, v.ctypes.data, u.shape[0], V, ids.ctypes.data,
+                                          f1.ctypes.data))
+    return ids[:k].copy(), f1[:k].astype(bool)
+
+
+def pipeline_certificate(u, v, V: int, M: int):
+    """Sec. 3 certificate pipeline: (ids of X_0, F flags of X_0, max |X_i| after each phase)."""
+    u, v = _edges(u, v)
+    ids = np.empty(max(2 * V + 2, 1), np.int64)
+    f1 = np.empty(max(2 * V + 2, 1), np.uint8)
+    pm = np.zeros(64, np.int64)
+    nq = np.zeros(1, np.int32)
+    k = _check(_load().oracle_pipeline_cert(u.ctypes.data, v.ctypes.data, u.shape[0], V, M, ids.ctypes.data,
+                                            f1.ctypes.data, pm.ctypes.data, nq.ctypes.data))
+    return ids[:k].copy(), f1[:k].astype(bool), pm[: int(nq[0])].copy()
+
+
+def components(u, v, V: int):
+    """(number of components, label per vertex = min vertex id of its component)."""
+    u, v = _edges(u, v)
+    lab = np.empty(max(V, 1), np.int32)
+    c = _check(_load().oracle_components(u.ctypes.data, v.ctypes.data, u.shape[0], V, lab.ctypes.data))
+    return int(c), lab[:V].copy()

@@ -1,0 +1,50 @@
+"""Input generators: determinism, normalisation and the sizes of the named workloads."""
+import numpy as np
+
+import graphgen
+
+
+def test_deterministic_and_normalised():
+    a = graphgen.workload("small")
+    b = graphgen.workload("small")
+    assert np.array_equal(a.u, b.u) and np.array_equal(a.v, b.v)
+    assert (a.u < a.v).all() and a.u.min() >= 0 and a.v.max() < a.V
+    # shuffled: edge order is not sorted by (u, v)
+    k = a.u.astype(np.int64) * a.V + a.v
+    assert not (np.diff(k) >= 0).all()
+    c = graphgen.workload("small", seed=1)
+    assert not np.array_equal(a.u, c.u)
+
+
+def test_sizes():
+    s = graphgen.workload("small")
+    # 8 clusters of 256 with p = 0.5: 8 * C(256, 2) / 2 = 130,560 expected ER edges
+    assert abs(s.n_er - 130560) < 5 * np.sqrt(8 * 32640 * 0.25)
+    assert s.E == s.n_er + 7 + 40 + 40
+    m = graphgen.workload("mid")
+    assert abs(m.n_er - 64 * 130816 * 0.3) < 5 * np.sqrt(64 * 130816 * 0.21)
+    assert m.V > 32768 + 1000
+
+
+def test_unshuffled_identity_labels():
+    g = graphgen.generate(graphgen.Spec(seed=3, n_clusters=1, core_vertices=10, p=1.0, shuffle=0, relabel=0))
+    assert g.E == 45
+    assert g.u.tolist() == [a for a in range(10) for b in range(a + 1, 10)]
+
+
+def test_workload_specs_in_range():
+    for i in range(200):
+        s = graphgen.workload_spec("batched", 3, i)
+        V = s.core_vertices + s.n_pendant
+        assert 64 <= V <= 4096 and 0.1 <= s.p <= 0.9
+        assert 2 <= s.n_clusters <= 8 and 1 <= s.n_clusters - 1 + s.n_pendant <= 32
+        t = graphgen.workload_spec("served", 4, i)
+        assert 256 <= t.core_vertices <= 65536 and 0.05 <= t.p <= 0.6
+
+
+def test_batched_planted_subset():
+    import oracle
+    for i in range(20):
+        g = graphgen.generate(graphgen.workload_spec("batched", 3, i))
+        found = {tuple(x) for x in oracle.bridges(g.u, g.v, g.V, 4).tolist()}
+        assert {tuple(x) for x in g.planted.tolist()} <= found

@@ -1,0 +1,218 @@
+"""Pins the CPU oracle to facts that do not come from the oracle itself.
+
+* hand-derived fixtures (tests/golden, Sec. 1 definition);
+* closed forms: trees, paths, cycles, complete graphs, doubled edges;
+* agreement of three independent methods (Alg. 1 DFS, Schmidt chains, the definition by
+  brute force) and of the Sec. 3 pipeline for many M on random multigraphs with V <= 64;
+* the generators' planted bridges (known by construction);
+* certificate invariants from Sec. 3 and Lemma 1.
+
+A plausible mistake in the oracle fails at least one of these: a dropped F' (Alg. 2) changes
+bridges on any cycle; a vertex-based parent skip (Alg. 1) makes a doubled edge a bridge; a
+">=" for ">" in the low/disc test makes cycle edges bridges; a lost merge partner (Sec. 3)
+changes components; a wrong partition bound loses edges.
+"""
+import itertools
+
+import numpy as np
+import pytest
+
+import graphgen
+import oracle
+from conftest import golden_names, load_golden
+
+ALL_METHODS = {
+    "dfs": lambda u, v, V: oracle.dfs_bridges(u, v, V),
+    "chain": lambda u, v, V: oracle.chain_bridges(u, v, V),
+    "brute": lambda u, v, V: oracle.brute_bridges(u, v, V),
+    "pipe1": lambda u, v, V: oracle.bridges(u, v, V, 1),
+    "pipe2": lambda u, v, V: oracle.bridges(u, v, V, 2),
+    "pipe3": lambda u, v, V: oracle.bridges(u, v, V, 3),
+    "pipe5": lambda u, v, V: oracle.bridges(u, v, V, 5),
+    "pipe16": lambda u, v, V: oracle.bridges(u, v, V, 16),
+    "pipe64": lambda u, v, V: oracle.bridges(u, v, V, 64),
+}
+
+
+def as_set(b):
+    return {tuple(x) for x in np.asarray(b).reshape(-1, 2).tolist()}
+
+
+@pytest.mark.parametrize("name", golden_names())
+@pytest.mark.parametrize("method", sorted(ALL_METHODS))
+def test_golden(name, method):
+    u, v, V, exp = load_golden(name)
+    got = ALL_METHODS[method](u, v, V)
+    assert got.tolist() == exp.tolist()
+
+
+def _random_tree(rng, n):
+    par = [int(rng.integers(0, i)) for i in range(1, n)]
+    return np.array(par, np.int32), np.arange(1, n, dtype=np.int32)
+
+
+@pytest.mark.parametrize("method", sorted(ALL_METHODS))
+def test_closed_forms(method):
+    f = ALL_METHODS[method]
+    rng = np.random.default_rng(11)
+    for n in [1, 2, 3, 7, 33, 64]:
+        # random recursive tree: every edge is a bridge
+        u, v = _random_tree(rng, n)
+        assert len(f(u, v, n)) == n - 1
+        # path of n-1 edges: n-1 bridges
+        u = np.arange(0, n - 1, dtype=np.int32)
+        v = u + 1
+        got = f(u, v, n)
+        assert got.tolist() == np.stack([u, v], 1).tolist()
+        # the same path with every edge doubled: no bridges
+        assert len(f(np.concatenate([u, v]), np.concatenate([v, u]), n)) == 0
+        if n >= 3:
+            # cycle: no bridges
+            u = np.arange(n, dtype=np.int32)
+            v = (u + 1) % n
+            assert len(f(u, v, n)) == 0
+            # complete graph: no bridges
+            pairs = np.array(list(itertools.combinations(range(n), 2)), np.int32)
+            assert len(f(pairs[:, 0], pairs[:, 1], n)) == 0
+            # star: every edge is a bridge
+            u = np.zeros(n - 1, np.int32)
+            v = np.arange(1, n, dtype=np.int32)
+            assert len(f(u, v, n)) == n - 1
+    # no edges / no vertices
+    e = np.zeros(0, np.int32)
+    assert len(f(e, e, 0)) == 0
+    assert len(f(e, e, 5)) == 0
+    # one self-loop
+    assert len(f(np.array([0], np.int32), np.array([0], np.int32), 1)) == 0
+
+
+def test_random_multigraphs_agree():
+    """Thousands of random multigraphs (self-loops and duplicates included), V <= 64."""
+    rng = np.random.default_rng(5)
+    for t in range(1500):
+        V = int(rng.integers(1, 65))
+        E = int(rng.integers(0, 3 * V + 2))
+        u, v = graphgen.random_multigraph(1000 + t, V, E)
+        ref = oracle.brute_bridges(u, v, V)
+        for name, f in ALL_METHODS.items():
+            if name == "brute":
+                continue
+            got = f(u, v, V)
+            assert got.tolist() == ref.tolist(), (t, name, V, E)
+
+
+def test_sparse_random_trees_plus_edges():
+    """Near-tree graphs, where most edges are bridges and the low/disc test decides each one."""
+    rng = np.random.default_rng(6)
+    for t in range(300):
+        n = int(rng.integers(2, 65))
+        u, v = _random_tree(rng, n)
+        k = int(rng.integers(0, 4))
+        xu = rng.integers(0, n, k).astype(np.int32)
+        xv = rng.integers(0, n, k).astype(np.int32)
+        u = np.concatenate([u, xu])
+        v = np.concatenate([v, xv])
+        perm = rng.permutation(len(u))
+        u, v = u[perm], v[perm]
+        ref = oracle.brute_bridges(u, v, n)
+        for M in (1, 2, 7):
+            assert oracle.bridges(u, v, n, M).tolist() == ref.tolist()
+        assert oracle.chain_bridges(u, v, n).tolist() == ref.tolist()
+
+
+@pytest.mark.parametrize("name", ["small", "mid"])
+def test_planted_bridges(name):
+    """The generators plant bridges whose status is known by construction."""
+    g = graphgen.workload(name)
+    got = oracle.bridges(g.u, g.v, g.V, 16)
+    # planted subset of found always; equal here because the ER clusters are 2-edge-connected
+    assert as_set(g.planted) <= as_set(got)
+    assert got.tolist() == g.planted.tolist()
+    assert oracle.chain_bridges(g.u, g.v, g.V).tolist() == got.tolist()
+
+
+def test_planted_counts_small():
+    """The small workload: 40 pendant vertices are bridges, and of the 7 cluster-tree edges only
+    those no inter-cluster pair covers (here exactly one, computed on the cluster tree)."""
+    g = graphgen.workload("small")
+    assert g.V == 2048 + 40
+    assert len(g.planted) == 41
+
+
+def _cert_invariants(u, v, V, ids, f1, M):
+    ids = np.asarray(ids)
+    # subset of the input, each input edge at most once (ids distinct)
+    assert len(np.unique(ids)) == len(ids)
+    assert ids.min(initial=0) >= 0 and ids.max(initial=-1) < len(u)
+    cu, cv = u[ids], v[ids]
+    c, lab = oracle.components(u, v, V)
+    c2, lab2 = oracle.components(cu, cv, V)
+    # same connected components
+    assert c == c2 and np.array_equal(lab, lab2)
+    # Lemma 1 (per component form): |S| <= 2(V - c)
+    assert len(ids) <= 2 * (V - c)
+    # F is a spanning forest: V - c edges, and acyclic (components of F equal those of S)
+    assert int(f1.sum()) == V - c
+    cf, labf = oracle.components(cu[f1], cv[f1], V)
+    assert cf == c and np.array_equal(labf, lab)
+    # same bridges (Sec. 3 "G(V, E u Y) = G(V, S u Y)" with Y empty)
+    assert oracle.dfs_bridges(cu, cv, V).tolist() == oracle.dfs_bridges(u, v, V).tolist()
+
+
+def test_certificate_invariants_random():
+    rng = np.random.default_rng(7)
+    for t in range(300):
+        V = int(rng.integers(1, 80))
+        E = int(rng.integers(0, 8 * V))
+        u, v = graphgen.random_multigraph(5000 + t, V, E)
+        ids, f1 = oracle.certificate(u, v, V)
+        _cert_invariants(u, v, V, ids, f1, 1)
+        for M in (2, 3, 8):
+            ids, f1, pm = oracle.pipeline_certificate(u, v, V, M)
+            _cert_invariants(u, v, V, ids, f1, M)
+            # Q = 1 + ceil(log2 M) phases, every intermediate |X_i| <= 2(V - 1)
+            assert len(pm) == 1 + int(np.ceil(np.log2(M)))
+            assert (pm <= 2 * max(V - 1, 0)).all()
+
+
+@pytest.mark.parametrize("M", [1, 4, 16, 33])
+def test_certificate_invariants_small_workload(M):
+    g = graphgen.workload("small")
+    ids, f1, pm = oracle.pipeline_certificate(g.u, g.v, g.V, M)
+    _cert_invariants(g.u, g.v, g.V, ids, f1, M)
+
+
+def test_certificate_cut_property():
+    """For every vertex set X, |delta_S(X)| >= min(|delta_E(X)|, 2) (the reading of the Sec. 3
+    certificate definition used throughout); checked exhaustively over all cuts of small graphs."""
+    rng = np.random.default_rng(8)
+    for t in range(60):
+        V = int(rng.integers(2, 11))
+        E = int(rng.integers(0, 4 * V))
+        u, v = graphgen.random_multigraph(9000 + t, V, E)
+        ids, _ = oracle.certificate(u, v, V)
+        cu, cv = u[ids], v[ids]
+        for mask in range(1, 1 << (V - 1)):
+            side = np.array([(mask >> i) & 1 for i in range(V)], bool)
+            de = int(np.sum(side[u] != side[v]))
+            ds = int(np.sum(side[cu] != side[cv]))
+            assert ds >= min(de, 2)
+
+
+def test_dropping_second_forest_is_caught():
+    """Planted mistake (in the oracle's inputs, on the CPU): keeping only F of Alg. 2 turns every
+    cycle edge into a 'bridge', which the invariant 'bridges(S) == bridges(E)' rejects."""
+    n = 6
+    u = np.arange(n, dtype=np.int32)
+    v = (u + 1) % n
+    ids, f1 = oracle.certificate(u, v, n)
+    only_f = ids[f1]
+    assert len(oracle.dfs_bridges(u[only_f], v[only_f], n)) == n - 1
+    assert len(oracle.dfs_bridges(u[ids], v[ids], n)) == 0
+
+
+def test_invalid_ids_rejected():
+    with pytest.raises(ValueError):
+        oracle.bridges(np.array([0], np.int32), np.array([5], np.int32), 3)
+    with pytest.raises(ValueError):
+        oracle.dfs_bridges(np.array([-1], np.int32), np.array([0], np.int32), 3)
