@@ -1,0 +1,162 @@
+/*
+ * bridges.h -- C ABI of libbridges.so: bridges of an undirected graph via sparse certificates
+ * on one GB300 GPU (sm_103a).
+ *
+ * Method (Kumar & Singh, "An Efficient Parallel Algorithm for finding Bridges in a Dense
+ * Graph", arXiv:2108.07346):
+ *   - a bridge is an edge whose removal increases the number of connected components (Sec. 1);
+ *   - the edge list is split into M partitions U_0..U_{M-1} (Sec. 3); each gets a sparse
+ *     certificate S = F u F', F a spanning forest of the partition and F' a spanning forest of
+ *     the remaining edges (Alg. 2, Sec. 4.B), |S| <= 2(V-1) (Lemma 1, Sec. 3);
+ *   - certificates are merged in a tree, each merge re-certifying the union (Sec. 3 phases);
+ *   - the bridges of the final certificate are the bridges of the graph (Sec. 3, end), found
+ *     here by an Euler tour with subtree low/high ranges in place of the DFS of Alg. 1.
+ *
+ * Conventions for every entry point:
+ *   - Edge lists are structure-of-arrays: edges_u[i], edges_v[i] (int32) is edge i, in either
+ *     order.  Self-loops are allowed and ignored; repeated edges are parallel edges (and hence
+ *     never bridges).  Vertex ids must lie in [0, V).
+ *   - Output bridges are written as interleaved (a, b) int32 pairs with a < b, sorted
+ *     ascending by (a, b); the result is unique, so it is exact and bit-reproducible.
+ *     Capacity needed: 2 * max(V-1, 0) int32.
+ *   - Pointers named "device" must be device pointers on the context's device; pointers named
+ *     "host" must be host pointers (pinned or pageable).  The caller owns every buffer; the
+ *     library never frees caller memory.  Input buffers are read-only during the call.
+ *   - Streams are cudaStream_t values passed as `struct CUstream_st*` (NULL = legacy stream).
+ *   - Return value: >= 0 on success (a count), or a negative bridges_status.  No C++
+ *     exception crosses this interface.  Device-side failures (bad vertex id, a bounded wait
+ *     that gave up) are reported through a device status word read back by the host; the
+ *     device never traps.
+ *   - A context is not thread-safe: use one per host thread (or serialise calls).
+ */
+#ifndef BRIDGES_H
+#define BRIDGES_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+struct CUstream_st;
+
+typedef enum bridges_status {
+  BRIDGES_OK = 0,
+  BRIDGES_EINVAL = -1,    /* null pointer, V < 0, E < 0, bad option */
+  BRIDGES_ERANGE = -2,    /* a vertex id outside [0, V) */
+  BRIDGES_ENOMEM = -3,    /* workspace larger than the context's budget, or allocation failed */
+  BRIDGES_ECUDA = -4,     /* a CUDA runtime call failed */
+  BRIDGES_ETIMEDOUT = -5, /* a bounded device-side wait gave up */
+  BRIDGES_EAGAIN = -6,    /* request can never fit the server's memory budget */
+  BRIDGES_EBUSY = -7,     /* result not ready yet */
+  BRIDGES_EINTERNAL = -8  /* an internal capacity invariant failed (a bug) */
+} bridges_status;
+
+/* Tuning options.  Zero-initialise and set what you need; zero / negative fields mean
+ * "choose automatically". */
+typedef struct bridges_opts {
+  int32_t M;           /* partitions of the edge list (Sec. 3 "M machines"); <= 0: auto */
+  int32_t fan_in;      /* certificates merged per merge job; <= 1: auto (Sec. 3 uses 2) */
+  int32_t block;       /* threads per block of the forest pass; 0: auto */
+  int32_t ctas_per_sm; /* resident blocks per SM for the forest pass; 0: auto */
+  int64_t warm_edges;  /* edges per partition certified before the label snapshot;
+                          < 0: auto, 0: never snapshot (every edge takes the union-find path) */
+  int32_t profile;     /* 1: record per-stage CUDA events on the launch stream */
+  int32_t reserved[7];
+} bridges_opts;
+
+typedef struct bridges_ctx bridges_ctx;
+
+/* ---------------------------------------------------------------------------------------
+ * Contexts.  A context owns a device workspace (grown on demand up to mem_budget_bytes, 0 =
+ * no limit) plus a small pinned host area.  bridges_ctx_create returns NULL on failure
+ * (bad device, CUDA error).  opts may be NULL (all automatic).
+ */
+bridges_ctx* bridges_ctx_create(int device, size_t mem_budget_bytes, const bridges_opts* opts);
+
+/* As bridges_ctx_create, but the caller supplies the device workspace (e.g. a framework's
+ * allocation); the context then never allocates device memory and returns BRIDGES_ENOMEM for
+ * a call that needs more than ws_bytes (see bridges_workspace_bytes).  ws must stay valid until
+ * bridges_ctx_destroy and must not be used by anything else meanwhile. */
+bridges_ctx* bridges_ctx_create_ws(int device, void* ws_device, size_t ws_bytes, const bridges_opts* opts);
+
+void bridges_ctx_destroy(bridges_ctx* ctx);
+
+/* Device workspace bytes a call with these sizes and the context's options needs (the value
+ * of M after automatic choice is used; M <= 0 picks it).  Returns 0 for invalid sizes. */
+size_t bridges_workspace_bytes(const bridges_ctx* ctx, int64_t E, int32_t V, int32_t M);
+
+/* ---------------------------------------------------------------------------------------
+ * bridges_find_ctx -- the whole path on device-resident input (Sec. 3 end to end).
+ *   edges_u, edges_v : device, E int32 each.
+ *   out_bridges      : device, capacity 2*max(V-1,0) int32; receives the sorted pairs.
+ *   out_count_device : device int64 or NULL; receives the bridge count (or a negative status).
+ *   M                : partitions (<= 0: the context's option, else automatic).
+ * Synchronous when out_count_device is NULL: waits for the stream and returns the count.
+ * When out_count_device is non-NULL the call only enqueues work and returns BRIDGES_OK (0);
+ * the count (or a negative status) appears in *out_count_device when the stream reaches it.
+ * Errors found on the host (EINVAL, ENOMEM) are returned in both modes.
+ */
+int64_t bridges_find_ctx(bridges_ctx* ctx, struct CUstream_st* stream, const int32_t* edges_u,
+                         const int32_t* edges_v, int64_t E, int32_t V, int32_t M, int32_t* out_bridges,
+                         int64_t* out_count_device);
+
+/* bridges_find -- plain synchronous call on device pointers, with a per-device default context
+ * (created on first use on the current device, workspace grown as needed) and the legacy
+ * stream.  Same arguments and result as bridges_find_ctx with out_count_device = NULL. */
+int64_t bridges_find(const int32_t* edges_u, const int32_t* edges_v, int64_t E, int32_t V, int32_t M,
+                     int32_t* out_bridges);
+
+/* bridges_find_host -- the same computation from HOST buffers: copies the edges to the
+ * context's device staging area on `stream`, runs the path, and copies the sorted bridges back
+ * to out_bridges_host.  Synchronous; returns the count.  Host buffers should be pinned for
+ * full copy bandwidth (pageable memory works, slower). */
+int64_t bridges_find_host(bridges_ctx* ctx, struct CUstream_st* stream, const int32_t* edges_u_host,
+                          const int32_t* edges_v_host, int64_t E, int32_t V, int32_t M,
+                          int32_t* out_bridges_host);
+
+/* ---------------------------------------------------------------------------------------
+ * Stage entry points (for testing and composition).
+ *
+ * bridges_certificate -- the sparse certificate of the whole edge list after the M-way
+ * partition and the merge tree (Sec. 3; Alg. 2 per job).  Writes |S| <= 2*max(V-1,0) edges:
+ * cert_u[i], cert_v[i] (device int32) and cert_tree[i] (device uint8: 1 = edge of the final
+ * spanning forest F, 0 = edge of F').  Synchronous; returns |S|.  Forests are not unique
+ * (concurrent union-find), but S always has the components and the bridges of the input.
+ */
+int64_t bridges_certificate(bridges_ctx* ctx, struct CUstream_st* stream, const int32_t* edges_u,
+                            const int32_t* edges_v, int64_t E, int32_t V, int32_t M, int32_t* cert_u,
+                            int32_t* cert_v, uint8_t* cert_tree);
+
+/* bridges_from_forest -- the final stage alone (the stand-in for Alg. 1 on X_0): given a
+ * spanning forest T (tree_u/tree_v, n_tree device int32 edges, acyclic, ids in [0,V)) and
+ * further edges (extra_u/extra_v, n_extra device int32, each joining two vertices of one tree
+ * of T), writes the sorted bridges of T u extra to out_bridges (device).  Synchronous; returns
+ * the count.  T must be a forest: a cycle in T gives an unspecified result (or
+ * BRIDGES_EINTERNAL), never a fault. */
+int64_t bridges_from_forest(bridges_ctx* ctx, struct CUstream_st* stream, const int32_t* tree_u,
+                            const int32_t* tree_v, int64_t n_tree, const int32_t* extra_u,
+                            const int32_t* extra_v, int64_t n_extra, int32_t V, int32_t* out_bridges);
+
+/* ---------------------------------------------------------------------------------------
+ * Introspection.
+ * bridges_ctx_stage_ms: per-stage device times (ms) of the context's last call, measured with
+ * CUDA events on the launch stream when opts.profile = 1: [0] partition warm-up, [1] label
+ * snapshot, [2] forest pass, [3] merge tree, [4] final stage (tree, tour, ranges, test, sort),
+ * [5] total.  Returns the number of values written (0 if profiling is off).
+ * bridges_ctx_launches: kernels launched by the context since creation.
+ * bridges_ctx_last_config: the M, fan-in, CTAs per partition, block size and warm-up edges
+ * of the last call (5 values).
+ * bridges_status_string: a static description of a status code.
+ */
+int32_t bridges_ctx_stage_ms(const bridges_ctx* ctx, float* ms, int32_t n);
+int64_t bridges_ctx_launches(const bridges_ctx* ctx);
+int32_t bridges_ctx_last_config(const bridges_ctx* ctx, int64_t* vals, int32_t n);
+const char* bridges_status_string(int32_t status);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* BRIDGES_H */

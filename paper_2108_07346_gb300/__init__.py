@@ -1,0 +1,250 @@
+"""Bridges of dense graphs via sparse certificates on one GB300 GPU (arXiv:2108.07346).
+
+A thin ctypes binding over ``libbridges.so`` (C ABI in ``include/bridges.h``).  Every step of
+the computation runs in the library's CUDA kernels; this module only marshals arguments.
+PyTorch supplies device memory (input/output tensors, optional workspace) and streams.  There
+is no CPU fallback: if the library cannot be built or loaded, every call raises.
+
+Functions keep the C names:
+
+* :func:`bridges_find` -- plain call on device tensors (default context, current stream).
+* :class:`Context` -- ``find`` (device tensors), ``find_host`` (host tensors, copies inside),
+  ``certificate`` (the Sec. 3 certificate), ``from_forest`` (the final stage alone), and the
+  introspection calls ``stage_ms``, ``launches``, ``last_config``.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import torch
+
+from . import build as _build
+
+_lib = None
+
+STATUS = {
+    0: "BRIDGES_OK",
+    -1: "BRIDGES_EINVAL",
+    -2: "BRIDGES_ERANGE",
+    -3: "BRIDGES_ENOMEM",
+    -4: "BRIDGES_ECUDA",
+    -5: "BRIDGES_ETIMEDOUT",
+    -6: "BRIDGES_EAGAIN",
+    -7: "BRIDGES_EBUSY",
+    -8: "BRIDGES_EINTERNAL",
+}
+
+
+class BridgesError(RuntimeError):
+    def __init__(self, code: int, what: str = ""):
+        self.code = int(code)
+        super().__init__(f"{what}: {STATUS.get(self.code, self.code)}")
+
+
+class Opts(ctypes.Structure):
+    _fields_ = [
+        ("M", ctypes.c_int32),
+        ("fan_in", ctypes.c_int32),
+        ("block", ctypes.c_int32),
+        ("ctas_per_sm", ctypes.c_int32),
+        ("warm_edges", ctypes.c_int64),
+        ("profile", ctypes.c_int32),
+        ("reserved", ctypes.c_int32 * 7),
+    ]
+
+
+_P = ctypes.c_void_p
+_I64 = ctypes.c_int64
+_I32 = ctypes.c_int32
+
+_SIGS = {
+    "bridges_ctx_create": (_P, [ctypes.c_int, ctypes.c_size_t, ctypes.POINTER(Opts)]),
+    "bridges_ctx_create_ws": (_P, [ctypes.c_int, _P, ctypes.c_size_t, ctypes.POINTER(Opts)]),
+    "bridges_ctx_destroy": (None, [_P]),
+    "bridges_workspace_bytes": (ctypes.c_size_t, [_P, _I64, _I32, _I32]),
+    "bridges_find_ctx": (_I64, [_P, _P, _P, _P, _I64, _I32, _I32, _P, _P]),
+    "bridges_find": (_I64, [_P, _P, _I64, _I32, _I32, _P]),
+    "bridges_find_host": (_I64, [_P, _P, _P, _P, _I64, _I32, _I32, _P]),
+    "bridges_certificate": (_I64, [_P, _P, _P, _P, _I64, _I32, _I32, _P, _P, _P]),
+    "bridges_from_forest": (_I64, [_P, _P, _P, _P, _I64, _P, _P, _I64, _I32, _P]),
+    "bridges_ctx_stage_ms": (_I32, [_P, ctypes.POINTER(ctypes.c_float), _I32]),
+    "bridges_ctx_launches": (_I64, [_P]),
+    "bridges_ctx_last_config": (_I32, [_P, ctypes.POINTER(ctypes.c_int64), _I32]),
+    "bridges_status_string": (ctypes.c_char_p, [_I32]),
+}
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True):
+    """Loads libbridges.so (building it from source first if it is missing or stale)."""
+    global _lib
+    if _lib is None:
+        if build_if_missing and _build.needs_build():
+            _build.build()
+        if not os.path.exists(_build.LIB):
+            raise RuntimeError(f"libbridges.so not found at {_build.LIB}; run __graft_entry__.build()")
+        lib = ctypes.CDLL(_build.LIB)
+        for name, (res, args) in _SIGS.items():
+            f = getattr(lib, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = lib
+    return _lib
+
+
+def exported_symbols():
+    return list(_SIGS)
+
+
+def _ptr(t):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def _dev_edges(u, v):
+    if not (isinstance(u, torch.Tensor) and isinstance(v, torch.Tensor)):
+        raise TypeError("edges must be torch tensors")
+    if u.dtype != torch.int32 or v.dtype != torch.int32 or u.shape != v.shape or u.dim() != 1:
+        raise ValueError("edges_u and edges_v must be 1-D int32 tensors of equal length")
+    if not (u.is_cuda and v.is_cuda):
+        raise ValueError("edges must be CUDA tensors (use Context.find_host for host input)")
+    return u.contiguous(), v.contiguous()
+
+
+def _check(rc, what):
+    rc = int(rc)
+    if rc < 0:
+        raise BridgesError(rc, what)
+    return rc
+
+
+def _stream(stream):
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+class Context:
+    """A libbridges context on one device.
+
+    ``workspace_bytes``: when given, the workspace is a torch allocation of that size and the
+    library never allocates device memory itself (calls that need more raise ENOMEM); otherwise
+    the library grows its own workspace up to ``mem_budget`` bytes (0: unlimited).
+    """
+
+    def __init__(self, device=None, M=0, fan_in=0, block=0, ctas_per_sm=0, warm_edges=-1, profile=False,
+                 mem_budget=0, workspace_bytes=None):
+        self._lib = load()
+        dev = torch.device("cuda", torch.cuda.current_device()) if device is None else torch.device(device)
+        self.device = dev
+        o = Opts()
+        o.M, o.fan_in, o.block, o.ctas_per_sm = M, fan_in, block, ctas_per_sm
+        o.warm_edges, o.profile = warm_edges, int(bool(profile))
+        self._opts = o
+        self._ws = None
+        with torch.cuda.device(dev):
+            if workspace_bytes is not None:
+                self._ws = torch.empty(int(workspace_bytes), dtype=torch.uint8, device=dev)
+                h = self._lib.bridges_ctx_create_ws(dev.index, _ptr(self._ws), int(workspace_bytes), ctypes.byref(o))
+            else:
+                h = self._lib.bridges_ctx_create(dev.index, int(mem_budget), ctypes.byref(o))
+        if not h:
+            raise BridgesError(-4, "bridges_ctx_create")
+        self._h = ctypes.c_void_p(h)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.bridges_ctx_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def workspace_bytes(self, E: int, V: int, M: int = 0) -> int:
+        return int(self._lib.bridges_workspace_bytes(self._h, E, V, M))
+
+    def find(self, u, v, V: int, M: int = 0, out=None, stream=None, count_device=None):
+        """bridges_find_ctx on device tensors.  Returns an (n, 2) int32 view of ``out``; with
+        ``count_device`` (a 1-element int64 CUDA tensor) the call is asynchronous and returns
+        ``out`` whole."""
+        u, v = _dev_edges(u, v)
+        if out is None:
+            out = torch.empty(2 * max(V - 1, 1), dtype=torch.int32, device=u.device)
+        rc = self._lib.bridges_find_ctx(self._h, _stream(stream), _ptr(u), _ptr(v), u.numel(), V, M, _ptr(out),
+                                        _ptr(count_device))
+        n = _check(rc, "bridges_find_ctx")
+        if count_device is not None:
+            return out
+        return out[: 2 * n].view(n, 2)
+
+    def find_host(self, u, v, V: int, M: int = 0, out=None, stream=None):
+        """bridges_find_host: host (ideally pinned) int32 tensors in, host bridges out."""
+        for t in (u, v):
+            if t.is_cuda or t.dtype != torch.int32 or t.dim() != 1:
+                raise ValueError("find_host takes 1-D int32 host tensors")
+        u, v = u.contiguous(), v.contiguous()
+        if out is None:
+            out = torch.empty(2 * max(V - 1, 1), dtype=torch.int32)
+        rc = self._lib.bridges_find_host(self._h, _stream(stream), _ptr(u), _ptr(v), u.numel(), V, M, _ptr(out))
+        n = _check(rc, "bridges_find_host")
+        return out[: 2 * n].view(n, 2)
+
+    def certificate(self, u, v, V: int, M: int = 0, stream=None):
+        """bridges_certificate: (cert_u, cert_v, cert_tree) device tensors of the final certificate."""
+        u, v = _dev_edges(u, v)
+        cap = 2 * max(V - 1, 1)
+        cu = torch.empty(cap, dtype=torch.int32, device=u.device)
+        cv = torch.empty(cap, dtype=torch.int32, device=u.device)
+        ct = torch.empty(cap, dtype=torch.uint8, device=u.device)
+        rc = self._lib.bridges_certificate(self._h, _stream(stream), _ptr(u), _ptr(v), u.numel(), V, M, _ptr(cu),
+                                           _ptr(cv), _ptr(ct))
+        n = _check(rc, "bridges_certificate")
+        return cu[:n], cv[:n], ct[:n].bool()
+
+    def from_forest(self, tu, tv, xu, xv, V: int, stream=None):
+        """bridges_from_forest: bridges of forest (tu, tv) plus extra edges (xu, xv)."""
+        tu, tv = _dev_edges(tu, tv)
+        xu, xv = _dev_edges(xu, xv)
+        out = torch.empty(2 * max(V - 1, 1), dtype=torch.int32, device=tu.device)
+        rc = self._lib.bridges_from_forest(self._h, _stream(stream), _ptr(tu), _ptr(tv), tu.numel(), _ptr(xu),
+                                           _ptr(xv), xu.numel(), V, _ptr(out))
+        n = _check(rc, "bridges_from_forest")
+        return out[: 2 * n].view(n, 2)
+
+    def stage_ms(self):
+        buf = (ctypes.c_float * 6)()
+        k = self._lib.bridges_ctx_stage_ms(self._h, buf, 6)
+        names = ["warmup", "snapshot", "forest", "merge", "final", "total"]
+        return {names[i]: float(buf[i]) for i in range(k)}
+
+    def launches(self) -> int:
+        return int(self._lib.bridges_ctx_launches(self._h))
+
+    def last_config(self):
+        buf = (ctypes.c_int64 * 5)()
+        k = self._lib.bridges_ctx_last_config(self._h, buf, 5)
+        names = ["M", "fan_in", "blocks_per_partition", "block", "warm_edges"]
+        return {names[i]: int(buf[i]) for i in range(k)}
+
+
+def bridges_find(u, v, V: int, M: int = 0, out=None):
+    """bridges_find: plain synchronous call on device tensors (default context, legacy stream)."""
+    lib = load()
+    u, v = _dev_edges(u, v)
+    if out is None:
+        out = torch.empty(2 * max(V - 1, 1), dtype=torch.int32, device=u.device)
+    with torch.cuda.device(u.device):
+        torch.cuda.current_stream().synchronize()
+        rc = lib.bridges_find(_ptr(u), _ptr(v), u.numel(), V, M, _ptr(out))
+    n = _check(rc, "bridges_find")
+    return out[: 2 * n].view(n, 2)
+
+
+def status_string(code: int) -> str:
+    return load().bridges_status_string(int(code)).decode()

@@ -1,0 +1,401 @@
+// api.cu -- the C ABI of libbridges (declared in include/bridges.h): contexts, workspace,
+// argument checks and the orchestration of the stages on one stream.
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <new>
+
+#include "../../include/bridges.h"
+#include "internal.h"
+
+using namespace bridges;
+
+struct bridges_ctx {
+  int device = 0;
+  size_t budget = 0;  // 0: unlimited
+  bool user_ws = false;
+  void* ws = nullptr;
+  size_t ws_bytes = 0;
+  // device staging for bridges_find_host
+  int32_t* stage = nullptr;
+  size_t stage_bytes = 0;
+  int64_t* h_pinned = nullptr;  // pinned host scratch (counts)
+  bridges_opts opts{};
+  int num_sms = 0;
+  size_t smem_optin = 0;
+  int64_t launches = 0;
+  cudaEvent_t ev[8]{};
+  bool events = false;
+  bool timings_pending = false;
+  float stage_ms[6]{};
+  int64_t last_cfg[5]{};
+};
+
+namespace {
+
+constexpr size_t kMiscBytes = 1024;  // status word, device counts of bridges_from_forest
+
+struct Carved {
+  int32_t* status;
+  int32_t* counts;  // [2]
+  CertBufs cert;
+  FinalBufs fin;
+};
+
+int64_t cuda_fail(cudaError_t e) {
+  (void)e;
+  cudaGetLastError();
+  return BRIDGES_ECUDA;
+}
+
+size_t total_bytes(const CertPlan& p) { return kMiscBytes + align_up(cert_bytes(p), 256) + final_bytes(p.V); }
+
+Carved carve(bridges_ctx* c, const CertPlan& p) {
+  Carved k{};
+  char* base = static_cast<char*>(c->ws);
+  k.status = reinterpret_cast<int32_t*>(base);
+  k.counts = reinterpret_cast<int32_t*>(base + 256);
+  k.cert = carve_cert(base + kMiscBytes, p);
+  k.cert.status = k.status;
+  k.fin = carve_final(base + kMiscBytes + align_up(cert_bytes(p), 256), p.V, k.status);
+  return k;
+}
+
+// Makes the workspace at least `need` bytes.  Waits for the context's previous work before
+// freeing an old, smaller workspace.
+int64_t ensure_ws(bridges_ctx* c, size_t need, cudaStream_t s) {
+  if (need <= c->ws_bytes) return BRIDGES_OK;
+  if (c->user_ws) return BRIDGES_ENOMEM;
+  if (c->budget && need + c->stage_bytes > c->budget) return BRIDGES_ENOMEM;
+  if (c->ws) {
+    cudaStreamSynchronize(s);
+    cudaDeviceSynchronize();
+    cudaFree(c->ws);
+    c->ws = nullptr;
+    c->ws_bytes = 0;
+  }
+  size_t bytes = align_up(need + need / 8, 1 << 20);
+  if (c->budget) bytes = std::min(bytes, c->budget - c->stage_bytes);
+  if (cudaMalloc(&c->ws, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    c->ws = nullptr;
+    return BRIDGES_ENOMEM;
+  }
+  c->ws_bytes = bytes;
+  return BRIDGES_OK;
+}
+
+CertPlan plan_for(const bridges_ctx* c, int64_t E, int32_t V, int32_t M) {
+  const bridges_opts& o = c->opts;
+  int32_t m = M > 0 ? M : o.M;
+  return make_plan(E, V, m, o.fan_in, o.block, o.ctas_per_sm, o.warm_edges < 0 ? -1 : (o.warm_edges == 0 ? 0 : o.warm_edges),
+                   c->num_sms, c->smem_optin);
+}
+
+void finish_timings(bridges_ctx* c) {
+  if (!c->timings_pending) return;
+  cudaEventSynchronize(c->ev[6]);
+  // [0] warm-up, [1] snapshot, [2] forest pass, [3] merge, [4] final, [5] total
+  const int pairs[6][2] = {{0, 1}, {1, 2}, {2, 3}, {3, 4}, {4, 5}, {6, 6}};
+  for (int i = 0; i < 5; i++) cudaEventElapsedTime(&c->stage_ms[i], c->ev[pairs[i][0]], c->ev[pairs[i][1]]);
+  cudaEventElapsedTime(&c->stage_ms[5], c->ev[7], c->ev[6]);
+  c->timings_pending = false;
+}
+
+int init_ctx(bridges_ctx* c, int device, const bridges_opts* opts) {
+  int n = 0;
+  if (cudaGetDeviceCount(&n) != cudaSuccess || device < 0 || device >= n) {
+    cudaGetLastError();
+    return -1;
+  }
+  c->device = device;
+  if (opts) c->opts = *opts;
+  if (!opts) c->opts.warm_edges = -1;
+  if (cudaSetDevice(device) != cudaSuccess) return -1;
+  cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device);
+  int optin = 0;
+  cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device);
+  c->smem_optin = (size_t)optin;
+  if (cudaMallocHost(&c->h_pinned, 64) != cudaSuccess) return -1;
+  if (c->opts.profile) {
+    for (auto& e : c->ev)
+      if (cudaEventCreate(&e) != cudaSuccess) return -1;
+    c->events = true;
+  }
+  return 0;
+}
+
+// The whole path on device-resident edges.  Leaves the count on the device (fin.count).
+int64_t run_path(bridges_ctx* c, cudaStream_t s, const int32_t* u, const int32_t* v, int64_t E, int32_t V, int32_t M,
+                 int32_t* out, Carved* kout, CertPlan* pout) {
+  CertPlan p = plan_for(c, E, V, M);
+  int64_t rc = ensure_ws(c, total_bytes(p), s);
+  if (rc != BRIDGES_OK) return rc;
+  Carved k = carve(c, p);
+  Launch L{s, &c->launches, c->num_sms, c->smem_optin};
+  c->last_cfg[0] = p.M;
+  c->last_cfg[1] = p.f;
+  c->last_cfg[2] = p.G;
+  c->last_cfg[3] = p.block;
+  c->last_cfg[4] = p.cache ? p.warm : -1;
+  cudaEvent_t* ev = c->events ? c->ev : nullptr;
+  if (ev) cudaEventRecord(c->ev[7], s);
+  cudaMemsetAsync(k.status, 0, sizeof(int32_t), s);
+  cert_init(L, p, k.cert);
+  cert_leaves(L, p, k.cert, u, v, ev);
+  if (ev && E == 0)
+    for (int i = 0; i < 4; i++) cudaEventRecord(c->ev[i], s);
+  cert_merge(L, p, k.cert);
+  if (ev) cudaEventRecord(c->ev[4], s);
+  if (out) {
+    // job 0 holds the final certificate: F (tree) and F' (extra); its UF1 roots the trees
+    final_stage(L, k.fin, V, k.cert.f1u, k.cert.f1v, k.cert.cnt + 0, V, k.cert.f2u, k.cert.f2v, k.cert.cnt + 1, V,
+                k.cert.P1, out);
+  }
+  if (ev) {
+    cudaEventRecord(c->ev[5], s);
+    cudaEventRecord(c->ev[6], s);
+    c->timings_pending = true;
+  }
+  if (cudaGetLastError() != cudaSuccess) return BRIDGES_ECUDA;
+  if (kout) *kout = k;
+  if (pout) *pout = p;
+  return BRIDGES_OK;
+}
+
+int64_t check_args(const bridges_ctx* c, const void* u, const void* v, int64_t E, int32_t V, const void* out) {
+  if (!c || E < 0 || V < 0) return BRIDGES_EINVAL;
+  if (E > 0 && (!u || !v)) return BRIDGES_EINVAL;
+  if (V > 1 && !out) return BRIDGES_EINVAL;
+  return BRIDGES_OK;
+}
+
+std::mutex g_default_mu[64];
+bridges_ctx* g_default[64];
+
+}  // namespace
+
+extern "C" {
+
+bridges_ctx* bridges_ctx_create(int device, size_t mem_budget_bytes, const bridges_opts* opts) {
+  bridges_ctx* c = new (std::nothrow) bridges_ctx();
+  if (!c) return nullptr;
+  c->budget = mem_budget_bytes;
+  if (init_ctx(c, device, opts) != 0) {
+    bridges_ctx_destroy(c);
+    return nullptr;
+  }
+  return c;
+}
+
+bridges_ctx* bridges_ctx_create_ws(int device, void* ws_device, size_t ws_bytes, const bridges_opts* opts) {
+  if (!ws_device || (reinterpret_cast<uintptr_t>(ws_device) & 255)) return nullptr;
+  bridges_ctx* c = new (std::nothrow) bridges_ctx();
+  if (!c) return nullptr;
+  c->user_ws = true;
+  c->ws = ws_device;
+  c->ws_bytes = ws_bytes;
+  if (init_ctx(c, device, opts) != 0) {
+    c->ws = nullptr;
+    bridges_ctx_destroy(c);
+    return nullptr;
+  }
+  return c;
+}
+
+void bridges_ctx_destroy(bridges_ctx* c) {
+  if (!c) return;
+  cudaSetDevice(c->device);
+  cudaDeviceSynchronize();
+  if (!c->user_ws && c->ws) cudaFree(c->ws);
+  if (c->stage) cudaFree(c->stage);
+  if (c->h_pinned) cudaFreeHost(c->h_pinned);
+  if (c->events)
+    for (auto& e : c->ev) cudaEventDestroy(e);
+  cudaGetLastError();
+  delete c;
+}
+
+size_t bridges_workspace_bytes(const bridges_ctx* c, int64_t E, int32_t V, int32_t M) {
+  if (!c || E < 0 || V < 0) return 0;
+  return total_bytes(plan_for(c, E, V, M));
+}
+
+int64_t bridges_find_ctx(bridges_ctx* c, struct CUstream_st* stream, const int32_t* u, const int32_t* v, int64_t E,
+                         int32_t V, int32_t M, int32_t* out, int64_t* out_count_device) {
+  int64_t rc = check_args(c, u, v, E, V, out);
+  if (rc) return rc;
+  if (V > (1 << 30)) return BRIDGES_EINVAL;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  if (cudaSetDevice(c->device) != cudaSuccess) return cuda_fail(cudaGetLastError());
+  finish_timings(c);
+  int32_t dummy_out[1];
+  Carved k{};
+  rc = run_path(c, s, u, v, E, V, M, out ? out : dummy_out, &k, nullptr);
+  if (rc) return rc;
+  if (out_count_device) {
+    if (cudaMemcpyAsync(out_count_device, k.fin.count, sizeof(int64_t), cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+      return cuda_fail(cudaGetLastError());
+    return BRIDGES_OK;
+  }
+  if (cudaMemcpyAsync(c->h_pinned, k.fin.count, sizeof(int64_t), cudaMemcpyDeviceToHost, s) != cudaSuccess)
+    return cuda_fail(cudaGetLastError());
+  if (cudaStreamSynchronize(s) != cudaSuccess) return cuda_fail(cudaGetLastError());
+  return c->h_pinned[0];
+}
+
+int64_t bridges_find(const int32_t* u, const int32_t* v, int64_t E, int32_t V, int32_t M, int32_t* out) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return cuda_fail(cudaGetLastError());
+  std::lock_guard<std::mutex> lock(g_default_mu[dev]);
+  if (!g_default[dev]) {
+    bridges_opts o{};
+    o.warm_edges = -1;
+    g_default[dev] = bridges_ctx_create(dev, 0, &o);
+    if (!g_default[dev]) return BRIDGES_ECUDA;
+  }
+  return bridges_find_ctx(g_default[dev], nullptr, u, v, E, V, M, out, nullptr);
+}
+
+int64_t bridges_find_host(bridges_ctx* c, struct CUstream_st* stream, const int32_t* hu, const int32_t* hv, int64_t E,
+                          int32_t V, int32_t M, int32_t* hout) {
+  int64_t rc = check_args(c, hu, hv, E, V, hout);
+  if (rc) return rc;
+  if (V > (1 << 30)) return BRIDGES_EINVAL;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  if (cudaSetDevice(c->device) != cudaSuccess) return cuda_fail(cudaGetLastError());
+  finish_timings(c);
+  // staging: u, v (E each) and the output (2V), 256-byte aligned pieces
+  const size_t eb = align_up(sizeof(int32_t) * (size_t)std::max<int64_t>(E, 1), 256);
+  const size_t ob = align_up(sizeof(int32_t) * 2 * (size_t)std::max(V, 1), 256);
+  const size_t need = 2 * eb + ob;
+  if (need > c->stage_bytes) {
+    if (c->user_ws) return BRIDGES_ENOMEM;
+    if (c->budget && need + c->ws_bytes > c->budget) return BRIDGES_ENOMEM;
+    if (c->stage) {
+      cudaStreamSynchronize(s);
+      cudaFree(c->stage);
+      c->stage = nullptr;
+      c->stage_bytes = 0;
+    }
+    if (cudaMalloc(&c->stage, need) != cudaSuccess) {
+      cudaGetLastError();
+      return BRIDGES_ENOMEM;
+    }
+    c->stage_bytes = need;
+  }
+  char* base = reinterpret_cast<char*>(c->stage);
+  int32_t* du = reinterpret_cast<int32_t*>(base);
+  int32_t* dv = reinterpret_cast<int32_t*>(base + eb);
+  int32_t* dout = reinterpret_cast<int32_t*>(base + 2 * eb);
+  if (E > 0) {
+    if (cudaMemcpyAsync(du, hu, sizeof(int32_t) * (size_t)E, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+        cudaMemcpyAsync(dv, hv, sizeof(int32_t) * (size_t)E, cudaMemcpyHostToDevice, s) != cudaSuccess)
+      return cuda_fail(cudaGetLastError());
+  }
+  Carved k{};
+  rc = run_path(c, s, du, dv, E, V, M, dout, &k, nullptr);
+  if (rc) return rc;
+  if (cudaMemcpyAsync(c->h_pinned, k.fin.count, sizeof(int64_t), cudaMemcpyDeviceToHost, s) != cudaSuccess)
+    return cuda_fail(cudaGetLastError());
+  if (cudaStreamSynchronize(s) != cudaSuccess) return cuda_fail(cudaGetLastError());
+  const int64_t n = c->h_pinned[0];
+  if (n > 0) {
+    if (cudaMemcpyAsync(hout, dout, sizeof(int32_t) * 2 * (size_t)n, cudaMemcpyDeviceToHost, s) != cudaSuccess)
+      return cuda_fail(cudaGetLastError());
+    if (cudaStreamSynchronize(s) != cudaSuccess) return cuda_fail(cudaGetLastError());
+  }
+  return n;
+}
+
+int64_t bridges_certificate(bridges_ctx* c, struct CUstream_st* stream, const int32_t* u, const int32_t* v, int64_t E,
+                            int32_t V, int32_t M, int32_t* cu, int32_t* cv, uint8_t* ct) {
+  int64_t rc = check_args(c, u, v, E, V, cu);
+  if (rc) return rc;
+  if (V > 1 && (!cv || !ct)) return BRIDGES_EINVAL;
+  if (V > (1 << 30)) return BRIDGES_EINVAL;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  if (cudaSetDevice(c->device) != cudaSuccess) return cuda_fail(cudaGetLastError());
+  finish_timings(c);
+  Carved k{};
+  CertPlan p{};
+  rc = run_path(c, s, u, v, E, V, M, nullptr, &k, &p);
+  if (rc) return rc;
+  if (V > 1) cert_export(Launch{s, &c->launches, c->num_sms, c->smem_optin}, p, k.cert, cu, cv, ct);
+  // counts and status
+  if (cudaMemcpyAsync(c->h_pinned, k.cert.cnt, 2 * sizeof(int32_t), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      cudaMemcpyAsync(c->h_pinned + 1, k.status, sizeof(int32_t), cudaMemcpyDeviceToHost, s) != cudaSuccess)
+    return cuda_fail(cudaGetLastError());
+  if (cudaStreamSynchronize(s) != cudaSuccess) return cuda_fail(cudaGetLastError());
+  const int32_t* h = reinterpret_cast<const int32_t*>(c->h_pinned);
+  const int32_t st = h[2];
+  if (st) return st;
+  const int64_t n = (int64_t)h[0] + h[1];
+  return std::min<int64_t>(n, 2 * (int64_t)std::max(V - 1, 0));
+}
+
+int64_t bridges_from_forest(bridges_ctx* c, struct CUstream_st* stream, const int32_t* tu, const int32_t* tv,
+                            int64_t n_tree, const int32_t* xu, const int32_t* xv, int64_t n_extra, int32_t V,
+                            int32_t* out) {
+  if (!c || V < 0 || n_tree < 0 || n_extra < 0) return BRIDGES_EINVAL;
+  if (n_tree > std::max(V - 1, 0)) return BRIDGES_EINVAL;
+  if ((n_tree > 0 && (!tu || !tv)) || (n_extra > 0 && (!xu || !xv)) || (V > 1 && !out)) return BRIDGES_EINVAL;
+  if (n_extra > INT32_MAX || V > (1 << 30)) return BRIDGES_EINVAL;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  if (cudaSetDevice(c->device) != cudaSuccess) return cuda_fail(cudaGetLastError());
+  finish_timings(c);
+  CertPlan p = make_plan(0, V, 1, 2, 0, 0, 0, c->num_sms, c->smem_optin);
+  int64_t rc = ensure_ws(c, total_bytes(p), s);
+  if (rc) return rc;
+  Carved k = carve(c, p);
+  Launch L{s, &c->launches, c->num_sms, c->smem_optin};
+  int32_t* h = reinterpret_cast<int32_t*>(c->h_pinned);
+  // the pinned scratch may still be read by an earlier copy on another stream: wait for it
+  cudaStreamSynchronize(s);
+  h[0] = (int32_t)n_tree;
+  h[1] = (int32_t)n_extra;
+  cudaMemsetAsync(k.status, 0, sizeof(int32_t), s);
+  cudaMemcpyAsync(k.counts, h, 2 * sizeof(int32_t), cudaMemcpyHostToDevice, s);
+  int32_t dummy[1];
+  final_stage(L, k.fin, V, tu, tv, k.counts, n_tree, xu, xv, k.counts + 1, n_extra, nullptr, out ? out : dummy);
+  if (cudaGetLastError() != cudaSuccess) return BRIDGES_ECUDA;
+  if (cudaMemcpyAsync(c->h_pinned + 1, k.fin.count, sizeof(int64_t), cudaMemcpyDeviceToHost, s) != cudaSuccess)
+    return cuda_fail(cudaGetLastError());
+  if (cudaStreamSynchronize(s) != cudaSuccess) return cuda_fail(cudaGetLastError());
+  return c->h_pinned[1];
+}
+
+int32_t bridges_ctx_stage_ms(const bridges_ctx* c, float* ms, int32_t n) {
+  if (!c || !c->events || !ms) return 0;
+  finish_timings(const_cast<bridges_ctx*>(c));
+  int32_t k = std::min<int32_t>(n, 6);
+  for (int i = 0; i < k; i++) ms[i] = c->stage_ms[i];
+  return k;
+}
+
+int64_t bridges_ctx_launches(const bridges_ctx* c) { return c ? c->launches : 0; }
+
+int32_t bridges_ctx_last_config(const bridges_ctx* c, int64_t* vals, int32_t n) {
+  if (!c || !vals) return 0;
+  int32_t k = std::min<int32_t>(n, 5);
+  for (int i = 0; i < k; i++) vals[i] = c->last_cfg[i];
+  return k;
+}
+
+const char* bridges_status_string(int32_t st) {
+  switch (st) {
+    case BRIDGES_OK: return "ok";
+    case BRIDGES_EINVAL: return "invalid argument";
+    case BRIDGES_ERANGE: return "vertex id outside [0, V)";
+    case BRIDGES_ENOMEM: return "workspace exceeds the memory budget or allocation failed";
+    case BRIDGES_ECUDA: return "CUDA runtime error";
+    case BRIDGES_ETIMEDOUT: return "bounded device wait gave up";
+    case BRIDGES_EAGAIN: return "request can never fit the memory budget";
+    case BRIDGES_EBUSY: return "result not ready";
+    case BRIDGES_EINTERNAL: return "internal invariant failed";
+    default: return "unknown status";
+  }
+}
+
+}  // extern "C"

@@ -1,0 +1,463 @@
+// certify.cu -- sparse certificates on the GPU: the partition forest pass and the merge tree.
+//
+// Sec. 3 splits the edge list into M sets U_i and certifies each (phase 0); Alg. 2 (Sec. 4.B)
+// certifies a set as S = F u F', F a spanning forest and F' a spanning forest of the rest.  On
+// one GPU a partition ("job") is a contiguous chunk of the edge list processed by G blocks that
+// share two concurrent union-finds in global memory (L2-resident): UF1 builds F and UF2 builds
+// F'.  Each edge is offered to UF1; if UF1 rejects it (its ends are already joined) it is
+// offered to UF2; if UF2 rejects it too, it is dropped.  Offering the rejected edges of F to
+// F' edge by edge is Alg. 2 with the edges taken in one arrival order: F ends up a spanning
+// forest of U_i and F' a spanning forest of U_i - F.  Concurrency changes which forests come
+// out, never their spanning property (see uf_link), and any pair of forests with that property
+// is a certificate: it keeps every cut of the input crossed min(cut, 2) times, so it keeps the
+// components and the bridges (Sec. 3, end).
+//
+// Dense partitions become one giant component after about V ln V edges, after which nearly all
+// edges are rejected by both forests.  To reject those from shared memory, each job first
+// certifies a warm-up prefix of its chunk through the union-finds, then takes a snapshot: a
+// 16-bit label per vertex naming its F' component (components with >= 2 vertices, up to 65,535
+// of them).  F' components nest inside F components (every F' edge joins two ends F already
+// joined), so two vertices with equal labels are joined in both forests and their edge can be
+// dropped exactly; connectivity only grows, so a stale snapshot is still sound.  Other edges
+// take the union-find path as before.
+//
+// The merge tree (Sec. 3 phases) certifies the union of f certificates per merge job.  The
+// first child's union-finds already encode its own certificate (every edge of a certificate
+// wins its forest when offered in order F then F'), so the merge job adopts them in place and
+// only offers the other children's edges, appending winners to the first child's lists.
+#include <algorithm>
+#include <cmath>
+
+#include "common.cuh"
+
+namespace bridges {
+
+namespace {
+
+struct Job {
+  int32_t* P1;
+  int32_t* P2;
+  int32_t* f1u;
+  int32_t* f1v;
+  int32_t* f2u;
+  int32_t* f2v;
+  int32_t* cnt;  // [2]
+};
+
+__device__ __forceinline__ Job job_of(const CertBufs& b, int32_t V, int64_t j) {
+  Job J;
+  int64_t o = j * (int64_t)V;
+  J.P1 = b.P1 + o;
+  J.P2 = b.P2 + o;
+  J.f1u = b.f1u + o;
+  J.f1v = b.f1v + o;
+  J.f2u = b.f2u + o;
+  J.f2v = b.f2v + o;
+  J.cnt = b.cnt + 2 * j;
+  return J;
+}
+
+// Offers edge (a, b) to F then F'.  Returns 0 (dropped), 1 (joined F) or 2 (joined F').
+__device__ __forceinline__ int offer(const Job& J, int32_t a, int32_t b) {
+  if (uf_link(J.P1, a, b)) return 1;
+  if (uf_link(J.P2, a, b)) return 2;
+  return 0;
+}
+
+// One edge slot for every lane of a warp.  `need` says whether this lane's edge must go to the
+// union-finds; winners are appended warp-aggregated.
+__device__ __forceinline__ void settle(const Job& J, bool need, int32_t a, int32_t b, int32_t cap,
+                                       int32_t* status) {
+  if (!__any_sync(kFull, need)) return;
+  int r = need ? offer(J, a, b) : 0;
+  warp_append(r == 1, a, b, J.cnt + 0, J.f1u, J.f1v, cap, status);
+  warp_append(r == 2, a, b, J.cnt + 1, J.f2u, J.f2v, cap, status);
+}
+
+// Decides whether a loaded edge needs the union-finds: out-of-range ids raise ERANGE and are
+// dropped, self-loops are dropped, and with the snapshot equal labels are dropped.
+template <bool CACHE>
+__device__ __forceinline__ bool needs_offer(bool valid, int32_t a, int32_t b, int32_t V, const uint16_t* slab,
+                                            int32_t* status) {
+  if (!valid) return false;
+  if ((uint32_t)a >= (uint32_t)V || (uint32_t)b >= (uint32_t)V) {
+    set_status(status, BRIDGES_ERANGE_CODE);
+    return false;
+  }
+  if (a == b) return false;
+  if (CACHE) {
+    uint16_t la = slab[a], lb = slab[b];
+    if (la == lb && la != kNoLabel) return false;
+  }
+  return true;
+}
+
+// Copies job j's label snapshot into shared memory.
+__device__ __forceinline__ void load_labels(uint16_t* slab, const uint16_t* glab, int64_t Vpad) {
+  const int4* src = reinterpret_cast<const int4*>(glab);
+  int4* dst = reinterpret_cast<int4*>(slab);
+  for (int64_t i = threadIdx.x; i < Vpad / 8; i += blockDim.x) dst[i] = src[i];
+  __syncthreads();
+}
+
+// Streams edges [s, t) of (u, v): vectorised 16-byte loads when both arrays are 16-byte
+// aligned, U int4 units (4U edges) in flight per thread.  Loop bounds are block-uniform so every
+// lane reaches the warp votes.
+template <bool CACHE, bool VEC, int U>
+__device__ __forceinline__ void stream_range(const Job& J, const int32_t* __restrict__ u,
+                                             const int32_t* __restrict__ v, int64_t s, int64_t t, int32_t V,
+                                             const uint16_t* slab, int32_t* status) {
+  const int32_t cap = V;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  int64_t s_al = s, t_al = s;
+  if (VEC) {
+    s_al = min((s + 3) & ~int64_t(3), t);
+    t_al = max(s_al, t & ~int64_t(3));
+  }
+  // scalar head [s, s_al)
+  for (int64_t i0 = s; i0 < s_al; i0 += nt) {
+    int64_t i = i0 + tid;
+    bool valid = i < s_al;
+    int32_t a = valid ? ld_stream1(u + i) : 0, b = valid ? ld_stream1(v + i) : 0;
+    settle(J, needs_offer<CACHE>(valid, a, b, V, slab, status), a, b, cap, status);
+  }
+  if (VEC) {
+    const int4* u4 = reinterpret_cast<const int4*>(u + s_al);
+    const int4* v4 = reinterpret_cast<const int4*>(v + s_al);
+    const int64_t nunits = (t_al - s_al) >> 2;
+    for (int64_t base = 0; base < nunits; base += (int64_t)nt * U) {
+      int4 ua[U], va[U];
+#pragma unroll
+      for (int k = 0; k < U; k++) {
+        int64_t idx = base + (int64_t)k * nt + tid;
+        if (idx < nunits) {
+          ua[k] = ld_stream4(u4 + idx);
+          va[k] = ld_stream4(v4 + idx);
+        } else {
+          ua[k] = make_int4(0, 0, 0, 0);
+          va[k] = make_int4(0, 0, 0, 0);
+        }
+      }
+#pragma unroll
+      for (int k = 0; k < U; k++) {
+        bool valid = base + (int64_t)k * nt + tid < nunits;
+        int32_t as[4] = {ua[k].x, ua[k].y, ua[k].z, ua[k].w};
+        int32_t bs[4] = {va[k].x, va[k].y, va[k].z, va[k].w};
+#pragma unroll
+        for (int c = 0; c < 4; c++) settle(J, needs_offer<CACHE>(valid, as[c], bs[c], V, slab, status), as[c], bs[c], cap, status);
+      }
+    }
+  }
+  // scalar tail [t_al, t)
+  for (int64_t i0 = t_al; i0 < t; i0 += nt) {
+    int64_t i = i0 + tid;
+    bool valid = i < t;
+    int32_t a = valid ? ld_stream1(u + i) : 0, b = valid ? ld_stream1(v + i) : 0;
+    settle(J, needs_offer<CACHE>(valid, a, b, V, slab, status), a, b, cap, status);
+  }
+}
+
+struct LeafArgs {
+  const int32_t* u;
+  const int32_t* v;
+  int64_t E;
+  int32_t V;
+  int32_t M;
+  int32_t G;
+  int64_t warm;
+  int32_t mode;  // 0: warm-up prefix of each chunk, 1: the rest of each chunk
+  CertBufs b;
+};
+
+// Forest pass over the partitions: block -> (job j = blockIdx / G, member m = blockIdx % G);
+// member m streams its share of job j's chunk [E j / M, E (j+1) / M) (Sec. 3 partition).
+template <bool CACHE, bool VEC>
+__global__ void __launch_bounds__(1024, 1) leaf_kernel(LeafArgs A) {
+  extern __shared__ __align__(16) uint16_t slab[];
+  const int64_t j = blockIdx.x / A.G, m = blockIdx.x % A.G;
+  const int64_t lo = A.E * j / A.M, hi = A.E * (j + 1) / A.M;
+  const int64_t w = min(A.warm, hi - lo);
+  const int64_t a = A.mode == 0 ? lo : lo + w;
+  const int64_t z = A.mode == 0 ? lo + w : hi;
+  const int64_t n = z - a;
+  const int64_t s = a + n * m / A.G, t = a + n * (m + 1) / A.G;
+  if (CACHE) load_labels(slab, A.b.lab + j * A.b.Vpad, A.b.Vpad);
+  Job J = job_of(A.b, A.V, j);
+  stream_range<CACHE, VEC, 4>(J, A.u, A.v, s, t, A.V, slab, A.b.status);
+}
+
+struct MergeArgs {
+  int32_t V;
+  int32_t M;
+  int32_t f;
+  int32_t G;
+  int64_t step;  // parent jobs are j * step
+  int64_t sub;   // children are parent + k * sub, k = 1 .. f-1
+  CertBufs b;
+};
+
+// One merge round (Sec. 3 phase q): parent job i adopts its own certificate and offers the
+// F and F' edges of children i + k*sub (k = 1..f-1, those < M).
+template <bool CACHE>
+__global__ void __launch_bounds__(1024) merge_kernel(MergeArgs A) {
+  extern __shared__ __align__(16) uint16_t slab[];
+  const int64_t jj = blockIdx.x / A.G, m = blockIdx.x % A.G;
+  const int64_t parent = jj * A.step;
+  if (CACHE) load_labels(slab, A.b.lab + parent * A.b.Vpad, A.b.Vpad);
+  Job J = job_of(A.b, A.V, parent);
+  const int tid = threadIdx.x, nt = blockDim.x;
+  for (int k = 1; k < A.f; k++) {
+    int64_t c = parent + k * A.sub;
+    if (c >= A.M) break;
+    Job C = job_of(A.b, A.V, c);
+    for (int which = 0; which < 2; which++) {
+      const int32_t n = min(C.cnt[which], A.V);  // capacity of a list slice
+      const int32_t* cu = which ? C.f2u : C.f1u;
+      const int32_t* cv = which ? C.f2v : C.f1v;
+      for (int64_t i0 = m * nt; i0 < n; i0 += (int64_t)A.G * nt) {
+        int64_t i = i0 + tid;
+        bool valid = i < n;
+        int32_t a = valid ? cu[i] : 0, b = valid ? cv[i] : 0;
+        settle(J, needs_offer<CACHE>(valid, a, b, A.V, slab, A.b.status), a, b, A.V, A.b.status);
+      }
+    }
+  }
+}
+
+__global__ void init_kernel(CertBufs b, int32_t V, int32_t M) {
+  const int64_t total = (int64_t)M * V;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+    int32_t x = (int32_t)(i % V);
+    b.P1[i] = x;
+    b.P2[i] = x;
+  }
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < 2 * (int64_t)M; i += (int64_t)gridDim.x * blockDim.x)
+    b.cnt[i] = 0;
+}
+
+// ---- label snapshot of F' for jobs j*step, j < njobs ----
+__global__ void snap_zero_kernel(CertBufs b, int32_t V, int64_t step, int64_t njobs) {
+  const int64_t total = njobs * V;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+    int64_t j = (i / V) * step;
+    b.tmp[j * V + i % V] = 0;
+    if (i % V == 0) b.nlab[j] = 0;
+  }
+}
+
+__global__ void snap_count_kernel(CertBufs b, int32_t V, int64_t step, int64_t njobs) {
+  const int64_t total = njobs * V;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+    int64_t j = (i / V) * step;
+    int32_t x = (int32_t)(i % V);
+    int32_t r = uf_find(b.P2 + j * V, x);
+    atomicAdd(b.tmp + j * V + r, 1);
+  }
+}
+
+constexpr int32_t kLabelFlag = 0x40000000;
+
+__global__ void snap_ids_kernel(CertBufs b, int32_t V, int64_t step, int64_t njobs) {
+  const int64_t total = njobs * V;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+    int64_t j = (i / V) * step;
+    int32_t x = (int32_t)(i % V);
+    if (ld_relaxed(b.P2 + j * V + x) != x) continue;  // roots do not change during a snapshot
+    int32_t* t = b.tmp + j * V + x;
+    int32_t c = *t;
+    int32_t val = 0;
+    if (c >= 2) {
+      int32_t id = atomicAdd(b.nlab + j, 1);
+      if (id < (int32_t)kNoLabel) val = kLabelFlag | id;
+    }
+    *t = val;
+  }
+}
+
+__global__ void snap_label_kernel(CertBufs b, int32_t V, int64_t step, int64_t njobs) {
+  const int64_t total = njobs * b.Vpad;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+    int64_t j = (i / b.Vpad) * step;
+    int64_t x = i % b.Vpad;
+    uint16_t l = kNoLabel;
+    if (x < V) {
+      int32_t r = uf_find(b.P2 + j * V, (int32_t)x);
+      int32_t t = b.tmp[j * V + r];
+      if (t & kLabelFlag) l = (uint16_t)(t & 0xffff);
+    }
+    b.lab[j * b.Vpad + x] = l;
+  }
+}
+
+__global__ void export_kernel(CertBufs b, int32_t cap, int32_t* cu, int32_t* cv, uint8_t* ct) {
+  const int32_t V = (cap + 2) / 2;  // each forest list holds at most V entries
+  const int32_t n1 = min(min(b.cnt[0], V), cap), n2 = min(min(b.cnt[1], V), cap - n1);
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < (int64_t)n1 + n2; i += (int64_t)gridDim.x * blockDim.x) {
+    if (i < n1) {
+      cu[i] = b.f1u[i];
+      cv[i] = b.f1v[i];
+      ct[i] = 1;
+    } else {
+      cu[i] = b.f2u[i - n1];
+      cv[i] = b.f2v[i - n1];
+      ct[i] = 0;
+    }
+  }
+}
+
+int grid_for(const Launch& L, int64_t work, int block) {
+  int64_t g = ceil_div(std::max<int64_t>(work, 1), block);
+  return (int)std::min<int64_t>(g, (int64_t)L.num_sms * 16);
+}
+
+void snapshot(const Launch& L, const CertPlan& p, const CertBufs& b, int64_t step, int64_t njobs) {
+  const int bs = 256;
+  int g = grid_for(L, njobs * (int64_t)p.V, bs);
+  snap_zero_kernel<<<g, bs, 0, L.stream>>>(b, p.V, step, njobs);
+  snap_count_kernel<<<g, bs, 0, L.stream>>>(b, p.V, step, njobs);
+  snap_ids_kernel<<<g, bs, 0, L.stream>>>(b, p.V, step, njobs);
+  snap_label_kernel<<<grid_for(L, njobs * b.Vpad, bs), bs, 0, L.stream>>>(b, p.V, step, njobs);
+  *L.launches += 4;
+}
+
+template <bool CACHE, bool VEC>
+void launch_leaf(const Launch& L, const CertPlan& p, const LeafArgs& a, size_t smem) {
+  auto k = leaf_kernel<CACHE, VEC>;
+  if (smem > 48 * 1024) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  k<<<(unsigned)((int64_t)p.M * p.G), p.block, smem, L.stream>>>(a);
+  *L.launches += 1;
+}
+
+}  // namespace
+
+CertPlan make_plan(int64_t E, int32_t V, int32_t M, int32_t fan_in, int32_t block, int32_t ctas_per_sm, int64_t warm,
+                   int num_sms, size_t smem_optin) {
+  CertPlan p{};
+  p.E = E;
+  p.V = V;
+  const double lnv = std::log((double)V + 1.0);
+  if (M <= 0) {
+    // Enough edges per partition to amortise its warm-up (about 2 V ln V edges), and no more
+    // partitions than resident blocks.
+    double per = 256.0 * V * lnv + 65536.0;
+    int64_t m = (int64_t)((double)E / per);
+    M = (int32_t)std::max<int64_t>(1, std::min<int64_t>(m, std::max(1, num_sms / 8)));
+  }
+  p.M = std::max(1, std::min(M, 65536));
+  p.f = fan_in > 1 ? fan_in : std::max(2, std::min(p.M, 16));
+  const int64_t Vpad = (int64_t)align_up((size_t)std::max(V, 1), 8);
+  const size_t lab_bytes = (size_t)Vpad * 2;
+  const bool fits = lab_bytes + 1024 <= smem_optin;
+  int cps = ctas_per_sm;
+  if (cps <= 0) {
+    cps = fits ? (int)std::max<size_t>(1, std::min<size_t>(4, (228 * 1024) / (lab_bytes + 2048))) : 2;
+  }
+  p.block = block > 0 ? block : (cps <= 2 ? 1024 : 512);
+  p.G = (int32_t)std::max<int64_t>(1, ((int64_t)num_sms * cps) / p.M);
+  const int64_t chunk = ceil_div(std::max<int64_t>(E, 1), p.M);
+  if (warm < 0) warm = (int64_t)std::ceil(2.0 * V * lnv) + 4096;
+  p.cache = fits && warm > 0 && warm < chunk;
+  p.warm = p.cache ? warm : chunk + 1;
+  return p;
+}
+
+size_t cert_bytes(const CertPlan& p) {
+  const size_t MV = (size_t)p.M * (size_t)std::max(p.V, 1);
+  const size_t Vpad = align_up((size_t)std::max(p.V, 1), 8);
+  size_t s = 0;
+  s += 256;                                         // status
+  s += align_up(sizeof(int32_t) * 2 * p.M, 256);    // cnt
+  s += align_up(sizeof(int32_t) * p.M, 256);        // nlab
+  s += 7 * align_up(sizeof(int32_t) * MV, 256);     // P1 P2 f1u f1v f2u f2v tmp
+  s += align_up(sizeof(uint16_t) * Vpad * p.M, 256);  // lab
+  return s;
+}
+
+CertBufs carve_cert(void* base, const CertPlan& p) {
+  CertBufs b{};
+  char* c = static_cast<char*>(base);
+  const size_t MV = (size_t)p.M * (size_t)std::max(p.V, 1);
+  const size_t Vpad = align_up((size_t)std::max(p.V, 1), 8);
+  b.status = reinterpret_cast<int32_t*>(c);
+  c += 256;
+  b.cnt = reinterpret_cast<int32_t*>(c);
+  c += align_up(sizeof(int32_t) * 2 * p.M, 256);
+  b.nlab = reinterpret_cast<int32_t*>(c);
+  c += align_up(sizeof(int32_t) * p.M, 256);
+  int32_t** arrs[7] = {&b.P1, &b.P2, &b.f1u, &b.f1v, &b.f2u, &b.f2v, &b.tmp};
+  for (auto a : arrs) {
+    *a = reinterpret_cast<int32_t*>(c);
+    c += align_up(sizeof(int32_t) * MV, 256);
+  }
+  b.lab = reinterpret_cast<uint16_t*>(c);
+  b.Vpad = (int64_t)Vpad;
+  return b;
+}
+
+void cert_init(const Launch& L, const CertPlan& p, const CertBufs& b) {
+  init_kernel<<<grid_for(L, (int64_t)p.M * p.V, 256), 256, 0, L.stream>>>(b, p.V, p.M);
+  *L.launches += 1;
+}
+
+void cert_leaves(const Launch& L, const CertPlan& p, const CertBufs& b, const int32_t* u, const int32_t* v,
+                 cudaEvent_t* ev) {
+  if (p.E == 0) return;
+  LeafArgs a{u, v, p.E, p.V, p.M, p.G, p.warm, 0, b};
+  const bool vec = ((reinterpret_cast<uintptr_t>(u) | reinterpret_cast<uintptr_t>(v)) & 15) == 0;
+  if (ev) cudaEventRecord(ev[0], L.stream);
+  if (vec)
+    launch_leaf<false, true>(L, p, a, 0);
+  else
+    launch_leaf<false, false>(L, p, a, 0);
+  if (ev) cudaEventRecord(ev[1], L.stream);
+  if (!p.cache) {
+    if (ev) {
+      cudaEventRecord(ev[2], L.stream);
+      cudaEventRecord(ev[3], L.stream);
+    }
+    return;
+  }
+  snapshot(L, p, b, 1, p.M);
+  if (ev) cudaEventRecord(ev[2], L.stream);
+  a.mode = 1;
+  const size_t smem = (size_t)b.Vpad * 2;
+  if (vec)
+    launch_leaf<true, true>(L, p, a, smem);
+  else
+    launch_leaf<true, false>(L, p, a, smem);
+  if (ev) cudaEventRecord(ev[3], L.stream);
+}
+
+void cert_merge(const Launch& L, const CertPlan& p, const CertBufs& b) {
+  const size_t smem = (size_t)b.Vpad * 2;
+  const bool fits = smem + 1024 <= L.smem_optin;
+  for (int64_t step = 1; step < p.M;) {
+    const int64_t sub = step;
+    step *= p.f;
+    const int64_t njobs = ceil_div(p.M, step);
+    // blocks per merge job: enough for (f-1) certificates of up to 2V edges, within the GPU
+    const int block = 512;
+    int64_t work = (int64_t)(p.f - 1) * 2 * p.V;
+    int64_t G = std::max<int64_t>(1, std::min<int64_t>(ceil_div(work, (int64_t)block * 8),
+                                                       std::max<int64_t>(1, (int64_t)L.num_sms * 2 / njobs)));
+    MergeArgs a{p.V, p.M, p.f, (int32_t)G, step, sub, b};
+    const bool cache = fits && work >= 4 * (int64_t)p.V;
+    if (cache) {
+      snapshot(L, p, b, step, njobs);
+      auto k = merge_kernel<true>;
+      if (smem > 48 * 1024) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      k<<<(unsigned)(njobs * G), block, smem, L.stream>>>(a);
+    } else {
+      merge_kernel<false><<<(unsigned)(njobs * G), block, 0, L.stream>>>(a);
+    }
+    *L.launches += 1;
+  }
+}
+
+void cert_export(const Launch& L, const CertPlan& p, const CertBufs& b, int32_t* cu, int32_t* cv, uint8_t* ct) {
+  const int32_t cap = 2 * std::max(p.V - 1, 0);
+  export_kernel<<<grid_for(L, 2 * (int64_t)p.V, 256), 256, 0, L.stream>>>(b, cap, cu, cv, ct);
+  *L.launches += 1;
+}
+
+}  // namespace bridges

@@ -1,0 +1,101 @@
+// common.cuh -- device helpers shared by the kernels of libbridges (union-find, status word,
+// warp compaction).  Nothing here is visible through the C ABI.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "internal.h"
+
+namespace bridges {
+
+constexpr unsigned kFull = 0xffffffffu;
+
+// First error wins; later errors leave the status unchanged.
+__device__ __forceinline__ void set_status(int32_t* status, int32_t code) { atomicCAS(status, 0, code); }
+
+__device__ __forceinline__ unsigned lanemask_lt() {
+  unsigned m;
+  asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+  return m;
+}
+
+// Relaxed, device-scope accesses to union-find parents that other blocks update concurrently.
+__device__ __forceinline__ int32_t ld_relaxed(const int32_t* p) {
+  int32_t v;
+  asm volatile("ld.relaxed.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ void st_relaxed(int32_t* p, int32_t v) {
+  asm volatile("st.relaxed.gpu.global.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// Read-only streaming loads of the edge list (never written during a call).
+__device__ __forceinline__ int4 ld_stream4(const int4* p) { return __ldcs(p); }
+__device__ __forceinline__ int32_t ld_stream1(const int32_t* p) { return __ldcs(p); }
+
+// ---------------------------------------------------------------------------------------------
+// Concurrent union-find on a parent array P[0..V) in global memory (Alg. 2's union-find,
+// Sec. 4.B, made concurrent as Sec. 7 suggests).
+//
+// Invariant: P[x] <= x for every x, i.e. a root is hooked only under a SMALLER root.  Hence the
+// parent graph is acyclic whatever the interleaving, the root of a set is its minimum vertex,
+// and a successful CAS P[a]: a -> b (a > b both roots when read) always joins two different
+// sets: if b were already in a's set its chain would lead to a, yet chains only descend.
+// Each successful link therefore adds one forest edge, so a forest gets at most V-1 links and
+// every CAS failure means another thread's link succeeded: the loops below terminate.
+// Path halving writes only ancestors into non-roots, which is safe under races.
+// ---------------------------------------------------------------------------------------------
+__device__ __forceinline__ int32_t uf_find(int32_t* P, int32_t x) {
+  while (true) {
+    int32_t p = ld_relaxed(P + x);
+    if (p == x) return x;
+    int32_t g = ld_relaxed(P + p);
+    if (g == p) return p;
+    st_relaxed(P + x, g);
+    x = g;
+  }
+}
+
+// Joins the sets of a and b.  Returns true iff they were different (the edge is a forest edge).
+__device__ __forceinline__ bool uf_link(int32_t* P, int32_t a, int32_t b) {
+  a = uf_find(P, a);
+  b = uf_find(P, b);
+  while (a != b) {
+    if (a < b) {
+      int32_t t = a;
+      a = b;
+      b = t;
+    }
+    int32_t old = atomicCAS(P + a, a, b);
+    if (old == a) return true;
+    a = uf_find(P, old);
+    b = uf_find(P, b);
+  }
+  return false;
+}
+
+// Warp-aggregated append of (a, b) to a list with a shared counter: one atomic per warp.
+// Every lane of the warp must call it (pred may be false).
+__device__ __forceinline__ void warp_append(bool pred, int32_t a, int32_t b, int32_t* cnt, int32_t* ou,
+                                            int32_t* ov, int32_t cap, int32_t* status) {
+  unsigned m = __ballot_sync(kFull, pred);
+  if (!m) return;
+  int lane = threadIdx.x & 31;
+  int leader = __ffs(m) - 1;
+  int32_t base = 0;
+  if (lane == leader) base = atomicAdd(cnt, __popc(m));
+  base = __shfl_sync(kFull, base, leader);
+  if (pred) {
+    int32_t i = base + __popc(m & lanemask_lt());
+    if (i < cap) {
+      ou[i] = a;
+      ov[i] = b;
+    } else {
+      set_status(status, BRIDGES_EINTERNAL_CODE);
+    }
+  }
+}
+
+}  // namespace bridges

@@ -1,0 +1,129 @@
+// internal.h -- host-side plumbing shared by the translation units of libbridges.
+// Nothing here is part of the C ABI.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#define BRIDGES_EINTERNAL_CODE (-8)
+#define BRIDGES_ERANGE_CODE (-2)
+#define BRIDGES_ETIMEDOUT_CODE (-5)
+
+namespace bridges {
+
+// Sentinel label: "no class", never equal to another vertex's label.
+constexpr uint16_t kNoLabel = 0xffff;
+
+// One launch context: the stream and the context's launch counter.
+struct Launch {
+  cudaStream_t stream;
+  int64_t* launches;
+  int num_sms;
+  size_t smem_optin;  // max dynamic shared memory per block
+};
+
+// Per-call plan for the certificate stages (Sec. 3): M partitions ("jobs"), G blocks per job,
+// merge fan-in f, warm-up edges per partition before the label snapshot.
+struct CertPlan {
+  int64_t E;
+  int32_t V;
+  int32_t M;
+  int32_t f;
+  int32_t G;       // blocks per job in the forest pass
+  int32_t block;   // threads per block in the forest pass
+  int64_t warm;    // edges per partition certified before the snapshot (>= partition: no cache)
+  bool cache;      // label snapshot used (2V bytes of shared memory fit)
+};
+
+// Device buffers of the certificate stages, carved from the workspace.  Job j owns the V-long
+// slices [j*V, (j+1)*V) of P1, P2, f1u, f1v, f2u, f2v, tmp and lab (lab stride Vpad).
+struct CertBufs {
+  int32_t* status;  // [1] device status word
+  int32_t* cnt;     // [2*M] forest sizes |F|, |F'| per job
+  int32_t* nlab;    // [M] labels handed out per job
+  int32_t* P1;
+  int32_t* P2;
+  int32_t* f1u;
+  int32_t* f1v;
+  int32_t* f2u;
+  int32_t* f2v;
+  int32_t* tmp;
+  uint16_t* lab;
+  int64_t Vpad;  // stride of lab
+};
+
+// Device buffers of the final stage (Euler tour, ranges, test, sort).
+struct FinalBufs {
+  int32_t* status;
+  int64_t* count;  // [1] bridges found (device)
+  int32_t* P;      // [V] union-find over the tree (built by the stage when owned_uf)
+  int32_t* root;   // [V]
+  int32_t* deg;    // [V]
+  int32_t* off;    // [V+1]
+  int32_t* cur;    // [V]
+  int32_t* dst;    // [2V]
+  int32_t* twin;   // [2V]
+  int32_t* succ;   // [2V]
+  int32_t* succ2;  // [2V]
+  int32_t* rnk;    // [2V]
+  int32_t* rnk2;   // [2V]
+  int32_t* aoff;   // [V+1] arc offset of each tree
+  int32_t* vbase;  // [V+1] preorder base of each tree
+  int32_t* dflag;  // [2V+1]
+  int32_t* dscan;  // [2V+1]
+  int32_t* pre;    // [V]
+  int32_t* sz;     // [V]
+  int32_t* par;    // [V] parent in the rooted tree (-1 for roots)
+  int32_t* stmin;  // [K*V] sparse tables of lo/hi over preorder (level 0: lo, hi themselves)
+  int32_t* stmax;  // [K*V]
+  int32_t K;
+  uint64_t* keys;   // [V]
+  uint64_t* keys2;  // [V]
+  int32_t* nkeys;   // [1]
+  int32_t* scan_tmp;  // scan scratch
+  size_t scan_tmp_elems;
+  uint32_t* hist;   // radix histograms
+  size_t hist_elems;
+};
+
+// ---- scan.cu ----
+// Exclusive prefix sum of n int32 values (out may equal in); out[n] receives the total when
+// write_total.  tmp must hold scan_tmp_elems(n) int32.
+size_t scan_tmp_elems(int64_t n);
+void exclusive_scan_i32(const Launch& L, const int32_t* in, int32_t* out, int64_t n, bool write_total, int32_t* tmp);
+// Sorts n (<= cap) unique 64-bit keys (count on device: *d_n) and writes them as (hi, lo)
+// int32 pairs to out.  key_bits bounds the significant bits.  keys2/hist are scratch.
+void sort_pairs(const Launch& L, uint64_t* keys, uint64_t* keys2, const int32_t* d_n, int64_t cap, int key_bits,
+                int32_t* out, uint32_t* hist, size_t hist_elems, int32_t* scan_tmp);
+size_t sort_hist_elems(int64_t cap);
+
+// ---- certify.cu ----
+void cert_init(const Launch& L, const CertPlan& p, const CertBufs& b);
+// Leaf certificates of the M partitions of (u, v) (Sec. 3 phase 0, Alg. 2 per partition).
+void cert_leaves(const Launch& L, const CertPlan& p, const CertBufs& b, const int32_t* u, const int32_t* v,
+                 cudaEvent_t* ev /* 4 events or null */);
+// Merge tree (Sec. 3 phases): fan-in f until one certificate remains in job 0.
+void cert_merge(const Launch& L, const CertPlan& p, const CertBufs& b);
+// Plan for (E, V, M) on this device.
+CertPlan make_plan(int64_t E, int32_t V, int32_t M, int32_t fan_in, int32_t block, int32_t ctas_per_sm,
+                   int64_t warm, int num_sms, size_t smem_optin);
+// Workspace bytes of the certificate stage.
+size_t cert_bytes(const CertPlan& p);
+CertBufs carve_cert(void* base, const CertPlan& p);
+// Copies job 0's certificate into caller arrays (u, v, tree flag), count on device in cnt[0..1].
+void cert_export(const Launch& L, const CertPlan& p, const CertBufs& b, int32_t* cu, int32_t* cv, uint8_t* ctree);
+
+// ---- final.cu ----
+size_t final_bytes(int32_t V);
+FinalBufs carve_final(void* base, int32_t V, int32_t* status);
+// Bridges of T u X (T a spanning forest of every tree it touches, X edges inside trees).
+// Counts on device.  P_tree: union-find of T (roots = minimum vertex), or null to build it.
+void final_stage(const Launch& L, const FinalBufs& fb, int32_t V, const int32_t* tu, const int32_t* tv,
+                 const int32_t* d_ntree, int64_t cap_tree, const int32_t* xu, const int32_t* xv,
+                 const int32_t* d_nextra, int64_t cap_extra, const int32_t* P_tree, int32_t* out);
+
+inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
+inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+}  // namespace bridges

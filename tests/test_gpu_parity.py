@@ -1,0 +1,226 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU oracle.
+
+Bridge sets are unique, so the sorted (a<b) list must match the oracle bit for bit.  Forests
+are not unique (concurrent union-find), so certificates are checked by their invariants:
+|S| <= 2(V - c), S a sub-multiset of the input, same components, same bridges.
+"""
+import numpy as np
+import pytest
+import torch
+
+import graphgen
+import oracle
+from conftest import golden_names, load_golden
+
+pytestmark = pytest.mark.gpu
+
+
+def dev_edges(u, v):
+    d = torch.device("cuda", 0)
+    return (torch.from_numpy(np.ascontiguousarray(u, dtype=np.int32)).to(d),
+            torch.from_numpy(np.ascontiguousarray(v, dtype=np.int32)).to(d))
+
+
+@pytest.fixture(scope="module")
+def ctx(cuda_lib):
+    return cuda_lib.Context(device="cuda:0")
+
+
+def gpu_bridges(ctx, u, v, V, M=0):
+    du, dv = dev_edges(u, v)
+    return ctx.find(du, dv, V, M).cpu().numpy()
+
+
+@pytest.mark.parametrize("name", golden_names())
+@pytest.mark.parametrize("M", [1, 2, 5])
+def test_golden(ctx, name, M):
+    u, v, V, exp = load_golden(name)
+    assert gpu_bridges(ctx, u, v, V, M).tolist() == exp.tolist()
+
+
+def test_random_multigraphs(ctx):
+    rng = np.random.default_rng(21)
+    for t in range(400):
+        V = int(rng.integers(1, 65))
+        E = int(rng.integers(0, 4 * V + 2))
+        u, v = graphgen.random_multigraph(20000 + t, V, E)
+        ref = oracle.brute_bridges(u, v, V)
+        M = int(rng.choice([1, 2, 3, 7, 16, 200]))
+        got = gpu_bridges(ctx, u, v, V, M)
+        assert got.tolist() == ref.tolist(), (t, V, E, M)
+
+
+def test_random_sparse_mid(ctx):
+    """Sparse random graphs (many bridges, many components) spanning several tiles."""
+    rng = np.random.default_rng(22)
+    for t in range(30):
+        V = int(rng.integers(100, 5000))
+        E = int(rng.integers(V // 2, 2 * V))
+        u, v = graphgen.random_multigraph(30000 + t, V, E)
+        ref = oracle.dfs_bridges(u, v, V)
+        for M in (1, 4, 33):
+            assert gpu_bridges(ctx, u, v, V, M).tolist() == ref.tolist(), (t, V, E, M)
+
+
+@pytest.mark.parametrize("M", [1, 2, 16, 64, 1000])
+def test_small_workload(ctx, M):
+    g = graphgen.workload("small")
+    got = gpu_bridges(ctx, g.u, g.v, g.V, M)
+    assert got.tolist() == oracle.bridges(g.u, g.v, g.V, 16).tolist()
+    assert got.tolist() == g.planted.tolist()
+
+
+@pytest.mark.parametrize("M", [16, 64, 256, 1024])
+def test_mid_workload_M_sweep(ctx, M):
+    g = graphgen.workload("mid")
+    got = gpu_bridges(ctx, g.u, g.v, g.V, M)
+    ref = oracle.bridges(g.u, g.v, g.V, 16)
+    assert got.tolist() == ref.tolist()
+    assert got.tolist() == g.planted.tolist()
+
+
+def test_trees_paths_stars(ctx):
+    """Closed forms at sizes that exercise the radix-sort path (more than 16k bridges)."""
+    rng = np.random.default_rng(23)
+    for n in (2, 1000, 20000, 70000):
+        par = (rng.random(n - 1) * np.arange(1, n)).astype(np.int32)
+        ch = np.arange(1, n, dtype=np.int32)
+        perm = rng.permutation(n - 1)
+        got = gpu_bridges(ctx, par[perm], ch[perm], n, 1)
+        exp = np.sort(np.stack([np.minimum(par, ch), np.maximum(par, ch)], 1).view(np.int64).ravel())
+        assert len(got) == n - 1
+        assert got.tolist() == oracle.dfs_bridges(par, ch, n).tolist()
+    n = 50000
+    u = np.arange(n - 1, dtype=np.int32)
+    assert len(gpu_bridges(ctx, u, u + 1, n, 3)) == n - 1  # path
+    assert len(gpu_bridges(ctx, np.concatenate([u, u + 1]), np.concatenate([u + 1, u]), n, 3)) == 0  # doubled
+    w = (u + 1) % (n - 1)
+    assert len(gpu_bridges(ctx, u, w, n, 2)) == 0  # cycle on n-1 vertices, vertex n-1 isolated
+    star = np.zeros(n - 1, np.int32)
+    assert len(gpu_bridges(ctx, star, u + 1, n, 4)) == n - 1
+
+
+def test_edge_cases(ctx, cuda_lib):
+    e = np.zeros(0, np.int32)
+    assert len(gpu_bridges(ctx, e, e, 0)) == 0
+    assert len(gpu_bridges(ctx, e, e, 10)) == 0
+    assert len(gpu_bridges(ctx, np.zeros(5, np.int32), np.zeros(5, np.int32), 1)) == 0  # self-loops
+    assert gpu_bridges(ctx, np.array([3], np.int32), np.array([1], np.int32), 4).tolist() == [[1, 3]]
+    # out-of-range ids -> ERANGE, and the context stays usable
+    with pytest.raises(cuda_lib.BridgesError) as ei:
+        gpu_bridges(ctx, np.array([0, 1], np.int32), np.array([1, 9], np.int32), 5)
+    assert ei.value.code == -2
+    with pytest.raises(cuda_lib.BridgesError):
+        gpu_bridges(ctx, np.array([-1], np.int32), np.array([1], np.int32), 5)
+    with pytest.raises(cuda_lib.BridgesError) as ei:
+        du, dv = dev_edges(np.array([0], np.int32), np.array([1], np.int32))
+        ctx.find(du, dv, -3)
+    assert ei.value.code == -1
+    assert gpu_bridges(ctx, np.array([0], np.int32), np.array([1], np.int32), 2).tolist() == [[0, 1]]
+
+
+def test_misaligned_and_offset_inputs(ctx):
+    """Pointers that are not 16-byte aligned (and misaligned relative to each other) take the
+    scalar load path; results are unchanged."""
+    g = graphgen.workload("small")
+    ref = oracle.bridges(g.u, g.v, g.V, 16)
+    du, dv = dev_edges(np.concatenate([[0], g.u]), np.concatenate([[0, 0, 0], g.v]))
+    u1, v1 = du[1:], dv[3:]
+    assert u1.data_ptr() % 16 != 0
+    assert ctx.find(u1, v1, g.V, 4).cpu().numpy().tolist() == ref.tolist()
+
+
+def test_repeatable(ctx):
+    g = graphgen.workload("mid")
+    du, dv = dev_edges(g.u, g.v)
+    first = ctx.find(du, dv, g.V, 32).cpu().numpy()
+    for _ in range(3):
+        assert np.array_equal(ctx.find(du, dv, g.V, 32).cpu().numpy(), first)
+
+
+def _cert_check(u, v, V, cu, cv, ct):
+    c, lab = oracle.components(u, v, V)
+    assert len(cu) <= 2 * (V - c)
+    # sub-multiset of the input (edges as unordered pairs)
+    key = lambda a, b: np.minimum(a, b).astype(np.int64) * V + np.maximum(a, b)
+    ku, kc = np.unique(key(u, v), return_counts=True)
+    cku, ckc = np.unique(key(cu, cv), return_counts=True)
+    pos = np.searchsorted(ku, cku)
+    assert (pos < len(ku)).all() and (ku[np.minimum(pos, len(ku) - 1)] == cku).all()
+    assert (ckc <= kc[pos]).all()
+    c2, lab2 = oracle.components(cu, cv, V)
+    assert c2 == c and np.array_equal(lab, lab2)
+    # the tree part is a spanning forest: V - c edges with the same components
+    assert int(ct.sum()) == V - c
+    c3, lab3 = oracle.components(cu[ct], cv[ct], V)
+    assert c3 == c and np.array_equal(lab3, lab)
+    assert oracle.dfs_bridges(cu, cv, V).tolist() == oracle.dfs_bridges(u, v, V).tolist()
+
+
+@pytest.mark.parametrize("name,M", [("small", 1), ("small", 16), ("mid", 8), ("mid", 300)])
+def test_certificate_invariants(ctx, name, M):
+    g = graphgen.workload(name)
+    du, dv = dev_edges(g.u, g.v)
+    cu, cv, ct = ctx.certificate(du, dv, g.V, M)
+    _cert_check(g.u, g.v, g.V, cu.cpu().numpy(), cv.cpu().numpy(), ct.cpu().numpy())
+
+
+def test_certificate_invariants_random(ctx):
+    for t in range(60):
+        V = 10 + 7 * t
+        u, v = graphgen.random_multigraph(40000 + t, V, 6 * V)
+        du, dv = dev_edges(u, v)
+        cu, cv, ct = ctx.certificate(du, dv, V, 1 + t % 9)
+        _cert_check(u, v, V, cu.cpu().numpy(), cv.cpu().numpy(), ct.cpu().numpy())
+
+
+def test_from_forest_matches_oracle(ctx):
+    """The final stage alone, fed the oracle's own certificate (Alg. 2 forests)."""
+    for name in ("small", "mid"):
+        g = graphgen.workload(name)
+        ids, f1 = oracle.certificate(g.u, g.v, g.V)
+        tu, tv = dev_edges(g.u[ids[f1]], g.v[ids[f1]])
+        xu, xv = dev_edges(g.u[ids[~f1]], g.v[ids[~f1]])
+        got = ctx.from_forest(tu, tv, xu, xv, g.V).cpu().numpy()
+        assert got.tolist() == oracle.dfs_bridges(g.u, g.v, g.V).tolist()
+
+
+def test_find_host_and_async(ctx, cuda_lib):
+    g = graphgen.workload("small")
+    ref = oracle.bridges(g.u, g.v, g.V, 16)
+    hu = torch.from_numpy(np.ascontiguousarray(g.u)).pin_memory()
+    hv = torch.from_numpy(np.ascontiguousarray(g.v)).pin_memory()
+    assert ctx.find_host(hu, hv, g.V, 8).numpy().tolist() == ref.tolist()
+    du, dv = dev_edges(g.u, g.v)
+    cnt = torch.zeros(1, dtype=torch.int64, device="cuda:0")
+    out = ctx.find(du, dv, g.V, 8, count_device=cnt)
+    torch.cuda.synchronize()
+    n = int(cnt.item())
+    assert out[: 2 * n].view(n, 2).cpu().numpy().tolist() == ref.tolist()
+
+
+def test_user_workspace_and_plain_call(cuda_lib):
+    g = graphgen.workload("small")
+    ref = oracle.bridges(g.u, g.v, g.V, 16)
+    probe = cuda_lib.Context(device="cuda:0")
+    need = probe.workspace_bytes(g.E, g.V, 4)
+    c2 = cuda_lib.Context(device="cuda:0", workspace_bytes=need)
+    du, dv = dev_edges(g.u, g.v)
+    assert c2.find(du, dv, g.V, 4).cpu().numpy().tolist() == ref.tolist()
+    with pytest.raises(cuda_lib.BridgesError) as ei:
+        c2.find(du, dv, g.V, 64)  # needs a bigger workspace than was given
+    assert ei.value.code == -3
+    assert cuda_lib.bridges_find(du, dv, g.V, 16).cpu().numpy().tolist() == ref.tolist()
+
+
+def test_stage_timings_and_launch_count(cuda_lib):
+    g = graphgen.workload("mid")
+    c = cuda_lib.Context(device="cuda:0", profile=True)
+    du, dv = dev_edges(g.u, g.v)
+    before = c.launches()
+    c.find(du, dv, g.V, 4)
+    ms = c.stage_ms()
+    assert set(ms) == {"warmup", "snapshot", "forest", "merge", "final", "total"}
+    assert ms["total"] > 0 and c.launches() > before
+    cfg = c.last_config()
+    assert cfg["M"] == 4
