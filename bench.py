@@ -1,0 +1,289 @@
+"""Benchmark: input edges/s to the exact bridge set on one GB300 (and N replicas under torchrun).
+
+A step is one pass of the whole path -- partition forest pass, label snapshot, merge tree,
+Euler tour / range test / sort -- over the large dense workload: an ER(65,536, 0.5) core with
+256 pendant trees and 128 two-edge vertices (about 1.07 G edges, 8.6 GB of int32 COO; seed 2).
+The inputs (8.6 GB) are larger than L2 (129 MB), so no flush is needed between steps.
+
+Prints one JSON line (rank 0).  ``--impl reference`` times the CPU oracle (the paper's
+pipeline, single-threaded C) on a bounded sample of the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import graphgen  # noqa: E402
+
+METRIC = "input edges/s to exact bridge set"
+UNIT = "GE/s"
+
+# DRAM bytes (read + write) of one forest-pass launch on the large workload, from the ncu capture
+# summarised in profiles/; valid only for the kernel source it was measured on.
+TRAFFIC = {"certify_sha": None, "bytes_per_edge": None}
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def certify_sha():
+    src = os.path.join(ROOT, "paper_2108_07346_gb300", "csrc", "certify.cu")
+    return hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.p = None
+
+    def start(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f,
+                                      stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return None
+        time.sleep(0.25)
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.p.kill()
+        self.f.flush()
+        rows = [ln.split(",") for ln in open(self.f.name).read().strip().splitlines() if ln.strip()]
+        os.unlink(self.f.name)
+        sm = [float(r[1]) for r in rows if len(r) >= 9 and r[1].strip().replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if len(r) >= 9 and r[2].strip().replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows if len(r) >= 9 for i in range(4) if "Active" in r[5 + i]})
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(sm)}
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def make_workload(args):
+    over = {}
+    if args.density is not None:
+        over["p"] = args.density
+    return graphgen.workload(args.workload, **over)
+
+
+def cpu_oracle_rate(g, M, sample_edges):
+    """The oracle (Sec. 3 pipeline + Alg. 1, single-threaded C) on the first `sample_edges` edges."""
+    import oracle
+
+    n = min(sample_edges, g.E)
+    u = np.ascontiguousarray(g.u[:n])
+    v = np.ascontiguousarray(g.v[:n])
+    t = time.perf_counter()
+    oracle.bridges(u, v, g.V, M)
+    dt = time.perf_counter() - t
+    return n / dt / 1e9, n, dt
+
+
+def run_reference(args, world, rank):
+    if rank != 0:
+        return
+    g = make_workload(args)
+    M = args.M if args.M > 0 else 5
+    per_step = args.ref_sample
+    for _ in range(args.warmup):
+        cpu_oracle_rate(g, M, max(per_step // 10, 1))
+    times = []
+    for _ in range(args.steps):
+        _, n, dt = cpu_oracle_rate(g, M, per_step)
+        times.append(dt)
+    tot = sum(times)
+    value = n * args.steps / tot / 1e9
+    sample = (f"oracle (Sec. 3 pipeline, M={M}, then Alg. 1; single-threaded C) on the first {n} edges of the "
+              f"{args.workload} workload per step")
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": tot / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+        "config": {"workload": args.workload, "V": g.V, "E": g.E, "sample_edges_per_step": n},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_native(args, world, rank, local):
+    import torch
+
+    import paper_2108_07346_gb300 as pb
+
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=dev)
+    g = make_workload(args)
+    E, V = g.E, g.V
+    du = torch.from_numpy(g.u).to(dev)
+    dv = torch.from_numpy(g.v).to(dev)
+    out = torch.empty(2 * max(V - 1, 1), dtype=torch.int32, device=dev)
+    cnt = torch.zeros(1, dtype=torch.int64, device=dev)
+    ctx = pb.Context(device=dev, profile=True, M=args.M)
+    stream = torch.cuda.current_stream(dev)
+
+    # correctness of what is timed: the planted bridges are exact on this workload
+    res = ctx.find(du, dv, V, args.M)
+    correct = bool(res.shape[0] == len(g.planted) and np.array_equal(res.cpu().numpy(), g.planted))
+    for _ in range(args.warmup):
+        ctx.find(du, dv, V, args.M, out=out, count_device=cnt, stream=stream)
+    torch.cuda.synchronize()
+
+    clocks = Clocks(local)
+    clocks.start()
+    l0 = ctx.launches()
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        ctx.find(du, dv, V, args.M, out=out, count_device=cnt, stream=stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    launches = ctx.launches() - l0
+    ms_total = e0.elapsed_time(e1)
+    hist = ctx.stage_ms_history(args.steps)
+    ck = clocks.stop()
+    if world > 1:
+        t = torch.tensor([ms_total], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms_total = float(t.item())
+    n_found = int(cnt.item())
+    ms_step = ms_total / args.steps
+    value = world * E * args.steps / (ms_total * 1e-3) / 1e9
+
+    cfg = ctx.last_config()
+    forest_ms = statistics.mean(h["forest"] for h in hist) if hist else None
+    forest_edges = E - cfg["M"] * max(cfg["warm_edges"], 0) if cfg["warm_edges"] > 0 else None
+    peak, peak_kind = peaks()
+    roof = None
+    if forest_ms and forest_edges:
+        achieved = 8.0 * forest_edges / (forest_ms * 1e-3) / 1e9
+        traffic = None
+        if TRAFFIC["certify_sha"] == certify_sha() and TRAFFIC["bytes_per_edge"]:
+            traffic = TRAFFIC["bytes_per_edge"] * forest_edges
+        roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": traffic, "kernel": "leaf_kernel<cache, vec> (partition forest pass)",
+                "algorithmic_bytes": 8 * forest_edges, "peak_kind": peak_kind,
+                "stage_ms_mean": {k: statistics.mean(h[k] for h in hist) for k in hist[0]}}
+
+    # end to end through the public API from pinned host buffers (copies inside the timed region)
+    e2e = None
+    if not args.no_e2e:
+        hu = torch.from_numpy(g.u).pin_memory()
+        hv = torch.from_numpy(g.v).pin_memory()
+        hout = torch.empty(2 * max(V - 1, 1), dtype=torch.int32).pin_memory()
+        ctx_h = pb.Context(device=dev, M=args.M)
+        ctx_h.find_host(hu, hv, V, args.M, out=hout)
+        ks = max(1, min(args.steps, args.e2e_steps))
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        nb = 0
+        for _ in range(ks):
+            nb = ctx_h.find_host(hu, hv, V, args.M, out=hout).shape[0]
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        if world > 1:
+            t = torch.tensor([dt], device=dev)
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            dt = float(t.item())
+        e2e = {"value": world * E * ks / dt / 1e9, "unit": UNIT, "h2d_bytes_per_step": 8 * E,
+               "d2h_bytes_per_step": 8 + 8 * nb, "steps": ks, "ms_per_step": dt / ks * 1e3}
+        del ctx_h
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        rate, n, dt = cpu_oracle_rate(g, cfg["M"], args.cpu_sample)
+        cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"Sec. 3 pipeline + Alg. 1 (single-threaded C) on the first {n} edges of the workload; "
+                         f"{dt:.1f} s"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+            "config": {"workload": f"{args.workload}: ER(65536, p={g.spec.p}) core + 256 pendant trees + 128 "
+                                   f"two-edge vertices, seed {g.spec.seed}" if args.workload == "large" else args.workload,
+                       "V": V, "E": E, "M": cfg["M"], "fan_in": cfg["fan_in"],
+                       "blocks_per_partition": cfg["blocks_per_partition"], "block": cfg["block"],
+                       "warm_edges": cfg["warm_edges"], "l2": "inputs (8E bytes) larger than L2; no flush",
+                       "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
+                       "bridges": n_found, "bridges_equal_planted": correct},
+            "clocks": ck, "e2e": e2e, "gpu_launches": launches, "roofline": roof, "cpu_baseline": cpu,
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["native", "reference"], default="native")
+    ap.add_argument("--workload", choices=["large", "mid", "small"], default="large")
+    ap.add_argument("--density", type=float, default=None, help="override the ER density (profiling)")
+    ap.add_argument("--M", type=int, default=0, help="partitions (0: automatic)")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--cpu-sample", type=int, default=200_000_000)
+    ap.add_argument("--ref-sample", type=int, default=50_000_000)
+    args = ap.parse_args()
+    world, rank, local = dist_setup()
+    if args.impl == "reference":
+        run_reference(args, world, rank)
+    else:
+        run_native(args, world, rank, local)
+
+
+if __name__ == "__main__":
+    main()

@@ -151,6 +151,10 @@ int64_t bridges_from_forest(bridges_ctx* ctx, struct CUstream_st* stream, const 
  * bridges_status_string: a static description of a status code.
  */
 int32_t bridges_ctx_stage_ms(const bridges_ctx* ctx, float* ms, int32_t n);
+/* bridges_ctx_stage_ms_history: the same six values for each of the context's last
+ * min(max_calls, 32) profiled calls, oldest first, 6 floats per call; returns the number of
+ * calls written.  Waits for those calls to finish. */
+int32_t bridges_ctx_stage_ms_history(const bridges_ctx* ctx, float* ms, int32_t max_calls);
 int64_t bridges_ctx_launches(const bridges_ctx* ctx);
 int32_t bridges_ctx_last_config(const bridges_ctx* ctx, int64_t* vals, int32_t n);
 const char* bridges_status_string(int32_t status);

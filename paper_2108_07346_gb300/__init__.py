@@ -69,6 +69,7 @@ _SIGS = {
     "bridges_certificate": (_I64, [_P, _P, _P, _P, _I64, _I32, _I32, _P, _P, _P]),
     "bridges_from_forest": (_I64, [_P, _P, _P, _P, _I64, _P, _P, _I64, _I32, _P]),
     "bridges_ctx_stage_ms": (_I32, [_P, ctypes.POINTER(ctypes.c_float), _I32]),
+    "bridges_ctx_stage_ms_history": (_I32, [_P, ctypes.POINTER(ctypes.c_float), _I32]),
     "bridges_ctx_launches": (_I64, [_P]),
     "bridges_ctx_last_config": (_I32, [_P, ctypes.POINTER(ctypes.c_int64), _I32]),
     "bridges_status_string": (ctypes.c_char_p, [_I32]),
@@ -222,6 +223,13 @@ class Context:
         k = self._lib.bridges_ctx_stage_ms(self._h, buf, 6)
         names = ["warmup", "snapshot", "forest", "merge", "final", "total"]
         return {names[i]: float(buf[i]) for i in range(k)}
+
+    def stage_ms_history(self, max_calls: int = 32):
+        """Stage times of the last min(max_calls, 32) profiled calls, oldest first."""
+        buf = (ctypes.c_float * (6 * max_calls))()
+        k = self._lib.bridges_ctx_stage_ms_history(self._h, buf, max_calls)
+        names = ["warmup", "snapshot", "forest", "merge", "final", "total"]
+        return [{names[j]: float(buf[6 * i + j]) for j in range(6)} for i in range(k)]
 
     def launches(self) -> int:
         return int(self._lib.bridges_ctx_launches(self._h))

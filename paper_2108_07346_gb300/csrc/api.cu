@@ -25,10 +25,13 @@ struct bridges_ctx {
   int num_sms = 0;
   size_t smem_optin = 0;
   int64_t launches = 0;
-  cudaEvent_t ev[8]{};
+  // profiling: a ring of kRing event sets, one per call; slot = call index % kRing
+  static constexpr int kRing = 32;
+  cudaEvent_t ev[kRing][8]{};
   bool events = false;
-  bool timings_pending = false;
-  float stage_ms[6]{};
+  int64_t calls = 0;         // profiled calls issued
+  int64_t resolved = 0;      // calls whose times have been read back
+  float stage_ms[kRing][6]{};
   int64_t last_cfg[5]{};
 };
 
@@ -93,14 +96,23 @@ CertPlan plan_for(const bridges_ctx* c, int64_t E, int32_t V, int32_t M) {
                    c->num_sms, c->smem_optin);
 }
 
-void finish_timings(bridges_ctx* c) {
-  if (!c->timings_pending) return;
-  cudaEventSynchronize(c->ev[6]);
-  // [0] warm-up, [1] snapshot, [2] forest pass, [3] merge, [4] final, [5] total
-  const int pairs[6][2] = {{0, 1}, {1, 2}, {2, 3}, {3, 4}, {4, 5}, {6, 6}};
-  for (int i = 0; i < 5; i++) cudaEventElapsedTime(&c->stage_ms[i], c->ev[pairs[i][0]], c->ev[pairs[i][1]]);
-  cudaEventElapsedTime(&c->stage_ms[5], c->ev[7], c->ev[6]);
-  c->timings_pending = false;
+// Reads back the stage times of every issued call up to (not including) call index `upto`.
+// [0] warm-up, [1] snapshot, [2] forest pass, [3] merge, [4] final, [5] total
+void resolve_timings(bridges_ctx* c, int64_t upto) {
+  for (; c->resolved < upto; c->resolved++) {
+    const int s = (int)(c->resolved % bridges_ctx::kRing);
+    cudaEvent_t* e = c->ev[s];
+    cudaEventSynchronize(e[6]);
+    for (int i = 0; i < 5; i++) cudaEventElapsedTime(&c->stage_ms[s][i], e[i], e[i + 1]);
+    cudaEventElapsedTime(&c->stage_ms[s][5], e[7], e[6]);
+  }
+}
+
+// Before a profiled call reuses a ring slot, the times of the call that last used it are read.
+cudaEvent_t* next_event_slot(bridges_ctx* c) {
+  if (!c->events) return nullptr;
+  resolve_timings(c, c->calls - bridges_ctx::kRing + 1);
+  return c->ev[c->calls % bridges_ctx::kRing];
 }
 
 int init_ctx(bridges_ctx* c, int device, const bridges_opts* opts) {
@@ -119,8 +131,9 @@ int init_ctx(bridges_ctx* c, int device, const bridges_opts* opts) {
   c->smem_optin = (size_t)optin;
   if (cudaMallocHost(&c->h_pinned, 64) != cudaSuccess) return -1;
   if (c->opts.profile) {
-    for (auto& e : c->ev)
-      if (cudaEventCreate(&e) != cudaSuccess) return -1;
+    for (auto& set : c->ev)
+      for (auto& e : set)
+        if (cudaEventCreate(&e) != cudaSuccess) return -1;
     c->events = true;
   }
   return 0;
@@ -139,24 +152,24 @@ int64_t run_path(bridges_ctx* c, cudaStream_t s, const int32_t* u, const int32_t
   c->last_cfg[2] = p.G;
   c->last_cfg[3] = p.block;
   c->last_cfg[4] = p.cache ? p.warm : -1;
-  cudaEvent_t* ev = c->events ? c->ev : nullptr;
-  if (ev) cudaEventRecord(c->ev[7], s);
+  cudaEvent_t* ev = next_event_slot(c);
+  if (ev) cudaEventRecord(ev[7], s);
   cudaMemsetAsync(k.status, 0, sizeof(int32_t), s);
   cert_init(L, p, k.cert);
   cert_leaves(L, p, k.cert, u, v, ev);
   if (ev && E == 0)
-    for (int i = 0; i < 4; i++) cudaEventRecord(c->ev[i], s);
+    for (int i = 0; i < 4; i++) cudaEventRecord(ev[i], s);
   cert_merge(L, p, k.cert);
-  if (ev) cudaEventRecord(c->ev[4], s);
+  if (ev) cudaEventRecord(ev[4], s);
   if (out) {
     // job 0 holds the final certificate: F (tree) and F' (extra); its UF1 roots the trees
     final_stage(L, k.fin, V, k.cert.f1u, k.cert.f1v, k.cert.cnt + 0, V, k.cert.f2u, k.cert.f2v, k.cert.cnt + 1, V,
                 k.cert.P1, out);
   }
   if (ev) {
-    cudaEventRecord(c->ev[5], s);
-    cudaEventRecord(c->ev[6], s);
-    c->timings_pending = true;
+    cudaEventRecord(ev[5], s);
+    cudaEventRecord(ev[6], s);
+    c->calls++;
   }
   if (cudaGetLastError() != cudaSuccess) return BRIDGES_ECUDA;
   if (kout) *kout = k;
@@ -212,7 +225,8 @@ void bridges_ctx_destroy(bridges_ctx* c) {
   if (c->stage) cudaFree(c->stage);
   if (c->h_pinned) cudaFreeHost(c->h_pinned);
   if (c->events)
-    for (auto& e : c->ev) cudaEventDestroy(e);
+    for (auto& set : c->ev)
+      for (auto& e : set) cudaEventDestroy(e);
   cudaGetLastError();
   delete c;
 }
@@ -229,7 +243,6 @@ int64_t bridges_find_ctx(bridges_ctx* c, struct CUstream_st* stream, const int32
   if (V > (1 << 30)) return BRIDGES_EINVAL;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   if (cudaSetDevice(c->device) != cudaSuccess) return cuda_fail(cudaGetLastError());
-  finish_timings(c);
   int32_t dummy_out[1];
   Carved k{};
   rc = run_path(c, s, u, v, E, V, M, out ? out : dummy_out, &k, nullptr);
@@ -265,7 +278,6 @@ int64_t bridges_find_host(bridges_ctx* c, struct CUstream_st* stream, const int3
   if (V > (1 << 30)) return BRIDGES_EINVAL;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   if (cudaSetDevice(c->device) != cudaSuccess) return cuda_fail(cudaGetLastError());
-  finish_timings(c);
   // staging: u, v (E each) and the output (2V), 256-byte aligned pieces
   const size_t eb = align_up(sizeof(int32_t) * (size_t)std::max<int64_t>(E, 1), 256);
   const size_t ob = align_up(sizeof(int32_t) * 2 * (size_t)std::max(V, 1), 256);
@@ -317,7 +329,6 @@ int64_t bridges_certificate(bridges_ctx* c, struct CUstream_st* stream, const in
   if (V > (1 << 30)) return BRIDGES_EINVAL;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   if (cudaSetDevice(c->device) != cudaSuccess) return cuda_fail(cudaGetLastError());
-  finish_timings(c);
   Carved k{};
   CertPlan p{};
   rc = run_path(c, s, u, v, E, V, M, nullptr, &k, &p);
@@ -344,7 +355,6 @@ int64_t bridges_from_forest(bridges_ctx* c, struct CUstream_st* stream, const in
   if (n_extra > INT32_MAX || V > (1 << 30)) return BRIDGES_EINVAL;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   if (cudaSetDevice(c->device) != cudaSuccess) return cuda_fail(cudaGetLastError());
-  finish_timings(c);
   CertPlan p = make_plan(0, V, 1, 2, 0, 0, 0, c->num_sms, c->smem_optin);
   int64_t rc = ensure_ws(c, total_bytes(p), s);
   if (rc) return rc;
@@ -367,11 +377,25 @@ int64_t bridges_from_forest(bridges_ctx* c, struct CUstream_st* stream, const in
 }
 
 int32_t bridges_ctx_stage_ms(const bridges_ctx* c, float* ms, int32_t n) {
-  if (!c || !c->events || !ms) return 0;
-  finish_timings(const_cast<bridges_ctx*>(c));
+  if (!c || !c->events || !ms || c->calls == 0) return 0;
+  bridges_ctx* m = const_cast<bridges_ctx*>(c);
+  resolve_timings(m, m->calls);
+  const int s = (int)((m->calls - 1) % bridges_ctx::kRing);
   int32_t k = std::min<int32_t>(n, 6);
-  for (int i = 0; i < k; i++) ms[i] = c->stage_ms[i];
+  for (int i = 0; i < k; i++) ms[i] = m->stage_ms[s][i];
   return k;
+}
+
+int32_t bridges_ctx_stage_ms_history(const bridges_ctx* c, float* ms, int32_t max_calls) {
+  if (!c || !c->events || !ms || max_calls <= 0) return 0;
+  bridges_ctx* m = const_cast<bridges_ctx*>(c);
+  resolve_timings(m, m->calls);
+  const int64_t n = std::min<int64_t>({(int64_t)max_calls, m->calls, (int64_t)bridges_ctx::kRing});
+  for (int64_t i = 0; i < n; i++) {
+    const int s = (int)((m->calls - n + i) % bridges_ctx::kRing);
+    for (int j = 0; j < 6; j++) ms[6 * i + j] = m->stage_ms[s][j];
+  }
+  return (int32_t)n;
 }
 
 int64_t bridges_ctx_launches(const bridges_ctx* c) { return c ? c->launches : 0; }
