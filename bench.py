@@ -51,7 +51,7 @@ def certify_sha():
 class Clocks:
     """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
 
-    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+    Q = ("timestamp,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
          "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
          "clocks_event_reasons.sw_power_cap")
 
@@ -63,10 +63,14 @@ class Clocks:
     def start(self):
         try:
             self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
-                                       "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f,
+                                       "--format=csv,noheader,nounits", "-lms", "100"], stdout=self.f,
                                       stderr=subprocess.DEVNULL)
         except OSError:
             self.p = None
+        time.sleep(0.5)  # let the sampler come up before the timed region
+
+    def mark(self, which):
+        setattr(self, which, time.time())
 
     def stop(self):
         if self.p is None:
@@ -78,16 +82,27 @@ class Clocks:
         except subprocess.TimeoutExpired:
             self.p.kill()
         self.f.flush()
-        rows = [ln.split(",") for ln in open(self.f.name).read().strip().splitlines() if ln.strip()]
+        rows = [[x.strip() for x in ln.split(",")] for ln in open(self.f.name).read().strip().splitlines()
+                if ln.strip()]
         os.unlink(self.f.name)
-        sm = [float(r[1]) for r in rows if len(r) >= 9 and r[1].strip().replace(".", "").isdigit()]
-        mx = [float(r[2]) for r in rows if len(r) >= 9 and r[2].strip().replace(".", "").isdigit()]
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        reasons = sorted({names[i] for r in rows if len(r) >= 9 for i in range(4) if "Active" in r[5 + i]})
-        if not sm:
+        t0, t1 = getattr(self, "t0", None), getattr(self, "t1", None)
+        samples = []
+        for r in rows:
+            if len(r) < 9:
+                continue
+            try:
+                ts = time.mktime(time.strptime(r[0].split(".")[0], "%Y/%m/%d %H:%M:%S"))
+                sm, mx = float(r[1]), float(r[2])
+            except ValueError:
+                continue
+            samples.append((ts, sm, mx, [names[i] for i in range(4) if r[5 + i] == "Active"]))
+        if not samples:
             return None
-        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
-                "samples": len(sm)}
+        inside = [x for x in samples if t0 is None or (t0 - 1.0 <= x[0] <= t1 + 1.0)] or samples
+        return {"sm_mhz": statistics.median(x[1] for x in inside), "sm_max_mhz": max(x[2] for x in inside),
+                "reasons": sorted({n for x in inside for n in x[3]}), "samples": len(inside),
+                "window_s": None if t0 is None else round(t1 - t0, 3)}
 
 
 def dist_setup():
@@ -173,6 +188,7 @@ def run_native(args, world, rank, local):
 
     clocks = Clocks(local)
     clocks.start()
+    clocks.mark("t0")
     l0 = ctx.launches()
     if world > 1:
         torch.distributed.barrier()
@@ -184,6 +200,7 @@ def run_native(args, world, rank, local):
         ctx.find(du, dv, V, args.M, out=out, count_device=cnt, stream=stream)
     e1.record(stream)
     torch.cuda.synchronize()
+    clocks.mark("t1")
     launches = ctx.launches() - l0
     ms_total = e0.elapsed_time(e1)
     hist = ctx.stage_ms_history(args.steps)
@@ -266,8 +283,8 @@ def run_native(args, world, rank, local):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
-    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["native", "reference"], default="native")
     ap.add_argument("--workload", choices=["large", "mid", "small"], default="large")
     ap.add_argument("--density", type=float, default=None, help="override the ER density (profiling)")
@@ -275,8 +292,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--cpu-sample", type=int, default=200_000_000)
-    ap.add_argument("--ref-sample", type=int, default=50_000_000)
+    ap.add_argument("--cpu-sample", type=int, default=2_000_000_000, help="oracle sample (edges; whole graph)")
+    ap.add_argument("--ref-sample", type=int, default=150_000_000, help="reference arm sample per step (edges)")
     args = ap.parse_args()
     world, rank, local = dist_setup()
     if args.impl == "reference":

@@ -74,22 +74,32 @@ __device__ __forceinline__ void settle(const Job& J, bool need, int32_t a, int32
   warp_append(r == 2, a, b, J.cnt + 1, J.f2u, J.f2v, cap, status);
 }
 
-// Decides whether a loaded edge needs the union-finds: out-of-range ids raise ERANGE and are
-// dropped, self-loops are dropped, and with the snapshot equal labels are dropped.
-template <bool CACHE>
-__device__ __forceinline__ bool needs_offer(bool valid, int32_t a, int32_t b, int32_t V, const uint16_t* slab,
-                                            int32_t* status) {
-  if (!valid) return false;
+// Range check and self-loop test of an edge that reached the union-find path.
+__device__ __forceinline__ bool checked(int32_t a, int32_t b, int32_t V, int32_t* status) {
   if ((uint32_t)a >= (uint32_t)V || (uint32_t)b >= (uint32_t)V) {
     set_status(status, BRIDGES_ERANGE_CODE);
     return false;
   }
-  if (a == b) return false;
-  if (CACHE) {
-    uint16_t la = slab[a], lb = slab[b];
-    if (la == lb && la != kNoLabel) return false;
+  return a != b;
+}
+
+// Scalar slot: every lane of the warp calls it (valid may be false).
+__device__ __forceinline__ void scalar_slot(const Job& J, bool valid, int32_t a, int32_t b, int32_t V,
+                                            const uint16_t* slab, bool cache, int32_t* status) {
+  bool need = valid;
+  if (need && cache) {
+    const uint16_t la = slab[min((uint32_t)a, (uint32_t)V)], lb = slab[min((uint32_t)b, (uint32_t)V)];
+    need = la == kNoLabel || la != lb;
   }
-  return true;
+  settle(J, need && checked(a, b, V, status), a, b, V, status);
+}
+
+// Fast-path test of one edge against the label snapshot.  Ids are clamped to V, whose label is
+// kNoLabel, so out-of-range ids (and unlabelled vertices) fall through to the checked path.
+__device__ __forceinline__ uint32_t miss_bit(int32_t a, int32_t b, int32_t V, const uint16_t* slab) {
+  const uint16_t la = slab[min((uint32_t)a, (uint32_t)V)];
+  const uint16_t lb = slab[min((uint32_t)b, (uint32_t)V)];
+  return (la == kNoLabel) | (la != lb);
 }
 
 // Copies job j's label snapshot into shared memory.
@@ -100,37 +110,63 @@ __device__ __forceinline__ void load_labels(uint16_t* slab, const uint16_t* glab
   __syncthreads();
 }
 
-// Streams edges [s, t) of (u, v): vectorised 16-byte loads when both arrays are 16-byte
-// aligned, U int4 units (4U edges) in flight per thread.  Loop bounds are block-uniform so every
-// lane reaches the warp votes.
+// The edges of this thread's current tile whose bit is set in `m` (bit 4k+c: element
+// 4*(base + k*nt + tid) + c of the range) go through the union-finds.  Kept out of line so the
+// streaming loop stays small; the edges are re-read (they are still in L1/L2).
+__device__ __noinline__ void offer_misses(const Job& J, uint32_t m, const int32_t* __restrict__ u,
+                                          const int32_t* __restrict__ v, int32_t base, int32_t V, int32_t* status) {
+  const int tid = threadIdx.x, nt = blockDim.x;
+  while (__any_sync(kFull, m != 0)) {
+    int32_t a = 0, b = 0;
+    bool go = false;
+    if (m) {
+      const int bit = __ffs(m) - 1;
+      m &= m - 1;
+      const int64_t e = 4 * ((int64_t)base + (int64_t)(bit >> 2) * nt + tid) + (bit & 3);
+      a = u[e];
+      b = v[e];
+      go = checked(a, b, V, status);
+    }
+    const int r = go ? offer(J, a, b) : 0;
+    warp_append(r == 1, a, b, J.cnt + 0, J.f1u, J.f1v, V, status);
+    warp_append(r == 2, a, b, J.cnt + 1, J.f2u, J.f2v, V, status);
+  }
+}
+
+// Streams edges [s, t) of (u, v): 16-byte loads when both arrays are 16-byte aligned, U int4
+// units (4U edges) in flight per thread.  With the snapshot, each edge costs two shared-memory
+// label reads; a per-thread bit mask collects the misses and one warp vote per tile decides
+// whether any lane must take the union-find path.  Loop bounds are block-uniform so every lane
+// reaches the votes.
 template <bool CACHE, bool VEC, int U>
 __device__ __forceinline__ void stream_range(const Job& J, const int32_t* __restrict__ u,
                                              const int32_t* __restrict__ v, int64_t s, int64_t t, int32_t V,
                                              const uint16_t* slab, int32_t* status) {
-  const int32_t cap = V;
+  static_assert(4 * U <= 32, "the miss mask holds 32 edges");
   const int tid = threadIdx.x, nt = blockDim.x;
   int64_t s_al = s, t_al = s;
   if (VEC) {
     s_al = min((s + 3) & ~int64_t(3), t);
     t_al = max(s_al, t & ~int64_t(3));
   }
-  // scalar head [s, s_al)
-  for (int64_t i0 = s; i0 < s_al; i0 += nt) {
-    int64_t i = i0 + tid;
-    bool valid = i < s_al;
-    int32_t a = valid ? ld_stream1(u + i) : 0, b = valid ? ld_stream1(v + i) : 0;
-    settle(J, needs_offer<CACHE>(valid, a, b, V, slab, status), a, b, cap, status);
+  for (int64_t i0 = s; i0 < s_al; i0 += nt) {  // scalar head
+    const int64_t i = i0 + tid;
+    const bool valid = i < s_al;
+    scalar_slot(J, valid, valid ? ld_stream1(u + i) : 0, valid ? ld_stream1(v + i) : 0, V, slab, CACHE, status);
   }
   if (VEC) {
-    const int4* u4 = reinterpret_cast<const int4*>(u + s_al);
-    const int4* v4 = reinterpret_cast<const int4*>(v + s_al);
-    const int64_t nunits = (t_al - s_al) >> 2;
-    for (int64_t base = 0; base < nunits; base += (int64_t)nt * U) {
+    const int32_t* ub = u + s_al;
+    const int32_t* vb = v + s_al;
+    const int4* u4 = reinterpret_cast<const int4*>(ub);
+    const int4* v4 = reinterpret_cast<const int4*>(vb);
+    const int32_t nunits = (int32_t)((t_al - s_al) >> 2);
+    for (int32_t base = 0; base < nunits; base += nt * U) {
+      const bool full = base + nt * U <= nunits;
       int4 ua[U], va[U];
 #pragma unroll
       for (int k = 0; k < U; k++) {
-        int64_t idx = base + (int64_t)k * nt + tid;
-        if (idx < nunits) {
+        const int32_t idx = base + k * nt + tid;
+        if (full || idx < nunits) {
           ua[k] = ld_stream4(u4 + idx);
           va[k] = ld_stream4(v4 + idx);
         } else {
@@ -138,24 +174,30 @@ __device__ __forceinline__ void stream_range(const Job& J, const int32_t* __rest
           va[k] = make_int4(0, 0, 0, 0);
         }
       }
+      uint32_t m = 0;
 #pragma unroll
       for (int k = 0; k < U; k++) {
-        bool valid = base + (int64_t)k * nt + tid < nunits;
-        int32_t as[4] = {ua[k].x, ua[k].y, ua[k].z, ua[k].w};
-        int32_t bs[4] = {va[k].x, va[k].y, va[k].z, va[k].w};
-#pragma unroll
-        for (int c = 0; c < 4; c++) settle(J, needs_offer<CACHE>(valid, as[c], bs[c], V, slab, status), as[c], bs[c], cap, status);
+        const bool valid = full || base + k * nt + tid < nunits;
+        uint32_t mk;
+        if (CACHE) {
+          mk = miss_bit(ua[k].x, va[k].x, V, slab) | (miss_bit(ua[k].y, va[k].y, V, slab) << 1) |
+               (miss_bit(ua[k].z, va[k].z, V, slab) << 2) | (miss_bit(ua[k].w, va[k].w, V, slab) << 3);
+        } else {
+          mk = 0xfu;
+        }
+        m |= (valid ? mk : 0u) << (4 * k);
       }
+      if (__any_sync(kFull, m != 0)) offer_misses(J, m, ub, vb, base, V, status);
     }
   }
-  // scalar tail [t_al, t)
-  for (int64_t i0 = t_al; i0 < t; i0 += nt) {
-    int64_t i = i0 + tid;
-    bool valid = i < t;
-    int32_t a = valid ? ld_stream1(u + i) : 0, b = valid ? ld_stream1(v + i) : 0;
-    settle(J, needs_offer<CACHE>(valid, a, b, V, slab, status), a, b, cap, status);
+  for (int64_t i0 = t_al; i0 < t; i0 += nt) {  // scalar tail
+    const int64_t i = i0 + tid;
+    const bool valid = i < t;
+    scalar_slot(J, valid, valid ? ld_stream1(u + i) : 0, valid ? ld_stream1(v + i) : 0, V, slab, CACHE, status);
   }
 }
+
+constexpr int kUnroll = 4;  // int4 units of u (and of v) in flight per thread: 16 edges
 
 struct LeafArgs {
   const int32_t* u;
@@ -183,7 +225,7 @@ __global__ void __launch_bounds__(1024, 1) leaf_kernel(LeafArgs A) {
   const int64_t s = a + n * m / A.G, t = a + n * (m + 1) / A.G;
   if (CACHE) load_labels(slab, A.b.lab + j * A.b.Vpad, A.b.Vpad);
   Job J = job_of(A.b, A.V, j);
-  stream_range<CACHE, VEC, 4>(J, A.u, A.v, s, t, A.V, slab, A.b.status);
+  stream_range<CACHE, VEC, kUnroll>(J, A.u, A.v, s, t, A.V, slab, A.b.status);
 }
 
 struct MergeArgs {
@@ -218,7 +260,7 @@ __global__ void __launch_bounds__(1024) merge_kernel(MergeArgs A) {
         int64_t i = i0 + tid;
         bool valid = i < n;
         int32_t a = valid ? cu[i] : 0, b = valid ? cv[i] : 0;
-        settle(J, needs_offer<CACHE>(valid, a, b, A.V, slab, A.b.status), a, b, A.V, A.b.status);
+        scalar_slot(J, valid, a, b, A.V, slab, CACHE, A.b.status);
       }
     }
   }
@@ -250,7 +292,7 @@ __global__ void snap_count_kernel(CertBufs b, int32_t V, int64_t step, int64_t n
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
     int64_t j = (i / V) * step;
     int32_t x = (int32_t)(i % V);
-    int32_t r = uf_find(b.P2 + j * V, x);
+    int32_t r = uf_find_static(b.P2 + j * V, x);
     atomicAdd(b.tmp + j * V + r, 1);
   }
 }
@@ -262,7 +304,7 @@ __global__ void snap_ids_kernel(CertBufs b, int32_t V, int64_t step, int64_t njo
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
     int64_t j = (i / V) * step;
     int32_t x = (int32_t)(i % V);
-    if (ld_relaxed(b.P2 + j * V + x) != x) continue;  // roots do not change during a snapshot
+    if (b.P2[j * V + x] != x) continue;  // roots do not change during a snapshot
     int32_t* t = b.tmp + j * V + x;
     int32_t c = *t;
     int32_t val = 0;
@@ -281,7 +323,7 @@ __global__ void snap_label_kernel(CertBufs b, int32_t V, int64_t step, int64_t n
     int64_t x = i % b.Vpad;
     uint16_t l = kNoLabel;
     if (x < V) {
-      int32_t r = uf_find(b.P2 + j * V, (int32_t)x);
+      int32_t r = uf_find_static(b.P2 + j * V, (int32_t)x);
       int32_t t = b.tmp[j * V + r];
       if (t & kLabelFlag) l = (uint16_t)(t & 0xffff);
     }
@@ -345,7 +387,7 @@ CertPlan make_plan(int64_t E, int32_t V, int32_t M, int32_t fan_in, int32_t bloc
   }
   p.M = std::max(1, std::min(M, 65536));
   p.f = fan_in > 1 ? fan_in : std::max(2, std::min(p.M, 16));
-  const int64_t Vpad = (int64_t)align_up((size_t)std::max(V, 1), 8);
+  const int64_t Vpad = (int64_t)align_up((size_t)V + 1, 8);  // entry V: the kNoLabel sentinel
   const size_t lab_bytes = (size_t)Vpad * 2;
   const bool fits = lab_bytes + 1024 <= smem_optin;
   int cps = ctas_per_sm;
@@ -363,7 +405,7 @@ CertPlan make_plan(int64_t E, int32_t V, int32_t M, int32_t fan_in, int32_t bloc
 
 size_t cert_bytes(const CertPlan& p) {
   const size_t MV = (size_t)p.M * (size_t)std::max(p.V, 1);
-  const size_t Vpad = align_up((size_t)std::max(p.V, 1), 8);
+  const size_t Vpad = align_up((size_t)p.V + 1, 8);
   size_t s = 0;
   s += 256;                                         // status
   s += align_up(sizeof(int32_t) * 2 * p.M, 256);    // cnt
@@ -377,7 +419,7 @@ CertBufs carve_cert(void* base, const CertPlan& p) {
   CertBufs b{};
   char* c = static_cast<char*>(base);
   const size_t MV = (size_t)p.M * (size_t)std::max(p.V, 1);
-  const size_t Vpad = align_up((size_t)std::max(p.V, 1), 8);
+  const size_t Vpad = align_up((size_t)p.V + 1, 8);
   b.status = reinterpret_cast<int32_t*>(c);
   c += 256;
   b.cnt = reinterpret_cast<int32_t*>(c);

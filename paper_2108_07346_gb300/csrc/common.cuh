@@ -58,22 +58,52 @@ __device__ __forceinline__ int32_t uf_find(int32_t* P, int32_t x) {
   }
 }
 
-// Joins the sets of a and b.  Returns true iff they were different (the edge is a forest edge).
-__device__ __forceinline__ bool uf_link(int32_t* P, int32_t a, int32_t b) {
-  a = uf_find(P, a);
-  b = uf_find(P, b);
-  while (a != b) {
-    if (a < b) {
-      int32_t t = a;
-      a = b;
-      b = t;
-    }
-    int32_t old = atomicCAS(P + a, a, b);
-    if (old == a) return true;
-    a = uf_find(P, old);
-    b = uf_find(P, b);
+// Root of x when no link can happen concurrently (snapshots, the final stage): roots are then
+// immutable, so their entries may come from L1 (ld.ca) and the many readers of one giant root
+// are served by each SM's L1 instead of queueing on one L2 slice.  Non-root entries read stale
+// are still ancestors, so the walk still ends at the root; halving uses plain stores.
+__device__ __forceinline__ int32_t uf_find_static(int32_t* P, int32_t x) {
+  int32_t p = __ldca(P + x);
+  while (p != x) {
+    const int32_t g = __ldca(P + p);
+    if (g == p) return p;
+    P[x] = g;
+    x = g;
+    p = __ldca(P + x);
   }
-  return false;
+  return x;
+}
+
+// Joins the sets of a and b.  Returns true iff they were different (the edge is a forest edge).
+//
+// Walks up from both ends comparing PARENTS, not roots: equal parents prove a common set, so in
+// the dense phase, where nearly every vertex points straight at its root, a rejection costs two
+// loads and never touches the root's own entry (which every block would otherwise hammer).  The
+// end with the larger parent moves up; when that end is itself a root x and the other end's
+// parent p is smaller, p cannot lie in x's set (members of a set are >= its root), so hooking
+// x under p joins two different sets even if p is not a root.
+__device__ __forceinline__ bool uf_link(int32_t* P, int32_t a, int32_t b) {
+  int32_t x = a, y = b;
+  while (true) {
+    int32_t px = ld_relaxed(P + x), py = ld_relaxed(P + y);
+    if (px == py) return false;
+    if (px < py) {
+      int32_t t = x;
+      x = y;
+      y = t;
+      t = px;
+      px = py;
+      py = t;
+    }
+    // now px > py
+    if (px == x) {
+      if (atomicCAS(P + x, x, py) == x) return true;
+      continue;  // x was hooked meanwhile: re-read its parent
+    }
+    const int32_t g = ld_relaxed(P + px);
+    if (g != px) st_relaxed(P + x, g);  // path halving
+    x = g;
+  }
 }
 
 // Warp-aggregated append of (a, b) to a list with a shared counter: one atomic per warp.

@@ -67,7 +67,7 @@ __global__ void fin_fill_kernel(FinalBufs f, int32_t V, const int32_t* tu, const
 
 __global__ void fin_root_kernel(FinalBufs f, int32_t V, const int32_t* P) {
   for (int64_t x = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; x < V; x += (int64_t)gridDim.x * blockDim.x)
-    f.root[x] = uf_find(const_cast<int32_t*>(P), (int32_t)x);
+    f.root[x] = uf_find_static(const_cast<int32_t*>(P), (int32_t)x);
 }
 
 // Euler tour successor of arc i = (x -> y): the arc after (y -> x) in y's list, cyclically.
