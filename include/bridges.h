@@ -140,6 +140,32 @@ int64_t bridges_from_forest(bridges_ctx* ctx, struct CUstream_st* stream, const 
                             const int32_t* extra_v, int64_t n_extra, int32_t V, int32_t* out_bridges);
 
 /* ---------------------------------------------------------------------------------------
+ * bridges_find_noalloc -- bridges_find for callers that must not allocate device memory.
+ *
+ * The paper has no counterpart; this is an interface for callers.  Some programs cannot call
+ * cudaMalloc at the point where they need bridges: the device allocator belongs to a framework
+ * (its caching allocator would be bypassed and could run out), a latency-critical loop must not
+ * block in the driver, or the process reserves all device memory up front.  This entry point
+ * allocates nothing: every intermediate buffer lives in one fixed 8 MiB array of device memory
+ * that is part of the library itself (each GPU that loads the library holds it until the process
+ * exits).  That bounds the graph: about 24,000 vertices with M <= 2, or 16,384 vertices with
+ * M <= 8 (the edge count is not limited by the array).  Larger graphs return BRIDGES_ENOMEM
+ * without running anything.
+ *
+ *   edges_u, edges_v, E, V, M, out_bridges, out_count_device : as for bridges_find_ctx, on the
+ *       current device; `stream` is the launch stream.  Synchronous (returns the count) when
+ *       out_count_device is NULL, otherwise enqueue-only (returns BRIDGES_OK).
+ *
+ * The first call on a device looks up the array's device address (cudaGetSymbolAddress); make
+ * that first call before capturing any stream into a CUDA graph.  All calls share the one
+ * array, and each call leaves its contents behind for the next: calls that can overlap on the
+ * GPU (different streams, or several host threads) race on it and must be serialised by the
+ * caller.  Calls on one stream are ordered and safe.
+ */
+int64_t bridges_find_noalloc(struct CUstream_st* stream, const int32_t* edges_u, const int32_t* edges_v, int64_t E,
+                             int32_t V, int32_t M, int32_t* out_bridges, int64_t* out_count_device);
+
+/* ---------------------------------------------------------------------------------------
  * Introspection.
  * bridges_ctx_stage_ms: per-stage device times (ms) of the context's last call, measured with
  * CUDA events on the launch stream when opts.profile = 1: [0] partition warm-up, [1] label

@@ -73,6 +73,7 @@ _SIGS = {
     "bridges_ctx_launches": (_I64, [_P]),
     "bridges_ctx_last_config": (_I32, [_P, ctypes.POINTER(ctypes.c_int64), _I32]),
     "bridges_status_string": (ctypes.c_char_p, [_I32]),
+    "bridges_find_noalloc": (_I64, [_P, _P, _P, _I64, _I32, _I32, _P, _P]),
 }
 
 
@@ -251,6 +252,20 @@ def bridges_find(u, v, V: int, M: int = 0, out=None):
         torch.cuda.current_stream().synchronize()
         rc = lib.bridges_find(_ptr(u), _ptr(v), u.numel(), V, M, _ptr(out))
     n = _check(rc, "bridges_find")
+    return out[: 2 * n].view(n, 2)
+
+
+def bridges_find_noalloc(u, v, V: int, M: int = 0, out=None, stream=None):
+    """bridges_find_noalloc: the same result as bridges_find, for callers that must not allocate
+    device memory (the library keeps all scratch in a fixed 8 MiB device array; graphs that need
+    more raise BridgesError ENOMEM).  Calls that may overlap on the GPU must be serialised."""
+    lib = load()
+    u, v = _dev_edges(u, v)
+    if out is None:
+        out = torch.empty(2 * max(V - 1, 1), dtype=torch.int32, device=u.device)
+    with torch.cuda.device(u.device):
+        rc = lib.bridges_find_noalloc(_stream(stream), _ptr(u), _ptr(v), u.numel(), V, M, _ptr(out), None)
+    n = _check(rc, "bridges_find_noalloc")
     return out[: 2 * n].view(n, 2)
 
 
