@@ -63,7 +63,10 @@ typedef struct bridges_opts {
   int64_t warm_edges;  /* edges per partition certified before the label snapshot;
                           < 0: auto, 0: never snapshot (every edge takes the union-find path) */
   int32_t profile;     /* 1: record per-stage CUDA events on the launch stream */
-  int32_t reserved[7];
+  int32_t host_read;   /* bridges_find_host: 1 = when the host buffers are pinned and mapped,
+                          kernels read them in place over the host link instead of copying
+                          them to the device first; 0 = always copy */
+  int32_t reserved[6];
 } bridges_opts;
 
 typedef struct bridges_ctx bridges_ctx;

@@ -50,7 +50,8 @@ class Opts(ctypes.Structure):
         ("ctas_per_sm", ctypes.c_int32),
         ("warm_edges", ctypes.c_int64),
         ("profile", ctypes.c_int32),
-        ("reserved", ctypes.c_int32 * 7),
+        ("host_read", ctypes.c_int32),
+        ("reserved", ctypes.c_int32 * 6),
     ]
 
 
@@ -138,13 +139,13 @@ class Context:
     """
 
     def __init__(self, device=None, M=0, fan_in=0, block=0, ctas_per_sm=0, warm_edges=-1, profile=False,
-                 mem_budget=0, workspace_bytes=None):
+                 mem_budget=0, workspace_bytes=None, host_read=False):
         self._lib = load()
         dev = torch.device("cuda", torch.cuda.current_device()) if device is None else torch.device(device)
         self.device = dev
         o = Opts()
         o.M, o.fan_in, o.block, o.ctas_per_sm = M, fan_in, block, ctas_per_sm
-        o.warm_edges, o.profile = warm_edges, int(bool(profile))
+        o.warm_edges, o.profile, o.host_read = warm_edges, int(bool(profile)), int(bool(host_read))
         self._opts = o
         self._ws = None
         with torch.cuda.device(dev):

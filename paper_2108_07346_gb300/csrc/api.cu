@@ -301,13 +301,27 @@ int64_t bridges_find_host(bridges_ctx* c, struct CUstream_st* stream, const int3
   int32_t* du = reinterpret_cast<int32_t*>(base);
   int32_t* dv = reinterpret_cast<int32_t*>(base + eb);
   int32_t* dout = reinterpret_cast<int32_t*>(base + 2 * eb);
-  if (E > 0) {
+  const int32_t* ru = du;
+  const int32_t* rv = dv;
+  bool in_place = false;
+  if (c->opts.host_read && E > 0) {
+    // pinned, mapped host memory can be streamed by the kernels directly
+    cudaPointerAttributes au{}, av{};
+    if (cudaPointerGetAttributes(&au, hu) == cudaSuccess && cudaPointerGetAttributes(&av, hv) == cudaSuccess &&
+        au.type == cudaMemoryTypeHost && av.type == cudaMemoryTypeHost && au.devicePointer && av.devicePointer) {
+      ru = static_cast<const int32_t*>(au.devicePointer);
+      rv = static_cast<const int32_t*>(av.devicePointer);
+      in_place = true;
+    }
+    cudaGetLastError();
+  }
+  if (E > 0 && !in_place) {
     if (cudaMemcpyAsync(du, hu, sizeof(int32_t) * (size_t)E, cudaMemcpyHostToDevice, s) != cudaSuccess ||
         cudaMemcpyAsync(dv, hv, sizeof(int32_t) * (size_t)E, cudaMemcpyHostToDevice, s) != cudaSuccess)
       return cuda_fail(cudaGetLastError());
   }
   Carved k{};
-  rc = run_path(c, s, du, dv, E, V, M, dout, &k, nullptr);
+  rc = run_path(c, s, ru, rv, E, V, M, dout, &k, nullptr);
   if (rc) return rc;
   if (cudaMemcpyAsync(c->h_pinned, k.fin.count, sizeof(int64_t), cudaMemcpyDeviceToHost, s) != cudaSuccess)
     return cuda_fail(cudaGetLastError());

@@ -278,54 +278,69 @@ __global__ void init_kernel(CertBufs b, int32_t V, int32_t M) {
 }
 
 // ---- label snapshot of F' for jobs j*step, j < njobs ----
-__global__ void snap_zero_kernel(CertBufs b, int32_t V, int64_t step, int64_t njobs) {
+// 1) flatten: P2[x] = root(x) (no link can run now, so roots are fixed and the walk is
+//    read-only); reset the per-root label ids (tmp) and the job's label counter.
+__global__ void snap_flatten_kernel(CertBufs b, int32_t V, int64_t step, int64_t njobs) {
   const int64_t total = njobs * V;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
-    int64_t j = (i / V) * step;
-    b.tmp[j * V + i % V] = 0;
-    if (i % V == 0) b.nlab[j] = 0;
-  }
-}
-
-__global__ void snap_count_kernel(CertBufs b, int32_t V, int64_t step, int64_t njobs) {
-  const int64_t total = njobs * V;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
-    int64_t j = (i / V) * step;
-    int32_t x = (int32_t)(i % V);
-    int32_t r = uf_find_static(b.P2 + j * V, x);
-    atomicAdd(b.tmp + j * V + r, 1);
-  }
-}
-
-constexpr int32_t kLabelFlag = 0x40000000;
-
-__global__ void snap_ids_kernel(CertBufs b, int32_t V, int64_t step, int64_t njobs) {
-  const int64_t total = njobs * V;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
-    int64_t j = (i / V) * step;
-    int32_t x = (int32_t)(i % V);
-    if (b.P2[j * V + x] != x) continue;  // roots do not change during a snapshot
-    int32_t* t = b.tmp + j * V + x;
-    int32_t c = *t;
-    int32_t val = 0;
-    if (c >= 2) {
-      int32_t id = atomicAdd(b.nlab + j, 1);
-      if (id < (int32_t)kNoLabel) val = kLabelFlag | id;
+    const int64_t j = (i / V) * step;
+    const int32_t x = (int32_t)(i % V);
+    int32_t* P2 = b.P2 + j * V;
+    int32_t r = x, p = __ldca(P2 + x);
+    while (p != r) {
+      r = p;
+      p = __ldca(P2 + r);
     }
-    *t = val;
+    P2[x] = r;
+    b.tmp[j * V + x] = -1;
+    if (x == 0) b.nlab[j] = 0;
   }
 }
 
-__global__ void snap_label_kernel(CertBufs b, int32_t V, int64_t step, int64_t njobs) {
+// 2) every non-root vertex labels itself with its root's id, handing out an id the first time a
+//    root is seen.  Lanes of a warp with the same root elect one lane, so a giant component's
+//    root entry is read once per warp, not once per vertex.
+__global__ void snap_members_kernel(CertBufs b, int32_t V, int64_t step, int64_t njobs) {
+  const int64_t total = njobs * V;
+  const int lane = threadIdx.x & 31;
+  for (int64_t base = blockIdx.x * (int64_t)blockDim.x; base < total; base += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = base + threadIdx.x;
+    const bool in = i < total;
+    const int64_t j = in ? (i / V) * step : 0;
+    const int32_t x = in ? (int32_t)(i % V) : 0;
+    const int32_t r = in ? b.P2[j * V + x] : x;
+    const bool member = in && r != x;
+    // key unique per (job, root); non-members get a key no other lane has
+    const long long key = member ? (long long)(j * V + r) : -1LL - lane;
+    const unsigned peers = __match_any_sync(kFull, (unsigned long long)key);
+    const int leader = __ffs(peers) - 1;
+    int32_t id = -1;
+    if (member && lane == leader) {
+      int32_t* slot = b.tmp + j * V + r;
+      id = ld_relaxed(slot);
+      if (id < 0) {
+        const int32_t fresh = atomicAdd(b.nlab + j, 1);
+        const int32_t old = atomicCAS(slot, -1, fresh);
+        id = old < 0 ? fresh : old;
+      }
+    }
+    id = __shfl_sync(kFull, id, leader);
+    if (member) b.lab[j * b.Vpad + x] = (id >= 0 && id < (int32_t)kNoLabel) ? (uint16_t)id : kNoLabel;
+  }
+}
+
+// 3) roots take their own id (kNoLabel for singletons); padding entries, including the
+//    sentinel at index V, are kNoLabel.
+__global__ void snap_roots_kernel(CertBufs b, int32_t V, int64_t step, int64_t njobs) {
   const int64_t total = njobs * b.Vpad;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
-    int64_t j = (i / b.Vpad) * step;
-    int64_t x = i % b.Vpad;
+    const int64_t j = (i / b.Vpad) * step;
+    const int64_t x = i % b.Vpad;
+    if (x < V && b.P2[j * V + x] != x) continue;  // members were labelled above
     uint16_t l = kNoLabel;
     if (x < V) {
-      int32_t r = uf_find_static(b.P2 + j * V, (int32_t)x);
-      int32_t t = b.tmp[j * V + r];
-      if (t & kLabelFlag) l = (uint16_t)(t & 0xffff);
+      const int32_t id = b.tmp[j * V + x];
+      if (id >= 0 && id < (int32_t)kNoLabel) l = (uint16_t)id;
     }
     b.lab[j * b.Vpad + x] = l;
   }
@@ -355,11 +370,10 @@ int grid_for(const Launch& L, int64_t work, int block) {
 void snapshot(const Launch& L, const CertPlan& p, const CertBufs& b, int64_t step, int64_t njobs) {
   const int bs = 256;
   int g = grid_for(L, njobs * (int64_t)p.V, bs);
-  snap_zero_kernel<<<g, bs, 0, L.stream>>>(b, p.V, step, njobs);
-  snap_count_kernel<<<g, bs, 0, L.stream>>>(b, p.V, step, njobs);
-  snap_ids_kernel<<<g, bs, 0, L.stream>>>(b, p.V, step, njobs);
-  snap_label_kernel<<<grid_for(L, njobs * b.Vpad, bs), bs, 0, L.stream>>>(b, p.V, step, njobs);
-  *L.launches += 4;
+  snap_flatten_kernel<<<g, bs, 0, L.stream>>>(b, p.V, step, njobs);
+  snap_members_kernel<<<g, bs, 0, L.stream>>>(b, p.V, step, njobs);
+  snap_roots_kernel<<<grid_for(L, njobs * b.Vpad, bs), bs, 0, L.stream>>>(b, p.V, step, njobs);
+  *L.launches += 3;
 }
 
 template <bool CACHE, bool VEC>
@@ -397,7 +411,8 @@ CertPlan make_plan(int64_t E, int32_t V, int32_t M, int32_t fan_in, int32_t bloc
   p.block = block > 0 ? block : (cps <= 2 ? 1024 : 512);
   p.G = (int32_t)std::max<int64_t>(1, ((int64_t)num_sms * cps) / p.M);
   const int64_t chunk = ceil_div(std::max<int64_t>(E, 1), p.M);
-  if (warm < 0) warm = (int64_t)std::ceil(2.0 * V * lnv) + 4096;
+  // about the number of random edges after which F' holds a giant component in a dense partition
+  if (warm < 0) warm = (int64_t)std::ceil(0.6 * V * lnv) + 4096;
   p.cache = fits && warm > 0 && warm < chunk;
   p.warm = p.cache ? warm : chunk + 1;
   return p;

@@ -9,10 +9,17 @@
 // test as Alg. 1's low[v] > disc[u], evaluated for all tree edges at once (Tarjan 1974;
 // Tarjan & Vishkin 1985).
 //
-// Steps: tree adjacency (degrees, scan, fill) -> Euler tour successors, cut at each tree's root
-// (its minimum vertex) -> list ranking by pointer jumping -> tour positions -> preorder and
-// subtree sizes (scan of "down" arcs) -> lo/hi by atomics over X -> sparse tables for range
-// min/max -> test -> sort.
+// The whole stage is ONE cooperative kernel (every block resident) whose phases are separated
+// by a software grid barrier; the work per phase is small (O(V)), so launch overhead, not
+// bandwidth, would dominate a kernel-per-phase design.  Phases:
+//   tree degrees -> scan -> adjacency + roots -> Euler-tour successors (cut at each tree's root,
+//   its minimum vertex) -> list ranking by pointer jumping -> tour positions -> preorder and
+//   subtree sizes (scan of "down" arcs) -> lo/hi (atomics over X) -> range min/max structure
+//   (32-element chunks, superchunks of >= 1024 elements, a per-block sparse table over the
+//   superchunks in shared memory) -> bridge test -> sort of the packed (a<<k | b) keys (all-pairs
+//   rank for up to 16,384 bridges, else an in-kernel stable LSD radix sort).
+// Every wait in the barrier is bounded: on expiry the block records BRIDGES_ETIMEDOUT in the
+// status word and leaves the kernel, and the others follow at their next barrier.
 #include <algorithm>
 
 #include "common.cuh"
@@ -21,95 +28,271 @@ namespace bridges {
 
 namespace {
 
-constexpr int kBs = 256;
+constexpr int kThreads = 512;
+constexpr int kWarps = kThreads / 32;
+constexpr int kChunk = 32;           // lo/hi elements per chunk (one warp)
+constexpr int kSuperChunks = 32;     // chunks per superchunk at the smallest superchunk size
+constexpr int kMaxSup = 1024;        // superchunks covered by the shared-memory table
+constexpr int kSupLevels = 11;       // log2(kMaxSup) + 1
+constexpr int64_t kRankMax = 16384;  // up to this many bridges: all-pairs rank sort
+constexpr unsigned kSpinCap = 1u << 22;
+constexpr int kMaxBlocks = 1024;
+constexpr size_t kSmemTables = sizeof(int32_t) * 2 * kSupLevels * kMaxSup;
 
-__global__ void fin_init_kernel(FinalBufs f, int32_t V, int64_t arcs_cap, bool own_uf) {
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < V; i += (int64_t)gridDim.x * blockDim.x) {
-    f.deg[i] = 0;
-    f.cur[i] = 0;
-    if (own_uf) f.P[i] = (int32_t)i;
-  }
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < arcs_cap; i += (int64_t)gridDim.x * blockDim.x)
-    f.dflag[i] = 0;
-  if (blockIdx.x == 0 && threadIdx.x == 0) *f.nkeys = 0;
+struct FinArgs {
+  FinalBufs f;
+  int32_t V;
+  const int32_t* tu;
+  const int32_t* tv;
+  const int32_t* d_nt;
+  int32_t ct;  // capacity of the tree list
+  const int32_t* xu;
+  const int32_t* xv;
+  const int32_t* d_nx;
+  int32_t cx;             // capacity of the extra list
+  const int32_t* P_tree;  // union-find of T, or null: built here in f.P
+  int32_t* out;
+  int kbits;
+  int32_t sup_log;  // chunks per superchunk = kSuperChunks << sup_log
+};
+
+__device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
 }
 
-// Range-checks the tree edges, builds the forest's union-find (when owned) and counts degrees.
-__global__ void fin_tree_kernel(FinalBufs f, int32_t V, const int32_t* tu, const int32_t* tv, const int32_t* d_nt,
-                                int32_t cap, bool own_uf) {
-  const int32_t nt = min(*d_nt, cap);
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < nt; e += (int64_t)gridDim.x * blockDim.x) {
-    int32_t a = tu[e], b = tv[e];
+__device__ __forceinline__ void st_release(unsigned* p, unsigned v) {
+  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// Grid-wide barrier for a cooperative launch.  Returns false if the wait gave up (the status
+// word then holds BRIDGES_ETIMEDOUT and the caller must leave the kernel).
+__device__ __noinline__ bool grid_barrier(unsigned* count, unsigned* gen, int32_t* status) {
+  __shared__ int ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    ok = 1;
+    const unsigned g = ld_acquire(gen);
+    __threadfence();
+    if (atomicAdd(count, 1u) == gridDim.x - 1) {
+      atomicExch(count, 0u);
+      __threadfence();
+      st_release(gen, g + 1);
+    } else {
+      unsigned spins = 0;
+      while (ld_acquire(gen) == g) {
+        __nanosleep(100);
+        if (++spins > kSpinCap) {
+          set_status(status, BRIDGES_ETIMEDOUT_CODE);
+          ok = 0;
+          break;
+        }
+      }
+    }
+    __threadfence();
+  }
+  __syncthreads();
+  return ok != 0;
+}
+
+#define BARRIER()                                                 \
+  do {                                                            \
+    if (!grid_barrier(f.bar_count, f.bar_gen, f.status)) return; \
+  } while (0)
+
+__device__ __forceinline__ int64_t gtid() { return (int64_t)blockIdx.x * blockDim.x + threadIdx.x; }
+__device__ __forceinline__ int64_t gstride() { return (int64_t)gridDim.x * blockDim.x; }
+
+// Block-wide sum (every thread gets the result).
+__device__ __forceinline__ int32_t block_sum(int32_t v, int32_t* red) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(kFull, v, o);
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  int32_t t = 0;
+  for (int w = 0; w < kWarps; w++) t += red[w];
+  __syncthreads();
+  return t;
+}
+
+// Block-wide exclusive scan of one value per thread; returns this thread's prefix, *tot the sum.
+__device__ __forceinline__ int32_t block_excl(int32_t v, int32_t* red, int32_t* tot) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  int32_t incl = v;
+  for (int o = 1; o < 32; o <<= 1) {
+    const int32_t y = __shfl_up_sync(kFull, incl, o);
+    if (lane >= o) incl += y;
+  }
+  __syncthreads();
+  if (lane == 31) red[w] = incl;
+  __syncthreads();
+  int32_t base = 0, t = 0;
+  for (int k = 0; k < kWarps; k++) {
+    if (k < w) base += red[k];
+    t += red[k];
+  }
+  __syncthreads();
+  *tot = t;
+  return base + incl - v;
+}
+
+// Exclusive scans of one or two int32 arrays of length n (in place allowed); out[n] = total.
+// Block b owns a contiguous range.  Contains one grid barrier; the caller adds the one after.
+__device__ bool grid_scan(const FinalBufs& f, const int32_t* in0, int32_t* out0, const int32_t* in1, int32_t* out1,
+                          int64_t n, int32_t* red) {
+  const int64_t per = (n + gridDim.x - 1) / gridDim.x;
+  const int64_t lo = min(n, per * (int64_t)blockIdx.x), hi = min(n, lo + per);
+  int32_t s0 = 0, s1 = 0;
+  for (int64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) {
+    s0 += in0[i];
+    if (in1) s1 += in1[i];
+  }
+  s0 = block_sum(s0, red);
+  if (in1) s1 = block_sum(s1, red);
+  if (threadIdx.x == 0) {
+    f.part[blockIdx.x] = s0;
+    if (in1) f.part[gridDim.x + blockIdx.x] = s1;
+  }
+  if (!grid_barrier(f.bar_count, f.bar_gen, f.status)) return false;
+  int32_t c0 = 0, c1 = 0;
+  for (int k = threadIdx.x; k < (int)blockIdx.x; k += blockDim.x) {
+    c0 += f.part[k];
+    if (in1) c1 += f.part[gridDim.x + k];
+  }
+  c0 = block_sum(c0, red);
+  if (in1) c1 = block_sum(c1, red);
+  for (int64_t t0 = lo; t0 < hi; t0 += blockDim.x) {
+    const int64_t i = t0 + threadIdx.x;
+    const int32_t v0 = i < hi ? in0[i] : 0;
+    const int32_t v1 = (in1 && i < hi) ? in1[i] : 0;
+    int32_t tot0 = 0, tot1 = 0;
+    const int32_t e0 = block_excl(v0, red, &tot0);
+    const int32_t e1 = in1 ? block_excl(v1, red, &tot1) : 0;
+    if (i < hi) {
+      out0[i] = c0 + e0;
+      if (in1) out1[i] = c1 + e1;
+    }
+    c0 += tot0;
+    c1 += tot1;
+  }
+  if (blockIdx.x == gridDim.x - 1 && threadIdx.x == 0) {  // the last block's carry is the total
+    out0[n] = c0;
+    if (in1) out1[n] = c1;
+  }
+  return true;
+}
+
+// min of lo[] and max of hi[] over [l, r) by direct reads.
+__device__ __forceinline__ void scan_range(const int32_t* lo, const int32_t* hi, int64_t l, int64_t r, int32_t& mn,
+                                           int32_t& mx) {
+  for (int64_t i = l; i < r; i++) {
+    mn = min(mn, lo[i]);
+    mx = max(mx, hi[i]);
+  }
+}
+
+__global__ void __launch_bounds__(kThreads) final_kernel(FinArgs A) {
+  extern __shared__ int32_t sm[];  // superchunk sparse tables: [2][kSupLevels][kMaxSup]
+  __shared__ int32_t red[kWarps];
+  __shared__ uint32_t wcnt[kWarps][256];
+  __shared__ uint32_t run[256];
+  __shared__ uint64_t ktile[1024];
+  const FinalBufs& f = A.f;
+  const int32_t V = A.V;
+  const bool own = A.P_tree == nullptr;
+  int32_t* P = own ? f.P : const_cast<int32_t*>(A.P_tree);
+  const int32_t nt = min(*A.d_nt, A.ct);
+  const int32_t nx = min(*A.d_nx, A.cx);
+  const int64_t narcs_cap = 2 * (int64_t)max(V, 1);
+
+  // 0: clear
+  for (int64_t i = gtid(); i < V; i += gstride()) {
+    f.deg[i] = 0;
+    f.cur[i] = 0;
+    if (own) f.P[i] = (int32_t)i;
+  }
+  for (int64_t i = gtid(); i <= narcs_cap; i += gstride()) f.dflag[i] = 0;
+  if (gtid() == 0) *f.nkeys = 0;
+  BARRIER();
+
+  // 1: tree edges -> degrees (and the forest's union-find when it is ours to build)
+  for (int64_t e = gtid(); e < nt; e += gstride()) {
+    const int32_t a = A.tu[e], b = A.tv[e];
     if ((uint32_t)a >= (uint32_t)V || (uint32_t)b >= (uint32_t)V) {
       set_status(f.status, BRIDGES_ERANGE_CODE);
       continue;
     }
-    if (own_uf && !uf_link(f.P, a, b)) set_status(f.status, BRIDGES_EINTERNAL_CODE);  // not a forest
+    if (own && !uf_link(f.P, a, b)) set_status(f.status, BRIDGES_EINTERNAL_CODE);  // not a forest
     atomicAdd(f.deg + a, 1);
     atomicAdd(f.deg + b, 1);
   }
-}
+  BARRIER();
+  if (!grid_scan(f, f.deg, f.off, nullptr, nullptr, V, red)) return;
+  BARRIER();
+  const int32_t narcs = (int32_t)min((int64_t)f.off[V], narcs_cap);
 
-__global__ void fin_fill_kernel(FinalBufs f, int32_t V, const int32_t* tu, const int32_t* tv, const int32_t* d_nt,
-                                int32_t cap) {
-  const int32_t nt = min(*d_nt, cap);
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < nt; e += (int64_t)gridDim.x * blockDim.x) {
-    int32_t a = tu[e], b = tv[e];
+  // 2: adjacency (arc slots, twins) and the root (minimum vertex) of every tree
+  for (int64_t e = gtid(); e < nt; e += gstride()) {
+    const int32_t a = A.tu[e], b = A.tv[e];
     if ((uint32_t)a >= (uint32_t)V || (uint32_t)b >= (uint32_t)V) continue;
-    int32_t ia = f.off[a] + atomicAdd(f.cur + a, 1);
-    int32_t ib = f.off[b] + atomicAdd(f.cur + b, 1);
+    const int32_t ia = f.off[a] + atomicAdd(f.cur + a, 1);
+    const int32_t ib = f.off[b] + atomicAdd(f.cur + b, 1);
+    if (ia >= narcs || ib >= narcs) continue;
     f.dst[ia] = b;
     f.dst[ib] = a;
     f.twin[ia] = ib;
     f.twin[ib] = ia;
   }
-}
+  for (int64_t x = gtid(); x < V; x += gstride()) f.root[x] = uf_find_static(P, (int32_t)x);
+  BARRIER();
 
-__global__ void fin_root_kernel(FinalBufs f, int32_t V, const int32_t* P) {
-  for (int64_t x = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; x < V; x += (int64_t)gridDim.x * blockDim.x)
-    f.root[x] = uf_find_static(const_cast<int32_t*>(P), (int32_t)x);
-}
-
-// Euler tour successor of arc i = (x -> y): the arc after (y -> x) in y's list, cyclically.
-__global__ void fin_succ_kernel(FinalBufs f, int32_t V) {
-  const int32_t narcs = f.off[V];
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < narcs; i += (int64_t)gridDim.x * blockDim.x) {
-    int32_t y = f.dst[i], t = f.twin[i];
-    f.succ[i] = (t + 1 < f.off[y + 1]) ? t + 1 : f.off[y];
-    f.rnk[i] = 1;
+  // 3: Euler-tour successor of arc i = (x -> y): the arc after (y -> x) in y's list, cyclically;
+  //    the arc that would wrap around to a root's first arc ends that tree's list
+  for (int64_t i = gtid(); i < narcs; i += gstride()) {
+    const int32_t y = f.dst[i], t = f.twin[i];
+    int32_t s;
+    if (t + 1 < f.off[y + 1])
+      s = t + 1;
+    else
+      s = f.root[y] == y ? -1 : f.off[y];
+    f.succ[i] = s;
+    f.rnk[i] = s < 0 ? 0 : 1;
   }
-}
+  BARRIER();
 
-// Each tree's tour starts at its root's first arc; the arc leading back into it ends the list.
-__global__ void fin_cut_kernel(FinalBufs f, int32_t V) {
-  for (int64_t x = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; x < V; x += (int64_t)gridDim.x * blockDim.x) {
-    if (f.root[x] == x && f.deg[x] > 0) {
-      int32_t last = f.twin[f.off[x + 1] - 1];
-      f.succ[last] = -1;
-      f.rnk[last] = 0;
+  // 4: list ranking (Wyllie): rank = arcs after this one in its tour
+  {
+    int rounds = 0;
+    while ((1LL << rounds) < (int64_t)max(narcs, 1)) rounds++;
+    int32_t *sa = f.succ, *ra = f.rnk, *sb = f.succ2, *rb = f.rnk2;
+    for (int r = 0; r < rounds; r++) {
+      for (int64_t i = gtid(); i < narcs; i += gstride()) {
+        const int32_t s = sa[i];
+        if (s >= 0) {
+          rb[i] = ra[i] + ra[s];
+          sb[i] = sa[s];
+        } else {
+          rb[i] = ra[i];
+          sb[i] = -1;
+        }
+      }
+      BARRIER();
+      int32_t* t = sa;
+      sa = sb;
+      sb = t;
+      t = ra;
+      ra = rb;
+      rb = t;
+    }
+    if (ra != f.rnk) {
+      for (int64_t i = gtid(); i < narcs; i += gstride()) f.rnk[i] = ra[i];
+      BARRIER();
     }
   }
-}
 
-// One pointer-jumping step (Wyllie): rank += rank[succ], succ = succ[succ].
-__global__ void fin_jump_kernel(const int32_t* succ, const int32_t* rnk, int32_t* succ2, int32_t* rnk2,
-                                const int32_t* off, int32_t V) {
-  const int32_t narcs = off[V];
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < narcs; i += (int64_t)gridDim.x * blockDim.x) {
-    int32_t s = succ[i];
-    if (s >= 0) {
-      rnk2[i] = rnk[i] + rnk[s];
-      succ2[i] = succ[s];
-    } else {
-      rnk2[i] = rnk[i];
-      succ2[i] = -1;
-    }
-  }
-}
-
-// Per root: arcs in its tour (aoff values) and vertices in its tree (vbase values).
-__global__ void fin_rootvals_kernel(FinalBufs f, int32_t V) {
-  for (int64_t x = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; x < V; x += (int64_t)gridDim.x * blockDim.x) {
+  // 5: per root: arcs of its tour (aoff) and vertices of its tree (vbase); scan both
+  for (int64_t x = gtid(); x < V; x += gstride()) {
     int32_t L = 0, nv = 0;
     if (f.root[x] == x) {
       L = f.deg[x] > 0 ? f.rnk[f.off[x]] + 1 : 0;
@@ -118,24 +301,22 @@ __global__ void fin_rootvals_kernel(FinalBufs f, int32_t V) {
     f.aoff[x] = L;
     f.vbase[x] = nv;
   }
-}
+  BARRIER();
+  if (!grid_scan(f, f.aoff, f.aoff, f.vbase, f.vbase, V, red)) return;
+  BARRIER();
 
-__device__ __forceinline__ int32_t src_of(const FinalBufs& f, int32_t i) { return f.dst[f.twin[i]]; }
-
-// Tour position of every arc; down arcs (parent -> child) come before their twins.
-__global__ void fin_down_kernel(FinalBufs f, int32_t V) {
-  const int32_t narcs = f.off[V];
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < narcs; i += (int64_t)gridDim.x * blockDim.x) {
-    const int32_t x = src_of(f, (int32_t)i);
+  // 6: tour positions; down arcs (parent -> child) come before their twins
+  for (int64_t i = gtid(); i < narcs; i += gstride()) {
+    const int32_t x = f.dst[f.twin[i]];
     const int32_t r = f.root[x];
     const int32_t L = f.rnk[f.off[r]] + 1;
     const int32_t ri = f.rnk[i], rt = f.rnk[f.twin[i]];
     const int32_t g = f.aoff[r] + L - 1 - ri;
-    const bool down = ri > rt;
     if (g < 0 || g >= narcs) {  // only if the tree input was not a forest
       set_status(f.status, BRIDGES_EINTERNAL_CODE);
       continue;
     }
+    const bool down = ri > rt;
     f.dflag[g] = down ? 1 : 0;
     if (down) {
       const int32_t y = f.dst[i];
@@ -144,11 +325,12 @@ __global__ void fin_down_kernel(FinalBufs f, int32_t V) {
       f.sz[y] = (ri - rt + 1) / 2;
     }
   }
-}
+  BARRIER();
+  if (!grid_scan(f, f.dflag, f.dscan, nullptr, nullptr, narcs, red)) return;
+  BARRIER();
 
-__global__ void fin_pre_kernel(FinalBufs f, int32_t V) {
-  const int32_t narcs = f.off[V];
-  for (int64_t x = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; x < V; x += (int64_t)gridDim.x * blockDim.x) {
+  // 7: preorder numbers and subtree sizes; lo / hi start at the vertex itself
+  for (int64_t x = gtid(); x < V; x += gstride()) {
     const int32_t r = f.root[x];
     int32_t p;
     if (r == x) {
@@ -165,64 +347,105 @@ __global__ void fin_pre_kernel(FinalBufs f, int32_t V) {
       p = 0;
     }
     f.pre[x] = p;
+    f.lo[p] = p;
+    f.hi[p] = p;
   }
-}
+  BARRIER();
 
-__global__ void fin_lohi_init_kernel(FinalBufs f, int32_t V) {
-  for (int64_t x = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; x < V; x += (int64_t)gridDim.x * blockDim.x) {
-    const int32_t p = f.pre[x];
-    f.stmin[p] = p;
-    f.stmax[p] = p;
-  }
-}
-
-__global__ void fin_extra_kernel(FinalBufs f, int32_t V, const int32_t* xu, const int32_t* xv, const int32_t* d_nx,
-                                 int32_t cap) {
-  const int32_t nx = min(*d_nx, cap);
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < nx; e += (int64_t)gridDim.x * blockDim.x) {
-    const int32_t a = xu[e], b = xv[e];
+  // 8: lo / hi over the extra edges
+  for (int64_t e = gtid(); e < nx; e += gstride()) {
+    const int32_t a = A.xu[e], b = A.xv[e];
     if ((uint32_t)a >= (uint32_t)V || (uint32_t)b >= (uint32_t)V) {
       set_status(f.status, BRIDGES_ERANGE_CODE);
       continue;
     }
     if (a == b) continue;
     const int32_t pa = f.pre[a], pb = f.pre[b];
-    atomicMin(f.stmin + pa, pb);
-    atomicMin(f.stmin + pb, pa);
-    atomicMax(f.stmax + pa, pb);
-    atomicMax(f.stmax + pb, pa);
+    atomicMin(f.lo + pa, pb);
+    atomicMin(f.lo + pb, pa);
+    atomicMax(f.hi + pa, pb);
+    atomicMax(f.hi + pb, pa);
   }
-}
+  BARRIER();
 
-__global__ void fin_sparse_kernel(int32_t* stmin, int32_t* stmax, int32_t V, int k) {
-  const int64_t half = 1LL << (k - 1);
-  const int64_t n = (int64_t)V - (1LL << k) + 1;
-  const int32_t* pmin = stmin + (int64_t)(k - 1) * V;
-  const int32_t* pmax = stmax + (int64_t)(k - 1) * V;
-  int32_t* qmin = stmin + (int64_t)k * V;
-  int32_t* qmax = stmax + (int64_t)k * V;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    qmin[i] = min(pmin[i], pmin[i + half]);
-    qmax[i] = max(pmax[i], pmax[i + half]);
+  // 9: chunk (32 elements) and superchunk min / max
+  const int64_t nchunks = (V + kChunk - 1) / kChunk;
+  const int64_t csup = (int64_t)kSuperChunks << A.sup_log;  // chunks per superchunk
+  const int64_t nsup = (nchunks + csup - 1) / csup;
+  {
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = gtid() >> 5, nwarps = gstride() >> 5;
+    for (int64_t c = warp; c < nchunks; c += nwarps) {
+      const int64_t i = c * kChunk + lane;
+      int32_t mn = i < V ? f.lo[i] : INT32_MAX, mx = i < V ? f.hi[i] : INT32_MIN;
+      for (int o = 16; o > 0; o >>= 1) {
+        mn = min(mn, __shfl_xor_sync(kFull, mn, o));
+        mx = max(mx, __shfl_xor_sync(kFull, mx, o));
+      }
+      if (lane == 0) {
+        f.cmin[c] = mn;
+        f.cmax[c] = mx;
+      }
+    }
   }
-}
+  BARRIER();
+  for (int64_t s = gtid(); s < nsup; s += gstride()) {
+    int32_t mn = INT32_MAX, mx = INT32_MIN;
+    for (int64_t c = s * csup; c < min(nchunks, (s + 1) * csup); c++) {
+      mn = min(mn, f.cmin[c]);
+      mx = max(mx, f.cmax[c]);
+    }
+    f.smin[s] = mn;
+    f.smax[s] = mx;
+  }
+  BARRIER();
 
-// Tree edge (par(y), y) is a bridge iff no X edge leaves y's preorder range.
-__global__ void fin_test_kernel(FinalBufs f, int32_t V, int kbits) {
-  for (int64_t base = blockIdx.x * (int64_t)blockDim.x; base < V; base += (int64_t)gridDim.x * blockDim.x) {
+  // 10: per-block sparse tables over the superchunks, then the bridge test
+  int32_t* tmin = sm;
+  int32_t* tmax = sm + kSupLevels * kMaxSup;
+  int levels = 1;
+  while ((1LL << levels) <= nsup) levels++;
+  for (int64_t s = threadIdx.x; s < nsup; s += blockDim.x) {
+    tmin[s] = f.smin[s];
+    tmax[s] = f.smax[s];
+  }
+  __syncthreads();
+  for (int k = 1; k < levels; k++) {
+    const int64_t half = 1LL << (k - 1);
+    for (int64_t s = threadIdx.x; s + (1LL << k) <= nsup; s += blockDim.x) {
+      tmin[k * kMaxSup + s] = min(tmin[(k - 1) * kMaxSup + s], tmin[(k - 1) * kMaxSup + s + half]);
+      tmax[k * kMaxSup + s] = max(tmax[(k - 1) * kMaxSup + s], tmax[(k - 1) * kMaxSup + s + half]);
+    }
+    __syncthreads();
+  }
+  for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < V; base += gstride()) {
     const int64_t y = base + threadIdx.x;
     bool is_bridge = false;
     uint64_t key = 0;
     if (y < V && f.par[y] >= 0) {
-      const int32_t p = f.pre[y];
-      const int32_t s = max(1, min(f.sz[y], V - p));
-      const int k = 31 - __clz(s);
-      const int64_t o = (int64_t)k * V;
-      const int32_t mn = min(f.stmin[o + p], f.stmin[o + p + s - (1 << k)]);
-      const int32_t mx = max(f.stmax[o + p], f.stmax[o + p + s - (1 << k)]);
-      if (mn >= p && mx < p + s) {
+      const int64_t l = f.pre[y];
+      const int64_t r = min((int64_t)V, l + max(f.sz[y], 1));
+      int32_t mn = INT32_MAX, mx = INT32_MIN;
+      const int64_t cl = (l + kChunk - 1) / kChunk, cr = r / kChunk;  // whole chunks [cl, cr)
+      if (cl >= cr) {
+        scan_range(f.lo, f.hi, l, r, mn, mx);
+      } else {
+        scan_range(f.lo, f.hi, l, cl * kChunk, mn, mx);
+        scan_range(f.lo, f.hi, cr * kChunk, r, mn, mx);
+        const int64_t sl = (cl + csup - 1) / csup, sr = cr / csup;  // whole superchunks [sl, sr)
+        if (sl >= sr) {
+          scan_range(f.cmin, f.cmax, cl, cr, mn, mx);
+        } else {
+          scan_range(f.cmin, f.cmax, cl, sl * csup, mn, mx);
+          scan_range(f.cmin, f.cmax, sr * csup, cr, mn, mx);
+          const int k = 63 - __clzll(sr - sl);
+          mn = min(mn, min(tmin[k * kMaxSup + sl], tmin[k * kMaxSup + sr - (1LL << k)]));
+          mx = max(mx, max(tmax[k * kMaxSup + sl], tmax[k * kMaxSup + sr - (1LL << k)]));
+        }
+      }
+      if (mn >= l && mx < r) {
         const uint32_t a = (uint32_t)min((int32_t)y, f.par[y]), b = (uint32_t)max((int32_t)y, f.par[y]);
-        key = ((uint64_t)a << kbits) | b;
+        key = ((uint64_t)a << A.kbits) | b;
         is_bridge = true;
       }
     }
@@ -241,25 +464,103 @@ __global__ void fin_test_kernel(FinalBufs f, int32_t V, int kbits) {
       }
     }
   }
+  BARRIER();
+
+  // 11: sort the keys; write (a, b) pairs
+  const int32_t cap = max(V - 1, 0);
+  const int32_t n = min(*f.nkeys, cap);
+  const uint64_t mask = (1ULL << A.kbits) - 1;
+  if (n <= kRankMax) {
+    for (int64_t i0 = (int64_t)blockIdx.x * blockDim.x; i0 < n; i0 += gstride()) {
+      const int64_t i = i0 + threadIdx.x;
+      const uint64_t mine = i < n ? f.keys[i] : ~0ULL;
+      int32_t rank = 0;
+      for (int32_t t0 = 0; t0 < n; t0 += 1024) {
+        __syncthreads();
+        for (int k = threadIdx.x; k < 1024; k += blockDim.x) ktile[k] = t0 + k < n ? f.keys[t0 + k] : ~0ULL;
+        __syncthreads();
+        const int lim = min(1024, n - t0);
+        for (int k = 0; k < lim; k++) rank += ktile[k] < mine;
+      }
+      if (i < n) {
+        A.out[2 * (int64_t)rank] = (int32_t)(mine >> A.kbits);
+        A.out[2 * (int64_t)rank + 1] = (int32_t)(mine & mask);
+      }
+    }
+  } else {
+    const int passes = (2 * A.kbits + 7) / 8;
+    const int64_t per = (n + gridDim.x - 1) / gridDim.x;
+    const int64_t lo = min((int64_t)n, per * (int64_t)blockIdx.x), hi = min((int64_t)n, lo + per);
+    uint64_t* src = f.keys;
+    uint64_t* dst = f.keys2;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int p = 0; p < passes; p++) {
+      const int shift = 8 * p;
+      if (threadIdx.x < 256) run[threadIdx.x] = 0;
+      __syncthreads();
+      for (int64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) atomicAdd(&run[(src[i] >> shift) & 255], 1u);
+      __syncthreads();
+      if (threadIdx.x < 256) f.hist[(int64_t)threadIdx.x * gridDim.x + blockIdx.x] = (int32_t)run[threadIdx.x];
+      BARRIER();
+      if (!grid_scan(f, f.hist, f.hist, nullptr, nullptr, (int64_t)256 * gridDim.x, red)) return;
+      BARRIER();
+      if (threadIdx.x < 256) {
+        run[threadIdx.x] = (uint32_t)f.hist[(int64_t)threadIdx.x * gridDim.x + blockIdx.x];
+        for (int w = 0; w < kWarps; w++) wcnt[w][threadIdx.x] = 0;
+      }
+      __syncthreads();
+      for (int64_t t0 = lo; t0 < hi; t0 += blockDim.x) {  // stable: chunk, warp, lane = index order
+        const int64_t i = t0 + threadIdx.x;
+        const bool valid = i < hi;
+        const uint64_t key = valid ? src[i] : 0;
+        const unsigned d = valid ? (unsigned)((key >> shift) & 255) : 256u + lane;
+        const unsigned peers = __match_any_sync(kFull, d);
+        const unsigned rank = __popc(peers & lanemask_lt());
+        if (valid && rank == 0) wcnt[warp][d] = __popc(peers);
+        __syncthreads();
+        if (threadIdx.x < 256) {
+          uint32_t acc = run[threadIdx.x];
+          for (int w = 0; w < kWarps; w++) {
+            const uint32_t c = wcnt[w][threadIdx.x];
+            wcnt[w][threadIdx.x] = acc;
+            acc += c;
+          }
+          run[threadIdx.x] = acc;
+        }
+        __syncthreads();
+        if (valid) {
+          const uint32_t pos = wcnt[warp][d] + rank;
+          if (pos < (uint32_t)n) {
+            if (p == passes - 1) {
+              A.out[2 * (int64_t)pos] = (int32_t)(key >> A.kbits);
+              A.out[2 * (int64_t)pos + 1] = (int32_t)(key & mask);
+            } else {
+              dst[pos] = key;
+            }
+          }
+        }
+        __syncthreads();
+        if (threadIdx.x < 256)
+          for (int w = 0; w < kWarps; w++) wcnt[w][threadIdx.x] = 0;
+        __syncthreads();
+      }
+      BARRIER();
+      uint64_t* t = src;
+      src = dst;
+      dst = t;
+    }
+  }
+
+  // 12: the count, or the first error
+  if (gtid() == 0) {
+    int32_t st = *f.status;
+    const int32_t nk = *f.nkeys;
+    if (st == 0 && nk > cap) st = BRIDGES_EINTERNAL_CODE;  // a forest has at most V-1 edges
+    *f.count = st != 0 ? (int64_t)st : (int64_t)nk;
+  }
 }
 
-__global__ void fin_count_kernel(FinalBufs f, int32_t cap) {
-  int32_t st = *f.status;
-  const int32_t n = *f.nkeys;
-  if (st == 0 && n > cap) st = BRIDGES_EINTERNAL_CODE;  // a forest has at most V-1 edges
-  *f.count = st != 0 ? (int64_t)st : (int64_t)n;
-}
-
-int grid(const Launch& L, int64_t work) {
-  int64_t g = ceil_div(std::max<int64_t>(work, 1), kBs);
-  return (int)std::min<int64_t>(g, (int64_t)L.num_sms * 16);
-}
-
-int levels_for(int32_t V) {
-  int K = 1;
-  while ((1LL << K) <= V) K++;
-  return K;  // levels 0..K-1, 2^(K-1) <= V
-}
+#undef BARRIER
 
 int bits_for(int32_t V) {
   int k = 1;
@@ -271,18 +572,14 @@ int bits_for(int32_t V) {
 
 size_t final_bytes(int32_t V) {
   const size_t Vs = (size_t)std::max(V, 1);
-  const size_t K = (size_t)levels_for(std::max(V, 1));
   size_t s = 0;
-  s += 256;                                                // count
-  s += 256;                                                // nkeys
-  s += 10 * align_up(sizeof(int32_t) * (Vs + 1), 256);     // V-long arrays
-  s += 7 * align_up(sizeof(int32_t) * (2 * Vs + 1), 256);  // 2V-long arrays
-  s += 2 * align_up(sizeof(int32_t) * K * Vs, 256);        // sparse tables
-  s += 2 * align_up(sizeof(uint64_t) * Vs, 256);           // keys
-  const size_t hist = sort_hist_elems((int64_t)Vs);
-  s += align_up(sizeof(uint32_t) * hist, 256);
-  const size_t st = std::max(scan_tmp_elems(2 * (int64_t)Vs + 1), scan_tmp_elems((int64_t)hist));
-  s += align_up(sizeof(int32_t) * st, 256);
+  s += 3 * 256;                                                           // count, nkeys, barrier
+  s += 12 * align_up(sizeof(int32_t) * (Vs + 1), 256);                    // V-long arrays
+  s += 7 * align_up(sizeof(int32_t) * (2 * Vs + 1), 256);                 // 2V-long arrays
+  s += 4 * align_up(sizeof(int32_t) * (Vs / kChunk + 2), 256);            // chunk / superchunk min, max
+  s += 2 * align_up(sizeof(uint64_t) * Vs, 256);                          // keys
+  s += align_up(sizeof(int32_t) * (256 * (size_t)kMaxBlocks + 1), 256);  // radix histograms
+  s += align_up(sizeof(int32_t) * 2 * kMaxBlocks, 256);                   // scan partials
   return s;
 }
 
@@ -290,13 +587,15 @@ FinalBufs carve_final(void* base, int32_t V, int32_t* status) {
   FinalBufs f{};
   char* c = static_cast<char*>(base);
   const size_t Vs = (size_t)std::max(V, 1);
-  f.K = levels_for(std::max(V, 1));
   f.status = status;
   f.count = reinterpret_cast<int64_t*>(c);
   c += 256;
   f.nkeys = reinterpret_cast<int32_t*>(c);
   c += 256;
-  int32_t** va[10] = {&f.P, &f.root, &f.deg, &f.off, &f.cur, &f.aoff, &f.vbase, &f.pre, &f.sz, &f.par};
+  f.bar_count = reinterpret_cast<unsigned*>(c);
+  f.bar_gen = f.bar_count + 1;
+  c += 256;
+  int32_t** va[12] = {&f.P, &f.root, &f.deg, &f.off, &f.cur, &f.aoff, &f.vbase, &f.pre, &f.sz, &f.par, &f.lo, &f.hi};
   for (auto a : va) {
     *a = reinterpret_cast<int32_t*>(c);
     c += align_up(sizeof(int32_t) * (Vs + 1), 256);
@@ -306,76 +605,56 @@ FinalBufs carve_final(void* base, int32_t V, int32_t* status) {
     *a = reinterpret_cast<int32_t*>(c);
     c += align_up(sizeof(int32_t) * (2 * Vs + 1), 256);
   }
-  // the pointer-jumping double buffer of the ranks reuses dscan, which is free until the
-  // preorder scan that follows the ranking
+  // the pointer-jumping double buffer of the ranks reuses dscan, free until the preorder scan
   f.rnk2 = f.dscan;
-  f.stmin = reinterpret_cast<int32_t*>(c);
-  c += align_up(sizeof(int32_t) * (size_t)f.K * Vs, 256);
-  f.stmax = reinterpret_cast<int32_t*>(c);
-  c += align_up(sizeof(int32_t) * (size_t)f.K * Vs, 256);
+  int32_t** vc[4] = {&f.cmin, &f.cmax, &f.smin, &f.smax};
+  for (auto a : vc) {
+    *a = reinterpret_cast<int32_t*>(c);
+    c += align_up(sizeof(int32_t) * (Vs / kChunk + 2), 256);
+  }
   f.keys = reinterpret_cast<uint64_t*>(c);
   c += align_up(sizeof(uint64_t) * Vs, 256);
   f.keys2 = reinterpret_cast<uint64_t*>(c);
   c += align_up(sizeof(uint64_t) * Vs, 256);
-  f.hist_elems = sort_hist_elems((int64_t)Vs);
-  f.hist = reinterpret_cast<uint32_t*>(c);
-  c += align_up(sizeof(uint32_t) * f.hist_elems, 256);
-  f.scan_tmp = reinterpret_cast<int32_t*>(c);
-  f.scan_tmp_elems = std::max(scan_tmp_elems(2 * (int64_t)Vs + 1), scan_tmp_elems((int64_t)f.hist_elems));
+  f.hist = reinterpret_cast<int32_t*>(c);
+  c += align_up(sizeof(int32_t) * (256 * (size_t)kMaxBlocks + 1), 256);
+  f.part = reinterpret_cast<int32_t*>(c);
   return f;
 }
 
 void final_stage(const Launch& L, const FinalBufs& f, int32_t V, const int32_t* tu, const int32_t* tv,
                  const int32_t* d_nt, int64_t cap_tree, const int32_t* xu, const int32_t* xv, const int32_t* d_nx,
                  int64_t cap_extra, const int32_t* P_tree, int32_t* out) {
-  cudaStream_t s = L.stream;
-  const bool own = P_tree == nullptr;
-  const int64_t arcs_cap = 2 * (int64_t)std::max(V, 1);
-  const int gV = grid(L, V), gA = grid(L, arcs_cap), gT = grid(L, cap_tree), gX = grid(L, cap_extra);
-  fin_init_kernel<<<std::max(gV, gA), kBs, 0, s>>>(f, V, arcs_cap + 1, own);
-  // at most V tree edges keep the 2V arc arrays in bounds whatever the counts say
-  const int32_t ct = (int32_t)std::min<int64_t>(cap_tree, std::max(V, 1));
-  const int32_t cx = (int32_t)std::min<int64_t>(cap_extra, INT32_MAX);
-  fin_tree_kernel<<<gT, kBs, 0, s>>>(f, V, tu, tv, d_nt, ct, own);
-  exclusive_scan_i32(L, f.deg, f.off, V, true, f.scan_tmp);
-  fin_fill_kernel<<<gT, kBs, 0, s>>>(f, V, tu, tv, d_nt, ct);
-  fin_root_kernel<<<gV, kBs, 0, s>>>(f, V, own ? f.P : P_tree);
-  fin_succ_kernel<<<gA, kBs, 0, s>>>(f, V);
-  fin_cut_kernel<<<gV, kBs, 0, s>>>(f, V);
-  *L.launches += 7;
-  // list ranking: ceil(log2(arcs)) pointer-jumping rounds
-  int rounds = 0;
-  while ((1LL << rounds) < arcs_cap) rounds++;
-  int32_t *sa = f.succ, *ra = f.rnk, *sb = f.succ2, *rb = f.rnk2;
-  for (int r = 0; r < rounds; r++) {
-    fin_jump_kernel<<<gA, kBs, 0, s>>>(sa, ra, sb, rb, f.off, V);
-    std::swap(sa, sb);
-    std::swap(ra, rb);
+  static int occ_blocks = -1;  // resident blocks per SM of final_kernel
+  if (occ_blocks < 0) {
+    cudaFuncSetAttribute(final_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemTables);
+    int occ = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, final_kernel, kThreads, kSmemTables);
+    occ_blocks = std::max(1, std::min(occ, 2));
   }
-  *L.launches += rounds;
-  if (ra != f.rnk) {
-    cudaMemcpyAsync(f.rnk, ra, sizeof(int32_t) * (size_t)arcs_cap, cudaMemcpyDeviceToDevice, s);
-  }
-  fin_rootvals_kernel<<<gV, kBs, 0, s>>>(f, V);
-  exclusive_scan_i32(L, f.aoff, f.aoff, V, true, f.scan_tmp);
-  exclusive_scan_i32(L, f.vbase, f.vbase, V, true, f.scan_tmp);
-  fin_down_kernel<<<gA, kBs, 0, s>>>(f, V);
-  exclusive_scan_i32(L, f.dflag, f.dscan, arcs_cap, true, f.scan_tmp);
-  fin_pre_kernel<<<gV, kBs, 0, s>>>(f, V);
-  fin_lohi_init_kernel<<<gV, kBs, 0, s>>>(f, V);
-  fin_extra_kernel<<<gX, kBs, 0, s>>>(f, V, xu, xv, d_nx, cx);
-  *L.launches += 5;
-  for (int k = 1; k < f.K; k++) {
-    fin_sparse_kernel<<<gV, kBs, 0, s>>>(f.stmin, f.stmax, V, k);
-  }
-  *L.launches += f.K - 1;
-  const int kbits = bits_for(std::max(V, 1));
-  fin_test_kernel<<<gV, kBs, 0, s>>>(f, V, kbits);
-  *L.launches += 1;
-  // at most V-1 bridges: the sort never writes beyond the caller's 2(V-1) output entries
-  sort_pairs(L, f.keys, f.keys2, f.nkeys, std::max<int64_t>(V - 1, 0), 2 * kbits, out, f.hist, f.hist_elems,
-             f.scan_tmp);
-  fin_count_kernel<<<1, 1, 0, s>>>(f, std::max(V - 1, 0));
+  FinArgs A{};
+  A.f = f;
+  A.V = V;
+  A.tu = tu;
+  A.tv = tv;
+  A.d_nt = d_nt;
+  A.ct = (int32_t)std::min<int64_t>(cap_tree, std::max(V, 1));  // <= V tree edges keep the arcs in bounds
+  A.xu = xu;
+  A.xv = xv;
+  A.d_nx = d_nx;
+  A.cx = (int32_t)std::min<int64_t>(cap_extra, INT32_MAX);
+  A.P_tree = P_tree;
+  A.out = out;
+  A.kbits = bits_for(std::max(V, 1));
+  // superchunk size: the shared-memory table covers at most kMaxSup superchunks
+  const int64_t nchunks = ceil_div(std::max(V, 1), kChunk);
+  int sl = 0;
+  while (ceil_div(nchunks, (int64_t)kSuperChunks << sl) > kMaxSup) sl++;
+  A.sup_log = sl;
+  const int blocks = std::min(kMaxBlocks, occ_blocks * L.num_sms);
+  cudaMemsetAsync(f.bar_count, 0, 2 * sizeof(unsigned), L.stream);
+  void* args[] = {&A};
+  cudaLaunchCooperativeKernel((void*)final_kernel, dim3(blocks), dim3(kThreads), args, kSmemTables, L.stream);
   *L.launches += 1;
 }
 

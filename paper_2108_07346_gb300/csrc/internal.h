@@ -53,11 +53,13 @@ struct CertBufs {
   int64_t Vpad;  // stride of lab
 };
 
-// Device buffers of the final stage (Euler tour, ranges, test, sort).
+// Device buffers of the final stage (Euler tour, ranges, test, sort), one cooperative kernel.
 struct FinalBufs {
   int32_t* status;
   int64_t* count;  // [1] bridges found (device)
-  int32_t* P;      // [V] union-find over the tree (built by the stage when owned_uf)
+  unsigned* bar_count;  // grid barrier: arrivals
+  unsigned* bar_gen;    // grid barrier: generation
+  int32_t* P;      // [V] union-find over the tree (built by the stage when it owns it)
   int32_t* root;   // [V]
   int32_t* deg;    // [V]
   int32_t* off;    // [V+1]
@@ -67,7 +69,7 @@ struct FinalBufs {
   int32_t* succ;   // [2V]
   int32_t* succ2;  // [2V]
   int32_t* rnk;    // [2V]
-  int32_t* rnk2;   // [2V]
+  int32_t* rnk2;   // [2V] (aliases dscan)
   int32_t* aoff;   // [V+1] arc offset of each tree
   int32_t* vbase;  // [V+1] preorder base of each tree
   int32_t* dflag;  // [2V+1]
@@ -75,28 +77,18 @@ struct FinalBufs {
   int32_t* pre;    // [V]
   int32_t* sz;     // [V]
   int32_t* par;    // [V] parent in the rooted tree (-1 for roots)
-  int32_t* stmin;  // [K*V] sparse tables of lo/hi over preorder (level 0: lo, hi themselves)
-  int32_t* stmax;  // [K*V]
-  int32_t K;
+  int32_t* lo;     // [V] indexed by preorder
+  int32_t* hi;     // [V]
+  int32_t* cmin;   // [V/32] chunk minima of lo
+  int32_t* cmax;   // [V/32] chunk maxima of hi
+  int32_t* smin;   // superchunk minima
+  int32_t* smax;   // superchunk maxima
   uint64_t* keys;   // [V]
   uint64_t* keys2;  // [V]
   int32_t* nkeys;   // [1]
-  int32_t* scan_tmp;  // scan scratch
-  size_t scan_tmp_elems;
-  uint32_t* hist;   // radix histograms
-  size_t hist_elems;
+  int32_t* hist;    // radix histograms
+  int32_t* part;    // per-block scan partials
 };
-
-// ---- scan.cu ----
-// Exclusive prefix sum of n int32 values (out may equal in); out[n] receives the total when
-// write_total.  tmp must hold scan_tmp_elems(n) int32.
-size_t scan_tmp_elems(int64_t n);
-void exclusive_scan_i32(const Launch& L, const int32_t* in, int32_t* out, int64_t n, bool write_total, int32_t* tmp);
-// Sorts n (<= cap) unique 64-bit keys (count on device: *d_n) and writes them as (hi, lo)
-// int32 pairs to out.  key_bits bounds the significant bits.  keys2/hist are scratch.
-void sort_pairs(const Launch& L, uint64_t* keys, uint64_t* keys2, const int32_t* d_n, int64_t cap, int key_bits,
-                int32_t* out, uint32_t* hist, size_t hist_elems, int32_t* scan_tmp);
-size_t sort_hist_elems(int64_t cap);
 
 // ---- certify.cu ----
 void cert_init(const Launch& L, const CertPlan& p, const CertBufs& b);
