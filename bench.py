@@ -280,13 +280,90 @@ def run_native(args, world, rank, local):
         torch.distributed.destroy_process_group()
 
 
+def make_batch(seed, count):
+    """The batched workload: `count` graphs with V log-uniform in [64, 4096], density in
+    [0.1, 0.9], 1-32 planted bridges each (pendant vertices and an inter-cluster tree)."""
+    us, vs, Vs, planted = [], [], [], []
+    for i in range(count):
+        g = graphgen.generate(graphgen.workload_spec("batched", seed, i))
+        us.append(np.array(g.u))
+        vs.append(np.array(g.v))
+        Vs.append(g.V)
+        planted.append(g.planted)
+    off = np.concatenate([[0], np.cumsum([len(x) for x in us])]).astype(np.int64)
+    return np.concatenate(us), np.concatenate(vs), off, np.array(Vs, np.int32), planted
+
+
+def run_batched(args, world, rank, local):
+    import torch
+
+    import paper_2108_07346_gb300 as pb
+
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    u, v, off, Vs, planted = make_batch(3, args.graphs)
+    G, E = len(Vs), int(off[-1])
+    du = torch.from_numpy(u).to(dev)
+    dv = torch.from_numpy(v).to(dev)
+    ctx = pb.Context(device=dev)
+    stream = torch.cuda.current_stream(dev)
+    out, counts, out_off = ctx.find_batched(du, dv, off, Vs)
+    cnt = counts.cpu().numpy()
+    o = out.cpu().numpy()
+    correct = all(
+        {tuple(x) for x in planted[g].tolist()} <= {tuple(x) for x in o[out_off[g]:out_off[g] + 2 * cnt[g]].reshape(-1, 2).tolist()}
+        for g in range(G))
+    for _ in range(args.warmup):
+        ctx.find_batched(du, dv, off, Vs, out=out, counts=counts, sync=False)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    l0 = ctx.launches()
+    e0.record(stream)
+    for _ in range(args.steps):
+        ctx.find_batched(du, dv, off, Vs, out=out, counts=counts, sync=False)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    # one plain call per graph, same GPU, same stream
+    plain = pb.Context(device=dev)
+    cnt_d = torch.zeros(1, dtype=torch.int64, device=dev)
+    outp = torch.empty(2 * 4096, dtype=torch.int32, device=dev)
+    for g in range(min(G, 64)):
+        plain.find(du[off[g]:off[g + 1]], dv[off[g]:off[g + 1]], int(Vs[g]), 1, out=outp, count_device=cnt_d)
+    torch.cuda.synchronize()
+    p0 = torch.cuda.Event(enable_timing=True)
+    p1 = torch.cuda.Event(enable_timing=True)
+    p0.record(stream)
+    for g in range(G):
+        plain.find(du[off[g]:off[g + 1]], dv[off[g]:off[g + 1]], int(Vs[g]), 1, out=outp, count_device=cnt_d)
+    p1.record(stream)
+    torch.cuda.synchronize()
+    ms_plain = p0.elapsed_time(p1)
+    peak, kind = peaks()
+    line = {
+        "metric": "graphs/s (batched bridge queries)", "value": G / (ms * 1e-3), "unit": "graphs/s", "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+        "config": {"workload": f"batched: {G} graphs, V log-uniform [64, 4096], density U[0.1, 0.9], seed 3",
+                   "E_total": E, "planted_subset_found": correct, "launches_per_step": (ctx.launches() - l0) / args.steps},
+        "input_GE_per_s": E / (ms * 1e-3) / 1e9,
+        "roofline": {"bound": "hbm", "achieved": 8.0 * E / (ms * 1e-3) / 1e9, "peak": peak, "unit": "GB/s",
+                     "frac": 8.0 * E / (ms * 1e-3) / 1e9 / peak, "peak_kind": kind},
+        "plain_per_graph": {"value": G / (ms_plain * 1e-3), "unit": "graphs/s", "ms_total": ms_plain},
+        "speedup_vs_plain": ms_plain / ms,
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["native", "reference"], default="native")
-    ap.add_argument("--workload", choices=["large", "mid", "small"], default="large")
+    ap.add_argument("--workload", choices=["large", "mid", "small", "batched"], default="large")
+    ap.add_argument("--graphs", type=int, default=4096, help="graphs of the batched workload")
     ap.add_argument("--density", type=float, default=None, help="override the ER density (profiling)")
     ap.add_argument("--M", type=int, default=0, help="partitions (0: automatic)")
     ap.add_argument("--no-e2e", action="store_true")
@@ -298,6 +375,8 @@ def main():
     world, rank, local = dist_setup()
     if args.impl == "reference":
         run_reference(args, world, rank)
+    elif args.workload == "batched":
+        run_batched(args, world, rank, local)
     else:
         run_native(args, world, rank, local)
 

@@ -18,7 +18,7 @@ from __future__ import annotations
 
 import ctypes
 import os
-from dataclasses import dataclass, field, asdict
+from dataclasses import dataclass, asdict
 
 import numpy as np
 
@@ -102,6 +102,29 @@ class Spec:
         return _Spec(**asdict(self))
 
 
+class _Owned:
+    """Exposes C-owned memory to numpy while holding the C handle: every array made from it keeps
+    the generator's allocation alive (numpy stores this object as the array's base)."""
+
+    def __init__(self, handle, ptr, n):
+        self._handle = handle
+        self.__array_interface__ = {"shape": (n,), "typestr": "<i4", "data": (ptr, True), "version": 3}
+
+    def __del__(self):
+        h = getattr(self, "_handle", None)
+        if h is not None and h.refs is not None:
+            h.refs -= 1
+            if h.refs == 0 and _lib is not None:
+                _lib.gg_free(h.ptr)
+                h.refs = None
+
+
+class _Handle:
+    def __init__(self, ptr):
+        self.ptr = ptr
+        self.refs = 0
+
+
 @dataclass
 class Graph:
     """An undirected edge list plus the bridges planted by construction.
@@ -117,18 +140,10 @@ class Graph:
     planted: np.ndarray
     spec: Spec | None = None
     n_er: int = 0
-    _handle: object = field(default=None, repr=False)
 
     @property
     def E(self) -> int:
         return int(self.u.shape[0])
-
-    def __del__(self):
-        h = getattr(self, "_handle", None)
-        if h is not None and _lib is not None:
-            self.u = self.v = None
-            _lib.gg_free(h)
-            self._handle = None
 
 
 def generate(spec: Spec) -> Graph:
@@ -140,14 +155,17 @@ def generate(spec: Spec) -> Graph:
         raise ValueError(f"invalid generator spec or out of memory: {spec}")
     g = h.contents
     E, V, npl = int(g.E), int(g.V), int(g.n_planted)
+    planted = np.ctypeslib.as_array(g.planted, shape=(max(npl, 1) * 2,))[: 2 * npl].reshape(npl, 2).copy()
+    handle = _Handle(h)
     if E > 0:
-        u = np.ctypeslib.as_array(g.u, shape=(E,))
-        v = np.ctypeslib.as_array(g.v, shape=(E,))
+        handle.refs = 2
+        u = np.asarray(_Owned(handle, ctypes.cast(g.u, ctypes.c_void_p).value, E))
+        v = np.asarray(_Owned(handle, ctypes.cast(g.v, ctypes.c_void_p).value, E))
     else:
+        lib.gg_free(h)
         u = np.zeros(0, np.int32)
         v = np.zeros(0, np.int32)
-    planted = np.ctypeslib.as_array(g.planted, shape=(max(npl, 1) * 2,))[: 2 * npl].reshape(npl, 2).copy()
-    return Graph(u=u, v=v, V=V, planted=planted, spec=spec, n_er=int(g.n_er), _handle=h)
+    return Graph(u=u, v=v, V=V, planted=planted, spec=spec, n_er=int(g.n_er))
 
 
 WORKLOADS = {

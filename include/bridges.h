@@ -120,6 +120,30 @@ int64_t bridges_find_host(bridges_ctx* ctx, struct CUstream_st* stream, const in
                           int32_t* out_bridges_host);
 
 /* ---------------------------------------------------------------------------------------
+ * bridges_find_batched -- G independent graphs in one persistent launch (Sec. 3 per graph).
+ *   edges_u, edges_v : device; graph g's edges are entries [edge_off[g], edge_off[g+1]) and its
+ *                      vertex ids are local, in [0, V[g]).
+ *   edge_off_host    : host, G+1 int64, non-decreasing (read during the call only).
+ *   V_host           : host, G int32 (read during the call only).
+ *   out_bridges      : device; graph g's sorted pairs start at int32 offset
+ *                      sum over h < g of 2*max(V[h]-1, 0).
+ *   out_counts_device: device, G int64; graph g's bridge count, or a negative status for that
+ *                      graph alone (e.g. BRIDGES_ERANGE).
+ * Graphs with V <= 4096 are certified and solved entirely in shared memory, one block per graph
+ * (graphs with many edges are split into partitions whose certificates are merged by the block
+ * that finishes last); the launch is a CUDA graph cached per capacity.  Larger graphs follow
+ * through the single-graph path on the same stream.  Enqueue-only: returns BRIDGES_OK or a
+ * host-detected error; synchronise the stream before reading the outputs.
+ */
+int64_t bridges_find_batched(bridges_ctx* ctx, struct CUstream_st* stream, const int32_t* edges_u,
+                             const int32_t* edges_v, const int64_t* edge_off_host, const int32_t* V_host, int32_t G,
+                             int32_t* out_bridges, int64_t* out_counts_device);
+
+/* Edge count above which a batched graph is split into partitions (0: automatic, about
+ * max(2^20, total edges / (4 x SMs))).  Returns BRIDGES_OK or BRIDGES_EINVAL. */
+int32_t bridges_ctx_set_batch_split(bridges_ctx* ctx, int64_t split_edges);
+
+/* ---------------------------------------------------------------------------------------
  * Stage entry points (for testing and composition).
  *
  * bridges_certificate -- the sparse certificate of the whole edge list after the M-way

@@ -75,6 +75,8 @@ _SIGS = {
     "bridges_ctx_last_config": (_I32, [_P, ctypes.POINTER(ctypes.c_int64), _I32]),
     "bridges_status_string": (ctypes.c_char_p, [_I32]),
     "bridges_find_noalloc": (_I64, [_P, _P, _P, _I64, _I32, _I32, _P, _P]),
+    "bridges_find_batched": (_I64, [_P, _P, _P, _P, _P, _P, _I32, _P, _P]),
+    "bridges_ctx_set_batch_split": (_I32, [_P, _I64]),
 }
 
 
@@ -219,6 +221,34 @@ class Context:
                                            _ptr(xv), xu.numel(), V, _ptr(out))
         n = _check(rc, "bridges_from_forest")
         return out[: 2 * n].view(n, 2)
+
+    def find_batched(self, u, v, edge_off, Vs, out=None, counts=None, stream=None, sync=True):
+        """bridges_find_batched.  ``edge_off`` (G+1) and ``Vs`` (G) are host integer arrays.
+        Returns (out, counts, out_off): graph g's bridges are
+        out[out_off[g] : out_off[g] + 2*counts[g]] (counts on the device)."""
+        import numpy as np
+
+        u, v = _dev_edges(u, v)
+        eo = np.ascontiguousarray(edge_off, dtype=np.int64)
+        vs = np.ascontiguousarray(Vs, dtype=np.int32)
+        G = int(vs.shape[0])
+        if eo.shape != (G + 1,):
+            raise ValueError("edge_off must have G+1 entries")
+        sizes = 2 * np.maximum(vs.astype(np.int64) - 1, 0)
+        out_off = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
+        if out is None:
+            out = torch.empty(max(int(out_off[-1]), 1), dtype=torch.int32, device=u.device)
+        if counts is None:
+            counts = torch.empty(max(G, 1), dtype=torch.int64, device=u.device)
+        rc = self._lib.bridges_find_batched(self._h, _stream(stream), _ptr(u), _ptr(v), eo.ctypes.data, vs.ctypes.data,
+                                            G, _ptr(out), _ptr(counts))
+        _check(rc, "bridges_find_batched")
+        if sync:
+            (stream or torch.cuda.current_stream()).synchronize()
+        return out, counts, out_off[:-1]
+
+    def set_batch_split(self, split_edges: int):
+        _check(self._lib.bridges_ctx_set_batch_split(self._h, int(split_edges)), "bridges_ctx_set_batch_split")
 
     def stage_ms(self):
         buf = (ctypes.c_float * 6)()

@@ -7,7 +7,11 @@
 #include <new>
 
 #include "../../include/bridges.h"
+#include "batched.h"
 #include "internal.h"
+
+#include <numeric>
+#include <vector>
 
 using namespace bridges;
 
@@ -33,6 +37,16 @@ struct bridges_ctx {
   int64_t resolved = 0;      // calls whose times have been read back
   float stage_ms[kRing][6]{};
   int64_t last_cfg[5]{};
+  // batched path: device descriptors, pinned staging and a CUDA graph per capacity
+  void* bws = nullptr;          // device: BatchArgs | ntasks | queue | tasks[cap] | done[gcap] | gerr[gcap] | slots
+  size_t bws_bytes = 0;
+  void* bstage = nullptr;        // pinned: BatchArgs | ntasks | tasks[cap]
+  size_t bstage_bytes = 0;
+  int64_t b_task_cap = 0, b_graph_cap = 0, b_slot_cap = 0;
+  cudaGraphExec_t b_exec = nullptr;
+  cudaStream_t b_exec_stream = nullptr;
+  cudaEvent_t b_done_ev = nullptr;
+  int64_t b_split_edges = 0;     // partition graphs with more edges than this (0: automatic)
 };
 
 namespace {
@@ -224,6 +238,10 @@ void bridges_ctx_destroy(bridges_ctx* c) {
   if (!c->user_ws && c->ws) cudaFree(c->ws);
   if (c->stage) cudaFree(c->stage);
   if (c->h_pinned) cudaFreeHost(c->h_pinned);
+  if (c->b_exec) cudaGraphExecDestroy(c->b_exec);
+  if (c->bws) cudaFree(c->bws);
+  if (c->bstage) cudaFreeHost(c->bstage);
+  if (c->b_done_ev) cudaEventDestroy(c->b_done_ev);
   if (c->events)
     for (auto& set : c->ev)
       for (auto& e : set) cudaEventDestroy(e);
@@ -437,3 +455,190 @@ const char* bridges_status_string(int32_t st) {
 }
 
 }  // extern "C"
+
+namespace {
+
+// Layout of the batched workspace for the given capacities (bytes from the start).
+struct BLayout {
+  size_t args, ntasks, queue, tasks, done, gerr, slots, total;
+  size_t s_args, s_ntasks, s_tasks, s_total;  // pinned staging
+};
+
+BLayout blayout(int64_t task_cap, int64_t graph_cap, int64_t slot_cap) {
+  // The first s_total bytes of the device area (args, ntasks, tasks) are a byte copy of the
+  // pinned staging area, so both use the same offsets for them.
+  BLayout L{};
+  size_t o = 0;
+  L.args = L.s_args = o;
+  o += align_up(sizeof(BatchArgs), 256);
+  L.ntasks = L.s_ntasks = o;
+  o += 256;
+  L.tasks = L.s_tasks = o;
+  o += align_up(sizeof(BatchTask) * (size_t)task_cap, 256);
+  L.s_total = o;
+  L.queue = o;
+  o += 256;
+  L.done = o;
+  o += align_up(sizeof(int32_t) * (size_t)graph_cap, 256);
+  L.gerr = o;
+  o += align_up(sizeof(int32_t) * (size_t)graph_cap, 256);
+  L.slots = o;
+  o += align_up(sizeof(uint32_t) * (size_t)std::max<int64_t>(slot_cap, 1), 256);
+  L.total = o;
+  return L;
+}
+
+int64_t next_pow2(int64_t x) {
+  int64_t p = 1;
+  while (p < x) p <<= 1;
+  return p;
+}
+
+// (Re)creates the batched buffers and the captured CUDA graph for these capacities.
+int64_t ensure_batched(bridges_ctx* c, cudaStream_t s, int64_t ntasks, int64_t G, int64_t slots) {
+  if (ntasks <= c->b_task_cap && G <= c->b_graph_cap && slots <= c->b_slot_cap && c->b_exec) return BRIDGES_OK;
+  const int64_t tcap = next_pow2(std::max<int64_t>(ntasks, 64)), gcap = next_pow2(std::max<int64_t>(G, 64));
+  const int64_t scap = next_pow2(std::max<int64_t>(slots, 1024));
+  const BLayout L = blayout(tcap, gcap, scap);
+  if (c->user_ws) return BRIDGES_ENOMEM;
+  if (c->budget && L.total + c->ws_bytes + c->stage_bytes > c->budget) return BRIDGES_ENOMEM;
+  if (c->b_done_ev) cudaEventSynchronize(c->b_done_ev);
+  cudaStreamSynchronize(s);
+  if (c->b_exec) cudaGraphExecDestroy(c->b_exec);
+  c->b_exec = nullptr;
+  if (c->bws) cudaFree(c->bws);
+  if (c->bstage) cudaFreeHost(c->bstage);
+  c->bws = nullptr;
+  c->bstage = nullptr;
+  if (cudaMalloc(&c->bws, L.total) != cudaSuccess || cudaMallocHost(&c->bstage, L.s_total) != cudaSuccess) {
+    cudaGetLastError();
+    return BRIDGES_ENOMEM;
+  }
+  if (!c->b_done_ev && cudaEventCreateWithFlags(&c->b_done_ev, cudaEventDisableTiming) != cudaSuccess)
+    return cuda_fail(cudaGetLastError());
+  c->b_task_cap = tcap;
+  c->b_graph_cap = gcap;
+  c->b_slot_cap = scap;
+  c->bws_bytes = L.total;
+  c->bstage_bytes = L.s_total;
+  // capture: reset counters, upload descriptors from the pinned staging, run the kernel
+  char* d = static_cast<char*>(c->bws);
+  char* h = static_cast<char*>(c->bstage);
+  cudaStream_t cs;
+  if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess) return cuda_fail(cudaGetLastError());
+  cudaGraph_t graph;
+  bool ok = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+  ok = ok && cudaMemsetAsync(d + L.queue, 0, 256, cs) == cudaSuccess;
+  ok = ok && cudaMemsetAsync(d + L.done, 0, L.slots - L.done, cs) == cudaSuccess;  // done and gerr
+  ok = ok && cudaMemcpyAsync(d, h, L.s_total, cudaMemcpyHostToDevice, cs) == cudaSuccess;  // args, ntasks, tasks
+  ok = ok && batched_launch(cs, reinterpret_cast<const BatchArgs*>(d + L.args), c->num_sms);
+  ok = (cudaStreamEndCapture(cs, &graph) == cudaSuccess) && ok;
+  if (ok) ok = cudaGraphInstantiate(&c->b_exec, graph, 0) == cudaSuccess;
+  cudaGraphDestroy(graph);
+  cudaStreamDestroy(cs);
+  if (!ok) {
+    cudaGetLastError();
+    c->b_exec = nullptr;
+    return BRIDGES_ECUDA;
+  }
+  return BRIDGES_OK;
+}
+
+}  // namespace
+
+extern "C" int64_t bridges_find_batched(bridges_ctx* c, struct CUstream_st* stream, const int32_t* u, const int32_t* v,
+                                        const int64_t* edge_off, const int32_t* Vs, int32_t G, int32_t* out,
+                                        int64_t* out_counts) {
+  if (!c || G < 0 || (G > 0 && (!edge_off || !Vs || !out_counts))) return BRIDGES_EINVAL;
+  if (G == 0) return BRIDGES_OK;
+  int64_t total_out = 0, total_e = 0;
+  for (int32_t g = 0; g < G; g++) {
+    if (Vs[g] < 0 || Vs[g] > (1 << 30) || edge_off[g] < 0 || edge_off[g + 1] < edge_off[g]) return BRIDGES_EINVAL;
+    total_out += 2 * (int64_t)std::max(Vs[g] - 1, 0);
+    total_e += edge_off[g + 1] - edge_off[g];
+  }
+  if (total_e > 0 && (!u || !v)) return BRIDGES_EINVAL;
+  if (total_out > 0 && !out) return BRIDGES_EINVAL;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  if (cudaSetDevice(c->device) != cudaSuccess) return cuda_fail(cudaGetLastError());
+  // plan: small graphs become tasks (large edge counts split into partitions); graphs above
+  // the shared-memory size go through the single-graph path afterwards
+  const int64_t split = c->b_split_edges > 0
+                            ? c->b_split_edges
+                            : std::max<int64_t>(1 << 20, total_e / std::max(1, c->num_sms * 4));
+  std::vector<BatchTask> tasks;
+  std::vector<int32_t> large;
+  std::vector<int64_t> out_off(G);
+  int64_t o = 0, slot = 0;
+  for (int32_t g = 0; g < G; g++) {
+    out_off[g] = o;
+    o += 2 * (int64_t)std::max(Vs[g] - 1, 0);
+    const int64_t lo = edge_off[g], hi = edge_off[g + 1], E = hi - lo;
+    if (Vs[g] > kBatchVmax) {
+      large.push_back(g);
+      continue;
+    }
+    const int32_t np = (int32_t)std::min<int64_t>(64, std::max<int64_t>(1, (E + split - 1) / split));
+    for (int32_t p = 0; p < np; p++) {
+      BatchTask t{};
+      t.lo = lo + E * p / np;
+      t.hi = lo + E * (p + 1) / np;
+      t.out_off = out_off[g];
+      t.slot = np > 1 ? slot + (int64_t)p * (2 + 2 * (int64_t)Vs[g]) : 0;
+      t.g = g;
+      t.part = p;
+      t.nparts = np;
+      t.V = Vs[g];
+      tasks.push_back(t);
+    }
+    if (np > 1) slot += (int64_t)np * (2 + 2 * (int64_t)Vs[g]);
+  }
+  // largest tasks first: the persistent blocks then finish together
+  std::stable_sort(tasks.begin(), tasks.end(),
+                   [](const BatchTask& x, const BatchTask& y) { return x.hi - x.lo > y.hi - y.lo; });
+  int64_t rc = BRIDGES_OK;
+  if (!tasks.empty()) {
+    rc = ensure_batched(c, s, (int64_t)tasks.size(), G, slot);
+    if (rc) return rc;
+    // the staging area may still feed the previous batch's upload
+    cudaEventSynchronize(c->b_done_ev);
+    const BLayout L = blayout(c->b_task_cap, c->b_graph_cap, c->b_slot_cap);
+    char* d = static_cast<char*>(c->bws);
+    char* h = static_cast<char*>(c->bstage);
+    BatchArgs A{};
+    A.u = u;
+    A.v = v;
+    A.tasks = reinterpret_cast<const BatchTask*>(d + L.tasks);
+    A.d_ntasks = reinterpret_cast<const int32_t*>(d + L.ntasks);
+    A.queue = reinterpret_cast<int32_t*>(d + L.queue);
+    A.done = reinterpret_cast<int32_t*>(d + L.done);
+    A.gerr = reinterpret_cast<int32_t*>(d + L.gerr);
+    A.slots = reinterpret_cast<uint32_t*>(d + L.slots);
+    A.out = out;
+    A.counts = out_counts;
+    A.G = G;
+    A.slot_words = c->b_slot_cap;
+    std::memcpy(h + L.s_args, &A, sizeof(A));
+    const int32_t nt = (int32_t)tasks.size();
+    std::memcpy(h + L.s_ntasks, &nt, sizeof(nt));
+    std::memcpy(h + L.s_tasks, tasks.data(), sizeof(BatchTask) * tasks.size());
+    if (cudaGraphLaunch(c->b_exec, s) != cudaSuccess) return cuda_fail(cudaGetLastError());
+    if (cudaEventRecord(c->b_done_ev, s) != cudaSuccess) return cuda_fail(cudaGetLastError());
+    c->launches += 1;
+  }
+  for (int32_t g : large) {
+    Carved k{};
+    const int64_t E = edge_off[g + 1] - edge_off[g];
+    rc = run_path(c, s, u + edge_off[g], v + edge_off[g], E, Vs[g], 0, out + out_off[g], &k, nullptr);
+    if (rc) return rc;
+    if (cudaMemcpyAsync(out_counts + g, k.fin.count, sizeof(int64_t), cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+      return cuda_fail(cudaGetLastError());
+  }
+  return BRIDGES_OK;
+}
+
+extern "C" int32_t bridges_ctx_set_batch_split(bridges_ctx* c, int64_t split_edges) {
+  if (!c || split_edges < 0) return BRIDGES_EINVAL;
+  c->b_split_edges = split_edges;
+  return BRIDGES_OK;
+}

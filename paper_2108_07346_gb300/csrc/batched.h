@@ -1,0 +1,43 @@
+// batched.h -- device-side descriptors of the batched (many small graphs) kernel.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace bridges {
+
+constexpr int kBatchVmax = 4096;  // graphs up to this many vertices are handled in shared memory
+
+// One unit of work: a whole graph (nparts == 1) or partition `part` of it.
+struct BatchTask {
+  int64_t lo, hi;    // edge range in the concatenated edge arrays
+  int64_t out_off;   // int32 offset of the graph's output pairs
+  int64_t slot;      // u32 offset of this partition's certificate slot (nparts > 1)
+  int32_t g;         // graph index
+  int32_t part;      // partition index within the graph
+  int32_t nparts;    // partitions of the graph
+  int32_t V;         // vertices of the graph
+};
+
+// Everything the kernel reads, in device memory so a captured CUDA graph stays valid when the
+// caller's pointers change between calls.
+struct BatchArgs {
+  const int32_t* u;
+  const int32_t* v;
+  const BatchTask* tasks;
+  const int32_t* d_ntasks;
+  int32_t* queue;    // next task (atomic)
+  int32_t* done;     // per graph: partitions finished
+  int32_t* gerr;     // per graph: first error of any partition
+  uint32_t* slots;   // certificates of partitions
+  int32_t* out;
+  int64_t* counts;
+  int32_t G;           // graphs (bounds the graph index of every task)
+  int64_t slot_words;  // capacity of slots (u32)
+};
+
+size_t batched_smem_bytes();
+// Launches the persistent kernel (one block per SM) reading its arguments from *dev_args.
+bool batched_launch(cudaStream_t s, const BatchArgs* dev_args, int num_sms);
+
+}  // namespace bridges

@@ -1,0 +1,112 @@
+"""Batched path (bridges_find_batched) against the oracle, graph by graph."""
+import numpy as np
+import pytest
+import torch
+
+import graphgen
+import oracle
+
+pytestmark = pytest.mark.gpu
+
+
+def concat(graphs):
+    u = np.concatenate([g[0] for g in graphs]).astype(np.int32) if graphs else np.zeros(0, np.int32)
+    v = np.concatenate([g[1] for g in graphs]).astype(np.int32) if graphs else np.zeros(0, np.int32)
+    off = np.concatenate([[0], np.cumsum([len(g[0]) for g in graphs])]).astype(np.int64)
+    Vs = np.array([g[2] for g in graphs], np.int32)
+    return u, v, off, Vs
+
+
+def run_batch(ctx, graphs):
+    u, v, off, Vs = concat(graphs)
+    du = torch.from_numpy(u).cuda()
+    dv = torch.from_numpy(v).cuda()
+    out, counts, out_off = ctx.find_batched(du, dv, off, Vs)
+    out = out.cpu().numpy()
+    counts = counts.cpu().numpy()
+    res = []
+    for g in range(len(graphs)):
+        n = int(counts[g])
+        res.append(n if n < 0 else out[out_off[g]: out_off[g] + 2 * n].reshape(n, 2))
+    return res
+
+
+@pytest.fixture(scope="module")
+def ctx(cuda_lib):
+    return cuda_lib.Context(device="cuda:0")
+
+
+def test_random_small_graphs(ctx):
+    rng = np.random.default_rng(31)
+    graphs = []
+    for t in range(300):
+        V = int(rng.integers(1, 200))
+        E = int(rng.integers(0, 4 * V + 1))
+        u, v = graphgen.random_multigraph(50000 + t, V, E)
+        graphs.append((u, v, V))
+    res = run_batch(ctx, graphs)
+    for (u, v, V), got in zip(graphs, res):
+        assert got.tolist() == oracle.dfs_bridges(u, v, V).tolist()
+
+
+def test_batched_workload_specs(ctx):
+    graphs = []
+    for i in range(48):
+        g = graphgen.generate(graphgen.workload_spec("batched", 3, i))
+        graphs.append((g.u, g.v, g.V, g.planted))
+    res = run_batch(ctx, [(a, b, c) for a, b, c, _ in graphs])
+    for (u, v, V, planted), got in zip(graphs, res):
+        ref = oracle.bridges(u, v, V, 4)
+        assert got.tolist() == ref.tolist()
+        assert {tuple(x) for x in planted.tolist()} <= {tuple(x) for x in got.tolist()}
+
+
+def test_split_partitions_and_large_graphs(ctx, cuda_lib):
+    """Force partitioning (certificates merged by the last block) and include graphs above the
+    shared-memory size (single-graph path)."""
+    graphs = []
+    for i in range(6):
+        g = graphgen.generate(graphgen.workload_spec("batched", 3, 100 + i))
+        graphs.append((g.u, g.v, g.V))
+    big = graphgen.workload("small")  # V = 2088: still shared memory, many edges
+    graphs.append((big.u, big.v, big.V))
+    n = 9000  # above 4096 vertices: a tree plus a few cycles
+    rng = np.random.default_rng(4)
+    par = (rng.random(n - 1) * np.arange(1, n)).astype(np.int32)
+    ch = np.arange(1, n, dtype=np.int32)
+    graphs.append((np.concatenate([par, [5, 77]]).astype(np.int32), np.concatenate([ch, [8000, 3]]).astype(np.int32), n))
+    ctx2 = cuda_lib.Context(device="cuda:0")
+    ctx2.set_batch_split(1000)
+    for c in (ctx, ctx2):
+        res = run_batch(c, graphs)
+        for (u, v, V), got in zip(graphs, res):
+            assert got.tolist() == oracle.dfs_bridges(u, v, V).tolist()
+
+
+def test_errors_are_per_graph(ctx):
+    good = graphgen.random_multigraph(7, 20, 30)
+    bad = (np.array([0, 1], np.int32), np.array([1, 50], np.int32), 10)
+    res = run_batch(ctx, [(good[0], good[1], 20), bad, (good[0], good[1], 20)])
+    assert res[1] == -2
+    ref = oracle.dfs_bridges(good[0], good[1], 20).tolist()
+    assert res[0].tolist() == ref and res[2].tolist() == ref
+
+
+def test_replay_with_new_inputs(ctx):
+    """The cached CUDA graph is replayed with different graphs and pointers."""
+    for seed in range(3):
+        graphs = []
+        for t in range(20):
+            V = 30 + 10 * t
+            u, v = graphgen.random_multigraph(seed * 1000 + t, V, 3 * V)
+            graphs.append((u, v, V))
+        res = run_batch(ctx, graphs)
+        for (u, v, V), got in zip(graphs, res):
+            assert got.tolist() == oracle.dfs_bridges(u, v, V).tolist()
+
+
+def test_empty_and_degenerate(ctx):
+    e = np.zeros(0, np.int32)
+    res = run_batch(ctx, [(e, e, 0), (e, e, 1), (np.array([0], np.int32), np.array([0], np.int32), 1),
+                          (np.array([0], np.int32), np.array([1], np.int32), 2)])
+    assert [r.tolist() for r in res] == [[], [], [], [[0, 1]]]
