@@ -356,13 +356,94 @@ def run_batched(args, world, rank, local):
     print(json.dumps(line), flush=True)
 
 
+def run_served(args, world, rank, local):
+    """Poisson arrivals of bridge queries against the continuous-batching server."""
+    import threading
+
+    import torch
+
+    import paper_2108_07346_gb300 as pb
+
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    rng = np.random.default_rng(4)
+    pool = []
+    for i in range(args.pool):
+        g = graphgen.generate(graphgen.workload_spec("served", 4, i))
+        pool.append((torch.from_numpy(np.array(g.u)).to(dev), torch.from_numpy(np.array(g.v)).to(dev), g.V, g.E))
+    N = args.requests
+    gaps = rng.exponential(1.0 / args.rate, N)
+    arrival = np.cumsum(gaps)
+    ring = 256
+    vmax = max(p[2] for p in pool)
+    outs = [torch.empty(2 * vmax, dtype=torch.int32, device=dev) for _ in range(ring)]
+    srv = pb.Server(device=dev, mem_budget=int(args.budget_gb * (1 << 30)), max_slots=args.slots)
+    # warm-up: every pool graph once
+    for i, (u, v, V, E) in enumerate(pool):
+        srv.wait(srv.submit(u, v, V, out=outs[i % ring]))
+    tickets = [None] * N
+    lat = np.zeros(N)
+    edges = 0
+    t0 = time.perf_counter()
+    for i in range(N):
+        j = i % ring
+        if i >= ring:
+            res = srv.wait(tickets[i - ring])
+            lat[i - ring] = res[1]
+        due = t0 + arrival[i]
+        now = time.perf_counter()
+        if due > now:
+            time.sleep(due - now)
+        u, v, V, E = pool[i % len(pool)]
+        tickets[i] = srv.submit(u, v, V, out=outs[j])
+        edges += E
+    for i in range(max(0, N - ring), N):
+        lat[i] = srv.wait(tickets[i])[1]
+    wall = time.perf_counter() - t0
+    st = srv.stats()
+    srv.close()
+    # one plain call per request, back to back, same requests
+    ctx = pb.Context(device=dev)
+    cnt = torch.zeros(1, dtype=torch.int64, device=dev)
+    for u, v, V, E in pool:
+        ctx.find(u, v, V, 0, out=outs[0], count_device=cnt)
+    torch.cuda.synchronize()
+    tp = time.perf_counter()
+    nplain = min(N, args.plain)
+    for i in range(nplain):
+        u, v, V, E = pool[i % len(pool)]
+        ctx.find(u, v, V, 0, out=outs[0], count_device=cnt)
+    torch.cuda.synchronize()
+    plain_s = time.perf_counter() - tp
+    line = {
+        "metric": "served graphs/s with p50/p99 latency", "value": N / wall, "unit": "graphs/s", "n_gpus": 1,
+        "steps": N, "warmup": len(pool), "ms_per_step": wall / N * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+        "config": {"workload": f"served: Poisson arrivals {args.rate}/s, {N} requests over {len(pool)} resident graphs, "
+                               "V log-uniform [256, 65536], density U[0.05, 0.6], clusters of 512 with pendant "
+                               "paths and extra inter-cluster edges, seed 4",
+                   "budget_gb": args.budget_gb, "slots": args.slots, "mean_edges": edges / N},
+        "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
+                       "max": float(lat.max())},
+        "served_GE_per_s": edges / wall / 1e9, "offered_per_s": args.rate, "server_stats": st,
+        "plain_per_graph": {"value": nplain / plain_s, "unit": "graphs/s"},
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["native", "reference"], default="native")
-    ap.add_argument("--workload", choices=["large", "mid", "small", "batched"], default="large")
+    ap.add_argument("--workload", choices=["large", "mid", "small", "batched", "served"], default="large")
+    ap.add_argument("--requests", type=int, default=4000, help="served: requests")
+    ap.add_argument("--rate", type=float, default=2000.0, help="served: mean arrivals per second")
+    ap.add_argument("--pool", type=int, default=64, help="served: distinct resident graphs")
+    ap.add_argument("--slots", type=int, default=4, help="served: concurrent units of work")
+    ap.add_argument("--budget-gb", type=float, default=40.0, help="served: device-memory budget")
+    ap.add_argument("--plain", type=int, default=1000, help="served: plain calls timed for comparison")
     ap.add_argument("--graphs", type=int, default=4096, help="graphs of the batched workload")
     ap.add_argument("--density", type=float, default=None, help="override the ER density (profiling)")
     ap.add_argument("--M", type=int, default=0, help="partitions (0: automatic)")
@@ -377,6 +458,8 @@ def main():
         run_reference(args, world, rank)
     elif args.workload == "batched":
         run_batched(args, world, rank, local)
+    elif args.workload == "served":
+        run_served(args, world, rank, local)
     else:
         run_native(args, world, rank, local)
 

@@ -144,6 +144,48 @@ int64_t bridges_find_batched(bridges_ctx* ctx, struct CUstream_st* stream, const
 int32_t bridges_ctx_set_batch_split(bridges_ctx* ctx, int64_t split_edges);
 
 /* ---------------------------------------------------------------------------------------
+ * Serving: a continuous-batching request loop on one GPU (thread-safe).
+ *
+ * A request is a graph whose edge arrays are already resident on the device; the caller keeps
+ * edges_u / edges_v / out_bridges valid until the request completes.  A scheduler thread keeps
+ * up to max_slots units of work in flight, each on its own stream and workspace, so requests
+ * overlap on the device.  Queued small graphs (V <= 4096) are gathered into one batched launch
+ * (as bridges_find_batched); a large graph runs the single-graph path once its workspace fits
+ * in what mem_budget_bytes has left.  Requests arriving while others run are admitted as slots
+ * and memory free up.  Results are exact and identical to a call on the graph alone.
+ */
+typedef struct bridges_request {
+  const int32_t* edges_u; /* device, E int32 */
+  const int32_t* edges_v; /* device, E int32 */
+  int64_t E;
+  int32_t V;
+  int32_t M;              /* partitions for the single-graph path (<= 0: automatic) */
+  int32_t* out_bridges;   /* device, capacity 2*max(V-1,0) int32 */
+} bridges_request;
+
+typedef struct bridges_server bridges_server;
+
+/* max_slots <= 0: 4; max_batch <= 0: 4096 graphs per batched launch; mem_budget_bytes 0: no
+ * limit; opts as for contexts (may be NULL).  Returns NULL on failure. */
+bridges_server* bridges_server_create(int device, size_t mem_budget_bytes, int32_t max_slots, int32_t max_batch,
+                                      const bridges_opts* opts);
+/* Queues a request; *ticket identifies it.  BRIDGES_EAGAIN if its workspace exceeds the whole
+ * budget (it could never run); BRIDGES_EINVAL for bad arguments. */
+int32_t bridges_server_submit(bridges_server* srv, const bridges_request* req, uint64_t* ticket);
+/* BRIDGES_EBUSY while the request is queued or running; BRIDGES_OK when done: *count gets the
+ * bridge count (or the request's negative status) and *latency_ms the time from submit to
+ * completion; the ticket is then released.  Either output pointer may be NULL. */
+int32_t bridges_server_poll(bridges_server* srv, uint64_t ticket, int64_t* count, double* latency_ms);
+/* As poll, but waits up to timeout_ms; BRIDGES_ETIMEDOUT if the request is still not done. */
+int32_t bridges_server_wait(bridges_server* srv, uint64_t ticket, int64_t timeout_ms, int64_t* count,
+                            double* latency_ms);
+/* [0] completed, [1] batched launches, [2] single-graph launches, [3] most requests in flight at
+ * once, [4] failed launches, [5] queued now.  Returns the number of values written. */
+int32_t bridges_server_stats(bridges_server* srv, int64_t* vals, int32_t n);
+/* Finishes queued and running requests, then frees everything. */
+void bridges_server_destroy(bridges_server* srv);
+
+/* ---------------------------------------------------------------------------------------
  * Stage entry points (for testing and composition).
  *
  * bridges_certificate -- the sparse certificate of the whole edge list after the M-way

@@ -77,6 +77,13 @@ _SIGS = {
     "bridges_find_noalloc": (_I64, [_P, _P, _P, _I64, _I32, _I32, _P, _P]),
     "bridges_find_batched": (_I64, [_P, _P, _P, _P, _P, _P, _I32, _P, _P]),
     "bridges_ctx_set_batch_split": (_I32, [_P, _I64]),
+    "bridges_server_create": (_P, [ctypes.c_int, ctypes.c_size_t, _I32, _I32, ctypes.POINTER(Opts)]),
+    "bridges_server_submit": (_I32, [_P, _P, ctypes.POINTER(ctypes.c_uint64)]),
+    "bridges_server_poll": (_I32, [_P, ctypes.c_uint64, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_double)]),
+    "bridges_server_wait": (_I32, [_P, ctypes.c_uint64, _I64, ctypes.POINTER(ctypes.c_int64),
+                                   ctypes.POINTER(ctypes.c_double)]),
+    "bridges_server_stats": (_I32, [_P, ctypes.POINTER(ctypes.c_int64), _I32]),
+    "bridges_server_destroy": (None, [_P]),
 }
 
 
@@ -271,6 +278,85 @@ class Context:
         k = self._lib.bridges_ctx_last_config(self._h, buf, 5)
         names = ["M", "fan_in", "blocks_per_partition", "block", "warm_edges"]
         return {names[i]: int(buf[i]) for i in range(k)}
+
+
+class Request(ctypes.Structure):
+    _fields_ = [
+        ("edges_u", ctypes.c_void_p),
+        ("edges_v", ctypes.c_void_p),
+        ("E", ctypes.c_int64),
+        ("V", ctypes.c_int32),
+        ("M", ctypes.c_int32),
+        ("out_bridges", ctypes.c_void_p),
+    ]
+
+
+class Server:
+    """bridges_server: continuous batching of bridge queries on one GPU (thread-safe).
+
+    ``submit`` keeps references to the request's tensors until its result has been collected."""
+
+    def __init__(self, device=None, mem_budget=0, max_slots=4, max_batch=4096, **opts):
+        self._lib = load()
+        dev = torch.device("cuda", torch.cuda.current_device()) if device is None else torch.device(device)
+        self.device = dev
+        o = Opts()
+        o.warm_edges = opts.get("warm_edges", -1)
+        o.M = opts.get("M", 0)
+        h = self._lib.bridges_server_create(dev.index, int(mem_budget), max_slots, max_batch, ctypes.byref(o))
+        if not h:
+            raise BridgesError(-4, "bridges_server_create")
+        self._h = ctypes.c_void_p(h)
+        self._live = {}
+
+    def submit(self, u, v, V: int, out=None, M: int = 0) -> int:
+        u, v = _dev_edges(u, v)
+        if out is None:
+            out = torch.empty(2 * max(V - 1, 1), dtype=torch.int32, device=u.device)
+        r = Request(u.data_ptr(), v.data_ptr(), u.numel(), V, M, out.data_ptr())
+        t = ctypes.c_uint64(0)
+        _check(self._lib.bridges_server_submit(self._h, ctypes.byref(r), ctypes.byref(t)), "bridges_server_submit")
+        self._live[t.value] = (u, v, out)
+        return t.value
+
+    def _result(self, ticket, rc, cnt, lat):
+        if rc == -7:
+            return None
+        _check(rc, "bridges_server")
+        u, v, out = self._live.pop(ticket)
+        n = int(cnt.value)
+        if n < 0:
+            raise BridgesError(n, "request")
+        return out[: 2 * n].view(n, 2), float(lat.value)
+
+    def poll(self, ticket: int):
+        """None while pending, else (bridges (n, 2) device view, latency ms)."""
+        cnt, lat = ctypes.c_int64(0), ctypes.c_double(0)
+        rc = self._lib.bridges_server_poll(self._h, ticket, ctypes.byref(cnt), ctypes.byref(lat))
+        return self._result(ticket, rc, cnt, lat)
+
+    def wait(self, ticket: int, timeout_ms: int = 60000):
+        cnt, lat = ctypes.c_int64(0), ctypes.c_double(0)
+        rc = self._lib.bridges_server_wait(self._h, ticket, timeout_ms, ctypes.byref(cnt), ctypes.byref(lat))
+        return self._result(ticket, rc, cnt, lat)
+
+    def stats(self):
+        buf = (ctypes.c_int64 * 6)()
+        k = self._lib.bridges_server_stats(self._h, buf, 6)
+        names = ["completed", "batches", "singles", "max_in_flight", "failures", "queued"]
+        return {names[i]: int(buf[i]) for i in range(k)}
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.bridges_server_destroy(self._h)
+            self._h = None
+            self._live.clear()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def bridges_find(u, v, V: int, M: int = 0, out=None):

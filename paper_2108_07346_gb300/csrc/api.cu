@@ -8,6 +8,7 @@
 
 #include "../../include/bridges.h"
 #include "batched.h"
+#include "ctx.h"
 #include "internal.h"
 
 #include <numeric>
@@ -15,39 +16,8 @@
 
 using namespace bridges;
 
-struct bridges_ctx {
-  int device = 0;
-  size_t budget = 0;  // 0: unlimited
-  bool user_ws = false;
-  void* ws = nullptr;
-  size_t ws_bytes = 0;
-  // device staging for bridges_find_host
-  int32_t* stage = nullptr;
-  size_t stage_bytes = 0;
-  int64_t* h_pinned = nullptr;  // pinned host scratch (counts)
-  bridges_opts opts{};
-  int num_sms = 0;
-  size_t smem_optin = 0;
-  int64_t launches = 0;
-  // profiling: a ring of kRing event sets, one per call; slot = call index % kRing
-  static constexpr int kRing = 32;
-  cudaEvent_t ev[kRing][8]{};
-  bool events = false;
-  int64_t calls = 0;         // profiled calls issued
-  int64_t resolved = 0;      // calls whose times have been read back
-  float stage_ms[kRing][6]{};
-  int64_t last_cfg[5]{};
-  // batched path: device descriptors, pinned staging and a CUDA graph per capacity
-  void* bws = nullptr;          // device: BatchArgs | ntasks | queue | tasks[cap] | done[gcap] | gerr[gcap] | slots
-  size_t bws_bytes = 0;
-  void* bstage = nullptr;        // pinned: BatchArgs | ntasks | tasks[cap]
-  size_t bstage_bytes = 0;
-  int64_t b_task_cap = 0, b_graph_cap = 0, b_slot_cap = 0;
-  cudaGraphExec_t b_exec = nullptr;
-  cudaStream_t b_exec_stream = nullptr;
-  cudaEvent_t b_done_ev = nullptr;
-  int64_t b_split_edges = 0;     // partition graphs with more edges than this (0: automatic)
-};
+
+
 
 namespace {
 
@@ -546,6 +516,84 @@ int64_t ensure_batched(bridges_ctx* c, cudaStream_t s, int64_t ntasks, int64_t G
 
 }  // namespace
 
+namespace bridges {
+
+// Splits graphs with many edges into partitions (slot offsets filled in) and orders the tasks
+// largest first.  Returns the certificate slot words needed.
+int64_t plan_batch_tasks(std::vector<BatchTask>& graphs, int64_t split, std::vector<BatchTask>& tasks) {
+  int64_t slot = 0;
+  tasks.clear();
+  for (const BatchTask& g : graphs) {
+    const int64_t E = g.hi - g.lo;
+    const int32_t np = (int32_t)std::min<int64_t>(64, std::max<int64_t>(1, (E + split - 1) / split));
+    for (int32_t p = 0; p < np; p++) {
+      BatchTask t = g;
+      t.lo = g.lo + E * p / np;
+      t.hi = g.lo + E * (p + 1) / np;
+      t.slot = np > 1 ? slot + (int64_t)p * (2 + 2 * (int64_t)g.V) : 0;
+      t.part = p;
+      t.nparts = np;
+      tasks.push_back(t);
+    }
+    if (np > 1) slot += (int64_t)np * (2 + 2 * (int64_t)g.V);
+  }
+  std::stable_sort(tasks.begin(), tasks.end(),
+                   [](const BatchTask& x, const BatchTask& y) { return x.hi - x.lo > y.hi - y.lo; });
+  return slot;
+}
+
+// Enqueues one persistent launch over `tasks` (G graphs) on stream s, through the context's
+// cached CUDA graph.
+int64_t launch_batch_tasks(bridges_ctx* c, cudaStream_t s, const std::vector<BatchTask>& tasks, int32_t G,
+                           int64_t slot_words) {
+  if (tasks.empty()) return BRIDGES_OK;
+  int64_t rc = ensure_batched(c, s, (int64_t)tasks.size(), G, slot_words);
+  if (rc) return rc;
+  // the staging area may still feed the previous batch's upload
+  cudaEventSynchronize(c->b_done_ev);
+  const BLayout L = blayout(c->b_task_cap, c->b_graph_cap, c->b_slot_cap);
+  char* d = static_cast<char*>(c->bws);
+  char* h = static_cast<char*>(c->bstage);
+  BatchArgs A{};
+  A.tasks = reinterpret_cast<const BatchTask*>(d + L.tasks);
+  A.d_ntasks = reinterpret_cast<const int32_t*>(d + L.ntasks);
+  A.queue = reinterpret_cast<int32_t*>(d + L.queue);
+  A.done = reinterpret_cast<int32_t*>(d + L.done);
+  A.gerr = reinterpret_cast<int32_t*>(d + L.gerr);
+  A.slots = reinterpret_cast<uint32_t*>(d + L.slots);
+  A.G = G;
+  A.slot_words = c->b_slot_cap;
+  std::memcpy(h + L.s_args, &A, sizeof(A));
+  const int32_t nt = (int32_t)tasks.size();
+  std::memcpy(h + L.s_ntasks, &nt, sizeof(nt));
+  std::memcpy(h + L.s_tasks, tasks.data(), sizeof(BatchTask) * tasks.size());
+  if (cudaGraphLaunch(c->b_exec, s) != cudaSuccess) return cuda_fail(cudaGetLastError());
+  if (cudaEventRecord(c->b_done_ev, s) != cudaSuccess) return cuda_fail(cudaGetLastError());
+  c->launches += 1;
+  return BRIDGES_OK;
+}
+
+int64_t default_split(const bridges_ctx* c, int64_t total_e) {
+  return c->b_split_edges > 0 ? c->b_split_edges
+                              : std::max<int64_t>(1 << 20, total_e / std::max(1, c->num_sms * 4));
+}
+
+// The single-graph path on a context, count copied to count_dev (device).
+int64_t run_single(bridges_ctx* c, cudaStream_t s, const int32_t* u, const int32_t* v, int64_t E, int32_t V, int32_t M,
+                   int32_t* out, int64_t* count_dev) {
+  Carved k{};
+  int32_t dummy[1];
+  int64_t rc = run_path(c, s, u, v, E, V, M, out ? out : dummy, &k, nullptr);
+  if (rc) return rc;
+  if (cudaMemcpyAsync(count_dev, k.fin.count, sizeof(int64_t), cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+    return cuda_fail(cudaGetLastError());
+  return BRIDGES_OK;
+}
+
+size_t single_workspace_bytes(const bridges_ctx* c, int64_t E, int32_t V) { return total_bytes(plan_for(c, E, V, 0)); }
+
+}  // namespace bridges
+
 extern "C" int64_t bridges_find_batched(bridges_ctx* c, struct CUstream_st* stream, const int32_t* u, const int32_t* v,
                                         const int64_t* edge_off, const int32_t* Vs, int32_t G, int32_t* out,
                                         int64_t* out_counts) {
@@ -561,78 +609,37 @@ extern "C" int64_t bridges_find_batched(bridges_ctx* c, struct CUstream_st* stre
   if (total_out > 0 && !out) return BRIDGES_EINVAL;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   if (cudaSetDevice(c->device) != cudaSuccess) return cuda_fail(cudaGetLastError());
-  // plan: small graphs become tasks (large edge counts split into partitions); graphs above
-  // the shared-memory size go through the single-graph path afterwards
-  const int64_t split = c->b_split_edges > 0
-                            ? c->b_split_edges
-                            : std::max<int64_t>(1 << 20, total_e / std::max(1, c->num_sms * 4));
-  std::vector<BatchTask> tasks;
+  // small graphs become batch tasks; graphs above the shared-memory size take the single-graph
+  // path afterwards on the same stream
+  std::vector<BatchTask> graphs, tasks;
   std::vector<int32_t> large;
   std::vector<int64_t> out_off(G);
-  int64_t o = 0, slot = 0;
+  int64_t o = 0;
   for (int32_t g = 0; g < G; g++) {
     out_off[g] = o;
     o += 2 * (int64_t)std::max(Vs[g] - 1, 0);
-    const int64_t lo = edge_off[g], hi = edge_off[g + 1], E = hi - lo;
     if (Vs[g] > kBatchVmax) {
       large.push_back(g);
       continue;
     }
-    const int32_t np = (int32_t)std::min<int64_t>(64, std::max<int64_t>(1, (E + split - 1) / split));
-    for (int32_t p = 0; p < np; p++) {
-      BatchTask t{};
-      t.lo = lo + E * p / np;
-      t.hi = lo + E * (p + 1) / np;
-      t.out_off = out_off[g];
-      t.slot = np > 1 ? slot + (int64_t)p * (2 + 2 * (int64_t)Vs[g]) : 0;
-      t.g = g;
-      t.part = p;
-      t.nparts = np;
-      t.V = Vs[g];
-      tasks.push_back(t);
-    }
-    if (np > 1) slot += (int64_t)np * (2 + 2 * (int64_t)Vs[g]);
+    BatchTask t{};
+    t.u = u;
+    t.v = v;
+    t.lo = edge_off[g];
+    t.hi = edge_off[g + 1];
+    t.out = out ? out + out_off[g] : nullptr;
+    t.count = out_counts + g;
+    t.g = (int32_t)graphs.size();
+    t.V = Vs[g];
+    graphs.push_back(t);
   }
-  // largest tasks first: the persistent blocks then finish together
-  std::stable_sort(tasks.begin(), tasks.end(),
-                   [](const BatchTask& x, const BatchTask& y) { return x.hi - x.lo > y.hi - y.lo; });
-  int64_t rc = BRIDGES_OK;
-  if (!tasks.empty()) {
-    rc = ensure_batched(c, s, (int64_t)tasks.size(), G, slot);
-    if (rc) return rc;
-    // the staging area may still feed the previous batch's upload
-    cudaEventSynchronize(c->b_done_ev);
-    const BLayout L = blayout(c->b_task_cap, c->b_graph_cap, c->b_slot_cap);
-    char* d = static_cast<char*>(c->bws);
-    char* h = static_cast<char*>(c->bstage);
-    BatchArgs A{};
-    A.u = u;
-    A.v = v;
-    A.tasks = reinterpret_cast<const BatchTask*>(d + L.tasks);
-    A.d_ntasks = reinterpret_cast<const int32_t*>(d + L.ntasks);
-    A.queue = reinterpret_cast<int32_t*>(d + L.queue);
-    A.done = reinterpret_cast<int32_t*>(d + L.done);
-    A.gerr = reinterpret_cast<int32_t*>(d + L.gerr);
-    A.slots = reinterpret_cast<uint32_t*>(d + L.slots);
-    A.out = out;
-    A.counts = out_counts;
-    A.G = G;
-    A.slot_words = c->b_slot_cap;
-    std::memcpy(h + L.s_args, &A, sizeof(A));
-    const int32_t nt = (int32_t)tasks.size();
-    std::memcpy(h + L.s_ntasks, &nt, sizeof(nt));
-    std::memcpy(h + L.s_tasks, tasks.data(), sizeof(BatchTask) * tasks.size());
-    if (cudaGraphLaunch(c->b_exec, s) != cudaSuccess) return cuda_fail(cudaGetLastError());
-    if (cudaEventRecord(c->b_done_ev, s) != cudaSuccess) return cuda_fail(cudaGetLastError());
-    c->launches += 1;
-  }
+  const int64_t slots = plan_batch_tasks(graphs, default_split(c, total_e), tasks);
+  int64_t rc = launch_batch_tasks(c, s, tasks, (int32_t)graphs.size(), slots);
+  if (rc) return rc;
   for (int32_t g : large) {
-    Carved k{};
-    const int64_t E = edge_off[g + 1] - edge_off[g];
-    rc = run_path(c, s, u + edge_off[g], v + edge_off[g], E, Vs[g], 0, out + out_off[g], &k, nullptr);
+    rc = run_single(c, s, u + edge_off[g], v + edge_off[g], edge_off[g + 1] - edge_off[g], Vs[g], 0, out + out_off[g],
+                    out_counts + g);
     if (rc) return rc;
-    if (cudaMemcpyAsync(out_counts + g, k.fin.count, sizeof(int64_t), cudaMemcpyDeviceToDevice, s) != cudaSuccess)
-      return cuda_fail(cudaGetLastError());
   }
   return BRIDGES_OK;
 }

@@ -457,10 +457,10 @@ __global__ void __launch_bounds__(kT, 1) batched_kernel(const BatchArgs* __restr
     // a malformed descriptor is skipped, never used to index shared memory
     const int64_t stride = 2 + 2 * (int64_t)V;
     if (V < 0 || V > kVmax || T.lo < 0 || T.hi < T.lo || T.g < 0 || T.g >= A.G || T.nparts < 1 ||
-        T.part < 0 || T.part >= T.nparts || T.out_off < 0 ||
+        T.part < 0 || T.part >= T.nparts || !T.count || (V > 1 && !T.out) ||
         (T.nparts > 1 && (T.slot < (int64_t)T.part * stride ||
                           T.slot + (int64_t)(T.nparts - T.part) * stride > A.slot_words))) {
-      if (tid == 0 && T.g >= 0 && T.g < A.G) A.counts[T.g] = BRIDGES_EINTERNAL;
+      if (tid == 0 && T.count) *T.count = BRIDGES_EINTERNAL;
       continue;
     }
     for (int x = tid; x < V; x += kT) {
@@ -473,7 +473,7 @@ __global__ void __launch_bounds__(kT, 1) batched_kernel(const BatchArgs* __restr
       err = 0;
     }
     __syncthreads();
-    s_certify_range(S, A.u, A.v, T.lo, T.hi, V, &n1, &n2, &err);
+    s_certify_range(S, T.u, T.v, T.lo, T.hi, V, &n1, &n2, &err);
     __syncthreads();
     int32_t nt = min(n1, V), nx = min(n2, V);
     if (T.nparts > 1) {
@@ -513,13 +513,13 @@ __global__ void __launch_bounds__(kT, 1) batched_kernel(const BatchArgs* __restr
       nt = min(n1, V);
       nx = min(n2, V);
     }
-    int64_t* cnt = A.counts + T.g;
+    int64_t* cnt = T.count;
     if (err) {
       if (tid == 0) *cnt = err;
       __syncthreads();
       continue;
     }
-    const int32_t nb = s_bridges(S, V, nt, nx, A.out + T.out_off, red, &sh);
+    const int32_t nb = s_bridges(S, V, nt, nx, T.out, red, &sh);
     if (tid == 0) *cnt = nb;
     __syncthreads();
   }

@@ -10,10 +10,13 @@ constexpr int kBatchVmax = 4096;  // graphs up to this many vertices are handled
 
 // One unit of work: a whole graph (nparts == 1) or partition `part` of it.
 struct BatchTask {
-  int64_t lo, hi;    // edge range in the concatenated edge arrays
-  int64_t out_off;   // int32 offset of the graph's output pairs
+  const int32_t* u;  // the graph's edge arrays
+  const int32_t* v;
+  int64_t lo, hi;    // edge range of this task in u / v
+  int32_t* out;      // the graph's output pairs
+  int64_t* count;    // the graph's count (or negative status)
   int64_t slot;      // u32 offset of this partition's certificate slot (nparts > 1)
-  int32_t g;         // graph index
+  int32_t g;         // graph index within the launch (done / gerr counters)
   int32_t part;      // partition index within the graph
   int32_t nparts;    // partitions of the graph
   int32_t V;         // vertices of the graph
@@ -22,16 +25,12 @@ struct BatchTask {
 // Everything the kernel reads, in device memory so a captured CUDA graph stays valid when the
 // caller's pointers change between calls.
 struct BatchArgs {
-  const int32_t* u;
-  const int32_t* v;
   const BatchTask* tasks;
   const int32_t* d_ntasks;
   int32_t* queue;    // next task (atomic)
   int32_t* done;     // per graph: partitions finished
   int32_t* gerr;     // per graph: first error of any partition
   uint32_t* slots;   // certificates of partitions
-  int32_t* out;
-  int64_t* counts;
   int32_t G;           // graphs (bounds the graph index of every task)
   int64_t slot_words;  // capacity of slots (u32)
 };

@@ -1,0 +1,63 @@
+// ctx.h -- the context object behind bridges_ctx* and the host helpers the server shares with
+// the plain and batched entry points.  Nothing here is part of the C ABI.
+#pragma once
+
+#include <cstdint>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "../../include/bridges.h"
+#include "batched.h"
+
+struct bridges_ctx {
+  int device = 0;
+  size_t budget = 0;  // 0: unlimited
+  bool user_ws = false;
+  void* ws = nullptr;
+  size_t ws_bytes = 0;
+  // device staging for bridges_find_host
+  int32_t* stage = nullptr;
+  size_t stage_bytes = 0;
+  int64_t* h_pinned = nullptr;  // pinned host scratch (counts)
+  bridges_opts opts{};
+  int num_sms = 0;
+  size_t smem_optin = 0;
+  int64_t launches = 0;
+  // profiling: a ring of kRing event sets, one per call; slot = call index % kRing
+  static constexpr int kRing = 32;
+  cudaEvent_t ev[kRing][8]{};
+  bool events = false;
+  int64_t calls = 0;         // profiled calls issued
+  int64_t resolved = 0;      // calls whose times have been read back
+  float stage_ms[kRing][6]{};
+  int64_t last_cfg[5]{};
+  // batched path: device descriptors, pinned staging and a CUDA graph per capacity
+  void* bws = nullptr;          // device: BatchArgs | ntasks | queue | tasks[cap] | done[gcap] | gerr[gcap] | slots
+  size_t bws_bytes = 0;
+  void* bstage = nullptr;        // pinned: BatchArgs | ntasks | tasks[cap]
+  size_t bstage_bytes = 0;
+  int64_t b_task_cap = 0, b_graph_cap = 0, b_slot_cap = 0;
+  cudaGraphExec_t b_exec = nullptr;
+  cudaStream_t b_exec_stream = nullptr;
+  cudaEvent_t b_done_ev = nullptr;
+  int64_t b_split_edges = 0;     // partition graphs with more edges than this (0: automatic)
+};
+
+namespace bridges {
+
+// Splits graphs (whole-graph tasks) with more than `split` edges into partitions, fills in the
+// certificate slots and orders the tasks largest first; returns the slot words needed.
+int64_t plan_batch_tasks(std::vector<BatchTask>& graphs, int64_t split, std::vector<BatchTask>& tasks);
+// One persistent launch over `tasks` (G graphs) on stream s, through the context's CUDA graph.
+int64_t launch_batch_tasks(bridges_ctx* c, cudaStream_t s, const std::vector<BatchTask>& tasks, int32_t G,
+                           int64_t slot_words);
+// Edge count above which a batched graph is partitioned.
+int64_t default_split(const bridges_ctx* c, int64_t total_e);
+// The single-graph path, count copied to count_dev (device); enqueue only.
+int64_t run_single(bridges_ctx* c, cudaStream_t s, const int32_t* u, const int32_t* v, int64_t E, int32_t V, int32_t M,
+                   int32_t* out, int64_t* count_dev);
+// Workspace bytes of the single-graph path for (E, V) with automatic M.
+size_t single_workspace_bytes(const bridges_ctx* c, int64_t E, int32_t V);
+
+}  // namespace bridges
