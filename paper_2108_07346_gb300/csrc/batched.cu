@@ -186,34 +186,121 @@ __device__ __forceinline__ void s_settle(const Smem& S, bool need, int32_t a, in
   }
 }
 
-// Certifies edges [lo, hi) of (u, v) into S.F1 / S.F2 (appending to *n1 / *n2).  Ids outside
-// [0, V) set *err.  Eight edges per thread are loaded before any is processed, so a block keeps
-// 64 KB of edge loads in flight; the fast path is "equal F' parents".
+// Points every vertex straight at its root (no link runs meanwhile), so that afterwards "equal
+// parents" recognises every pair that shares a set.
+__device__ __forceinline__ void s_flatten(int32_t* P, int32_t V) {
+  __syncthreads();
+  for (int x = threadIdx.x; x < V; x += kT) {
+    int32_t r = x, p = P[x];
+    while (p != r) {
+      r = p;
+      p = P[r];
+    }
+    P[x] = r;
+  }
+  __syncthreads();
+}
+
+// Scalar certification of edges [lo, hi): every lane takes one edge per step.
+__device__ void s_certify_scalar(const Smem& S, const int32_t* __restrict__ u, const int32_t* __restrict__ v,
+                                 int64_t lo, int64_t hi, int32_t V, int32_t* n1, int32_t* n2, int32_t* err) {
+  volatile int32_t* P2 = S.P2;
+  for (int64_t t0 = lo; t0 < hi; t0 += kT) {
+    const int64_t i = t0 + threadIdx.x;
+    const bool valid = i < hi;
+    const int32_t a = valid ? __ldcs(u + i) : 0, b = valid ? __ldcs(v + i) : 0;
+    bool need = valid;
+    if (need && ((uint32_t)a >= (uint32_t)V || (uint32_t)b >= (uint32_t)V)) {
+      *err = BRIDGES_ERANGE;
+      need = false;
+    }
+    if (need && (a == b || P2[a] == P2[b])) need = false;
+    s_settle(S, need, a, b, n1, n2, V);
+  }
+}
+
+// The lanes' flagged edges of one tile go through the union-finds (bit 4k+c of m: element
+// 4*(base + k*kT + tid) + c of ub / vb).  Out of line: rare after the flatten.
+__device__ __noinline__ void s_offer_misses(const Smem& S, uint32_t m, const int32_t* __restrict__ ub,
+                                            const int32_t* __restrict__ vb, int64_t base, int32_t V, int32_t* n1,
+                                            int32_t* n2, int32_t* err) {
+  while (__any_sync(kFull, m != 0)) {
+    int32_t a = 0, b = 0;
+    bool go = false;
+    if (m) {
+      const int bit = __ffs(m) - 1;
+      m &= m - 1;
+      const int64_t e = 4 * (base + (int64_t)(bit >> 2) * kT + threadIdx.x) + (bit & 3);
+      a = ub[e];
+      b = vb[e];
+      if ((uint32_t)a >= (uint32_t)V || (uint32_t)b >= (uint32_t)V)
+        *err = BRIDGES_ERANGE;
+      else
+        go = a != b;
+    }
+    s_settle(S, go, a, b, n1, n2, V);
+  }
+}
+
+// Certifies edges [lo, hi) of (u, v) into S.F1 / S.F2 (appending to *n1 / *n2); ids outside
+// [0, V) set *err.  A warm-up prefix goes edge by edge, then both union-finds are flattened and
+// the rest streams with 16-byte loads (when u and v share their alignment), four units of four
+// edges per thread in flight, a per-thread miss mask and one warp vote per tile.
 __device__ void s_certify_range(const Smem& S, const int32_t* __restrict__ u, const int32_t* __restrict__ v,
                                 int64_t lo, int64_t hi, int32_t V, int32_t* n1, int32_t* n2, int32_t* err) {
-  constexpr int K = 8;
-  volatile int32_t* P2 = S.P2;
-  for (int64_t t0 = lo; t0 < hi; t0 += (int64_t)K * kT) {
-    int32_t as[K], bs[K];
-#pragma unroll
-    for (int k = 0; k < K; k++) {
-      const int64_t i = t0 + (int64_t)k * kT + threadIdx.x;
-      as[k] = i < hi ? __ldcs(u + i) : 0;
-      bs[k] = i < hi ? __ldcs(v + i) : 0;
-    }
-#pragma unroll
-    for (int k = 0; k < K; k++) {
-      const int64_t i = t0 + (int64_t)k * kT + threadIdx.x;
-      const int32_t a = as[k], b = bs[k];
-      bool need = i < hi;
-      if (need && ((uint32_t)a >= (uint32_t)V || (uint32_t)b >= (uint32_t)V)) {
-        *err = BRIDGES_ERANGE;
-        need = false;
-      }
-      if (need && (a == b || P2[a] == P2[b])) need = false;
-      s_settle(S, need, a, b, n1, n2, V);
-    }
+  constexpr int U = 4;
+  const int64_t warm = min(hi - lo, (int64_t)8 * V + 2048);
+  s_certify_scalar(S, u, v, lo, lo + warm, V, n1, n2, err);
+  lo += warm;
+  if (lo >= hi) return;
+  s_flatten(S.P1, V);
+  s_flatten(S.P2, V);
+  // head up to 16-byte alignment of u (v must share it for the vector body)
+  const bool same = ((reinterpret_cast<uintptr_t>(u) ^ reinterpret_cast<uintptr_t>(v)) & 15) == 0;
+  int64_t body = lo;
+  if (same) {
+    while (body < hi && (reinterpret_cast<uintptr_t>(u + body) & 15)) body++;
+  } else {
+    body = hi;
   }
+  s_certify_scalar(S, u, v, lo, body, V, n1, n2, err);
+  const int64_t nunits = (hi - body) >> 2;
+  const int32_t* ub = u + body;
+  const int32_t* vb = v + body;
+  const int4* u4 = reinterpret_cast<const int4*>(ub);
+  const int4* v4 = reinterpret_cast<const int4*>(vb);
+  volatile int32_t* P2 = S.P2;
+  const uint32_t cl = (uint32_t)(kVmax - 1);
+  for (int64_t base = 0; base < nunits; base += (int64_t)kT * U) {
+    int4 ua[U], va[U];
+#pragma unroll
+    for (int k = 0; k < U; k++) {
+      const int64_t idx = base + (int64_t)k * kT + threadIdx.x;
+      if (idx < nunits) {
+        ua[k] = __ldcs(u4 + idx);
+        va[k] = __ldcs(v4 + idx);
+      } else {
+        ua[k] = make_int4(0, 0, 0, 0);
+        va[k] = make_int4(0, 0, 0, 0);
+      }
+    }
+    uint32_t m = 0;
+#pragma unroll
+    for (int k = 0; k < U; k++) {
+      if (base + (int64_t)k * kT + threadIdx.x >= nunits) continue;
+      const int32_t as[4] = {ua[k].x, ua[k].y, ua[k].z, ua[k].w};
+      const int32_t bs[4] = {va[k].x, va[k].y, va[k].z, va[k].w};
+#pragma unroll
+      for (int c = 0; c < 4; c++) {
+        const uint32_t a = (uint32_t)as[c], b = (uint32_t)bs[c];
+        const bool bad = a >= (uint32_t)V || b >= (uint32_t)V;
+        const bool same_set = P2[min(a, cl)] == P2[min(b, cl)];
+        m |= (uint32_t)(bad || !same_set) << (4 * k + c);
+      }
+    }
+    if (__any_sync(kFull, m != 0)) s_offer_misses(S, m, ub, vb, base, V, n1, n2, err);
+  }
+  s_certify_scalar(S, u, v, body + 4 * nunits, hi, V, n1, n2, err);
 }
 
 // Certifies packed edges (a | b << 16) of a global list.
