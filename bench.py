@@ -105,6 +105,23 @@ class Clocks:
                 "window_s": None if t0 is None else round(t1 - t0, 3)}
 
 
+def reduce_max(value, device=None):
+    """Max of a float over the ranks of the default process group (the value itself if none)."""
+    import torch
+    import torch.distributed as dist
+
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(value)
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank, world, seconds):
+    """Units all ranks processed per second (x1e-9): every rank does the same work (replicas)."""
+    return world * units_per_rank / seconds / 1e9
+
+
 def dist_setup():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -178,6 +195,22 @@ def run_native(args, world, rank, local):
     cnt = torch.zeros(1, dtype=torch.int64, device=dev)
     ctx = pb.Context(device=dev, profile=True, M=args.M)
     stream = torch.cuda.current_stream(dev)
+    plan = None
+    if args.M <= 0 and not args.no_tune:
+        plan = ctx.autotune(du, dv, V, reps=3)  # outside the timed region; kept in the context
+    # the merge-tree cost at fixed M (a few steps each, outside the timed region)
+    sweep = {}
+    if not args.no_sweep:
+        for m in (1, 2, 4, 8, 16):
+            sctx = pb.Context(device=dev, profile=True, M=m)
+            for _ in range(3):
+                sctx.find(du, dv, V, m, out=out, count_device=cnt, stream=stream)
+            for _ in range(10):
+                sctx.find(du, dv, V, m, out=out, count_device=cnt, stream=stream)
+            hh = sctx.stage_ms_history(10)
+            sweep[str(m)] = {k: round(statistics.median(x[k] for x in hh), 4) for k in hh[0]}
+            sweep[str(m)]["GE_per_s"] = round(E / sweep[str(m)]["total"] / 1e6, 1)
+            del sctx
 
     # correctness of what is timed: the planted bridges are exact on this workload
     res = ctx.find(du, dv, V, args.M)
@@ -205,13 +238,10 @@ def run_native(args, world, rank, local):
     ms_total = e0.elapsed_time(e1)
     hist = ctx.stage_ms_history(args.steps)
     ck = clocks.stop()
-    if world > 1:
-        t = torch.tensor([ms_total], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms_total = float(t.item())
+    ms_total = reduce_max(ms_total, dev)
     n_found = int(cnt.item())
     ms_step = ms_total / args.steps
-    value = world * E * args.steps / (ms_total * 1e-3) / 1e9
+    value = whole_job_rate(E * args.steps, world, ms_total * 1e-3)
 
     cfg = ctx.last_config()
     forest_ms = statistics.mean(h["forest"] for h in hist) if hist else None
@@ -245,12 +275,8 @@ def run_native(args, world, rank, local):
         for _ in range(ks):
             nb = ctx_h.find_host(hu, hv, V, args.M, out=hout).shape[0]
         torch.cuda.synchronize()
-        dt = time.perf_counter() - t0
-        if world > 1:
-            t = torch.tensor([dt], device=dev)
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            dt = float(t.item())
-        e2e = {"value": world * E * ks / dt / 1e9, "unit": UNIT, "h2d_bytes_per_step": 8 * E,
+        dt = reduce_max(time.perf_counter() - t0, dev)
+        e2e = {"value": whole_job_rate(E * ks, world, dt), "unit": UNIT, "h2d_bytes_per_step": 8 * E,
                "d2h_bytes_per_step": 8 + 8 * nb, "steps": ks, "ms_per_step": dt / ks * 1e3}
         del ctx_h
 
@@ -272,7 +298,8 @@ def run_native(args, world, rank, local):
                        "blocks_per_partition": cfg["blocks_per_partition"], "block": cfg["block"],
                        "warm_edges": cfg["warm_edges"], "l2": "inputs (8E bytes) larger than L2; no flush",
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
-                       "bridges": n_found, "bridges_equal_planted": correct},
+                       "bridges": n_found, "bridges_equal_planted": correct,
+                       "autotuned_plan": plan, "stage_ms_by_M": sweep},
             "clocks": ck, "e2e": e2e, "gpu_launches": launches, "roofline": roof, "cpu_baseline": cpu,
         }
         print(json.dumps(line), flush=True)
@@ -448,6 +475,8 @@ def main():
     ap.add_argument("--density", type=float, default=None, help="override the ER density (profiling)")
     ap.add_argument("--M", type=int, default=0, help="partitions (0: automatic)")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-tune", action="store_true", help="skip the autotuner (use --M or the default plan)")
+    ap.add_argument("--no-sweep", action="store_true", help="skip the per-M stage timings")
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-sample", type=int, default=2_000_000_000, help="oracle sample (edges; whole graph)")

@@ -235,6 +235,31 @@ int64_t bridges_find_noalloc(struct CUstream_st* stream, const int32_t* edges_u,
                              int32_t V, int32_t M, int32_t* out_bridges, int64_t* out_count_device);
 
 /* ---------------------------------------------------------------------------------------
+ * Autotuning.
+ * bridges_autotune: times candidate plans on the given device-resident input (M in
+ * {1,2,4,8,16,32}, fan-in 2 or M, warm-up 0.3/0.6/1.2 x V ln V edges, block 1024 or 512; `reps`
+ * timed calls each, CUDA events on `stream`) and keeps the fastest in the context's options.
+ * best[0..4] receives M, fan-in, warm-up edges, block size and microseconds per call.  Uses
+ * a little scratch memory of its own (the output buffers).  Returns BRIDGES_OK or an error (the
+ * options are then unchanged).
+ * bridges_ctx_set_opts: replaces the context's tuning options (e.g. from a cache of tuning
+ * results); the profiling flag stays as created.
+ */
+int32_t bridges_autotune(bridges_ctx* ctx, struct CUstream_st* stream, const int32_t* edges_u,
+                         const int32_t* edges_v, int64_t E, int32_t V, int32_t reps, int64_t* best);
+int32_t bridges_ctx_set_opts(bridges_ctx* ctx, const bridges_opts* opts);
+
+/* bridges_wait_value: a bounded device-side wait -- one thread polls the device int32 *flag
+ * (acquire loads, ~100 ns apart) until it equals `value` or max_polls polls were made, on
+ * `stream`.  Synchronous: BRIDGES_OK if the value was seen, BRIDGES_ETIMEDOUT if the wait gave
+ * up; the context stays usable either way.  This is the primitive behind the library's device
+ * barriers (which never wait unboundedly); it is exposed so that callers can order work on a
+ * flag written by another stream, and so that tests can check that a wait nothing satisfies ends
+ * in an error status instead of a hang. */
+int32_t bridges_wait_value(bridges_ctx* ctx, struct CUstream_st* stream, const int32_t* flag_device, int32_t value,
+                           int64_t max_polls);
+
+/* ---------------------------------------------------------------------------------------
  * Introspection.
  * bridges_ctx_stage_ms: per-stage device times (ms) of the context's last call, measured with
  * CUDA events on the launch stream when opts.profile = 1: [0] partition warm-up, [1] label

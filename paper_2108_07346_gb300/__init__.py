@@ -84,6 +84,9 @@ _SIGS = {
                                    ctypes.POINTER(ctypes.c_double)]),
     "bridges_server_stats": (_I32, [_P, ctypes.POINTER(ctypes.c_int64), _I32]),
     "bridges_server_destroy": (None, [_P]),
+    "bridges_autotune": (_I32, [_P, _P, _P, _P, _I64, _I32, _I32, ctypes.POINTER(ctypes.c_int64)]),
+    "bridges_ctx_set_opts": (_I32, [_P, ctypes.POINTER(Opts)]),
+    "bridges_wait_value": (_I32, [_P, _P, _P, _I32, _I64]),
 }
 
 
@@ -253,6 +256,27 @@ class Context:
         if sync:
             (stream or torch.cuda.current_stream()).synchronize()
         return out, counts, out_off[:-1]
+
+    def autotune(self, u, v, V: int, reps: int = 3, stream=None):
+        """bridges_autotune on device tensors; returns the chosen plan (also kept in the context)."""
+        u, v = _dev_edges(u, v)
+        best = (ctypes.c_int64 * 5)()
+        _check(self._lib.bridges_autotune(self._h, _stream(stream), _ptr(u), _ptr(v), u.numel(), V, reps, best),
+               "bridges_autotune")
+        names = ["M", "fan_in", "warm_edges", "block", "us_per_call"]
+        return {names[i]: int(best[i]) for i in range(5)}
+
+    def set_opts(self, M=0, fan_in=0, block=0, ctas_per_sm=0, warm_edges=-1, host_read=False):
+        o = Opts()
+        o.M, o.fan_in, o.block, o.ctas_per_sm, o.warm_edges = M, fan_in, block, ctas_per_sm, warm_edges
+        o.host_read = int(bool(host_read))
+        _check(self._lib.bridges_ctx_set_opts(self._h, ctypes.byref(o)), "bridges_ctx_set_opts")
+
+    def wait_value(self, flag, value: int, max_polls: int, stream=None) -> int:
+        """bridges_wait_value on a 1-element int32 CUDA tensor; returns the status code."""
+        if not (flag.is_cuda and flag.dtype == torch.int32):
+            raise ValueError("flag must be an int32 CUDA tensor")
+        return int(self._lib.bridges_wait_value(self._h, _stream(stream), _ptr(flag), int(value), int(max_polls)))
 
     def set_batch_split(self, split_edges: int):
         _check(self._lib.bridges_ctx_set_batch_split(self._h, int(split_edges)), "bridges_ctx_set_batch_split")

@@ -9,8 +9,10 @@
 #include "../../include/bridges.h"
 #include "batched.h"
 #include "ctx.h"
+#include "common.cuh"
 #include "internal.h"
 
+#include <cmath>
 #include <numeric>
 #include <vector>
 
@@ -648,4 +650,124 @@ extern "C" int32_t bridges_ctx_set_batch_split(bridges_ctx* c, int64_t split_edg
   if (!c || split_edges < 0) return BRIDGES_EINVAL;
   c->b_split_edges = split_edges;
   return BRIDGES_OK;
+}
+
+// ---------------------------------------------------------------------------------------------
+// Autotuner: times candidate plans on the caller's input and keeps the fastest in the context.
+extern "C" int32_t bridges_autotune(bridges_ctx* c, struct CUstream_st* stream, const int32_t* u, const int32_t* v,
+                                    int64_t E, int32_t V, int32_t reps, int64_t* best) {
+  if (!c || E < 0 || V < 0 || (E > 0 && (!u || !v)) || !best) return BRIDGES_EINVAL;
+  if (V > (1 << 30)) return BRIDGES_EINVAL;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  if (cudaSetDevice(c->device) != cudaSuccess) return (int32_t)cuda_fail(cudaGetLastError());
+  if (reps <= 0) reps = 3;
+  int32_t* out = nullptr;
+  int64_t* cnt = nullptr;
+  if (cudaMalloc(&out, sizeof(int32_t) * 2 * (size_t)std::max(V, 1)) != cudaSuccess ||
+      cudaMalloc(&cnt, sizeof(int64_t)) != cudaSuccess) {
+    cudaGetLastError();
+    if (out) cudaFree(out);
+    return BRIDGES_ENOMEM;
+  }
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  const bridges_opts saved = c->opts;
+  const double lnv = std::log((double)V + 1.0);
+  float best_ms = 1e30f;
+  bridges_opts best_o = saved;
+  int32_t rc = BRIDGES_OK;
+  const int32_t Ms[] = {1, 2, 4, 8, 16, 32};
+  const double warms[] = {0.3, 0.6, 1.2};
+  const int32_t blocks[] = {1024, 512};
+  for (int32_t M : Ms) {
+    if (M > 1 && (int64_t)M > std::max<int64_t>(E, 1)) break;
+    for (int32_t f : {2, M}) {
+      if (M == 1 && f != 2) continue;
+      if (M > 1 && f == 2 && M == 2) continue;  // same as f = M
+      for (double w : warms) {
+        for (int32_t blk : blocks) {
+          bridges_opts o = saved;
+          o.M = M;
+          o.fan_in = f;
+          o.block = blk;
+          o.warm_edges = (int64_t)std::ceil(w * V * lnv) + 4096;
+          o.profile = 0;
+          c->opts = o;
+          // one untimed run (workspace growth, first-touch), then reps timed runs
+          int64_t r = BRIDGES_OK;
+          Carved k{};
+          r = run_path(c, s, u, v, E, V, 0, out, &k, nullptr);
+          if (r) {
+            rc = (int32_t)r;
+            break;
+          }
+          cudaEventRecord(e0, s);
+          for (int i = 0; i < reps && !r; i++) r = run_path(c, s, u, v, E, V, 0, out, &k, nullptr);
+          cudaEventRecord(e1, s);
+          if (r || cudaEventSynchronize(e1) != cudaSuccess) {
+            rc = r ? (int32_t)r : (int32_t)BRIDGES_ECUDA;
+            break;
+          }
+          float ms = 0;
+          cudaEventElapsedTime(&ms, e0, e1);
+          ms /= reps;
+          if (ms < best_ms) {
+            best_ms = ms;
+            best_o = o;
+          }
+        }
+        if (rc) break;
+      }
+      if (rc) break;
+    }
+    if (rc) break;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaFree(out);
+  cudaFree(cnt);
+  best_o.profile = saved.profile;
+  best_o.host_read = saved.host_read;
+  c->opts = rc ? saved : best_o;
+  best[0] = best_o.M;
+  best[1] = best_o.fan_in;
+  best[2] = best_o.warm_edges;
+  best[3] = best_o.block;
+  best[4] = (int64_t)(best_ms * 1000.0f);  // microseconds per call
+  return rc;
+}
+
+// Sets the tuning options of a context (e.g. from a cache of autotune results).
+extern "C" int32_t bridges_ctx_set_opts(bridges_ctx* c, const bridges_opts* o) {
+  if (!c || !o) return BRIDGES_EINVAL;
+  const int32_t prof = c->opts.profile;
+  c->opts = *o;
+  c->opts.profile = prof;  // event slots exist only if created with profiling
+  return BRIDGES_OK;
+}
+
+// ---------------------------------------------------------------------------------------------
+// A bounded device-side wait on a flag (the primitive behind the library's barriers).
+namespace {
+__global__ void wait_value_kernel(const int32_t* flag, int32_t value, unsigned long long max_polls, int32_t* status) {
+  const bool ok = bounded_poll([&] { return ld_acquire_s32(flag) == value; }, max_polls);
+  *status = ok ? BRIDGES_OK : BRIDGES_ETIMEDOUT;
+}
+}  // namespace
+
+extern "C" int32_t bridges_wait_value(bridges_ctx* c, struct CUstream_st* stream, const int32_t* flag, int32_t value,
+                                      int64_t max_polls) {
+  if (!c || !flag || max_polls < 0) return BRIDGES_EINVAL;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  if (cudaSetDevice(c->device) != cudaSuccess) return (int32_t)cuda_fail(cudaGetLastError());
+  int64_t rc = ensure_ws(c, kMiscBytes, s);
+  if (rc) return (int32_t)rc;
+  int32_t* st = static_cast<int32_t*>(c->ws);
+  wait_value_kernel<<<1, 1, 0, s>>>(flag, value, (unsigned long long)max_polls, st);
+  c->launches += 1;
+  if (cudaMemcpyAsync(c->h_pinned, st, sizeof(int32_t), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      cudaStreamSynchronize(s) != cudaSuccess)
+    return (int32_t)cuda_fail(cudaGetLastError());
+  return *reinterpret_cast<int32_t*>(c->h_pinned);
 }

@@ -106,6 +106,24 @@ __device__ __forceinline__ bool uf_link(int32_t* P, int32_t a, int32_t b) {
   }
 }
 
+// Bounded poll: calls done() until it returns true or max_polls polls have been made (sleeping
+// ~100 ns between polls).  Returns whether done() became true.  Every device-side wait of the
+// library goes through this, so no wait can hang a kernel.
+template <class Done>
+__device__ __forceinline__ bool bounded_poll(Done done, unsigned long long max_polls) {
+  for (unsigned long long i = 0; i < max_polls; i++) {
+    if (done()) return true;
+    if (i >= 32) __nanosleep(100);
+  }
+  return done();
+}
+
+__device__ __forceinline__ int32_t ld_acquire_s32(const int32_t* p) {
+  int32_t v;
+  asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
 // Warp-aggregated append of (a, b) to a list with a shared counter: one atomic per warp.
 // Every lane of the warp must call it (pred may be false).
 __device__ __forceinline__ void warp_append(bool pred, int32_t a, int32_t b, int32_t* cnt, int32_t* ou,

@@ -79,16 +79,9 @@ __device__ __noinline__ bool grid_barrier(unsigned* count, unsigned* gen, int32_
       atomicExch(count, 0u);
       __threadfence();
       st_release(gen, g + 1);
-    } else {
-      unsigned spins = 0;
-      while (ld_acquire(gen) == g) {
-        __nanosleep(100);
-        if (++spins > kSpinCap) {
-          set_status(status, BRIDGES_ETIMEDOUT_CODE);
-          ok = 0;
-          break;
-        }
-      }
+    } else if (!bounded_poll([&] { return ld_acquire(gen) != g; }, kSpinCap)) {
+      set_status(status, BRIDGES_ETIMEDOUT_CODE);
+      ok = 0;
     }
     __threadfence();
   }

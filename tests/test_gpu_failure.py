@@ -1,0 +1,38 @@
+"""Failure handling on the GPU without faulting it: a bounded wait that nothing satisfies ends in
+BRIDGES_ETIMEDOUT and leaves the context usable; bad inputs come back as error codes."""
+import numpy as np
+import pytest
+import torch
+
+import graphgen
+
+pytestmark = pytest.mark.gpu
+
+
+def test_bounded_wait_times_out_and_context_survives(cuda_lib):
+    ctx = cuda_lib.Context(device="cuda:0")
+    flag = torch.zeros(1, dtype=torch.int32, device="cuda:0")
+    assert ctx.wait_value(flag, 1, 20000) == -5  # nothing ever sets the flag
+    flag.fill_(1)
+    assert ctx.wait_value(flag, 1, 20000) == 0
+    g = graphgen.workload("small")
+    u = torch.from_numpy(np.array(g.u)).cuda()
+    v = torch.from_numpy(np.array(g.v)).cuda()
+    assert ctx.find(u, v, g.V, 4).cpu().numpy().tolist() == g.planted.tolist()
+
+
+def test_errors_leave_context_usable(cuda_lib):
+    ctx = cuda_lib.Context(device="cuda:0")
+    u = torch.tensor([0, 1, 2], dtype=torch.int32, device="cuda:0")
+    v = torch.tensor([1, 2, 7], dtype=torch.int32, device="cuda:0")
+    for _ in range(3):
+        with pytest.raises(cuda_lib.BridgesError) as ei:
+            ctx.find(u, v, 5, 2)
+        assert ei.value.code == -2
+    v2 = torch.tensor([1, 2, 0], dtype=torch.int32, device="cuda:0")
+    assert ctx.find(u, v2, 5, 2).shape == (0, 2)
+    # a budget too small for the workspace: ENOMEM, nothing launched
+    small = cuda_lib.Context(device="cuda:0", mem_budget=4096)
+    with pytest.raises(cuda_lib.BridgesError) as ei:
+        small.find(u, v2, 5)
+    assert ei.value.code == -3
