@@ -125,7 +125,12 @@ __device__ __forceinline__ bool s_link(int32_t* P, int32_t a, int32_t b) {
       py = t;
     }
     if (px == x) {
-      if (atomicCAS(P + x, x, py) == x) return true;
+      int32_t r = py, q = VP[r];  // hook under the other side's root (shallow trees)
+      while (q != r) {
+        r = q;
+        q = VP[r];
+      }
+      if (atomicCAS(P + x, x, r) == x) return true;
       continue;
     }
     const int32_t g = VP[px];

@@ -79,9 +79,10 @@ __device__ __forceinline__ int32_t uf_find_static(int32_t* P, int32_t x) {
 // Walks up from both ends comparing PARENTS, not roots: equal parents prove a common set, so in
 // the dense phase, where nearly every vertex points straight at its root, a rejection costs two
 // loads and never touches the root's own entry (which every block would otherwise hammer).  The
-// end with the larger parent moves up; when that end is itself a root x and the other end's
-// parent p is smaller, p cannot lie in x's set (members of a set are >= its root), so hooking
-// x under p joins two different sets even if p is not a root.
+// end with the larger parent moves up (path halving).  When that end is itself a root x, the
+// other end is walked to its root r < x and x is hooked under r: members of a set are >= its
+// root, so r is not in x's set and the CAS joins two different sets, and hooking root under
+// root keeps the trees shallow while they are still growing.
 __device__ __forceinline__ bool uf_link(int32_t* P, int32_t a, int32_t b) {
   int32_t x = a, y = b;
   while (true) {
@@ -97,7 +98,8 @@ __device__ __forceinline__ bool uf_link(int32_t* P, int32_t a, int32_t b) {
     }
     // now px > py
     if (px == x) {
-      if (atomicCAS(P + x, x, py) == x) return true;
+      const int32_t ry = uf_find(P, py);  // ry <= py < x
+      if (atomicCAS(P + x, x, ry) == x) return true;
       continue;  // x was hooked meanwhile: re-read its parent
     }
     const int32_t g = ld_relaxed(P + px);

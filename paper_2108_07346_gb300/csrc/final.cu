@@ -190,7 +190,6 @@ __global__ void __launch_bounds__(kThreads) final_kernel(FinArgs A) {
   __shared__ int32_t red[kWarps];
   __shared__ uint32_t wcnt[kWarps][256];
   __shared__ uint32_t run[256];
-  __shared__ uint64_t ktile[1024];
   const FinalBufs& f = A.f;
   const int32_t V = A.V;
   const bool own = A.P_tree == nullptr;
@@ -382,22 +381,33 @@ __global__ void __launch_bounds__(kThreads) final_kernel(FinArgs A) {
     }
   }
   BARRIER();
-  for (int64_t s = gtid(); s < nsup; s += gstride()) {
-    int32_t mn = INT32_MAX, mx = INT32_MIN;
-    for (int64_t c = s * csup; c < min(nchunks, (s + 1) * csup); c++) {
-      mn = min(mn, f.cmin[c]);
-      mx = max(mx, f.cmax[c]);
+  {  // one warp per superchunk
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = gtid() >> 5, nwarps = gstride() >> 5;
+    for (int64_t s = warp; s < nsup; s += nwarps) {
+      int32_t mn = INT32_MAX, mx = INT32_MIN;
+      for (int64_t c = s * csup + lane; c < min(nchunks, (s + 1) * csup); c += 32) {
+        mn = min(mn, f.cmin[c]);
+        mx = max(mx, f.cmax[c]);
+      }
+      for (int o = 16; o > 0; o >>= 1) {
+        mn = min(mn, __shfl_xor_sync(kFull, mn, o));
+        mx = max(mx, __shfl_xor_sync(kFull, mx, o));
+      }
+      if (lane == 0) {
+        f.smin[s] = mn;
+        f.smax[s] = mx;
+      }
     }
-    f.smin[s] = mn;
-    f.smax[s] = mx;
   }
   BARRIER();
 
   // 10: per-block sparse tables over the superchunks, then the bridge test
-  int32_t* tmin = sm;
-  int32_t* tmax = sm + kSupLevels * kMaxSup;
   int levels = 1;
   while ((1LL << levels) <= nsup) levels++;
+  const int64_t T = nsup;  // table stride: tmin[k * T + s]
+  int32_t* tmin = sm;
+  int32_t* tmax = sm + levels * T;
   for (int64_t s = threadIdx.x; s < nsup; s += blockDim.x) {
     tmin[s] = f.smin[s];
     tmax[s] = f.smax[s];
@@ -406,8 +416,8 @@ __global__ void __launch_bounds__(kThreads) final_kernel(FinArgs A) {
   for (int k = 1; k < levels; k++) {
     const int64_t half = 1LL << (k - 1);
     for (int64_t s = threadIdx.x; s + (1LL << k) <= nsup; s += blockDim.x) {
-      tmin[k * kMaxSup + s] = min(tmin[(k - 1) * kMaxSup + s], tmin[(k - 1) * kMaxSup + s + half]);
-      tmax[k * kMaxSup + s] = max(tmax[(k - 1) * kMaxSup + s], tmax[(k - 1) * kMaxSup + s + half]);
+      tmin[k * T + s] = min(tmin[(k - 1) * T + s], tmin[(k - 1) * T + s + half]);
+      tmax[k * T + s] = max(tmax[(k - 1) * T + s], tmax[(k - 1) * T + s + half]);
     }
     __syncthreads();
   }
@@ -432,8 +442,8 @@ __global__ void __launch_bounds__(kThreads) final_kernel(FinArgs A) {
           scan_range(f.cmin, f.cmax, cl, sl * csup, mn, mx);
           scan_range(f.cmin, f.cmax, sr * csup, cr, mn, mx);
           const int k = 63 - __clzll(sr - sl);
-          mn = min(mn, min(tmin[k * kMaxSup + sl], tmin[k * kMaxSup + sr - (1LL << k)]));
-          mx = max(mx, max(tmax[k * kMaxSup + sl], tmax[k * kMaxSup + sr - (1LL << k)]));
+          mn = min(mn, min(tmin[k * T + sl], tmin[k * T + sr - (1LL << k)]));
+          mx = max(mx, max(tmax[k * T + sl], tmax[k * T + sr - (1LL << k)]));
         }
       }
       if (mn >= l && mx < r) {
@@ -464,18 +474,15 @@ __global__ void __launch_bounds__(kThreads) final_kernel(FinArgs A) {
   const int32_t n = min(*f.nkeys, cap);
   const uint64_t mask = (1ULL << A.kbits) - 1;
   if (n <= kRankMax) {
-    for (int64_t i0 = (int64_t)blockIdx.x * blockDim.x; i0 < n; i0 += gstride()) {
-      const int64_t i = i0 + threadIdx.x;
-      const uint64_t mine = i < n ? f.keys[i] : ~0ULL;
+    // one warp per key: rank = number of smaller keys (keys are unique), lanes split the scan
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = gtid() >> 5, nwarps = gstride() >> 5;
+    for (int64_t i = warp; i < n; i += nwarps) {
+      const uint64_t mine = f.keys[i];
       int32_t rank = 0;
-      for (int32_t t0 = 0; t0 < n; t0 += 1024) {
-        __syncthreads();
-        for (int k = threadIdx.x; k < 1024; k += blockDim.x) ktile[k] = t0 + k < n ? f.keys[t0 + k] : ~0ULL;
-        __syncthreads();
-        const int lim = min(1024, n - t0);
-        for (int k = 0; k < lim; k++) rank += ktile[k] < mine;
-      }
-      if (i < n) {
+      for (int32_t j = lane; j < n; j += 32) rank += f.keys[j] < mine;
+      for (int o = 16; o > 0; o >>= 1) rank += __shfl_xor_sync(kFull, rank, o);
+      if (lane == 0) {
         A.out[2 * (int64_t)rank] = (int32_t)(mine >> A.kbits);
         A.out[2 * (int64_t)rank + 1] = (int32_t)(mine & mask);
       }
@@ -618,13 +625,23 @@ FinalBufs carve_final(void* base, int32_t V, int32_t* status) {
 void final_stage(const Launch& L, const FinalBufs& f, int32_t V, const int32_t* tu, const int32_t* tv,
                  const int32_t* d_nt, int64_t cap_tree, const int32_t* xu, const int32_t* xv, const int32_t* d_nx,
                  int64_t cap_extra, const int32_t* P_tree, int32_t* out) {
-  static int occ_blocks = -1;  // resident blocks per SM of final_kernel
-  if (occ_blocks < 0) {
+  // shared memory: the superchunk sparse tables actually needed, [2][levels][nsup]
+  const int64_t nch = ceil_div(std::max(V, 1), kChunk);
+  int slg = 0;
+  while (ceil_div(nch, (int64_t)kSuperChunks << slg) > kMaxSup) slg++;
+  const int64_t nsup = ceil_div(nch, (int64_t)kSuperChunks << slg);
+  int levels = 1;
+  while ((1LL << levels) <= nsup) levels++;
+  const size_t smem = sizeof(int32_t) * 2 * (size_t)levels * (size_t)nsup;
+  static bool attr = false;
+  if (!attr) {
     cudaFuncSetAttribute(final_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemTables);
-    int occ = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, final_kernel, kThreads, kSmemTables);
-    occ_blocks = std::max(1, std::min(occ, 2));
+    attr = true;
   }
+  int occ = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, final_kernel, kThreads, smem);
+  // one block per SM: more blocks make every grid barrier slower than they make the phases faster
+  const int occ_blocks = std::max(1, std::min(occ, 1));
   FinArgs A{};
   A.f = f;
   A.V = V;
@@ -647,7 +664,7 @@ void final_stage(const Launch& L, const FinalBufs& f, int32_t V, const int32_t* 
   const int blocks = std::min(kMaxBlocks, occ_blocks * L.num_sms);
   cudaMemsetAsync(f.bar_count, 0, 2 * sizeof(unsigned), L.stream);
   void* args[] = {&A};
-  cudaLaunchCooperativeKernel((void*)final_kernel, dim3(blocks), dim3(kThreads), args, kSmemTables, L.stream);
+  cudaLaunchCooperativeKernel((void*)final_kernel, dim3(blocks), dim3(kThreads), args, smem, L.stream);
   *L.launches += 1;
 }
 
