@@ -36,6 +36,8 @@ constexpr int kMaxSup = 1024;        // superchunks covered by the shared-memory
 constexpr int kSupLevels = 11;       // log2(kMaxSup) + 1
 constexpr int64_t kRankMax = 16384;  // up to this many bridges: all-pairs rank sort
 constexpr unsigned kSpinCap = 1u << 22;
+constexpr int kHopsLog = 2;  // pointer-jumping hops per round: 4 (8 was slower: longer load chains)
+constexpr int kHops = 1 << kHopsLog;
 constexpr int kMaxBlocks = 1024;
 constexpr size_t kSmemTables = sizeof(int32_t) * 2 * kSupLevels * kMaxSup;
 
@@ -253,21 +255,24 @@ __global__ void __launch_bounds__(kThreads) final_kernel(FinArgs A) {
   }
   BARRIER();
 
-  // 4: list ranking (Wyllie): rank = arcs after this one in its tour
+  // 4: list ranking by pointer jumping (Wyllie), kHops hops per round: after round r every arc
+  //    knows the arc kHops^r places ahead and the rank sum up to it, so ceil(log_kHops n) rounds
+  //    (and barriers) suffice; each round reads the previous round's arrays only.  Longer hop
+  //    chains trade dependent loads (cheap) for barriers (expensive).
   {
     int rounds = 0;
-    while ((1LL << rounds) < (int64_t)max(narcs, 1)) rounds++;
+    while ((1LL << (kHopsLog * rounds)) < (int64_t)max(narcs, 1)) rounds++;
     int32_t *sa = f.succ, *ra = f.rnk, *sb = f.succ2, *rb = f.rnk2;
     for (int r = 0; r < rounds; r++) {
       for (int64_t i = gtid(); i < narcs; i += gstride()) {
-        const int32_t s = sa[i];
-        if (s >= 0) {
-          rb[i] = ra[i] + ra[s];
-          sb[i] = sa[s];
-        } else {
-          rb[i] = ra[i];
-          sb[i] = -1;
+        int32_t s = sa[i], acc = ra[i];
+#pragma unroll
+        for (int h = 0; h < kHops - 1 && s >= 0; h++) {
+          acc += ra[s];
+          s = sa[s];
         }
+        rb[i] = acc;
+        sb[i] = s;
       }
       BARRIER();
       int32_t* t = sa;
