@@ -235,6 +235,42 @@ int64_t bridges_find_noalloc(struct CUstream_st* stream, const int32_t* edges_u,
                              int32_t V, int32_t M, int32_t* out_bridges, int64_t* out_count_device);
 
 /* ---------------------------------------------------------------------------------------
+ * 2-edge-connected components and incremental edge additions.
+ *
+ * bridges_two_edge_components: labels[x] (device, V int32) = the minimum vertex of x's
+ * 2-edge-connected component (the components left after deleting every bridge); the bridges
+ * themselves go to out_bridges (device, may be NULL).  Synchronous; returns the number of
+ * components.
+ *
+ * Incremental sessions keep the final certificate X of the current graph, and its union-finds,
+ * resident on the device.  Adding an edge set Y offers Y to those union-finds, which turns X
+ * into a certificate of X u Y and hence of E u Y (the certificate definition of Sec. 3: bridges
+ * of E u Y = bridges of X u Y), then reruns the O(V) bridge stage: O(|Y| + V) per query instead
+ * of O(|E| + V).  Vertex ids of Y must lie in [0, V) of the reset graph.
+ *   bridges_inc_create / _destroy: one session per (device, options); not thread-safe.
+ *   bridges_inc_reset(inc, stream, u, v, E, V, M, out): computes the bridges of (u, v) as
+ *     bridges_find_ctx does and keeps its certificate; returns the count.
+ *   bridges_inc_add(inc, stream, yu, yv, n, out): adds n edges (device); returns the bridge
+ *     count of everything added so far.  On BRIDGES_ERANGE the session is unchanged.
+ *   bridges_inc_two_edge_components(inc, stream, labels): 2-edge-connected components of the
+ *     current graph (after the last reset / add); returns their number.
+ *   bridges_inc_certificate_size: |X| of the current certificate (<= 2(V-1)).
+ */
+int64_t bridges_two_edge_components(bridges_ctx* ctx, struct CUstream_st* stream, const int32_t* edges_u,
+                                    const int32_t* edges_v, int64_t E, int32_t V, int32_t M, int32_t* labels,
+                                    int32_t* out_bridges);
+
+typedef struct bridges_inc bridges_inc;
+bridges_inc* bridges_inc_create(int device, const bridges_opts* opts);
+void bridges_inc_destroy(bridges_inc* inc);
+int64_t bridges_inc_reset(bridges_inc* inc, struct CUstream_st* stream, const int32_t* edges_u, const int32_t* edges_v,
+                          int64_t E, int32_t V, int32_t M, int32_t* out_bridges);
+int64_t bridges_inc_add(bridges_inc* inc, struct CUstream_st* stream, const int32_t* add_u, const int32_t* add_v,
+                        int64_t n, int32_t* out_bridges);
+int64_t bridges_inc_two_edge_components(bridges_inc* inc, struct CUstream_st* stream, int32_t* labels);
+int64_t bridges_inc_certificate_size(const bridges_inc* inc);
+
+/* ---------------------------------------------------------------------------------------
  * Autotuning.
  * bridges_autotune: times candidate plans on the given device-resident input (M in
  * {1,2,4,8,16,32}, fan-in 2 or M, warm-up 0.3/0.6/1.2 x V ln V edges, block 1024 or 512; `reps`

@@ -38,6 +38,8 @@ def _load():
         lib.oracle_pipeline_cert.restype = ctypes.c_int64
         lib.oracle_pipeline_cert.argtypes = [_I32P, _I32P, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32,
                                              _I32P, _I32P, _I32P, _I32P]
+        lib.oracle_two_edge_components.restype = ctypes.c_int32
+        lib.oracle_two_edge_components.argtypes = [_I32P, _I32P, ctypes.c_int64, ctypes.c_int32, _I32P]
         lib.oracle_components.restype = ctypes.c_int32
         lib.oracle_components.argtypes = [_I32P, _I32P, ctypes.c_int64, ctypes.c_int32, _I32P]
         _lib = lib
@@ -114,4 +116,13 @@ def components(u, v, V: int):
     u, v = _edges(u, v)
     lab = np.empty(max(V, 1), np.int32)
     c = _check(_load().oracle_components(u.ctypes.data, v.ctypes.data, u.shape[0], V, lab.ctypes.data))
+    return int(c), lab[:V].copy()
+
+
+def two_edge_components(u, v, V: int):
+    """(number of 2-edge-connected components, label per vertex = min vertex of its component):
+    the components of the graph after deleting its bridges."""
+    u, v = _edges(u, v)
+    lab = np.empty(max(V, 1), np.int32)
+    c = _check(_load().oracle_two_edge_components(u.ctypes.data, v.ctypes.data, u.shape[0], V, lab.ctypes.data))
     return int(c), lab[:V].copy()

@@ -22,6 +22,8 @@
  *   oracle_brute_bridges    Independent check: the Sec. 1 definition itself -- delete each
  *                           edge and search for another path between its ends (BFS).
  *   oracle_components       Connected components (min vertex id of each component).
+ *   oracle_two_edge_components  2-edge-connected components: the components of the graph
+ *                           after deleting its bridges (found by Alg. 1); label = min vertex.
  *
  * Readings of the paper used here (each one listed in the design notes):
  *   - Alg. 1 recurses into v when v is NOT yet visited; the timer is global and increments at
@@ -528,4 +530,45 @@ int32_t oracle_components(const int32_t* u, const int32_t* v, int64_t E, int32_t
   free(minv);
   uf_free(&f);
   return ncomp;
+}
+
+/* ------------------------------------------------------------------ */
+/* 2-edge-connected components: components of G minus its bridges     */
+/* ------------------------------------------------------------------ */
+int32_t oracle_two_edge_components(const int32_t* u, const int32_t* v, int64_t E, int32_t V, int32_t* label) {
+  if (E < 0 || V < 0) return -1;
+  if (check_ids(u, v, E, V)) return -1;
+  int32_t* br = (int32_t*)malloc(sizeof(int32_t) * (size_t)(2 * (int64_t)V + 2));
+  if (!br) return -2;
+  int64_t nb = dfs_bridges_impl(u, v, NULL, E, V, br);
+  if (nb < 0) {
+    free(br);
+    return (int32_t)nb;
+  }
+  /* an edge is deleted iff it is a bridge; a bridge has no parallel copy, so matching the pair
+   * (a, b) identifies it */
+  uint64_t* keys = (uint64_t*)malloc(sizeof(uint64_t) * (size_t)(nb + 1));
+  for (int64_t i = 0; i < nb; i++) keys[i] = pair_key(br[2 * i], br[2 * i + 1]);
+  uf_t f;
+  if (uf_init(&f, V)) return -2;
+  for (int64_t e = 0; e < E; e++) {
+    if (u[e] == v[e]) continue;
+    uint64_t k = pair_key(u[e], v[e]);
+    if (bsearch(&k, keys, (size_t)nb, sizeof(uint64_t), cmp_u64)) continue;
+    uf_union(&f, u[e], v[e]);
+  }
+  int32_t* minv = (int32_t*)malloc(sizeof(int32_t) * (size_t)(V > 0 ? V : 1));
+  for (int32_t x = 0; x < V; x++) minv[x] = INT32_MAX;
+  int32_t nc = 0;
+  for (int32_t x = 0; x < V; x++) {
+    int32_t r = uf_find(&f, x);
+    if (minv[r] == INT32_MAX) nc++;
+    if (x < minv[r]) minv[r] = x;
+  }
+  for (int32_t x = 0; x < V; x++) label[x] = minv[uf_find(&f, x)];
+  free(minv);
+  free(keys);
+  free(br);
+  uf_free(&f);
+  return nc;
 }

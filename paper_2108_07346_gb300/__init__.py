@@ -87,6 +87,13 @@ _SIGS = {
     "bridges_autotune": (_I32, [_P, _P, _P, _P, _I64, _I32, _I32, ctypes.POINTER(ctypes.c_int64)]),
     "bridges_ctx_set_opts": (_I32, [_P, ctypes.POINTER(Opts)]),
     "bridges_wait_value": (_I32, [_P, _P, _P, _I32, _I64]),
+    "bridges_two_edge_components": (_I64, [_P, _P, _P, _P, _I64, _I32, _I32, _P, _P]),
+    "bridges_inc_create": (_P, [ctypes.c_int, ctypes.POINTER(Opts)]),
+    "bridges_inc_destroy": (None, [_P]),
+    "bridges_inc_reset": (_I64, [_P, _P, _P, _P, _I64, _I32, _I32, _P]),
+    "bridges_inc_add": (_I64, [_P, _P, _P, _P, _I64, _P]),
+    "bridges_inc_two_edge_components": (_I64, [_P, _P, _P]),
+    "bridges_inc_certificate_size": (_I64, [_P]),
 }
 
 
@@ -278,6 +285,15 @@ class Context:
             raise ValueError("flag must be an int32 CUDA tensor")
         return int(self._lib.bridges_wait_value(self._h, _stream(stream), _ptr(flag), int(value), int(max_polls)))
 
+    def two_edge_components(self, u, v, V: int, M: int = 0, stream=None):
+        """bridges_two_edge_components: (count, labels (V,) int32 device tensor, bridges (n, 2))."""
+        u, v = _dev_edges(u, v)
+        labels = torch.empty(max(V, 1), dtype=torch.int32, device=u.device)
+        out = torch.empty(2 * max(V - 1, 1), dtype=torch.int32, device=u.device)
+        n = _check(self._lib.bridges_two_edge_components(self._h, _stream(stream), _ptr(u), _ptr(v), u.numel(), V, M,
+                                                         _ptr(labels), _ptr(out)), "bridges_two_edge_components")
+        return n, labels[:V]
+
     def set_batch_split(self, split_edges: int):
         _check(self._lib.bridges_ctx_set_batch_split(self._h, int(split_edges)), "bridges_ctx_set_batch_split")
 
@@ -375,6 +391,58 @@ class Server:
             self._lib.bridges_server_destroy(self._h)
             self._h = None
             self._live.clear()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Incremental:
+    """bridges_inc: a resident certificate answering "add these edges" queries."""
+
+    def __init__(self, device=None, **opts):
+        self._lib = load()
+        dev = torch.device("cuda", torch.cuda.current_device()) if device is None else torch.device(device)
+        self.device = dev
+        o = Opts()
+        o.warm_edges = opts.get("warm_edges", -1)
+        o.M = opts.get("M", 0)
+        h = self._lib.bridges_inc_create(dev.index, ctypes.byref(o))
+        if not h:
+            raise BridgesError(-4, "bridges_inc_create")
+        self._h = ctypes.c_void_p(h)
+        self.V = 0
+
+    def reset(self, u, v, V: int, M: int = 0, stream=None):
+        u, v = _dev_edges(u, v)
+        out = torch.empty(2 * max(V - 1, 1), dtype=torch.int32, device=u.device)
+        n = _check(self._lib.bridges_inc_reset(self._h, _stream(stream), _ptr(u), _ptr(v), u.numel(), V, M, _ptr(out)),
+                   "bridges_inc_reset")
+        self.V = V
+        return out[: 2 * n].view(n, 2)
+
+    def add(self, u, v, stream=None):
+        u, v = _dev_edges(u, v)
+        out = torch.empty(2 * max(self.V - 1, 1), dtype=torch.int32, device=u.device)
+        n = _check(self._lib.bridges_inc_add(self._h, _stream(stream), _ptr(u), _ptr(v), u.numel(), _ptr(out)),
+                   "bridges_inc_add")
+        return out[: 2 * n].view(n, 2)
+
+    def two_edge_components(self, stream=None):
+        labels = torch.empty(max(self.V, 1), dtype=torch.int32, device=self.device)
+        n = _check(self._lib.bridges_inc_two_edge_components(self._h, _stream(stream), _ptr(labels)),
+                   "bridges_inc_two_edge_components")
+        return n, labels[: self.V]
+
+    def certificate_size(self) -> int:
+        return _check(self._lib.bridges_inc_certificate_size(self._h), "bridges_inc_certificate_size")
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.bridges_inc_destroy(self._h)
+            self._h = None
 
     def __del__(self):
         try:

@@ -268,8 +268,23 @@ int64_t bridges_find_host(bridges_ctx* c, struct CUstream_st* stream, const int3
   if (V > (1 << 30)) return BRIDGES_EINVAL;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   if (cudaSetDevice(c->device) != cudaSuccess) return cuda_fail(cudaGetLastError());
-  // staging: u, v (E each) and the output (2V), 256-byte aligned pieces
-  const size_t eb = align_up(sizeof(int32_t) * (size_t)std::max<int64_t>(E, 1), 256);
+  // pinned, mapped host memory can be streamed by the kernels in place (no device copy of the
+  // edges: graphs larger than device memory work this way)
+  const int32_t* ru = nullptr;
+  const int32_t* rv = nullptr;
+  bool in_place = false;
+  if (c->opts.host_read && E > 0) {
+    cudaPointerAttributes au{}, av{};
+    if (cudaPointerGetAttributes(&au, hu) == cudaSuccess && cudaPointerGetAttributes(&av, hv) == cudaSuccess &&
+        au.type == cudaMemoryTypeHost && av.type == cudaMemoryTypeHost && au.devicePointer && av.devicePointer) {
+      ru = static_cast<const int32_t*>(au.devicePointer);
+      rv = static_cast<const int32_t*>(av.devicePointer);
+      in_place = true;
+    }
+    cudaGetLastError();
+  }
+  // device staging: the output (2V) and, unless read in place, u and v (E each)
+  const size_t eb = in_place ? 0 : align_up(sizeof(int32_t) * (size_t)std::max<int64_t>(E, 1), 256);
   const size_t ob = align_up(sizeof(int32_t) * 2 * (size_t)std::max(V, 1), 256);
   const size_t need = 2 * eb + ob;
   if (need > c->stage_bytes) {
@@ -288,26 +303,14 @@ int64_t bridges_find_host(bridges_ctx* c, struct CUstream_st* stream, const int3
     c->stage_bytes = need;
   }
   char* base = reinterpret_cast<char*>(c->stage);
-  int32_t* du = reinterpret_cast<int32_t*>(base);
-  int32_t* dv = reinterpret_cast<int32_t*>(base + eb);
   int32_t* dout = reinterpret_cast<int32_t*>(base + 2 * eb);
-  const int32_t* ru = du;
-  const int32_t* rv = dv;
-  bool in_place = false;
-  if (c->opts.host_read && E > 0) {
-    // pinned, mapped host memory can be streamed by the kernels directly
-    cudaPointerAttributes au{}, av{};
-    if (cudaPointerGetAttributes(&au, hu) == cudaSuccess && cudaPointerGetAttributes(&av, hv) == cudaSuccess &&
-        au.type == cudaMemoryTypeHost && av.type == cudaMemoryTypeHost && au.devicePointer && av.devicePointer) {
-      ru = static_cast<const int32_t*>(au.devicePointer);
-      rv = static_cast<const int32_t*>(av.devicePointer);
-      in_place = true;
-    }
-    cudaGetLastError();
-  }
-  if (E > 0 && !in_place) {
-    if (cudaMemcpyAsync(du, hu, sizeof(int32_t) * (size_t)E, cudaMemcpyHostToDevice, s) != cudaSuccess ||
-        cudaMemcpyAsync(dv, hv, sizeof(int32_t) * (size_t)E, cudaMemcpyHostToDevice, s) != cudaSuccess)
+  if (!in_place) {
+    int32_t* du = reinterpret_cast<int32_t*>(base);
+    int32_t* dv = reinterpret_cast<int32_t*>(base + eb);
+    ru = du;
+    rv = dv;
+    if (E > 0 && (cudaMemcpyAsync(du, hu, sizeof(int32_t) * (size_t)E, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+                  cudaMemcpyAsync(dv, hv, sizeof(int32_t) * (size_t)E, cudaMemcpyHostToDevice, s) != cudaSuccess))
       return cuda_fail(cudaGetLastError());
   }
   Carved k{};
@@ -770,4 +773,121 @@ extern "C" int32_t bridges_wait_value(bridges_ctx* c, struct CUstream_st* stream
       cudaStreamSynchronize(s) != cudaSuccess)
     return (int32_t)cuda_fail(cudaGetLastError());
   return *reinterpret_cast<int32_t*>(c->h_pinned);
+}
+
+// ---------------------------------------------------------------------------------------------
+// 2-edge-connected components and incremental sessions on a resident certificate.
+extern "C" int64_t bridges_two_edge_components(bridges_ctx* c, struct CUstream_st* stream, const int32_t* u,
+                                               const int32_t* v, int64_t E, int32_t V, int32_t M, int32_t* labels,
+                                               int32_t* out_bridges) {
+  int64_t rc = check_args(c, u, v, E, V, labels);
+  if (rc) return rc;
+  if (V > (1 << 30)) return BRIDGES_EINVAL;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  if (cudaSetDevice(c->device) != cudaSuccess) return cuda_fail(cudaGetLastError());
+  // the bridges go to the caller's buffer or to the (then unused) workspace key area
+  Carved k{};
+  CertPlan p{};
+  rc = run_path(c, s, u, v, E, V, M, out_bridges ? out_bridges : nullptr, &k, &p);
+  if (rc) return rc;
+  Launch L{s, &c->launches, c->num_sms, c->smem_optin};
+  if (!out_bridges) {
+    // run_path skipped the final stage: run it with the bridges written to dscan, a 2V+1 array
+    // the final stage no longer reads by the time it sorts
+    final_stage(L, k.fin, V, k.cert.f1u, k.cert.f1v, k.cert.cnt + 0, V, k.cert.f2u, k.cert.f2v, k.cert.cnt + 1, V,
+                k.cert.P1, k.fin.dscan);
+  }
+  two_edge_components(L, k.fin, V, k.cert.f2u, k.cert.f2v, k.cert.cnt + 1, V, labels, k.fin.count);
+  if (cudaMemcpyAsync(c->h_pinned, k.fin.count, sizeof(int64_t), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      cudaStreamSynchronize(s) != cudaSuccess)
+    return cuda_fail(cudaGetLastError());
+  return c->h_pinned[0];
+}
+
+struct bridges_inc {
+  bridges_ctx* ctx = nullptr;
+  bool ready = false;
+  int32_t V = 0;
+  CertPlan p{};
+  Carved k{};
+};
+
+extern "C" bridges_inc* bridges_inc_create(int device, const bridges_opts* opts) {
+  bridges_inc* I = new (std::nothrow) bridges_inc();
+  if (!I) return nullptr;
+  I->ctx = bridges_ctx_create(device, 0, opts);
+  if (!I->ctx) {
+    delete I;
+    return nullptr;
+  }
+  return I;
+}
+
+extern "C" void bridges_inc_destroy(bridges_inc* I) {
+  if (!I) return;
+  bridges_ctx_destroy(I->ctx);
+  delete I;
+}
+
+extern "C" int64_t bridges_inc_reset(bridges_inc* I, struct CUstream_st* stream, const int32_t* u, const int32_t* v,
+                                     int64_t E, int32_t V, int32_t M, int32_t* out_bridges) {
+  if (!I) return BRIDGES_EINVAL;
+  I->ready = false;
+  int64_t rc = check_args(I->ctx, u, v, E, V, out_bridges);
+  if (rc) return rc;
+  if (V > (1 << 30)) return BRIDGES_EINVAL;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  if (cudaSetDevice(I->ctx->device) != cudaSuccess) return cuda_fail(cudaGetLastError());
+  int32_t dummy[1];
+  rc = run_path(I->ctx, s, u, v, E, V, M, out_bridges ? out_bridges : dummy, &I->k, &I->p);
+  if (rc) return rc;
+  if (cudaMemcpyAsync(I->ctx->h_pinned, I->k.fin.count, sizeof(int64_t), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      cudaStreamSynchronize(s) != cudaSuccess)
+    return cuda_fail(cudaGetLastError());
+  const int64_t n = I->ctx->h_pinned[0];
+  I->V = V;
+  I->ready = n >= 0;
+  return n;
+}
+
+extern "C" int64_t bridges_inc_add(bridges_inc* I, struct CUstream_st* stream, const int32_t* yu, const int32_t* yv,
+                                   int64_t n, int32_t* out_bridges) {
+  if (!I || !I->ready || n < 0 || (n > 0 && (!yu || !yv)) || (I->V > 1 && !out_bridges)) return BRIDGES_EINVAL;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  bridges_ctx* c = I->ctx;
+  if (cudaSetDevice(c->device) != cudaSuccess) return cuda_fail(cudaGetLastError());
+  Launch L{s, &c->launches, c->num_sms, c->smem_optin};
+  const Carved& k = I->k;
+  const int32_t V = I->V;
+  if (cudaMemsetAsync(k.status, 0, sizeof(int32_t), s) != cudaSuccess) return cuda_fail(cudaGetLastError());
+  cert_offer(L, I->p, k.cert, yu, yv, n);
+  int32_t dummy[1];
+  final_stage(L, k.fin, V, k.cert.f1u, k.cert.f1v, k.cert.cnt + 0, V, k.cert.f2u, k.cert.f2v, k.cert.cnt + 1, V,
+              k.cert.P1, out_bridges ? out_bridges : dummy);
+  if (cudaMemcpyAsync(c->h_pinned, k.fin.count, sizeof(int64_t), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      cudaStreamSynchronize(s) != cudaSuccess)
+    return cuda_fail(cudaGetLastError());
+  return c->h_pinned[0];
+}
+
+extern "C" int64_t bridges_inc_two_edge_components(bridges_inc* I, struct CUstream_st* stream, int32_t* labels) {
+  if (!I || !I->ready || (I->V > 0 && !labels)) return BRIDGES_EINVAL;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  bridges_ctx* c = I->ctx;
+  if (cudaSetDevice(c->device) != cudaSuccess) return cuda_fail(cudaGetLastError());
+  Launch L{s, &c->launches, c->num_sms, c->smem_optin};
+  const Carved& k = I->k;
+  two_edge_components(L, k.fin, I->V, k.cert.f2u, k.cert.f2v, k.cert.cnt + 1, I->V, labels, k.fin.count);
+  if (cudaMemcpyAsync(c->h_pinned, k.fin.count, sizeof(int64_t), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      cudaStreamSynchronize(s) != cudaSuccess)
+    return cuda_fail(cudaGetLastError());
+  return c->h_pinned[0];
+}
+
+extern "C" int64_t bridges_inc_certificate_size(const bridges_inc* I) {
+  if (!I || !I->ready) return BRIDGES_EINVAL;
+  int32_t h[2] = {0, 0};
+  if (cudaMemcpy(h, I->k.cert.cnt, sizeof(h), cudaMemcpyDeviceToHost) != cudaSuccess)
+    return cuda_fail(cudaGetLastError());
+  return (int64_t)h[0] + h[1];
 }

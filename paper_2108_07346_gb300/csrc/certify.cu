@@ -346,6 +346,24 @@ __global__ void snap_roots_kernel(CertBufs b, int32_t V, int64_t step, int64_t n
   }
 }
 
+// Range check of edges offered to an existing certificate; the offer is skipped on failure.
+__global__ void offer_check_kernel(int32_t* status, int32_t V, const int32_t* u, const int32_t* v, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    if ((uint32_t)u[i] >= (uint32_t)V || (uint32_t)v[i] >= (uint32_t)V) set_status(status, BRIDGES_ERANGE_CODE);
+}
+
+// Offers edges to partition 0's union-finds: its certificate becomes one of the union.
+__global__ void offer_kernel(CertBufs b, int32_t V, const int32_t* u, const int32_t* v, int64_t n) {
+  if (*b.status) return;
+  const Job J = job_of(b, V, 0);
+  for (int64_t i0 = blockIdx.x * (int64_t)blockDim.x; i0 < n; i0 += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = i0 + threadIdx.x;
+    const bool valid = i < n;
+    const int32_t a = valid ? u[i] : 0, c = valid ? v[i] : 0;
+    scalar_slot(J, valid, a, c, V, nullptr, false, b.status);
+  }
+}
+
 __global__ void export_kernel(CertBufs b, int32_t cap, int32_t* cu, int32_t* cv, uint8_t* ct) {
   const int32_t V = (cap + 2) / 2;  // each forest list holds at most V entries
   const int32_t n1 = min(min(b.cnt[0], V), cap), n2 = min(min(b.cnt[1], V), cap - n1);
@@ -509,6 +527,14 @@ void cert_merge(const Launch& L, const CertPlan& p, const CertBufs& b) {
     }
     *L.launches += 1;
   }
+}
+
+void cert_offer(const Launch& L, const CertPlan& p, const CertBufs& b, const int32_t* u, const int32_t* v, int64_t n) {
+  if (n <= 0) return;
+  const int g = grid_for(L, n, 256);
+  offer_check_kernel<<<g, 256, 0, L.stream>>>(b.status, p.V, u, v, n);
+  offer_kernel<<<g, 256, 0, L.stream>>>(b, p.V, u, v, n);
+  *L.launches += 2;
 }
 
 void cert_export(const Launch& L, const CertPlan& p, const CertBufs& b, int32_t* cu, int32_t* cv, uint8_t* ct) {

@@ -430,6 +430,7 @@ __global__ void __launch_bounds__(kThreads) final_kernel(FinArgs A) {
     const int64_t y = base + threadIdx.x;
     bool is_bridge = false;
     uint64_t key = 0;
+    if (y < V) f.bflag[y] = 0;
     if (y < V && f.par[y] >= 0) {
       const int64_t l = f.pre[y];
       const int64_t r = min((int64_t)V, l + max(f.sz[y], 1));
@@ -455,6 +456,7 @@ __global__ void __launch_bounds__(kThreads) final_kernel(FinArgs A) {
         const uint32_t a = (uint32_t)min((int32_t)y, f.par[y]), b = (uint32_t)max((int32_t)y, f.par[y]);
         key = ((uint64_t)a << A.kbits) | b;
         is_bridge = true;
+        f.bflag[y] = 1;
       }
     }
     const unsigned m = __ballot_sync(kFull, is_bridge);
@@ -573,13 +575,66 @@ int bits_for(int32_t V) {
   return k;
 }
 
+// ---- 2-edge-connected components: union-find over the certificate minus its bridges ----
+__global__ void tecc_init_kernel(FinalBufs f, int32_t V) {
+  for (int64_t x = gtid(); x < V; x += gstride()) f.P[x] = (int32_t)x;
+  if (gtid() == 0) *f.nkeys = 0;
+}
+
+__global__ void tecc_link_kernel(FinalBufs f, int32_t V, const int32_t* xu, const int32_t* xv, const int32_t* d_nx,
+                                 int32_t cx) {
+  if (*f.status) return;  // the bridge stage failed: labels are left untouched
+  for (int64_t y = gtid(); y < V; y += gstride())
+    if (f.par[y] >= 0 && !f.bflag[y]) uf_link(f.P, (int32_t)y, f.par[y]);
+  const int32_t nx = min(*d_nx, cx);
+  for (int64_t e = gtid(); e < nx; e += gstride()) {
+    const int32_t a = xu[e], b = xv[e];
+    if ((uint32_t)a < (uint32_t)V && (uint32_t)b < (uint32_t)V && a != b) uf_link(f.P, a, b);
+  }
+}
+
+__global__ void tecc_label_kernel(FinalBufs f, int32_t V, int32_t* labels, int64_t* count) {
+  const int32_t st = *f.status;
+  for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < V; base += gstride()) {
+    const int64_t x = base + threadIdx.x;
+    bool root = false;
+    if (x < V && !st) {
+      const int32_t r = uf_find_static(f.P, (int32_t)x);
+      labels[x] = r;
+      root = r == x;
+    }
+    const unsigned m = __ballot_sync(kFull, root);
+    if (m && (threadIdx.x & 31) == __ffs(m) - 1) atomicAdd(f.nkeys, __popc(m));
+  }
+}
+
+__global__ void tecc_count_kernel(FinalBufs f, int64_t* count) {
+  const int32_t st = *f.status;
+  *count = st ? (int64_t)st : (int64_t)*f.nkeys;
+}
+
+}  // namespace
+
+void two_edge_components(const Launch& L, const FinalBufs& f, int32_t V, const int32_t* xu, const int32_t* xv,
+                         const int32_t* d_nx, int64_t cap_extra, int32_t* labels, int64_t* count_dev) {
+  const int bs = 256;
+  const int g = (int)std::min<int64_t>(ceil_div(std::max(V, 1), bs), (int64_t)L.num_sms * 16);
+  const int32_t cx = (int32_t)std::min<int64_t>(cap_extra, INT32_MAX);
+  tecc_init_kernel<<<g, bs, 0, L.stream>>>(f, V);
+  tecc_link_kernel<<<g, bs, 0, L.stream>>>(f, V, xu, xv, d_nx, cx);
+  tecc_label_kernel<<<g, bs, 0, L.stream>>>(f, V, labels, count_dev);
+  tecc_count_kernel<<<1, 1, 0, L.stream>>>(f, count_dev);
+  *L.launches += 4;
+}
+
+namespace {
 }  // namespace
 
 size_t final_bytes(int32_t V) {
   const size_t Vs = (size_t)std::max(V, 1);
   size_t s = 0;
   s += 3 * 256;                                                           // count, nkeys, barrier
-  s += 12 * align_up(sizeof(int32_t) * (Vs + 1), 256);                    // V-long arrays
+  s += 13 * align_up(sizeof(int32_t) * (Vs + 1), 256);                    // V-long arrays
   s += 7 * align_up(sizeof(int32_t) * (2 * Vs + 1), 256);                 // 2V-long arrays
   s += 4 * align_up(sizeof(int32_t) * (Vs / kChunk + 2), 256);            // chunk / superchunk min, max
   s += 2 * align_up(sizeof(uint64_t) * Vs, 256);                          // keys
@@ -600,7 +655,8 @@ FinalBufs carve_final(void* base, int32_t V, int32_t* status) {
   f.bar_count = reinterpret_cast<unsigned*>(c);
   f.bar_gen = f.bar_count + 1;
   c += 256;
-  int32_t** va[12] = {&f.P, &f.root, &f.deg, &f.off, &f.cur, &f.aoff, &f.vbase, &f.pre, &f.sz, &f.par, &f.lo, &f.hi};
+  int32_t** va[13] = {&f.P,    &f.root, &f.deg, &f.off, &f.cur, &f.aoff, &f.vbase,
+                      &f.pre,  &f.sz,   &f.par, &f.lo,  &f.hi,  &f.bflag};
   for (auto a : va) {
     *a = reinterpret_cast<int32_t*>(c);
     c += align_up(sizeof(int32_t) * (Vs + 1), 256);

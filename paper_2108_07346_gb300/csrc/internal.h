@@ -77,6 +77,7 @@ struct FinalBufs {
   int32_t* pre;    // [V]
   int32_t* sz;     // [V]
   int32_t* par;    // [V] parent in the rooted tree (-1 for roots)
+  int32_t* bflag;  // [V] 1 if the tree edge (par[y], y) is a bridge
   int32_t* lo;     // [V] indexed by preorder
   int32_t* hi;     // [V]
   int32_t* cmin;   // [V/32] chunk minima of lo
@@ -109,6 +110,13 @@ void cert_export(const Launch& L, const CertPlan& p, const CertBufs& b, int32_t*
 // ---- final.cu ----
 size_t final_bytes(int32_t V);
 FinalBufs carve_final(void* base, int32_t V, int32_t* status);
+// 2-edge-connected components after final_stage: labels[x] = minimum vertex of x's component
+// (the components of T u X minus its bridges); count_dev receives their number.
+void two_edge_components(const Launch& L, const FinalBufs& fb, int32_t V, const int32_t* xu, const int32_t* xv,
+                         const int32_t* d_nx, int64_t cap_extra, int32_t* labels, int64_t* count_dev);
+// Offers n extra edges to partition 0's union-finds (its certificate grows to a certificate of
+// the union).  Ids are range-checked first; on ERANGE nothing is changed.
+void cert_offer(const Launch& L, const CertPlan& p, const CertBufs& b, const int32_t* u, const int32_t* v, int64_t n);
 // Bridges of T u X (T a spanning forest of every tree it touches, X edges inside trees).
 // Counts on device.  P_tree: union-find of T (roots = minimum vertex), or null to build it.
 void final_stage(const Launch& L, const FinalBufs& fb, int32_t V, const int32_t* tu, const int32_t* tv,

@@ -17,8 +17,8 @@ pytestmark = pytest.mark.gpu
 
 def dev_edges(u, v):
     d = torch.device("cuda", 0)
-    return (torch.from_numpy(np.ascontiguousarray(u, dtype=np.int32)).to(d),
-            torch.from_numpy(np.ascontiguousarray(v, dtype=np.int32)).to(d))
+    return (torch.from_numpy(np.array(u, dtype=np.int32)).to(d),
+            torch.from_numpy(np.array(v, dtype=np.int32)).to(d))
 
 
 @pytest.fixture(scope="module")
@@ -224,3 +224,17 @@ def test_stage_timings_and_launch_count(cuda_lib):
     assert ms["total"] > 0 and c.launches() > before
     cfg = c.last_config()
     assert cfg["M"] == 4
+
+
+def test_host_read_in_place(cuda_lib):
+    """opts.host_read: kernels stream pinned host memory directly (no device copy of the edges),
+    the out-of-core form; results unchanged."""
+    g = graphgen.workload("mid")
+    ref = oracle.bridges(g.u, g.v, g.V, 16)
+    hu = torch.from_numpy(np.array(g.u)).pin_memory()
+    hv = torch.from_numpy(np.array(g.v)).pin_memory()
+    c = cuda_lib.Context(device="cuda:0", host_read=True)
+    assert c.find_host(hu, hv, g.V, 4).numpy().tolist() == ref.tolist()
+    # pageable host memory falls back to copying
+    assert c.find_host(torch.from_numpy(np.array(g.u)), torch.from_numpy(np.array(g.v)), g.V, 4).numpy().tolist() \
+        == ref.tolist()

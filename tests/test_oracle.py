@@ -216,3 +216,54 @@ def test_invalid_ids_rejected():
         oracle.bridges(np.array([0], np.int32), np.array([5], np.int32), 3)
     with pytest.raises(ValueError):
         oracle.dfs_bridges(np.array([-1], np.int32), np.array([0], np.int32), 3)
+
+
+def _brute_2ecc(u, v, V):
+    """Definition: x and y are 2-edge-connected iff they stay connected after deleting any one
+    edge (Menger: two edge-disjoint paths).  Labels = min vertex of each class."""
+    E = len(u)
+
+    def comp(skip):
+        par = list(range(V))
+
+        def f(x):
+            while par[x] != x:
+                par[x] = par[par[x]]
+                x = par[x]
+            return x
+
+        for e in range(E):
+            if e != skip:
+                a, b = f(int(u[e])), f(int(v[e]))
+                if a != b:
+                    par[max(a, b)] = min(a, b)
+        return [f(x) for x in range(V)]
+
+    base = comp(-1)
+    cut = [comp(e) for e in range(E)]
+    lab = []
+    for x in range(V):
+        cls = [y for y in range(V) if base[y] == base[x] and all(c[x] == c[y] for c in cut)]
+        lab.append(min(cls))
+    return lab
+
+
+def test_two_edge_components_brute():
+    for t in range(200):
+        rng = np.random.default_rng(600 + t)
+        V = int(rng.integers(1, 11))
+        E = int(rng.integers(0, 2 * V + 3))
+        u, v = graphgen.random_multigraph(8800 + t, V, E)
+        c, lab = oracle.two_edge_components(u, v, V)
+        assert lab.tolist() == _brute_2ecc(u, v, V), (t, V, E)
+        assert c == len(set(lab.tolist()))
+
+
+def test_two_edge_components_closed_forms():
+    u, v, V, _ = load_golden("barbell.txt")
+    c, lab = oracle.two_edge_components(u, v, V)
+    assert lab.tolist() == [0, 0, 0, 0, 4, 4, 4, 4, 8] and c == 3
+    n = 9
+    a = np.arange(n - 1, dtype=np.int32)
+    c, lab = oracle.two_edge_components(a, a + 1, n)  # a path: every vertex alone
+    assert c == n and lab.tolist() == list(range(n))
