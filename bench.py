@@ -30,9 +30,10 @@ import graphgen  # noqa: E402
 METRIC = "input edges/s to exact bridge set"
 UNIT = "GE/s"
 
-# DRAM bytes (read + write) of one forest-pass launch on the large workload, from the ncu capture
-# summarised in profiles/; valid only for the kernel source it was measured on.
-TRAFFIC = {"certify_sha": "2e55e2f2841dbfd6", "bytes_per_edge": 8.272}
+# DRAM bytes (read + write) per streamed edge of the forest pass on the large workload, from the
+# full-size ncu capture summarised in profiles/forest_pass_large_dense.md (9.4487 GB read +
+# 7.50 MB written for 1,073,198,031 edges); valid only for the kernel sources it was measured on.
+TRAFFIC = {"certify_sha": "422b9da375aa940d", "bytes_per_edge": 8.811}
 
 
 def peaks():
@@ -44,8 +45,11 @@ def peaks():
 
 
 def certify_sha():
-    src = os.path.join(ROOT, "paper_2108_07346_gb300", "csrc", "certify.cu")
-    return hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    """Hash of the forest pass's sources (the traffic figure is only valid for them)."""
+    h = hashlib.sha256()
+    for name in ("certify.cu", "common.cuh"):
+        h.update(open(os.path.join(ROOT, "paper_2108_07346_gb300", "csrc", name), "rb").read())
+    return h.hexdigest()[:16]
 
 
 class Clocks:
