@@ -31,9 +31,9 @@ METRIC = "input edges/s to exact bridge set"
 UNIT = "GE/s"
 
 # DRAM bytes (read + write) per streamed edge of the forest pass on the large workload, from the
-# full-size ncu capture summarised in profiles/forest_pass_large_dense.md (9.4487 GB read +
-# 7.50 MB written for 1,073,198,031 edges); valid only for the kernel sources it was measured on.
-TRAFFIC = {"certify_sha": "422b9da375aa940d", "bytes_per_edge": 8.811}
+# full-size ncu capture summarised in profiles/launch_list_large_dense.md (9.31 GB read + 7.2 MB
+# written for 1,072,703,284 edges, M = 1); valid only for the kernel sources it was measured on.
+TRAFFIC = {"certify_sha": "e17c42dc593d1285", "bytes_per_edge": 8.683}
 
 
 def peaks():

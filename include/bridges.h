@@ -273,7 +273,7 @@ int64_t bridges_inc_certificate_size(const bridges_inc* inc);
 /* ---------------------------------------------------------------------------------------
  * Autotuning.
  * bridges_autotune: times candidate plans on the given device-resident input (M in
- * {1,2,4,8,16,32}, fan-in 2 or M, warm-up 0.3/0.6/1.2 x V ln V edges, block 1024 or 512; `reps`
+ * {1,2,4,8,16,32}, fan-in 2 or M, warm-up 0.6/1.2/2.0 x V ln V edges, block 1024 or 512; `reps`
  * timed calls each, CUDA events on `stream`) and keeps the fastest in the context's options.
  * best[0..4] receives M, fan-in, warm-up edges, block size and microseconds per call.  Uses
  * a little scratch memory of its own (the output buffers).  Returns BRIDGES_OK or an error (the
