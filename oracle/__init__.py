@@ -38,6 +38,13 @@ def _load():
         lib.oracle_pipeline_cert.restype = ctypes.c_int64
         lib.oracle_pipeline_cert.argtypes = [_I32P, _I32P, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32,
                                              _I32P, _I32P, _I32P, _I32P]
+        for name in ("oracle_articulation_points", "oracle_brute_articulation"):
+            f = getattr(lib, name)
+            f.restype = ctypes.c_int64
+            f.argtypes = [_I32P, _I32P, ctypes.c_int64, ctypes.c_int32, _I32P]
+        lib.oracle_block_certificate.restype = ctypes.c_int64
+        lib.oracle_block_certificate.argtypes = [_I32P, _I32P, ctypes.c_int64, ctypes.c_int32, _I32P, _I32P, _I32P,
+                                                 _I32P]
         lib.oracle_two_edge_components.restype = ctypes.c_int32
         lib.oracle_two_edge_components.argtypes = [_I32P, _I32P, ctypes.c_int64, ctypes.c_int32, _I32P]
         lib.oracle_components.restype = ctypes.c_int32
@@ -126,3 +133,33 @@ def two_edge_components(u, v, V: int):
     lab = np.empty(max(V, 1), np.int32)
     c = _check(_load().oracle_two_edge_components(u.ctypes.data, v.ctypes.data, u.shape[0], V, lab.ctypes.data))
     return int(c), lab[:V].copy()
+
+
+def _vertex_call(name, u, v, V):
+    u, v = _edges(u, v)
+    out = np.empty(max(V, 1), np.int32)
+    n = _check(getattr(_load(), name)(u.ctypes.data, v.ctypes.data, u.shape[0], V, out.ctypes.data))
+    return out[:n].copy()
+
+
+def articulation_points(u, v, V: int) -> np.ndarray:
+    """Articulation points (sorted vertex ids) by Tarjan's DFS low/disc test."""
+    return _vertex_call("oracle_articulation_points", u, v, V)
+
+
+def brute_articulation(u, v, V: int) -> np.ndarray:
+    """The definition: vertices whose deletion increases the number of components."""
+    return _vertex_call("oracle_brute_articulation", u, v, V)
+
+
+def block_certificate(u, v, V: int):
+    """Tree edges T plus the edges that merge fundamental-cycle classes, in input order:
+    (edge ids, tree flags, articulation points derived from the classes)."""
+    u, v = _edges(u, v)
+    ids = np.empty(max(2 * V, 1), np.int64)
+    tr = np.empty(max(2 * V, 1), np.uint8)
+    pts = np.empty(max(V, 1), np.int32)
+    npt = np.zeros(1, np.int64)
+    k = _check(_load().oracle_block_certificate(u.ctypes.data, v.ctypes.data, u.shape[0], V, ids.ctypes.data,
+                                                tr.ctypes.data, pts.ctypes.data, npt.ctypes.data))
+    return ids[:k].copy(), tr[:k].astype(bool), pts[: int(npt[0])].copy()

@@ -24,6 +24,14 @@
  *   oracle_components       Connected components (min vertex id of each component).
  *   oracle_two_edge_components  2-edge-connected components: the components of the graph
  *                           after deleting its bridges (found by Alg. 1); label = min vertex.
+ *   oracle_articulation_points  articulation ("failure") points, abstract of the paper: vertices
+ *                           whose removal increases the number of components.  Tarjan's DFS
+ *                           low/disc test (a root with >= 2 children; another vertex with a
+ *                           child whose low >= its disc), iterative.
+ *   oracle_brute_articulation   the definition: delete each vertex, count components.
+ *   oracle_block_certificate    the articulation-point method of the CUDA path, sequential: the
+ *                           blocks restricted to a spanning forest T as classes of fundamental
+ *                           cycles, the edges that merge classes, and the cut vertices they give.
  *
  * Readings of the paper used here (each one listed in the design notes):
  *   - Alg. 1 recurses into v when v is NOT yet visited; the timer is global and increments at
@@ -571,4 +579,220 @@ int32_t oracle_two_edge_components(const int32_t* u, const int32_t* v, int64_t E
   free(br);
   uf_free(&f);
   return nc;
+}
+
+/* ------------------------------------------------------------------ */
+/* articulation points                                                 */
+/* ------------------------------------------------------------------ */
+static int64_t emit_vertices(uint8_t* flag, int32_t V, int32_t* out) {
+  int64_t n = 0;
+  for (int32_t x = 0; x < V; x++)
+    if (flag[x]) out[n++] = x;
+  return n;
+}
+
+int64_t oracle_articulation_points(const int32_t* u, const int32_t* v, int64_t E, int32_t V, int32_t* out) {
+  if (E < 0 || V < 0) return -1;
+  if (check_ids(u, v, E, V)) return -1;
+  csr_t g;
+  if (csr_build(&g, u, v, NULL, E, V)) return -2;
+  size_t Vs = (size_t)(V > 0 ? V : 1);
+  int64_t* disc = (int64_t*)calloc(Vs, sizeof(int64_t));
+  int64_t* low = (int64_t*)malloc(sizeof(int64_t) * Vs);
+  int32_t* st_v = (int32_t*)malloc(sizeof(int32_t) * Vs);
+  int64_t* st_pe = (int64_t*)malloc(sizeof(int64_t) * Vs);
+  int64_t* st_it = (int64_t*)malloc(sizeof(int64_t) * Vs);
+  int64_t* nchild = (int64_t*)calloc(Vs, sizeof(int64_t));
+  uint8_t* ap = (uint8_t*)calloc(Vs, 1);
+  if (!disc || !low || !st_v || !st_pe || !st_it || !nchild || !ap) return -2;
+  int64_t time = 0;
+  for (int32_t s = 0; s < V; s++) {
+    if (disc[s]) continue;
+    int64_t sp = 0;
+    st_v[0] = s;
+    st_pe[0] = -1;
+    st_it[0] = g.off[s];
+    disc[s] = low[s] = ++time;
+    while (sp >= 0) {
+      int32_t x = st_v[sp];
+      if (st_it[sp] < g.off[x + 1]) {
+        int64_t k = st_it[sp]++;
+        int32_t w = g.nbr[k];
+        int64_t e = g.eid[k];
+        if (e == st_pe[sp]) continue;
+        if (!disc[w]) {
+          nchild[x]++;
+          sp++;
+          st_v[sp] = w;
+          st_pe[sp] = e;
+          st_it[sp] = g.off[w];
+          disc[w] = low[w] = ++time;
+        } else if (disc[w] < low[x]) {
+          low[x] = disc[w];
+        }
+      } else {
+        if (sp > 0) {
+          int32_t p = st_v[sp - 1];
+          if (low[x] < low[p]) low[p] = low[x];
+          /* a non-root p separates its child's subtree when nothing there reaches above p */
+          if (sp - 1 > 0 && low[x] >= disc[p]) ap[p] = 1;
+        }
+        sp--;
+      }
+    }
+    if (nchild[s] >= 2) ap[s] = 1; /* a root separates its >= 2 children */
+  }
+  int64_t n = emit_vertices(ap, V, out);
+  csr_free(&g);
+  free(disc);
+  free(low);
+  free(st_v);
+  free(st_pe);
+  free(st_it);
+  free(nchild);
+  free(ap);
+  return n;
+}
+
+/* components of the graph with vertex `skip` deleted (skip < 0: none), ignoring that vertex */
+static int32_t count_components_without(const int32_t* u, const int32_t* v, int64_t E, int32_t V, int32_t skip,
+                                        uf_t* f) {
+  uf_reset(f);
+  for (int64_t e = 0; e < E; e++) {
+    if (u[e] == skip || v[e] == skip) continue;
+    uf_union(f, u[e], v[e]);
+  }
+  int32_t c = 0;
+  for (int32_t x = 0; x < V; x++)
+    if (x != skip && uf_find(f, x) == x) c++;
+  return c;
+}
+
+int64_t oracle_brute_articulation(const int32_t* u, const int32_t* v, int64_t E, int32_t V, int32_t* out) {
+  if (E < 0 || V < 0) return -1;
+  if (check_ids(u, v, E, V)) return -1;
+  uf_t f;
+  if (uf_init(&f, V)) return -2;
+  uint8_t* ap = (uint8_t*)calloc((size_t)(V > 0 ? V : 1), 1);
+  const int32_t base = count_components_without(u, v, E, V, -1, &f);
+  for (int32_t x = 0; x < V; x++) {
+    /* deleting x removes its own component when x is isolated; otherwise compare */
+    int isolated = 1;
+    for (int64_t e = 0; e < E && isolated; e++)
+      if ((u[e] == x || v[e] == x) && u[e] != v[e]) isolated = 0;
+    if (isolated) continue;
+    if (count_components_without(u, v, E, V, x, &f) > base) ap[x] = 1;
+  }
+  int64_t n = emit_vertices(ap, V, out);
+  free(ap);
+  uf_free(&f);
+  return n;
+}
+
+/* The block certificate of a spanning forest T (the GPU's articulation-point method, restated
+ * sequentially).  T = the first forest of Alg. 2 (union-find over the edges in input order), each
+ * tree rooted at its minimum vertex.  Tree edge (x, parent x) is named by x.  Every non-tree edge
+ * closes a fundamental cycle with T, and the tree edges of one cycle lie in one block; so the
+ * blocks, restricted to T, are the classes of the transitive closure of "on a common fundamental
+ * cycle".  Edges are taken in input order: an edge whose cycle touches at least two current
+ * classes merges them and is kept, any other adds nothing to the block structure and is dropped.
+ * Each kept edge lowers the class count, so at most V - 1 are kept.  A vertex is an articulation
+ * point iff its incident tree edges fall into at least two classes (each block through it holds
+ * one of its tree edges).  Returns |T| + kept, fills out_ids (room for 2V) / out_tree flags and
+ * the sorted articulation points (out_points, *out_np). */
+int64_t oracle_block_certificate(const int32_t* u, const int32_t* v, int64_t E, int32_t V, int64_t* out_ids,
+                                 uint8_t* out_tree, int32_t* out_points, int64_t* out_np) {
+  if (E < 0 || V < 0) return -1;
+  if (check_ids(u, v, E, V)) return -1;
+  size_t Vs = (size_t)(V > 0 ? V : 1);
+  uf_t f;
+  if (uf_init(&f, V)) return -2;
+  uint8_t* in_t = (uint8_t*)calloc((size_t)(E > 0 ? E : 1), 1);
+  int64_t* tids = (int64_t*)malloc(sizeof(int64_t) * Vs);
+  int64_t nt = 0;
+  for (int64_t e = 0; e < E; e++)
+    if (uf_union(&f, u[e], v[e])) {
+      in_t[e] = 1;
+      tids[nt++] = e;
+    }
+  /* root every tree at its minimum vertex: parent and depth by an explicit-stack traversal */
+  csr_t t;
+  if (csr_build(&t, u, v, tids, nt, V)) return -2;
+  int32_t* parent = (int32_t*)malloc(sizeof(int32_t) * Vs);
+  int32_t* depth = (int32_t*)malloc(sizeof(int32_t) * Vs);
+  int32_t* stack = (int32_t*)malloc(sizeof(int32_t) * Vs);
+  for (int32_t x = 0; x < V; x++) parent[x] = -2;
+  for (int32_t s = 0; s < V; s++) {
+    if (parent[s] != -2) continue;
+    parent[s] = -1;
+    depth[s] = 0;
+    int32_t sp = 0;
+    stack[sp++] = s;
+    while (sp) {
+      int32_t x = stack[--sp];
+      for (int64_t k = t.off[x]; k < t.off[x + 1]; k++) {
+        int32_t w = t.nbr[k];
+        if (parent[w] != -2) continue;
+        parent[w] = x;
+        depth[w] = depth[x] + 1;
+        stack[sp++] = w;
+      }
+    }
+  }
+  /* classes of tree edges */
+  uf_t g;
+  if (uf_init(&g, V)) return -2;
+  int32_t* path = (int32_t*)malloc(sizeof(int32_t) * Vs);
+  int64_t k = 0;
+  for (int64_t i = 0; i < nt; i++) {
+    out_ids[k] = tids[i];
+    out_tree[k++] = 1;
+  }
+  for (int64_t e = 0; e < E; e++) {
+    if (in_t[e] || u[e] == v[e]) continue;
+    int32_t x = u[e], y = v[e], n = 0;
+    while (x != y) { /* the tree path between the ends: climb the deeper end */
+      if (depth[x] >= depth[y]) {
+        path[n++] = x;
+        x = parent[x];
+      } else {
+        path[n++] = y;
+        y = parent[y];
+      }
+    }
+    int merged = 0;
+    for (int32_t j = 1; j < n; j++) merged |= uf_union(&g, path[0], path[j]);
+    if (merged) {
+      out_ids[k] = e;
+      out_tree[k++] = 0;
+    }
+  }
+  uint8_t* ap = (uint8_t*)calloc(Vs, 1);
+  int32_t* first = (int32_t*)malloc(sizeof(int32_t) * Vs);
+  for (int32_t x = 0; x < V; x++) first[x] = -1;
+  for (int32_t c = 0; c < V; c++) {
+    int32_t p = parent[c];
+    if (p < 0) continue;
+    int32_t gc = uf_find(&g, c);
+    if (parent[p] >= 0) {
+      if (gc != uf_find(&g, p)) ap[p] = 1; /* child edge and parent edge in different blocks */
+    } else if (first[p] < 0) {
+      first[p] = gc;
+    } else if (first[p] != gc) {
+      ap[p] = 1; /* a root whose child edges span two blocks */
+    }
+  }
+  *out_np = emit_vertices(ap, V, out_points);
+  uf_free(&f);
+  uf_free(&g);
+  csr_free(&t);
+  free(in_t);
+  free(tids);
+  free(parent);
+  free(depth);
+  free(stack);
+  free(path);
+  free(ap);
+  free(first);
+  return k;
 }

@@ -267,3 +267,71 @@ def test_two_edge_components_closed_forms():
     a = np.arange(n - 1, dtype=np.int32)
     c, lab = oracle.two_edge_components(a, a + 1, n)  # a path: every vertex alone
     assert c == n and lab.tolist() == list(range(n))
+
+
+def test_articulation_points_brute_and_closed_forms():
+    rng = np.random.default_rng(41)
+    for t in range(1000):
+        V = int(rng.integers(1, 40))
+        E = int(rng.integers(0, 3 * V + 2))
+        u, v = graphgen.random_multigraph(12000 + t, V, E)
+        assert oracle.articulation_points(u, v, V).tolist() == oracle.brute_articulation(u, v, V).tolist(), t
+    n = 12
+    a = np.arange(n - 1, dtype=np.int32)
+    assert oracle.articulation_points(a, a + 1, n).tolist() == list(range(1, n - 1))  # path
+    assert oracle.articulation_points(np.zeros(n - 1, np.int32), a + 1, n).tolist() == [0]  # star
+    c = np.arange(n, dtype=np.int32)
+    assert len(oracle.articulation_points(c, (c + 1) % n, n)) == 0  # cycle
+    # two triangles sharing vertex 2 (bow tie): 2 is the only cut vertex
+    u = np.array([0, 1, 2, 2, 3, 4], np.int32)
+    v = np.array([1, 2, 0, 3, 4, 2], np.int32)
+    assert oracle.articulation_points(u, v, 5).tolist() == [2]
+    # a random tree: exactly the vertices of degree >= 2
+    rng = np.random.default_rng(43)
+    for n in (2, 3, 50, 3000):
+        par = (rng.random(n - 1) * np.arange(1, n)).astype(np.int32)
+        ch = np.arange(1, n, dtype=np.int32)
+        deg = np.bincount(np.concatenate([par, ch]), minlength=n)
+        assert oracle.articulation_points(par, ch, n).tolist() == np.flatnonzero(deg >= 2).tolist()
+        assert oracle.block_certificate(par, ch, n)[2].tolist() == np.flatnonzero(deg >= 2).tolist()
+    # complete graph K_6 with every edge doubled and self-loops: none
+    a, b = np.triu_indices(6, 1)
+    u = np.concatenate([a, b, np.arange(6)]).astype(np.int32)
+    v = np.concatenate([b, a, np.arange(6)]).astype(np.int32)
+    assert len(oracle.articulation_points(u, v, 6)) == 0 and len(oracle.block_certificate(u, v, 6)[2]) == 0
+    # barbell fixture: the path 3-8-4 makes 3, 8 and 4 cut vertices
+    bu, bv, bV, _ = load_golden("barbell.txt")
+    assert oracle.articulation_points(bu, bv, bV).tolist() == [3, 4, 8]
+
+
+def test_block_certificate_articulation_points():
+    """The fundamental-cycle classes over a spanning forest give the cut vertices of the
+    definition; T plus the kept edges keeps them, with at most V - 1 kept non-tree edges."""
+    rng = np.random.default_rng(42)
+    for t in range(1500):
+        V = int(rng.integers(1, 40))
+        E = int(rng.integers(0, 6 * V + 2))
+        u, v = graphgen.random_multigraph(13000 + t, V, E)
+        ids, tr, pts = oracle.block_certificate(u, v, V)
+        brute = oracle.brute_articulation(u, v, V).tolist()
+        assert pts.tolist() == brute, t
+        c, _ = oracle.components(u, v, V)
+        assert int(tr.sum()) == V - c and int((~tr).sum()) <= max(V - 1, 0)
+        assert oracle.brute_articulation(u[ids], v[ids], V).tolist() == brute, t
+        assert len(np.unique(ids)) == len(ids)
+
+
+def test_arbitrary_forests_do_not_keep_articulation_points():
+    """Why a separate certificate: the union-find forests of Alg. 2 keep bridges but not cut
+    vertices.  A 4-cycle 0-1-2-3 with chord 1-3 and a pendant path through 0: an Alg. 2
+    certificate may drop edges so that a non-cut vertex becomes one."""
+    found = False
+    for t in range(300):
+        rng = np.random.default_rng(t)
+        V = 7
+        u, v = graphgen.random_multigraph(14000 + t, V, 14)
+        ids, f1 = oracle.certificate(u, v, V)
+        if oracle.articulation_points(u[ids], v[ids], V).tolist() != oracle.articulation_points(u, v, V).tolist():
+            found = True
+            break
+    assert found
