@@ -271,6 +271,41 @@ int64_t bridges_inc_two_edge_components(bridges_inc* inc, struct CUstream_st* st
 int64_t bridges_inc_certificate_size(const bridges_inc* inc);
 
 /* ---------------------------------------------------------------------------------------
+ * Articulation points ("failure points", abstract of the paper): the vertices whose removal
+ * increases the number of connected components.  The paper names them but gives no method;
+ * its bridge certificate does not keep them (two arbitrary spanning forests can split a
+ * biconnected graph at a vertex), so this call runs the bridge path (Sec. 3) for its rooted
+ * spanning forest T and then streams the edge list once more, merging for every edge the
+ * classes of the tree edges on its fundamental cycle with T; the final classes are the blocks
+ * (biconnected components) restricted to T, and a vertex is a cut vertex iff its tree edges lie
+ * in two or more of them.  Parallel edges and self-loops are allowed and change nothing.
+ *
+ * bridges_articulation_points
+ *   edges_u, edges_v, E, V, M : as for bridges_find_ctx (device edges; M for the bridge path).
+ *   out_points        : device, capacity max(V, 1) int32; receives the cut vertices in
+ *                       increasing order (may be NULL only when V <= 1).
+ *   out_bridges       : device, capacity 2*max(V-1, 0) int32, or NULL; receives the sorted
+ *                       bridge pairs as bridges_find_ctx does.
+ *   out_counts_device : device int64[2] or NULL: [0] the number of cut vertices, [1] the number
+ *                       of bridges (either may be a negative status).
+ * Synchronous when out_counts_device is NULL (returns the number of cut vertices or a negative
+ * status); otherwise enqueue-only, returning BRIDGES_OK.  Errors: as bridges_find_ctx (ERANGE for
+ * a vertex id outside [0, V), found on the device; EINVAL / ENOMEM on the host).
+ *
+ * bridges_articulation_workspace_bytes: workspace a context needs for this call (contexts made
+ *   with bridges_ctx_create_ws must be at least this large).
+ * bridges_ctx_ap_stage_ms: on a profiling context, the stage times of the last call's block
+ *   pass in ms: [0] warm-up (certificate edges + prefix), [1] label snapshot, [2] stream,
+ *   [3] marking and compaction, [4] the whole block pass; waits for them; returns how many were
+ *   written (0 when none are available).
+ */
+int64_t bridges_articulation_points(bridges_ctx* ctx, struct CUstream_st* stream, const int32_t* edges_u,
+                                    const int32_t* edges_v, int64_t E, int32_t V, int32_t M, int32_t* out_points,
+                                    int32_t* out_bridges, int64_t* out_counts_device);
+int64_t bridges_articulation_workspace_bytes(const bridges_ctx* ctx, int64_t E, int32_t V, int32_t M);
+int32_t bridges_ctx_ap_stage_ms(const bridges_ctx* ctx, float* ms, int32_t n);
+
+/* ---------------------------------------------------------------------------------------
  * Autotuning.
  * bridges_autotune: times candidate plans on the given device-resident input (M in
  * {1,2,4,8,16,32}, fan-in 2 or M, warm-up 0.6/1.2/2.0 x V ln V edges, block 1024 or 512; `reps`

@@ -42,6 +42,8 @@ def _load():
             f = getattr(lib, name)
             f.restype = ctypes.c_int64
             f.argtypes = [_I32P, _I32P, ctypes.c_int64, ctypes.c_int32, _I32P]
+        lib.oracle_is_articulation.restype = ctypes.c_int32
+        lib.oracle_is_articulation.argtypes = [_I32P, _I32P, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32]
         lib.oracle_block_certificate.restype = ctypes.c_int64
         lib.oracle_block_certificate.argtypes = [_I32P, _I32P, ctypes.c_int64, ctypes.c_int32, _I32P, _I32P, _I32P,
                                                  _I32P]
@@ -150,6 +152,12 @@ def articulation_points(u, v, V: int) -> np.ndarray:
 def brute_articulation(u, v, V: int) -> np.ndarray:
     """The definition: vertices whose deletion increases the number of components."""
     return _vertex_call("oracle_brute_articulation", u, v, V)
+
+
+def is_articulation(u, v, V: int, x: int) -> bool:
+    """The definition for one vertex: does deleting x increase the number of components?"""
+    u, v = _edges(u, v)
+    return bool(_check(_load().oracle_is_articulation(u.ctypes.data, v.ctypes.data, u.shape[0], V, int(x))))
 
 
 def block_certificate(u, v, V: int):

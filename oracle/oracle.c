@@ -29,6 +29,7 @@
  *                           low/disc test (a root with >= 2 children; another vertex with a
  *                           child whose low >= its disc), iterative.
  *   oracle_brute_articulation   the definition: delete each vertex, count components.
+ *   oracle_is_articulation      the same definition for one vertex (sampled checks at full size).
  *   oracle_block_certificate    the articulation-point method of the CUDA path, sequential: the
  *                           blocks restricted to a spanning forest T as classes of fundamental
  *                           cycles, the edges that merge classes, and the cut vertices they give.
@@ -687,6 +688,23 @@ int64_t oracle_brute_articulation(const int32_t* u, const int32_t* v, int64_t E,
   free(ap);
   uf_free(&f);
   return n;
+}
+
+/* The definition for one vertex x: 1 if deleting x (and its edges) leaves more components than
+ * the graph has, not counting x itself; an isolated x (only self-loops) is never one. */
+int32_t oracle_is_articulation(const int32_t* u, const int32_t* v, int64_t E, int32_t V, int32_t x) {
+  if (E < 0 || V < 0 || x < 0 || x >= V) return -1;
+  if (check_ids(u, v, E, V)) return -1;
+  int isolated = 1;
+  for (int64_t e = 0; e < E && isolated; e++)
+    if ((u[e] == x || v[e] == x) && u[e] != v[e]) isolated = 0;
+  if (isolated) return 0;
+  uf_t f;
+  if (uf_init(&f, V)) return -2;
+  const int32_t base = count_components_without(u, v, E, V, -1, &f);
+  const int32_t without = count_components_without(u, v, E, V, x, &f);
+  uf_free(&f);
+  return without > base ? 1 : 0;
 }
 
 /* The block certificate of a spanning forest T (the GPU's articulation-point method, restated

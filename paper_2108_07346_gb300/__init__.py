@@ -94,6 +94,9 @@ _SIGS = {
     "bridges_inc_add": (_I64, [_P, _P, _P, _P, _I64, _P]),
     "bridges_inc_two_edge_components": (_I64, [_P, _P, _P]),
     "bridges_inc_certificate_size": (_I64, [_P]),
+    "bridges_articulation_points": (_I64, [_P, _P, _P, _P, _I64, _I32, _I32, _P, _P, _P]),
+    "bridges_articulation_workspace_bytes": (_I64, [_P, _I64, _I32, _I32]),
+    "bridges_ctx_ap_stage_ms": (_I32, [_P, ctypes.POINTER(ctypes.c_float), _I32]),
 }
 
 
@@ -293,6 +296,42 @@ class Context:
         n = _check(self._lib.bridges_two_edge_components(self._h, _stream(stream), _ptr(u), _ptr(v), u.numel(), V, M,
                                                          _ptr(labels), _ptr(out)), "bridges_two_edge_components")
         return n, labels[:V]
+
+    def articulation_points(self, u, v, V: int, M: int = 0, stream=None, with_bridges: bool = False,
+                            counts_device=None, out=None):
+        """bridges_articulation_points: the cut vertices (sorted int32 device tensor); with
+        with_bridges also the bridges as an (n, 2) tensor.  With counts_device (an int64 device
+        tensor of 2 elements) the call only enqueues work and returns the full-capacity output
+        buffers (counts appear in counts_device)."""
+        u, v = _dev_edges(u, v)
+        pts = out if out is not None else torch.empty(max(V, 1), dtype=torch.int32, device=u.device)
+        br = torch.empty(2 * max(V - 1, 1), dtype=torch.int32, device=u.device) if with_bridges else None
+        if counts_device is not None:
+            _check(self._lib.bridges_articulation_points(self._h, _stream(stream), _ptr(u), _ptr(v), u.numel(), V, M,
+                                                         _ptr(pts), _ptr(br), _ptr(counts_device)),
+                   "bridges_articulation_points")
+            return (pts, br) if with_bridges else pts
+        cnt = torch.zeros(2, dtype=torch.int64, device=u.device) if with_bridges else None
+        n = _check(self._lib.bridges_articulation_points(self._h, _stream(stream), _ptr(u), _ptr(v), u.numel(), V, M,
+                                                         _ptr(pts), _ptr(br), _ptr(cnt)),
+                   "bridges_articulation_points")
+        if not with_bridges:
+            return pts[:n]
+        (stream or torch.cuda.current_stream(u.device)).synchronize()
+        na, nb = (int(x) for x in cnt.cpu())
+        _check(na, "bridges_articulation_points")
+        _check(nb, "bridges_articulation_points")
+        return pts[:na], br[: 2 * nb].view(nb, 2)
+
+    def articulation_workspace_bytes(self, E: int, V: int, M: int = 0) -> int:
+        return int(self._lib.bridges_articulation_workspace_bytes(self._h, E, V, M))
+
+    def ap_stage_ms(self):
+        """Stage times (ms) of the last profiled articulation-point call's block pass."""
+        buf = (ctypes.c_float * 5)()
+        k = self._lib.bridges_ctx_ap_stage_ms(self._h, buf, 5)
+        names = ["warmup", "snapshot", "stream", "mark", "total"]
+        return {names[i]: float(buf[i]) for i in range(max(k, 0))}
 
     def set_batch_split(self, split_edges: int):
         _check(self._lib.bridges_ctx_set_batch_split(self._h, int(split_edges)), "bridges_ctx_set_batch_split")

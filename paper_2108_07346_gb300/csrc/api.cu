@@ -120,6 +120,8 @@ int init_ctx(bridges_ctx* c, int device, const bridges_opts* opts) {
     for (auto& set : c->ev)
       for (auto& e : set)
         if (cudaEventCreate(&e) != cudaSuccess) return -1;
+    for (auto& e : c->ap_ev)
+      if (cudaEventCreate(&e) != cudaSuccess) return -1;
     c->events = true;
   }
   return 0;
@@ -214,9 +216,11 @@ void bridges_ctx_destroy(bridges_ctx* c) {
   if (c->bws) cudaFree(c->bws);
   if (c->bstage) cudaFreeHost(c->bstage);
   if (c->b_done_ev) cudaEventDestroy(c->b_done_ev);
-  if (c->events)
+  if (c->events) {
     for (auto& set : c->ev)
       for (auto& e : set) cudaEventDestroy(e);
+    for (auto& e : c->ap_ev) cudaEventDestroy(e);
+  }
   cudaGetLastError();
   delete c;
 }
@@ -802,6 +806,74 @@ extern "C" int64_t bridges_two_edge_components(bridges_ctx* c, struct CUstream_s
       cudaStreamSynchronize(s) != cudaSuccess)
     return cuda_fail(cudaGetLastError());
   return c->h_pinned[0];
+}
+
+// ---------------------------------------------------------------------------------------------
+// Articulation points: the bridge path, then the block pass over the same edges.
+extern "C" int64_t bridges_articulation_points(bridges_ctx* c, struct CUstream_st* stream, const int32_t* u,
+                                               const int32_t* v, int64_t E, int32_t V, int32_t M,
+                                               int32_t* out_points, int32_t* out_bridges,
+                                               int64_t* out_counts_device) {
+  int64_t rc = check_args(c, u, v, E, V, out_points);
+  if (rc) return rc;
+  if (V > (1 << 30)) return BRIDGES_EINVAL;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  if (cudaSetDevice(c->device) != cudaSuccess) return cuda_fail(cudaGetLastError());
+  int32_t dummy_out[1];
+  if (!out_points) out_points = dummy_out;  // V <= 1: nothing is written
+  const CertPlan p0 = plan_for(c, E, V, M);
+  const size_t ap_at = align_up(total_bytes(p0), 256);
+  rc = ensure_ws(c, ap_at + ap_bytes(V), s);
+  if (rc) return rc;
+  Carved k{};
+  CertPlan p{};
+  rc = run_path(c, s, u, v, E, V, M, out_bridges, &k, &p);
+  if (rc) return rc;
+  Launch L{s, &c->launches, c->num_sms, c->smem_optin};
+  if (!out_bridges) {
+    // the rooted forest is needed either way; the bridges go to dscan, free by the time it sorts
+    final_stage(L, k.fin, V, k.cert.f1u, k.cert.f1v, k.cert.cnt + 0, V, k.cert.f2u, k.cert.f2v, k.cert.cnt + 1, V,
+                k.cert.P1, k.fin.dscan);
+  }
+  ApBufs b = carve_ap(static_cast<char*>(c->ws) + ap_at, V);
+  // the block pass streams the whole list as one partition
+  const CertPlan q = plan_for(c, E, V, 1);
+  cudaEvent_t* ev = c->events ? c->ap_ev : nullptr;
+  if (ev) cudaEventRecord(ev[0], s);
+  articulation_stage(L, q, k.fin, b, u, v, k.cert.f2u, k.cert.f2v, k.cert.cnt + 1, out_points, b.count,
+                     ev ? ev + 1 : nullptr);
+  if (ev) {
+    cudaEventRecord(ev[4], s);
+    c->ap_profiled = true;
+  }
+  if (cudaGetLastError() != cudaSuccess) return BRIDGES_ECUDA;
+  if (out_counts_device) {
+    if (cudaMemcpyAsync(out_counts_device, b.count, sizeof(int64_t), cudaMemcpyDeviceToDevice, s) != cudaSuccess ||
+        cudaMemcpyAsync(out_counts_device + 1, k.fin.count, sizeof(int64_t), cudaMemcpyDeviceToDevice, s) !=
+            cudaSuccess)
+      return cuda_fail(cudaGetLastError());
+    return BRIDGES_OK;
+  }
+  if (cudaMemcpyAsync(c->h_pinned, b.count, sizeof(int64_t), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      cudaStreamSynchronize(s) != cudaSuccess)
+    return cuda_fail(cudaGetLastError());
+  return c->h_pinned[0];
+}
+
+extern "C" int64_t bridges_articulation_workspace_bytes(const bridges_ctx* c, int64_t E, int32_t V, int32_t M) {
+  if (!c || E < 0 || V < 0) return 0;
+  return (int64_t)(align_up(total_bytes(plan_for(c, E, V, M)), 256) + ap_bytes(V));
+}
+
+extern "C" int32_t bridges_ctx_ap_stage_ms(const bridges_ctx* c, float* ms, int32_t n) {
+  if (!c || !ms || n <= 0 || !c->ap_profiled) return 0;
+  if (cudaEventSynchronize(c->ap_ev[4]) != cudaSuccess) return cuda_fail(cudaGetLastError());
+  float t[5];
+  for (int i = 0; i < 4; i++) cudaEventElapsedTime(&t[i], c->ap_ev[i], c->ap_ev[i + 1]);
+  cudaEventElapsedTime(&t[4], c->ap_ev[0], c->ap_ev[4]);
+  const int32_t k = std::min(n, 5);
+  for (int i = 0; i < k; i++) ms[i] = t[i];
+  return k;
 }
 
 struct bridges_inc {

@@ -1,0 +1,435 @@
+// blocks.cu -- articulation points ("failure points", abstract of the paper) on the GPU.
+//
+// Bridges survive any pair of spanning forests (Alg. 2), cut vertices do not: an arbitrary
+// F u F' can split a biconnected graph at a vertex.  This path therefore takes the spanning
+// forest T of the bridge path (the F of the final certificate, rooted and numbered in preorder
+// by the final stage) and streams the whole edge list a second time against T:
+//
+//   * A tree edge (x, parent x) is named by the preorder number of x.  Every non-tree edge
+//     (a, b) closes a fundamental cycle with T, and all tree edges of one cycle lie in one block
+//     (biconnected component).  The blocks restricted to T are exactly the classes of the
+//     transitive closure of "lie on a common fundamental cycle", so merging, edge by edge, the
+//     classes that each cycle touches ends with one class per block (Tarjan & Vishkin 1985 reach
+//     the same classes through their auxiliary graph).
+//   * A class is always a connected subtree of T (merges only join classes that share a
+//     vertex), so it has one topmost vertex, its head, and every tree path from one of its
+//     vertices up to the head stays inside it.  With the classes kept in a union-find over
+//     preorder numbers whose root is the minimum element, the root is the class's first edge in
+//     preorder, a child of the head: head = parent of the root.  A cycle is walked from each end
+//     by jumping from class to head until the walk reaches an ancestor of the other end; the
+//     classes met are joined in walk order (each shares a vertex with the previous one).
+//   * A vertex is an articulation point iff its tree edges fall into at least two classes
+//     (each block through a vertex holds one of its tree edges).
+//
+// An edge whose two ends lie in one class is redundant: its cycle is inside the class.  After a
+// warm-up (the certificate's F' edges, then a prefix of the edge list) nearly every edge is, so
+// the stream reuses the forest pass's machinery: a 16-bit label per vertex in shared memory (the
+// largest class containing the vertex), two label reads per edge, and the cycle walk only for
+// the misses.  Classes only grow, so a stale label is still sound.
+#include <algorithm>
+#include <cmath>
+
+#include "common.cuh"
+#include "stream.cuh"
+
+namespace bridges {
+
+namespace {
+
+constexpr int kUnroll = 4;
+
+struct ApArgs {
+  const int32_t* pre;   // [V] vertex -> preorder number (final stage)
+  int32_t* Q;           // [V] class union-find over preorder numbers
+  const int32_t* PP;    // [V] preorder number of the parent (-1: tree root)
+  const int32_t* LAST;  // [V] last preorder number of the subtree
+  int32_t V;
+  int32_t* status;
+  int32_t* hooks;  // successful class merges
+};
+
+// Merges the classes of the tree edges on the fundamental cycle of the edge between the
+// vertices with preorder numbers A and B; returns the number of successful hooks.
+__device__ int32_t cycle_merge(const ApArgs& A, int32_t a, int32_t b) {
+  if (a == b) return 0;
+  int32_t hooks = 0;
+  int32_t last[2];
+  for (int side = 0; side < 2; side++) {
+    int32_t x = side ? b : a;
+    const int32_t y = side ? a : b;
+    int32_t prev = -1;
+    // climb while x is not an ancestor of y: then x's tree edge is on the cycle
+    for (int32_t it = 0; !(x <= y && y <= __ldg(A.LAST + x)); it++) {
+      if (it >= A.V) {  // cannot happen on a forest: each step moves strictly up
+        set_status(A.status, BRIDGES_EINTERNAL_CODE);
+        return hooks;
+      }
+      if (prev >= 0 && uf_link(A.Q, prev, x)) hooks++;  // prev's class has head x: they touch
+      prev = x;
+      const int32_t h = __ldg(A.PP + uf_find(A.Q, x));
+      if (h < 0) {  // only if the ends lie in different trees of T
+        set_status(A.status, BRIDGES_EINTERNAL_CODE);
+        return hooks;
+      }
+      x = h;
+    }
+    last[side] = prev;
+  }
+  // both last classes hold the lowest common ancestor
+  if (last[0] >= 0 && last[1] >= 0 && uf_link(A.Q, last[0], last[1])) hooks++;
+  return hooks;
+}
+
+__device__ __forceinline__ bool checked_edge(const ApArgs& A, int32_t a, int32_t b) {
+  if ((uint32_t)a >= (uint32_t)A.V || (uint32_t)b >= (uint32_t)A.V) {
+    set_status(A.status, BRIDGES_ERANGE_CODE);
+    return false;
+  }
+  return a != b;
+}
+
+__device__ __forceinline__ void offer_edge(const ApArgs& A, int32_t a, int32_t b) {
+  if (!checked_edge(A, a, b)) return;
+  const int32_t h = cycle_merge(A, __ldg(A.pre + a), __ldg(A.pre + b));
+  if (h) atomicAdd(A.hooks, h);
+}
+
+__device__ __noinline__ void cycle_misses(const ApArgs& A, uint32_t m, const int32_t* __restrict__ u,
+                                          const int32_t* __restrict__ v, int32_t base) {
+  while (m) {
+    const int bit = __ffs(m) - 1;
+    m &= m - 1;
+    const int64_t e = miss_edge(bit, base);
+    offer_edge(A, u[e], v[e]);
+  }
+}
+
+// The block pass's slow path (see stream_range).
+struct CycleSink {
+  const ApArgs& A;
+  __device__ __forceinline__ void slot(bool need, int32_t a, int32_t b) const {
+    if (need) offer_edge(A, a, b);
+  }
+  __device__ __forceinline__ void misses(uint32_t m, const int32_t* ub, const int32_t* vb, int32_t base) const {
+    cycle_misses(A, m, ub, vb, base);
+  }
+};
+
+__device__ __forceinline__ int64_t gtid() { return (int64_t)blockIdx.x * blockDim.x + threadIdx.x; }
+__device__ __forceinline__ int64_t gstride() { return (int64_t)gridDim.x * blockDim.x; }
+
+// Preorder-indexed copies of T (parent, subtree end, vertex) and singleton classes.
+__global__ void ap_init_kernel(FinalBufs f, ApBufs b, int32_t V) {
+  if (*f.status) return;
+  for (int64_t x = gtid(); x < V; x += gstride()) {
+    const int32_t i = f.pre[x], p = f.par[x], s = f.sz[x];
+    b.flag[x] = 0;
+    if ((uint32_t)i >= (uint32_t)V || p >= V || (p >= 0 && (uint32_t)f.pre[p] >= (uint32_t)V) || s < 1 ||
+        (int64_t)i + s > V) {
+      set_status(f.status, BRIDGES_EINTERNAL_CODE);
+      continue;
+    }
+    b.vtx[i] = (int32_t)x;
+    b.PP[i] = p >= 0 ? f.pre[p] : -1;
+    b.LAST[i] = i + s - 1;
+    b.Q[i] = i;
+  }
+  if (gtid() == 0) *b.hooks = 0;
+}
+
+// Offers a device-counted edge list (the certificate's F' edges) to the classes.
+__global__ void ap_seed_kernel(ApArgs A, const int32_t* xu, const int32_t* xv, const int32_t* d_n, int32_t cap) {
+  if (*A.status) return;
+  const int32_t n = min(*d_n, cap);
+  for (int64_t e = gtid(); e < n; e += gstride()) offer_edge(A, xu[e], xv[e]);
+}
+
+struct PassArgs {
+  ApArgs A;
+  const int32_t* u;
+  const int32_t* v;
+  int64_t s;  // edge range [s, t) shared by the grid
+  int64_t t;
+  const uint16_t* lab;
+  int64_t Vpad;
+};
+
+template <bool CACHE, bool VEC>
+__global__ void __launch_bounds__(1024, 1) ap_pass_kernel(PassArgs P) {
+  extern __shared__ __align__(16) uint16_t slab[];
+  __shared__ int32_t stop;
+  if (threadIdx.x == 0) stop = *P.A.status;
+  __syncthreads();
+  if (stop) return;  // block-uniform: the stream below contains barriers
+  const int64_t n = P.t - P.s;
+  const int64_t s = P.s + n * blockIdx.x / gridDim.x, t = P.s + n * (blockIdx.x + 1) / gridDim.x;
+  if (CACHE) load_labels(slab, P.lab, P.Vpad);
+  const CycleSink S{P.A};
+  stream_range<CACHE, VEC, kUnroll>(S, P.u, P.v, s, t, P.A.V, slab);
+}
+
+// ---- label snapshot: each vertex takes the largest class it belongs to ----
+// 1) flatten the classes; reset sizes, proposals and label ids
+__global__ void ap_flatten_kernel(ApBufs b, int32_t V, const int32_t* status) {
+  if (*status) return;  // T is not valid: its arrays may be partly unset
+  for (int64_t i = gtid(); i < V; i += gstride()) {
+    int32_t r = (int32_t)i, p = __ldca(b.Q + i);
+    while (p != r) {
+      r = p;
+      p = __ldca(b.Q + r);
+    }
+    b.Q[i] = r;
+    b.csize[i] = 0;
+    b.tmp[i] = -1;
+    b.best[i] = 0;
+  }
+  if (gtid() == 0) *b.nlab = 0;
+}
+
+// 2) class sizes (tree edges per class); lanes with the same root add once per warp
+__global__ void ap_count_kernel(ApBufs b, int32_t V, const int32_t* status) {
+  if (*status) return;  // T is not valid: its arrays may be partly unset
+  const int lane = threadIdx.x & 31;
+  for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < V; base += gstride()) {
+    const int64_t i = base + threadIdx.x;
+    const bool edge = i < V && b.PP[i] >= 0;
+    const int32_t r = edge ? b.Q[i] : -1 - lane;
+    const unsigned peers = __match_any_sync(kFull, r);
+    if (edge && lane == __ffs(peers) - 1) atomicAdd(b.csize + r, __popc(peers));
+  }
+}
+
+// 3) every class with >= 2 edges proposes itself to the two ends of each of its edges
+__global__ void ap_propose_kernel(ApBufs b, int32_t V, const int32_t* status) {
+  if (*status) return;  // T is not valid: its arrays may be partly unset
+  const int lane = threadIdx.x & 31;
+  for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < V; base += gstride()) {
+    const int64_t i = base + threadIdx.x;
+    const int32_t p = i < V ? b.PP[i] : -1;
+    uint64_t key = 0;
+    if (p >= 0) {
+      const int32_t r = b.Q[i];
+      const int32_t c = b.csize[r];
+      if (c >= 2) key = ((uint64_t)c << 32) | (uint32_t)r;
+    }
+    if (key) atomicMax(reinterpret_cast<unsigned long long*>(b.best + i), key);
+    // siblings share a parent: one proposal per distinct (parent, key) in the warp
+    const unsigned peers = __match_any_sync(kFull, p) & __match_any_sync(kFull, key);
+    if (key && lane == __ffs(peers) - 1) atomicMax(reinterpret_cast<unsigned long long*>(b.best + p), key);
+  }
+}
+
+// 4) 16-bit labels by vertex id; classes get ids on first sight (kNoLabel past 65,534)
+__global__ void ap_label_kernel(ApBufs b, const int32_t* pre, int32_t V, const int32_t* status) {
+  if (*status) return;  // T is not valid: its arrays may be partly unset
+  const int lane = threadIdx.x & 31;
+  for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < b.Vpad; base += gstride()) {
+    const int64_t x = base + threadIdx.x;
+    const uint64_t key = x < V ? b.best[pre[x]] : 0;
+    const int32_t r = key ? (int32_t)(uint32_t)key : -1 - lane;
+    const unsigned peers = __match_any_sync(kFull, r);
+    const int leader = __ffs(peers) - 1;
+    int32_t id = -1;
+    if (key && lane == leader) {
+      int32_t* slot = b.tmp + r;
+      id = ld_relaxed(slot);
+      if (id < 0) {
+        const int32_t fresh = atomicAdd(b.nlab, 1);
+        const int32_t old = atomicCAS(slot, -1, fresh);
+        id = old < 0 ? fresh : old;
+      }
+    }
+    id = __shfl_sync(kFull, id, leader);
+    if (x < b.Vpad) b.lab[x] = (key && id >= 0 && id < (int32_t)kNoLabel) ? (uint16_t)id : kNoLabel;
+  }
+}
+
+// ---- articulation points from the final classes ----
+__global__ void ap_mark_kernel(ApBufs b, int32_t V, const int32_t* status) {
+  if (*status) return;
+  for (int64_t i = gtid(); i < V; i += gstride()) {
+    const int32_t p = b.PP[i];
+    if (p < 0) continue;
+    const int32_t gi = uf_find_static(b.Q, (int32_t)i);
+    // a non-root parent compares with its own tree edge, a root with its first child's edge
+    const int32_t gp = uf_find_static(b.Q, b.PP[p] >= 0 ? p : p + 1);
+    if (gi != gp) b.flag[b.vtx[p]] = 1;
+  }
+}
+
+constexpr int kCompactThreads = 1024;
+constexpr int kCompactItems = 4;  // flags per thread and tile
+
+// Ordered compaction of the flagged vertices: per-tile counts, one-block scan, scatter.
+__global__ void ap_tile_count_kernel(ApBufs b, int32_t V, int64_t ntiles) {
+  __shared__ int32_t red[kCompactThreads / 32];
+  const int64_t tile_sz = (int64_t)kCompactThreads * kCompactItems;
+  for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    int32_t c = 0;
+    for (int k = 0; k < kCompactItems; k++) {
+      const int64_t x = tile * tile_sz + k * kCompactThreads + threadIdx.x;
+      c += x < V ? b.flag[x] : 0;
+    }
+    for (int o = 16; o > 0; o >>= 1) c += __shfl_down_sync(kFull, c, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = c;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      int32_t t = 0;
+      for (int w = 0; w < kCompactThreads / 32; w++) t += red[w];
+      b.tiles[tile] = t;
+    }
+    __syncthreads();
+  }
+}
+
+// One block: exclusive scan of the tile counts in place; the total (or the status) to *count.
+__global__ void ap_tile_scan_kernel(ApBufs b, int64_t ntiles, const int32_t* status, int64_t* count) {
+  __shared__ int32_t wsum[kCompactThreads / 32];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  int32_t carry = 0;
+  for (int64_t t0 = 0; t0 < ntiles; t0 += blockDim.x) {
+    const int64_t t = t0 + threadIdx.x;
+    const int32_t c = t < ntiles ? b.tiles[t] : 0;
+    int32_t incl = c;
+    for (int o = 1; o < 32; o <<= 1) {
+      const int32_t y = __shfl_up_sync(kFull, incl, o);
+      if (lane >= o) incl += y;
+    }
+    if (lane == 31) wsum[w] = incl;
+    __syncthreads();
+    int32_t before = 0, total = 0;
+    for (int q = 0; q < (int)(blockDim.x >> 5); q++) {
+      if (q < w) before += wsum[q];
+      total += wsum[q];
+    }
+    if (t < ntiles) b.tiles[t] = carry + before + incl - c;
+    carry += total;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *count = *status ? (int64_t)*status : (int64_t)carry;
+}
+
+__global__ void ap_scatter_kernel(ApBufs b, int32_t V, int64_t ntiles, const int32_t* status, int32_t* out) {
+  __shared__ int32_t wsum[kCompactThreads / 32];
+  if (*status) return;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int64_t tile_sz = (int64_t)kCompactThreads * kCompactItems;
+  for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    int32_t at = b.tiles[tile];
+    for (int k = 0; k < kCompactItems; k++) {
+      const int64_t x = tile * tile_sz + k * kCompactThreads + threadIdx.x;
+      const bool f = x < V && b.flag[x];
+      const unsigned m = __ballot_sync(kFull, f);
+      if (lane == 0) wsum[w] = __popc(m);
+      __syncthreads();
+      int32_t before = 0, total = 0;
+      for (int q = 0; q < kCompactThreads / 32; q++) {
+        if (q < w) before += wsum[q];
+        total += wsum[q];
+      }
+      if (f) out[at + before + __popc(m & lanemask_lt())] = (int32_t)x;
+      at += total;
+      __syncthreads();
+    }
+  }
+}
+
+int grid_of(const Launch& L, int64_t work, int block) {
+  const int64_t g = ceil_div(std::max<int64_t>(work, 1), block);
+  return (int)std::min<int64_t>(g, (int64_t)L.num_sms * 16);
+}
+
+template <bool CACHE, bool VEC>
+void launch_pass(const Launch& L, const PassArgs& a, int grid, int block, size_t smem) {
+  auto k = ap_pass_kernel<CACHE, VEC>;
+  if (smem > 48 * 1024) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  k<<<grid, block, smem, L.stream>>>(a);
+  *L.launches += 1;
+}
+
+}  // namespace
+
+size_t ap_bytes(int32_t V) {
+  const size_t Vs = (size_t)std::max(V, 1);
+  const size_t Vpad = align_up(Vs + 1, 8);
+  const size_t ntiles = ceil_div((int64_t)Vs, (int64_t)kCompactThreads * kCompactItems);
+  size_t s = 3 * 256;                                    // hooks, nlab, count
+  s += 7 * align_up(sizeof(int32_t) * Vs, 256);          // Q PP LAST vtx csize tmp flag
+  s += align_up(sizeof(uint64_t) * Vs, 256);             // best
+  s += align_up(sizeof(int32_t) * (ntiles + 1), 256);    // tiles
+  s += align_up(sizeof(uint16_t) * Vpad, 256);           // lab
+  return s;
+}
+
+ApBufs carve_ap(void* base, int32_t V) {
+  ApBufs b{};
+  char* c = static_cast<char*>(base);
+  const size_t Vs = (size_t)std::max(V, 1);
+  const size_t ntiles = ceil_div((int64_t)Vs, (int64_t)kCompactThreads * kCompactItems);
+  b.hooks = reinterpret_cast<int32_t*>(c);
+  b.nlab = reinterpret_cast<int32_t*>(c + 256);
+  b.count = reinterpret_cast<int64_t*>(c + 512);
+  c += 3 * 256;
+  int32_t** arrs[7] = {&b.Q, &b.PP, &b.LAST, &b.vtx, &b.csize, &b.tmp, &b.flag};
+  for (auto a : arrs) {
+    *a = reinterpret_cast<int32_t*>(c);
+    c += align_up(sizeof(int32_t) * Vs, 256);
+  }
+  b.best = reinterpret_cast<uint64_t*>(c);
+  c += align_up(sizeof(uint64_t) * Vs, 256);
+  b.tiles = reinterpret_cast<int32_t*>(c);
+  c += align_up(sizeof(int32_t) * (ntiles + 1), 256);
+  b.lab = reinterpret_cast<uint16_t*>(c);
+  b.Vpad = (int64_t)align_up(Vs + 1, 8);
+  return b;
+}
+
+void articulation_stage(const Launch& L, const CertPlan& p, const FinalBufs& f, const ApBufs& b, const int32_t* u,
+                        const int32_t* v, const int32_t* xu, const int32_t* xv, const int32_t* d_nx, int32_t* out,
+                        int64_t* count_dev, cudaEvent_t* ev) {
+  const int32_t V = p.V;
+  const int bs = 256;
+  const int g = grid_of(L, V, bs);
+  ap_init_kernel<<<g, bs, 0, L.stream>>>(f, b, V);
+  ApArgs A{f.pre, b.Q, b.PP, b.LAST, V, f.status, b.hooks};
+  ap_seed_kernel<<<grid_of(L, V, bs), bs, 0, L.stream>>>(A, xu, xv, d_nx, V);
+  *L.launches += 2;
+  const bool vec = ((reinterpret_cast<uintptr_t>(u) | reinterpret_cast<uintptr_t>(v)) & 15) == 0;
+  const int grid = (int)std::max<int64_t>(1, (int64_t)p.G * p.M);
+  PassArgs a{A, u, v, 0, p.cache ? std::min(p.warm, p.E) : p.E, b.lab, b.Vpad};
+  if (p.E > 0) {
+    if (vec)
+      launch_pass<false, true>(L, a, grid, p.block, 0);
+    else
+      launch_pass<false, false>(L, a, grid, p.block, 0);
+  }
+  if (ev) cudaEventRecord(ev[0], L.stream);
+  if (p.cache && p.E > a.t) {
+    ap_flatten_kernel<<<g, bs, 0, L.stream>>>(b, V, f.status);
+    ap_count_kernel<<<g, bs, 0, L.stream>>>(b, V, f.status);
+    ap_propose_kernel<<<g, bs, 0, L.stream>>>(b, V, f.status);
+    ap_label_kernel<<<grid_of(L, b.Vpad, bs), bs, 0, L.stream>>>(b, f.pre, V, f.status);
+    *L.launches += 4;
+    if (ev) cudaEventRecord(ev[1], L.stream);
+    a.s = a.t;
+    a.t = p.E;
+    const size_t smem = (size_t)b.Vpad * 2;
+    if (vec)
+      launch_pass<true, true>(L, a, grid, p.block, smem);
+    else
+      launch_pass<true, false>(L, a, grid, p.block, smem);
+  } else if (ev) {
+    cudaEventRecord(ev[1], L.stream);
+  }
+  if (ev) cudaEventRecord(ev[2], L.stream);
+  const int64_t ntiles = ceil_div(std::max(V, 1), (int64_t)kCompactThreads * kCompactItems);
+  ap_mark_kernel<<<g, bs, 0, L.stream>>>(b, V, f.status);
+  ap_tile_count_kernel<<<grid_of(L, ntiles * kCompactThreads, kCompactThreads), kCompactThreads, 0, L.stream>>>(
+      b, V, ntiles);
+  ap_tile_scan_kernel<<<1, kCompactThreads, 0, L.stream>>>(b, ntiles, f.status, count_dev);
+  ap_scatter_kernel<<<grid_of(L, ntiles * kCompactThreads, kCompactThreads), kCompactThreads, 0, L.stream>>>(
+      b, V, ntiles, f.status, out);
+  *L.launches += 4;
+}
+
+}  // namespace bridges

@@ -29,6 +29,7 @@
 #include <cmath>
 
 #include "common.cuh"
+#include "stream.cuh"
 
 namespace bridges {
 
@@ -83,46 +84,25 @@ __device__ __forceinline__ bool checked(int32_t a, int32_t b, int32_t V, int32_t
   return a != b;
 }
 
-// Scalar slot: every lane of the warp calls it (valid may be false).
+// Scalar slot for the merge and offer kernels: every lane of the warp calls it (valid may be
+// false).
 __device__ __forceinline__ void scalar_slot(const Job& J, bool valid, int32_t a, int32_t b, int32_t V,
                                             const uint16_t* slab, bool cache, int32_t* status) {
-  bool need = valid;
-  if (need && cache) {
-    const uint16_t la = slab[min((uint32_t)a, (uint32_t)V)], lb = slab[min((uint32_t)b, (uint32_t)V)];
-    need = la == kNoLabel || la != lb;
-  }
-  settle(J, need && checked(a, b, V, status), a, b, V, status);
+  settle(J, valid && (!cache || miss_bit(a, b, V, slab)) && checked(a, b, V, status), a, b, V, status);
 }
 
-// Fast-path test of one edge against the label snapshot.  Ids are clamped to V, whose label is
-// kNoLabel, so out-of-range ids (and unlabelled vertices) fall through to the checked path.
-__device__ __forceinline__ uint32_t miss_bit(int32_t a, int32_t b, int32_t V, const uint16_t* slab) {
-  const uint16_t la = slab[min((uint32_t)a, (uint32_t)V)];
-  const uint16_t lb = slab[min((uint32_t)b, (uint32_t)V)];
-  return (la == kNoLabel) | (la != lb);
-}
-
-// Copies job j's label snapshot into shared memory.
-__device__ __forceinline__ void load_labels(uint16_t* slab, const uint16_t* glab, int64_t Vpad) {
-  const int4* src = reinterpret_cast<const int4*>(glab);
-  int4* dst = reinterpret_cast<int4*>(slab);
-  for (int64_t i = threadIdx.x; i < Vpad / 8; i += blockDim.x) dst[i] = src[i];
-  __syncthreads();
-}
-
-// The edges of this thread's current tile whose bit is set in `m` (bit 4k+c: element
-// 4*(base + k*nt + tid) + c of the range) go through the union-finds.  Kept out of line so the
-// streaming loop stays small; the edges are re-read (they are still in L1/L2).
+// The edges of this thread's current tile whose bit is set in `m` go through the union-finds.
+// Kept out of line so the streaming loop stays small; the edges are re-read (they are still in
+// L1/L2).
 __device__ __noinline__ void offer_misses(const Job& J, uint32_t m, const int32_t* __restrict__ u,
                                           const int32_t* __restrict__ v, int32_t base, int32_t V, int32_t* status) {
-  const int tid = threadIdx.x, nt = blockDim.x;
   while (__any_sync(kFull, m != 0)) {
     int32_t a = 0, b = 0;
     bool go = false;
     if (m) {
       const int bit = __ffs(m) - 1;
       m &= m - 1;
-      const int64_t e = 4 * ((int64_t)base + (int64_t)(bit >> 2) * nt + tid) + (bit & 3);
+      const int64_t e = miss_edge(bit, base);
       a = u[e];
       b = v[e];
       go = checked(a, b, V, status);
@@ -133,69 +113,18 @@ __device__ __noinline__ void offer_misses(const Job& J, uint32_t m, const int32_
   }
 }
 
-// Streams edges [s, t) of (u, v): 16-byte loads when both arrays are 16-byte aligned, U int4
-// units (4U edges) in flight per thread.  With the snapshot, each edge costs two shared-memory
-// label reads; a per-thread bit mask collects the misses and one warp vote per tile decides
-// whether any lane must take the union-find path.  Loop bounds are block-uniform so every lane
-// reaches the votes.
-template <bool CACHE, bool VEC, int U>
-__device__ __forceinline__ void stream_range(const Job& J, const int32_t* __restrict__ u,
-                                             const int32_t* __restrict__ v, int64_t s, int64_t t, int32_t V,
-                                             const uint16_t* slab, int32_t* status) {
-  static_assert(4 * U <= 32, "the miss mask holds 32 edges");
-  const int tid = threadIdx.x, nt = blockDim.x;
-  int64_t s_al = s, t_al = s;
-  if (VEC) {
-    s_al = min((s + 3) & ~int64_t(3), t);
-    t_al = max(s_al, t & ~int64_t(3));
+// The forest pass's slow path (see stream_range): Alg. 2's two union-finds.
+struct ForestSink {
+  const Job& J;
+  int32_t V;
+  int32_t* status;
+  __device__ __forceinline__ void slot(bool need, int32_t a, int32_t b) const {
+    settle(J, need && checked(a, b, V, status), a, b, V, status);
   }
-  for (int64_t i0 = s; i0 < s_al; i0 += nt) {  // scalar head
-    const int64_t i = i0 + tid;
-    const bool valid = i < s_al;
-    scalar_slot(J, valid, valid ? ld_stream1(u + i) : 0, valid ? ld_stream1(v + i) : 0, V, slab, CACHE, status);
+  __device__ __forceinline__ void misses(uint32_t m, const int32_t* ub, const int32_t* vb, int32_t base) const {
+    offer_misses(J, m, ub, vb, base, V, status);
   }
-  if (VEC) {
-    const int32_t* ub = u + s_al;
-    const int32_t* vb = v + s_al;
-    const int4* u4 = reinterpret_cast<const int4*>(ub);
-    const int4* v4 = reinterpret_cast<const int4*>(vb);
-    const int32_t nunits = (int32_t)((t_al - s_al) >> 2);
-    for (int32_t base = 0; base < nunits; base += nt * U) {
-      const bool full = base + nt * U <= nunits;
-      int4 ua[U], va[U];
-#pragma unroll
-      for (int k = 0; k < U; k++) {
-        const int32_t idx = base + k * nt + tid;
-        if (full || idx < nunits) {
-          ua[k] = ld_stream4(u4 + idx);
-          va[k] = ld_stream4(v4 + idx);
-        } else {
-          ua[k] = make_int4(0, 0, 0, 0);
-          va[k] = make_int4(0, 0, 0, 0);
-        }
-      }
-      uint32_t m = 0;
-#pragma unroll
-      for (int k = 0; k < U; k++) {
-        const bool valid = full || base + k * nt + tid < nunits;
-        uint32_t mk;
-        if (CACHE) {
-          mk = miss_bit(ua[k].x, va[k].x, V, slab) | (miss_bit(ua[k].y, va[k].y, V, slab) << 1) |
-               (miss_bit(ua[k].z, va[k].z, V, slab) << 2) | (miss_bit(ua[k].w, va[k].w, V, slab) << 3);
-        } else {
-          mk = 0xfu;
-        }
-        m |= (valid ? mk : 0u) << (4 * k);
-      }
-      if (__any_sync(kFull, m != 0)) offer_misses(J, m, ub, vb, base, V, status);
-    }
-  }
-  for (int64_t i0 = t_al; i0 < t; i0 += nt) {  // scalar tail
-    const int64_t i = i0 + tid;
-    const bool valid = i < t;
-    scalar_slot(J, valid, valid ? ld_stream1(u + i) : 0, valid ? ld_stream1(v + i) : 0, V, slab, CACHE, status);
-  }
-}
+};
 
 constexpr int kUnroll = 4;  // int4 units of u (and of v) in flight per thread: 16 edges
 
@@ -224,8 +153,9 @@ __global__ void __launch_bounds__(1024, 1) leaf_kernel(LeafArgs A) {
   const int64_t n = z - a;
   const int64_t s = a + n * m / A.G, t = a + n * (m + 1) / A.G;
   if (CACHE) load_labels(slab, A.b.lab + j * A.b.Vpad, A.b.Vpad);
-  Job J = job_of(A.b, A.V, j);
-  stream_range<CACHE, VEC, kUnroll>(J, A.u, A.v, s, t, A.V, slab, A.b.status);
+  const Job J = job_of(A.b, A.V, j);
+  const ForestSink S{J, A.V, A.b.status};
+  stream_range<CACHE, VEC, kUnroll>(S, A.u, A.v, s, t, A.V, slab);
 }
 
 struct MergeArgs {

@@ -32,6 +32,9 @@ struct bridges_ctx {
   int64_t resolved = 0;      // calls whose times have been read back
   float stage_ms[kRing][6]{};
   int64_t last_cfg[5]{};
+  // profiling of the articulation-point stage: start, after warm-up, snapshot, stream, end
+  cudaEvent_t ap_ev[5]{};
+  bool ap_profiled = false;
   // batched path: device descriptors, pinned staging and a CUDA graph per capacity
   void* bws = nullptr;          // device: BatchArgs | ntasks | queue | tasks[cap] | done[gcap] | gerr[gcap] | slots
   size_t bws_bytes = 0;

@@ -91,6 +91,25 @@ struct FinalBufs {
   int32_t* part;    // per-block scan partials
 };
 
+// Device buffers of the articulation-point stage (blocks.cu), indexed by preorder number unless
+// noted.
+struct ApBufs {
+  int32_t* hooks;  // [1] successful class merges
+  int32_t* nlab;   // [1] labels handed out
+  int64_t* count;  // [1] articulation points found, or the status
+  int32_t* Q;      // class union-find over tree edges (edge (x, parent x) = preorder of x)
+  int32_t* PP;     // parent's preorder number, -1 for tree roots
+  int32_t* LAST;   // last preorder number of the subtree
+  int32_t* vtx;    // vertex of each preorder number
+  int32_t* csize;  // tree edges per class (snapshot)
+  int32_t* tmp;    // label id per class root (snapshot)
+  int32_t* flag;   // by vertex id: 1 if an articulation point
+  uint64_t* best;  // largest class containing each vertex: (size << 32 | root), 0 if none
+  int32_t* tiles;  // compaction tile counts, then offsets
+  uint16_t* lab;   // by vertex id: 16-bit class label (kNoLabel: none); Vpad entries
+  int64_t Vpad;
+};
+
 // ---- certify.cu ----
 void cert_init(const Launch& L, const CertPlan& p, const CertBufs& b);
 // Leaf certificates of the M partitions of (u, v) (Sec. 3 phase 0, Alg. 2 per partition).
@@ -122,6 +141,18 @@ void cert_offer(const Launch& L, const CertPlan& p, const CertBufs& b, const int
 void final_stage(const Launch& L, const FinalBufs& fb, int32_t V, const int32_t* tu, const int32_t* tv,
                  const int32_t* d_ntree, int64_t cap_tree, const int32_t* xu, const int32_t* xv,
                  const int32_t* d_nextra, int64_t cap_extra, const int32_t* P_tree, int32_t* out);
+
+// ---- blocks.cu ----
+size_t ap_bytes(int32_t V);
+ApBufs carve_ap(void* base, int32_t V);
+// Articulation points of (u, v) after the bridge path: f holds the final stage's rooted forest
+// T (pre, par, sz) and (xu, xv, *d_nx) the certificate's non-tree edges.  Streams the edge list
+// once more (warm-up of p.warm edges, label snapshot, the rest) with p's grid (M = 1 plan);
+// writes the sorted points to out and their number (or the status) to *count_dev.  ev: three
+// events recorded after the warm-up, the snapshot and the stream (or null).
+void articulation_stage(const Launch& L, const CertPlan& p, const FinalBufs& f, const ApBufs& b, const int32_t* u,
+                        const int32_t* v, const int32_t* xu, const int32_t* xv, const int32_t* d_nx, int32_t* out,
+                        int64_t* count_dev, cudaEvent_t* ev);
 
 inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
 inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }

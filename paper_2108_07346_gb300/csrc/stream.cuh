@@ -1,0 +1,105 @@
+// stream.cuh -- the streaming loop shared by the certificate's forest pass and the block pass
+// of the articulation-point path: edges are read once with 16-byte loads, tested against a
+// 16-bit label snapshot in shared memory, and only the misses reach a slow path in global
+// memory.  Nothing here is visible through the C ABI.
+#pragma once
+
+#include "common.cuh"
+
+namespace bridges {
+
+// Fast-path test of one edge against the label snapshot.  Ids are clamped to V, whose label is
+// kNoLabel, so out-of-range ids (and unlabelled vertices) fall through to the checked path.
+__device__ __forceinline__ uint32_t miss_bit(int32_t a, int32_t b, int32_t V, const uint16_t* slab) {
+  const uint16_t la = slab[min((uint32_t)a, (uint32_t)V)];
+  const uint16_t lb = slab[min((uint32_t)b, (uint32_t)V)];
+  return (la == kNoLabel) | (la != lb);
+}
+
+// Copies a label snapshot (Vpad entries, Vpad a multiple of 8) into shared memory.
+__device__ __forceinline__ void load_labels(uint16_t* slab, const uint16_t* glab, int64_t Vpad) {
+  const int4* src = reinterpret_cast<const int4*>(glab);
+  int4* dst = reinterpret_cast<int4*>(slab);
+  for (int64_t i = threadIdx.x; i < Vpad / 8; i += blockDim.x) dst[i] = src[i];
+  __syncthreads();
+}
+
+// Streams edges [s, t) of (u, v): 16-byte loads when both arrays are 16-byte aligned, U int4
+// units (4U edges) in flight per thread.  With the snapshot (CACHE), each edge costs two
+// shared-memory label reads; a per-thread bit mask collects the misses and one warp vote per
+// tile decides whether any lane must take the slow path.  Loop bounds are block-uniform so
+// every lane reaches the votes.
+//
+// The slow path is the Sink:
+//   S.slot(need, a, b)            every lane of the warp calls it; `need` marks a live edge that
+//                                 missed the snapshot (scalar head and tail);
+//   S.misses(m, ub, vb, base)     the edges of this thread's tile whose bit is set in m (bit
+//                                 4k+c: element 4*(base + k*nt + tid) + c of ub / vb); every
+//                                 lane of the warp calls it.
+template <bool CACHE, bool VEC, int U, class Sink>
+__device__ __forceinline__ void stream_range(const Sink& S, const int32_t* __restrict__ u,
+                                             const int32_t* __restrict__ v, int64_t s, int64_t t, int32_t V,
+                                             const uint16_t* slab) {
+  static_assert(4 * U <= 32, "the miss mask holds 32 edges");
+  const int tid = threadIdx.x, nt = blockDim.x;
+  int64_t s_al = s, t_al = s;
+  if (VEC) {
+    s_al = min((s + 3) & ~int64_t(3), t);
+    t_al = max(s_al, t & ~int64_t(3));
+  }
+  for (int64_t i0 = s; i0 < s_al; i0 += nt) {  // scalar head
+    const int64_t i = i0 + tid;
+    const bool valid = i < s_al;
+    const int32_t a = valid ? ld_stream1(u + i) : 0, b = valid ? ld_stream1(v + i) : 0;
+    S.slot(valid && (!CACHE || miss_bit(a, b, V, slab)), a, b);
+  }
+  if (VEC) {
+    const int32_t* ub = u + s_al;
+    const int32_t* vb = v + s_al;
+    const int4* u4 = reinterpret_cast<const int4*>(ub);
+    const int4* v4 = reinterpret_cast<const int4*>(vb);
+    const int32_t nunits = (int32_t)((t_al - s_al) >> 2);
+    for (int32_t base = 0; base < nunits; base += nt * U) {
+      const bool full = base + nt * U <= nunits;
+      int4 ua[U], va[U];
+#pragma unroll
+      for (int k = 0; k < U; k++) {
+        const int32_t idx = base + k * nt + tid;
+        if (full || idx < nunits) {
+          ua[k] = ld_stream4(u4 + idx);
+          va[k] = ld_stream4(v4 + idx);
+        } else {
+          ua[k] = make_int4(0, 0, 0, 0);
+          va[k] = make_int4(0, 0, 0, 0);
+        }
+      }
+      uint32_t m = 0;
+#pragma unroll
+      for (int k = 0; k < U; k++) {
+        const bool valid = full || base + k * nt + tid < nunits;
+        uint32_t mk;
+        if (CACHE) {
+          mk = miss_bit(ua[k].x, va[k].x, V, slab) | (miss_bit(ua[k].y, va[k].y, V, slab) << 1) |
+               (miss_bit(ua[k].z, va[k].z, V, slab) << 2) | (miss_bit(ua[k].w, va[k].w, V, slab) << 3);
+        } else {
+          mk = 0xfu;
+        }
+        m |= (valid ? mk : 0u) << (4 * k);
+      }
+      if (__any_sync(kFull, m != 0)) S.misses(m, ub, vb, base);
+    }
+  }
+  for (int64_t i0 = t_al; i0 < t; i0 += nt) {  // scalar tail
+    const int64_t i = i0 + tid;
+    const bool valid = i < t;
+    const int32_t a = valid ? ld_stream1(u + i) : 0, b = valid ? ld_stream1(v + i) : 0;
+    S.slot(valid && (!CACHE || miss_bit(a, b, V, slab)), a, b);
+  }
+}
+
+// Edge index of bit `bit` of a miss mask (see stream_range).
+__device__ __forceinline__ int64_t miss_edge(int bit, int32_t base) {
+  return 4 * ((int64_t)base + (int64_t)(bit >> 2) * blockDim.x + threadIdx.x) + (bit & 3);
+}
+
+}  // namespace bridges

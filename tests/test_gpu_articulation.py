@@ -1,0 +1,149 @@
+"""Parity of the articulation-point path (through the C ABI) with the CPU oracle.
+
+The set of cut vertices is unique, so the sorted list must match the oracle's bit for bit:
+Tarjan's low/disc test (oracle.articulation_points) and, on small graphs, the definition itself
+(oracle.brute_articulation).  Sizes span several 4,096-edge tiles with ragged tails, and M
+varies the bridge path's partitioning underneath.
+"""
+import numpy as np
+import pytest
+import torch
+
+import graphgen
+import oracle
+from conftest import golden_names, load_golden
+
+pytestmark = pytest.mark.gpu
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.int32)).to("cuda:0")
+
+
+@pytest.fixture(scope="module")
+def ctx(cuda_lib):
+    return cuda_lib.Context(device="cuda:0")
+
+
+def gpu_points(ctx, u, v, V, M=0):
+    return ctx.articulation_points(dev(u), dev(v), V, M).cpu().numpy()
+
+
+@pytest.mark.parametrize("name", golden_names())
+@pytest.mark.parametrize("M", [1, 3])
+def test_golden(ctx, name, M):
+    u, v, V, _ = load_golden(name)
+    assert gpu_points(ctx, u, v, V, M).tolist() == oracle.brute_articulation(u, v, V).tolist()
+
+
+def test_random_multigraphs_against_definition(ctx):
+    rng = np.random.default_rng(61)
+    for t in range(400):
+        V = int(rng.integers(1, 65))
+        E = int(rng.integers(0, 4 * V + 2))
+        u, v = graphgen.random_multigraph(50000 + t, V, E)
+        M = int(rng.choice([1, 2, 5, 64]))
+        assert gpu_points(ctx, u, v, V, M).tolist() == oracle.brute_articulation(u, v, V).tolist(), (t, V, E, M)
+
+
+def test_random_sparse_mid(ctx):
+    """Sparse graphs: many small blocks, long tree paths, many components."""
+    rng = np.random.default_rng(62)
+    for t in range(30):
+        V = int(rng.integers(100, 20000))
+        E = int(rng.integers(V // 2, 3 * V))
+        u, v = graphgen.random_multigraph(51000 + t, V, E)
+        ref = oracle.articulation_points(u, v, V)
+        for M in (1, 7):
+            assert gpu_points(ctx, u, v, V, M).tolist() == ref.tolist(), (t, V, E, M)
+
+
+def test_dense_with_snapshot(ctx):
+    """Dense enough that the block pass takes its label snapshot (E > warm-up)."""
+    for t, (V, E) in enumerate([(300, 200000), (2000, 600000), (5000, 3000001)]):
+        u, v = graphgen.random_multigraph(52000 + t, V, E)
+        ref = oracle.articulation_points(u, v, V)
+        for M in (1, 4):
+            assert gpu_points(ctx, u, v, V, M).tolist() == ref.tolist(), (t, M)
+
+
+@pytest.mark.parametrize("name,Ms", [("small", (1, 16)), ("mid", (1, 8, 64))])
+def test_workloads(ctx, name, Ms):
+    g = graphgen.workload(name)
+    ref = oracle.articulation_points(g.u, g.v, g.V)
+    assert len(ref) > 0
+    for M in Ms:
+        assert gpu_points(ctx, g.u, g.v, g.V, M).tolist() == ref.tolist(), M
+
+
+def test_closed_forms(ctx):
+    rng = np.random.default_rng(63)
+    for n in (2, 3, 1000, 70000):  # random trees: the vertices of degree >= 2
+        par = (rng.random(n - 1) * np.arange(1, n)).astype(np.int32)
+        ch = np.arange(1, n, dtype=np.int32)
+        perm = rng.permutation(n - 1)
+        deg = np.bincount(np.concatenate([par, ch]), minlength=n)
+        assert gpu_points(ctx, par[perm], ch[perm], n, 1).tolist() == np.flatnonzero(deg >= 2).tolist()
+    n = 50000
+    a = np.arange(n - 1, dtype=np.int32)
+    assert gpu_points(ctx, a, a + 1, n, 3).tolist() == list(range(1, n - 1))  # path
+    c = np.arange(n, dtype=np.int32)
+    assert len(gpu_points(ctx, c, (c + 1) % n, n, 2)) == 0  # cycle
+    assert gpu_points(ctx, np.zeros(n - 1, np.int32), a + 1, n, 4).tolist() == [0]  # star
+    # a chain of 1,000 triangles sharing one vertex each: the 999 shared vertices
+    k = 1000
+    base = 2 * np.arange(k, dtype=np.int32)
+    u = np.concatenate([base, base + 1, base + 2])
+    v = np.concatenate([base + 1, base + 2, base])
+    assert gpu_points(ctx, u, v, 2 * k + 1, 2).tolist() == (2 * np.arange(1, k)).tolist()
+
+
+def test_edge_cases(ctx, cuda_lib):
+    e = np.zeros(0, np.int32)
+    assert len(gpu_points(ctx, e, e, 0)) == 0
+    assert len(gpu_points(ctx, e, e, 1)) == 0
+    assert len(gpu_points(ctx, e, e, 10)) == 0
+    assert len(gpu_points(ctx, np.zeros(5, np.int32), np.zeros(5, np.int32), 1)) == 0  # self-loops
+    assert len(gpu_points(ctx, np.array([3], np.int32), np.array([1], np.int32), 4)) == 0  # one edge
+    # doubled path: every edge has a parallel copy, yet the inner vertices still cut
+    a = np.arange(9, dtype=np.int32)
+    assert gpu_points(ctx, np.concatenate([a, a]), np.concatenate([a + 1, a + 1]), 10).tolist() == list(range(1, 9))
+    with pytest.raises(cuda_lib.BridgesError) as ei:
+        gpu_points(ctx, np.array([0, 1], np.int32), np.array([1, 9], np.int32), 5)
+    assert ei.value.code == -2
+    assert gpu_points(ctx, np.array([0, 1], np.int32), np.array([1, 2], np.int32), 3).tolist() == [1]
+
+
+def test_misaligned_input(ctx):
+    g = graphgen.workload("small")
+    ref = oracle.articulation_points(g.u, g.v, g.V)
+    du, dv = dev(np.concatenate([[0], g.u])), dev(np.concatenate([[0, 0, 0], g.v]))
+    assert ctx.articulation_points(du[1:], dv[3:], g.V, 2).cpu().numpy().tolist() == ref.tolist()
+
+
+def test_with_bridges_async_and_profile(cuda_lib):
+    g = graphgen.workload("mid")
+    ref_ap = oracle.articulation_points(g.u, g.v, g.V)
+    ref_br = oracle.dfs_bridges(g.u, g.v, g.V)
+    c = cuda_lib.Context(device="cuda:0", profile=True)
+    du, dv = dev(g.u), dev(g.v)
+    pts, br = c.articulation_points(du, dv, g.V, 4, with_bridges=True)
+    assert pts.cpu().numpy().tolist() == ref_ap.tolist()
+    assert br.cpu().numpy().tolist() == ref_br.tolist()
+    ms = c.ap_stage_ms()
+    assert set(ms) == {"warmup", "snapshot", "stream", "mark", "total"} and ms["total"] > 0
+    cnt = torch.zeros(2, dtype=torch.int64, device="cuda:0")
+    out = c.articulation_points(du, dv, g.V, 4, counts_device=cnt)
+    torch.cuda.synchronize()
+    na, nb = (int(x) for x in cnt.cpu())
+    assert na == len(ref_ap) and nb == len(ref_br)
+    assert out[:na].cpu().numpy().tolist() == ref_ap.tolist()
+
+
+def test_user_workspace(cuda_lib):
+    g = graphgen.workload("small")
+    probe = cuda_lib.Context(device="cuda:0")
+    need = probe.articulation_workspace_bytes(g.E, g.V, 2)
+    c = cuda_lib.Context(device="cuda:0", workspace_bytes=need)
+    assert c.articulation_points(dev(g.u), dev(g.v), g.V, 2).cpu().numpy().tolist() == \
+        oracle.articulation_points(g.u, g.v, g.V).tolist()
