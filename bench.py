@@ -156,6 +156,8 @@ def cpu_oracle_rate(g, M, sample_edges):
 def run_reference(args, world, rank):
     if rank != 0:
         return
+    if args.workload == "articulation":
+        return run_reference_ap(args, world)
     g = make_workload(args)
     M = args.M if args.M > 0 else 5
     per_step = args.ref_sample
@@ -178,6 +180,30 @@ def run_reference(args, world, rank):
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
+
+
+def run_reference_ap(args, world):
+    g = graphgen.workload("large", **({} if args.density is None else {"p": args.density}))
+    per_step = args.ref_sample // 3
+    for _ in range(args.warmup):
+        cpu_oracle_ap_rate(g, max(per_step // 10, 1))
+    times = []
+    n = 0
+    for _ in range(args.steps):
+        _, n, dt = cpu_oracle_ap_rate(g, per_step)
+        times.append(dt)
+    tot = sum(times)
+    value = n * args.steps / tot / 1e9
+    sample = (f"oracle Tarjan low/disc articulation points (single-threaded C) on the first {n} edges of the large "
+              f"workload per step")
+    print(json.dumps({
+        "impl": "reference", "metric": AP_METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": tot / args.steps * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+        "config": {"workload": "articulation points of large", "V": g.V, "E": g.E, "sample_edges_per_step": n},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
 
 
 def run_native(args, world, rank, local):
@@ -304,6 +330,161 @@ def run_native(args, world, rank, local):
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
                        "bridges": n_found, "bridges_equal_planted": correct,
                        "autotuned_plan": plan, "stage_ms_by_M": sweep},
+            "clocks": ck, "e2e": e2e, "gpu_launches": launches, "roofline": roof, "cpu_baseline": cpu,
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+AP_METRIC = "input edges/s to exact articulation points and bridges"
+
+
+def planted_cut_vertices(g):
+    """Cut vertices of a generated graph whose blocks are its dense cores and its planted bridges:
+    the bridge ends that have another edge (true by construction of the large workload)."""
+    loop = g.u == g.v
+    deg = np.bincount(np.concatenate([g.u[~loop], g.v[~loop]]), minlength=g.V)
+    ends = np.unique(g.planted.ravel())
+    return ends[deg[ends] >= 2]
+
+
+def cpu_oracle_ap_rate(g, sample_edges):
+    """The oracle's articulation points (Tarjan low/disc, single-threaded C) on a prefix sample."""
+    import oracle
+
+    n = min(sample_edges, g.E)
+    u = np.ascontiguousarray(g.u[:n])
+    v = np.ascontiguousarray(g.v[:n])
+    t = time.perf_counter()
+    oracle.articulation_points(u, v, g.V)
+    dt = time.perf_counter() - t
+    return n / dt / 1e9, n, dt
+
+
+def run_articulation(args, world, rank, local):
+    """Articulation points (and bridges) of the large workload: the bridge path, then the block
+    pass over the same 1.07 G edges; a step is one bridges_articulation_points call."""
+    import torch
+
+    import paper_2108_07346_gb300 as pb
+
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=dev)
+    over = {} if args.density is None else {"p": args.density}
+    g = graphgen.workload("large", **over)
+    E, V = g.E, g.V
+    du = torch.from_numpy(g.u).to(dev)
+    dv = torch.from_numpy(g.v).to(dev)
+    ctx = pb.Context(device=dev, profile=True, M=args.M)
+    stream = torch.cuda.current_stream(dev)
+    plan = ctx.autotune(du, dv, V, reps=3) if args.M <= 0 and not args.no_tune else None
+    pts, br = ctx.articulation_points(du, dv, V, args.M, with_bridges=True)
+    expect = planted_cut_vertices(g)
+    correct = bool(np.array_equal(pts.cpu().numpy(), expect) and np.array_equal(br.cpu().numpy(), g.planted))
+    out = torch.empty(max(V, 1), dtype=torch.int32, device=dev)
+    cnt = torch.zeros(2, dtype=torch.int64, device=dev)
+    for _ in range(args.warmup):
+        ctx.articulation_points(du, dv, V, args.M, counts_device=cnt, out=out, stream=stream)
+    torch.cuda.synchronize()
+
+    clocks = Clocks(local)
+    clocks.start()
+    clocks.mark("t0")
+    l0 = ctx.launches()
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        ctx.articulation_points(du, dv, V, args.M, counts_device=cnt, out=out, stream=stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clocks.mark("t1")
+    launches = ctx.launches() - l0
+    ms_total = reduce_max(e0.elapsed_time(e1), dev)
+    ck = clocks.stop()
+    n_pts, n_br = (int(x) for x in cnt.cpu())
+    steps_seen = min(args.steps, 32)
+    ap_hist = ctx.ap_stage_ms_history(steps_seen)
+    br_hist = ctx.stage_ms_history(steps_seen)
+    cfg = ctx.last_config()
+    warm = cfg["warm_edges"] if cfg["warm_edges"] > 0 else None
+    ap_warm = cfg["ap_warm_edges"] if cfg["ap_warm_edges"] >= 0 else None
+    peak, peak_kind = peaks()
+    kernels = {}
+    if warm is not None and ap_warm is not None and ap_hist and br_hist:
+        fe = E - cfg["M"] * warm
+        se = E - ap_warm
+        kernels = {
+            "block pass stream (ap_pass_kernel<cache, vec>)": (statistics.mean(h["stream"] for h in ap_hist), se),
+            "forest pass (leaf_kernel<cache, vec>)": (statistics.mean(h["forest"] for h in br_hist), fe),
+        }
+    roof = None
+    if kernels:
+        name, (ms, edges) = max(kernels.items(), key=lambda kv: kv[1][0])
+        achieved = 8.0 * edges / (ms * 1e-3) / 1e9
+        roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": None, "kernel": name, "algorithmic_bytes": 8 * edges, "peak_kind": peak_kind,
+                "per_kernel": {k: {"ms": m, "GB_per_s": 8.0 * e / (m * 1e-3) / 1e9,
+                                   "frac": 8.0 * e / (m * 1e-3) / 1e9 / peak} for k, (m, e) in kernels.items()},
+                "ap_stage_ms_mean": {k: statistics.mean(h[k] for h in ap_hist) for k in ap_hist[0]},
+                "bridge_stage_ms_mean": {k: statistics.mean(h[k] for h in br_hist) for k in br_hist[0]}}
+
+    e2e = None
+    if not args.no_e2e:
+        # the user's call from host memory: pinned copies in, the call, the points and counts out
+        hu = torch.from_numpy(g.u).pin_memory()
+        hv = torch.from_numpy(g.v).pin_memory()
+        hpts = torch.empty(max(V, 1), dtype=torch.int32).pin_memory()
+        hcnt = torch.empty(2, dtype=torch.int64).pin_memory()
+        du2 = torch.empty_like(du)
+        dv2 = torch.empty_like(dv)
+        ks = max(1, min(args.steps, args.e2e_steps))
+        nb = 0
+        for it in range(ks + 1):  # the first round is an untimed warm-up
+            if it == 1:
+                if world > 1:
+                    torch.distributed.barrier()
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+            du2.copy_(hu, non_blocking=True)
+            dv2.copy_(hv, non_blocking=True)
+            ctx.articulation_points(du2, dv2, V, args.M, counts_device=cnt, out=out, stream=stream)
+            hcnt.copy_(cnt, non_blocking=True)
+            stream.synchronize()
+            nb = int(hcnt[0])
+            hpts[:nb].copy_(out[:nb])
+        dt = reduce_max(time.perf_counter() - t0, dev)
+        e2e = {"value": whole_job_rate(E * ks, world, dt), "unit": UNIT, "h2d_bytes_per_step": 8 * E,
+               "d2h_bytes_per_step": 16 + 4 * nb, "steps": ks, "ms_per_step": dt / ks * 1e3}
+        del du2, dv2
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        rate, n, dt = cpu_oracle_ap_rate(g, args.ap_cpu_sample)
+        cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"Tarjan low/disc articulation points (single-threaded C) on the first {n} edges of the "
+                         f"workload; {dt:.1f} s"}
+    if rank == 0:
+        line = {
+            "metric": AP_METRIC, "value": whole_job_rate(E * args.steps, world, ms_total * 1e-3), "unit": UNIT,
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_total / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+            "config": {"workload": f"articulation points of large: ER(65536, p={g.spec.p}) core + 256 pendant trees "
+                                   f"+ 128 two-edge vertices, seed {g.spec.seed}",
+                       "V": V, "E": E, "M": cfg["M"], "warm_edges": cfg["warm_edges"],
+                       "block_pass_prefix_edges": cfg["ap_warm_edges"], "block_pass_blocks": cfg["ap_blocks"],
+                       "l2": "inputs (8E bytes) larger than L2; no flush",
+                       "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
+                       "cut_vertices": n_pts, "bridges": n_br, "equal_construction": correct,
+                       "autotuned_plan": plan},
             "clocks": ck, "e2e": e2e, "gpu_launches": launches, "roofline": roof, "cpu_baseline": cpu,
         }
         print(json.dumps(line), flush=True)
@@ -468,7 +649,8 @@ def main():
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["native", "reference"], default="native")
-    ap.add_argument("--workload", choices=["large", "mid", "small", "batched", "served"], default="large")
+    ap.add_argument("--workload", choices=["large", "mid", "small", "batched", "served", "articulation"],
+                    default="large")
     ap.add_argument("--requests", type=int, default=4000, help="served: requests")
     ap.add_argument("--rate", type=float, default=2000.0, help="served: mean arrivals per second")
     ap.add_argument("--pool", type=int, default=64, help="served: distinct resident graphs")
@@ -485,6 +667,8 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-sample", type=int, default=2_000_000_000, help="oracle sample (edges; whole graph)")
     ap.add_argument("--ref-sample", type=int, default=150_000_000, help="reference arm sample per step (edges)")
+    ap.add_argument("--ap-cpu-sample", type=int, default=100_000_000,
+                    help="articulation: oracle sample for cpu_baseline (edges)")
     args = ap.parse_args()
     world, rank, local = dist_setup()
     if args.impl == "reference":
@@ -493,6 +677,8 @@ def main():
         run_batched(args, world, rank, local)
     elif args.workload == "served":
         run_served(args, world, rank, local)
+    elif args.workload == "articulation":
+        run_articulation(args, world, rank, local)
     else:
         run_native(args, world, rank, local)
 

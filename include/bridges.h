@@ -66,7 +66,10 @@ typedef struct bridges_opts {
   int32_t host_read;   /* bridges_find_host: 1 = when the host buffers are pinned and mapped,
                           kernels read them in place over the host link instead of copying
                           them to the device first; 0 = always copy */
-  int32_t reserved[6];
+  int32_t ap_warm_edges; /* bridges_articulation_points: edges of the list offered to the block
+                            pass before its label snapshot; 0: auto, > 0: that many, < 0: none
+                            (snapshot right after the certificate's own edges) */
+  int32_t reserved[5];
 } bridges_opts;
 
 typedef struct bridges_ctx bridges_ctx;
@@ -298,12 +301,15 @@ int64_t bridges_inc_certificate_size(const bridges_inc* inc);
  *   pass in ms: [0] warm-up (certificate edges + prefix), [1] label snapshot, [2] stream,
  *   [3] marking and compaction, [4] the whole block pass; waits for them; returns how many were
  *   written (0 when none are available).
+ * bridges_ctx_ap_stage_ms_history: the same five times for each of the last min(max_calls, 32)
+ *   calls, oldest first, 5 floats per call; returns the number of calls written.
  */
 int64_t bridges_articulation_points(bridges_ctx* ctx, struct CUstream_st* stream, const int32_t* edges_u,
                                     const int32_t* edges_v, int64_t E, int32_t V, int32_t M, int32_t* out_points,
                                     int32_t* out_bridges, int64_t* out_counts_device);
 int64_t bridges_articulation_workspace_bytes(const bridges_ctx* ctx, int64_t E, int32_t V, int32_t M);
 int32_t bridges_ctx_ap_stage_ms(const bridges_ctx* ctx, float* ms, int32_t n);
+int32_t bridges_ctx_ap_stage_ms_history(const bridges_ctx* ctx, float* ms, int32_t max_calls);
 
 /* ---------------------------------------------------------------------------------------
  * Autotuning.
@@ -338,7 +344,8 @@ int32_t bridges_wait_value(bridges_ctx* ctx, struct CUstream_st* stream, const i
  * [5] total.  Returns the number of values written (0 if profiling is off).
  * bridges_ctx_launches: kernels launched by the context since creation.
  * bridges_ctx_last_config: the M, fan-in, CTAs per partition, block size and warm-up edges
- * of the last call (5 values).
+ * of the last call (5 values), then the last bridges_articulation_points call's block-pass
+ * prefix edges (-1: no snapshot) and blocks (values 6 and 7); returns min(n, 7).
  * bridges_status_string: a static description of a status code.
  */
 int32_t bridges_ctx_stage_ms(const bridges_ctx* ctx, float* ms, int32_t n);

@@ -51,7 +51,8 @@ class Opts(ctypes.Structure):
         ("warm_edges", ctypes.c_int64),
         ("profile", ctypes.c_int32),
         ("host_read", ctypes.c_int32),
-        ("reserved", ctypes.c_int32 * 6),
+        ("ap_warm_edges", ctypes.c_int32),
+        ("reserved", ctypes.c_int32 * 5),
     ]
 
 
@@ -97,6 +98,7 @@ _SIGS = {
     "bridges_articulation_points": (_I64, [_P, _P, _P, _P, _I64, _I32, _I32, _P, _P, _P]),
     "bridges_articulation_workspace_bytes": (_I64, [_P, _I64, _I32, _I32]),
     "bridges_ctx_ap_stage_ms": (_I32, [_P, ctypes.POINTER(ctypes.c_float), _I32]),
+    "bridges_ctx_ap_stage_ms_history": (_I32, [_P, ctypes.POINTER(ctypes.c_float), _I32]),
 }
 
 
@@ -161,13 +163,14 @@ class Context:
     """
 
     def __init__(self, device=None, M=0, fan_in=0, block=0, ctas_per_sm=0, warm_edges=-1, profile=False,
-                 mem_budget=0, workspace_bytes=None, host_read=False):
+                 mem_budget=0, workspace_bytes=None, host_read=False, ap_warm_edges=0):
         self._lib = load()
         dev = torch.device("cuda", torch.cuda.current_device()) if device is None else torch.device(device)
         self.device = dev
         o = Opts()
         o.M, o.fan_in, o.block, o.ctas_per_sm = M, fan_in, block, ctas_per_sm
         o.warm_edges, o.profile, o.host_read = warm_edges, int(bool(profile)), int(bool(host_read))
+        o.ap_warm_edges = int(ap_warm_edges)
         self._opts = o
         self._ws = None
         with torch.cuda.device(dev):
@@ -333,6 +336,13 @@ class Context:
         names = ["warmup", "snapshot", "stream", "mark", "total"]
         return {names[i]: float(buf[i]) for i in range(max(k, 0))}
 
+    def ap_stage_ms_history(self, max_calls: int = 32):
+        """Block-pass stage times of the last min(max_calls, 32) profiled calls, oldest first."""
+        buf = (ctypes.c_float * (5 * max_calls))()
+        k = self._lib.bridges_ctx_ap_stage_ms_history(self._h, buf, max_calls)
+        names = ["warmup", "snapshot", "stream", "mark", "total"]
+        return [{names[j]: float(buf[5 * i + j]) for j in range(5)} for i in range(k)]
+
     def set_batch_split(self, split_edges: int):
         _check(self._lib.bridges_ctx_set_batch_split(self._h, int(split_edges)), "bridges_ctx_set_batch_split")
 
@@ -353,9 +363,9 @@ class Context:
         return int(self._lib.bridges_ctx_launches(self._h))
 
     def last_config(self):
-        buf = (ctypes.c_int64 * 5)()
-        k = self._lib.bridges_ctx_last_config(self._h, buf, 5)
-        names = ["M", "fan_in", "blocks_per_partition", "block", "warm_edges"]
+        buf = (ctypes.c_int64 * 7)()
+        k = self._lib.bridges_ctx_last_config(self._h, buf, 7)
+        names = ["M", "fan_in", "blocks_per_partition", "block", "warm_edges", "ap_warm_edges", "ap_blocks"]
         return {names[i]: int(buf[i]) for i in range(k)}
 
 

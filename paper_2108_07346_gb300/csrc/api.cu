@@ -94,6 +94,18 @@ void resolve_timings(bridges_ctx* c, int64_t upto) {
   }
 }
 
+// The same for the articulation-point block pass: [0] warm-up, [1] snapshot, [2] stream,
+// [3] marking and compaction, [4] the whole pass.
+void resolve_ap_timings(bridges_ctx* c, int64_t upto) {
+  for (; c->ap_resolved < upto; c->ap_resolved++) {
+    const int s = (int)(c->ap_resolved % bridges_ctx::kRing);
+    cudaEvent_t* e = c->ap_ev[s];
+    cudaEventSynchronize(e[4]);
+    for (int i = 0; i < 4; i++) cudaEventElapsedTime(&c->ap_ms[s][i], e[i], e[i + 1]);
+    cudaEventElapsedTime(&c->ap_ms[s][4], e[0], e[4]);
+  }
+}
+
 // Before a profiled call reuses a ring slot, the times of the call that last used it are read.
 cudaEvent_t* next_event_slot(bridges_ctx* c) {
   if (!c->events) return nullptr;
@@ -120,8 +132,9 @@ int init_ctx(bridges_ctx* c, int device, const bridges_opts* opts) {
     for (auto& set : c->ev)
       for (auto& e : set)
         if (cudaEventCreate(&e) != cudaSuccess) return -1;
-    for (auto& e : c->ap_ev)
-      if (cudaEventCreate(&e) != cudaSuccess) return -1;
+    for (auto& set : c->ap_ev)
+      for (auto& e : set)
+        if (cudaEventCreate(&e) != cudaSuccess) return -1;
     c->events = true;
   }
   return 0;
@@ -219,7 +232,8 @@ void bridges_ctx_destroy(bridges_ctx* c) {
   if (c->events) {
     for (auto& set : c->ev)
       for (auto& e : set) cudaEventDestroy(e);
-    for (auto& e : c->ap_ev) cudaEventDestroy(e);
+    for (auto& set : c->ap_ev)
+      for (auto& e : set) cudaEventDestroy(e);
   }
   cudaGetLastError();
   delete c;
@@ -413,7 +427,7 @@ int64_t bridges_ctx_launches(const bridges_ctx* c) { return c ? c->launches : 0;
 
 int32_t bridges_ctx_last_config(const bridges_ctx* c, int64_t* vals, int32_t n) {
   if (!c || !vals) return 0;
-  int32_t k = std::min<int32_t>(n, 5);
+  int32_t k = std::min<int32_t>(n, 7);
   for (int i = 0; i < k; i++) vals[i] = c->last_cfg[i];
   return k;
 }
@@ -810,6 +824,14 @@ extern "C" int64_t bridges_two_edge_components(bridges_ctx* c, struct CUstream_s
 
 // ---------------------------------------------------------------------------------------------
 // Articulation points: the bridge path, then the block pass over the same edges.
+// Edges of the list offered to the block pass before its snapshot (after the certificate's).
+static int64_t ap_warm_edges(const bridges_ctx* c, int64_t E, int32_t V) {
+  const int32_t w = c->opts.ap_warm_edges;
+  if (w < 0) return 0;
+  if (w > 0) return std::min<int64_t>(w, E);
+  return std::min<int64_t>(E, 2 * (int64_t)V + 4096);
+}
+
 extern "C" int64_t bridges_articulation_points(bridges_ctx* c, struct CUstream_st* stream, const int32_t* u,
                                                const int32_t* v, int64_t E, int32_t V, int32_t M,
                                                int32_t* out_points, int32_t* out_bridges,
@@ -836,15 +858,23 @@ extern "C" int64_t bridges_articulation_points(bridges_ctx* c, struct CUstream_s
                 k.cert.P1, k.fin.dscan);
   }
   ApBufs b = carve_ap(static_cast<char*>(c->ws) + ap_at, V);
-  // the block pass streams the whole list as one partition
-  const CertPlan q = plan_for(c, E, V, 1);
-  cudaEvent_t* ev = c->events ? c->ap_ev : nullptr;
-  if (ev) cudaEventRecord(ev[0], s);
+  // the block pass streams the whole list as one partition, its own warm-up before the snapshot
+  CertPlan q = plan_for(c, E, V, 1);
+  q.warm = ap_warm_edges(c, E, V);
+  q.cache = (size_t)align_up((size_t)V + 1, 8) * 2 + 1024 <= c->smem_optin && q.warm < E;
+  c->last_cfg[5] = q.cache ? q.warm : -1;
+  c->last_cfg[6] = (int64_t)q.G * q.M;
+  cudaEvent_t* ev = nullptr;
+  if (c->events) {
+    resolve_ap_timings(c, c->ap_calls - bridges_ctx::kRing + 1);  // the slot's previous call
+    ev = c->ap_ev[c->ap_calls % bridges_ctx::kRing];
+    cudaEventRecord(ev[0], s);
+  }
   articulation_stage(L, q, k.fin, b, u, v, k.cert.f2u, k.cert.f2v, k.cert.cnt + 1, out_points, b.count,
                      ev ? ev + 1 : nullptr);
   if (ev) {
     cudaEventRecord(ev[4], s);
-    c->ap_profiled = true;
+    c->ap_calls++;
   }
   if (cudaGetLastError() != cudaSuccess) return BRIDGES_ECUDA;
   if (out_counts_device) {
@@ -866,14 +896,25 @@ extern "C" int64_t bridges_articulation_workspace_bytes(const bridges_ctx* c, in
 }
 
 extern "C" int32_t bridges_ctx_ap_stage_ms(const bridges_ctx* c, float* ms, int32_t n) {
-  if (!c || !ms || n <= 0 || !c->ap_profiled) return 0;
-  if (cudaEventSynchronize(c->ap_ev[4]) != cudaSuccess) return cuda_fail(cudaGetLastError());
-  float t[5];
-  for (int i = 0; i < 4; i++) cudaEventElapsedTime(&t[i], c->ap_ev[i], c->ap_ev[i + 1]);
-  cudaEventElapsedTime(&t[4], c->ap_ev[0], c->ap_ev[4]);
+  if (!c || !c->events || !ms || n <= 0 || c->ap_calls == 0) return 0;
+  bridges_ctx* m = const_cast<bridges_ctx*>(c);
+  resolve_ap_timings(m, m->ap_calls);
+  const int s = (int)((m->ap_calls - 1) % bridges_ctx::kRing);
   const int32_t k = std::min(n, 5);
-  for (int i = 0; i < k; i++) ms[i] = t[i];
+  for (int i = 0; i < k; i++) ms[i] = m->ap_ms[s][i];
   return k;
+}
+
+extern "C" int32_t bridges_ctx_ap_stage_ms_history(const bridges_ctx* c, float* ms, int32_t max_calls) {
+  if (!c || !c->events || !ms || max_calls <= 0) return 0;
+  bridges_ctx* m = const_cast<bridges_ctx*>(c);
+  resolve_ap_timings(m, m->ap_calls);
+  const int64_t n = std::min<int64_t>({(int64_t)max_calls, m->ap_calls, (int64_t)bridges_ctx::kRing});
+  for (int64_t i = 0; i < n; i++) {
+    const int s = (int)((m->ap_calls - n + i) % bridges_ctx::kRing);
+    for (int j = 0; j < 5; j++) ms[5 * i + j] = m->ap_ms[s][j];
+  }
+  return (int32_t)n;
 }
 
 struct bridges_inc {

@@ -21,8 +21,9 @@
 //   * A vertex is an articulation point iff its tree edges fall into at least two classes
 //     (each block through a vertex holds one of its tree edges).
 //
-// An edge whose two ends lie in one class is redundant: its cycle is inside the class.  After a
-// warm-up (the certificate's F' edges, then a prefix of the edge list) nearly every edge is, so
+// An edge whose two ends lie in one class is redundant: its cycle is inside the class.  Once the
+// classes start as the blocks of the certificate S = T u F' (linked in O(V) by Tarjan & Vishkin's
+// rules, below) and a short prefix of the list has been walked, nearly every edge is, so
 // the stream reuses the forest pass's machinery: a 16-bit label per vertex in shared memory (the
 // largest class containing the vertex), two label reads per edge, and the cycle walk only for
 // the misses.  Classes only grow, so a stale label is still sound.
@@ -137,11 +138,31 @@ __global__ void ap_init_kernel(FinalBufs f, ApBufs b, int32_t V) {
   if (gtid() == 0) *b.hooks = 0;
 }
 
-// Offers a device-counted edge list (the certificate's F' edges) to the classes.
-__global__ void ap_seed_kernel(ApArgs A, const int32_t* xu, const int32_t* xv, const int32_t* d_n, int32_t cap) {
+// The blocks of the certificate S = T u F' as the starting classes, by the two link rules of
+// Tarjan & Vishkin (1985) over T: (1) a non-tree edge of S between two unrelated vertices joins
+// their tree edges; (2) a tree edge (y, p), p not a root, joins p's tree edge when y's subtree
+// has an S-neighbour outside p's subtree -- read off the subtree minimum / maximum preorder
+// (slo / shi) that the bridge test computed.  Every link joins two edges of one fundamental
+// cycle, and the closure of the links is the blocks of S restricted to T: each a connected
+// subtree of T again once all links are in, which the cycle walk of the later passes needs.
+__global__ void ap_tv_kernel(FinalBufs f, ApArgs A, const int32_t* xu, const int32_t* xv, const int32_t* d_n,
+                             int32_t cap) {
   if (*A.status) return;
+  const int32_t V = A.V;
+  for (int64_t y = gtid(); y < V; y += gstride()) {
+    const int32_t p = f.par[y];
+    if (p < 0 || f.par[p] < 0) continue;
+    const int32_t pp = f.pre[p];
+    if (f.slo[y] < pp || f.shi[y] > A.LAST[pp]) uf_link(A.Q, f.pre[y], pp);
+  }
   const int32_t n = min(*d_n, cap);
-  for (int64_t e = gtid(); e < n; e += gstride()) offer_edge(A, xu[e], xv[e]);
+  for (int64_t e = gtid(); e < n; e += gstride()) {
+    const int32_t a = xu[e], b = xv[e];
+    if (!checked_edge(A, a, b)) continue;
+    const int32_t pa = f.pre[a], pb = f.pre[b];
+    const bool related = (pa <= pb && pb <= A.LAST[pa]) || (pb <= pa && pa <= A.LAST[pb]);
+    if (!related) uf_link(A.Q, pa, pb);
+  }
 }
 
 struct PassArgs {
@@ -392,12 +413,12 @@ void articulation_stage(const Launch& L, const CertPlan& p, const FinalBufs& f, 
   const int g = grid_of(L, V, bs);
   ap_init_kernel<<<g, bs, 0, L.stream>>>(f, b, V);
   ApArgs A{f.pre, b.Q, b.PP, b.LAST, V, f.status, b.hooks};
-  ap_seed_kernel<<<grid_of(L, V, bs), bs, 0, L.stream>>>(A, xu, xv, d_nx, V);
+  ap_tv_kernel<<<grid_of(L, V, bs), bs, 0, L.stream>>>(f, A, xu, xv, d_nx, V);
   *L.launches += 2;
   const bool vec = ((reinterpret_cast<uintptr_t>(u) | reinterpret_cast<uintptr_t>(v)) & 15) == 0;
   const int grid = (int)std::max<int64_t>(1, (int64_t)p.G * p.M);
   PassArgs a{A, u, v, 0, p.cache ? std::min(p.warm, p.E) : p.E, b.lab, b.Vpad};
-  if (p.E > 0) {
+  if (a.t > 0) {
     if (vec)
       launch_pass<false, true>(L, a, grid, p.block, 0);
     else

@@ -31,10 +31,13 @@ struct bridges_ctx {
   int64_t calls = 0;         // profiled calls issued
   int64_t resolved = 0;      // calls whose times have been read back
   float stage_ms[kRing][6]{};
-  int64_t last_cfg[5]{};
-  // profiling of the articulation-point stage: start, after warm-up, snapshot, stream, end
-  cudaEvent_t ap_ev[5]{};
-  bool ap_profiled = false;
+  int64_t last_cfg[7]{};  // [5], [6]: block pass prefix edges (-1: no snapshot) and blocks
+  // profiling of the articulation-point block pass, a ring like the above; per call the events
+  // are start, after warm-up, after snapshot, after stream, end
+  cudaEvent_t ap_ev[kRing][5]{};
+  int64_t ap_calls = 0;
+  int64_t ap_resolved = 0;
+  float ap_ms[kRing][5]{};
   // batched path: device descriptors, pinned staging and a CUDA graph per capacity
   void* bws = nullptr;          // device: BatchArgs | ntasks | queue | tasks[cap] | done[gcap] | gerr[gcap] | slots
   size_t bws_bytes = 0;

@@ -452,6 +452,8 @@ __global__ void __launch_bounds__(kThreads) final_kernel(FinArgs A) {
           mx = max(mx, max(tmax[k * T + sl], tmax[k * T + sr - (1LL << k)]));
         }
       }
+      f.slo[y] = mn;
+      f.shi[y] = mx;
       if (mn >= l && mx < r) {
         const uint32_t a = (uint32_t)min((int32_t)y, f.par[y]), b = (uint32_t)max((int32_t)y, f.par[y]);
         key = ((uint64_t)a << A.kbits) | b;
@@ -634,7 +636,7 @@ size_t final_bytes(int32_t V) {
   const size_t Vs = (size_t)std::max(V, 1);
   size_t s = 0;
   s += 3 * 256;                                                           // count, nkeys, barrier
-  s += 13 * align_up(sizeof(int32_t) * (Vs + 1), 256);                    // V-long arrays
+  s += 15 * align_up(sizeof(int32_t) * (Vs + 1), 256);                    // V-long arrays
   s += 7 * align_up(sizeof(int32_t) * (2 * Vs + 1), 256);                 // 2V-long arrays
   s += 4 * align_up(sizeof(int32_t) * (Vs / kChunk + 2), 256);            // chunk / superchunk min, max
   s += 2 * align_up(sizeof(uint64_t) * Vs, 256);                          // keys
@@ -655,8 +657,8 @@ FinalBufs carve_final(void* base, int32_t V, int32_t* status) {
   f.bar_count = reinterpret_cast<unsigned*>(c);
   f.bar_gen = f.bar_count + 1;
   c += 256;
-  int32_t** va[13] = {&f.P,    &f.root, &f.deg, &f.off, &f.cur, &f.aoff, &f.vbase,
-                      &f.pre,  &f.sz,   &f.par, &f.lo,  &f.hi,  &f.bflag};
+  int32_t** va[15] = {&f.P,   &f.root, &f.deg, &f.off, &f.cur,   &f.aoff, &f.vbase, &f.pre,
+                      &f.sz,  &f.par,  &f.lo,  &f.hi,  &f.bflag, &f.slo,  &f.shi};
   for (auto a : va) {
     *a = reinterpret_cast<int32_t*>(c);
     c += align_up(sizeof(int32_t) * (Vs + 1), 256);

@@ -78,6 +78,8 @@ struct FinalBufs {
   int32_t* sz;     // [V]
   int32_t* par;    // [V] parent in the rooted tree (-1 for roots)
   int32_t* bflag;  // [V] 1 if the tree edge (par[y], y) is a bridge
+  int32_t* slo;    // [V] by vertex y (non-roots): min of lo over y's subtree range
+  int32_t* shi;    // [V] by vertex y (non-roots): max of hi over y's subtree range
   int32_t* lo;     // [V] indexed by preorder
   int32_t* hi;     // [V]
   int32_t* cmin;   // [V/32] chunk minima of lo
