@@ -30,10 +30,13 @@ import graphgen  # noqa: E402
 METRIC = "input edges/s to exact bridge set"
 UNIT = "GE/s"
 
-# DRAM bytes (read + write) per streamed edge of the forest pass on the large workload, from the
-# full-size ncu capture summarised in profiles/launch_list_large_dense.md (9.31 GB read + 7.2 MB
-# written for 1,072,703,284 edges, M = 1); valid only for the kernel sources it was measured on.
-TRAFFIC = {"certify_sha": "e17c42dc593d1285", "bytes_per_edge": 8.683}
+# DRAM bytes (read + write) per streamed edge, from full-size single-pass ncu captures on the large
+# workload (profiles/launch_list_large_dense.md, profiles/block_pass_large_dense.md); each is valid
+# only for the kernel sources it was measured on (hash of those sources).
+#   forest pass, M = 1: 9.226 GB read + 7.2 MB written for 1,072,703,284 streamed edges
+#   block pass stream: 9.494 GB read + 10.8 MB written for 1,073,547,340 streamed edges
+TRAFFIC = {"certify_sha": "57e6c29f07bc86dc", "bytes_per_edge": 8.6078}
+AP_TRAFFIC = {"blocks_sha": "e40f3ec967d1ea6b", "bytes_per_edge": 8.8536}
 
 
 def peaks():
@@ -44,12 +47,21 @@ def peaks():
     return 6800.0, "fallback"
 
 
-def certify_sha():
-    """Hash of the forest pass's sources (the traffic figure is only valid for them)."""
+def sources_sha(names):
     h = hashlib.sha256()
-    for name in ("certify.cu", "common.cuh"):
+    for name in names:
         h.update(open(os.path.join(ROOT, "paper_2108_07346_gb300", "csrc", name), "rb").read())
     return h.hexdigest()[:16]
+
+
+def certify_sha():
+    """Hash of the forest pass's sources (the traffic figure is only valid for them)."""
+    return sources_sha(("certify.cu", "common.cuh", "stream.cuh"))
+
+
+def blocks_sha():
+    """Hash of the block pass's sources."""
+    return sources_sha(("blocks.cu", "common.cuh", "stream.cuh"))
 
 
 class Clocks:
@@ -422,49 +434,47 @@ def run_articulation(args, world, rank, local):
     if warm is not None and ap_warm is not None and ap_hist and br_hist:
         fe = E - cfg["M"] * warm
         se = E - ap_warm
+        ap_bpe = AP_TRAFFIC["bytes_per_edge"] if AP_TRAFFIC["blocks_sha"] == blocks_sha() else None
+        fo_bpe = TRAFFIC["bytes_per_edge"] if TRAFFIC["certify_sha"] == certify_sha() else None
         kernels = {
-            "block pass stream (ap_pass_kernel<cache, vec>)": (statistics.mean(h["stream"] for h in ap_hist), se),
-            "forest pass (leaf_kernel<cache, vec>)": (statistics.mean(h["forest"] for h in br_hist), fe),
+            "block pass stream (ap_pass_kernel<cache, vec>)": (statistics.mean(h["stream"] for h in ap_hist), se,
+                                                               ap_bpe),
+            "forest pass (leaf_kernel<cache, vec>)": (statistics.mean(h["forest"] for h in br_hist), fe, fo_bpe),
         }
     roof = None
     if kernels:
-        name, (ms, edges) = max(kernels.items(), key=lambda kv: kv[1][0])
+        name, (ms, edges, bpe) = max(kernels.items(), key=lambda kv: kv[1][0])
         achieved = 8.0 * edges / (ms * 1e-3) / 1e9
         roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": None, "kernel": name, "algorithmic_bytes": 8 * edges, "peak_kind": peak_kind,
+                "traffic": None if bpe is None else bpe * edges, "kernel": name, "algorithmic_bytes": 8 * edges, "peak_kind": peak_kind,
                 "per_kernel": {k: {"ms": m, "GB_per_s": 8.0 * e / (m * 1e-3) / 1e9,
-                                   "frac": 8.0 * e / (m * 1e-3) / 1e9 / peak} for k, (m, e) in kernels.items()},
+                                   "frac": 8.0 * e / (m * 1e-3) / 1e9 / peak,
+                                   "traffic": None if x is None else x * e} for k, (m, e, x) in kernels.items()},
                 "ap_stage_ms_mean": {k: statistics.mean(h[k] for h in ap_hist) for k in ap_hist[0]},
                 "bridge_stage_ms_mean": {k: statistics.mean(h[k] for h in br_hist) for k in br_hist[0]}}
 
     e2e = None
     if not args.no_e2e:
-        # the user's call from host memory: pinned copies in, the call, the points and counts out
+        # the user's call from host memory: bridges_articulation_points_host copies the pinned edges
+        # in, runs the path and copies the cut vertices out
         hu = torch.from_numpy(g.u).pin_memory()
         hv = torch.from_numpy(g.v).pin_memory()
         hpts = torch.empty(max(V, 1), dtype=torch.int32).pin_memory()
-        hcnt = torch.empty(2, dtype=torch.int64).pin_memory()
-        du2 = torch.empty_like(du)
-        dv2 = torch.empty_like(dv)
+        ctx_h = pb.Context(device=dev, M=args.M)
+        ctx_h.articulation_points_host(hu, hv, V, args.M, out=hpts)
         ks = max(1, min(args.steps, args.e2e_steps))
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
         nb = 0
-        for it in range(ks + 1):  # the first round is an untimed warm-up
-            if it == 1:
-                if world > 1:
-                    torch.distributed.barrier()
-                torch.cuda.synchronize()
-                t0 = time.perf_counter()
-            du2.copy_(hu, non_blocking=True)
-            dv2.copy_(hv, non_blocking=True)
-            ctx.articulation_points(du2, dv2, V, args.M, counts_device=cnt, out=out, stream=stream)
-            hcnt.copy_(cnt, non_blocking=True)
-            stream.synchronize()
-            nb = int(hcnt[0])
-            hpts[:nb].copy_(out[:nb])
+        for _ in range(ks):
+            nb = ctx_h.articulation_points_host(hu, hv, V, args.M, out=hpts).shape[0]
+        torch.cuda.synchronize()
         dt = reduce_max(time.perf_counter() - t0, dev)
         e2e = {"value": whole_job_rate(E * ks, world, dt), "unit": UNIT, "h2d_bytes_per_step": 8 * E,
-               "d2h_bytes_per_step": 16 + 4 * nb, "steps": ks, "ms_per_step": dt / ks * 1e3}
-        del du2, dv2
+               "d2h_bytes_per_step": 8 + 4 * nb, "steps": ks, "ms_per_step": dt / ks * 1e3}
+        del ctx_h
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:

@@ -69,7 +69,9 @@ typedef struct bridges_opts {
   int32_t ap_warm_edges; /* bridges_articulation_points: edges of the list offered to the block
                             pass before its label snapshot; 0: auto, > 0: that many, < 0: none
                             (snapshot right after the certificate's own edges) */
-  int32_t reserved[5];
+  int32_t warm_block;    /* threads per block of the forest pass's warm-up launch (the prefix certified
+                            through the union-finds before the snapshot); 0: auto */
+  int32_t reserved[4];
 } bridges_opts;
 
 typedef struct bridges_ctx bridges_ctx;
@@ -295,6 +297,10 @@ int64_t bridges_inc_certificate_size(const bridges_inc* inc);
  * status); otherwise enqueue-only, returning BRIDGES_OK.  Errors: as bridges_find_ctx (ERANGE for
  * a vertex id outside [0, V), found on the device; EINVAL / ENOMEM on the host).
  *
+ * bridges_articulation_points_host: the same from HOST edge buffers (copied to the context's
+ *   device staging area, or read in place when opts.host_read is set and they are pinned and
+ *   mapped); the cut vertices go to out_points_host (host, capacity max(V, 1)).  Synchronous;
+ *   returns their number or a negative status.
  * bridges_articulation_workspace_bytes: workspace a context needs for this call (contexts made
  *   with bridges_ctx_create_ws must be at least this large).
  * bridges_ctx_ap_stage_ms: on a profiling context, the stage times of the last call's block
@@ -307,6 +313,9 @@ int64_t bridges_inc_certificate_size(const bridges_inc* inc);
 int64_t bridges_articulation_points(bridges_ctx* ctx, struct CUstream_st* stream, const int32_t* edges_u,
                                     const int32_t* edges_v, int64_t E, int32_t V, int32_t M, int32_t* out_points,
                                     int32_t* out_bridges, int64_t* out_counts_device);
+int64_t bridges_articulation_points_host(bridges_ctx* ctx, struct CUstream_st* stream, const int32_t* edges_u_host,
+                                         const int32_t* edges_v_host, int64_t E, int32_t V, int32_t M,
+                                         int32_t* out_points_host);
 int64_t bridges_articulation_workspace_bytes(const bridges_ctx* ctx, int64_t E, int32_t V, int32_t M);
 int32_t bridges_ctx_ap_stage_ms(const bridges_ctx* ctx, float* ms, int32_t n);
 int32_t bridges_ctx_ap_stage_ms_history(const bridges_ctx* ctx, float* ms, int32_t max_calls);
@@ -315,16 +324,20 @@ int32_t bridges_ctx_ap_stage_ms_history(const bridges_ctx* ctx, float* ms, int32
  * Autotuning.
  * bridges_autotune: times candidate plans on the given device-resident input (M in
  * {1,2,4,8,16,32}, fan-in 2 or M, warm-up 0.6/1.2/2.0 x V ln V edges, block 1024 or 512; `reps`
- * timed calls each, CUDA events on `stream`) and keeps the fastest in the context's options.
- * best[0..4] receives M, fan-in, warm-up edges, block size and microseconds per call.  Uses
+ * timed calls each, CUDA events on `stream`), then the warm-up launch's block size (128 to 1024)
+ * for the winner, and keeps the fastest in the context's options (read them back whole with
+ * bridges_ctx_get_opts).  best[0..4] receives M, fan-in, warm-up edges, block size and
+ * microseconds per call.  Uses
  * a little scratch memory of its own (the output buffers).  Returns BRIDGES_OK or an error (the
  * options are then unchanged).
  * bridges_ctx_set_opts: replaces the context's tuning options (e.g. from a cache of tuning
  * results); the profiling flag stays as created.
+ * bridges_ctx_get_opts: copies the context's current options to *opts.
  */
 int32_t bridges_autotune(bridges_ctx* ctx, struct CUstream_st* stream, const int32_t* edges_u,
                          const int32_t* edges_v, int64_t E, int32_t V, int32_t reps, int64_t* best);
 int32_t bridges_ctx_set_opts(bridges_ctx* ctx, const bridges_opts* opts);
+int32_t bridges_ctx_get_opts(const bridges_ctx* ctx, bridges_opts* opts);
 
 /* bridges_wait_value: a bounded device-side wait -- one thread polls the device int32 *flag
  * (acquire loads, ~100 ns apart) until it equals `value` or max_polls polls were made, on

@@ -52,7 +52,8 @@ class Opts(ctypes.Structure):
         ("profile", ctypes.c_int32),
         ("host_read", ctypes.c_int32),
         ("ap_warm_edges", ctypes.c_int32),
-        ("reserved", ctypes.c_int32 * 5),
+        ("warm_block", ctypes.c_int32),
+        ("reserved", ctypes.c_int32 * 4),
     ]
 
 
@@ -87,6 +88,7 @@ _SIGS = {
     "bridges_server_destroy": (None, [_P]),
     "bridges_autotune": (_I32, [_P, _P, _P, _P, _I64, _I32, _I32, ctypes.POINTER(ctypes.c_int64)]),
     "bridges_ctx_set_opts": (_I32, [_P, ctypes.POINTER(Opts)]),
+    "bridges_ctx_get_opts": (_I32, [_P, ctypes.POINTER(Opts)]),
     "bridges_wait_value": (_I32, [_P, _P, _P, _I32, _I64]),
     "bridges_two_edge_components": (_I64, [_P, _P, _P, _P, _I64, _I32, _I32, _P, _P]),
     "bridges_inc_create": (_P, [ctypes.c_int, ctypes.POINTER(Opts)]),
@@ -96,6 +98,7 @@ _SIGS = {
     "bridges_inc_two_edge_components": (_I64, [_P, _P, _P]),
     "bridges_inc_certificate_size": (_I64, [_P]),
     "bridges_articulation_points": (_I64, [_P, _P, _P, _P, _I64, _I32, _I32, _P, _P, _P]),
+    "bridges_articulation_points_host": (_I64, [_P, _P, _P, _P, _I64, _I32, _I32, _P]),
     "bridges_articulation_workspace_bytes": (_I64, [_P, _I64, _I32, _I32]),
     "bridges_ctx_ap_stage_ms": (_I32, [_P, ctypes.POINTER(ctypes.c_float), _I32]),
     "bridges_ctx_ap_stage_ms_history": (_I32, [_P, ctypes.POINTER(ctypes.c_float), _I32]),
@@ -163,7 +166,7 @@ class Context:
     """
 
     def __init__(self, device=None, M=0, fan_in=0, block=0, ctas_per_sm=0, warm_edges=-1, profile=False,
-                 mem_budget=0, workspace_bytes=None, host_read=False, ap_warm_edges=0):
+                 mem_budget=0, workspace_bytes=None, host_read=False, ap_warm_edges=0, warm_block=0):
         self._lib = load()
         dev = torch.device("cuda", torch.cuda.current_device()) if device is None else torch.device(device)
         self.device = dev
@@ -171,6 +174,7 @@ class Context:
         o.M, o.fan_in, o.block, o.ctas_per_sm = M, fan_in, block, ctas_per_sm
         o.warm_edges, o.profile, o.host_read = warm_edges, int(bool(profile)), int(bool(host_read))
         o.ap_warm_edges = int(ap_warm_edges)
+        o.warm_block = int(warm_block)
         self._opts = o
         self._ws = None
         with torch.cuda.device(dev):
@@ -277,12 +281,22 @@ class Context:
         _check(self._lib.bridges_autotune(self._h, _stream(stream), _ptr(u), _ptr(v), u.numel(), V, reps, best),
                "bridges_autotune")
         names = ["M", "fan_in", "warm_edges", "block", "us_per_call"]
-        return {names[i]: int(best[i]) for i in range(5)}
+        plan = {names[i]: int(best[i]) for i in range(5)}
+        plan["warm_block"] = self.get_opts()["warm_block"]
+        return plan
 
-    def set_opts(self, M=0, fan_in=0, block=0, ctas_per_sm=0, warm_edges=-1, host_read=False):
+    def get_opts(self):
+        """bridges_ctx_get_opts: the context's current options as a dict."""
+        o = Opts()
+        _check(self._lib.bridges_ctx_get_opts(self._h, ctypes.byref(o)), "bridges_ctx_get_opts")
+        return {name: getattr(o, name) for name, _ in Opts._fields_ if name != "reserved"}
+
+    def set_opts(self, M=0, fan_in=0, block=0, ctas_per_sm=0, warm_edges=-1, host_read=False, warm_block=0,
+                 ap_warm_edges=0):
         o = Opts()
         o.M, o.fan_in, o.block, o.ctas_per_sm, o.warm_edges = M, fan_in, block, ctas_per_sm, warm_edges
         o.host_read = int(bool(host_read))
+        o.warm_block, o.ap_warm_edges = int(warm_block), int(ap_warm_edges)
         _check(self._lib.bridges_ctx_set_opts(self._h, ctypes.byref(o)), "bridges_ctx_set_opts")
 
     def wait_value(self, flag, value: int, max_polls: int, stream=None) -> int:
@@ -325,6 +339,20 @@ class Context:
         _check(na, "bridges_articulation_points")
         _check(nb, "bridges_articulation_points")
         return pts[:na], br[: 2 * nb].view(nb, 2)
+
+    def articulation_points_host(self, u, v, V: int, M: int = 0, stream=None, out=None):
+        """bridges_articulation_points_host: host int32 edge tensors (pinned for full speed) in,
+        a host int32 tensor of the cut vertices out."""
+        for t in (u, v):
+            if not isinstance(t, torch.Tensor) or t.is_cuda or t.dtype != torch.int32 or t.dim() != 1:
+                raise ValueError("edges must be 1-D int32 host tensors")
+        if u.shape != v.shape:
+            raise ValueError("edges_u and edges_v must have equal length")
+        u, v = u.contiguous(), v.contiguous()
+        pts = out if out is not None else torch.empty(max(V, 1), dtype=torch.int32)
+        n = _check(self._lib.bridges_articulation_points_host(self._h, _stream(stream), _ptr(u), _ptr(v), u.numel(),
+                                                              V, M, _ptr(pts)), "bridges_articulation_points_host")
+        return pts[:n]
 
     def articulation_workspace_bytes(self, E: int, V: int, M: int = 0) -> int:
         return int(self._lib.bridges_articulation_workspace_bytes(self._h, E, V, M))

@@ -35,7 +35,8 @@ def tune(ctx, u, v, V: int, path: str = DEFAULT_PATH, reps: int = 3, refresh: bo
     cache = _load(path)
     if not refresh and key in cache:
         plan = cache[key]
-        ctx.set_opts(M=plan["M"], fan_in=plan["fan_in"], block=plan["block"], warm_edges=plan["warm_edges"])
+        ctx.set_opts(M=plan["M"], fan_in=plan["fan_in"], block=plan["block"], warm_edges=plan["warm_edges"],
+                     warm_block=plan.get("warm_block", 0))
         return plan, True
     plan = ctx.autotune(u, v, V, reps=reps)
     cache[key] = plan

@@ -79,7 +79,7 @@ CertPlan plan_for(const bridges_ctx* c, int64_t E, int32_t V, int32_t M) {
   const bridges_opts& o = c->opts;
   int32_t m = M > 0 ? M : o.M;
   return make_plan(E, V, m, o.fan_in, o.block, o.ctas_per_sm, o.warm_edges < 0 ? -1 : (o.warm_edges == 0 ? 0 : o.warm_edges),
-                   c->num_sms, c->smem_optin);
+                   c->num_sms, c->smem_optin, o.warm_block);
 }
 
 // Reads back the stage times of every issued call up to (not including) call index `upto`.
@@ -185,6 +185,62 @@ int64_t check_args(const bridges_ctx* c, const void* u, const void* v, int64_t E
   return BRIDGES_OK;
 }
 
+// Stages host edges for a call: either the device aliases of pinned, mapped buffers (opts.host_read)
+// or copies into the context's device staging area; *dout receives 2*max(V,1) int32 of device
+// output space.  Enqueue only.
+int64_t stage_host_edges(bridges_ctx* c, cudaStream_t s, const int32_t* hu, const int32_t* hv, int64_t E, int32_t V,
+                         const int32_t** ru_out, const int32_t** rv_out, int32_t** dout_out) {
+  // pinned, mapped host memory can be streamed by the kernels in place (no device copy of the
+  // edges: graphs larger than device memory work this way)
+  const int32_t* ru = nullptr;
+  const int32_t* rv = nullptr;
+  bool in_place = false;
+  if (c->opts.host_read && E > 0) {
+    cudaPointerAttributes au{}, av{};
+    if (cudaPointerGetAttributes(&au, hu) == cudaSuccess && cudaPointerGetAttributes(&av, hv) == cudaSuccess &&
+        au.type == cudaMemoryTypeHost && av.type == cudaMemoryTypeHost && au.devicePointer && av.devicePointer) {
+      ru = static_cast<const int32_t*>(au.devicePointer);
+      rv = static_cast<const int32_t*>(av.devicePointer);
+      in_place = true;
+    }
+    cudaGetLastError();
+  }
+  // device staging: the output (2V) and, unless read in place, u and v (E each)
+  const size_t eb = in_place ? 0 : align_up(sizeof(int32_t) * (size_t)std::max<int64_t>(E, 1), 256);
+  const size_t ob = align_up(sizeof(int32_t) * 2 * (size_t)std::max(V, 1), 256);
+  const size_t need = 2 * eb + ob;
+  if (need > c->stage_bytes) {
+    if (c->user_ws) return BRIDGES_ENOMEM;
+    if (c->budget && need + c->ws_bytes > c->budget) return BRIDGES_ENOMEM;
+    if (c->stage) {
+      cudaStreamSynchronize(s);
+      cudaFree(c->stage);
+      c->stage = nullptr;
+      c->stage_bytes = 0;
+    }
+    if (cudaMalloc(&c->stage, need) != cudaSuccess) {
+      cudaGetLastError();
+      return BRIDGES_ENOMEM;
+    }
+    c->stage_bytes = need;
+  }
+  char* base = reinterpret_cast<char*>(c->stage);
+  int32_t* dout = reinterpret_cast<int32_t*>(base + 2 * eb);
+  if (!in_place) {
+    int32_t* du = reinterpret_cast<int32_t*>(base);
+    int32_t* dv = reinterpret_cast<int32_t*>(base + eb);
+    ru = du;
+    rv = dv;
+    if (E > 0 && (cudaMemcpyAsync(du, hu, sizeof(int32_t) * (size_t)E, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+                  cudaMemcpyAsync(dv, hv, sizeof(int32_t) * (size_t)E, cudaMemcpyHostToDevice, s) != cudaSuccess))
+      return cuda_fail(cudaGetLastError());
+  }
+  *ru_out = ru;
+  *rv_out = rv;
+  *dout_out = dout;
+  return BRIDGES_OK;
+}
+
 std::mutex g_default_mu[64];
 bridges_ctx* g_default[64];
 
@@ -286,51 +342,11 @@ int64_t bridges_find_host(bridges_ctx* c, struct CUstream_st* stream, const int3
   if (V > (1 << 30)) return BRIDGES_EINVAL;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   if (cudaSetDevice(c->device) != cudaSuccess) return cuda_fail(cudaGetLastError());
-  // pinned, mapped host memory can be streamed by the kernels in place (no device copy of the
-  // edges: graphs larger than device memory work this way)
   const int32_t* ru = nullptr;
   const int32_t* rv = nullptr;
-  bool in_place = false;
-  if (c->opts.host_read && E > 0) {
-    cudaPointerAttributes au{}, av{};
-    if (cudaPointerGetAttributes(&au, hu) == cudaSuccess && cudaPointerGetAttributes(&av, hv) == cudaSuccess &&
-        au.type == cudaMemoryTypeHost && av.type == cudaMemoryTypeHost && au.devicePointer && av.devicePointer) {
-      ru = static_cast<const int32_t*>(au.devicePointer);
-      rv = static_cast<const int32_t*>(av.devicePointer);
-      in_place = true;
-    }
-    cudaGetLastError();
-  }
-  // device staging: the output (2V) and, unless read in place, u and v (E each)
-  const size_t eb = in_place ? 0 : align_up(sizeof(int32_t) * (size_t)std::max<int64_t>(E, 1), 256);
-  const size_t ob = align_up(sizeof(int32_t) * 2 * (size_t)std::max(V, 1), 256);
-  const size_t need = 2 * eb + ob;
-  if (need > c->stage_bytes) {
-    if (c->user_ws) return BRIDGES_ENOMEM;
-    if (c->budget && need + c->ws_bytes > c->budget) return BRIDGES_ENOMEM;
-    if (c->stage) {
-      cudaStreamSynchronize(s);
-      cudaFree(c->stage);
-      c->stage = nullptr;
-      c->stage_bytes = 0;
-    }
-    if (cudaMalloc(&c->stage, need) != cudaSuccess) {
-      cudaGetLastError();
-      return BRIDGES_ENOMEM;
-    }
-    c->stage_bytes = need;
-  }
-  char* base = reinterpret_cast<char*>(c->stage);
-  int32_t* dout = reinterpret_cast<int32_t*>(base + 2 * eb);
-  if (!in_place) {
-    int32_t* du = reinterpret_cast<int32_t*>(base);
-    int32_t* dv = reinterpret_cast<int32_t*>(base + eb);
-    ru = du;
-    rv = dv;
-    if (E > 0 && (cudaMemcpyAsync(du, hu, sizeof(int32_t) * (size_t)E, cudaMemcpyHostToDevice, s) != cudaSuccess ||
-                  cudaMemcpyAsync(dv, hv, sizeof(int32_t) * (size_t)E, cudaMemcpyHostToDevice, s) != cudaSuccess))
-      return cuda_fail(cudaGetLastError());
-  }
+  int32_t* dout = nullptr;
+  rc = stage_host_edges(c, s, hu, hv, E, V, &ru, &rv, &dout);
+  if (rc) return rc;
   Carved k{};
   rc = run_path(c, s, ru, rv, E, V, M, dout, &k, nullptr);
   if (rc) return rc;
@@ -744,6 +760,30 @@ extern "C" int32_t bridges_autotune(bridges_ctx* c, struct CUstream_st* stream, 
     }
     if (rc) break;
   }
+  // refinement: the warm-up launch's block size for the chosen plan
+  for (int32_t wb : {128, 256, 512, 1024}) {
+    if (rc) break;
+    bridges_opts o = best_o;
+    o.warm_block = wb;
+    o.profile = 0;
+    c->opts = o;
+    Carved k{};
+    int64_t r = run_path(c, s, u, v, E, V, 0, out, &k, nullptr);
+    cudaEventRecord(e0, s);
+    for (int i = 0; i < reps && !r; i++) r = run_path(c, s, u, v, E, V, 0, out, &k, nullptr);
+    cudaEventRecord(e1, s);
+    if (r || cudaEventSynchronize(e1) != cudaSuccess) {
+      rc = r ? (int32_t)r : (int32_t)BRIDGES_ECUDA;
+      break;
+    }
+    float ms = 0;
+    cudaEventElapsedTime(&ms, e0, e1);
+    ms /= reps;
+    if (ms < best_ms) {
+      best_ms = ms;
+      best_o = o;
+    }
+  }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   cudaFree(out);
@@ -757,6 +797,12 @@ extern "C" int32_t bridges_autotune(bridges_ctx* c, struct CUstream_st* stream, 
   best[3] = best_o.block;
   best[4] = (int64_t)(best_ms * 1000.0f);  // microseconds per call
   return rc;
+}
+
+extern "C" int32_t bridges_ctx_get_opts(const bridges_ctx* c, bridges_opts* o) {
+  if (!c || !o) return BRIDGES_EINVAL;
+  *o = c->opts;
+  return BRIDGES_OK;
 }
 
 // Sets the tuning options of a context (e.g. from a cache of autotune results).
@@ -888,6 +934,27 @@ extern "C" int64_t bridges_articulation_points(bridges_ctx* c, struct CUstream_s
       cudaStreamSynchronize(s) != cudaSuccess)
     return cuda_fail(cudaGetLastError());
   return c->h_pinned[0];
+}
+
+extern "C" int64_t bridges_articulation_points_host(bridges_ctx* c, struct CUstream_st* stream, const int32_t* hu,
+                                                    const int32_t* hv, int64_t E, int32_t V, int32_t M,
+                                                    int32_t* out_points_host) {
+  int64_t rc = check_args(c, hu, hv, E, V, out_points_host);
+  if (rc) return rc;
+  if (V > (1 << 30)) return BRIDGES_EINVAL;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  if (cudaSetDevice(c->device) != cudaSuccess) return cuda_fail(cudaGetLastError());
+  const int32_t* ru = nullptr;
+  const int32_t* rv = nullptr;
+  int32_t* dout = nullptr;
+  rc = stage_host_edges(c, s, hu, hv, E, V, &ru, &rv, &dout);
+  if (rc) return rc;
+  const int64_t n = bridges_articulation_points(c, stream, ru, rv, E, V, M, dout, nullptr, nullptr);
+  if (n <= 0) return n;
+  if (cudaMemcpyAsync(out_points_host, dout, sizeof(int32_t) * (size_t)n, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      cudaStreamSynchronize(s) != cudaSuccess)
+    return cuda_fail(cudaGetLastError());
+  return n;
 }
 
 extern "C" int64_t bridges_articulation_workspace_bytes(const bridges_ctx* c, int64_t E, int32_t V, int32_t M) {

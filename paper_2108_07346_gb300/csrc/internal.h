@@ -32,6 +32,7 @@ struct CertPlan {
   int32_t f;
   int32_t G;       // blocks per job in the forest pass
   int32_t block;   // threads per block in the forest pass
+  int32_t warm_block;  // threads per block of its warm-up launch
   int64_t warm;    // edges per partition certified before the snapshot (>= partition: no cache)
   bool cache;      // label snapshot used (2V bytes of shared memory fit)
 };
@@ -121,7 +122,7 @@ void cert_leaves(const Launch& L, const CertPlan& p, const CertBufs& b, const in
 void cert_merge(const Launch& L, const CertPlan& p, const CertBufs& b);
 // Plan for (E, V, M) on this device.
 CertPlan make_plan(int64_t E, int32_t V, int32_t M, int32_t fan_in, int32_t block, int32_t ctas_per_sm,
-                   int64_t warm, int num_sms, size_t smem_optin);
+                   int64_t warm, int num_sms, size_t smem_optin, int32_t warm_block = 0);
 // Workspace bytes of the certificate stage.
 size_t cert_bytes(const CertPlan& p);
 CertBufs carve_cert(void* base, const CertPlan& p);

@@ -147,3 +147,16 @@ def test_user_workspace(cuda_lib):
     c = cuda_lib.Context(device="cuda:0", workspace_bytes=need)
     assert c.articulation_points(dev(g.u), dev(g.v), g.V, 2).cpu().numpy().tolist() == \
         oracle.articulation_points(g.u, g.v, g.V).tolist()
+
+
+def test_host_entry(cuda_lib):
+    """bridges_articulation_points_host: pinned and pageable host input, copied or read in place."""
+    g = graphgen.workload("mid")
+    ref = oracle.articulation_points(g.u, g.v, g.V).tolist()
+    hu = torch.from_numpy(np.array(g.u)).pin_memory()
+    hv = torch.from_numpy(np.array(g.v)).pin_memory()
+    for host_read in (False, True):
+        c = cuda_lib.Context(device="cuda:0", host_read=host_read)
+        assert c.articulation_points_host(hu, hv, g.V, 4).numpy().tolist() == ref
+        assert c.articulation_points_host(torch.from_numpy(np.array(g.u)), torch.from_numpy(np.array(g.v)), g.V,
+                                          2).numpy().tolist() == ref
