@@ -33,9 +33,9 @@ UNIT = "GE/s"
 # DRAM bytes (read + write) per streamed edge, from full-size single-pass ncu captures on the large
 # workload (profiles/launch_list_large_dense.md, profiles/block_pass_large_dense.md); each is valid
 # only for the kernel sources it was measured on (hash of those sources).
-#   forest pass, M = 1: 9.226 GB read + 7.2 MB written for 1,072,703,284 streamed edges
+#   forest pass, M = 1: 9.313 GB read + 7.3 MB written for 1,072,703,284 streamed edges
 #   block pass stream: 9.494 GB read + 10.8 MB written for 1,073,547,340 streamed edges
-TRAFFIC = {"certify_sha": "57e6c29f07bc86dc", "bytes_per_edge": 8.6078}
+TRAFFIC = {"certify_sha": "a3aadd48ba1c58f6", "bytes_per_edge": 8.6815}
 AP_TRAFFIC = {"blocks_sha": "e40f3ec967d1ea6b", "bytes_per_edge": 8.8536}
 
 
