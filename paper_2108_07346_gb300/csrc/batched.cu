@@ -10,7 +10,9 @@
 // bridge stage.  Nothing waits on another block, so there is no spin anywhere.
 //
 // The bridge stage is the same Euler-tour / preorder-range test as final.cu, on 16-bit arrays
-// with __syncthreads between phases, and a bitonic sort of the packed (a << 12 | b) keys.
+// with __syncthreads between phases (list ranking four hops per round), then a rank sort of the
+// packed (a << 12 | b) keys (bitonic above 1,024 bridges).  A graph's fixed cost is its block
+// barriers, so the stage keeps their number low.
 #include <algorithm>
 #include <cstring>
 #include <mutex>
@@ -168,6 +170,46 @@ __device__ int32_t block_scan16(uint16_t* a, int32_t n, int32_t* red) {
   return tot;
 }
 
+// The same for two arrays of equal length at once (one pair of block barriers for both).
+__device__ void block_scan16_pair(uint16_t* a, uint16_t* b, int32_t n, int32_t* red) {
+  __shared__ int32_t red_b[kW];
+  const int per = (n + kT - 1) / kT;
+  const int lo = min(n, (int)threadIdx.x * per), hi = min(n, lo + per);
+  int32_t sa = 0, sb = 0;
+  for (int i = lo; i < hi; i++) {
+    sa += a[i];
+    sb += b[i];
+  }
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  int32_t ia = sa, ib = sb;
+  for (int o = 1; o < 32; o <<= 1) {
+    const int32_t ya = __shfl_up_sync(kFull, ia, o), yb = __shfl_up_sync(kFull, ib, o);
+    if (lane >= o) {
+      ia += ya;
+      ib += yb;
+    }
+  }
+  if (lane == 31) {
+    red[w] = ia;
+    red_b[w] = ib;
+  }
+  __syncthreads();
+  int32_t ba = 0, bb = 0;
+  for (int k = 0; k < w; k++) {
+    ba += red[k];
+    bb += red_b[k];
+  }
+  int32_t ra = ba + ia - sa, rb = bb + ib - sb;
+  for (int i = lo; i < hi; i++) {
+    const int32_t va = a[i], vb = b[i];
+    a[i] = (uint16_t)ra;
+    b[i] = (uint16_t)rb;
+    ra += va;
+    rb += vb;
+  }
+  __syncthreads();
+}
+
 // Offers edge (a, b) to F, then F'; appends winners (warp-aggregated).  Every lane calls it.
 __device__ __forceinline__ void s_settle(const Smem& S, bool need, int32_t a, int32_t b, int32_t* n1, int32_t* n2,
                                          int32_t V) {
@@ -247,20 +289,13 @@ __device__ __noinline__ void s_offer_misses(const Smem& S, uint32_t m, const int
   }
 }
 
-// Certifies edges [lo, hi) of (u, v) into S.F1 / S.F2 (appending to *n1 / *n2); ids outside
-// [0, V) set *err.  A warm-up prefix goes edge by edge, then both union-finds are flattened and
-// the rest streams with 16-byte loads (when u and v share their alignment), four units of four
-// edges per thread in flight, a per-thread miss mask and one warp vote per tile.
-__device__ void s_certify_range(const Smem& S, const int32_t* __restrict__ u, const int32_t* __restrict__ v,
-                                int64_t lo, int64_t hi, int32_t V, int32_t* n1, int32_t* n2, int32_t* err) {
+// Certifies edges [lo, hi) of (u, v) with 16-byte loads when u and v share their alignment (a
+// scalar head and tail otherwise), four units of four edges per thread in flight, a per-thread
+// miss mask (the ends' F' parents differ, or an id is out of range) and one warp vote per tile.
+__device__ __forceinline__ void s_certify_vec(const Smem& S, const int32_t* __restrict__ u, const int32_t* __restrict__ v, int64_t lo,
+                              int64_t hi, int32_t V, int32_t* n1, int32_t* n2, int32_t* err) {
   constexpr int U = 4;
-  const int64_t warm = min(hi - lo, (int64_t)8 * V + 2048);
-  s_certify_scalar(S, u, v, lo, lo + warm, V, n1, n2, err);
-  lo += warm;
   if (lo >= hi) return;
-  s_flatten(S.P1, V);
-  s_flatten(S.P2, V);
-  // head up to 16-byte alignment of u (v must share it for the vector body)
   const bool same = ((reinterpret_cast<uintptr_t>(u) ^ reinterpret_cast<uintptr_t>(v)) & 15) == 0;
   int64_t body = lo;
   if (same) {
@@ -306,6 +341,22 @@ __device__ void s_certify_range(const Smem& S, const int32_t* __restrict__ u, co
     if (__any_sync(kFull, m != 0)) s_offer_misses(S, m, ub, vb, base, V, n1, n2, err);
   }
   s_certify_scalar(S, u, v, body + 4 * nunits, hi, V, n1, n2, err);
+}
+
+// Certifies edges [lo, hi) of (u, v) into S.F1 / S.F2 (appending to *n1 / *n2); ids outside
+// [0, V) set *err.  A warm-up prefix goes edge by edge (most of its edges still link; a vector
+// tile's miss loop would run as long as its busiest lane), then both union-finds are flattened,
+// so that "equal F' parents" afterwards recognises nearly every pair inside one F' component,
+// and the rest streams through the vector loop.
+__device__ void s_certify_range(const Smem& S, const int32_t* __restrict__ u, const int32_t* __restrict__ v,
+                                int64_t lo, int64_t hi, int32_t V, int32_t* n1, int32_t* n2, int32_t* err) {
+  const int64_t warm = min(hi - lo, (int64_t)8 * V + 2048);
+  s_certify_scalar(S, u, v, lo, lo + warm, V, n1, n2, err);
+  lo += warm;
+  if (lo >= hi) return;
+  s_flatten(S.P1, V);
+  s_flatten(S.P2, V);
+  s_certify_vec(S, u, v, lo, hi, V, n1, n2, err);
 }
 
 // Certifies packed edges (a | b << 16) of a global list.
@@ -366,35 +417,37 @@ __device__ int32_t s_bridges(const Smem& S, int32_t V, int32_t nt, int32_t nx, i
     S.rnk[i] = s == kNone16 ? 0 : 1;
   }
   __syncthreads();
-  // list ranking: each thread owns arcs tid, tid + kT, ... (<= 8)
+  // list ranking by pointer jumping, four hops per round (shared-memory loads are cheap, the
+  // block barriers between rounds are not): ceil(log4 n) rounds, double-buffered in the P1 and F
+  // regions (both free now: the roots are known and the adjacency is built)
   {
     int rounds = 0;
-    while ((1 << rounds) < max(narcs, 1)) rounds++;
+    while ((1 << (2 * rounds)) < max(narcs, 1)) rounds++;
+    uint16_t* sa = S.succ;
+    uint16_t* ra = S.rnk;
+    uint16_t* sb = reinterpret_cast<uint16_t*>(S.P1);
+    uint16_t* rb = reinterpret_cast<uint16_t*>(S.F1);
     for (int r = 0; r < rounds; r++) {
-      uint16_t ns[kAmax / kT], nr[kAmax / kT];
+      for (int i = tid; i < narcs; i += kT) {
+        uint16_t s = sa[i], acc = ra[i];
 #pragma unroll
-      for (int k = 0; k < kAmax / kT; k++) {
-        const int i = tid + k * kT;
-        if (i < narcs) {
-          const uint16_t s = S.succ[i];
-          if (s != kNone16) {
-            nr[k] = (uint16_t)(S.rnk[i] + S.rnk[s]);
-            ns[k] = S.succ[s];
-          } else {
-            nr[k] = S.rnk[i];
-            ns[k] = kNone16;
-          }
+        for (int h = 0; h < 3 && s != kNone16; h++) {
+          acc = (uint16_t)(acc + ra[s]);
+          s = sa[s];
         }
+        rb[i] = acc;
+        sb[i] = s;
       }
       __syncthreads();
-#pragma unroll
-      for (int k = 0; k < kAmax / kT; k++) {
-        const int i = tid + k * kT;
-        if (i < narcs) {
-          S.succ[i] = ns[k];
-          S.rnk[i] = nr[k];
-        }
-      }
+      uint16_t* t = sa;
+      sa = sb;
+      sb = t;
+      t = ra;
+      ra = rb;
+      rb = t;
+    }
+    if (ra != S.rnk) {
+      for (int i = tid; i < narcs; i += kT) S.rnk[i] = ra[i];
       __syncthreads();
     }
   }
@@ -409,8 +462,7 @@ __device__ int32_t s_bridges(const Smem& S, int32_t V, int32_t nt, int32_t nx, i
     S.vbase[x] = nv;
   }
   __syncthreads();
-  block_scan16(S.aoff, V + 1, red);
-  block_scan16(S.vbase, V + 1, red);
+  block_scan16_pair(S.aoff, S.vbase, V + 1, red);
   // tour positions; down arcs (dflag reuses succ, free after ranking)
   for (int i = tid; i <= narcs; i += kT) S.dflag[i] = 0;
   __syncthreads();
@@ -501,6 +553,19 @@ __device__ int32_t s_bridges(const Smem& S, int32_t V, int32_t nt, int32_t nx, i
   }
   __syncthreads();
   const int32_t n = min(*sh, max(V - 1, 0));
+  if (n <= kT) {
+    // rank sort: keys are unique (a bridge has no parallel copy), every thread ranks one key
+    // against all n with broadcast reads; one pass, no barrier
+    if (tid < n) {
+      const uint32_t mine = S.keys[tid];
+      int32_t rank = 0;
+      for (int j = 0; j < n; j++) rank += S.keys[j] < mine;
+      out[2 * rank] = (int32_t)(mine >> 12);
+      out[2 * rank + 1] = (int32_t)(mine & 0xfff);
+    }
+    __syncthreads();
+    return n;
+  }
   // bitonic sort of n keys (padded to a power of two with ~0)
   int np = 1;
   while (np < n) np <<= 1;
