@@ -298,6 +298,7 @@ def run_native(args, world, rank, local):
         roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                 "traffic": traffic, "kernel": "leaf_kernel<cache, vec> (partition forest pass)",
                 "algorithmic_bytes": 8 * forest_edges, "peak_kind": peak_kind,
+                "frac_of_nominal_7900": achieved / 7900.0,
                 "stage_ms_mean": {k: statistics.mean(h[k] for h in hist) for k in hist[0]}}
 
     # end to end through the public API from pinned host buffers (copies inside the timed region)
@@ -343,6 +344,10 @@ def run_native(args, world, rank, local):
                        "bridges": n_found, "bridges_equal_planted": correct,
                        "autotuned_plan": plan, "stage_ms_by_M": sweep},
             "clocks": ck, "e2e": e2e, "gpu_launches": launches, "roofline": roof, "cpu_baseline": cpu,
+            "per_call_ms": None if not hist else {
+                "median": statistics.median(h["total"] for h in hist), "min": min(h["total"] for h in hist),
+                "max": max(h["total"] for h in hist), "calls": len(hist),
+                "note": "CUDA-event time of each of the last timed calls (stage events)"},
         }
         print(json.dumps(line), flush=True)
     if world > 1:

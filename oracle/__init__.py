@@ -33,6 +33,8 @@ def _load():
             f.argtypes = [_I32P, _I32P, ctypes.c_int64, ctypes.c_int32, _I32P]
         lib.oracle_bridges.restype = ctypes.c_int64
         lib.oracle_bridges.argtypes = [_I32P, _I32P, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32, _I32P]
+        lib.oracle_certificate_stream.restype = ctypes.c_int64
+        lib.oracle_certificate_stream.argtypes = [_I32P, _I32P, ctypes.c_int64, ctypes.c_int32, _I32P, _I32P]
         lib.oracle_certificate.restype = ctypes.c_int64
         lib.oracle_certificate.argtypes = [_I32P, _I32P, ctypes.c_int64, ctypes.c_int32, _I32P, _I32P]
         lib.oracle_pipeline_cert.restype = ctypes.c_int64
@@ -105,6 +107,16 @@ def certificate(u, v, V: int):
     f1 = np.empty(max(2 * V, 1), np.uint8)
     k = _check(_load().oracle_certificate(u.ctypes.data, v.ctypes.data, u.shape[0], V, ids.ctypes.data,
                                           f1.ctypes.data))
+    return ids[:k].copy(), f1[:k].astype(bool)
+
+
+def certificate_stream(u, v, V: int):
+    """Alg. 2 as one streaming pass (F, else F'): (edge ids of S in list order, F flags)."""
+    u, v = _edges(u, v)
+    ids = np.empty(max(2 * V, 1), np.int64)
+    f1 = np.empty(max(2 * V, 1), np.uint8)
+    k = _check(_load().oracle_certificate_stream(u.ctypes.data, v.ctypes.data, u.shape[0], V, ids.ctypes.data,
+                                                 f1.ctypes.data))
     return ids[:k].copy(), f1[:k].astype(bool)
 
 

@@ -15,6 +15,7 @@
  *                           (phase 0), then phases q = 1..ceil(log2 M) replace X_i by the
  *                           certificate of X_i u X_{i+2^(q-1)} for i = 0 mod 2^q (absent
  *                           partners are empty); X_0 is the final certificate.
+ *   oracle_certificate_stream   Alg. 2 as one streaming pass (F, else F'), the GPU's form.
  *   oracle_dfs_bridges      Alg. 1 (Sec. 4.A), Tarjan's disc/low test, written iteratively.
  *   oracle_bridges          Sec. 3 end to end: oracle_pipeline_cert then Alg. 1 on X_0.
  *   oracle_chain_bridges    Independent check: Schmidt's chain decomposition (IPL 113, 2013):
@@ -180,6 +181,32 @@ int64_t oracle_certificate(const int32_t* u, const int32_t* v, int64_t E, int32_
   uf_free(&f1);
   uf_free(&f2);
   free(in_f);
+  return k;
+}
+
+/* Alg. 2 in one streaming pass, as the GPU runs it: each edge in list order is offered to F and,
+ * if F rejects it, to F' at once.  The edges F rejects and their order are the same as in the
+ * two-pass form (F is the same forest), so the certificate is identical; this form exists to pin
+ * that equivalence.  Same output convention as oracle_certificate except that S is listed in
+ * list order with its F flags. */
+int64_t oracle_certificate_stream(const int32_t* u, const int32_t* v, int64_t E, int32_t V, int64_t* out_ids,
+                                  uint8_t* out_f1) {
+  if (E < 0 || V < 0) return -1;
+  if (check_ids(u, v, E, V)) return -1;
+  uf_t f1, f2;
+  if (uf_init(&f1, V) || uf_init(&f2, V)) return -2;
+  int64_t k = 0;
+  for (int64_t e = 0; e < E; e++) {
+    if (uf_union(&f1, u[e], v[e])) {
+      out_ids[k] = e;
+      out_f1[k++] = 1;
+    } else if (uf_union(&f2, u[e], v[e])) {
+      out_ids[k] = e;
+      out_f1[k++] = 0;
+    }
+  }
+  uf_free(&f1);
+  uf_free(&f2);
   return k;
 }
 

@@ -338,3 +338,16 @@ def test_arbitrary_forests_do_not_keep_articulation_points():
             found = True
             break
     assert found
+
+
+def test_streaming_certificate_equals_two_pass():
+    """Alg. 2 taken as one streaming pass (each edge to F, else to F') -- the GPU's form -- gives
+    the same certificate as the two passes (F over the list, then F' over what F rejected)."""
+    for t in range(300):
+        rng = np.random.default_rng(15000 + t)
+        V = int(rng.integers(1, 50))
+        E = int(rng.integers(0, 8 * V))
+        u, v = graphgen.random_multigraph(15000 + t, V, E)
+        ids2, f2 = oracle.certificate(u, v, V)
+        ids1, f1 = oracle.certificate_stream(u, v, V)
+        assert sorted(zip(ids1.tolist(), f1.tolist())) == sorted(zip(ids2.tolist(), f2.tolist())), t
