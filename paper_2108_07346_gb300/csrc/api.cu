@@ -576,8 +576,12 @@ int64_t plan_batch_tasks(std::vector<BatchTask>& graphs, int64_t split, std::vec
     }
     if (np > 1) slot += (int64_t)np * (2 + 2 * (int64_t)g.V);
   }
-  std::stable_sort(tasks.begin(), tasks.end(),
-                   [](const BatchTask& x, const BatchTask& y) { return x.hi - x.lo > y.hi - y.lo; });
+  // whole-block tasks first, then the ones two of which share a block; largest first in each
+  std::stable_sort(tasks.begin(), tasks.end(), [](const BatchTask& x, const BatchTask& y) {
+    const bool bx = batch_task_is_big(x), by = batch_task_is_big(y);
+    if (bx != by) return bx;
+    return x.hi - x.lo > y.hi - y.lo;
+  });
   return slot;
 }
 
@@ -601,6 +605,16 @@ int64_t launch_batch_tasks(bridges_ctx* c, cudaStream_t s, const std::vector<Bat
   A.gerr = reinterpret_cast<int32_t*>(d + L.gerr);
   A.slots = reinterpret_cast<uint32_t*>(d + L.slots);
   A.G = G;
+  // tasks up to the first small one run on whole blocks; a caller's unordered list runs every
+  // task on whole blocks
+  int32_t nbig = 0;
+  while (nbig < (int32_t)tasks.size() && batch_task_is_big(tasks[nbig])) nbig++;
+  for (size_t i = nbig; i < tasks.size(); i++)
+    if (batch_task_is_big(tasks[i])) {
+      nbig = (int32_t)tasks.size();
+      break;
+    }
+  A.nbig = nbig;
   A.slot_words = c->b_slot_cap;
   std::memcpy(h + L.s_args, &A, sizeof(A));
   const int32_t nt = (int32_t)tasks.size();

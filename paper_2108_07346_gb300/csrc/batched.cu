@@ -10,9 +10,11 @@
 // bridge stage.  Nothing waits on another block, so there is no spin anywhere.
 //
 // The bridge stage is the same Euler-tour / preorder-range test as final.cu, on 16-bit arrays
-// with __syncthreads between phases (list ranking four hops per round), then a rank sort of the
-// packed (a << 12 | b) keys (bitonic above 1,024 bridges).  A graph's fixed cost is its block
-// barriers, so the stage keeps their number low.
+// with barriers between phases (list ranking four hops per round), then a rank sort of the
+// packed (a << 12 | b) keys (bitonic above 1,024 bridges).  A graph's fixed cost is its barriers,
+// so the stage keeps their number low, and graphs of up to 2,048 vertices run two per block: the
+// block splits into two 512-thread groups with their own half of shared memory and their own
+// named barrier, so that one graph's barrier waits overlap with the other's work.
 #include <algorithm>
 #include <cstring>
 #include <mutex>
@@ -26,24 +28,41 @@ namespace bridges {
 
 namespace {
 
-constexpr int kT = 1024;          // threads per block
-constexpr int kW = kT / 32;
-constexpr int kVmax = kBatchVmax;  // 4096
-constexpr int kAmax = 2 * kVmax;  // arcs
+constexpr int kT = 1024;           // threads per block
+constexpr int kVmax = kBatchVmax;  // 4096: a whole block's graph
+constexpr int kHalfT = kT / 2;     // threads of a half-block group
+constexpr int kHalfVmax = kVmax / 2;  // 2048: a half-block group's graph
 constexpr uint16_t kNone16 = 0xffff;
 
-// shared-memory regions (bytes), each a multiple of 16
-constexpr int kR0 = 16448;  // P1 (int32[V]); later aoff (u16[V+1]) + vbase (u16[V+1])
-constexpr int kR1 = 16448;  // P2 (int32[V]); later root (u16[V]) + cur (u16[V])
-constexpr int kR2 = 16384;  // F list (u32[V]); later bridge keys (u32[V])
-constexpr int kR3 = 16384;  // F' list (u32[V])
-constexpr int kR4 = 8208;   // off (u16[V+1])
-constexpr int kR5 = 16384;  // dst (u16[2V]); later lo (int32[V])
-constexpr int kR6 = 16384;  // twin (u16[2V]); later hi (int32[V])
-constexpr int kR7 = 16400;  // succ (u16[2V]); later dflag / dscan (u16[2V+1])
-constexpr int kR8 = 16384;  // rnk (u16[2V])
-constexpr int kR9 = 24576;  // pre, sz, par (u16[V] each)
-constexpr int kSmem = kR0 + kR1 + kR2 + kR3 + kR4 + kR5 + kR6 + kR7 + kR8 + kR9;
+constexpr int a16(int x) { return (x + 15) & ~15; }
+// Shared-memory layout for graphs of up to VM vertices (bytes, each region a multiple of 16):
+//   R0  P1 (int32[V]); later aoff + vbase (u16[V+1] each)
+//   R1  P2 (int32[V]); later root + cur (u16[V+2] each)
+//   R2  F list (u32[V]); later bridge keys (u32[V])
+//   R3  F' list (u32[V])
+//   R4  off (u16[V+2]); later chunk minima / maxima
+//   R5  dst (u16[2V]); later lo (int32[V])
+//   R6  twin (u16[2V]); later hi (int32[V])
+//   R7  succ (u16[2V]); later dflag / dscan (u16[2V+1])
+//   R8  rnk (u16[2V])
+//   R9  pre, sz, par (u16[V] each)
+template <int VM>
+struct Layout {
+  static constexpr int kU16 = a16(2 * (VM + 16));  // a u16[V+2] array
+  static constexpr int R0 = 2 * kU16 > 4 * VM ? 2 * kU16 : 4 * VM;
+  static constexpr int R1 = R0;
+  static constexpr int R2 = 4 * VM;
+  static constexpr int R3 = 4 * VM;
+  static constexpr int R4 = kU16 > VM / 4 ? kU16 : VM / 4;
+  static constexpr int R5 = 4 * VM;
+  static constexpr int R6 = 4 * VM;
+  static constexpr int R7 = a16(2 * (2 * VM + 8));
+  static constexpr int R8 = 4 * VM;
+  static constexpr int R9 = 6 * VM;
+  static constexpr int kBytes = R0 + R1 + R2 + R3 + R4 + R5 + R6 + R7 + R8 + R9;
+};
+constexpr int kSmem = Layout<kVmax>::kBytes > 2 * Layout<kHalfVmax>::kBytes ? Layout<kVmax>::kBytes
+                                                                               : 2 * Layout<kHalfVmax>::kBytes;
 
 struct Smem {
   int32_t* P1;
@@ -68,40 +87,63 @@ struct Smem {
   uint16_t* par;
 };
 
+template <int VM>
 __device__ Smem carve_smem(char* base) {
+  using L = Layout<VM>;
   Smem s;
   char* c = base;
   s.P1 = reinterpret_cast<int32_t*>(c);
   s.aoff = reinterpret_cast<uint16_t*>(c);
-  s.vbase = reinterpret_cast<uint16_t*>(c + 8224);
-  c += kR0;
+  s.vbase = reinterpret_cast<uint16_t*>(c + L::kU16);
+  c += L::R0;
   s.P2 = reinterpret_cast<int32_t*>(c);
   s.root = reinterpret_cast<uint16_t*>(c);
-  s.cur = reinterpret_cast<uint16_t*>(c + 8224);
-  c += kR1;
+  s.cur = reinterpret_cast<uint16_t*>(c + L::kU16);
+  c += L::R1;
   s.F1 = reinterpret_cast<uint32_t*>(c);
   s.keys = s.F1;
-  c += kR2;
+  c += L::R2;
   s.F2 = reinterpret_cast<uint32_t*>(c);
-  c += kR3;
+  c += L::R3;
   s.off = reinterpret_cast<uint16_t*>(c);
-  c += kR4;
+  c += L::R4;
   s.dst = reinterpret_cast<uint16_t*>(c);
   s.lo = reinterpret_cast<int32_t*>(c);
-  c += kR5;
+  c += L::R5;
   s.twin = reinterpret_cast<uint16_t*>(c);
   s.hi = reinterpret_cast<int32_t*>(c);
-  c += kR6;
+  c += L::R6;
   s.succ = reinterpret_cast<uint16_t*>(c);
   s.dflag = s.succ;
-  c += kR7;
+  c += L::R7;
   s.rnk = reinterpret_cast<uint16_t*>(c);
-  c += kR8;
+  c += L::R8;
   s.pre = reinterpret_cast<uint16_t*>(c);
-  s.sz = s.pre + kVmax;
-  s.par = s.sz + kVmax;
+  s.sz = s.pre + VM;
+  s.par = s.sz + VM;
   return s;
 }
+
+// A group of NT threads (whole block, or one half) working on one task: its thread index and
+// its barrier (0 = the block's; 1 and 2 = the halves' named barriers).
+template <int NT>
+struct Grp {
+  int tid;
+  int bar;
+  __device__ __forceinline__ void sync() const {
+    if (NT == kT)
+      __syncthreads();
+    else
+      asm volatile("bar.sync %0, %1;" ::"r"(bar), "r"(NT) : "memory");
+  }
+};
+
+// Per-group scalars in shared memory.
+struct GroupShared {
+  int32_t red[kT / 32];
+  int32_t red_b[kT / 32];
+  int32_t task, n1, n2, err, flag, sh;
+};
 
 // 16-bit counters packed two to a 32-bit word (shared-memory atomics are 32-bit).
 __device__ __forceinline__ uint16_t inc16(uint16_t* a, int i) {
@@ -141,22 +183,23 @@ __device__ __forceinline__ bool s_link(int32_t* P, int32_t a, int32_t b) {
   }
 }
 
-// Block-wide exclusive scan of n (<= 2*kT*... ) u16 values in place; returns the total.
-__device__ int32_t block_scan16(uint16_t* a, int32_t n, int32_t* red) {
-  const int per = (n + kT - 1) / kT;  // contiguous items per thread
-  const int lo = min(n, (int)threadIdx.x * per), hi = min(n, lo + per);
+// Block-wide exclusive scan of n (<= 2*NT*... ) u16 values in place; returns the total.
+template <int NT>
+__device__ int32_t block_scan16(const Grp<NT>& G, uint16_t* a, int32_t n, int32_t* red) {
+  const int per = (n + NT - 1) / NT;  // contiguous items per thread
+  const int lo = min(n, G.tid * per), hi = min(n, lo + per);
   int32_t s = 0;
   for (int i = lo; i < hi; i++) s += a[i];
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int lane = G.tid & 31, w = G.tid >> 5;
   int32_t incl = s;
   for (int o = 1; o < 32; o <<= 1) {
     const int32_t y = __shfl_up_sync(kFull, incl, o);
     if (lane >= o) incl += y;
   }
   if (lane == 31) red[w] = incl;
-  __syncthreads();
+  G.sync();
   int32_t base = 0, tot = 0;
-  for (int k = 0; k < kW; k++) {
+  for (int k = 0; k < (NT / 32); k++) {
     if (k < w) base += red[k];
     tot += red[k];
   }
@@ -166,21 +209,22 @@ __device__ int32_t block_scan16(uint16_t* a, int32_t n, int32_t* red) {
     a[i] = (uint16_t)run;
     run += v;
   }
-  __syncthreads();
+  G.sync();
   return tot;
 }
 
 // The same for two arrays of equal length at once (one pair of block barriers for both).
-__device__ void block_scan16_pair(uint16_t* a, uint16_t* b, int32_t n, int32_t* red) {
-  __shared__ int32_t red_b[kW];
-  const int per = (n + kT - 1) / kT;
-  const int lo = min(n, (int)threadIdx.x * per), hi = min(n, lo + per);
+template <int NT>
+__device__ void block_scan16_pair(const Grp<NT>& G, uint16_t* a, uint16_t* b, int32_t n, int32_t* red,
+                                  int32_t* red_b) {
+  const int per = (n + NT - 1) / NT;
+  const int lo = min(n, G.tid * per), hi = min(n, lo + per);
   int32_t sa = 0, sb = 0;
   for (int i = lo; i < hi; i++) {
     sa += a[i];
     sb += b[i];
   }
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int lane = G.tid & 31, w = G.tid >> 5;
   int32_t ia = sa, ib = sb;
   for (int o = 1; o < 32; o <<= 1) {
     const int32_t ya = __shfl_up_sync(kFull, ia, o), yb = __shfl_up_sync(kFull, ib, o);
@@ -193,7 +237,7 @@ __device__ void block_scan16_pair(uint16_t* a, uint16_t* b, int32_t n, int32_t* 
     red[w] = ia;
     red_b[w] = ib;
   }
-  __syncthreads();
+  G.sync();
   int32_t ba = 0, bb = 0;
   for (int k = 0; k < w; k++) {
     ba += red[k];
@@ -207,7 +251,7 @@ __device__ void block_scan16_pair(uint16_t* a, uint16_t* b, int32_t n, int32_t* 
     ra += va;
     rb += vb;
   }
-  __syncthreads();
+  G.sync();
 }
 
 // Offers edge (a, b) to F, then F'; appends winners (warp-aggregated).  Every lane calls it.
@@ -217,7 +261,7 @@ __device__ __forceinline__ void s_settle(const Smem& S, bool need, int32_t a, in
   int r = 0;
   if (need) r = s_link(S.P1, a, b) ? 1 : (s_link(S.P2, a, b) ? 2 : 0);
   const unsigned m1 = __ballot_sync(kFull, r == 1), m2 = __ballot_sync(kFull, r == 2);
-  const int lane = threadIdx.x & 31;
+  const int lane = threadIdx.x & 31;  // groups are whole warps
   int32_t b1 = 0, b2 = 0;
   if (m1 && lane == __ffs(m1) - 1) b1 = atomicAdd(n1, __popc(m1));
   if (m2 && lane == __ffs(m2) - 1) b2 = atomicAdd(n2, __popc(m2));
@@ -235,9 +279,10 @@ __device__ __forceinline__ void s_settle(const Smem& S, bool need, int32_t a, in
 
 // Points every vertex straight at its root (no link runs meanwhile), so that afterwards "equal
 // parents" recognises every pair that shares a set.
-__device__ __forceinline__ void s_flatten(int32_t* P, int32_t V) {
-  __syncthreads();
-  for (int x = threadIdx.x; x < V; x += kT) {
+template <int NT>
+__device__ __forceinline__ void s_flatten(const Grp<NT>& G, int32_t* P, int32_t V) {
+  G.sync();
+  for (int x = G.tid; x < V; x += NT) {
     int32_t r = x, p = P[x];
     while (p != r) {
       r = p;
@@ -245,15 +290,16 @@ __device__ __forceinline__ void s_flatten(int32_t* P, int32_t V) {
     }
     P[x] = r;
   }
-  __syncthreads();
+  G.sync();
 }
 
 // Scalar certification of edges [lo, hi): every lane takes one edge per step.
-__device__ void s_certify_scalar(const Smem& S, const int32_t* __restrict__ u, const int32_t* __restrict__ v,
+template <int NT>
+__device__ void s_certify_scalar(const Grp<NT>& G, const Smem& S, const int32_t* __restrict__ u, const int32_t* __restrict__ v,
                                  int64_t lo, int64_t hi, int32_t V, int32_t* n1, int32_t* n2, int32_t* err) {
   volatile int32_t* P2 = S.P2;
-  for (int64_t t0 = lo; t0 < hi; t0 += kT) {
-    const int64_t i = t0 + threadIdx.x;
+  for (int64_t t0 = lo; t0 < hi; t0 += NT) {
+    const int64_t i = t0 + G.tid;
     const bool valid = i < hi;
     const int32_t a = valid ? __ldcs(u + i) : 0, b = valid ? __ldcs(v + i) : 0;
     bool need = valid;
@@ -267,8 +313,9 @@ __device__ void s_certify_scalar(const Smem& S, const int32_t* __restrict__ u, c
 }
 
 // The lanes' flagged edges of one tile go through the union-finds (bit 4k+c of m: element
-// 4*(base + k*kT + tid) + c of ub / vb).  Out of line: rare after the flatten.
-__device__ __noinline__ void s_offer_misses(const Smem& S, uint32_t m, const int32_t* __restrict__ ub,
+// 4*(base + k*NT + tid) + c of ub / vb).  Out of line: rare after the flatten.
+template <int NT>
+__device__ __noinline__ void s_offer_misses(const Grp<NT>& G, const Smem& S, uint32_t m, const int32_t* __restrict__ ub,
                                             const int32_t* __restrict__ vb, int64_t base, int32_t V, int32_t* n1,
                                             int32_t* n2, int32_t* err) {
   while (__any_sync(kFull, m != 0)) {
@@ -277,7 +324,7 @@ __device__ __noinline__ void s_offer_misses(const Smem& S, uint32_t m, const int
     if (m) {
       const int bit = __ffs(m) - 1;
       m &= m - 1;
-      const int64_t e = 4 * (base + (int64_t)(bit >> 2) * kT + threadIdx.x) + (bit & 3);
+      const int64_t e = 4 * (base + (int64_t)(bit >> 2) * NT + G.tid) + (bit & 3);
       a = ub[e];
       b = vb[e];
       if ((uint32_t)a >= (uint32_t)V || (uint32_t)b >= (uint32_t)V)
@@ -292,7 +339,8 @@ __device__ __noinline__ void s_offer_misses(const Smem& S, uint32_t m, const int
 // Certifies edges [lo, hi) of (u, v) with 16-byte loads when u and v share their alignment (a
 // scalar head and tail otherwise), four units of four edges per thread in flight, a per-thread
 // miss mask (the ends' F' parents differ, or an id is out of range) and one warp vote per tile.
-__device__ __forceinline__ void s_certify_vec(const Smem& S, const int32_t* __restrict__ u, const int32_t* __restrict__ v, int64_t lo,
+template <int NT, int VM>
+__device__ __forceinline__ void s_certify_vec(const Grp<NT>& G, const Smem& S, const int32_t* __restrict__ u, const int32_t* __restrict__ v, int64_t lo,
                               int64_t hi, int32_t V, int32_t* n1, int32_t* n2, int32_t* err) {
   constexpr int U = 4;
   if (lo >= hi) return;
@@ -303,19 +351,19 @@ __device__ __forceinline__ void s_certify_vec(const Smem& S, const int32_t* __re
   } else {
     body = hi;
   }
-  s_certify_scalar(S, u, v, lo, body, V, n1, n2, err);
+  s_certify_scalar(G, S, u, v, lo, body, V, n1, n2, err);
   const int64_t nunits = (hi - body) >> 2;
   const int32_t* ub = u + body;
   const int32_t* vb = v + body;
   const int4* u4 = reinterpret_cast<const int4*>(ub);
   const int4* v4 = reinterpret_cast<const int4*>(vb);
   volatile int32_t* P2 = S.P2;
-  const uint32_t cl = (uint32_t)(kVmax - 1);
-  for (int64_t base = 0; base < nunits; base += (int64_t)kT * U) {
+  const uint32_t cl = (uint32_t)(VM - 1);
+  for (int64_t base = 0; base < nunits; base += (int64_t)NT * U) {
     int4 ua[U], va[U];
 #pragma unroll
     for (int k = 0; k < U; k++) {
-      const int64_t idx = base + (int64_t)k * kT + threadIdx.x;
+      const int64_t idx = base + (int64_t)k * NT + G.tid;
       if (idx < nunits) {
         ua[k] = __ldcs(u4 + idx);
         va[k] = __ldcs(v4 + idx);
@@ -327,7 +375,7 @@ __device__ __forceinline__ void s_certify_vec(const Smem& S, const int32_t* __re
     uint32_t m = 0;
 #pragma unroll
     for (int k = 0; k < U; k++) {
-      if (base + (int64_t)k * kT + threadIdx.x >= nunits) continue;
+      if (base + (int64_t)k * NT + G.tid >= nunits) continue;
       const int32_t as[4] = {ua[k].x, ua[k].y, ua[k].z, ua[k].w};
       const int32_t bs[4] = {va[k].x, va[k].y, va[k].z, va[k].w};
 #pragma unroll
@@ -338,9 +386,9 @@ __device__ __forceinline__ void s_certify_vec(const Smem& S, const int32_t* __re
         m |= (uint32_t)(bad || !same_set) << (4 * k + c);
       }
     }
-    if (__any_sync(kFull, m != 0)) s_offer_misses(S, m, ub, vb, base, V, n1, n2, err);
+    if (__any_sync(kFull, m != 0)) s_offer_misses(G, S, m, ub, vb, base, V, n1, n2, err);
   }
-  s_certify_scalar(S, u, v, body + 4 * nunits, hi, V, n1, n2, err);
+  s_certify_scalar(G, S, u, v, body + 4 * nunits, hi, V, n1, n2, err);
 }
 
 // Certifies edges [lo, hi) of (u, v) into S.F1 / S.F2 (appending to *n1 / *n2); ids outside
@@ -348,22 +396,24 @@ __device__ __forceinline__ void s_certify_vec(const Smem& S, const int32_t* __re
 // tile's miss loop would run as long as its busiest lane), then both union-finds are flattened,
 // so that "equal F' parents" afterwards recognises nearly every pair inside one F' component,
 // and the rest streams through the vector loop.
-__device__ void s_certify_range(const Smem& S, const int32_t* __restrict__ u, const int32_t* __restrict__ v,
+template <int NT, int VM>
+__device__ void s_certify_range(const Grp<NT>& G, const Smem& S, const int32_t* __restrict__ u, const int32_t* __restrict__ v,
                                 int64_t lo, int64_t hi, int32_t V, int32_t* n1, int32_t* n2, int32_t* err) {
   const int64_t warm = min(hi - lo, (int64_t)8 * V + 2048);
-  s_certify_scalar(S, u, v, lo, lo + warm, V, n1, n2, err);
+  s_certify_scalar(G, S, u, v, lo, lo + warm, V, n1, n2, err);
   lo += warm;
   if (lo >= hi) return;
-  s_flatten(S.P1, V);
-  s_flatten(S.P2, V);
-  s_certify_vec(S, u, v, lo, hi, V, n1, n2, err);
+  s_flatten(G, S.P1, V);
+  s_flatten(G, S.P2, V);
+  s_certify_vec<NT, VM>(G, S, u, v, lo, hi, V, n1, n2, err);
 }
 
 // Certifies packed edges (a | b << 16) of a global list.
-__device__ void s_certify_packed(const Smem& S, const uint32_t* e, int32_t n, int32_t V, int32_t* n1, int32_t* n2) {
+template <int NT>
+__device__ void s_certify_packed(const Grp<NT>& G, const Smem& S, const uint32_t* e, int32_t n, int32_t V, int32_t* n1, int32_t* n2) {
   volatile int32_t* P2 = S.P2;
-  for (int32_t t0 = 0; t0 < n; t0 += kT) {
-    const int32_t i = t0 + threadIdx.x;
+  for (int32_t t0 = 0; t0 < n; t0 += NT) {
+    const int32_t i = t0 + G.tid;
     const bool valid = i < n;
     const uint32_t x = valid ? __ldcg(e + i) : 0;
     const int32_t a = (int32_t)(x & 0xffff), b = (int32_t)(x >> 16);
@@ -373,11 +423,12 @@ __device__ void s_certify_packed(const Smem& S, const uint32_t* e, int32_t n, in
 }
 
 // Bridges of the certificate in S (F1 = tree, F2 = extra), written sorted to out; returns count.
-__device__ int32_t s_bridges(const Smem& S, int32_t V, int32_t nt, int32_t nx, int32_t* out, int32_t* red,
-                             int32_t* sh) {
-  const int tid = threadIdx.x;
+template <int NT, int VM>
+__device__ int32_t s_bridges(const Grp<NT>& G, const Smem& S, int32_t V, int32_t nt, int32_t nx, int32_t* out,
+                             int32_t* red, int32_t* red_b, int32_t* sh) {
+  const int tid = G.tid;
   // roots (minimum vertex of each tree), degrees
-  for (int x = tid; x < V; x += kT) {
+  for (int x = tid; x < V; x += NT) {
     int32_t r = x, p = S.P1[x];
     while (p != r) {
       r = p;
@@ -385,17 +436,17 @@ __device__ int32_t s_bridges(const Smem& S, int32_t V, int32_t nt, int32_t nx, i
     }
     S.root[x] = (uint16_t)r;  // P2 region: F' union-find no longer needed
   }
-  for (int x = tid; x <= V + 1; x += kT) S.off[x] = 0;
-  for (int x = tid; x < V + 2; x += kT) S.cur[x] = 0;
-  __syncthreads();
-  for (int e = tid; e < nt; e += kT) {
+  for (int x = tid; x <= V + 1; x += NT) S.off[x] = 0;
+  for (int x = tid; x < V + 2; x += NT) S.cur[x] = 0;
+  G.sync();
+  for (int e = tid; e < nt; e += NT) {
     const uint32_t p = S.F1[e];
     inc16(S.off, (int)(p & 0xffff));
     inc16(S.off, (int)(p >> 16));
   }
-  __syncthreads();
-  const int32_t narcs = block_scan16(S.off, V + 1, red);  // off[V] = narcs
-  for (int e = tid; e < nt; e += kT) {
+  G.sync();
+  const int32_t narcs = block_scan16(G, S.off, V + 1, red);  // off[V] = narcs
+  for (int e = tid; e < nt; e += NT) {
     const uint32_t p = S.F1[e];
     const int32_t a = (int32_t)(p & 0xffff), b = (int32_t)(p >> 16);
     const int32_t ia = S.off[a] + inc16(S.cur, a), ib = S.off[b] + inc16(S.cur, b);
@@ -404,9 +455,9 @@ __device__ int32_t s_bridges(const Smem& S, int32_t V, int32_t nt, int32_t nx, i
     S.twin[ia] = (uint16_t)ib;
     S.twin[ib] = (uint16_t)ia;
   }
-  __syncthreads();
+  G.sync();
   // Euler-tour successors, cut at each root
-  for (int i = tid; i < narcs; i += kT) {
+  for (int i = tid; i < narcs; i += NT) {
     const int32_t y = S.dst[i], t = S.twin[i];
     uint16_t s;
     if (t + 1 < S.off[y + 1])
@@ -416,7 +467,7 @@ __device__ int32_t s_bridges(const Smem& S, int32_t V, int32_t nt, int32_t nx, i
     S.succ[i] = s;
     S.rnk[i] = s == kNone16 ? 0 : 1;
   }
-  __syncthreads();
+  G.sync();
   // list ranking by pointer jumping, four hops per round (shared-memory loads are cheap, the
   // block barriers between rounds are not): ceil(log4 n) rounds, double-buffered in the P1 and F
   // regions (both free now: the roots are known and the adjacency is built)
@@ -428,7 +479,7 @@ __device__ int32_t s_bridges(const Smem& S, int32_t V, int32_t nt, int32_t nx, i
     uint16_t* sb = reinterpret_cast<uint16_t*>(S.P1);
     uint16_t* rb = reinterpret_cast<uint16_t*>(S.F1);
     for (int r = 0; r < rounds; r++) {
-      for (int i = tid; i < narcs; i += kT) {
+      for (int i = tid; i < narcs; i += NT) {
         uint16_t s = sa[i], acc = ra[i];
 #pragma unroll
         for (int h = 0; h < 3 && s != kNone16; h++) {
@@ -438,7 +489,7 @@ __device__ int32_t s_bridges(const Smem& S, int32_t V, int32_t nt, int32_t nx, i
         rb[i] = acc;
         sb[i] = s;
       }
-      __syncthreads();
+      G.sync();
       uint16_t* t = sa;
       sa = sb;
       sb = t;
@@ -447,12 +498,12 @@ __device__ int32_t s_bridges(const Smem& S, int32_t V, int32_t nt, int32_t nx, i
       rb = t;
     }
     if (ra != S.rnk) {
-      for (int i = tid; i < narcs; i += kT) S.rnk[i] = ra[i];
-      __syncthreads();
+      for (int i = tid; i < narcs; i += NT) S.rnk[i] = ra[i];
+      G.sync();
     }
   }
   // per root: tour arcs (aoff) and tree vertices (vbase); P1 region is free now
-  for (int x = tid; x <= V; x += kT) {
+  for (int x = tid; x <= V; x += NT) {
     uint16_t L = 0, nv = 0;
     if (x < V && S.root[x] == x) {
       L = S.off[x + 1] > S.off[x] ? (uint16_t)(S.rnk[S.off[x]] + 1) : 0;
@@ -461,12 +512,12 @@ __device__ int32_t s_bridges(const Smem& S, int32_t V, int32_t nt, int32_t nx, i
     S.aoff[x] = L;
     S.vbase[x] = nv;
   }
-  __syncthreads();
-  block_scan16_pair(S.aoff, S.vbase, V + 1, red);
+  G.sync();
+  block_scan16_pair(G, S.aoff, S.vbase, V + 1, red, red_b);
   // tour positions; down arcs (dflag reuses succ, free after ranking)
-  for (int i = tid; i <= narcs; i += kT) S.dflag[i] = 0;
-  __syncthreads();
-  for (int i = tid; i < narcs; i += kT) {
+  for (int i = tid; i <= narcs; i += NT) S.dflag[i] = 0;
+  G.sync();
+  for (int i = tid; i < narcs; i += NT) {
     const int32_t x = S.dst[S.twin[i]];
     const int32_t r = S.root[x];
     const int32_t L = S.rnk[S.off[r]] + 1;
@@ -481,10 +532,10 @@ __device__ int32_t s_bridges(const Smem& S, int32_t V, int32_t nt, int32_t nx, i
       S.sz[y] = (uint16_t)((ri - rt + 1) / 2);
     }
   }
-  __syncthreads();
-  block_scan16(S.dflag, narcs, red);  // dscan in place
+  G.sync();
+  block_scan16(G, S.dflag, narcs, red);  // dscan in place
   // preorder numbers; lo / hi (dst and twin are free now)
-  for (int x = tid; x < V; x += kT) {
+  for (int x = tid; x < V; x += NT) {
     const int32_t r = S.root[x];
     int32_t p;
     if (r == x) {
@@ -497,13 +548,13 @@ __device__ int32_t s_bridges(const Smem& S, int32_t V, int32_t nt, int32_t nx, i
     }
     S.pre[x] = (uint16_t)min(max(p, 0), V - 1);
   }
-  __syncthreads();
-  for (int x = tid; x < V; x += kT) {
+  G.sync();
+  for (int x = tid; x < V; x += NT) {
     S.lo[S.pre[x]] = S.pre[x];
     S.hi[S.pre[x]] = S.pre[x];
   }
-  __syncthreads();
-  for (int e = tid; e < nx; e += kT) {
+  G.sync();
+  for (int e = tid; e < nx; e += NT) {
     const uint32_t p = S.F2[e];
     const int32_t a = (int32_t)(p & 0xffff), b = (int32_t)(p >> 16);
     if (a == b) continue;
@@ -513,12 +564,12 @@ __device__ int32_t s_bridges(const Smem& S, int32_t V, int32_t nt, int32_t nx, i
     atomicMax(S.hi + pa, pb);
     atomicMax(S.hi + pb, pa);
   }
-  __syncthreads();
+  G.sync();
   // chunk (32) minima / maxima kept in the off region, free now
   int32_t* cmin = reinterpret_cast<int32_t*>(S.off);
-  int32_t* cmax = cmin + kVmax / 32;
+  int32_t* cmax = cmin + VM / 32;
   const int nch = (V + 31) / 32;
-  for (int c = tid >> 5; c < nch; c += kW) {
+  for (int c = tid >> 5; c < nch; c += (NT / 32)) {
     const int i = c * 32 + (tid & 31);
     int32_t mn = i < V ? S.lo[i] : INT32_MAX, mx = i < V ? S.hi[i] : INT32_MIN;
     for (int o = 16; o > 0; o >>= 1) {
@@ -531,9 +582,9 @@ __device__ int32_t s_bridges(const Smem& S, int32_t V, int32_t nt, int32_t nx, i
     }
   }
   if (tid == 0) *sh = 0;
-  __syncthreads();
+  G.sync();
   // test every tree edge (par(y), y); keys reuse the F region
-  for (int y = tid; y < V; y += kT) {
+  for (int y = tid; y < V; y += NT) {
     if (S.par[y] == kNone16) continue;
     const int32_t l = S.pre[y], r = min(V, l + max((int32_t)S.sz[y], 1));
     int32_t mn = INT32_MAX, mx = INT32_MIN;
@@ -551,9 +602,9 @@ __device__ int32_t s_bridges(const Smem& S, int32_t V, int32_t nt, int32_t nx, i
       if (k < V) S.keys[k] = (a << 12) | b;
     }
   }
-  __syncthreads();
+  G.sync();
   const int32_t n = min(*sh, max(V - 1, 0));
-  if (n <= kT) {
+  if (n <= NT) {
     // rank sort: keys are unique (a bridge has no parallel copy), every thread ranks one key
     // against all n with broadcast reads; one pass, no barrier
     if (tid < n) {
@@ -563,17 +614,17 @@ __device__ int32_t s_bridges(const Smem& S, int32_t V, int32_t nt, int32_t nx, i
       out[2 * rank] = (int32_t)(mine >> 12);
       out[2 * rank + 1] = (int32_t)(mine & 0xfff);
     }
-    __syncthreads();
+    G.sync();
     return n;
   }
   // bitonic sort of n keys (padded to a power of two with ~0)
   int np = 1;
   while (np < n) np <<= 1;
-  for (int i = n + tid; i < np; i += kT) S.keys[i] = 0xffffffffu;
-  __syncthreads();
+  for (int i = n + tid; i < np; i += NT) S.keys[i] = 0xffffffffu;
+  G.sync();
   for (int k = 2; k <= np; k <<= 1) {
     for (int j = k >> 1; j > 0; j >>= 1) {
-      for (int i = tid; i < np; i += kT) {
+      for (int i = tid; i < np; i += NT) {
         const int l = i ^ j;
         if (l > i) {
           const uint32_t x = S.keys[i], y = S.keys[l];
@@ -584,102 +635,122 @@ __device__ int32_t s_bridges(const Smem& S, int32_t V, int32_t nt, int32_t nx, i
           }
         }
       }
-      __syncthreads();
+      G.sync();
     }
   }
-  for (int i = tid; i < n; i += kT) {
+  for (int i = tid; i < n; i += NT) {
     out[2 * i] = (int32_t)(S.keys[i] >> 12);
     out[2 * i + 1] = (int32_t)(S.keys[i] & 0xfff);
   }
-  __syncthreads();
+  G.sync();
   return n;
 }
 
-__global__ void __launch_bounds__(kT, 1) batched_kernel(const BatchArgs* __restrict__ dA) {
-  const BatchArgs A = *dA;
-  extern __shared__ __align__(16) char smem_raw[];
-  __shared__ int32_t red[kW];
-  __shared__ int32_t task_sh, n1, n2, err, flag, sh;
-  const Smem S = carve_smem(smem_raw);
-  const int tid = threadIdx.x;
-  const int32_t ntasks = *A.d_ntasks;
-  while (true) {
-    __syncthreads();  // every thread is done with the previous task (and with task_sh)
-    if (tid == 0) task_sh = atomicAdd(A.queue, 1);
-    __syncthreads();
-    const int32_t t = task_sh;
-    if (t >= ntasks) break;
-    const BatchTask T = A.tasks[t];
-    const int32_t V = T.V;
-    // a malformed descriptor is skipped, never used to index shared memory
-    const int64_t stride = 2 + 2 * (int64_t)V;
-    if (V < 0 || V > kVmax || T.lo < 0 || T.hi < T.lo || T.g < 0 || T.g >= A.G || T.nparts < 1 ||
-        T.part < 0 || T.part >= T.nparts || !T.count || (V > 1 && !T.out) ||
-        (T.nparts > 1 && (T.slot < (int64_t)T.part * stride ||
-                          T.slot + (int64_t)(T.nparts - T.part) * stride > A.slot_words))) {
-      if (tid == 0 && T.count) *T.count = BRIDGES_EINTERNAL;
-      continue;
+// One task -- a whole graph, or one partition of a large graph -- by a group of NT threads whose
+// graphs have at most VM vertices.
+template <int NT, int VM>
+__device__ void run_task(const BatchArgs& A, const BatchTask& T, const Smem& S, const Grp<NT>& G, GroupShared& gs) {
+  const int tid = G.tid;
+  const int32_t V = T.V;
+  // a malformed descriptor is skipped, never used to index shared memory; partitioned graphs
+  // (which merge through the slots) only run on whole blocks
+  const int64_t stride = 2 + 2 * (int64_t)V;
+  if (V < 0 || V > VM || T.lo < 0 || T.hi < T.lo || T.g < 0 || T.g >= A.G || T.nparts < 1 || T.part < 0 ||
+      T.part >= T.nparts || !T.count || (V > 1 && !T.out) || (T.nparts > 1 && NT != kT) ||
+      (T.nparts > 1 &&
+       (T.slot < (int64_t)T.part * stride || T.slot + (int64_t)(T.nparts - T.part) * stride > A.slot_words))) {
+    if (tid == 0 && T.count) *T.count = BRIDGES_EINTERNAL;
+    return;
+  }
+  for (int x = tid; x < V; x += NT) {
+    S.P1[x] = x;
+    S.P2[x] = x;
+  }
+  if (tid == 0) {
+    gs.n1 = 0;
+    gs.n2 = 0;
+    gs.err = 0;
+  }
+  G.sync();
+  s_certify_range<NT, VM>(G, S, T.u, T.v, T.lo, T.hi, V, &gs.n1, &gs.n2, &gs.err);
+  G.sync();
+  int32_t nt = min(gs.n1, V), nx = min(gs.n2, V);
+  if (T.nparts > 1) {
+    // publish this partition's certificate; the last partition of the graph merges
+    uint32_t* slot = A.slots + T.slot;
+    for (int i = tid; i < nt; i += NT) slot[2 + i] = S.F1[i];
+    for (int i = tid; i < nx; i += NT) slot[2 + nt + i] = S.F2[i];
+    if (tid == 0) {
+      slot[0] = (uint32_t)nt;
+      slot[1] = (uint32_t)nx;
+      if (gs.err) atomicExch(A.gerr + T.g, gs.err);
     }
-    for (int x = tid; x < V; x += kT) {
+    __threadfence();
+    G.sync();
+    if (tid == 0) gs.flag = atomicAdd(A.done + T.g, 1) == T.nparts - 1;
+    G.sync();
+    if (!gs.flag) return;
+    __threadfence();
+    // merge: certify the union of every partition's certificate (this one included)
+    for (int x = tid; x < V; x += NT) {
       S.P1[x] = x;
       S.P2[x] = x;
     }
     if (tid == 0) {
-      n1 = 0;
-      n2 = 0;
-      err = 0;
+      gs.n1 = 0;
+      gs.n2 = 0;
+      const int32_t e = ld_relaxed(A.gerr + T.g);
+      if (e) gs.err = e;
     }
-    __syncthreads();
-    s_certify_range(S, T.u, T.v, T.lo, T.hi, V, &n1, &n2, &err);
-    __syncthreads();
-    int32_t nt = min(n1, V), nx = min(n2, V);
-    if (T.nparts > 1) {
-      // publish this partition's certificate; the last partition of the graph merges
-      uint32_t* slot = A.slots + T.slot;
-      for (int i = tid; i < nt; i += kT) slot[2 + i] = S.F1[i];
-      for (int i = tid; i < nx; i += kT) slot[2 + nt + i] = S.F2[i];
-      if (tid == 0) {
-        slot[0] = (uint32_t)nt;
-        slot[1] = (uint32_t)nx;
-        if (err) atomicExch(A.gerr + T.g, err);
-      }
-      __threadfence();
-      __syncthreads();
-      if (tid == 0) flag = atomicAdd(A.done + T.g, 1) == T.nparts - 1;
-      __syncthreads();
-      if (!flag) continue;
-      __threadfence();
-      // merge: certify the union of every partition's certificate (this one included)
-      for (int x = tid; x < V; x += kT) {
-        S.P1[x] = x;
-        S.P2[x] = x;
-      }
-      if (tid == 0) {
-        n1 = 0;
-        n2 = 0;
-        const int32_t e = ld_relaxed(A.gerr + T.g);
-        if (e) err = e;
-      }
-      __syncthreads();
-      for (int p = 0; p < T.nparts; p++) {
-        const uint32_t* sp = A.slots + T.slot - (int64_t)T.part * stride + (int64_t)p * stride;
-        const int32_t pn = (int32_t)(__ldcg(sp) + __ldcg(sp + 1));
-        s_certify_packed(S, sp + 2, min(pn, 2 * V), V, &n1, &n2);
-        __syncthreads();
-      }
-      nt = min(n1, V);
-      nx = min(n2, V);
+    G.sync();
+    for (int p = 0; p < T.nparts; p++) {
+      const uint32_t* sp = A.slots + T.slot - (int64_t)T.part * stride + (int64_t)p * stride;
+      const int32_t pn = (int32_t)(__ldcg(sp) + __ldcg(sp + 1));
+      s_certify_packed(G, S, sp + 2, min(pn, 2 * V), V, &gs.n1, &gs.n2);
+      G.sync();
     }
-    int64_t* cnt = T.count;
-    if (err) {
-      if (tid == 0) *cnt = err;
-      __syncthreads();
-      continue;
-    }
-    const int32_t nb = s_bridges(S, V, nt, nx, T.out, red, &sh);
-    if (tid == 0) *cnt = nb;
-    __syncthreads();
+    nt = min(gs.n1, V);
+    nx = min(gs.n2, V);
   }
+  if (gs.err) {
+    G.sync();  // every thread has read gs.err before the next task resets it
+    if (tid == 0) *T.count = gs.err;
+    return;
+  }
+  const int32_t nb = s_bridges<NT, VM>(G, S, V, nt, nx, T.out, gs.red, gs.red_b, &gs.sh);
+  if (tid == 0) *T.count = nb;
+}
+
+// Takes tasks first + 0, 1, ... from `queue` until `last` and runs them on group G.
+template <int NT, int VM>
+__device__ void run_queue(const BatchArgs& A, char* smem, const Grp<NT>& G, GroupShared& gs, int32_t* queue,
+                          int32_t first, int32_t last) {
+  const Smem S = carve_smem<VM>(smem);
+  while (true) {
+    G.sync();  // every thread of the group is done with the previous task (and with gs.task)
+    if (G.tid == 0) gs.task = first + atomicAdd(queue, 1);
+    G.sync();
+    const int32_t t = gs.task;
+    if (t >= last) break;
+    run_task<NT, VM>(A, A.tasks[t], S, G, gs);
+  }
+}
+
+// Persistent: whole-block tasks first (graphs above kHalfVmax vertices and the partitions of
+// large graphs), then the block splits into two independent half-block groups, each with half
+// the shared memory and its own named barrier, for the rest.  A small graph's cost is mostly
+// its block barriers, and two of them now overlap on one SM.
+__global__ void __launch_bounds__(kT, 1) batched_kernel(const BatchArgs* __restrict__ dA) {
+  const BatchArgs A = *dA;
+  extern __shared__ __align__(16) char smem_raw[];
+  __shared__ GroupShared gs[2];
+  const int32_t ntasks = *A.d_ntasks;
+  const int32_t nbig = min(max(A.nbig, 0), ntasks);
+  run_queue<kT, kVmax>(A, smem_raw, Grp<kT>{(int)threadIdx.x, 0}, gs[0], A.queue, 0, nbig);
+  __syncthreads();  // the halves reuse the shared memory
+  const int h = (int)threadIdx.x / kHalfT;
+  run_queue<kHalfT, kHalfVmax>(A, smem_raw + h * Layout<kHalfVmax>::kBytes,
+                               Grp<kHalfT>{(int)threadIdx.x % kHalfT, 1 + h}, gs[h], A.queue + 1, nbig, ntasks);
 }
 
 }  // namespace

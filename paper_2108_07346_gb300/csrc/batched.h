@@ -7,6 +7,7 @@
 namespace bridges {
 
 constexpr int kBatchVmax = 4096;  // graphs up to this many vertices are handled in shared memory
+constexpr int kBatchHalfVmax = kBatchVmax / 2;  // ... and up to this many, two per block
 
 // One unit of work: a whole graph (nparts == 1) or partition `part` of it.
 struct BatchTask {
@@ -32,8 +33,13 @@ struct BatchArgs {
   int32_t* gerr;     // per graph: first error of any partition
   uint32_t* slots;   // certificates of partitions
   int32_t G;           // graphs (bounds the graph index of every task)
+  int32_t nbig;        // tasks [0, nbig) run on whole blocks, the rest on half-block groups
   int64_t slot_words;  // capacity of slots (u32)
 };
+
+// True if a task needs a whole block: more than kBatchHalfVmax vertices, or a partition of a
+// graph (partitions merge through the slots).
+inline bool batch_task_is_big(const BatchTask& t) { return t.V > kBatchHalfVmax || t.nparts > 1; }
 
 size_t batched_smem_bytes();
 // Launches the persistent kernel (one block per SM) reading its arguments from *dev_args.

@@ -160,3 +160,15 @@ def test_host_entry(cuda_lib):
         assert c.articulation_points_host(hu, hv, g.V, 4).numpy().tolist() == ref
         assert c.articulation_points_host(torch.from_numpy(np.array(g.u)), torch.from_numpy(np.array(g.v)), g.V,
                                           2).numpy().tolist() == ref
+
+
+@pytest.mark.parametrize("ap_warm_edges", [-1, 0, 5000, 10_000_000])
+def test_block_pass_prefix_options(cuda_lib, ap_warm_edges):
+    """The block pass's prefix before its snapshot: none (-1), automatic, short, and longer than
+    the list (no snapshot): the cut vertices do not change."""
+    g = graphgen.workload("mid")
+    ref = oracle.articulation_points(g.u, g.v, g.V).tolist()
+    c = cuda_lib.Context(device="cuda:0", ap_warm_edges=ap_warm_edges)
+    assert c.articulation_points(dev(g.u), dev(g.v), g.V, 3).cpu().numpy().tolist() == ref
+    cfg = c.last_config()
+    assert cfg["ap_warm_edges"] == (-1 if ap_warm_edges >= g.E else (0 if ap_warm_edges < 0 else cfg["ap_warm_edges"]))

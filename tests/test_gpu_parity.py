@@ -238,3 +238,17 @@ def test_host_read_in_place(cuda_lib):
     # pageable host memory falls back to copying
     assert c.find_host(torch.from_numpy(np.array(g.u)), torch.from_numpy(np.array(g.v)), g.V, 4).numpy().tolist() \
         == ref.tolist()
+
+
+@pytest.mark.parametrize("warm_block", [32, 64, 256, 1024])
+@pytest.mark.parametrize("warm_edges", [0, 1000, 200000])
+def test_plan_options(cuda_lib, warm_block, warm_edges):
+    """Every plan the options can select gives the same exact set: warm-up launch block sizes,
+    no snapshot at all (0), a short warm-up (many misses take the union-find path) and a long one."""
+    g = graphgen.workload("mid")
+    ref = oracle.bridges(g.u, g.v, g.V, 16)
+    c = cuda_lib.Context(device="cuda:0", warm_edges=warm_edges, warm_block=warm_block)
+    du, dv = dev_edges(g.u, g.v)
+    for M in (1, 6):
+        assert c.find(du, dv, g.V, M).cpu().numpy().tolist() == ref.tolist(), (warm_block, warm_edges, M)
+    assert c.get_opts()["warm_block"] == warm_block
