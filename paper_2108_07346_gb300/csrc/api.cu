@@ -576,10 +576,10 @@ int64_t plan_batch_tasks(std::vector<BatchTask>& graphs, int64_t split, std::vec
     }
     if (np > 1) slot += (int64_t)np * (2 + 2 * (int64_t)g.V);
   }
-  // whole-block tasks first, then the ones two of which share a block; largest first in each
+  // whole-block tasks first, then the ones for half and for quarter blocks; largest first in each
   std::stable_sort(tasks.begin(), tasks.end(), [](const BatchTask& x, const BatchTask& y) {
-    const bool bx = batch_task_is_big(x), by = batch_task_is_big(y);
-    if (bx != by) return bx;
+    const int cx = batch_task_class(x), cy = batch_task_class(y);
+    if (cx != cy) return cx < cy;
     return x.hi - x.lo > y.hi - y.lo;
   });
   return slot;
@@ -605,16 +605,20 @@ int64_t launch_batch_tasks(bridges_ctx* c, cudaStream_t s, const std::vector<Bat
   A.gerr = reinterpret_cast<int32_t*>(d + L.gerr);
   A.slots = reinterpret_cast<uint32_t*>(d + L.slots);
   A.G = G;
-  // tasks up to the first small one run on whole blocks; a caller's unordered list runs every
-  // task on whole blocks
-  int32_t nbig = 0;
-  while (nbig < (int32_t)tasks.size() && batch_task_is_big(tasks[nbig])) nbig++;
-  for (size_t i = nbig; i < tasks.size(); i++)
-    if (batch_task_is_big(tasks[i])) {
-      nbig = (int32_t)tasks.size();
+  // the class boundaries of the ordered list; a list out of class order runs every task on whole
+  // blocks (always correct)
+  const int32_t n = (int32_t)tasks.size();
+  int32_t nbig = 0, nmid = 0;
+  while (nbig < n && batch_task_class(tasks[nbig]) == 0) nbig++;
+  while (nbig + nmid < n && batch_task_class(tasks[nbig + nmid]) == 1) nmid++;
+  for (int32_t i = nbig + nmid; i < n; i++)
+    if (batch_task_class(tasks[i]) != 2) {
+      nbig = n;
+      nmid = 0;
       break;
     }
   A.nbig = nbig;
+  A.nmid = nmid;
   A.slot_words = c->b_slot_cap;
   std::memcpy(h + L.s_args, &A, sizeof(A));
   const int32_t nt = (int32_t)tasks.size();

@@ -32,6 +32,8 @@ constexpr int kT = 1024;           // threads per block
 constexpr int kVmax = kBatchVmax;  // 4096: a whole block's graph
 constexpr int kHalfT = kT / 2;     // threads of a half-block group
 constexpr int kHalfVmax = kVmax / 2;  // 2048: a half-block group's graph
+constexpr int kQuarterT = kT / 4;     // threads of a quarter-block group
+constexpr int kQuarterVmax = kVmax / 4;  // 1024: a quarter-block group's graph
 constexpr uint16_t kNone16 = 0xffff;
 
 constexpr int a16(int x) { return (x + 15) & ~15; }
@@ -61,8 +63,10 @@ struct Layout {
   static constexpr int R9 = 6 * VM;
   static constexpr int kBytes = R0 + R1 + R2 + R3 + R4 + R5 + R6 + R7 + R8 + R9;
 };
-constexpr int kSmem = Layout<kVmax>::kBytes > 2 * Layout<kHalfVmax>::kBytes ? Layout<kVmax>::kBytes
-                                                                               : 2 * Layout<kHalfVmax>::kBytes;
+constexpr int cmax(int a, int b) { return a > b ? a : b; }
+// a half block's share holds one half-group layout or two quarter-group layouts
+constexpr int kHalfBytes = cmax(Layout<kHalfVmax>::kBytes, 2 * Layout<kQuarterVmax>::kBytes);
+constexpr int kSmem = cmax(Layout<kVmax>::kBytes, 2 * kHalfBytes);
 
 struct Smem {
   int32_t* P1;
@@ -124,8 +128,8 @@ __device__ Smem carve_smem(char* base) {
   return s;
 }
 
-// A group of NT threads (whole block, or one half) working on one task: its thread index and
-// its barrier (0 = the block's; 1 and 2 = the halves' named barriers).
+// A group of NT threads (whole block, a half or a quarter) working on one task: its thread index
+// and its barrier (0 = the block's; 1, 2 = the halves' and 3 to 6 = the quarters' named ones).
 template <int NT>
 struct Grp {
   int tid;
@@ -737,20 +741,29 @@ __device__ void run_queue(const BatchArgs& A, char* smem, const Grp<NT>& G, Grou
 }
 
 // Persistent: whole-block tasks first (graphs above kHalfVmax vertices and the partitions of
-// large graphs), then the block splits into two independent half-block groups, each with half
-// the shared memory and its own named barrier, for the rest.  A small graph's cost is mostly
-// its block barriers, and two of them now overlap on one SM.
+// large graphs); then the block splits into two independent half-block groups, each with half
+// the shared memory and its own named barrier, for graphs of up to kHalfVmax vertices; when a
+// half runs out of those it splits again into two quarter-block groups for graphs of up to
+// kQuarterVmax.  A small graph's cost is mostly its barriers, and this overlaps up to four of
+// them on one SM.  No barrier spans groups after the first split.
 __global__ void __launch_bounds__(kT, 1) batched_kernel(const BatchArgs* __restrict__ dA) {
   const BatchArgs A = *dA;
   extern __shared__ __align__(16) char smem_raw[];
-  __shared__ GroupShared gs[2];
+  __shared__ GroupShared gs[6];  // [0] the block, then [h] each half, then [2 + 2h + q] each quarter
   const int32_t ntasks = *A.d_ntasks;
   const int32_t nbig = min(max(A.nbig, 0), ntasks);
+  const int32_t nmid = min(max(A.nmid, 0), ntasks - nbig);
   run_queue<kT, kVmax>(A, smem_raw, Grp<kT>{(int)threadIdx.x, 0}, gs[0], A.queue, 0, nbig);
   __syncthreads();  // the halves reuse the shared memory
   const int h = (int)threadIdx.x / kHalfT;
-  run_queue<kHalfT, kHalfVmax>(A, smem_raw + h * Layout<kHalfVmax>::kBytes,
-                               Grp<kHalfT>{(int)threadIdx.x % kHalfT, 1 + h}, gs[h], A.queue + 1, nbig, ntasks);
+  char* half = smem_raw + h * kHalfBytes;
+  const Grp<kHalfT> gh{(int)threadIdx.x % kHalfT, 1 + h};
+  run_queue<kHalfT, kHalfVmax>(A, half, gh, gs[h], A.queue + 1, nbig, nbig + nmid);
+  gh.sync();  // the quarters reuse this half's shared memory
+  const int q = ((int)threadIdx.x % kHalfT) / kQuarterT;
+  run_queue<kQuarterT, kQuarterVmax>(A, half + q * Layout<kQuarterVmax>::kBytes,
+                                     Grp<kQuarterT>{(int)threadIdx.x % kQuarterT, 3 + 2 * h + q}, gs[2 + 2 * h + q],
+                                     A.queue + 2, nbig + nmid, ntasks);
 }
 
 }  // namespace

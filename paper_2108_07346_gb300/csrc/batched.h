@@ -7,7 +7,8 @@
 namespace bridges {
 
 constexpr int kBatchVmax = 4096;  // graphs up to this many vertices are handled in shared memory
-constexpr int kBatchHalfVmax = kBatchVmax / 2;  // ... and up to this many, two per block
+constexpr int kBatchHalfVmax = kBatchVmax / 2;     // ... up to this many, two per block
+constexpr int kBatchQuarterVmax = kBatchVmax / 4;  // ... up to this many, four per block
 
 // One unit of work: a whole graph (nparts == 1) or partition `part` of it.
 struct BatchTask {
@@ -33,13 +34,17 @@ struct BatchArgs {
   int32_t* gerr;     // per graph: first error of any partition
   uint32_t* slots;   // certificates of partitions
   int32_t G;           // graphs (bounds the graph index of every task)
-  int32_t nbig;        // tasks [0, nbig) run on whole blocks, the rest on half-block groups
+  int32_t nbig;        // tasks [0, nbig) run on whole blocks,
+  int32_t nmid;        // [nbig, nbig + nmid) on half-block groups, the rest on quarter-block groups
   int64_t slot_words;  // capacity of slots (u32)
 };
 
-// True if a task needs a whole block: more than kBatchHalfVmax vertices, or a partition of a
-// graph (partitions merge through the slots).
-inline bool batch_task_is_big(const BatchTask& t) { return t.V > kBatchHalfVmax || t.nparts > 1; }
+// Which group a task needs: 0 a whole block (more than kBatchHalfVmax vertices, or a partition of
+// a graph: partitions merge through the slots), 1 a half block, 2 a quarter block.
+inline int batch_task_class(const BatchTask& t) {
+  if (t.V > kBatchHalfVmax || t.nparts > 1) return 0;
+  return t.V > kBatchQuarterVmax ? 1 : 2;
+}
 
 size_t batched_smem_bytes();
 // Launches the persistent kernel (one block per SM) reading its arguments from *dev_args.
