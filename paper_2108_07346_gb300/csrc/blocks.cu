@@ -119,7 +119,8 @@ struct CycleSink {
 __device__ __forceinline__ int64_t gtid() { return (int64_t)blockIdx.x * blockDim.x + threadIdx.x; }
 __device__ __forceinline__ int64_t gstride() { return (int64_t)gridDim.x * blockDim.x; }
 
-// Preorder-indexed copies of T (parent, subtree end, vertex) and singleton classes.
+// Preorder-indexed copies of T (parent, subtree end, vertex), singleton classes, and the jump of
+// Tarjan & Vishkin's rule 2 (below): J[i] = the parent's edge if tree edge i joins it, else i.
 __global__ void ap_init_kernel(FinalBufs f, ApBufs b, int32_t V) {
   if (*f.status) return;
   for (int64_t x = gtid(); x < V; x += gstride()) {
@@ -130,12 +131,39 @@ __global__ void ap_init_kernel(FinalBufs f, ApBufs b, int32_t V) {
       set_status(f.status, BRIDGES_EINTERNAL_CODE);
       continue;
     }
+    const int32_t pp = p >= 0 ? f.pre[p] : -1;
     b.vtx[i] = (int32_t)x;
-    b.PP[i] = p >= 0 ? f.pre[p] : -1;
+    b.PP[i] = pp;
     b.LAST[i] = i + s - 1;
     b.Q[i] = i;
+    // rule 2: y's subtree has a certificate neighbour outside p's subtree (p not a root)
+    bool join = false;
+    if (p >= 0 && f.par[p] >= 0) {
+      const int32_t sp = f.sz[p];
+      join = f.slo[x] < pp || (int64_t)f.shi[x] > (int64_t)pp + sp - 1;
+    }
+    b.tmp[i] = join ? pp : i;
   }
   if (gtid() == 0) *b.hooks = 0;
+}
+
+constexpr int kChainCap = 64;  // rule-2 chain steps walked directly; longer chains are linked
+
+// Rule 2 alone links every tree edge to its parent's edge along upward chains, so its classes
+// are read off by walking the jumps to the chain's top (J[t] == t): Q[i] = top, a valid flat
+// union-find (the top is an ancestor: a smaller preorder number).  A walk that needs more than
+// kChainCap steps stops there; the edge stays a singleton and records where it stopped (csize)
+// for a union-find link in ap_tv_kernel, so the cost stays bounded on long chains.
+__global__ void ap_chain_kernel(ApBufs b, int32_t V, const int32_t* status) {
+  if (*status) return;
+  for (int64_t i = gtid(); i < V; i += gstride()) {
+    int32_t t = (int32_t)i;
+    int k = 0;
+    for (int32_t j = b.tmp[t]; j != t && k < kChainCap; j = b.tmp[t], k++) t = j;
+    const bool top = b.tmp[t] == t;
+    b.Q[i] = top ? t : (int32_t)i;
+    b.csize[i] = top ? -1 : t;
+  }
 }
 
 // The blocks of the certificate S = T u F' as the starting classes, by the two link rules of
@@ -145,21 +173,21 @@ __global__ void ap_init_kernel(FinalBufs f, ApBufs b, int32_t V) {
 // (slo / shi) that the bridge test computed.  Every link joins two edges of one fundamental
 // cycle, and the closure of the links is the blocks of S restricted to T: each a connected
 // subtree of T again once all links are in, which the cycle walk of the later passes needs.
-__global__ void ap_tv_kernel(FinalBufs f, ApArgs A, const int32_t* xu, const int32_t* xv, const int32_t* d_n,
-                             int32_t cap) {
+// Rule 2's chains are already flattened by ap_chain_kernel; this kernel adds the links of the
+// chains it cut short, then rule 1.
+__global__ void ap_tv_kernel(FinalBufs f, ApArgs A, ApBufs b, const int32_t* xu, const int32_t* xv,
+                             const int32_t* d_n, int32_t cap) {
   if (*A.status) return;
   const int32_t V = A.V;
-  for (int64_t y = gtid(); y < V; y += gstride()) {
-    const int32_t p = f.par[y];
-    if (p < 0 || f.par[p] < 0) continue;
-    const int32_t pp = f.pre[p];
-    if (f.slo[y] < pp || f.shi[y] > A.LAST[pp]) uf_link(A.Q, f.pre[y], pp);
+  for (int64_t i = gtid(); i < V; i += gstride()) {
+    const int32_t t = b.csize[i];
+    if (t >= 0) uf_link(A.Q, (int32_t)i, t);
   }
   const int32_t n = min(*d_n, cap);
   for (int64_t e = gtid(); e < n; e += gstride()) {
-    const int32_t a = xu[e], b = xv[e];
-    if (!checked_edge(A, a, b)) continue;
-    const int32_t pa = f.pre[a], pb = f.pre[b];
+    const int32_t a = xu[e], c = xv[e];
+    if (!checked_edge(A, a, c)) continue;
+    const int32_t pa = f.pre[a], pb = f.pre[c];
     const bool related = (pa <= pb && pb <= A.LAST[pa]) || (pb <= pa && pa <= A.LAST[pb]);
     if (!related) uf_link(A.Q, pa, pb);
   }
@@ -413,8 +441,9 @@ void articulation_stage(const Launch& L, const CertPlan& p, const FinalBufs& f, 
   const int g = grid_of(L, V, bs);
   ap_init_kernel<<<g, bs, 0, L.stream>>>(f, b, V);
   ApArgs A{f.pre, b.Q, b.PP, b.LAST, V, f.status, b.hooks};
-  ap_tv_kernel<<<grid_of(L, V, bs), bs, 0, L.stream>>>(f, A, xu, xv, d_nx, V);
-  *L.launches += 2;
+  ap_chain_kernel<<<g, bs, 0, L.stream>>>(b, V, f.status);
+  ap_tv_kernel<<<grid_of(L, V, bs), bs, 0, L.stream>>>(f, A, b, xu, xv, d_nx, V);
+  *L.launches += 3;
   const bool vec = ((reinterpret_cast<uintptr_t>(u) | reinterpret_cast<uintptr_t>(v)) & 15) == 0;
   const int grid = (int)std::max<int64_t>(1, (int64_t)p.G * p.M);
   PassArgs a{A, u, v, 0, p.cache ? std::min(p.warm, p.E) : p.E, b.lab, b.Vpad};
