@@ -731,7 +731,10 @@ void final_stage(const Launch& L, const FinalBufs& f, int32_t V, const int32_t* 
   int sl = 0;
   while (ceil_div(nchunks, (int64_t)kSuperChunks << sl) > kMaxSup) sl++;
   A.sup_log = sl;
-  const int blocks = std::min(kMaxBlocks, occ_blocks * L.num_sms);
+  // one block per SM at most; small forests take fewer (a block per 256 vertices), which makes
+  // every grid barrier cheaper and leaves SMs free for work on other streams (the server)
+  const int64_t want = ceil_div(std::max(V, 1), 256);
+  const int blocks = (int)std::min<int64_t>({(int64_t)kMaxBlocks, (int64_t)occ_blocks * L.num_sms, want});
   cudaMemsetAsync(f.bar_count, 0, 2 * sizeof(unsigned), L.stream);
   void* args[] = {&A};
   cudaLaunchCooperativeKernel((void*)final_kernel, dim3(blocks), dim3(kThreads), args, smem, L.stream);
