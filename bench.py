@@ -34,9 +34,9 @@ UNIT = "GE/s"
 # workload (profiles/launch_list_large_dense.md, profiles/block_pass_large_dense.md); each is valid
 # only for the kernel sources it was measured on (hash of those sources).
 #   forest pass, M = 1: 9.313 GB read + 7.3 MB written for 1,072,703,284 streamed edges
-#   block pass stream: 9.494 GB read + 10.8 MB written for 1,073,547,340 streamed edges
+#   block pass stream: 9.508 GB read + 10.8 MB written for 1,073,547,340 streamed edges
 TRAFFIC = {"certify_sha": "a3aadd48ba1c58f6", "bytes_per_edge": 8.6815}
-AP_TRAFFIC = {"blocks_sha": "e40f3ec967d1ea6b", "bytes_per_edge": 8.8536}
+AP_TRAFFIC = {"blocks_sha": "288877966afd280c", "bytes_per_edge": 8.8667}
 
 
 def peaks():
