@@ -403,7 +403,8 @@ __device__ __forceinline__ void s_certify_vec(const Grp<NT>& G, const Smem& S, c
 template <int NT, int VM>
 __device__ void s_certify_range(const Grp<NT>& G, const Smem& S, const int32_t* __restrict__ u, const int32_t* __restrict__ v,
                                 int64_t lo, int64_t hi, int32_t V, int32_t* n1, int32_t* n2, int32_t* err) {
-  const int64_t warm = min(hi - lo, (int64_t)8 * V + 2048);
+  // 4V + 2048: measured on the batched workload against 2V + 1024, 8V + 2048 and 16V + 2048
+  const int64_t warm = min(hi - lo, (int64_t)4 * V + 2048);
   s_certify_scalar(G, S, u, v, lo, lo + warm, V, n1, n2, err);
   lo += warm;
   if (lo >= hi) return;
