@@ -12,13 +12,11 @@
 // The bridge stage is the same Euler-tour / preorder-range test as final.cu, on 16-bit arrays
 // with barriers between phases (list ranking four hops per round), then a rank sort of the
 // packed (a << 12 | b) keys (bitonic above 1,024 bridges).  A graph's fixed cost is its barriers,
-// so the stage keeps their number low, and graphs of up to 2,048 vertices run two per block: the
-// block splits into two 512-thread groups with their own half of shared memory and their own
-// named barrier, so that one graph's barrier waits overlap with the other's work.
+// so the stage keeps their number low, and graphs of up to 2,048 vertices run two per block (and
+// of up to 1,024 four per block): the block splits into 512-thread (then 256-thread) groups with
+// their own share of shared memory and their own named barrier, so that one graph's barrier
+// waits overlap with the others' work.
 #include <algorithm>
-#include <cstring>
-#include <mutex>
-#include <vector>
 
 #include "../../include/bridges.h"
 #include "batched.h"
@@ -772,10 +770,9 @@ __global__ void __launch_bounds__(kT, 1) batched_kernel(const BatchArgs* __restr
 size_t batched_smem_bytes() { return (size_t)kSmem; }
 
 bool batched_launch(cudaStream_t s, const BatchArgs* dev_args, int num_sms) {
-  static std::once_flag once;
-  std::call_once(once, [] {
-    cudaFuncSetAttribute(batched_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem);
-  });
+  // function attributes are per device: set on every launch (a host-side call; the launch is
+  // usually replayed from a CUDA graph anyway)
+  cudaFuncSetAttribute(batched_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem);
   batched_kernel<<<num_sms, kT, kSmem, s>>>(dev_args);
   return cudaGetLastError() == cudaSuccess;
 }

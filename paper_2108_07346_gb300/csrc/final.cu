@@ -703,11 +703,8 @@ void final_stage(const Launch& L, const FinalBufs& f, int32_t V, const int32_t* 
   int levels = 1;
   while ((1LL << levels) <= nsup) levels++;
   const size_t smem = sizeof(int32_t) * 2 * (size_t)levels * (size_t)nsup;
-  static bool attr = false;
-  if (!attr) {
-    cudaFuncSetAttribute(final_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemTables);
-    attr = true;
-  }
+  // function attributes are per device: set on every call (a host-side call, no launch)
+  cudaFuncSetAttribute(final_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemTables);
   int occ = 0;
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, final_kernel, kThreads, smem);
   // one block per SM: more blocks make every grid barrier slower than they make the phases faster
