@@ -16,6 +16,8 @@
 #include <numeric>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 using namespace bridges;
 
 
@@ -24,6 +26,15 @@ using namespace bridges;
 namespace {
 
 constexpr size_t kMiscBytes = 1024;  // status word, device counts of bridges_from_forest
+
+// NVTX range for the duration of a host scope (what the host enqueues; a profiler correlates the
+// launches inside it).  Header-only NVTX: without an attached tool a push / pop is a no-op.
+struct Range {
+  explicit Range(const char* name) { nvtxRangePushA(name); }
+  ~Range() { nvtxRangePop(); }
+  Range(const Range&) = delete;
+  Range& operator=(const Range&) = delete;
+};
 
 struct Carved {
   int32_t* status;
@@ -143,6 +154,7 @@ int init_ctx(bridges_ctx* c, int device, const bridges_opts* opts) {
 // The whole path on device-resident edges.  Leaves the count on the device (fin.count).
 int64_t run_path(bridges_ctx* c, cudaStream_t s, const int32_t* u, const int32_t* v, int64_t E, int32_t V, int32_t M,
                  int32_t* out, Carved* kout, CertPlan* pout) {
+  Range range("bridges: certificate + final stage");
   CertPlan p = plan_for(c, E, V, M);
   int64_t rc = ensure_ws(c, total_bytes(p), s);
   if (rc != BRIDGES_OK) return rc;
@@ -190,6 +202,7 @@ int64_t check_args(const bridges_ctx* c, const void* u, const void* v, int64_t E
 // output space.  Enqueue only.
 int64_t stage_host_edges(bridges_ctx* c, cudaStream_t s, const int32_t* hu, const int32_t* hv, int64_t E, int32_t V,
                          const int32_t** ru_out, const int32_t** rv_out, int32_t** dout_out) {
+  Range range("bridges: host edges");
   // pinned, mapped host memory can be streamed by the kernels in place (no device copy of the
   // edges: graphs larger than device memory work this way)
   const int32_t* ru = nullptr;
@@ -590,6 +603,7 @@ int64_t plan_batch_tasks(std::vector<BatchTask>& graphs, int64_t split, std::vec
 int64_t launch_batch_tasks(bridges_ctx* c, cudaStream_t s, const std::vector<BatchTask>& tasks, int32_t G,
                            int64_t slot_words) {
   if (tasks.empty()) return BRIDGES_OK;
+  Range range("bridges: batched launch");
   int64_t rc = ensure_batched(c, s, (int64_t)tasks.size(), G, slot_words);
   if (rc) return rc;
   // the staging area may still feed the previous batch's upload
@@ -921,6 +935,7 @@ extern "C" int64_t bridges_articulation_points(bridges_ctx* c, struct CUstream_s
     final_stage(L, k.fin, V, k.cert.f1u, k.cert.f1v, k.cert.cnt + 0, V, k.cert.f2u, k.cert.f2v, k.cert.cnt + 1, V,
                 k.cert.P1, k.fin.dscan);
   }
+  Range range("bridges: articulation block pass");
   ApBufs b = carve_ap(static_cast<char*>(c->ws) + ap_at, V);
   // the block pass streams the whole list as one partition, its own warm-up before the snapshot
   CertPlan q = plan_for(c, E, V, 1);

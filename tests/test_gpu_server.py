@@ -86,3 +86,47 @@ def test_budget_and_errors(cuda_lib):
     got, _ = srv.wait(t)
     assert got.cpu().numpy().tolist() == [[0, 1], [1, 2]]
     srv.close()
+
+
+def test_client_threads_and_an_abandoned_ticket(cuda_lib):
+    """Several client threads submit and wait concurrently; one thread dies right after
+    submitting (its ticket is never waited on).  The others get their exact results, the server
+    still completes the abandoned request, and closing it does not hang."""
+    import threading
+
+    graphs = [graphgen.generate(graphgen.workload_spec("batched", 8, i)) for i in range(24)]
+    refs = [oracle.dfs_bridges(g.u, g.v, g.V).tolist() for g in graphs]
+    dgraphs = [(dev(g.u), dev(g.v), g.V) for g in graphs]
+    srv = cuda_lib.Server(device="cuda:0", max_slots=3)
+    errors = []
+
+    def client(k):
+        try:
+            for i in range(k, len(dgraphs), 4):
+                u, v, V = dgraphs[i]
+                got, _ = srv.wait(srv.submit(u, v, V))
+                if got.cpu().numpy().tolist() != refs[i]:
+                    errors.append(i)
+        except Exception as e:  # surfaced below
+            errors.append(repr(e))
+
+    def dying_client():
+        u, v, V = dgraphs[0]
+        srv.submit(u, v, V)
+        raise SystemExit  # the thread ends without waiting for its ticket
+
+    threads = [threading.Thread(target=client, args=(k,)) for k in range(4)] + [threading.Thread(target=dying_client)]
+    for t in threads:
+        t.start()
+    for t in threads:
+        t.join(timeout=120)
+        assert not t.is_alive()
+    assert errors == []
+    import time
+
+    for _ in range(1000):  # the abandoned request completes on its own
+        if srv.stats()["completed"] >= len(dgraphs) + 1:
+            break
+        time.sleep(0.01)
+    assert srv.stats()["completed"] == len(dgraphs) + 1 and srv.stats()["failures"] == 0
+    srv.close()
