@@ -72,6 +72,9 @@ def _load():
         lib.gg_workload_spec.argtypes = [ctypes.c_int, ctypes.c_uint64, ctypes.c_int64, ctypes.c_int32,
                                          ctypes.c_int32, ctypes.c_double, ctypes.c_double,
                                          ctypes.POINTER(_Spec)]
+        lib.gg_rmat.restype = None
+        lib.gg_rmat.argtypes = [ctypes.c_uint64, ctypes.c_int32, ctypes.c_int64, ctypes.c_double, ctypes.c_double,
+                                ctypes.c_double, ctypes.c_void_p, ctypes.c_void_p]
         lib.gg_random_multigraph.argtypes = [ctypes.c_uint64, ctypes.c_int32, ctypes.c_int64,
                                              ctypes.c_void_p, ctypes.c_void_p]
         lib.gg_num_threads.restype = ctypes.c_int
@@ -205,6 +208,18 @@ def random_multigraph(seed: int, V: int, E: int):
     v = np.empty(E, np.int32)
     if E:
         lib.gg_random_multigraph(seed, V, E, u.ctypes.data, v.ctypes.data)
+    return u, v
+
+
+def rmat(seed: int, scale: int, E: int, a: float = 0.57, b: float = 0.19, c: float = 0.19):
+    """Seeded R-MAT graph on 2**scale vertices (skewed degrees; self-loops and repeats kept)."""
+    if not 1 <= scale <= 30:
+        raise ValueError("scale must be in [1, 30]")
+    lib = _load()
+    u = np.empty(E, np.int32)
+    v = np.empty(E, np.int32)
+    if E:
+        lib.gg_rmat(seed, scale, E, a, b, c, u.ctypes.data, v.ctypes.data)
     return u, v
 
 

@@ -499,6 +499,29 @@ void gg_random_multigraph(uint64_t seed, int32_t V, int64_t E, int32_t* u, int32
   }
 }
 
+/* R-MAT graph (Chakrabarti, Zhan & Faloutsos, SDM 2004): each of E edges picks one of the four
+ * quadrants of the 2^scale x 2^scale adjacency matrix with probabilities a, b, c, 1-a-b-c, scale
+ * times over; vertex ids are then relabelled by the keyed bijection (so hubs do not sit at small
+ * ids).  Self-loops and repeated edges are kept.  Skewed degrees: a few hubs, many leaves. */
+void gg_rmat(uint64_t seed, int32_t scale, int64_t E, double a, double b, double c, int32_t* u, int32_t* v) {
+  const uint64_t ta = density_threshold(a), tb = density_threshold(a + b), tc = density_threshold(a + b + c);
+  const uint64_t key = stream_key(seed, 91);
+  perm_t P;
+  perm_init(&P, (uint64_t)1 << scale, seed, 92);
+#pragma omp parallel for schedule(static)
+  for (int64_t i = 0; i < E; i++) {
+    uint64_t x = 0, y = 0;
+    for (int32_t k = 0; k < scale; k++) {
+      const uint64_t r = draw(key, (uint64_t)i * (uint64_t)scale + (uint64_t)k);
+      const uint64_t bx = r >= tb, by = (r >= ta && r < tb) || r >= tc;
+      x = (x << 1) | bx;
+      y = (y << 1) | by;
+    }
+    u[i] = (int32_t)perm_apply(&P, x);
+    v[i] = (int32_t)perm_apply(&P, y);
+  }
+}
+
 int gg_num_threads(void) {
 #ifdef _OPENMP
   return omp_get_max_threads();

@@ -110,3 +110,20 @@ def test_empty_and_degenerate(ctx):
     res = run_batch(ctx, [(e, e, 0), (e, e, 1), (np.array([0], np.int32), np.array([0], np.int32), 1),
                           (np.array([0], np.int32), np.array([1], np.int32), 2)])
     assert [r.tolist() for r in res] == [[], [], [], [[0, 1]]]
+
+
+def test_rmat_graphs_all_group_sizes(ctx):
+    """Skewed-degree graphs of every group size: whole-block (V > 2048), half-block (1025-2048)
+    and quarter-block (<= 1024) tasks in one launch, each against the oracle."""
+    graphs = []
+    for t, scale in enumerate([6, 8, 10, 10, 11, 11, 12, 12] * 6):
+        V = 1 << scale
+        if t % 3 == 0:
+            V -= t  # ragged sizes: not every graph a power of two
+        u, v = graphgen.rmat(300 + t, scale, 8 << scale)
+        keep = (u < V) & (v < V)
+        graphs.append((u[keep], v[keep], V))
+    assert any(V > 2048 for _, _, V in graphs) and any(1024 < V <= 2048 for _, _, V in graphs)
+    res = run_batch(ctx, graphs)
+    for (u, v, V), got in zip(graphs, res):
+        assert got.tolist() == oracle.dfs_bridges(u, v, V).tolist()

@@ -252,3 +252,14 @@ def test_plan_options(cuda_lib, warm_block, warm_edges):
     for M in (1, 6):
         assert c.find(du, dv, g.V, M).cpu().numpy().tolist() == ref.tolist(), (warm_block, warm_edges, M)
     assert c.get_opts()["warm_block"] == warm_block
+
+
+@pytest.mark.parametrize("scale,factor", [(10, 4), (12, 16), (14, 8), (16, 16), (17, 4)])
+def test_rmat_skewed_degrees(ctx, scale, factor):
+    """Power-law (R-MAT) graphs: hubs with thousands of edges, many leaves and isolated vertices,
+    self-loops and repeats -- a contention pattern the uniform workloads do not have."""
+    V = 1 << scale
+    u, v = graphgen.rmat(100 + scale, scale, factor * V)
+    ref = oracle.dfs_bridges(u, v, V)
+    for M in (1, 5):
+        assert gpu_bridges(ctx, u, v, V, M).tolist() == ref.tolist(), M

@@ -48,3 +48,17 @@ def test_batched_planted_subset():
         g = graphgen.generate(graphgen.workload_spec("batched", 3, i))
         found = {tuple(x) for x in oracle.bridges(g.u, g.v, g.V, 4).tolist()}
         assert {tuple(x) for x in g.planted.tolist()} <= found
+
+
+def test_rmat_is_seeded_skewed_and_in_range():
+    u, v = graphgen.rmat(5, 12, 60000)
+    u2, v2 = graphgen.rmat(5, 12, 60000)
+    assert np.array_equal(u, u2) and np.array_equal(v, v2)
+    assert u.min() >= 0 and v.min() >= 0 and u.max() < 4096 and v.max() < 4096
+    deg = np.bincount(np.concatenate([u, v]), minlength=4096)
+    assert deg.max() > 50 * np.median(deg[deg > 0])  # hubs
+    assert not np.array_equal(graphgen.rmat(6, 12, 60000)[0], u)
+    # the uniform quadrant mix is a uniform random multigraph: no hubs
+    uu, vv = graphgen.rmat(5, 12, 60000, 0.25, 0.25, 0.25)
+    d2 = np.bincount(np.concatenate([uu, vv]), minlength=4096)
+    assert d2.max() < 3 * d2.mean()
