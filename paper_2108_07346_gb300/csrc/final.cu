@@ -39,6 +39,7 @@ constexpr unsigned kSpinCap = 1u << 22;
 constexpr int kHopsLog = 2;  // pointer-jumping hops per round: 4 (8 was slower: longer load chains)
 constexpr int kHops = 1 << kHopsLog;
 constexpr int kMaxBlocks = 1024;
+constexpr int kScanItems = 8;  // consecutive elements per thread in a grid-scan tile
 constexpr size_t kSmemTables = sizeof(int32_t) * 2 * kSupLevels * kMaxSup;
 
 struct FinArgs {
@@ -164,16 +165,33 @@ __device__ bool grid_scan(const FinalBufs& f, const int32_t* in0, int32_t* out0,
   }
   c0 = block_sum(c0, red);
   if (in1) c1 = block_sum(c1, red);
-  for (int64_t t0 = lo; t0 < hi; t0 += blockDim.x) {
-    const int64_t i = t0 + threadIdx.x;
-    const int32_t v0 = i < hi ? in0[i] : 0;
-    const int32_t v1 = (in1 && i < hi) ? in1[i] : 0;
+  // tiles of blockDim * kScanItems; each thread scans kScanItems consecutive elements itself,
+  // so a block barrier pair serves kScanItems elements per thread, not one
+  const int64_t tile = (int64_t)blockDim.x * kScanItems;
+  for (int64_t t0 = lo; t0 < hi; t0 += tile) {
+    const int64_t i0 = t0 + (int64_t)threadIdx.x * kScanItems;
+    int32_t a0[kScanItems], a1[kScanItems];
+    int32_t s0 = 0, s1 = 0;
+#pragma unroll
+    for (int k = 0; k < kScanItems; k++) {
+      const int64_t i = i0 + k;
+      a0[k] = i < hi ? in0[i] : 0;
+      a1[k] = (in1 && i < hi) ? in1[i] : 0;
+      s0 += a0[k];
+      s1 += a1[k];
+    }
     int32_t tot0 = 0, tot1 = 0;
-    const int32_t e0 = block_excl(v0, red, &tot0);
-    const int32_t e1 = in1 ? block_excl(v1, red, &tot1) : 0;
-    if (i < hi) {
-      out0[i] = c0 + e0;
-      if (in1) out1[i] = c1 + e1;
+    int32_t e0 = block_excl(s0, red, &tot0);
+    int32_t e1 = in1 ? block_excl(s1, red, &tot1) : 0;
+#pragma unroll
+    for (int k = 0; k < kScanItems; k++) {
+      const int64_t i = i0 + k;
+      if (i < hi) {
+        out0[i] = c0 + e0;
+        if (in1) out1[i] = c1 + e1;
+      }
+      e0 += a0[k];
+      e1 += a1[k];
     }
     c0 += tot0;
     c1 += tot1;
@@ -257,41 +275,39 @@ __global__ void __launch_bounds__(kThreads) final_kernel(FinArgs A) {
       s = t + 1;
     else
       s = f.root[y] == y ? -1 : f.off[y];
-    f.succ[i] = s;
+    f.sr[i] = make_int2(s, s < 0 ? 0 : 1);
     f.rnk[i] = s < 0 ? 0 : 1;
   }
   BARRIER();
 
   // 4: list ranking by pointer jumping (Wyllie), kHops hops per round: after round r every arc
   //    knows the arc kHops^r places ahead and the rank sum up to it, so ceil(log_kHops n) rounds
-  //    (and barriers) suffice; each round reads the previous round's arrays only.  Longer hop
-  //    chains trade dependent loads (cheap) for barriers (expensive).
+  //    (and barriers) suffice; each round reads the previous round's array only.  Longer hop
+  //    chains trade dependent loads (cheap) for barriers (expensive).  Successor and rank share
+  //    one 8-byte word, so a hop is one random load (one sector), not two.
   {
     int rounds = 0;
     while ((1LL << (kHopsLog * rounds)) < (int64_t)max(narcs, 1)) rounds++;
-    int32_t *sa = f.succ, *ra = f.rnk, *sb = f.succ2, *rb = f.rnk2;
+    int2* sa = f.sr;
+    int2* sb = f.sr2;
     for (int r = 0; r < rounds; r++) {
+      const bool last = r == rounds - 1;
       for (int64_t i = gtid(); i < narcs; i += gstride()) {
-        int32_t s = sa[i], acc = ra[i];
+        const int2 x = sa[i];
+        int32_t s = x.x, acc = x.y;
 #pragma unroll
         for (int h = 0; h < kHops - 1 && s >= 0; h++) {
-          acc += ra[s];
-          s = sa[s];
+          const int2 y = sa[s];
+          acc += y.y;
+          s = y.x;
         }
-        rb[i] = acc;
-        sb[i] = s;
+        sb[i] = make_int2(s, acc);
+        if (last) f.rnk[i] = acc;
       }
       BARRIER();
-      int32_t* t = sa;
+      int2* t = sa;
       sa = sb;
       sb = t;
-      t = ra;
-      ra = rb;
-      rb = t;
-    }
-    if (ra != f.rnk) {
-      for (int64_t i = gtid(); i < narcs; i += gstride()) f.rnk[i] = ra[i];
-      BARRIER();
     }
   }
 
@@ -644,7 +660,8 @@ size_t final_bytes(int32_t V) {
   size_t s = 0;
   s += 3 * 256;                                                           // count, nkeys, barrier
   s += 15 * align_up(sizeof(int32_t) * (Vs + 1), 256);                    // V-long arrays
-  s += 7 * align_up(sizeof(int32_t) * (2 * Vs + 1), 256);                 // 2V-long arrays
+  s += 5 * align_up(sizeof(int32_t) * (2 * Vs + 1), 256);                 // 2V-long arrays
+  s += 2 * align_up(sizeof(int2) * (2 * Vs + 1), 256);                    // packed successor / rank
   s += 4 * align_up(sizeof(int32_t) * (Vs / kChunk + 2), 256);            // chunk / superchunk min, max
   s += 2 * align_up(sizeof(uint64_t) * Vs, 256);                          // keys
   s += align_up(sizeof(int32_t) * (256 * (size_t)kMaxBlocks + 1), 256);  // radix histograms
@@ -670,13 +687,16 @@ FinalBufs carve_final(void* base, int32_t V, int32_t* status) {
     *a = reinterpret_cast<int32_t*>(c);
     c += align_up(sizeof(int32_t) * (Vs + 1), 256);
   }
-  int32_t** va2[7] = {&f.dst, &f.twin, &f.succ, &f.succ2, &f.rnk, &f.dflag, &f.dscan};
+  int32_t** va2[5] = {&f.dst, &f.twin, &f.rnk, &f.dflag, &f.dscan};
   for (auto a : va2) {
     *a = reinterpret_cast<int32_t*>(c);
     c += align_up(sizeof(int32_t) * (2 * Vs + 1), 256);
   }
-  // the pointer-jumping double buffer of the ranks reuses dscan, free until the preorder scan
-  f.rnk2 = f.dscan;
+  int2** vp[2] = {&f.sr, &f.sr2};
+  for (auto a : vp) {
+    *a = reinterpret_cast<int2*>(c);
+    c += align_up(sizeof(int2) * (2 * Vs + 1), 256);
+  }
   int32_t** vc[4] = {&f.cmin, &f.cmax, &f.smin, &f.smax};
   for (auto a : vc) {
     *a = reinterpret_cast<int32_t*>(c);
@@ -707,8 +727,10 @@ void final_stage(const Launch& L, const FinalBufs& f, int32_t V, const int32_t* 
   cudaFuncSetAttribute(final_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemTables);
   int occ = 0;
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, final_kernel, kThreads, smem);
-  // one block per SM: more blocks make every grid barrier slower than they make the phases faster
-  const int occ_blocks = std::max(1, std::min(occ, 1));
+  // one block per SM: more blocks make every grid barrier slower than they make the phases
+  // faster -- except on forests of a million vertices and more, where the phases' dependent
+  // random loads need the extra threads
+  const int occ_blocks = std::max(1, std::min(occ, V >= (1 << 20) ? 2 : 1));
   FinArgs A{};
   A.f = f;
   A.V = V;

@@ -67,10 +67,9 @@ struct FinalBufs {
   int32_t* cur;    // [V]
   int32_t* dst;    // [2V]
   int32_t* twin;   // [2V]
-  int32_t* succ;   // [2V]
-  int32_t* succ2;  // [2V]
-  int32_t* rnk;    // [2V]
-  int32_t* rnk2;   // [2V] (aliases dscan)
+  int2* sr;        // [2V] Euler-tour successor and rank, packed (one load per pointer jump)
+  int2* sr2;       // [2V] its double buffer
+  int32_t* rnk;    // [2V] final ranks
   int32_t* aoff;   // [V+1] arc offset of each tree
   int32_t* vbase;  // [V+1] preorder base of each tree
   int32_t* dflag;  // [2V+1]
