@@ -214,7 +214,7 @@ __global__ void __launch_bounds__(1024, 1) ap_pass_kernel(PassArgs P) {
   const int64_t s = P.s + n * blockIdx.x / gridDim.x, t = P.s + n * (blockIdx.x + 1) / gridDim.x;
   if (CACHE) load_labels(slab, P.lab, P.Vpad);
   const CycleSink S{P.A};
-  stream_range<CACHE, VEC, kUnroll>(S, P.u, P.v, s, t, P.A.V, slab);
+  stream_range<CACHE ? 1 : 0, VEC, kUnroll>(S, P.u, P.v, s, t, (uint32_t)P.A.V, slab);
 }
 
 // ---- label snapshot: each vertex takes the largest class it belongs to ----

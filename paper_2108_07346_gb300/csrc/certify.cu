@@ -137,12 +137,13 @@ struct LeafArgs {
   int32_t G;
   int64_t warm;
   int32_t mode;  // 0: warm-up prefix of each chunk, 1: the rest of each chunk
+  int32_t Vb;    // bitmap snapshot: vertices it covers
   CertBufs b;
 };
 
 // Forest pass over the partitions: block -> (job j = blockIdx / G, member m = blockIdx % G);
 // member m streams its share of job j's chunk [E j / M, E (j+1) / M) (Sec. 3 partition).
-template <bool CACHE, bool VEC>
+template <int MODE, bool VEC>
 __global__ void __launch_bounds__(1024, 1) leaf_kernel(LeafArgs A) {
   extern __shared__ __align__(16) uint16_t slab[];
   const int64_t j = blockIdx.x / A.G, m = blockIdx.x % A.G;
@@ -152,10 +153,11 @@ __global__ void __launch_bounds__(1024, 1) leaf_kernel(LeafArgs A) {
   const int64_t z = A.mode == 0 ? lo + w : hi;
   const int64_t n = z - a;
   const int64_t s = a + n * m / A.G, t = a + n * (m + 1) / A.G;
-  if (CACHE) load_labels(slab, A.b.lab + j * A.b.Vpad, A.b.Vpad);
+  if (MODE == 1) load_labels(slab, A.b.lab + j * A.b.Vpad, A.b.Vpad);
+  if (MODE == 2) load_words(slab, A.b.lab + j * A.b.Vpad, (A.Vb / 32 + 4) / 4);
   const Job J = job_of(A.b, A.V, j);
   const ForestSink S{J, A.V, A.b.status};
-  stream_range<CACHE, VEC, kUnroll>(S, A.u, A.v, s, t, A.V, slab);
+  stream_range<MODE, VEC, kUnroll>(S, A.u, A.v, s, t, MODE == 2 ? (uint32_t)A.Vb : (uint32_t)A.V, slab);
 }
 
 struct MergeArgs {
@@ -210,7 +212,7 @@ __global__ void init_kernel(CertBufs b, int32_t V, int32_t M) {
 // ---- label snapshot of F' for jobs j*step, j < njobs ----
 // 1) flatten: P2[x] = root(x) (no link can run now, so roots are fixed and the walk is
 //    read-only); reset the per-root label ids (tmp) and the job's label counter.
-__global__ void snap_flatten_kernel(CertBufs b, int32_t V, int64_t step, int64_t njobs) {
+__global__ void snap_flatten_kernel(CertBufs b, int32_t V, int64_t step, int64_t njobs, int32_t tmp_init) {
   const int64_t total = njobs * V;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
     const int64_t j = (i / V) * step;
@@ -222,8 +224,11 @@ __global__ void snap_flatten_kernel(CertBufs b, int32_t V, int64_t step, int64_t
       p = __ldca(P2 + r);
     }
     P2[x] = r;
-    b.tmp[j * V + x] = -1;
-    if (x == 0) b.nlab[j] = 0;
+    b.tmp[j * V + x] = tmp_init;
+    if (x == 0) {
+      b.nlab[j] = 0;
+      b.giant[j] = 0;
+    }
   }
 }
 
@@ -276,6 +281,53 @@ __global__ void snap_roots_kernel(CertBufs b, int32_t V, int64_t step, int64_t n
   }
 }
 
+// ---- bitmap snapshot (large V): the largest F' component of each job as one bit per vertex ----
+// 1) sizes of the F' components (tmp counts members; the flatten set tmp to 0), lanes with the
+//    same root adding once per warp
+__global__ void bm_count_kernel(CertBufs b, int32_t V, int64_t njobs) {
+  const int64_t total = njobs * V;
+  const int lane = threadIdx.x & 31;
+  for (int64_t base = blockIdx.x * (int64_t)blockDim.x; base < total; base += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = base + threadIdx.x;
+    const bool in = i < total;
+    const int64_t j = in ? i / V : 0;
+    const int32_t x = in ? (int32_t)(i % V) : 0;
+    const long long key = in ? j * (long long)V + b.P2[j * V + x] : -1LL - lane;
+    const unsigned peers = __match_any_sync(kFull, (unsigned long long)key);
+    if (in && lane == __ffs(peers) - 1) atomicAdd(b.tmp + key, __popc(peers));
+  }
+}
+
+// 2) the largest component of each job: (size << 32 | ~root), ties to the smaller root
+__global__ void bm_best_kernel(CertBufs b, int32_t V, int64_t njobs) {
+  const int64_t total = njobs * V;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t j = i / V;
+    const int32_t x = (int32_t)(i % V);
+    if (b.P2[i] != x) continue;
+    const int32_t c = b.tmp[i];
+    if (c >= 2) atomicMax(b.giant + j, ((unsigned long long)c << 32) | (0xffffffffu - (uint32_t)x));
+  }
+}
+
+// 3) the bitmap words (in the job's label area): bit x set iff x < min(V, Vb) lies in the largest
+//    component; the word past Vb / 32 stays clear (the clamp target of out-of-range ids)
+__global__ void bm_write_kernel(CertBufs b, int32_t V, int32_t Vb, int64_t njobs) {
+  const int64_t nw = Vb / 32 + 4;  // a multiple of 4 words: the leaf kernel copies 16-byte units
+  const int64_t total = njobs * nw;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t j = i / nw, w = i % nw;
+    const unsigned long long g = b.giant[j];
+    const int32_t root = g ? (int32_t)(0xffffffffu - (uint32_t)(g & 0xffffffffu)) : -1;
+    uint32_t bits = 0;
+    for (int k = 0; k < 32; k++) {
+      const int64_t x = w * 32 + k;
+      if (root >= 0 && x < V && x < Vb && b.P2[j * V + x] == root) bits |= 1u << k;
+    }
+    reinterpret_cast<uint32_t*>(b.lab + j * b.Vpad)[w] = bits;
+  }
+}
+
 // Range check of edges offered to an existing certificate; the offer is skipped on failure.
 __global__ void offer_check_kernel(int32_t* status, int32_t V, const int32_t* u, const int32_t* v, int64_t n) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
@@ -318,15 +370,26 @@ int grid_for(const Launch& L, int64_t work, int block) {
 void snapshot(const Launch& L, const CertPlan& p, const CertBufs& b, int64_t step, int64_t njobs) {
   const int bs = 256;
   int g = grid_for(L, njobs * (int64_t)p.V, bs);
-  snap_flatten_kernel<<<g, bs, 0, L.stream>>>(b, p.V, step, njobs);
+  snap_flatten_kernel<<<g, bs, 0, L.stream>>>(b, p.V, step, njobs, -1);
   snap_members_kernel<<<g, bs, 0, L.stream>>>(b, p.V, step, njobs);
   snap_roots_kernel<<<grid_for(L, njobs * b.Vpad, bs), bs, 0, L.stream>>>(b, p.V, step, njobs);
   *L.launches += 3;
 }
 
-template <bool CACHE, bool VEC>
+// The bitmap snapshot of every job (M partitions after the warm-up).
+void snapshot_bitmap(const Launch& L, const CertPlan& p, const CertBufs& b) {
+  const int bs = 256;
+  const int g = grid_for(L, (int64_t)p.M * p.V, bs);
+  snap_flatten_kernel<<<g, bs, 0, L.stream>>>(b, p.V, 1, p.M, 0);
+  bm_count_kernel<<<g, bs, 0, L.stream>>>(b, p.V, p.M);
+  bm_best_kernel<<<g, bs, 0, L.stream>>>(b, p.V, p.M);
+  bm_write_kernel<<<grid_for(L, (int64_t)p.M * (p.Vb / 32 + 4), bs), bs, 0, L.stream>>>(b, p.V, p.Vb, p.M);
+  *L.launches += 4;
+}
+
+template <int MODE, bool VEC>
 void launch_leaf(const Launch& L, const CertPlan& p, const LeafArgs& a, size_t smem) {
-  auto k = leaf_kernel<CACHE, VEC>;
+  auto k = leaf_kernel<MODE, VEC>;
   if (smem > 48 * 1024) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   // the warm-up launch is contention-bound on the union-finds: it may use fewer threads
   k<<<(unsigned)((int64_t)p.M * p.G), a.mode == 0 ? p.warm_block : p.block, smem, L.stream>>>(a);
@@ -352,10 +415,18 @@ CertPlan make_plan(int64_t E, int32_t V, int32_t M, int32_t fan_in, int32_t bloc
   p.f = fan_in > 1 ? fan_in : std::max(2, std::min(p.M, 16));
   const int64_t Vpad = (int64_t)align_up((size_t)V + 1, 8);  // entry V: the kNoLabel sentinel
   const size_t lab_bytes = (size_t)Vpad * 2;
-  const bool fits = lab_bytes + 1024 <= smem_optin;
+  const bool labels_fit = lab_bytes + 1024 <= smem_optin;
+  // Too many vertices for 16-bit labels: one bit per vertex marks the largest F' component
+  // (vertices past the bitmap's reach, if any, always take the union-find path).  The bitmap
+  // lives in the job's label area (2 Vpad bytes >= its (Vb / 32 + 4) words).
+  const int64_t bm_cap = (((int64_t)(smem_optin - 1024) / 4 - 4) * 32) / 128 * 128;
+  p.mode = labels_fit ? 1 : 2;
+  p.Vb = (int32_t)std::min<int64_t>(align_up((size_t)std::max(V, 1), 128), std::max<int64_t>(bm_cap, 128));
+  const bool fits = labels_fit || bm_cap >= 128;
   int cps = ctas_per_sm;
   if (cps <= 0) {
-    cps = fits ? (int)std::max<size_t>(1, std::min<size_t>(4, (228 * 1024) / (lab_bytes + 2048))) : 2;
+    const size_t snap_bytes = labels_fit ? lab_bytes : (size_t)(p.Vb / 32 + 4) * 4;
+    cps = fits ? (int)std::max<size_t>(1, std::min<size_t>(4, (228 * 1024) / (snap_bytes + 2048))) : 2;
   }
   p.block = block > 0 ? block : (cps <= 2 ? 1024 : 512);
   p.G = (int32_t)std::max<int64_t>(1, ((int64_t)num_sms * cps) / p.M);
@@ -365,7 +436,13 @@ CertPlan make_plan(int64_t E, int32_t V, int32_t M, int32_t fan_in, int32_t bloc
   // 0.6 V ln V the snapshot still misses a few vertices whose edges then all take the union-find
   // path (measured on the large workload: 41 k such edges and a 2.3x slower forest pass at
   // 0.6 V ln V, only the 8.3 k pendant-tree edges at 1.2 V ln V).
-  if (warm < 0) warm = (int64_t)std::ceil(1.2 * V * lnv) + 4096;
+  if (warm < 0) {
+    warm = (int64_t)std::ceil(1.2 * V * lnv) + 4096;
+    // graphs too large for labels (usually sparse): their giant F' component forms within a
+    // small fraction of the list, while the V ln V prefix of dense graphs could exceed it; a
+    // sixteenth was fastest or near it on R-MAT graphs of 2^17 to 2^22 vertices (E/64 to E/4)
+    if (!labels_fit) warm = std::min<int64_t>(warm, chunk / 16 + 4096);
+  }
   p.cache = fits && warm > 0 && warm < chunk;
   p.warm = p.cache ? warm : chunk + 1;
   // The warm-up prefix is bound by contention on the union-finds' roots, not by bandwidth: a
@@ -386,6 +463,7 @@ size_t cert_bytes(const CertPlan& p) {
   s += 256;                                         // status
   s += align_up(sizeof(int32_t) * 2 * p.M, 256);    // cnt
   s += align_up(sizeof(int32_t) * p.M, 256);        // nlab
+  s += align_up(sizeof(unsigned long long) * p.M, 256);  // giant
   s += 7 * align_up(sizeof(int32_t) * MV, 256);     // P1 P2 f1u f1v f2u f2v tmp
   s += align_up(sizeof(uint16_t) * Vpad * p.M, 256);  // lab
   return s;
@@ -402,6 +480,8 @@ CertBufs carve_cert(void* base, const CertPlan& p) {
   c += align_up(sizeof(int32_t) * 2 * p.M, 256);
   b.nlab = reinterpret_cast<int32_t*>(c);
   c += align_up(sizeof(int32_t) * p.M, 256);
+  b.giant = reinterpret_cast<unsigned long long*>(c);
+  c += align_up(sizeof(unsigned long long) * p.M, 256);
   int32_t** arrs[7] = {&b.P1, &b.P2, &b.f1u, &b.f1v, &b.f2u, &b.f2v, &b.tmp};
   for (auto a : arrs) {
     *a = reinterpret_cast<int32_t*>(c);
@@ -420,13 +500,13 @@ void cert_init(const Launch& L, const CertPlan& p, const CertBufs& b) {
 void cert_leaves(const Launch& L, const CertPlan& p, const CertBufs& b, const int32_t* u, const int32_t* v,
                  cudaEvent_t* ev) {
   if (p.E == 0) return;
-  LeafArgs a{u, v, p.E, p.V, p.M, p.G, p.warm, 0, b};
+  LeafArgs a{u, v, p.E, p.V, p.M, p.G, p.warm, 0, p.Vb, b};
   const bool vec = ((reinterpret_cast<uintptr_t>(u) | reinterpret_cast<uintptr_t>(v)) & 15) == 0;
   if (ev) cudaEventRecord(ev[0], L.stream);
   if (vec)
-    launch_leaf<false, true>(L, p, a, 0);
+    launch_leaf<0, true>(L, p, a, 0);
   else
-    launch_leaf<false, false>(L, p, a, 0);
+    launch_leaf<0, false>(L, p, a, 0);
   if (ev) cudaEventRecord(ev[1], L.stream);
   if (!p.cache) {
     if (ev) {
@@ -435,14 +515,24 @@ void cert_leaves(const Launch& L, const CertPlan& p, const CertBufs& b, const in
     }
     return;
   }
-  snapshot(L, p, b, 1, p.M);
-  if (ev) cudaEventRecord(ev[2], L.stream);
   a.mode = 1;
-  const size_t smem = (size_t)b.Vpad * 2;
-  if (vec)
-    launch_leaf<true, true>(L, p, a, smem);
-  else
-    launch_leaf<true, false>(L, p, a, smem);
+  if (p.mode == 1) {
+    snapshot(L, p, b, 1, p.M);
+    if (ev) cudaEventRecord(ev[2], L.stream);
+    const size_t smem = (size_t)b.Vpad * 2;
+    if (vec)
+      launch_leaf<1, true>(L, p, a, smem);
+    else
+      launch_leaf<1, false>(L, p, a, smem);
+  } else {
+    snapshot_bitmap(L, p, b);
+    if (ev) cudaEventRecord(ev[2], L.stream);
+    const size_t smem = (size_t)(p.Vb / 32 + 4) * 4;
+    if (vec)
+      launch_leaf<2, true>(L, p, a, smem);
+    else
+      launch_leaf<2, false>(L, p, a, smem);
+  }
   if (ev) cudaEventRecord(ev[3], L.stream);
 }
 

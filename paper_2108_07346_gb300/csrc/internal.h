@@ -34,7 +34,10 @@ struct CertPlan {
   int32_t block;   // threads per block in the forest pass
   int32_t warm_block;  // threads per block of its warm-up launch
   int64_t warm;    // edges per partition certified before the snapshot (>= partition: no cache)
-  bool cache;      // label snapshot used (2V bytes of shared memory fit)
+  bool cache;      // a snapshot is taken after the warm-up
+  int32_t mode;    // its form: 1 = 16-bit F' labels (2V bytes fit in shared memory), 2 = bitmap
+                   // of the largest F' component (for larger V)
+  int32_t Vb;      // mode 2: vertices [0, Vb) covered by the bitmap (a multiple of 128)
 };
 
 // Device buffers of the certificate stages, carved from the workspace.  Job j owns the V-long
@@ -43,6 +46,7 @@ struct CertBufs {
   int32_t* status;  // [1] device status word
   int32_t* cnt;     // [2*M] forest sizes |F|, |F'| per job
   int32_t* nlab;    // [M] labels handed out per job
+  unsigned long long* giant;  // [M] bitmap snapshot: (size << 32 | ~root) of the largest F' component
   int32_t* P1;
   int32_t* P2;
   int32_t* f1u;

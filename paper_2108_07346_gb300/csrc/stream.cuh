@@ -16,6 +16,30 @@ __device__ __forceinline__ uint32_t miss_bit(int32_t a, int32_t b, int32_t V, co
   return (la == kNoLabel) | (la != lb);
 }
 
+// Fast-path test against a membership bitmap (bit x set: vertex x is in the one F' component the
+// bitmap marks).  Ids are clamped to clampv, whose bit is always clear, so out-of-range ids and
+// vertices beyond the bitmap fall through to the checked path.
+__device__ __forceinline__ uint32_t miss_bit_bm(int32_t a, int32_t b, uint32_t clampv, const uint32_t* sbm) {
+  const uint32_t ia = min((uint32_t)a, clampv), ib = min((uint32_t)b, clampv);
+  return ((sbm[ia >> 5] >> (ia & 31)) & (sbm[ib >> 5] >> (ib & 31)) & 1u) ^ 1u;
+}
+
+// The fast-path test of a stream: MODE 0 none (every edge misses), 1 16-bit labels, 2 bitmap.
+template <int MODE>
+__device__ __forceinline__ uint32_t miss_of(int32_t a, int32_t b, uint32_t clampv, const void* cache) {
+  if (MODE == 1) return miss_bit(a, b, (int32_t)clampv, static_cast<const uint16_t*>(cache));
+  if (MODE == 2) return miss_bit_bm(a, b, clampv, static_cast<const uint32_t*>(cache));
+  return 1u;
+}
+
+// Copies n 16-byte words of a snapshot into shared memory.
+__device__ __forceinline__ void load_words(void* dst, const void* src, int64_t n16) {
+  const int4* s = static_cast<const int4*>(src);
+  int4* d = static_cast<int4*>(dst);
+  for (int64_t i = threadIdx.x; i < n16; i += blockDim.x) d[i] = s[i];
+  __syncthreads();
+}
+
 // Copies a label snapshot (Vpad entries, Vpad a multiple of 8) into shared memory.
 __device__ __forceinline__ void load_labels(uint16_t* slab, const uint16_t* glab, int64_t Vpad) {
   const int4* src = reinterpret_cast<const int4*>(glab);
@@ -25,10 +49,11 @@ __device__ __forceinline__ void load_labels(uint16_t* slab, const uint16_t* glab
 }
 
 // Streams edges [s, t) of (u, v): 16-byte loads when both arrays are 16-byte aligned, U int4
-// units (4U edges) in flight per thread.  With the snapshot (CACHE), each edge costs two
-// shared-memory label reads; a per-thread bit mask collects the misses and one warp vote per
-// tile decides whether any lane must take the slow path.  Loop bounds are block-uniform so
-// every lane reaches the votes.
+// units (4U edges) in flight per thread.  With a snapshot in shared memory (MODE 1: labels,
+// clampv = V; MODE 2: bitmap, clampv = its first always-clear bit), each edge costs two
+// shared-memory reads; a per-thread bit mask collects the misses and one warp vote per tile
+// decides whether any lane must take the slow path.  Loop bounds are block-uniform so every
+// lane reaches the votes.
 //
 // The slow path is the Sink:
 //   S.slot(need, a, b)            every lane of the warp calls it; `need` marks a live edge that
@@ -36,10 +61,10 @@ __device__ __forceinline__ void load_labels(uint16_t* slab, const uint16_t* glab
 //   S.misses(m, ub, vb, base)     the edges of this thread's tile whose bit is set in m (bit
 //                                 4k+c: element 4*(base + k*nt + tid) + c of ub / vb); every
 //                                 lane of the warp calls it.
-template <bool CACHE, bool VEC, int U, class Sink>
+template <int MODE, bool VEC, int U, class Sink>
 __device__ __forceinline__ void stream_range(const Sink& S, const int32_t* __restrict__ u,
-                                             const int32_t* __restrict__ v, int64_t s, int64_t t, int32_t V,
-                                             const uint16_t* slab) {
+                                             const int32_t* __restrict__ v, int64_t s, int64_t t, uint32_t clampv,
+                                             const void* cache) {
   static_assert(4 * U <= 32, "the miss mask holds 32 edges");
   const int tid = threadIdx.x, nt = blockDim.x;
   int64_t s_al = s, t_al = s;
@@ -51,7 +76,7 @@ __device__ __forceinline__ void stream_range(const Sink& S, const int32_t* __res
     const int64_t i = i0 + tid;
     const bool valid = i < s_al;
     const int32_t a = valid ? ld_stream1(u + i) : 0, b = valid ? ld_stream1(v + i) : 0;
-    S.slot(valid && (!CACHE || miss_bit(a, b, V, slab)), a, b);
+    S.slot(valid && miss_of<MODE>(a, b, clampv, cache), a, b);
   }
   if (VEC) {
     const int32_t* ub = u + s_al;
@@ -77,13 +102,10 @@ __device__ __forceinline__ void stream_range(const Sink& S, const int32_t* __res
 #pragma unroll
       for (int k = 0; k < U; k++) {
         const bool valid = full || base + k * nt + tid < nunits;
-        uint32_t mk;
-        if (CACHE) {
-          mk = miss_bit(ua[k].x, va[k].x, V, slab) | (miss_bit(ua[k].y, va[k].y, V, slab) << 1) |
-               (miss_bit(ua[k].z, va[k].z, V, slab) << 2) | (miss_bit(ua[k].w, va[k].w, V, slab) << 3);
-        } else {
-          mk = 0xfu;
-        }
+        const uint32_t mk = miss_of<MODE>(ua[k].x, va[k].x, clampv, cache) |
+                            (miss_of<MODE>(ua[k].y, va[k].y, clampv, cache) << 1) |
+                            (miss_of<MODE>(ua[k].z, va[k].z, clampv, cache) << 2) |
+                            (miss_of<MODE>(ua[k].w, va[k].w, clampv, cache) << 3);
         m |= (valid ? mk : 0u) << (4 * k);
       }
       if (__any_sync(kFull, m != 0)) S.misses(m, ub, vb, base);
@@ -93,7 +115,7 @@ __device__ __forceinline__ void stream_range(const Sink& S, const int32_t* __res
     const int64_t i = i0 + tid;
     const bool valid = i < t;
     const int32_t a = valid ? ld_stream1(u + i) : 0, b = valid ? ld_stream1(v + i) : 0;
-    S.slot(valid && (!CACHE || miss_bit(a, b, V, slab)), a, b);
+    S.slot(valid && miss_of<MODE>(a, b, clampv, cache), a, b);
   }
 }
 

@@ -174,7 +174,7 @@ def test_block_pass_prefix_options(cuda_lib, ap_warm_edges):
     assert cfg["ap_warm_edges"] == (-1 if ap_warm_edges >= g.E else (0 if ap_warm_edges < 0 else cfg["ap_warm_edges"]))
 
 
-@pytest.mark.parametrize("scale,factor", [(10, 4), (13, 16), (16, 8)])
+@pytest.mark.parametrize("scale,factor", [(10, 4), (13, 16), (16, 8), (18, 8)])
 def test_rmat_skewed_degrees(ctx, scale, factor):
     V = 1 << scale
     u, v = graphgen.rmat(200 + scale, scale, factor * V)

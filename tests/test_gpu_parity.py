@@ -254,12 +254,26 @@ def test_plan_options(cuda_lib, warm_block, warm_edges):
     assert c.get_opts()["warm_block"] == warm_block
 
 
-@pytest.mark.parametrize("scale,factor", [(10, 4), (12, 16), (14, 8), (16, 16), (17, 4)])
+@pytest.mark.parametrize("scale,factor", [(10, 4), (12, 16), (14, 8), (16, 16), (17, 4), (19, 16), (20, 8),
+                                          (21, 4)])
 def test_rmat_skewed_degrees(ctx, scale, factor):
     """Power-law (R-MAT) graphs: hubs with thousands of edges, many leaves and isolated vertices,
-    self-loops and repeats -- a contention pattern the uniform workloads do not have."""
+    self-loops and repeats -- a contention pattern the uniform workloads do not have.  From 2^17
+    vertices on, 16-bit labels no longer fit in shared memory and the forest pass takes the
+    bitmap snapshot of the largest F' component; 2^21 vertices exceed the bitmap's reach (the
+    vertices past it always take the union-find path)."""
     V = 1 << scale
     u, v = graphgen.rmat(100 + scale, scale, factor * V)
     ref = oracle.dfs_bridges(u, v, V)
     for M in (1, 5):
         assert gpu_bridges(ctx, u, v, V, M).tolist() == ref.tolist(), M
+    if scale >= 17:  # the bitmap path, with and without a warm-up long enough to take it
+        for warm in (4096, 1 << 20, 0):
+            c = cuda_lib_ctx(warm_edges=warm)
+            assert gpu_bridges(c, u, v, V, 1).tolist() == ref.tolist(), warm
+
+
+def cuda_lib_ctx(**kw):
+    import paper_2108_07346_gb300 as pb
+
+    return pb.Context(device="cuda:0", **kw)
