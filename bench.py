@@ -33,10 +33,10 @@ UNIT = "GE/s"
 # DRAM bytes (read + write) per streamed edge, from full-size single-pass ncu captures on the large
 # workload (profiles/launch_list_large_dense.md, profiles/block_pass_large_dense.md); each is valid
 # only for the kernel sources it was measured on (hash of those sources).
-#   forest pass, M = 1: 9.313 GB read + 7.3 MB written for 1,072,703,284 streamed edges
-#   block pass stream: 9.508 GB read + 10.8 MB written for 1,073,547,340 streamed edges
-TRAFFIC = {"certify_sha": "a3aadd48ba1c58f6", "bytes_per_edge": 8.6815}
-AP_TRAFFIC = {"blocks_sha": "288877966afd280c", "bytes_per_edge": 8.8667}
+#   forest pass, M = 1: 9.295 GB read + 7.2 MB written for 1,072,703,284 streamed edges
+#   block pass stream: 9.512 GB read + 11.0 MB written for 1,073,547,340 streamed edges
+TRAFFIC = {"certify_sha": "f188fb6c7bf29658", "bytes_per_edge": 8.6711}
+AP_TRAFFIC = {"blocks_sha": "8e29d42c4a051393", "bytes_per_edge": 8.8710}
 
 
 def peaks():
