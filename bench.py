@@ -165,6 +165,12 @@ def cpu_oracle_rate(g, M, sample_edges):
     return n / dt / 1e9, n, dt
 
 
+def ref_sample_per_step(args, budget_edges):
+    """Edges the reference arm times per step: the requested sample, shrunk so that all steps
+    together stay near `budget_edges` (about two minutes of the single-threaded oracle)."""
+    return max(1_000_000, min(args.ref_sample, budget_edges // max(1, args.steps)))
+
+
 def run_reference(args, world, rank):
     if rank != 0:
         return
@@ -172,7 +178,7 @@ def run_reference(args, world, rank):
         return run_reference_ap(args, world)
     g = make_workload(args)
     M = args.M if args.M > 0 else 5
-    per_step = args.ref_sample
+    per_step = ref_sample_per_step(args, 18_000_000_000)  # 0.15 GE/s: ~2 minutes
     for _ in range(args.warmup):
         cpu_oracle_rate(g, M, max(per_step // 10, 1))
     times = []
@@ -196,7 +202,7 @@ def run_reference(args, world, rank):
 
 def run_reference_ap(args, world):
     g = graphgen.workload("large", **({} if args.density is None else {"p": args.density}))
-    per_step = args.ref_sample // 3
+    per_step = ref_sample_per_step(args, 3_600_000_000)  # 0.03 GE/s: ~2 minutes
     for _ in range(args.warmup):
         cpu_oracle_ap_rate(g, max(per_step // 10, 1))
     times = []
