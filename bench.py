@@ -690,7 +690,7 @@ def main():
     ap.add_argument("--requests", type=int, default=4000, help="served: requests")
     ap.add_argument("--rate", type=float, default=2000.0, help="served: mean arrivals per second")
     ap.add_argument("--pool", type=int, default=64, help="served: distinct resident graphs")
-    ap.add_argument("--slots", type=int, default=4, help="served: concurrent units of work")
+    ap.add_argument("--slots", type=int, default=8, help="served: concurrent units of work")
     ap.add_argument("--budget-gb", type=float, default=40.0, help="served: device-memory budget")
     ap.add_argument("--plain", type=int, default=1000, help="served: plain calls timed for comparison")
     ap.add_argument("--graphs", type=int, default=4096, help="graphs of the batched workload")

@@ -413,7 +413,7 @@ class Server:
 
     ``submit`` keeps references to the request's tensors until its result has been collected."""
 
-    def __init__(self, device=None, mem_budget=0, max_slots=4, max_batch=4096, **opts):
+    def __init__(self, device=None, mem_budget=0, max_slots=8, max_batch=4096, **opts):
         self._lib = load()
         dev = torch.device("cuda", torch.cuda.current_device()) if device is None else torch.device(device)
         self.device = dev
