@@ -56,7 +56,8 @@ typedef enum bridges_status {
 /* Tuning options.  Zero-initialise and set what you need; zero / negative fields mean
  * "choose automatically". */
 typedef struct bridges_opts {
-  int32_t M;           /* partitions of the edge list (Sec. 3 "M machines"); <= 0: auto */
+  int32_t M;           /* partitions of the edge list (Sec. 3 "M machines"); <= 0: auto (one
+                          partition: on one GPU the merge rounds cost more than they save) */
   int32_t fan_in;      /* certificates merged per merge job; <= 1: auto (Sec. 3 uses 2) */
   int32_t block;       /* threads per block of the forest pass; 0: auto */
   int32_t ctas_per_sm; /* resident blocks per SM for the forest pass; 0: auto */

@@ -201,7 +201,8 @@ int64_t check_args(const bridges_ctx* c, const void* u, const void* v, int64_t E
 // or copies into the context's device staging area; *dout receives 2*max(V,1) int32 of device
 // output space.  Enqueue only.
 int64_t stage_host_edges(bridges_ctx* c, cudaStream_t s, const int32_t* hu, const int32_t* hv, int64_t E, int32_t V,
-                         const int32_t** ru_out, const int32_t** rv_out, int32_t** dout_out) {
+                         const int32_t** ru_out, const int32_t** rv_out, int32_t** dout_out,
+                         bool defer_copy = false, bool* copy_deferred = nullptr) {
   Range range("bridges: host edges");
   // pinned, mapped host memory can be streamed by the kernels in place (no device copy of the
   // edges: graphs larger than device memory work this way)
@@ -244,13 +245,83 @@ int64_t stage_host_edges(bridges_ctx* c, cudaStream_t s, const int32_t* hu, cons
     int32_t* dv = reinterpret_cast<int32_t*>(base + eb);
     ru = du;
     rv = dv;
-    if (E > 0 && (cudaMemcpyAsync(du, hu, sizeof(int32_t) * (size_t)E, cudaMemcpyHostToDevice, s) != cudaSuccess ||
-                  cudaMemcpyAsync(dv, hv, sizeof(int32_t) * (size_t)E, cudaMemcpyHostToDevice, s) != cudaSuccess))
+    if (!defer_copy && E > 0 &&
+        (cudaMemcpyAsync(du, hu, sizeof(int32_t) * (size_t)E, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+         cudaMemcpyAsync(dv, hv, sizeof(int32_t) * (size_t)E, cudaMemcpyHostToDevice, s) != cudaSuccess))
       return cuda_fail(cudaGetLastError());
   }
+  if (copy_deferred) *copy_deferred = defer_copy && !in_place;
   *ru_out = ru;
   *rv_out = rv;
   *dout_out = dout;
+  return BRIDGES_OK;
+}
+
+// Host input with the copy overlapped: the list is copied in chunks on the context's copy stream
+// while the forest pass (one pass over the list, Sec. 3 phase 0) streams the chunks already on
+// the device.  Single partition with a snapshot only; returns 1 when the plan does not qualify
+// (nothing enqueued: the caller copies everything first).
+int64_t run_path_host(bridges_ctx* c, cudaStream_t s, const int32_t* hu, const int32_t* hv, int32_t* du, int32_t* dv,
+                      int64_t E, int32_t V, int32_t M, int32_t* out, Carved* kout) {
+  Range range("bridges: pipelined host input");
+  const CertPlan p = plan_for(c, E, V, M);
+  if (p.M != 1 || !p.cache) return 1;
+  const int64_t C = std::max<int64_t>({p.warm, ceil_div(E, bridges_ctx::kMaxChunks), (int64_t)16 << 20});
+  const int K = (int)ceil_div(E, C);
+  if (K < 2 || K > bridges_ctx::kMaxChunks) return 1;
+  if (!c->copy_stream) {
+    if (cudaStreamCreateWithFlags(&c->copy_stream, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->entry_ev, cudaEventDisableTiming) != cudaSuccess)
+      return cuda_fail(cudaGetLastError());
+    for (auto& e : c->chunk_ev)
+      if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) return cuda_fail(cudaGetLastError());
+  }
+  int64_t rc = ensure_ws(c, total_bytes(p), s);
+  if (rc != BRIDGES_OK) return rc;
+  Carved k = carve(c, p);
+  Launch L{s, &c->launches, c->num_sms, c->smem_optin};
+  c->last_cfg[0] = p.M;
+  c->last_cfg[1] = p.f;
+  c->last_cfg[2] = p.G;
+  c->last_cfg[3] = p.block;
+  c->last_cfg[4] = p.warm;
+  // the copies start once the stream's earlier work (which may still read the staging) is done
+  cudaStream_t cs = c->copy_stream;
+  if (cudaEventRecord(c->entry_ev, s) != cudaSuccess || cudaStreamWaitEvent(cs, c->entry_ev, 0) != cudaSuccess)
+    return cuda_fail(cudaGetLastError());
+  for (int i = 0; i < K; i++) {
+    const int64_t lo = C * i, n = std::min<int64_t>(C, E - lo);
+    if (cudaMemcpyAsync(du + lo, hu + lo, sizeof(int32_t) * (size_t)n, cudaMemcpyHostToDevice, cs) != cudaSuccess ||
+        cudaMemcpyAsync(dv + lo, hv + lo, sizeof(int32_t) * (size_t)n, cudaMemcpyHostToDevice, cs) != cudaSuccess ||
+        cudaEventRecord(c->chunk_ev[i], cs) != cudaSuccess)
+      return cuda_fail(cudaGetLastError());
+  }
+  cudaEvent_t* ev = next_event_slot(c);
+  if (ev) cudaEventRecord(ev[7], s);
+  cudaMemsetAsync(k.status, 0, sizeof(int32_t), s);
+  cert_init(L, p, k.cert);
+  cudaStreamWaitEvent(s, c->chunk_ev[0], 0);  // the first chunk holds the warm-up prefix (C >= warm)
+  if (ev) cudaEventRecord(ev[0], s);
+  cert_warm(L, p, k.cert, du, dv);
+  if (ev) cudaEventRecord(ev[1], s);
+  cert_snapshot(L, p, k.cert);
+  if (ev) cudaEventRecord(ev[2], s);
+  for (int i = 0; i < K; i++) {
+    if (i > 0) cudaStreamWaitEvent(s, c->chunk_ev[i], 0);
+    cert_stream(L, p, k.cert, du, dv, C * i, std::min<int64_t>(E, C * (i + 1)));
+  }
+  if (ev) cudaEventRecord(ev[3], s);
+  cert_merge(L, p, k.cert);
+  if (ev) cudaEventRecord(ev[4], s);
+  final_stage(L, k.fin, V, k.cert.f1u, k.cert.f1v, k.cert.cnt + 0, V, k.cert.f2u, k.cert.f2v, k.cert.cnt + 1, V,
+              k.cert.P1, out);
+  if (ev) {
+    cudaEventRecord(ev[5], s);
+    cudaEventRecord(ev[6], s);
+    c->calls++;
+  }
+  if (cudaGetLastError() != cudaSuccess) return BRIDGES_ECUDA;
+  *kout = k;
   return BRIDGES_OK;
 }
 
@@ -298,6 +369,11 @@ void bridges_ctx_destroy(bridges_ctx* c) {
   if (c->bws) cudaFree(c->bws);
   if (c->bstage) cudaFreeHost(c->bstage);
   if (c->b_done_ev) cudaEventDestroy(c->b_done_ev);
+  if (c->copy_stream) {
+    cudaStreamDestroy(c->copy_stream);
+    cudaEventDestroy(c->entry_ev);
+    for (auto& e : c->chunk_ev) cudaEventDestroy(e);
+  }
   if (c->events) {
     for (auto& set : c->ev)
       for (auto& e : set) cudaEventDestroy(e);
@@ -358,11 +434,24 @@ int64_t bridges_find_host(bridges_ctx* c, struct CUstream_st* stream, const int3
   const int32_t* ru = nullptr;
   const int32_t* rv = nullptr;
   int32_t* dout = nullptr;
-  rc = stage_host_edges(c, s, hu, hv, E, V, &ru, &rv, &dout);
+  bool deferred = false;
+  rc = stage_host_edges(c, s, hu, hv, E, V, &ru, &rv, &dout, true, &deferred);
   if (rc) return rc;
   Carved k{};
-  rc = run_path(c, s, ru, rv, E, V, M, dout, &k, nullptr);
-  if (rc) return rc;
+  rc = 1;
+  if (deferred)  // copies not issued yet: overlap them with the forest pass if the plan allows
+    rc = run_path_host(c, s, hu, hv, const_cast<int32_t*>(ru), const_cast<int32_t*>(rv), E, V, M, dout, &k);
+  if (rc < 0) return rc;
+  if (rc == 1) {
+    if (deferred && E > 0 &&
+        (cudaMemcpyAsync(const_cast<int32_t*>(ru), hu, sizeof(int32_t) * (size_t)E, cudaMemcpyHostToDevice, s) !=
+             cudaSuccess ||
+         cudaMemcpyAsync(const_cast<int32_t*>(rv), hv, sizeof(int32_t) * (size_t)E, cudaMemcpyHostToDevice, s) !=
+             cudaSuccess))
+      return cuda_fail(cudaGetLastError());
+    rc = run_path(c, s, ru, rv, E, V, M, dout, &k, nullptr);
+    if (rc) return rc;
+  }
   if (cudaMemcpyAsync(c->h_pinned, k.fin.count, sizeof(int64_t), cudaMemcpyDeviceToHost, s) != cudaSuccess)
     return cuda_fail(cudaGetLastError());
   if (cudaStreamSynchronize(s) != cudaSuccess) return cuda_fail(cudaGetLastError());

@@ -48,6 +48,11 @@ struct bridges_ctx {
   cudaStream_t b_exec_stream = nullptr;
   cudaEvent_t b_done_ev = nullptr;
   int64_t b_split_edges = 0;     // partition graphs with more edges than this (0: automatic)
+  // pipelined host input: a copy stream and one event per chunk copied
+  static constexpr int kMaxChunks = 64;
+  cudaStream_t copy_stream = nullptr;
+  cudaEvent_t entry_ev = nullptr;
+  cudaEvent_t chunk_ev[kMaxChunks]{};
 };
 
 namespace bridges {

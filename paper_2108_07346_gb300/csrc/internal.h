@@ -121,6 +121,14 @@ void cert_init(const Launch& L, const CertPlan& p, const CertBufs& b);
 // Leaf certificates of the M partitions of (u, v) (Sec. 3 phase 0, Alg. 2 per partition).
 void cert_leaves(const Launch& L, const CertPlan& p, const CertBufs& b, const int32_t* u, const int32_t* v,
                  cudaEvent_t* ev /* 4 events or null */);
+// The same in its three steps, for callers that interleave them with copies: the warm-up prefix
+// of every partition (edges [0, warm) of each chunk must be present), the snapshot, and the
+// rest of every chunk restricted to edges [r0, r1) (r1 <= r0: all of it; no-ops without a
+// snapshot, when the warm-up covered everything).
+void cert_warm(const Launch& L, const CertPlan& p, const CertBufs& b, const int32_t* u, const int32_t* v);
+void cert_snapshot(const Launch& L, const CertPlan& p, const CertBufs& b);
+void cert_stream(const Launch& L, const CertPlan& p, const CertBufs& b, const int32_t* u, const int32_t* v, int64_t r0,
+                 int64_t r1);
 // Merge tree (Sec. 3 phases): fan-in f until one certificate remains in job 0.
 void cert_merge(const Launch& L, const CertPlan& p, const CertBufs& b);
 // Plan for (E, V, M) on this device.

@@ -277,3 +277,21 @@ def cuda_lib_ctx(**kw):
     import paper_2108_07346_gb300 as pb
 
     return pb.Context(device="cuda:0", **kw)
+
+
+def test_find_host_pipelined_chunks(cuda_lib):
+    """bridges_find_host on a list long enough to be copied in chunks overlapped with the forest
+    pass (the large workload's vertex set at density 0.04: about 86 M edges, 6 chunks): the same
+    exact set as the device path and the planted bridges, pinned and pageable input alike."""
+    g = graphgen.workload("large", p=0.04)
+    assert g.E > 64 << 20
+    c = cuda_lib.Context(device="cuda:0", profile=True)
+    hu = torch.from_numpy(np.array(g.u)).pin_memory()
+    hv = torch.from_numpy(np.array(g.v)).pin_memory()
+    got = c.find_host(hu, hv, g.V, 1).numpy()
+    assert got.tolist() == g.planted.tolist()
+    du, dv = dev_edges(g.u, g.v)
+    assert c.find(du, dv, g.V, 1).cpu().numpy().tolist() == got.tolist()
+    assert c.find_host(hu, hv, g.V, 1).numpy().tolist() == got.tolist()  # reuses the chunk events
+    assert c.find_host(torch.from_numpy(np.array(g.u)), torch.from_numpy(np.array(g.v)), g.V, 1).numpy().tolist() \
+        == got.tolist()
