@@ -295,3 +295,20 @@ def test_find_host_pipelined_chunks(cuda_lib):
     assert c.find_host(hu, hv, g.V, 1).numpy().tolist() == got.tolist()  # reuses the chunk events
     assert c.find_host(torch.from_numpy(np.array(g.u)), torch.from_numpy(np.array(g.v)), g.V, 1).numpy().tolist() \
         == got.tolist()
+
+
+def test_large_v_closed_forms(ctx):
+    """Closed forms beyond the 16-bit label capacity (the bitmap snapshot): a star and a path of
+    300,000 vertices (every edge a bridge), a perfect matching (largest F' component of two
+    vertices), the same matching with every edge doubled (no bridges), and no edges at all."""
+    n = 300_000
+    a = np.arange(n - 1, dtype=np.int32)
+    perm = np.random.default_rng(71).permutation(n - 1)
+    star = gpu_bridges(ctx, np.zeros(n - 1, np.int32)[perm], (a + 1)[perm], n, 1)
+    assert len(star) == n - 1 and star[:, 0].max() == 0
+    assert len(gpu_bridges(ctx, a[perm], (a + 1)[perm], n, 1)) == n - 1
+    m = np.arange(0, n, 2, dtype=np.int32)
+    assert gpu_bridges(ctx, m, m + 1, n, 1).tolist() == np.stack([m, m + 1], 1).tolist()
+    assert len(gpu_bridges(ctx, np.concatenate([m, m + 1]), np.concatenate([m + 1, m]), n, 1)) == 0
+    e = np.zeros(0, np.int32)
+    assert len(gpu_bridges(ctx, e, e, n, 1)) == 0
