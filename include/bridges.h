@@ -118,9 +118,13 @@ int64_t bridges_find(const int32_t* edges_u, const int32_t* edges_v, int64_t E, 
                      int32_t* out_bridges);
 
 /* bridges_find_host -- the same computation from HOST buffers: copies the edges to the
- * context's device staging area on `stream`, runs the path, and copies the sorted bridges back
- * to out_bridges_host.  Synchronous; returns the count.  Host buffers should be pinned for
- * full copy bandwidth (pageable memory works, slower). */
+ * context's device staging area, runs the path, and copies the sorted bridges back to
+ * out_bridges_host.  With one partition (the automatic choice) and a list of 32 M edges or more,
+ * the copy runs in chunks on a copy stream of the context while the forest pass streams the
+ * chunks already copied; work on `stream` before the call is waited for first.  Synchronous;
+ * returns the count.  Host buffers should be pinned for full copy bandwidth and overlap
+ * (pageable memory works, slower).  With opts.host_read and pinned, mapped buffers the kernels
+ * read the host memory in place instead (no device copy of the edges). */
 int64_t bridges_find_host(bridges_ctx* ctx, struct CUstream_st* stream, const int32_t* edges_u_host,
                           const int32_t* edges_v_host, int64_t E, int32_t V, int32_t M,
                           int32_t* out_bridges_host);

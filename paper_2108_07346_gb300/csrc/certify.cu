@@ -19,7 +19,9 @@
 // of them).  F' components nest inside F components (every F' edge joins two ends F already
 // joined), so two vertices with equal labels are joined in both forests and their edge can be
 // dropped exactly; connectivity only grows, so a stale snapshot is still sound.  Other edges
-// take the union-find path as before.
+// take the union-find path as before.  When 16-bit labels need more shared memory than a block
+// has (V above about 113 k), the snapshot is instead a bitmap of the largest F' component, one
+// bit per vertex: an edge with both ends in it is dropped the same way.
 //
 // The merge tree (Sec. 3 phases) certifies the union of f certificates per merge job.  The
 // first child's union-finds already encode its own certificate (every edge of a certificate
