@@ -55,3 +55,15 @@ def test_ctx_create_fails_cleanly_without_gpu():
 
     lib = pb.load()
     assert not lib.bridges_ctx_create(0, 0, None)
+
+
+def test_missing_library_fails_loudly(monkeypatch, tmp_path):
+    """No fallback: without the compiled library the binding raises instead of computing
+    anything on the CPU."""
+    import paper_2108_07346_gb300 as pb
+    from paper_2108_07346_gb300 import build
+
+    monkeypatch.setattr(build, "LIB", str(tmp_path / "absent.so"))
+    monkeypatch.setattr(pb, "_lib", None)
+    with pytest.raises(RuntimeError, match="libbridges.so not found"):
+        pb.load(build_if_missing=False)

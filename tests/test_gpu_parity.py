@@ -312,3 +312,43 @@ def test_large_v_closed_forms(ctx):
     assert len(gpu_bridges(ctx, np.concatenate([m, m + 1]), np.concatenate([m + 1, m]), n, 1)) == 0
     e = np.zeros(0, np.int32)
     assert len(gpu_bridges(ctx, e, e, n, 1)) == 0
+
+
+def test_seeded_fuzz_against_oracle(cuda_lib):
+    """A seeded mix of graph families and plans: uniform multigraphs, R-MAT, trees with a few
+    cycles, duplicated lists, planted clusters; M, warm-up length and warm-up block size drawn at
+    random.  Bridges and cut vertices against the oracle every time."""
+    rng = np.random.default_rng(77)
+    for t in range(120):
+        fam = t % 5
+        if fam == 0:
+            V = int(rng.integers(2, 3000))
+            u, v = graphgen.random_multigraph(60000 + t, V, int(rng.integers(V // 2, 8 * V)))
+        elif fam == 1:
+            scale = int(rng.integers(6, 15))
+            V = 1 << scale
+            u, v = graphgen.rmat(61000 + t, scale, int(rng.integers(2, 24)) << scale)
+        elif fam == 2:
+            V = int(rng.integers(2, 20000))
+            par = (rng.random(V - 1) * np.arange(1, V)).astype(np.int32)
+            ch = np.arange(1, V, dtype=np.int32)
+            k = int(rng.integers(0, 20))
+            u = np.concatenate([par, rng.integers(0, V, k).astype(np.int32)])
+            v = np.concatenate([ch, rng.integers(0, V, k).astype(np.int32)])
+        elif fam == 3:
+            V = int(rng.integers(2, 2000))
+            u0, v0 = graphgen.random_multigraph(62000 + t, V, int(rng.integers(0, 3 * V)))
+            u, v = np.concatenate([u0, v0, u0]), np.concatenate([v0, u0, v0])
+        else:
+            g = graphgen.generate(graphgen.workload_spec("batched", 9, t))
+            u, v, V = g.u, g.v, g.V
+        perm = rng.permutation(len(u))
+        u, v = np.ascontiguousarray(u[perm]), np.ascontiguousarray(v[perm])
+        M = int(rng.choice([1, 1, 2, 3, 8]))
+        c = cuda_lib.Context(device="cuda:0", warm_edges=int(rng.choice([-1, 0, 500, 20000])),
+                             warm_block=int(rng.choice([0, 64, 256, 1024])))
+        du, dv = dev_edges(u, v)
+        assert c.find(du, dv, V, M).cpu().numpy().tolist() == oracle.dfs_bridges(u, v, V).tolist(), (t, fam, V, M)
+        if t % 3 == 0:
+            assert c.articulation_points(du, dv, V, M).cpu().numpy().tolist() == \
+                oracle.articulation_points(u, v, V).tolist(), (t, fam, V, M)
