@@ -303,9 +303,10 @@ int64_t bridges_inc_certificate_size(const bridges_inc* inc);
  * a vertex id outside [0, V), found on the device; EINVAL / ENOMEM on the host).
  *
  * bridges_articulation_points_host: the same from HOST edge buffers (copied to the context's
- *   device staging area, or read in place when opts.host_read is set and they are pinned and
- *   mapped); the cut vertices go to out_points_host (host, capacity max(V, 1)).  Synchronous;
- *   returns their number or a negative status.
+ *   device staging area -- in chunks overlapped with the first pass, as bridges_find_host does --
+ *   or read in place when opts.host_read is set and they are pinned and mapped); the cut
+ *   vertices go to out_points_host (host, capacity max(V, 1)).  Synchronous; returns their
+ *   number or a negative status.
  * bridges_articulation_workspace_bytes: workspace a context needs for this call (contexts made
  *   with bridges_ctx_create_ws must be at least this large).
  * bridges_ctx_ap_stage_ms: on a profiling context, the stage times of the last call's block

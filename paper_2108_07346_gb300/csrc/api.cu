@@ -999,30 +999,41 @@ static int64_t ap_warm_edges(const bridges_ctx* c, int64_t E, int32_t V) {
   return std::min<int64_t>(E, 2 * (int64_t)V + 4096);
 }
 
-extern "C" int64_t bridges_articulation_points(bridges_ctx* c, struct CUstream_st* stream, const int32_t* u,
-                                               const int32_t* v, int64_t E, int32_t V, int32_t M,
-                                               int32_t* out_points, int32_t* out_bridges,
-                                               int64_t* out_counts_device) {
-  int64_t rc = check_args(c, u, v, E, V, out_points);
-  if (rc) return rc;
-  if (V > (1 << 30)) return BRIDGES_EINVAL;
-  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-  if (cudaSetDevice(c->device) != cudaSuccess) return cuda_fail(cudaGetLastError());
+// The articulation-point path on device edges (u, v).  When hu / hv are given (and the edges
+// were not copied yet), the bridge path's forest pass runs behind a chunked copy of them into
+// (u, v) (run_path_host); the block pass then streams (u, v) from the device.
+static int64_t articulation_run(bridges_ctx* c, cudaStream_t s, const int32_t* u, const int32_t* v, int64_t E, int32_t V,
+                         int32_t M, int32_t* out_points, int32_t* out_bridges, int64_t* out_counts_device,
+                         const int32_t* hu, const int32_t* hv) {
   int32_t dummy_out[1];
   if (!out_points) out_points = dummy_out;  // V <= 1: nothing is written
   const CertPlan p0 = plan_for(c, E, V, M);
   const size_t ap_at = align_up(total_bytes(p0), 256);
-  rc = ensure_ws(c, ap_at + ap_bytes(V), s);
+  int64_t rc = ensure_ws(c, ap_at + ap_bytes(V), s);
   if (rc) return rc;
   Carved k{};
-  CertPlan p{};
-  rc = run_path(c, s, u, v, E, V, M, out_bridges, &k, &p);
-  if (rc) return rc;
   Launch L{s, &c->launches, c->num_sms, c->smem_optin};
-  if (!out_bridges) {
-    // the rooted forest is needed either way; the bridges go to dscan, free by the time it sorts
-    final_stage(L, k.fin, V, k.cert.f1u, k.cert.f1v, k.cert.cnt + 0, V, k.cert.f2u, k.cert.f2v, k.cert.cnt + 1, V,
-                k.cert.P1, k.fin.dscan);
+  rc = 1;
+  if (hu) {
+    // the rooted forest is needed either way; without a bridge buffer the bridges go to dscan,
+    // free by the time the final stage sorts
+    const Carved k0 = carve(c, p0);
+    rc = run_path_host(c, s, hu, hv, const_cast<int32_t*>(u), const_cast<int32_t*>(v), E, V, M,
+                       out_bridges ? out_bridges : k0.fin.dscan, &k);
+    if (rc < 0) return rc;
+    if (rc == 1 && E > 0 &&
+        (cudaMemcpyAsync(const_cast<int32_t*>(u), hu, sizeof(int32_t) * (size_t)E, cudaMemcpyHostToDevice, s) !=
+             cudaSuccess ||
+         cudaMemcpyAsync(const_cast<int32_t*>(v), hv, sizeof(int32_t) * (size_t)E, cudaMemcpyHostToDevice, s) !=
+             cudaSuccess))
+      return cuda_fail(cudaGetLastError());
+  }
+  if (rc == 1) {
+    rc = run_path(c, s, u, v, E, V, M, out_bridges, &k, nullptr);
+    if (rc) return rc;
+    if (!out_bridges)
+      final_stage(L, k.fin, V, k.cert.f1u, k.cert.f1v, k.cert.cnt + 0, V, k.cert.f2u, k.cert.f2v, k.cert.cnt + 1, V,
+                  k.cert.P1, k.fin.dscan);
   }
   Range range("bridges: articulation block pass");
   ApBufs b = carve_ap(static_cast<char*>(c->ws) + ap_at, V);
@@ -1058,6 +1069,18 @@ extern "C" int64_t bridges_articulation_points(bridges_ctx* c, struct CUstream_s
   return c->h_pinned[0];
 }
 
+extern "C" int64_t bridges_articulation_points(bridges_ctx* c, struct CUstream_st* stream, const int32_t* u,
+                                               const int32_t* v, int64_t E, int32_t V, int32_t M,
+                                               int32_t* out_points, int32_t* out_bridges,
+                                               int64_t* out_counts_device) {
+  int64_t rc = check_args(c, u, v, E, V, out_points);
+  if (rc) return rc;
+  if (V > (1 << 30)) return BRIDGES_EINVAL;
+  if (cudaSetDevice(c->device) != cudaSuccess) return cuda_fail(cudaGetLastError());
+  return articulation_run(c, reinterpret_cast<cudaStream_t>(stream), u, v, E, V, M, out_points, out_bridges,
+                          out_counts_device, nullptr, nullptr);
+}
+
 extern "C" int64_t bridges_articulation_points_host(bridges_ctx* c, struct CUstream_st* stream, const int32_t* hu,
                                                     const int32_t* hv, int64_t E, int32_t V, int32_t M,
                                                     int32_t* out_points_host) {
@@ -1069,9 +1092,11 @@ extern "C" int64_t bridges_articulation_points_host(bridges_ctx* c, struct CUstr
   const int32_t* ru = nullptr;
   const int32_t* rv = nullptr;
   int32_t* dout = nullptr;
-  rc = stage_host_edges(c, s, hu, hv, E, V, &ru, &rv, &dout);
+  bool deferred = false;
+  rc = stage_host_edges(c, s, hu, hv, E, V, &ru, &rv, &dout, true, &deferred);
   if (rc) return rc;
-  const int64_t n = bridges_articulation_points(c, stream, ru, rv, E, V, M, dout, nullptr, nullptr);
+  const int64_t n = articulation_run(c, s, ru, rv, E, V, M, dout, nullptr, nullptr, deferred ? hu : nullptr,
+                                     deferred ? hv : nullptr);
   if (n <= 0) return n;
   if (cudaMemcpyAsync(out_points_host, dout, sizeof(int32_t) * (size_t)n, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
       cudaStreamSynchronize(s) != cudaSuccess)

@@ -179,3 +179,19 @@ def test_rmat_skewed_degrees(ctx, scale, factor):
     V = 1 << scale
     u, v = graphgen.rmat(200 + scale, scale, factor * V)
     assert gpu_points(ctx, u, v, V, 2).tolist() == oracle.articulation_points(u, v, V).tolist()
+
+
+def test_host_entry_pipelined(cuda_lib):
+    """bridges_articulation_points_host on a list long enough for the chunked copy overlapped with
+    the forest pass (the large workload's vertex set at density 0.04, about 86 M edges): the
+    cut vertices are the construction's, as on the device path."""
+    import bench
+
+    g = graphgen.workload("large", p=0.04)
+    expect = bench.planted_cut_vertices(g).tolist()
+    hu = torch.from_numpy(np.array(g.u)).pin_memory()
+    hv = torch.from_numpy(np.array(g.v)).pin_memory()
+    c = cuda_lib.Context(device="cuda:0")
+    assert c.articulation_points_host(hu, hv, g.V).numpy().tolist() == expect
+    assert c.articulation_points_host(hu, hv, g.V).numpy().tolist() == expect
+    assert c.articulation_points(dev(g.u), dev(g.v), g.V).cpu().numpy().tolist() == expect
