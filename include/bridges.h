@@ -68,7 +68,8 @@ typedef struct bridges_opts {
                           kernels read them in place over the host link instead of copying
                           them to the device first; 0 = always copy */
   int32_t ap_warm_edges; /* bridges_articulation_points: edges of the list offered to the block
-                            pass before its label snapshot; 0: auto, > 0: that many, < 0: none
+                            pass before its snapshot; 0: auto (2V + 4096 with 16-bit labels,
+                            none with the bitmap that larger V takes), > 0: that many, < 0: none
                             (snapshot right after the certificate's own edges) */
   int32_t warm_block;    /* threads per block of the forest pass's warm-up launch (the prefix certified
                             through the union-finds before the snapshot); 0: auto */
@@ -310,7 +311,7 @@ int64_t bridges_inc_certificate_size(const bridges_inc* inc);
  * bridges_articulation_workspace_bytes: workspace a context needs for this call (contexts made
  *   with bridges_ctx_create_ws must be at least this large).
  * bridges_ctx_ap_stage_ms: on a profiling context, the stage times of the last call's block
- *   pass in ms: [0] warm-up (certificate edges + prefix), [1] label snapshot, [2] stream,
+ *   pass in ms: [0] warm-up (certificate edges + prefix), [1] snapshot, [2] stream,
  *   [3] marking and compaction, [4] the whole block pass; waits for them; returns how many were
  *   written (0 when none are available).
  * bridges_ctx_ap_stage_ms_history: the same five times for each of the last min(max_calls, 32)

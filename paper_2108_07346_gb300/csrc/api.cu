@@ -1040,7 +1040,13 @@ static int64_t articulation_run(bridges_ctx* c, cudaStream_t s, const int32_t* u
   // the block pass streams the whole list as one partition, its own warm-up before the snapshot
   CertPlan q = plan_for(c, E, V, 1);
   q.warm = ap_warm_edges(c, E, V);
-  q.cache = (size_t)align_up((size_t)V + 1, 8) * 2 + 1024 <= c->smem_optin && q.warm < E;
+  // The plan's snapshot form: 16-bit labels when 2V bytes fit in shared memory, else a bitmap of
+  // the largest class, taken only when it reaches every vertex (R-MAT, 2^21 vertices, 1.85 M in
+  // reach: 0.71 ms for the block pass with it, 0.66 without).  With the bitmap the automatic
+  // prefix is none: the certificate's blocks already seed the classes (R-MAT 2^18 / 2^20: 0.12 /
+  // 0.22 ms without a prefix, 0.16 / 0.31 ms with 2V + 4096 edges, 0.21 / 0.59 ms with no snapshot).
+  if (q.mode == 2 && c->opts.ap_warm_edges == 0) q.warm = 0;
+  q.cache = (q.mode == 1 || (q.mode == 2 && q.Vb >= V)) && q.warm < E;
   c->last_cfg[5] = q.cache ? q.warm : -1;
   c->last_cfg[6] = (int64_t)q.G * q.M;
   cudaEvent_t* ev = nullptr;

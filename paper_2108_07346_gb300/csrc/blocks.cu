@@ -26,7 +26,9 @@
 // rules, below) and a short prefix of the list has been walked, nearly every edge is, so
 // the stream reuses the forest pass's machinery: a 16-bit label per vertex in shared memory (the
 // largest class containing the vertex), two label reads per edge, and the cycle walk only for
-// the misses.  Classes only grow, so a stale label is still sound.
+// the misses.  Classes only grow, so a stale label is still sound.  When 2V bytes of labels do
+// not fit in shared memory, one bit per vertex marks the largest class of all instead (both
+// ends in it: redundant), for the vertices below the bitmap's reach; every other edge walks.
 #include <algorithm>
 #include <cmath>
 
@@ -201,9 +203,11 @@ struct PassArgs {
   int64_t t;
   const uint16_t* lab;
   int64_t Vpad;
+  int32_t Vb;  // MODE 2: vertices covered by the bitmap (a multiple of 128)
 };
 
-template <bool CACHE, bool VEC>
+// MODE 0: no snapshot (every edge walks); 1: 16-bit labels; 2: bitmap of vertices [0, Vb).
+template <int MODE, bool VEC>
 __global__ void __launch_bounds__(1024, 1) ap_pass_kernel(PassArgs P) {
   extern __shared__ __align__(16) uint16_t slab[];
   __shared__ int32_t stop;
@@ -212,9 +216,10 @@ __global__ void __launch_bounds__(1024, 1) ap_pass_kernel(PassArgs P) {
   if (stop) return;  // block-uniform: the stream below contains barriers
   const int64_t n = P.t - P.s;
   const int64_t s = P.s + n * blockIdx.x / gridDim.x, t = P.s + n * (blockIdx.x + 1) / gridDim.x;
-  if (CACHE) load_labels(slab, P.lab, P.Vpad);
+  if (MODE == 1) load_labels(slab, P.lab, P.Vpad);
+  if (MODE == 2) load_words(slab, P.lab, (P.Vb / 32 + 4) / 4);
   const CycleSink S{P.A};
-  stream_range<CACHE ? 1 : 0, VEC, kUnroll>(S, P.u, P.v, s, t, (uint32_t)P.A.V, slab);
+  stream_range<MODE, VEC, kUnroll>(S, P.u, P.v, s, t, MODE == 2 ? (uint32_t)P.Vb : (uint32_t)P.A.V, slab);
 }
 
 // ---- label snapshot: each vertex takes the largest class it belongs to ----
@@ -232,7 +237,10 @@ __global__ void ap_flatten_kernel(ApBufs b, int32_t V, const int32_t* status) {
     b.tmp[i] = -1;
     b.best[i] = 0;
   }
-  if (gtid() == 0) *b.nlab = 0;
+  if (gtid() == 0) {
+    *b.nlab = 0;
+    *b.giant = 0;
+  }
 }
 
 // 2) class sizes (tree edges per class); lanes with the same root add once per warp
@@ -265,6 +273,10 @@ __global__ void ap_propose_kernel(ApBufs b, int32_t V, const int32_t* status) {
     // siblings share a parent: one proposal per distinct (parent, key) in the warp
     const unsigned peers = __match_any_sync(kFull, p) & __match_any_sync(kFull, key);
     if (key && lane == __ffs(peers) - 1) atomicMax(reinterpret_cast<unsigned long long*>(b.best + p), key);
+    // the largest class overall (the bitmap snapshot's), one atomic per warp
+    unsigned long long wmax = key;
+    for (int o = 16; o > 0; o >>= 1) wmax = max(wmax, __shfl_xor_sync(kFull, wmax, o));
+    if (lane == 0 && wmax) atomicMax(b.giant, wmax);
   }
 }
 
@@ -290,6 +302,24 @@ __global__ void ap_label_kernel(ApBufs b, const int32_t* pre, int32_t V, const i
     }
     id = __shfl_sync(kFull, id, leader);
     if (x < b.Vpad) b.lab[x] = (key && id >= 0 && id < (int32_t)kNoLabel) ? (uint16_t)id : kNoLabel;
+  }
+}
+
+// 4') the bitmap instead of labels: bit x set iff x < min(V, Vb) and the largest class containing
+//     x is the largest class of all; the words from Vb / 32 on stay clear (the clamp target of
+//     ids past the bitmap and of out-of-range ids)
+__global__ void ap_bitmap_kernel(ApBufs b, const int32_t* pre, int32_t V, int32_t Vb, const int32_t* status) {
+  if (*status) return;  // T is not valid: its arrays may be partly unset
+  const int64_t nw = Vb / 32 + 4;  // a multiple of 4 words: the pass copies 16-byte units
+  const unsigned long long g = *b.giant;
+  uint32_t* words = reinterpret_cast<uint32_t*>(b.lab);
+  for (int64_t w = gtid(); w < nw; w += gstride()) {
+    uint32_t bits = 0;
+    for (int k = 0; k < 32; k++) {
+      const int64_t x = w * 32 + k;
+      if (g && x < V && x < Vb && b.best[pre[x]] == g) bits |= 1u << k;
+    }
+    words[w] = bits;
   }
 }
 
@@ -388,9 +418,9 @@ int grid_of(const Launch& L, int64_t work, int block) {
   return (int)std::min<int64_t>(g, (int64_t)L.num_sms * 16);
 }
 
-template <bool CACHE, bool VEC>
+template <int MODE, bool VEC>
 void launch_pass(const Launch& L, const PassArgs& a, int grid, int block, size_t smem) {
-  auto k = ap_pass_kernel<CACHE, VEC>;
+  auto k = ap_pass_kernel<MODE, VEC>;
   if (smem > 48 * 1024) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   k<<<grid, block, smem, L.stream>>>(a);
   *L.launches += 1;
@@ -402,7 +432,7 @@ size_t ap_bytes(int32_t V) {
   const size_t Vs = (size_t)std::max(V, 1);
   const size_t Vpad = align_up(Vs + 1, 8);
   const size_t ntiles = ceil_div((int64_t)Vs, (int64_t)kCompactThreads * kCompactItems);
-  size_t s = 3 * 256;                                    // hooks, nlab, count
+  size_t s = 4 * 256;                                    // hooks, nlab, count, giant
   s += 7 * align_up(sizeof(int32_t) * Vs, 256);          // Q PP LAST vtx csize tmp flag
   s += align_up(sizeof(uint64_t) * Vs, 256);             // best
   s += align_up(sizeof(int32_t) * (ntiles + 1), 256);    // tiles
@@ -418,7 +448,8 @@ ApBufs carve_ap(void* base, int32_t V) {
   b.hooks = reinterpret_cast<int32_t*>(c);
   b.nlab = reinterpret_cast<int32_t*>(c + 256);
   b.count = reinterpret_cast<int64_t*>(c + 512);
-  c += 3 * 256;
+  b.giant = reinterpret_cast<unsigned long long*>(c + 768);
+  c += 4 * 256;
   int32_t** arrs[7] = {&b.Q, &b.PP, &b.LAST, &b.vtx, &b.csize, &b.tmp, &b.flag};
   for (auto a : arrs) {
     *a = reinterpret_cast<int32_t*>(c);
@@ -446,28 +477,39 @@ void articulation_stage(const Launch& L, const CertPlan& p, const FinalBufs& f, 
   *L.launches += 3;
   const bool vec = ((reinterpret_cast<uintptr_t>(u) | reinterpret_cast<uintptr_t>(v)) & 15) == 0;
   const int grid = (int)std::max<int64_t>(1, (int64_t)p.G * p.M);
-  PassArgs a{A, u, v, 0, p.cache ? std::min(p.warm, p.E) : p.E, b.lab, b.Vpad};
+  PassArgs a{A, u, v, 0, p.cache ? std::min(p.warm, p.E) : p.E, b.lab, b.Vpad, p.Vb};
   if (a.t > 0) {
     if (vec)
-      launch_pass<false, true>(L, a, grid, p.block, 0);
+      launch_pass<0, true>(L, a, grid, p.block, 0);
     else
-      launch_pass<false, false>(L, a, grid, p.block, 0);
+      launch_pass<0, false>(L, a, grid, p.block, 0);
   }
   if (ev) cudaEventRecord(ev[0], L.stream);
   if (p.cache && p.E > a.t) {
     ap_flatten_kernel<<<g, bs, 0, L.stream>>>(b, V, f.status);
     ap_count_kernel<<<g, bs, 0, L.stream>>>(b, V, f.status);
     ap_propose_kernel<<<g, bs, 0, L.stream>>>(b, V, f.status);
-    ap_label_kernel<<<grid_of(L, b.Vpad, bs), bs, 0, L.stream>>>(b, f.pre, V, f.status);
+    if (p.mode == 2)
+      ap_bitmap_kernel<<<grid_of(L, p.Vb / 32 + 4, bs), bs, 0, L.stream>>>(b, f.pre, V, p.Vb, f.status);
+    else
+      ap_label_kernel<<<grid_of(L, b.Vpad, bs), bs, 0, L.stream>>>(b, f.pre, V, f.status);
     *L.launches += 4;
     if (ev) cudaEventRecord(ev[1], L.stream);
     a.s = a.t;
     a.t = p.E;
-    const size_t smem = (size_t)b.Vpad * 2;
-    if (vec)
-      launch_pass<true, true>(L, a, grid, p.block, smem);
-    else
-      launch_pass<true, false>(L, a, grid, p.block, smem);
+    if (p.mode == 2) {
+      const size_t smem = (size_t)(p.Vb / 32 + 4) * 4;
+      if (vec)
+        launch_pass<2, true>(L, a, grid, p.block, smem);
+      else
+        launch_pass<2, false>(L, a, grid, p.block, smem);
+    } else {
+      const size_t smem = (size_t)b.Vpad * 2;
+      if (vec)
+        launch_pass<1, true>(L, a, grid, p.block, smem);
+      else
+        launch_pass<1, false>(L, a, grid, p.block, smem);
+    }
   } else if (ev) {
     cudaEventRecord(ev[1], L.stream);
   }

@@ -111,8 +111,10 @@ struct ApBufs {
   int32_t* tmp;    // label id per class root (snapshot)
   int32_t* flag;   // by vertex id: 1 if an articulation point
   uint64_t* best;  // largest class containing each vertex: (size << 32 | root), 0 if none
+  unsigned long long* giant;  // [1] largest class overall: its key in `best`'s form (bitmap snapshot)
   int32_t* tiles;  // compaction tile counts, then offsets
-  uint16_t* lab;   // by vertex id: 16-bit class label (kNoLabel: none); Vpad entries
+  uint16_t* lab;   // by vertex id: 16-bit class label (kNoLabel: none); Vpad entries, or the
+                  // bitmap snapshot's words (bit x: x lies in the largest class)
   int64_t Vpad;
 };
 
@@ -161,7 +163,8 @@ size_t ap_bytes(int32_t V);
 ApBufs carve_ap(void* base, int32_t V);
 // Articulation points of (u, v) after the bridge path: f holds the final stage's rooted forest
 // T (pre, par, sz) and (xu, xv, *d_nx) the certificate's non-tree edges.  Streams the edge list
-// once more (warm-up of p.warm edges, label snapshot, the rest) with p's grid (M = 1 plan);
+// once more (warm-up of p.warm edges, snapshot in p.mode's form -- 16-bit labels, or for larger
+// V a bitmap of vertices [0, p.Vb) -- then the rest) with p's grid (M = 1 plan);
 // writes the sorted points to out and their number (or the status) to *count_dev.  ev: three
 // events recorded after the warm-up, the snapshot and the stream (or null).
 void articulation_stage(const Launch& L, const CertPlan& p, const FinalBufs& f, const ApBufs& b, const int32_t* u,

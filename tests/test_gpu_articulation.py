@@ -195,3 +195,43 @@ def test_host_entry_pipelined(cuda_lib):
     assert c.articulation_points_host(hu, hv, g.V).numpy().tolist() == expect
     assert c.articulation_points_host(hu, hv, g.V).numpy().tolist() == expect
     assert c.articulation_points(dev(g.u), dev(g.v), g.V).cpu().numpy().tolist() == expect
+
+
+def chain_of_blocks(seed, k, size, deg):
+    """k random blocks of `size` vertices and about deg * size edges each, block i sharing its
+    last vertex with block i + 1 (a chain through k - 1 shared vertices), ids shuffled."""
+    rng = np.random.default_rng(seed)
+    us, vs = [], []
+    for i in range(k):
+        lo = i * (size - 1)
+        m = deg * size
+        us.append(lo + rng.integers(0, size, m))
+        vs.append(lo + rng.integers(0, size, m))
+    V = k * (size - 1) + 1
+    perm = rng.permutation(V).astype(np.int32)
+    u, v = perm[np.concatenate(us)], perm[np.concatenate(vs)]
+    order = rng.permutation(len(u))
+    return u[order].astype(np.int32), v[order].astype(np.int32), V
+
+
+@pytest.mark.parametrize("ap_warm_edges", [-1, 0, 5000])
+def test_large_v_bitmap_snapshot(cuda_lib, ap_warm_edges):
+    """More vertices than 16-bit labels fit in shared memory: the block pass snapshots the
+    largest class as a bitmap (vertices past its reach always walk).  R-MAT graphs (one large
+    block and a periphery), a chain of dense blocks, and a graph beyond the bitmap's reach."""
+    c = cuda_lib.Context(device="cuda:0", ap_warm_edges=ap_warm_edges)
+    cases = [graphgen.rmat(317, 17, 8 << 17) + (1 << 17,), graphgen.rmat(319, 19, 4 << 19) + (1 << 19,),
+             chain_of_blocks(321, 150, 1000, 12)]
+    for u, v, V in cases:
+        ref = oracle.articulation_points(u, v, V).tolist()
+        assert c.articulation_points(dev(u), dev(v), V, 1).cpu().numpy().tolist() == ref, V
+        cfg = c.last_config()
+        assert cfg["ap_warm_edges"] == (0 if ap_warm_edges < 0 else cfg["ap_warm_edges"]) and cfg["ap_warm_edges"] >= 0
+
+
+@pytest.mark.slow
+def test_beyond_bitmap_reach(ctx):
+    """2^21 vertices: ids past the bitmap's reach (about 1.85 M) take the cycle walk."""
+    u, v = graphgen.rmat(323, 21, 4 << 21)
+    V = 1 << 21
+    assert gpu_points(ctx, u, v, V, 1).tolist() == oracle.articulation_points(u, v, V).tolist()
