@@ -35,8 +35,8 @@ UNIT = "GE/s"
 # only for the kernel sources it was measured on (hash of those sources).
 #   forest pass, M = 1: 9.295 GB read + 7.2 MB written for 1,072,703,284 streamed edges
 #   block pass stream: 9.512 GB read + 11.0 MB written for 1,073,547,340 streamed edges
-TRAFFIC = {"certify_sha": "f188fb6c7bf29658", "bytes_per_edge": 8.6711}
-AP_TRAFFIC = {"blocks_sha": "8e29d42c4a051393", "bytes_per_edge": 8.8710}
+TRAFFIC = {"certify_sha": "6120be18ea0521d8", "bytes_per_edge": 8.6864}
+AP_TRAFFIC = {"blocks_sha": "cc633b86cfc99c54", "bytes_per_edge": 8.8912}
 
 
 def peaks():
