@@ -219,6 +219,22 @@ int64_t bridges_from_forest(bridges_ctx* ctx, struct CUstream_st* stream, const 
                             const int32_t* tree_v, int64_t n_tree, const int32_t* extra_u,
                             const int32_t* extra_v, int64_t n_extra, int32_t V, int32_t* out_bridges);
 
+/* bridges_rooted_forest -- the rooted, numbered forest that the final stage's bridge test runs
+ * on (its Euler tour and list ranking; the DFS of Alg. 1 visits T in such an order).  Given a
+ * spanning forest T as for bridges_from_forest, each tree is rooted at its minimum vertex and:
+ *   out_parent[x] : x's parent, -1 for a root (vertices on no edge of T are one-vertex trees);
+ *   out_pre[x]    : x's preorder number.  The trees take consecutive ranges of [0, V) in
+ *                   increasing order of their roots; inside a tree a vertex precedes its
+ *                   subtree, and siblings appear in the order of the Euler tour, which follows
+ *                   the adjacency lists as built concurrently (not a fixed order);
+ *   out_size[x]   : the number of vertices in x's subtree (x included).
+ * Each output is a device int32[V] or NULL (not written).  Synchronous; returns BRIDGES_OK or a
+ * negative status (EINVAL for bad sizes or pointers, ERANGE for an id outside [0, V)); a cycle
+ * in T gives unspecified output or BRIDGES_EINTERNAL, never a fault. */
+int64_t bridges_rooted_forest(bridges_ctx* ctx, struct CUstream_st* stream, const int32_t* tree_u,
+                              const int32_t* tree_v, int64_t n_tree, int32_t V, int32_t* out_parent,
+                              int32_t* out_pre, int32_t* out_size);
+
 /* ---------------------------------------------------------------------------------------
  * bridges_find_noalloc -- bridges_find for callers that must not allocate device memory.
  *

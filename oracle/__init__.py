@@ -183,3 +183,58 @@ def block_certificate(u, v, V: int):
     k = _check(_load().oracle_block_certificate(u.ctypes.data, v.ctypes.data, u.shape[0], V, ids.ctypes.data,
                                                 tr.ctypes.data, pts.ctypes.data, npt.ctypes.data))
     return ids[:k].copy(), tr[:k].astype(bool), pts[: int(npt[0])].copy()
+
+
+def rooted_forest(tu, tv, V: int, child_key=None):
+    """The rooted, numbered forest that Alg. 1's depth-first search walks, for a spanning forest
+    given as edges (tu, tv): every tree is rooted at its minimum vertex, the trees are searched in
+    increasing order of their roots, and one global counter numbers the vertices in the order the
+    search discovers them (Alg. 1's disc with the global timer of reading 7, counted from 0).
+    Siblings are visited in increasing ``child_key`` (default: vertex id).
+
+    Returns (parent, pre, size) as int32 arrays of length V: parent -1 for roots, size = vertices
+    in the subtree.  Pure Python (an explicit stack); raises ValueError if the edges contain a
+    cycle or an id outside [0, V)."""
+    tu = np.asarray(tu, dtype=np.int64).ravel()
+    tv = np.asarray(tv, dtype=np.int64).ravel()
+    if tu.shape != tv.shape:
+        raise ValueError("tu and tv differ in length")
+    if tu.size and (min(tu.min(), tv.min()) < 0 or max(tu.max(), tv.max()) >= V):
+        raise ValueError("vertex id outside [0, V)")
+    key = np.arange(V) if child_key is None else np.asarray(child_key)
+    adj = [[] for _ in range(V)]
+    for a, b in zip(tu.tolist(), tv.tolist()):
+        adj[a].append(b)
+        adj[b].append(a)
+    parent = np.full(V, -1, np.int32)
+    pre = np.full(V, -1, np.int32)
+    size = np.zeros(V, np.int32)
+    clock = 0
+    for r in range(V):  # the first unvisited vertex of a tree is its minimum
+        if pre[r] >= 0:
+            continue
+        pre[r] = clock
+        clock += 1
+        order = [r]
+        # each vertex's unvisited neighbours in key order (its parent's edge left out once)
+        stack = [(r, iter(sorted(adj[r], key=lambda y: key[y])))]
+        while stack:
+            x, it = stack[-1]
+            y = next(it, None)
+            if y is None:
+                stack.pop()
+                continue
+            if pre[y] >= 0:  # reached twice: a cycle (or a doubled edge)
+                raise ValueError("the edges contain a cycle")
+            parent[y] = x
+            pre[y] = clock
+            clock += 1
+            order.append(y)
+            rest = list(adj[y])
+            rest.remove(x)  # the edge to the parent, once
+            stack.append((y, iter(sorted(rest, key=lambda z: key[z]))))
+        for x in reversed(order):  # subtree sizes, children before parents
+            size[x] += 1
+            if parent[x] >= 0:
+                size[parent[x]] += size[x]
+    return parent, pre, size

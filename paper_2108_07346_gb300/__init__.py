@@ -71,6 +71,7 @@ _SIGS = {
     "bridges_find_host": (_I64, [_P, _P, _P, _P, _I64, _I32, _I32, _P]),
     "bridges_certificate": (_I64, [_P, _P, _P, _P, _I64, _I32, _I32, _P, _P, _P]),
     "bridges_from_forest": (_I64, [_P, _P, _P, _P, _I64, _P, _P, _I64, _I32, _P]),
+    "bridges_rooted_forest": (_I64, [_P, _P, _P, _P, _I64, _I32, _P, _P, _P]),
     "bridges_ctx_stage_ms": (_I32, [_P, ctypes.POINTER(ctypes.c_float), _I32]),
     "bridges_ctx_stage_ms_history": (_I32, [_P, ctypes.POINTER(ctypes.c_float), _I32]),
     "bridges_ctx_launches": (_I64, [_P]),
@@ -248,6 +249,16 @@ class Context:
                                            _ptr(xv), xu.numel(), V, _ptr(out))
         n = _check(rc, "bridges_from_forest")
         return out[: 2 * n].view(n, 2)
+
+    def rooted_forest(self, tu, tv, V: int, stream=None):
+        """bridges_rooted_forest: (parent, pre, size) of forest (tu, tv), each tree rooted at its
+        minimum vertex and numbered in preorder (int32 CUDA tensors of length V)."""
+        tu, tv = _dev_edges(tu, tv)
+        outs = [torch.empty(max(V, 1), dtype=torch.int32, device=tu.device) for _ in range(3)]
+        rc = self._lib.bridges_rooted_forest(self._h, _stream(stream), _ptr(tu), _ptr(tv), tu.numel(), V,
+                                             *[_ptr(o) for o in outs])
+        _check(rc, "bridges_rooted_forest")
+        return tuple(o[:V] for o in outs)
 
     def find_batched(self, u, v, edge_off, Vs, out=None, counts=None, stream=None, sync=True):
         """bridges_find_batched.  ``edge_off`` (G+1) and ``Vs`` (G) are host integer arrays.

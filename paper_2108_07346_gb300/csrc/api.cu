@@ -519,6 +519,37 @@ int64_t bridges_from_forest(bridges_ctx* c, struct CUstream_st* stream, const in
   return c->h_pinned[1];
 }
 
+int64_t bridges_rooted_forest(bridges_ctx* c, struct CUstream_st* stream, const int32_t* tu, const int32_t* tv,
+                              int64_t n_tree, int32_t V, int32_t* out_parent, int32_t* out_pre, int32_t* out_size) {
+  if (!c || V < 0 || n_tree < 0 || n_tree > std::max(V - 1, 0) || V > (1 << 30)) return BRIDGES_EINVAL;
+  if (n_tree > 0 && (!tu || !tv)) return BRIDGES_EINVAL;
+  if (V == 0) return BRIDGES_OK;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  if (cudaSetDevice(c->device) != cudaSuccess) return cuda_fail(cudaGetLastError());
+  CertPlan p = make_plan(0, V, 1, 2, 0, 0, 0, c->num_sms, c->smem_optin);
+  int64_t rc = ensure_ws(c, total_bytes(p), s);
+  if (rc) return rc;
+  Carved k = carve(c, p);
+  Launch L{s, &c->launches, c->num_sms, c->smem_optin};
+  int32_t* h = reinterpret_cast<int32_t*>(c->h_pinned);
+  cudaStreamSynchronize(s);  // the pinned scratch may still be read by an earlier copy
+  h[0] = (int32_t)n_tree;
+  h[1] = 0;
+  cudaMemsetAsync(k.status, 0, sizeof(int32_t), s);
+  cudaMemcpyAsync(k.counts, h, 2 * sizeof(int32_t), cudaMemcpyHostToDevice, s);
+  // with no extra edges every tree edge is a bridge; the sorted list goes to dscan, which the
+  // stage no longer reads once it sorts
+  final_stage(L, k.fin, V, tu, tv, k.counts, n_tree, nullptr, nullptr, k.counts + 1, 0, nullptr, k.fin.dscan);
+  const size_t bytes = sizeof(int32_t) * (size_t)V;
+  if ((out_parent && cudaMemcpyAsync(out_parent, k.fin.par, bytes, cudaMemcpyDeviceToDevice, s) != cudaSuccess) ||
+      (out_pre && cudaMemcpyAsync(out_pre, k.fin.pre, bytes, cudaMemcpyDeviceToDevice, s) != cudaSuccess) ||
+      (out_size && cudaMemcpyAsync(out_size, k.fin.sz, bytes, cudaMemcpyDeviceToDevice, s) != cudaSuccess) ||
+      cudaMemcpyAsync(c->h_pinned + 1, k.fin.count, sizeof(int64_t), cudaMemcpyDeviceToHost, s) != cudaSuccess)
+    return cuda_fail(cudaGetLastError());
+  if (cudaStreamSynchronize(s) != cudaSuccess) return cuda_fail(cudaGetLastError());
+  return c->h_pinned[1] < 0 ? c->h_pinned[1] : BRIDGES_OK;
+}
+
 int32_t bridges_ctx_stage_ms(const bridges_ctx* c, float* ms, int32_t n) {
   if (!c || !c->events || !ms || c->calls == 0) return 0;
   bridges_ctx* m = const_cast<bridges_ctx*>(c);

@@ -351,3 +351,79 @@ def test_streaming_certificate_equals_two_pass():
         ids2, f2 = oracle.certificate(u, v, V)
         ids1, f1 = oracle.certificate_stream(u, v, V)
         assert sorted(zip(ids1.tolist(), f1.tolist())) == sorted(zip(ids2.tolist(), f2.tolist())), t
+
+
+def _check_rooted_forest(tu, tv, V, parent, pre, size, key):
+    """The rooted forest by its definitions, not by a second search: the parent edges are the
+    input edges, every root is its component's minimum vertex, sizes count the vertices whose
+    root path passes through each vertex, and the numbering is the preorder for the sibling
+    order `key` (a vertex, then its children's subtrees in key order, the trees consecutive in
+    increasing order of their roots)."""
+    tu, tv = np.asarray(tu), np.asarray(tv)
+    got = {(min(x, int(p)), max(x, int(p))) for x, p in enumerate(parent) if p >= 0}
+    assert got == {(min(a, b), max(a, b)) for a, b in zip(tu.tolist(), tv.tolist())}
+    _, comp = oracle.components(tu, tv, V)
+    roots = [x for x in range(V) if parent[x] < 0]
+    assert roots == sorted(set(comp.tolist()))  # one root per component, its minimum vertex
+    count = np.zeros(V, np.int64)
+    for y in range(V):  # brute force: y counts for every vertex on its root path
+        x, steps = y, 0
+        while x >= 0:
+            count[x] += 1
+            x = parent[x]
+            steps += 1
+            assert steps <= V
+    assert count.tolist() == np.asarray(size).tolist()
+    kids = [[] for _ in range(V)]
+    for x in range(V):
+        if parent[x] >= 0:
+            kids[parent[x]].append(x)
+    at = 0
+    for r in roots:
+        assert pre[r] == at
+        at += size[r]
+    for p in range(V):
+        nxt = pre[p] + 1
+        for c in sorted(kids[p], key=lambda c: key[c]):
+            assert pre[c] == nxt
+            nxt += size[c]
+        assert nxt == pre[p] + size[p]
+    assert sorted(np.asarray(pre).tolist()) == list(range(V))
+
+
+def test_rooted_forest_closed_forms():
+    rng = np.random.default_rng(81)
+    n = 50
+    a = np.arange(n - 1)
+    perm = rng.permutation(n - 1)
+    flip = rng.random(n - 1) < 0.5
+    pu, pv = np.where(flip, a + 1, a)[perm], np.where(flip, a, a + 1)[perm]
+    parent, pre, size = oracle.rooted_forest(pu, pv, n)  # path in shuffled order and direction
+    assert parent.tolist() == [-1] + list(range(n - 1))
+    assert pre.tolist() == list(range(n)) and size.tolist() == list(range(n, 0, -1))
+    c = 7  # star around vertex 7: the root is leaf 0, then the centre, then the other leaves
+    leaves = np.array([x for x in range(n) if x != c])
+    parent, pre, size = oracle.rooted_forest(np.full(n - 1, c), leaves, n)
+    assert parent[0] == -1 and parent[c] == 0 and all(parent[x] == c for x in leaves[1:])
+    assert size[0] == n and size[c] == n - 1 and pre[c] == 1
+    assert [pre[x] for x in leaves[1:]] == list(range(2, n))
+    parent, pre, size = oracle.rooted_forest([], [], 5)  # no edges: five one-vertex trees
+    assert parent.tolist() == [-1] * 5 and pre.tolist() == list(range(5)) and size.tolist() == [1] * 5
+    for bad in (([0, 1, 2], [1, 2, 0], 3), ([0, 0], [1, 1], 2), ([0], [3], 3)):
+        with pytest.raises(ValueError):
+            oracle.rooted_forest(*bad)
+
+
+def test_rooted_forest_against_definitions():
+    rng = np.random.default_rng(82)
+    for t in range(60):
+        V = int(rng.integers(1, 120))
+        par = [int(rng.integers(0, x)) if (x and rng.random() < 0.8) else -1 for x in range(V)]
+        relabel = rng.permutation(V)
+        edges = [(int(relabel[x]), int(relabel[p])) for x, p in enumerate(par) if p >= 0]
+        rng.shuffle(edges)
+        tu = np.array([e[0] for e in edges], np.int32)
+        tv = np.array([e[1] for e in edges], np.int32)
+        key = rng.permutation(V) if t % 2 else None
+        parent, pre, size = oracle.rooted_forest(tu, tv, V, key)
+        _check_rooted_forest(tu, tv, V, parent, pre, size, np.arange(V) if key is None else key)
