@@ -37,6 +37,7 @@ UNIT = "GE/s"
 #   block pass stream: 9.512 GB read + 11.0 MB written for 1,073,547,340 streamed edges
 TRAFFIC = {"certify_sha": "6120be18ea0521d8", "bytes_per_edge": 8.6864}
 AP_TRAFFIC = {"blocks_sha": "cc633b86cfc99c54", "bytes_per_edge": 8.8912}
+FUSED_TRAFFIC = {"blocks_sha": None, "bytes_per_edge": None}
 
 
 def peaks():
@@ -56,12 +57,12 @@ def sources_sha(names):
 
 def certify_sha():
     """Hash of the forest pass's sources (the traffic figure is only valid for them)."""
-    return sources_sha(("certify.cu", "common.cuh", "stream.cuh"))
+    return sources_sha(("certify.cu", "common.cuh", "forest.cuh", "stream.cuh"))
 
 
 def blocks_sha():
     """Hash of the block pass's sources."""
-    return sources_sha(("blocks.cu", "common.cuh", "stream.cuh"))
+    return sources_sha(("blocks.cu", "common.cuh", "forest.cuh", "stream.cuh"))
 
 
 class Clocks:
@@ -386,8 +387,9 @@ def cpu_oracle_ap_rate(g, sample_edges):
 
 
 def run_articulation(args, world, rank, local):
-    """Articulation points (and bridges) of the large workload: the bridge path, then the block
-    pass over the same 1.07 G edges; a step is one bridges_articulation_points call."""
+    """Articulation points (and bridges) of the large workload; a step is one
+    bridges_articulation_points call: one fused read of the 1.07 G edges for the certificate and
+    the block pass (the automatic form for this plan), or the bridge path and then a second pass."""
     import torch
 
     import paper_2108_07346_gb300 as pb
@@ -442,7 +444,13 @@ def run_articulation(args, world, rank, local):
     ap_warm = cfg["ap_warm_edges"] if cfg["ap_warm_edges"] >= 0 else None
     peak, peak_kind = peaks()
     kernels = {}
-    if warm is not None and ap_warm is not None and ap_hist and br_hist:
+    fused = cfg.get("ap_fused", 0) == 1
+    if fused and ap_hist and br_hist:
+        # one stream over all E edges: the warm-up prefix for the classes, the rest for both
+        fs_bpe = FUSED_TRAFFIC["bytes_per_edge"] if FUSED_TRAFFIC["blocks_sha"] == blocks_sha() else None
+        kernels = {"fused stream (ap_fused_kernel<forest, vec>)": (statistics.mean(h["stream"] for h in ap_hist), E,
+                                                                  fs_bpe)}
+    elif warm is not None and ap_warm is not None and ap_hist and br_hist:
         fe = E - cfg["M"] * warm
         se = E - ap_warm
         ap_bpe = AP_TRAFFIC["bytes_per_edge"] if AP_TRAFFIC["blocks_sha"] == blocks_sha() else None
@@ -501,6 +509,7 @@ def run_articulation(args, world, rank, local):
             "config": {"workload": f"articulation points of large: ER(65536, p={g.spec.p}) core + 256 pendant trees "
                                    f"+ 128 two-edge vertices, seed {g.spec.seed}",
                        "V": V, "E": E, "M": cfg["M"], "warm_edges": cfg["warm_edges"],
+                       "form": "one fused read of the list" if fused else "bridge path, then a second pass",
                        "block_pass_prefix_edges": cfg["ap_warm_edges"], "block_pass_blocks": cfg["ap_blocks"],
                        "l2": "inputs (8E bytes) larger than L2; no flush",
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU",

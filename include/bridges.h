@@ -73,7 +73,10 @@ typedef struct bridges_opts {
                             (snapshot right after the certificate's own edges) */
   int32_t warm_block;    /* threads per block of the forest pass's warm-up launch (the prefix certified
                             through the union-finds before the snapshot); 0: auto */
-  int32_t reserved[4];
+  int32_t ap_fused;      /* bridges_articulation_points on device edges: 0 = auto (one read of the list
+                            for the certificate and the block pass when the plan is one partition
+                            with a 16-bit label snapshot), < 0 = always the two-pass form */
+  int32_t reserved[3];
 } bridges_opts;
 
 typedef struct bridges_ctx bridges_ctx;
@@ -301,11 +304,15 @@ int64_t bridges_inc_certificate_size(const bridges_inc* inc);
  * Articulation points ("failure points", abstract of the paper): the vertices whose removal
  * increases the number of connected components.  The paper names them but gives no method;
  * its bridge certificate does not keep them (two arbitrary spanning forests can split a
- * biconnected graph at a vertex), so this call runs the bridge path (Sec. 3) for its rooted
- * spanning forest T and then streams the edge list once more, merging for every edge the
- * classes of the tree edges on its fundamental cycle with T; the final classes are the blocks
- * (biconnected components) restricted to T, and a vertex is a cut vertex iff its tree edges lie
- * in two or more of them.  Parallel edges and self-loops are allowed and change nothing.
+ * biconnected graph at a vertex), so this call merges, for every edge, the classes of the tree
+ * edges on its fundamental cycle with a rooted spanning forest T of the bridge path (Sec. 3);
+ * the final classes are the blocks (biconnected components) restricted to T, and a vertex is a
+ * cut vertex iff its tree edges lie in two or more of them.  On device edges with a single-
+ * partition plan that takes a 16-bit label snapshot (opts.ap_fused = 0) both passes share one
+ * read of the list: the forest after the certificate's warm-up is rooted early, and edges whose
+ * cycle needs the final forest are marked and walked at the end; otherwise (and from host
+ * buffers) the bridge path runs first and the list is streamed a second time.  Parallel edges
+ * and self-loops are allowed and change nothing.
  *
  * bridges_articulation_points
  *   edges_u, edges_v, E, V, M : as for bridges_find_ctx (device edges; M for the bridge path).
@@ -381,7 +388,8 @@ int32_t bridges_wait_value(bridges_ctx* ctx, struct CUstream_st* stream, const i
  * bridges_ctx_launches: kernels launched by the context since creation.
  * bridges_ctx_last_config: the M, fan-in, CTAs per partition, block size and warm-up edges
  * of the last call (5 values), then the last bridges_articulation_points call's block-pass
- * prefix edges (-1: no snapshot) and blocks (values 6 and 7); returns min(n, 7).
+ * prefix edges (-1: no snapshot) and blocks (values 6 and 7) and its form (value 8: 1 = one
+ * fused read of the list, 0 = two passes); returns min(n, 8).
  * bridges_status_string: a static description of a status code.
  */
 int32_t bridges_ctx_stage_ms(const bridges_ctx* ctx, float* ms, int32_t n);

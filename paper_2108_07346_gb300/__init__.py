@@ -53,7 +53,8 @@ class Opts(ctypes.Structure):
         ("host_read", ctypes.c_int32),
         ("ap_warm_edges", ctypes.c_int32),
         ("warm_block", ctypes.c_int32),
-        ("reserved", ctypes.c_int32 * 4),
+        ("ap_fused", ctypes.c_int32),
+        ("reserved", ctypes.c_int32 * 3),
     ]
 
 
@@ -167,7 +168,7 @@ class Context:
     """
 
     def __init__(self, device=None, M=0, fan_in=0, block=0, ctas_per_sm=0, warm_edges=-1, profile=False,
-                 mem_budget=0, workspace_bytes=None, host_read=False, ap_warm_edges=0, warm_block=0):
+                 mem_budget=0, workspace_bytes=None, host_read=False, ap_warm_edges=0, warm_block=0, ap_fused=0):
         self._lib = load()
         dev = torch.device("cuda", torch.cuda.current_device()) if device is None else torch.device(device)
         self.device = dev
@@ -176,6 +177,7 @@ class Context:
         o.warm_edges, o.profile, o.host_read = warm_edges, int(bool(profile)), int(bool(host_read))
         o.ap_warm_edges = int(ap_warm_edges)
         o.warm_block = int(warm_block)
+        o.ap_fused = int(ap_fused)
         self._opts = o
         self._ws = None
         with torch.cuda.device(dev):
@@ -303,11 +305,12 @@ class Context:
         return {name: getattr(o, name) for name, _ in Opts._fields_ if name != "reserved"}
 
     def set_opts(self, M=0, fan_in=0, block=0, ctas_per_sm=0, warm_edges=-1, host_read=False, warm_block=0,
-                 ap_warm_edges=0):
+                 ap_warm_edges=0, ap_fused=0):
         o = Opts()
         o.M, o.fan_in, o.block, o.ctas_per_sm, o.warm_edges = M, fan_in, block, ctas_per_sm, warm_edges
         o.host_read = int(bool(host_read))
         o.warm_block, o.ap_warm_edges = int(warm_block), int(ap_warm_edges)
+        o.ap_fused = int(ap_fused)
         _check(self._lib.bridges_ctx_set_opts(self._h, ctypes.byref(o)), "bridges_ctx_set_opts")
 
     def wait_value(self, flag, value: int, max_polls: int, stream=None) -> int:
@@ -402,9 +405,9 @@ class Context:
         return int(self._lib.bridges_ctx_launches(self._h))
 
     def last_config(self):
-        buf = (ctypes.c_int64 * 7)()
-        k = self._lib.bridges_ctx_last_config(self._h, buf, 7)
-        names = ["M", "fan_in", "blocks_per_partition", "block", "warm_edges", "ap_warm_edges", "ap_blocks"]
+        buf = (ctypes.c_int64 * 8)()
+        k = self._lib.bridges_ctx_last_config(self._h, buf, 8)
+        names = ["M", "fan_in", "blocks_per_partition", "block", "warm_edges", "ap_warm_edges", "ap_blocks", "ap_fused"]
         return {names[i]: int(buf[i]) for i in range(k)}
 
 

@@ -576,7 +576,7 @@ int64_t bridges_ctx_launches(const bridges_ctx* c) { return c ? c->launches : 0;
 
 int32_t bridges_ctx_last_config(const bridges_ctx* c, int64_t* vals, int32_t n) {
   if (!c || !vals) return 0;
-  int32_t k = std::min<int32_t>(n, 7);
+  int32_t k = std::min<int32_t>(n, 8);
   for (int i = 0; i < k; i++) vals[i] = c->last_cfg[i];
   return k;
 }
@@ -1030,6 +1030,79 @@ static int64_t ap_warm_edges(const bridges_ctx* c, int64_t E, int32_t V) {
   return std::min<int64_t>(E, 2 * (int64_t)V + 4096);
 }
 
+// The plan of the two-pass block pass (also the fused form's fallback): the whole list as one
+// partition, its own prefix before the snapshot.
+static CertPlan block_pass_plan(const bridges_ctx* c, int64_t E, int32_t V) {
+  CertPlan q = plan_for(c, E, V, 1);
+  q.warm = ap_warm_edges(c, E, V);
+  // The plan's snapshot form: 16-bit labels when 2V bytes fit in shared memory, else a bitmap of
+  // the largest class, taken only when it reaches every vertex (R-MAT, 2^21 vertices, 1.85 M in
+  // reach: 0.71 ms for the block pass with it, 0.66 without).  With the bitmap the automatic
+  // prefix is none: the certificate's blocks already seed the classes (R-MAT 2^18 / 2^20: 0.12 /
+  // 0.22 ms without a prefix, 0.16 / 0.31 ms with 2V + 4096 edges, 0.21 / 0.59 ms with no snapshot).
+  if (q.mode == 2 && c->opts.ap_warm_edges == 0) q.warm = 0;
+  q.cache = (q.mode == 1 || (q.mode == 2 && q.Vb >= V)) && q.warm < E;
+  return q;
+}
+
+// One read of the list for both passes: one partition with a 16-bit label snapshot.
+static bool fused_eligible(const bridges_ctx* c, const CertPlan& p, int64_t E, int32_t V) {
+  return c->opts.ap_fused >= 0 && p.M == 1 && p.cache && p.mode == 1 && V >= 2 && E > p.warm;
+}
+
+// Workspace of the fused form: the bridge path's, two sets of class buffers (T_0's, the final
+// T's) and one mark per edge.
+static size_t fused_ws_bytes(const CertPlan& p, int32_t V) {
+  return align_up(total_bytes(p), 256) + 2 * align_up(ap_bytes(V), 256) + fused_bytes(p.E);
+}
+
+static int64_t articulation_fused_run(bridges_ctx* c, cudaStream_t s, const Launch& L, const CertPlan& p,
+                                      const int32_t* u, const int32_t* v, int64_t E, int32_t V, int32_t* out_points,
+                                      int32_t* out_bridges, int64_t* out_counts_device) {
+  Range range("bridges: articulation points, fused");
+  const size_t ap_at = align_up(total_bytes(p), 256);
+  const size_t apb = align_up(ap_bytes(V), 256);
+  int64_t rc = ensure_ws(c, fused_ws_bytes(p, V), s);
+  if (rc) return rc;
+  Carved k = carve(c, p);
+  char* ws = static_cast<char*>(c->ws);
+  const ApBufs b0 = carve_ap(ws + ap_at, V);
+  const ApBufs b1 = carve_ap(ws + ap_at + apb, V);
+  const FusedBufs fb = carve_fused(ws + ap_at + 2 * apb, E);
+  c->last_cfg[0] = p.M;
+  c->last_cfg[1] = p.f;
+  c->last_cfg[2] = p.G;
+  c->last_cfg[3] = p.block;
+  c->last_cfg[4] = p.warm;
+  c->last_cfg[5] = p.warm;
+  c->last_cfg[6] = p.G;
+  c->last_cfg[7] = 1;
+  cudaEvent_t* bev = next_event_slot(c);
+  if (bev) cudaEventRecord(bev[7], s);
+  cudaEvent_t* aev = nullptr;
+  if (c->events) {
+    resolve_ap_timings(c, c->ap_calls - bridges_ctx::kRing + 1);  // the slot's previous call
+    aev = c->ap_ev[c->ap_calls % bridges_ctx::kRing];
+  }
+  cudaMemsetAsync(k.status, 0, sizeof(int32_t), s);
+  cert_init(L, p, k.cert);
+  articulation_fused(L, p, k.cert, k.fin, b0, b1, fb, u, v, out_points, out_bridges, b1.count, bev, aev);
+  if (bev) c->calls++;
+  if (aev) c->ap_calls++;
+  if (cudaGetLastError() != cudaSuccess) return BRIDGES_ECUDA;
+  if (out_counts_device) {
+    if (cudaMemcpyAsync(out_counts_device, b1.count, sizeof(int64_t), cudaMemcpyDeviceToDevice, s) != cudaSuccess ||
+        cudaMemcpyAsync(out_counts_device + 1, k.fin.count, sizeof(int64_t), cudaMemcpyDeviceToDevice, s) !=
+            cudaSuccess)
+      return cuda_fail(cudaGetLastError());
+    return BRIDGES_OK;
+  }
+  if (cudaMemcpyAsync(c->h_pinned, b1.count, sizeof(int64_t), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      cudaStreamSynchronize(s) != cudaSuccess)
+    return cuda_fail(cudaGetLastError());
+  return c->h_pinned[0];
+}
+
 // The articulation-point path on device edges (u, v).  When hu / hv are given (and the edges
 // were not copied yet), the bridge path's forest pass runs behind a chunked copy of them into
 // (u, v) (run_path_host); the block pass then streams (u, v) from the device.
@@ -1040,10 +1113,13 @@ static int64_t articulation_run(bridges_ctx* c, cudaStream_t s, const int32_t* u
   if (!out_points) out_points = dummy_out;  // V <= 1: nothing is written
   const CertPlan p0 = plan_for(c, E, V, M);
   const size_t ap_at = align_up(total_bytes(p0), 256);
+  Launch L{s, &c->launches, c->num_sms, c->smem_optin};
+  if (!hu && fused_eligible(c, p0, E, V)) return articulation_fused_run(c, s, L, p0, u, v, E, V, out_points, out_bridges,
+                                                                       out_counts_device);
   int64_t rc = ensure_ws(c, ap_at + ap_bytes(V), s);
   if (rc) return rc;
   Carved k{};
-  Launch L{s, &c->launches, c->num_sms, c->smem_optin};
+  c->last_cfg[7] = 0;
   rc = 1;
   if (hu) {
     // the rooted forest is needed either way; without a bridge buffer the bridges go to dscan,
@@ -1069,15 +1145,7 @@ static int64_t articulation_run(bridges_ctx* c, cudaStream_t s, const int32_t* u
   Range range("bridges: articulation block pass");
   ApBufs b = carve_ap(static_cast<char*>(c->ws) + ap_at, V);
   // the block pass streams the whole list as one partition, its own warm-up before the snapshot
-  CertPlan q = plan_for(c, E, V, 1);
-  q.warm = ap_warm_edges(c, E, V);
-  // The plan's snapshot form: 16-bit labels when 2V bytes fit in shared memory, else a bitmap of
-  // the largest class, taken only when it reaches every vertex (R-MAT, 2^21 vertices, 1.85 M in
-  // reach: 0.71 ms for the block pass with it, 0.66 without).  With the bitmap the automatic
-  // prefix is none: the certificate's blocks already seed the classes (R-MAT 2^18 / 2^20: 0.12 /
-  // 0.22 ms without a prefix, 0.16 / 0.31 ms with 2V + 4096 edges, 0.21 / 0.59 ms with no snapshot).
-  if (q.mode == 2 && c->opts.ap_warm_edges == 0) q.warm = 0;
-  q.cache = (q.mode == 1 || (q.mode == 2 && q.Vb >= V)) && q.warm < E;
+  const CertPlan q = block_pass_plan(c, E, V);
   c->last_cfg[5] = q.cache ? q.warm : -1;
   c->last_cfg[6] = (int64_t)q.G * q.M;
   cudaEvent_t* ev = nullptr;
@@ -1143,7 +1211,10 @@ extern "C" int64_t bridges_articulation_points_host(bridges_ctx* c, struct CUstr
 
 extern "C" int64_t bridges_articulation_workspace_bytes(const bridges_ctx* c, int64_t E, int32_t V, int32_t M) {
   if (!c || E < 0 || V < 0) return 0;
-  return (int64_t)(align_up(total_bytes(plan_for(c, E, V, M)), 256) + ap_bytes(V));
+  const CertPlan p = plan_for(c, E, V, M);
+  const size_t two_pass = align_up(total_bytes(p), 256) + ap_bytes(V);
+  if (!fused_eligible(c, p, E, V)) return (int64_t)two_pass;  // (the host form never fuses)
+  return (int64_t)std::max(two_pass, fused_ws_bytes(p, V));
 }
 
 extern "C" int32_t bridges_ctx_ap_stage_ms(const bridges_ctx* c, float* ms, int32_t n) {

@@ -29,10 +29,15 @@
 // the misses.  Classes only grow, so a stale label is still sound.  When 2V bytes of labels do
 // not fit in shared memory, one bit per vertex marks the largest class of all instead (both
 // ends in it: redundant), for the vertices below the bitmap's reach; every other edge walks.
+//
+// For one partition with labels the two streams are fused into one (see "the fused path"
+// below): the forest after the certificate's warm-up is rooted early and serves as T for every
+// edge inside one of its trees.
 #include <algorithm>
 #include <cmath>
 
 #include "common.cuh"
+#include "forest.cuh"
 #include "stream.cuh"
 
 namespace bridges {
@@ -110,7 +115,7 @@ __device__ __noinline__ void cycle_misses(const ApArgs& A, uint32_t m, const int
 // The block pass's slow path (see stream_range).
 struct CycleSink {
   const ApArgs& A;
-  __device__ __forceinline__ void slot(bool need, int32_t a, int32_t b) const {
+  __device__ __forceinline__ void slot(bool need, int32_t a, int32_t b, int64_t) const {
     if (need) offer_edge(A, a, b);
   }
   __device__ __forceinline__ void misses(uint32_t m, const int32_t* ub, const int32_t* vb, int32_t base) const {
@@ -413,6 +418,165 @@ __global__ void ap_scatter_kernel(ApBufs b, int32_t V, int64_t ntiles, const int
   }
 }
 
+// ---- the fused path: the certificate's stream and the block pass in one read of the list ----
+//
+// The block pass needs a rooted spanning forest, which the bridge path only has at its end.  In
+// a dense graph, though, F after the forest pass's warm-up (T_0) already spans nearly every
+// vertex, and F only grows: T_0 is a subforest of the final T.  So T_0 is rooted and numbered
+// right after the warm-up (the final stage on the partial certificate), its classes are seeded
+// (the blocks of T_0 u F'), and one stream then serves both passes: an edge is dropped from
+// shared memory when both ends carry the same combined label (same F' component, both in the
+// largest class), otherwise it is offered to the union-finds and, unless it just became a tree
+// edge, its cycle is merged on T_0 -- its path in the final T is its path in T_0 whenever both
+// ends lie in one tree of T_0.  Edges between two trees of T_0 are marked in a bitmap over the
+// list and walked once the final T is known, after the classes are renamed from T_0's edges to
+// T's (every edge of T_0 is an edge of T).  Walking any edge of the list is a valid merge, so
+// the marks need no order and no bound, and the bitmap is never cleared as a whole: a top-level
+// bitmap (one bit per word, cleared by every call) says which words this call marked, and the
+// walk clears each word it reads.  A stale bit in such a word only adds a walk.
+
+struct FusedArgs {
+  ApArgs A;               // classes over T_0: its preorder numbers, parents and subtree ends
+  Job J;                  // the certificate's union-finds and lists (one partition)
+  const int32_t* root0;   // [V] the root of each vertex's tree in T_0
+  uint32_t* keep;         // [E/32 + 1] marks of the edges walked on the final T
+  uint32_t* top;          // one bit per word of keep: marked in this call
+  const int32_t* u;
+  const int32_t* v;
+  int64_t s, t;           // edge range of this launch
+  const uint16_t* lab;    // combined labels (Vpad entries)
+  int64_t Vpad;
+};
+
+// One edge per lane (list index i), every lane of the warp calls it; `go`: the lane has a live
+// edge (ids in range, not a loop) that missed the snapshot.
+template <bool FOREST>
+__device__ __forceinline__ void fused_edge(const FusedArgs& F, bool go, int32_t a, int32_t b, int64_t i) {
+  int r = 0;
+  if (FOREST) {
+    r = go ? offer(F.J, a, b) : 0;
+    warp_append(r == 1, a, b, F.J.cnt + 0, F.J.f1u, F.J.f1v, F.A.V, F.A.status);
+    warp_append(r == 2, a, b, F.J.cnt + 1, F.J.f2u, F.J.f2v, F.A.V, F.A.status);
+  }
+  // a new edge of T closes no cycle; an edge inside one tree of T_0 is walked now, any other
+  // edge once the final T is known
+  if (!go || r == 1) return;
+  if (__ldg(F.root0 + a) == __ldg(F.root0 + b)) {
+    const int32_t h = cycle_merge(F.A, __ldg(F.A.pre + a), __ldg(F.A.pre + b));
+    if (h) atomicAdd(F.A.hooks, h);
+  } else {
+    const int64_t w = i >> 5;
+    atomicOr(F.keep + w, 1u << (i & 31));
+    atomicOr(F.top + (w >> 5), 1u << (w & 31));
+  }
+}
+
+template <bool FOREST>
+__device__ __noinline__ void fused_misses(const FusedArgs& F, uint32_t m, const int32_t* __restrict__ u,
+                                          const int32_t* __restrict__ v, int32_t base) {
+  while (__any_sync(kFull, m != 0)) {
+    int32_t a = 0, b = 0;
+    int64_t e = 0;
+    bool go = false;
+    if (m) {
+      const int bit = __ffs(m) - 1;
+      m &= m - 1;
+      e = miss_edge(bit, base);
+      a = u[e];
+      b = v[e];
+      go = checked_edge(F.A, a, b);
+    }
+    fused_edge<FOREST>(F, go, a, b, (u - F.u) + e);
+  }
+}
+
+template <bool FOREST>
+struct FusedSink {
+  const FusedArgs& F;
+  __device__ __forceinline__ void slot(bool need, int32_t a, int32_t b, int64_t i) const {
+    fused_edge<FOREST>(F, need && checked_edge(F.A, a, b), a, b, i);
+  }
+  __device__ __forceinline__ void misses(uint32_t m, const int32_t* ub, const int32_t* vb, int32_t base) const {
+    fused_misses<FOREST>(F, m, ub, vb, base);
+  }
+};
+
+// FOREST: the edges after the warm-up prefix (certificate and block pass); otherwise the
+// prefix itself, which the certificate has already seen (block pass only).
+template <bool FOREST, bool VEC>
+__global__ void __launch_bounds__(1024, 1) ap_fused_kernel(FusedArgs F) {
+  extern __shared__ __align__(16) uint16_t slab[];
+  __shared__ int32_t stop;
+  if (threadIdx.x == 0) stop = *F.A.status;
+  __syncthreads();
+  if (stop) return;  // block-uniform: the stream below contains barriers
+  const int64_t n = F.t - F.s;
+  const int64_t s = F.s + n * blockIdx.x / gridDim.x, t = F.s + n * (blockIdx.x + 1) / gridDim.x;
+  load_labels(slab, F.lab, F.Vpad);
+  const FusedSink<FOREST> S{F};
+  stream_range<1, VEC, kUnroll>(S, F.u, F.v, s, t, (uint32_t)F.A.V, slab);
+}
+
+// The combined snapshot, in place over the certificate's F' labels: a vertex keeps its F' label
+// only if it lies in the largest class (whose label id the class root's tmp entry holds).
+__global__ void ap_combine_kernel(uint16_t* flab, ApBufs b, int64_t Vpad, int32_t V, const int32_t* status) {
+  if (*status) return;
+  const unsigned long long g = *b.giant;
+  const int32_t gid = g ? b.tmp[(int32_t)(uint32_t)g] : -1;
+  for (int64_t x = gtid(); x < Vpad; x += gstride()) {
+    const bool keep = x < V && gid >= 0 && gid < (int32_t)kNoLabel && b.lab[x] == (uint16_t)gid;
+    if (!keep) flab[x] = kNoLabel;
+  }
+}
+
+// T_0's classes renamed onto the final T: tree edge i of T_0 (child x, parent p) is the edge of
+// T whose child is x or p, whichever T makes the child; it joins the renamed edge of its class's
+// root in b1's union-find (which starts as singletons over T's preorder numbers).
+__device__ __forceinline__ int32_t renamed(const FinalBufs& f, int32_t x, int32_t p, int32_t* status) {
+  if (f.par[x] == p) return f.pre[x];
+  if (f.par[p] == x) return f.pre[p];
+  set_status(status, BRIDGES_EINTERNAL_CODE);  // T_0 must be part of T
+  return -1;
+}
+
+__global__ void ap_rename_kernel(FinalBufs f, ApBufs b0, ApBufs b1, int32_t V) {
+  if (*f.status) return;
+  for (int64_t i = gtid(); i < V; i += gstride()) {
+    const int32_t pi = b0.PP[i];
+    if (pi < 0) continue;
+    const int32_t r = uf_find_static(b0.Q, (int32_t)i);
+    const int32_t pr = b0.PP[r];
+    if (pr < 0) {
+      set_status(f.status, BRIDGES_EINTERNAL_CODE);  // a class root is a tree edge
+      continue;
+    }
+    const int32_t n = renamed(f, b0.vtx[i], b0.vtx[pi], f.status);
+    const int32_t nr = renamed(f, b0.vtx[r], b0.vtx[pr], f.status);
+    if (n >= 0 && nr >= 0 && n != nr) uf_link(b1.Q, n, nr);
+  }
+}
+
+// The marked edges, walked on the final T: the words the top level names are read and cleared
+// (marks past E are ignored).
+__global__ void ap_kept_kernel(ApArgs A, const int32_t* u, const int32_t* v, uint32_t* keep, const uint32_t* top,
+                               int64_t ntop, int64_t E) {
+  const bool ok = *A.status == 0;
+  for (int64_t t = gtid(); t < ntop; t += gstride()) {
+    uint32_t words = top[t];
+    while (words) {
+      const int64_t w = t * 32 + (__ffs(words) - 1);
+      words &= words - 1;
+      uint32_t bits = keep[w];
+      keep[w] = 0;
+      while (ok && bits) {
+        const int64_t i = w * 32 + (__ffs(bits) - 1);
+        bits &= bits - 1;
+        if (i < E) offer_edge(A, u[i], v[i]);
+      }
+    }
+  }
+}
+
 int grid_of(const Launch& L, int64_t work, int block) {
   const int64_t g = ceil_div(std::max<int64_t>(work, 1), block);
   return (int)std::min<int64_t>(g, (int64_t)L.num_sms * 16);
@@ -421,6 +585,57 @@ int grid_of(const Launch& L, int64_t work, int block) {
 template <int MODE, bool VEC>
 void launch_pass(const Launch& L, const PassArgs& a, int grid, int block, size_t smem) {
   auto k = ap_pass_kernel<MODE, VEC>;
+  if (smem > 48 * 1024) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  k<<<grid, block, smem, L.stream>>>(a);
+  *L.launches += 1;
+}
+
+// Articulation points from the final classes: marking and ordered compaction into out, their
+// number (or the status) into *count_dev.
+void ap_finish(const Launch& L, const FinalBufs& f, const ApBufs& b, int32_t V, int32_t* out, int64_t* count_dev) {
+  const int bs = 256;
+  const int64_t ntiles = ceil_div(std::max(V, 1), (int64_t)kCompactThreads * kCompactItems);
+  ap_mark_kernel<<<grid_of(L, V, bs), bs, 0, L.stream>>>(b, V, f.status);
+  ap_tile_count_kernel<<<grid_of(L, ntiles * kCompactThreads, kCompactThreads), kCompactThreads, 0, L.stream>>>(
+      b, V, ntiles);
+  ap_tile_scan_kernel<<<1, kCompactThreads, 0, L.stream>>>(b, ntiles, f.status, count_dev);
+  ap_scatter_kernel<<<grid_of(L, ntiles * kCompactThreads, kCompactThreads), kCompactThreads, 0, L.stream>>>(
+      b, V, ntiles, f.status, out);
+  *L.launches += 4;
+}
+
+// The classes' starting point on a rooted forest: T's preorder copies, then Tarjan & Vishkin's
+// two rules over T u (xu, xv).
+void ap_seed(const Launch& L, const FinalBufs& f, const ApBufs& b, int32_t V, const int32_t* xu, const int32_t* xv,
+             const int32_t* d_nx) {
+  const int bs = 256;
+  const int g = grid_of(L, V, bs);
+  ap_init_kernel<<<g, bs, 0, L.stream>>>(f, b, V);
+  ApArgs A{f.pre, b.Q, b.PP, b.LAST, V, f.status, b.hooks};
+  ap_chain_kernel<<<g, bs, 0, L.stream>>>(b, V, f.status);
+  ap_tv_kernel<<<g, bs, 0, L.stream>>>(f, A, b, xu, xv, d_nx, V);
+  *L.launches += 3;
+}
+
+// The snapshot of the classes: mode 1, 16-bit labels (each vertex labelled with the largest
+// class containing it); mode 2, the bitmap of the largest class over vertices [0, Vb).
+void ap_snapshot(const Launch& L, const FinalBufs& f, const ApBufs& b, int32_t V, int32_t mode, int32_t Vb) {
+  const int bs = 256;
+  const int g = grid_of(L, V, bs);
+  ap_flatten_kernel<<<g, bs, 0, L.stream>>>(b, V, f.status);
+  ap_count_kernel<<<g, bs, 0, L.stream>>>(b, V, f.status);
+  ap_propose_kernel<<<g, bs, 0, L.stream>>>(b, V, f.status);
+  if (mode == 2)
+    ap_bitmap_kernel<<<grid_of(L, Vb / 32 + 4, bs), bs, 0, L.stream>>>(b, f.pre, V, Vb, f.status);
+  else
+    ap_label_kernel<<<grid_of(L, b.Vpad, bs), bs, 0, L.stream>>>(b, f.pre, V, f.status);
+  *L.launches += 4;
+}
+
+template <bool FOREST, bool VEC>
+void launch_fused(const Launch& L, const FusedArgs& a, int grid, int block) {
+  auto k = ap_fused_kernel<FOREST, VEC>;
+  const size_t smem = (size_t)a.Vpad * 2;
   if (smem > 48 * 1024) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   k<<<grid, block, smem, L.stream>>>(a);
   *L.launches += 1;
@@ -468,13 +683,8 @@ void articulation_stage(const Launch& L, const CertPlan& p, const FinalBufs& f, 
                         const int32_t* v, const int32_t* xu, const int32_t* xv, const int32_t* d_nx, int32_t* out,
                         int64_t* count_dev, cudaEvent_t* ev) {
   const int32_t V = p.V;
-  const int bs = 256;
-  const int g = grid_of(L, V, bs);
-  ap_init_kernel<<<g, bs, 0, L.stream>>>(f, b, V);
+  ap_seed(L, f, b, V, xu, xv, d_nx);
   ApArgs A{f.pre, b.Q, b.PP, b.LAST, V, f.status, b.hooks};
-  ap_chain_kernel<<<g, bs, 0, L.stream>>>(b, V, f.status);
-  ap_tv_kernel<<<grid_of(L, V, bs), bs, 0, L.stream>>>(f, A, b, xu, xv, d_nx, V);
-  *L.launches += 3;
   const bool vec = ((reinterpret_cast<uintptr_t>(u) | reinterpret_cast<uintptr_t>(v)) & 15) == 0;
   const int grid = (int)std::max<int64_t>(1, (int64_t)p.G * p.M);
   PassArgs a{A, u, v, 0, p.cache ? std::min(p.warm, p.E) : p.E, b.lab, b.Vpad, p.Vb};
@@ -486,14 +696,7 @@ void articulation_stage(const Launch& L, const CertPlan& p, const FinalBufs& f, 
   }
   if (ev) cudaEventRecord(ev[0], L.stream);
   if (p.cache && p.E > a.t) {
-    ap_flatten_kernel<<<g, bs, 0, L.stream>>>(b, V, f.status);
-    ap_count_kernel<<<g, bs, 0, L.stream>>>(b, V, f.status);
-    ap_propose_kernel<<<g, bs, 0, L.stream>>>(b, V, f.status);
-    if (p.mode == 2)
-      ap_bitmap_kernel<<<grid_of(L, p.Vb / 32 + 4, bs), bs, 0, L.stream>>>(b, f.pre, V, p.Vb, f.status);
-    else
-      ap_label_kernel<<<grid_of(L, b.Vpad, bs), bs, 0, L.stream>>>(b, f.pre, V, f.status);
-    *L.launches += 4;
+    ap_snapshot(L, f, b, V, p.mode, p.Vb);
     if (ev) cudaEventRecord(ev[1], L.stream);
     a.s = a.t;
     a.t = p.E;
@@ -514,14 +717,78 @@ void articulation_stage(const Launch& L, const CertPlan& p, const FinalBufs& f, 
     cudaEventRecord(ev[1], L.stream);
   }
   if (ev) cudaEventRecord(ev[2], L.stream);
-  const int64_t ntiles = ceil_div(std::max(V, 1), (int64_t)kCompactThreads * kCompactItems);
-  ap_mark_kernel<<<g, bs, 0, L.stream>>>(b, V, f.status);
-  ap_tile_count_kernel<<<grid_of(L, ntiles * kCompactThreads, kCompactThreads), kCompactThreads, 0, L.stream>>>(
-      b, V, ntiles);
-  ap_tile_scan_kernel<<<1, kCompactThreads, 0, L.stream>>>(b, ntiles, f.status, count_dev);
-  ap_scatter_kernel<<<grid_of(L, ntiles * kCompactThreads, kCompactThreads), kCompactThreads, 0, L.stream>>>(
-      b, V, ntiles, f.status, out);
-  *L.launches += 4;
+  ap_finish(L, f, b, V, out, count_dev);
+}
+
+size_t fused_bytes(int64_t E) {
+  const int64_t nw = E / 32 + 1, nt = nw / 32 + 1;
+  return align_up(sizeof(uint32_t) * (size_t)nw, 256) + align_up(sizeof(uint32_t) * (size_t)nt, 256);
+}
+
+FusedBufs carve_fused(void* base, int64_t E) {
+  FusedBufs b{};
+  b.nwords = E / 32 + 1;
+  b.ntop = b.nwords / 32 + 1;
+  b.keep = static_cast<uint32_t*>(base);
+  b.top = reinterpret_cast<uint32_t*>(static_cast<char*>(base) + align_up(sizeof(uint32_t) * (size_t)b.nwords, 256));
+  return b;
+}
+
+void articulation_fused(const Launch& L, const CertPlan& p, const CertBufs& cb, const FinalBufs& f, const ApBufs& b0,
+                        const ApBufs& b1, const FusedBufs& fb, const int32_t* u, const int32_t* v, int32_t* out_points,
+                        int32_t* out_bridges, int64_t* count_dev, cudaEvent_t* bev, cudaEvent_t* aev) {
+  const int32_t V = p.V;
+  int32_t* cnt = cb.cnt;
+  if (bev) cudaEventRecord(bev[0], L.stream);
+  if (aev) cudaEventRecord(aev[0], L.stream);
+  cudaMemsetAsync(fb.top, 0, sizeof(uint32_t) * (size_t)fb.ntop, L.stream);
+  cert_warm(L, p, cb, u, v);
+  if (bev) cudaEventRecord(bev[1], L.stream);
+  // T_0: F after the warm-up, rooted and numbered (the bridges of this partial certificate are
+  // not needed and go to dscan), then the classes of T_0 u F'
+  final_stage(L, f, V, cb.f1u, cb.f1v, cnt + 0, V, cb.f2u, cb.f2v, cnt + 1, V, cb.P1, f.dscan);
+  ap_seed(L, f, b0, V, cb.f2u, cb.f2v, cnt + 1);
+  if (aev) cudaEventRecord(aev[1], L.stream);
+  cert_snapshot(L, p, cb);
+  ap_snapshot(L, f, b0, V, 1, 0);
+  const int bs = 256;
+  ap_combine_kernel<<<grid_of(L, cb.Vpad, bs), bs, 0, L.stream>>>(cb.lab, b0, cb.Vpad, V, f.status);
+  *L.launches += 1;
+  if (bev) cudaEventRecord(bev[2], L.stream);
+  if (aev) cudaEventRecord(aev[2], L.stream);
+  const bool vec = ((reinterpret_cast<uintptr_t>(u) | reinterpret_cast<uintptr_t>(v)) & 15) == 0;
+  const int grid = (int)std::max<int64_t>(1, (int64_t)p.G);
+  const Job J{cb.P1, cb.P2, cb.f1u, cb.f1v, cb.f2u, cb.f2v, cnt};
+  FusedArgs a{ApArgs{f.pre, b0.Q, b0.PP, b0.LAST, V, f.status, b0.hooks}, J, f.root, fb.keep, fb.top, u, v, 0,
+              p.warm, cb.lab, cb.Vpad};
+  if (vec)
+    launch_fused<false, true>(L, a, grid, p.block);
+  else
+    launch_fused<false, false>(L, a, grid, p.block);
+  a.s = p.warm;
+  a.t = p.E;
+  if (vec)
+    launch_fused<true, true>(L, a, grid, p.block);
+  else
+    launch_fused<true, false>(L, a, grid, p.block);
+  if (bev) {
+    cudaEventRecord(bev[3], L.stream);
+    cudaEventRecord(bev[4], L.stream);
+  }
+  if (aev) cudaEventRecord(aev[3], L.stream);
+  // the final certificate: its bridges and the final T
+  final_stage(L, f, V, cb.f1u, cb.f1v, cnt + 0, V, cb.f2u, cb.f2v, cnt + 1, V, cb.P1,
+              out_bridges ? out_bridges : f.dscan);
+  if (bev) cudaEventRecord(bev[5], L.stream);
+  const int g = grid_of(L, V, bs);
+  ap_init_kernel<<<g, bs, 0, L.stream>>>(f, b1, V);
+  ap_rename_kernel<<<g, bs, 0, L.stream>>>(f, b0, b1, V);
+  const ApArgs A1{f.pre, b1.Q, b1.PP, b1.LAST, V, f.status, b1.hooks};
+  ap_kept_kernel<<<grid_of(L, fb.ntop, bs), bs, 0, L.stream>>>(A1, u, v, fb.keep, fb.top, fb.ntop, p.E);
+  *L.launches += 3;
+  ap_finish(L, f, b1, V, out_points, count_dev);
+  if (bev) cudaEventRecord(bev[6], L.stream);
+  if (aev) cudaEventRecord(aev[4], L.stream);
 }
 
 }  // namespace bridges

@@ -31,41 +31,12 @@
 #include <cmath>
 
 #include "common.cuh"
+#include "forest.cuh"
 #include "stream.cuh"
 
 namespace bridges {
 
 namespace {
-
-struct Job {
-  int32_t* P1;
-  int32_t* P2;
-  int32_t* f1u;
-  int32_t* f1v;
-  int32_t* f2u;
-  int32_t* f2v;
-  int32_t* cnt;  // [2]
-};
-
-__device__ __forceinline__ Job job_of(const CertBufs& b, int32_t V, int64_t j) {
-  Job J;
-  int64_t o = j * (int64_t)V;
-  J.P1 = b.P1 + o;
-  J.P2 = b.P2 + o;
-  J.f1u = b.f1u + o;
-  J.f1v = b.f1v + o;
-  J.f2u = b.f2u + o;
-  J.f2v = b.f2v + o;
-  J.cnt = b.cnt + 2 * j;
-  return J;
-}
-
-// Offers edge (a, b) to F then F'.  Returns 0 (dropped), 1 (joined F) or 2 (joined F').
-__device__ __forceinline__ int offer(const Job& J, int32_t a, int32_t b) {
-  if (uf_link(J.P1, a, b)) return 1;
-  if (uf_link(J.P2, a, b)) return 2;
-  return 0;
-}
 
 // One edge slot for every lane of a warp.  `need` says whether this lane's edge must go to the
 // union-finds; winners are appended warp-aggregated.
@@ -120,7 +91,7 @@ struct ForestSink {
   const Job& J;
   int32_t V;
   int32_t* status;
-  __device__ __forceinline__ void slot(bool need, int32_t a, int32_t b) const {
+  __device__ __forceinline__ void slot(bool need, int32_t a, int32_t b, int64_t) const {
     settle(J, need && checked(a, b, V, status), a, b, V, status);
   }
   __device__ __forceinline__ void misses(uint32_t m, const int32_t* ub, const int32_t* vb, int32_t base) const {

@@ -31,7 +31,7 @@ struct bridges_ctx {
   int64_t calls = 0;         // profiled calls issued
   int64_t resolved = 0;      // calls whose times have been read back
   float stage_ms[kRing][6]{};
-  int64_t last_cfg[7]{};  // [5], [6]: block pass prefix edges (-1: no snapshot) and blocks
+  int64_t last_cfg[8]{};  // [5], [6]: block pass prefix edges (-1: no snapshot) and blocks; [7] fused
   // profiling of the articulation-point block pass, a ring like the above; per call the events
   // are start, after warm-up, after snapshot, after stream, end
   cudaEvent_t ap_ev[kRing][5]{};

@@ -118,6 +118,14 @@ struct ApBufs {
   int64_t Vpad;
 };
 
+// Buffers of the fused articulation path (blocks.cu).
+struct FusedBufs {
+  uint32_t* keep;  // [nwords] one mark per edge of the list: walked on the final T
+  uint32_t* top;   // [ntop] one bit per word of keep that the current call marked
+  int64_t nwords;  // E / 32 + 1
+  int64_t ntop;    // nwords / 32 + 1
+};
+
 // ---- certify.cu ----
 void cert_init(const Launch& L, const CertPlan& p, const CertBufs& b);
 // Leaf certificates of the M partitions of (u, v) (Sec. 3 phase 0, Alg. 2 per partition).
@@ -170,6 +178,18 @@ ApBufs carve_ap(void* base, int32_t V);
 void articulation_stage(const Launch& L, const CertPlan& p, const FinalBufs& f, const ApBufs& b, const int32_t* u,
                         const int32_t* v, const int32_t* xu, const int32_t* xv, const int32_t* d_nx, int32_t* out,
                         int64_t* count_dev, cudaEvent_t* ev);
+
+// Articulation points and bridges with one read of the list (the fused path; single partition
+// with a 16-bit label snapshot, p): the forest pass's warm-up, T_0 = F rooted and seeded, the
+// combined snapshot, one stream for the certificate and the classes, the final stage (bridges
+// to out_bridges, or scratch when null), the classes renamed onto the final T and the marked
+// edges walked, the points to out_points and their number (or the status) to *count_dev.
+// bev: the bridge path's 8 stage events, aev: the block pass's 5 (either may be null).
+size_t fused_bytes(int64_t E);
+FusedBufs carve_fused(void* base, int64_t E);
+void articulation_fused(const Launch& L, const CertPlan& p, const CertBufs& cb, const FinalBufs& f, const ApBufs& b0,
+                        const ApBufs& b1, const FusedBufs& fb, const int32_t* u, const int32_t* v, int32_t* out_points,
+                        int32_t* out_bridges, int64_t* count_dev, cudaEvent_t* bev, cudaEvent_t* aev);
 
 inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
 inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }

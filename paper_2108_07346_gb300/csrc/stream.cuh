@@ -56,8 +56,8 @@ __device__ __forceinline__ void load_labels(uint16_t* slab, const uint16_t* glab
 // lane reaches the votes.
 //
 // The slow path is the Sink:
-//   S.slot(need, a, b)            every lane of the warp calls it; `need` marks a live edge that
-//                                 missed the snapshot (scalar head and tail);
+//   S.slot(need, a, b, i)         every lane of the warp calls it; `need` marks a live edge (list
+//                                 index i) that missed the snapshot (scalar head and tail);
 //   S.misses(m, ub, vb, base)     the edges of this thread's tile whose bit is set in m (bit
 //                                 4k+c: element 4*(base + k*nt + tid) + c of ub / vb); every
 //                                 lane of the warp calls it.
@@ -76,7 +76,7 @@ __device__ __forceinline__ void stream_range(const Sink& S, const int32_t* __res
     const int64_t i = i0 + tid;
     const bool valid = i < s_al;
     const int32_t a = valid ? ld_stream1(u + i) : 0, b = valid ? ld_stream1(v + i) : 0;
-    S.slot(valid && miss_of<MODE>(a, b, clampv, cache), a, b);
+    S.slot(valid && miss_of<MODE>(a, b, clampv, cache), a, b, i);
   }
   if (VEC) {
     const int32_t* ub = u + s_al;
@@ -115,7 +115,7 @@ __device__ __forceinline__ void stream_range(const Sink& S, const int32_t* __res
     const int64_t i = i0 + tid;
     const bool valid = i < t;
     const int32_t a = valid ? ld_stream1(u + i) : 0, b = valid ? ld_stream1(v + i) : 0;
-    S.slot(valid && miss_of<MODE>(a, b, clampv, cache), a, b);
+    S.slot(valid && miss_of<MODE>(a, b, clampv, cache), a, b, i);
   }
 }
 

@@ -17,7 +17,7 @@ pytestmark = pytest.mark.gpu
 
 
 def dev(a):
-    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.int32)).to("cuda:0")
+    return torch.from_numpy(np.array(a, dtype=np.int32)).to("cuda:0")
 
 
 @pytest.fixture(scope="module")
@@ -168,7 +168,7 @@ def test_block_pass_prefix_options(cuda_lib, ap_warm_edges):
     the list (no snapshot): the cut vertices do not change."""
     g = graphgen.workload("mid")
     ref = oracle.articulation_points(g.u, g.v, g.V).tolist()
-    c = cuda_lib.Context(device="cuda:0", ap_warm_edges=ap_warm_edges)
+    c = cuda_lib.Context(device="cuda:0", ap_warm_edges=ap_warm_edges, ap_fused=-1)
     assert c.articulation_points(dev(g.u), dev(g.v), g.V, 3).cpu().numpy().tolist() == ref
     cfg = c.last_config()
     assert cfg["ap_warm_edges"] == (-1 if ap_warm_edges >= g.E else (0 if ap_warm_edges < 0 else cfg["ap_warm_edges"]))
@@ -235,3 +235,63 @@ def test_beyond_bitmap_reach(ctx):
     u, v = graphgen.rmat(323, 21, 4 << 21)
     V = 1 << 21
     assert gpu_points(ctx, u, v, V, 1).tolist() == oracle.articulation_points(u, v, V).tolist()
+
+
+def two_clusters(seed, n, m, cross, tail=True, pendants=0):
+    """Two dense random clusters of n vertices (m edges each) joined by `cross` disjoint edges,
+    listed after every cluster edge when `tail` (so they arrive after the forest pass's warm-up,
+    between two trees of its forest), plus `pendants` vertices hung on the first cluster."""
+    rng = np.random.default_rng(seed)
+    a = rng.integers(0, n, (2, m))
+    b = rng.integers(n, 2 * n, (2, m))
+    body_u, body_v = np.concatenate([a[0], b[0]]), np.concatenate([a[1], b[1]])
+    cu, cv = rng.permutation(n)[:cross], n + rng.permutation(n)[:cross]
+    pu = 2 * n + np.arange(pendants)
+    pv = rng.integers(0, n, pendants)
+    if tail:  # body shuffled, then the pendants, then the cross edges
+        order = rng.permutation(len(body_u))
+        u, v = np.concatenate([body_u[order], pu, cu]), np.concatenate([body_v[order], pv, cv])
+    else:  # everything shuffled together
+        u, v = np.concatenate([body_u, pu, cu]), np.concatenate([body_v, pv, cv])
+        order = rng.permutation(len(u))
+        u, v = u[order], v[order]
+    return u.astype(np.int32), v.astype(np.int32), 2 * n + pendants
+
+
+def test_fused_against_two_pass(cuda_lib):
+    """One read of the list (the default for one partition with labels) and the two-pass form
+    agree with the oracle on dense graphs, on graphs whose late edges join two trees of the
+    warm-up's forest (walked once the final tree is known), and with the bridges alongside."""
+    fused = cuda_lib.Context(device="cuda:0")
+    two = cuda_lib.Context(device="cuda:0", ap_fused=-1)
+    cases = [graphgen.random_multigraph(53000 + t, V, E) + (V,) for t, (V, E) in
+             enumerate([(300, 200000), (2000, 600000), (5000, 3000001)])]
+    cases += [two_clusters(54000, 1500, 400000, 3, pendants=5), two_clusters(54001, 800, 200000, 400),
+              two_clusters(54002, 1200, 300000, 1, pendants=3), two_clusters(54003, 1000, 250000, 50, tail=False)]
+    g = graphgen.workload("mid")
+    cases.append((g.u, g.v, g.V))
+    for u, v, V in cases:
+        ref = oracle.articulation_points(u, v, V).tolist()
+        refb = oracle.bridges(u, v, V).tolist()
+        pts, br = fused.articulation_points(dev(u), dev(v), V, 0, with_bridges=True)
+        assert fused.last_config()["ap_fused"] == 1, V
+        assert pts.cpu().numpy().tolist() == ref and br.cpu().numpy().tolist() == refb, V
+        assert two.articulation_points(dev(u), dev(v), V, 0).cpu().numpy().tolist() == ref, V
+        assert two.last_config()["ap_fused"] == 0
+
+
+def test_fused_enqueue_only(cuda_lib):
+    """The fused form enqueued with device counts: points and bridges as from the synchronous
+    call, on a graph with edges marked for the final tree."""
+    c = cuda_lib.Context(device="cuda:0")
+    u, v, V = two_clusters(55000, 1500, 400000, 200, pendants=7)
+    ref, refb = oracle.articulation_points(u, v, V).tolist(), oracle.bridges(u, v, V).tolist()
+    cnt = torch.zeros(2, dtype=torch.int64, device="cuda:0")
+    out = torch.full((V,), -7, dtype=torch.int32, device="cuda:0")
+    for _ in range(3):  # the marks of one call must not leak into the next
+        pts, br = c.articulation_points(dev(u), dev(v), V, 0, with_bridges=True, counts_device=cnt, out=out)
+        torch.cuda.synchronize()
+        n, nb = (int(x) for x in cnt.cpu())
+        assert c.last_config()["ap_fused"] == 1
+        assert out[:n].cpu().numpy().tolist() == ref
+        assert br[: 2 * nb].view(nb, 2).cpu().numpy().tolist() == refb
