@@ -35,7 +35,7 @@ UNIT = "GE/s"
 # only for the kernel sources it was measured on (hash of those sources).
 #   forest pass, M = 1: 9.295 GB read + 7.2 MB written for 1,072,703,284 streamed edges
 #   block pass stream: 9.512 GB read + 11.0 MB written for 1,073,547,340 streamed edges
-TRAFFIC = {"certify_sha": "6120be18ea0521d8", "bytes_per_edge": 8.6864}
+TRAFFIC = {"certify_sha": "16e2761306c2235d", "bytes_per_edge": 8.6808}
 AP_TRAFFIC = {"blocks_sha": "cc633b86cfc99c54", "bytes_per_edge": 8.8912}
 FUSED_TRAFFIC = {"blocks_sha": None, "bytes_per_edge": None}
 
@@ -405,7 +405,7 @@ def run_articulation(args, world, rank, local):
     E, V = g.E, g.V
     du = torch.from_numpy(g.u).to(dev)
     dv = torch.from_numpy(g.v).to(dev)
-    ctx = pb.Context(device=dev, profile=True, M=args.M)
+    ctx = pb.Context(device=dev, profile=True, M=args.M, ap_fused=-1 if args.ap_two_pass else 0)
     stream = torch.cuda.current_stream(dev)
     plan = ctx.autotune(du, dv, V, reps=3) if args.M <= 0 and not args.no_tune else None
     pts, br = ctx.articulation_points(du, dv, V, args.M, with_bridges=True)
@@ -710,6 +710,8 @@ def main():
     ap.add_argument("--no-sweep", action="store_true", help="skip the per-M stage timings")
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--ap-two-pass", action="store_true",
+                    help="articulation workload: the bridge path, then a second pass (not the fused read)")
     ap.add_argument("--cpu-sample", type=int, default=2_000_000_000, help="oracle sample (edges; whole graph)")
     ap.add_argument("--ref-sample", type=int, default=150_000_000, help="reference arm sample per step (edges)")
     ap.add_argument("--ap-cpu-sample", type=int, default=100_000_000,

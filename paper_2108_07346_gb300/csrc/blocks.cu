@@ -143,6 +143,7 @@ __global__ void ap_init_kernel(FinalBufs f, ApBufs b, int32_t V) {
     b.PP[i] = pp;
     b.LAST[i] = i + s - 1;
     b.Q[i] = i;
+    b.csize[i] = INT32_MAX;  // the fused form's renaming takes class minima here
     // rule 2: y's subtree has a certificate neighbour outside p's subtree (p not a root)
     bool join = false;
     if (p >= 0 && f.par[p] >= 0) {
@@ -530,8 +531,13 @@ __global__ void ap_combine_kernel(uint16_t* flab, ApBufs b, int64_t Vpad, int32_
 }
 
 // T_0's classes renamed onto the final T: tree edge i of T_0 (child x, parent p) is the edge of
-// T whose child is x or p, whichever T makes the child; it joins the renamed edge of its class's
-// root in b1's union-find (which starts as singletons over T's preorder numbers).
+// T whose child is x or p, whichever T makes the child.  A class of T_0 is a connected subtree of
+// T as well, so its renamed edges form one class of T whose root (minimum preorder number) is the
+// minimum of its members' new names; b1's union-find is written flat, every member pointing at it.
+// Two passes without contention on the big classes: 1) each tree edge records its new name (in
+// b0.tmp) and its class (b0.csize, -1 for none), and the lanes of a warp that share a class take
+// one atomicMin of their minimum into b1.csize[class]; 2) every new name points at its class's
+// minimum.  (b0.tmp and b0.csize are free once the combined snapshot is built.)
 __device__ __forceinline__ int32_t renamed(const FinalBufs& f, int32_t x, int32_t p, int32_t* status) {
   if (f.par[x] == p) return f.pre[x];
   if (f.par[p] == x) return f.pre[p];
@@ -539,20 +545,45 @@ __device__ __forceinline__ int32_t renamed(const FinalBufs& f, int32_t x, int32_
   return -1;
 }
 
-__global__ void ap_rename_kernel(FinalBufs f, ApBufs b0, ApBufs b1, int32_t V) {
+__global__ void ap_rename_min_kernel(FinalBufs f, ApBufs b0, ApBufs b1, int32_t V) {
   if (*f.status) return;
-  for (int64_t i = gtid(); i < V; i += gstride()) {
-    const int32_t pi = b0.PP[i];
-    if (pi < 0) continue;
-    const int32_t r = uf_find_static(b0.Q, (int32_t)i);
-    const int32_t pr = b0.PP[r];
-    if (pr < 0) {
-      set_status(f.status, BRIDGES_EINTERNAL_CODE);  // a class root is a tree edge
-      continue;
+  const int lane = threadIdx.x & 31;
+  for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < V; base += gstride()) {
+    const int64_t i = base + threadIdx.x;
+    int32_t n = -1, r = -1;
+    if (i < V && b0.PP[i] >= 0) {
+      r = uf_find_static(b0.Q, (int32_t)i);
+      const int32_t pr = b0.PP[r];
+      if (pr < 0) {
+        set_status(f.status, BRIDGES_EINTERNAL_CODE);  // a class root is a tree edge
+        r = -1;
+      } else {
+        n = renamed(f, b0.vtx[i], b0.vtx[b0.PP[i]], f.status);
+        if (n < 0) r = -1;
+      }
     }
-    const int32_t n = renamed(f, b0.vtx[i], b0.vtx[pi], f.status);
-    const int32_t nr = renamed(f, b0.vtx[r], b0.vtx[pr], f.status);
-    if (n >= 0 && nr >= 0 && n != nr) uf_link(b1.Q, n, nr);
+    if (i < V) {
+      b0.tmp[i] = n;
+      b0.csize[i] = r;
+    }
+    // one reduction per distinct class among the warp's lanes (the whole warp takes part)
+    unsigned todo = __ballot_sync(kFull, r >= 0);
+    while (todo) {
+      const int lead = __ffs(todo) - 1;
+      const int32_t key = __shfl_sync(kFull, r, lead);
+      const bool mine = r == key && r >= 0;
+      todo &= ~__ballot_sync(kFull, mine);
+      const int32_t mn = __reduce_min_sync(kFull, mine ? n : INT32_MAX);
+      if (lane == lead) atomicMin(b1.csize + key, mn);
+    }
+  }
+}
+
+__global__ void ap_rename_set_kernel(ApBufs b0, ApBufs b1, int32_t V, const int32_t* status) {
+  if (*status) return;
+  for (int64_t i = gtid(); i < V; i += gstride()) {
+    const int32_t r = b0.csize[i];
+    if (r >= 0) b1.Q[b0.tmp[i]] = b1.csize[r];
   }
 }
 
@@ -782,10 +813,11 @@ void articulation_fused(const Launch& L, const CertPlan& p, const CertBufs& cb, 
   if (bev) cudaEventRecord(bev[5], L.stream);
   const int g = grid_of(L, V, bs);
   ap_init_kernel<<<g, bs, 0, L.stream>>>(f, b1, V);
-  ap_rename_kernel<<<g, bs, 0, L.stream>>>(f, b0, b1, V);
+  ap_rename_min_kernel<<<g, bs, 0, L.stream>>>(f, b0, b1, V);
+  ap_rename_set_kernel<<<g, bs, 0, L.stream>>>(b0, b1, V, f.status);
   const ApArgs A1{f.pre, b1.Q, b1.PP, b1.LAST, V, f.status, b1.hooks};
   ap_kept_kernel<<<grid_of(L, fb.ntop, bs), bs, 0, L.stream>>>(A1, u, v, fb.keep, fb.top, fb.ntop, p.E);
-  *L.launches += 3;
+  *L.launches += 4;
   ap_finish(L, f, b1, V, out_points, count_dev);
   if (bev) cudaEventRecord(bev[6], L.stream);
   if (aev) cudaEventRecord(aev[4], L.stream);
