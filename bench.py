@@ -36,8 +36,8 @@ UNIT = "GE/s"
 #   forest pass, M = 1: 9.295 GB read + 7.2 MB written for 1,072,703,284 streamed edges
 #   block pass stream: 9.512 GB read + 11.0 MB written for 1,073,547,340 streamed edges
 TRAFFIC = {"certify_sha": "16e2761306c2235d", "bytes_per_edge": 8.6808}
-AP_TRAFFIC = {"blocks_sha": "cc633b86cfc99c54", "bytes_per_edge": 8.8912}
-FUSED_TRAFFIC = {"blocks_sha": None, "bytes_per_edge": None}
+AP_TRAFFIC = {"blocks_sha": "513fb04f521d72b9", "bytes_per_edge": 8.8934}
+FUSED_TRAFFIC = {"blocks_sha": "513fb04f521d72b9", "bytes_per_edge": 8.6135}
 
 
 def peaks():
