@@ -1030,7 +1030,7 @@ static int64_t ap_warm_edges(const bridges_ctx* c, int64_t E, int32_t V) {
   return std::min<int64_t>(E, 2 * (int64_t)V + 4096);
 }
 
-// The plan of the two-pass block pass (also the fused form's fallback): the whole list as one
+// The plan of the two-pass block pass: the whole list as one
 // partition, its own prefix before the snapshot.
 static CertPlan block_pass_plan(const bridges_ctx* c, int64_t E, int32_t V) {
   CertPlan q = plan_for(c, E, V, 1);
