@@ -10,8 +10,9 @@
 // bridge stage.  Nothing waits on another block, so there is no spin anywhere.
 //
 // The bridge stage is the same Euler-tour / preorder-range test as final.cu, on 16-bit arrays
-// with barriers between phases (list ranking four hops per round), then a rank sort of the
-// packed (a << 12 | b) keys (bitonic above 1,024 bridges).  A graph's fixed cost is its barriers,
+// with barriers between phases (list ranking four hops per round on packed successor / rank
+// words, subtree ranges of more than 32 entries tested by a whole warp), then a rank sort of
+// the packed (a << 12 | b) keys (bitonic above 1,024 bridges).  A graph's fixed cost is its barriers,
 // so the stage keeps their number low, and graphs of up to 2,048 vertices run two per block (and
 // of up to 1,024 four per block): the block splits into 512-thread (then 256-thread) groups with
 // their own share of shared memory and their own named barrier, so that one graph's barrier
@@ -35,15 +36,18 @@ constexpr int kQuarterVmax = kVmax / 4;  // 1024: a quarter-block group's graph
 constexpr uint16_t kNone16 = 0xffff;
 
 constexpr int a16(int x) { return (x + 15) & ~15; }
-// Shared-memory layout for graphs of up to VM vertices (bytes, each region a multiple of 16):
-//   R0  P1 (int32[V]); later aoff + vbase (u16[V+1] each)
+// Shared-memory layout for graphs of up to VM vertices (bytes, each region a multiple of 16),
+// in address order R0, R2, R1, R3, ... so that R0 and R2 (both free while the tour is ranked)
+// form one buffer of 8 VM bytes, as R7 and R8 do:
+//   R0  P1 (int32[V]); later the ranking's second buffer (with R2); later aoff + vbase (u16[V+1] each)
 //   R1  P2 (int32[V]); later root + cur (u16[V+2] each)
 //   R2  F list (u32[V]); later bridge keys (u32[V])
 //   R3  F' list (u32[V])
 //   R4  off (u16[V+2]); later chunk minima / maxima
 //   R5  dst (u16[2V]); later lo (int32[V])
 //   R6  twin (u16[2V]); later hi (int32[V])
-//   R7  succ (u16[2V]); later dflag / dscan (u16[2V+1])
+//   R7  succ (u16[2V]); with R8 the ranking's packed (successor, rank) words; later dflag /
+//       dscan (u16[2V+1])
 //   R8  rnk (u16[2V])
 //   R9  pre, sz, par (u16[V] each)
 template <int VM>
@@ -98,13 +102,13 @@ __device__ Smem carve_smem(char* base) {
   s.aoff = reinterpret_cast<uint16_t*>(c);
   s.vbase = reinterpret_cast<uint16_t*>(c + L::kU16);
   c += L::R0;
+  s.F1 = reinterpret_cast<uint32_t*>(c);
+  s.keys = s.F1;
+  c += L::R2;
   s.P2 = reinterpret_cast<int32_t*>(c);
   s.root = reinterpret_cast<uint16_t*>(c);
   s.cur = reinterpret_cast<uint16_t*>(c + L::kU16);
   c += L::R1;
-  s.F1 = reinterpret_cast<uint32_t*>(c);
-  s.keys = s.F1;
-  c += L::R2;
   s.F2 = reinterpret_cast<uint32_t*>(c);
   c += L::R3;
   s.off = reinterpret_cast<uint16_t*>(c);
@@ -459,51 +463,51 @@ __device__ int32_t s_bridges(const Grp<NT>& G, const Smem& S, int32_t V, int32_t
     S.twin[ib] = (uint16_t)ia;
   }
   G.sync();
-  // Euler-tour successors, cut at each root
+  // Euler-tour successors, cut at each root, packed with the rank so far: (succ | rank << 16)
+  uint32_t* pa = reinterpret_cast<uint32_t*>(S.succ);  // R7 + R8
+  uint32_t* pb = reinterpret_cast<uint32_t*>(S.P1);    // R0 + R2
   for (int i = tid; i < narcs; i += NT) {
     const int32_t y = S.dst[i], t = S.twin[i];
-    uint16_t s;
+    uint32_t s;
     if (t + 1 < S.off[y + 1])
-      s = (uint16_t)(t + 1);
+      s = (uint32_t)(t + 1);
     else
       s = S.root[y] == y ? kNone16 : S.off[y];
-    S.succ[i] = s;
-    S.rnk[i] = s == kNone16 ? 0 : 1;
+    pa[i] = s | (s == kNone16 ? 0u : 1u << 16);
   }
   G.sync();
   // list ranking by pointer jumping, four hops per round (shared-memory loads are cheap, the
-  // block barriers between rounds are not): ceil(log4 n) rounds, double-buffered in the P1 and F
-  // regions (both free now: the roots are known and the adjacency is built)
+  // block barriers between rounds are not): ceil(log4 n) rounds.  Successor and rank share one
+  // 32-bit word, so a hop is one random load; the words are double-buffered in R7 + R8 and
+  // R0 + R2 (both free now: the roots are known and the adjacency is built), and the ranks end
+  // up unpacked in rnk.
   {
     int rounds = 0;
     while ((1 << (2 * rounds)) < max(narcs, 1)) rounds++;
-    uint16_t* sa = S.succ;
-    uint16_t* ra = S.rnk;
-    uint16_t* sb = reinterpret_cast<uint16_t*>(S.P1);
-    uint16_t* rb = reinterpret_cast<uint16_t*>(S.F1);
     for (int r = 0; r < rounds; r++) {
       for (int i = tid; i < narcs; i += NT) {
-        uint16_t s = sa[i], acc = ra[i];
+        uint32_t w = pa[i];
+        uint32_t s = w & 0xffffu, acc = w >> 16;
 #pragma unroll
         for (int h = 0; h < 3 && s != kNone16; h++) {
-          acc = (uint16_t)(acc + ra[s]);
-          s = sa[s];
+          const uint32_t x = pa[s];
+          acc += x >> 16;
+          s = x & 0xffffu;
         }
-        rb[i] = acc;
-        sb[i] = s;
+        pb[i] = s | (acc << 16);
       }
       G.sync();
-      uint16_t* t = sa;
-      sa = sb;
-      sb = t;
-      t = ra;
-      ra = rb;
-      rb = t;
+      uint32_t* t = pa;
+      pa = pb;
+      pb = t;
     }
-    if (ra != S.rnk) {
-      for (int i = tid; i < narcs; i += NT) S.rnk[i] = ra[i];
+    if (pa == reinterpret_cast<uint32_t*>(S.succ)) {  // rnk lies inside R7 + R8: move them first
+      for (int i = tid; i < narcs; i += NT) pb[i] = pa[i];
       G.sync();
+      pa = pb;
     }
+    for (int i = tid; i < narcs; i += NT) S.rnk[i] = (uint16_t)(pa[i] >> 16);
+    G.sync();
   }
   // per root: tour arcs (aoff) and tree vertices (vbase); P1 region is free now
   for (int x = tid; x <= V; x += NT) {
@@ -586,20 +590,46 @@ __device__ int32_t s_bridges(const Grp<NT>& G, const Smem& S, int32_t V, int32_t
   }
   if (tid == 0) *sh = 0;
   G.sync();
-  // test every tree edge (par(y), y); keys reuse the F region
-  for (int y = tid; y < V; y += NT) {
-    if (S.par[y] == kNone16) continue;
-    const int32_t l = S.pre[y], r = min(V, l + max((int32_t)S.sz[y], 1));
-    int32_t mn = INT32_MAX, mx = INT32_MIN;
-    const int32_t cl = (l + 31) / 32, cr = r / 32;
-    if (cl >= cr) {
-      for (int i = l; i < r; i++) mn = min(mn, S.lo[i]), mx = max(mx, S.hi[i]);
-    } else {
-      for (int i = l; i < cl * 32; i++) mn = min(mn, S.lo[i]), mx = max(mx, S.hi[i]);
-      for (int c = cl; c < cr; c++) mn = min(mn, cmin[c]), mx = max(mx, cmax[c]);
-      for (int i = cr * 32; i < r; i++) mn = min(mn, S.lo[i]), mx = max(mx, S.hi[i]);
+  // test every tree edge (par(y), y); keys reuse the F region.  A subtree range of up to 32
+  // entries is scanned by its own lane; a larger one (the vertices near a root) by the whole
+  // warp, one chunk minimum per lane, so no lane scans V / 32 chunks alone (32 measured faster
+  // than 64 and 96 on the batched workload).
+  const int lane = tid & 31;
+  for (int y0 = 0; y0 < V; y0 += NT) {  // group-uniform: every lane of a warp takes part
+    const int y = y0 + tid;
+    const bool live = y < V && S.par[y] != kNone16;
+    int32_t l = 0, r = 0;
+    if (live) {
+      l = S.pre[y];
+      r = min(V, l + max((int32_t)S.sz[y], 1));
     }
-    if (mn >= l && mx < r) {
+    const bool big = live && r - l > 32;
+    int32_t mn = INT32_MAX, mx = INT32_MIN;
+    if (live && !big) {
+      const int32_t cl = (l + 31) / 32, cr = r / 32;
+      if (cl >= cr) {
+        for (int i = l; i < r; i++) mn = min(mn, S.lo[i]), mx = max(mx, S.hi[i]);
+      } else {
+        for (int i = l; i < cl * 32; i++) mn = min(mn, S.lo[i]), mx = max(mx, S.hi[i]);
+        for (int c = cl; c < cr; c++) mn = min(mn, cmin[c]), mx = max(mx, cmax[c]);
+        for (int i = cr * 32; i < r; i++) mn = min(mn, S.lo[i]), mx = max(mx, S.hi[i]);
+      }
+    }
+    unsigned todo = __ballot_sync(kFull, big);
+    while (todo) {
+      const int src = __ffs(todo) - 1;
+      todo &= todo - 1;
+      const int32_t L = __shfl_sync(kFull, l, src), R = __shfl_sync(kFull, r, src);
+      const int32_t cl = (L + 31) / 32, cr = R / 32;  // cl <= cr: the range holds a multiple of 32
+      int32_t a = INT32_MAX, b = INT32_MIN;
+      if (L + lane < cl * 32) a = S.lo[L + lane], b = S.hi[L + lane];
+      if (cr * 32 + lane < R) a = min(a, S.lo[cr * 32 + lane]), b = max(b, S.hi[cr * 32 + lane]);
+      for (int c = cl + lane; c < cr; c += 32) a = min(a, cmin[c]), b = max(b, cmax[c]);
+      a = __reduce_min_sync(kFull, a);
+      b = __reduce_max_sync(kFull, b);
+      if (lane == src) mn = a, mx = b;
+    }
+    if (live && mn >= l && mx < r) {
       const uint32_t a = (uint32_t)min(y, (int)S.par[y]), b = (uint32_t)max(y, (int)S.par[y]);
       const int32_t k = atomicAdd(sh, 1);
       if (k < V) S.keys[k] = (a << 12) | b;
