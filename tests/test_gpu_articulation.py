@@ -140,13 +140,21 @@ def test_with_bridges_async_and_profile(cuda_lib):
     assert out[:na].cpu().numpy().tolist() == ref_ap.tolist()
 
 
-def test_user_workspace(cuda_lib):
+@pytest.mark.parametrize("M,fused", [(2, 0), (1, 1)])
+def test_user_workspace(cuda_lib, M, fused):
+    """A caller's workspace of exactly bridges_articulation_workspace_bytes suffices for either
+    form (the fused one for a single partition); one byte less is refused with ENOMEM."""
     g = graphgen.workload("small")
+    ref = oracle.articulation_points(g.u, g.v, g.V).tolist()
     probe = cuda_lib.Context(device="cuda:0")
-    need = probe.articulation_workspace_bytes(g.E, g.V, 2)
+    need = probe.articulation_workspace_bytes(g.E, g.V, M)
     c = cuda_lib.Context(device="cuda:0", workspace_bytes=need)
-    assert c.articulation_points(dev(g.u), dev(g.v), g.V, 2).cpu().numpy().tolist() == \
-        oracle.articulation_points(g.u, g.v, g.V).tolist()
+    assert c.articulation_points(dev(g.u), dev(g.v), g.V, M).cpu().numpy().tolist() == ref
+    assert c.last_config()["ap_fused"] == fused
+    small = cuda_lib.Context(device="cuda:0", workspace_bytes=need - 1)
+    with pytest.raises(cuda_lib.BridgesError) as ei:
+        small.articulation_points(dev(g.u), dev(g.v), g.V, M)
+    assert ei.value.code == -3
 
 
 def test_host_entry(cuda_lib):
