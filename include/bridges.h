@@ -307,12 +307,11 @@ int64_t bridges_inc_certificate_size(const bridges_inc* inc);
  * biconnected graph at a vertex), so this call merges, for every edge, the classes of the tree
  * edges on its fundamental cycle with a rooted spanning forest T of the bridge path (Sec. 3);
  * the final classes are the blocks (biconnected components) restricted to T, and a vertex is a
- * cut vertex iff its tree edges lie in two or more of them.  On device edges with a single-
- * partition plan that takes a 16-bit label snapshot (opts.ap_fused = 0) both passes share one
- * read of the list: the forest after the certificate's warm-up is rooted early, and edges whose
- * cycle needs the final forest are marked and walked at the end; otherwise (and from host
- * buffers) the bridge path runs first and the list is streamed a second time.  Parallel edges
- * and self-loops are allowed and change nothing.
+ * cut vertex iff its tree edges lie in two or more of them.  With a single-partition plan that
+ * takes a 16-bit label snapshot (opts.ap_fused = 0) both passes share one read of the list: the
+ * forest after the certificate's warm-up is rooted early, and edges whose cycle needs the final
+ * forest are marked and walked at the end; otherwise the bridge path runs first and the list is
+ * streamed a second time.  Parallel edges and self-loops are allowed and change nothing.
  *
  * bridges_articulation_points
  *   edges_u, edges_v, E, V, M : as for bridges_find_ctx (device edges; M for the bridge path).
@@ -327,7 +326,8 @@ int64_t bridges_inc_certificate_size(const bridges_inc* inc);
  * a vertex id outside [0, V), found on the device; EINVAL / ENOMEM on the host).
  *
  * bridges_articulation_points_host: the same from HOST edge buffers (copied to the context's
- *   device staging area -- in chunks overlapped with the first pass, as bridges_find_host does --
+ *   device staging area -- in chunks that the (first or only) pass follows as they land, as
+ *   bridges_find_host does --
  *   or read in place when opts.host_read is set and they are pinned and mapped); the cut
  *   vertices go to out_points_host (host, capacity max(V, 1)).  Synchronous; returns their
  *   number or a negative status.

@@ -261,14 +261,20 @@ int64_t stage_host_edges(bridges_ctx* c, cudaStream_t s, const int32_t* hu, cons
 // while the forest pass (one pass over the list, Sec. 3 phase 0) streams the chunks already on
 // the device.  Single partition with a snapshot only; returns 1 when the plan does not qualify
 // (nothing enqueued: the caller copies everything first).
-int64_t run_path_host(bridges_ctx* c, cudaStream_t s, const int32_t* hu, const int32_t* hv, int32_t* du, int32_t* dv,
-                      int64_t E, int32_t V, int32_t M, int32_t* out, Carved* kout) {
-  Range range("bridges: pipelined host input");
-  const CertPlan p = plan_for(c, E, V, M);
-  if (p.M != 1 || !p.cache) return 1;
-  const int64_t C = std::max<int64_t>({p.warm, ceil_div(E, bridges_ctx::kMaxChunks), (int64_t)16 << 20});
-  const int K = (int)ceil_div(E, C);
-  if (K < 2 || K > bridges_ctx::kMaxChunks) return 1;
+// The chunk schedule of an overlapped host copy for a plan with warm-up prefix `warm`: chunks of
+// C edges (16 M or more, at most kMaxChunks, the first holding the prefix); false when the list
+// is too short to gain from it.
+static bool chunk_plan(int64_t E, int64_t warm, int64_t* C, int* K) {
+  *C = std::max<int64_t>({warm, ceil_div(E, bridges_ctx::kMaxChunks), (int64_t)16 << 20});
+  *K = (int)ceil_div(E, *C);
+  return *K >= 2 && *K <= bridges_ctx::kMaxChunks;
+}
+
+// Issues the chunk copies of (hu, hv) into (du, dv) on the context's copy stream, chunk i's
+// completion recorded in c->chunk_ev[i]; the copies start once the work already on `s` (which
+// may still read the staging) is done.
+static int64_t issue_chunks(bridges_ctx* c, cudaStream_t s, const int32_t* hu, const int32_t* hv, int32_t* du,
+                            int32_t* dv, int64_t E, int64_t C, int K) {
   if (!c->copy_stream) {
     if (cudaStreamCreateWithFlags(&c->copy_stream, cudaStreamNonBlocking) != cudaSuccess ||
         cudaEventCreateWithFlags(&c->entry_ev, cudaEventDisableTiming) != cudaSuccess)
@@ -276,16 +282,6 @@ int64_t run_path_host(bridges_ctx* c, cudaStream_t s, const int32_t* hu, const i
     for (auto& e : c->chunk_ev)
       if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) return cuda_fail(cudaGetLastError());
   }
-  int64_t rc = ensure_ws(c, total_bytes(p), s);
-  if (rc != BRIDGES_OK) return rc;
-  Carved k = carve(c, p);
-  Launch L{s, &c->launches, c->num_sms, c->smem_optin};
-  c->last_cfg[0] = p.M;
-  c->last_cfg[1] = p.f;
-  c->last_cfg[2] = p.G;
-  c->last_cfg[3] = p.block;
-  c->last_cfg[4] = p.warm;
-  // the copies start once the stream's earlier work (which may still read the staging) is done
   cudaStream_t cs = c->copy_stream;
   if (cudaEventRecord(c->entry_ev, s) != cudaSuccess || cudaStreamWaitEvent(cs, c->entry_ev, 0) != cudaSuccess)
     return cuda_fail(cudaGetLastError());
@@ -296,6 +292,28 @@ int64_t run_path_host(bridges_ctx* c, cudaStream_t s, const int32_t* hu, const i
         cudaEventRecord(c->chunk_ev[i], cs) != cudaSuccess)
       return cuda_fail(cudaGetLastError());
   }
+  return BRIDGES_OK;
+}
+
+int64_t run_path_host(bridges_ctx* c, cudaStream_t s, const int32_t* hu, const int32_t* hv, int32_t* du, int32_t* dv,
+                      int64_t E, int32_t V, int32_t M, int32_t* out, Carved* kout) {
+  Range range("bridges: pipelined host input");
+  const CertPlan p = plan_for(c, E, V, M);
+  if (p.M != 1 || !p.cache) return 1;
+  int64_t C = 0;
+  int K = 0;
+  if (!chunk_plan(E, p.warm, &C, &K)) return 1;
+  int64_t rc = ensure_ws(c, total_bytes(p), s);
+  if (rc != BRIDGES_OK) return rc;
+  Carved k = carve(c, p);
+  Launch L{s, &c->launches, c->num_sms, c->smem_optin};
+  c->last_cfg[0] = p.M;
+  c->last_cfg[1] = p.f;
+  c->last_cfg[2] = p.G;
+  c->last_cfg[3] = p.block;
+  c->last_cfg[4] = p.warm;
+  rc = issue_chunks(c, s, hu, hv, du, dv, E, C, K);
+  if (rc != BRIDGES_OK) return rc;
   cudaEvent_t* ev = next_event_slot(c);
   if (ev) cudaEventRecord(ev[7], s);
   cudaMemsetAsync(k.status, 0, sizeof(int32_t), s);
@@ -1056,9 +1074,12 @@ static size_t fused_ws_bytes(const CertPlan& p, int32_t V) {
   return align_up(total_bytes(p), 256) + 2 * align_up(ap_bytes(V), 256) + fused_bytes(p.E);
 }
 
+// The fused form.  With host edges (hu, hv) not yet on the device, (u, v) is their device
+// staging: the copy runs in chunks and the stream follows it chunk by chunk.
 static int64_t articulation_fused_run(bridges_ctx* c, cudaStream_t s, const Launch& L, const CertPlan& p,
                                       const int32_t* u, const int32_t* v, int64_t E, int32_t V, int32_t* out_points,
-                                      int32_t* out_bridges, int64_t* out_counts_device) {
+                                      int32_t* out_bridges, int64_t* out_counts_device, const int32_t* hu,
+                                      const int32_t* hv) {
   Range range("bridges: articulation points, fused");
   const size_t ap_at = align_up(total_bytes(p), 256);
   const size_t apb = align_up(ap_bytes(V), 256);
@@ -1084,9 +1105,25 @@ static int64_t articulation_fused_run(bridges_ctx* c, cudaStream_t s, const Laun
     resolve_ap_timings(c, c->ap_calls - bridges_ctx::kRing + 1);  // the slot's previous call
     aev = c->ap_ev[c->ap_calls % bridges_ctx::kRing];
   }
+  ChunkSchedule chunks{};
+  if (hu) {
+    int64_t C = 0;
+    int K = 0;
+    if (chunk_plan(E, p.warm, &C, &K)) {
+      rc = issue_chunks(c, s, hu, hv, const_cast<int32_t*>(u), const_cast<int32_t*>(v), E, C, K);
+      if (rc) return rc;
+      chunks = ChunkSchedule{c->chunk_ev, C, K};
+    } else if (E > 0 &&
+               (cudaMemcpyAsync(const_cast<int32_t*>(u), hu, sizeof(int32_t) * (size_t)E, cudaMemcpyHostToDevice, s) !=
+                    cudaSuccess ||
+                cudaMemcpyAsync(const_cast<int32_t*>(v), hv, sizeof(int32_t) * (size_t)E, cudaMemcpyHostToDevice, s) !=
+                    cudaSuccess)) {
+      return cuda_fail(cudaGetLastError());
+    }
+  }
   cudaMemsetAsync(k.status, 0, sizeof(int32_t), s);
   cert_init(L, p, k.cert);
-  articulation_fused(L, p, k.cert, k.fin, b0, b1, fb, u, v, out_points, out_bridges, b1.count, bev, aev);
+  articulation_fused(L, p, k.cert, k.fin, b0, b1, fb, u, v, out_points, out_bridges, b1.count, bev, aev, chunks);
   if (bev) c->calls++;
   if (aev) c->ap_calls++;
   if (cudaGetLastError() != cudaSuccess) return BRIDGES_ECUDA;
@@ -1114,8 +1151,8 @@ static int64_t articulation_run(bridges_ctx* c, cudaStream_t s, const int32_t* u
   const CertPlan p0 = plan_for(c, E, V, M);
   const size_t ap_at = align_up(total_bytes(p0), 256);
   Launch L{s, &c->launches, c->num_sms, c->smem_optin};
-  if (!hu && fused_eligible(c, p0, E, V)) return articulation_fused_run(c, s, L, p0, u, v, E, V, out_points, out_bridges,
-                                                                       out_counts_device);
+  if (fused_eligible(c, p0, E, V))
+    return articulation_fused_run(c, s, L, p0, u, v, E, V, out_points, out_bridges, out_counts_device, hu, hv);
   int64_t rc = ensure_ws(c, ap_at + ap_bytes(V), s);
   if (rc) return rc;
   Carved k{};
@@ -1213,7 +1250,7 @@ extern "C" int64_t bridges_articulation_workspace_bytes(const bridges_ctx* c, in
   if (!c || E < 0 || V < 0) return 0;
   const CertPlan p = plan_for(c, E, V, M);
   const size_t two_pass = align_up(total_bytes(p), 256) + ap_bytes(V);
-  if (!fused_eligible(c, p, E, V)) return (int64_t)two_pass;  // (the host form never fuses)
+  if (!fused_eligible(c, p, E, V)) return (int64_t)two_pass;
   return (int64_t)std::max(two_pass, fused_ws_bytes(p, V));
 }
 

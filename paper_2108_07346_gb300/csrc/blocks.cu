@@ -767,9 +767,11 @@ FusedBufs carve_fused(void* base, int64_t E) {
 
 void articulation_fused(const Launch& L, const CertPlan& p, const CertBufs& cb, const FinalBufs& f, const ApBufs& b0,
                         const ApBufs& b1, const FusedBufs& fb, const int32_t* u, const int32_t* v, int32_t* out_points,
-                        int32_t* out_bridges, int64_t* count_dev, cudaEvent_t* bev, cudaEvent_t* aev) {
+                        int32_t* out_bridges, int64_t* count_dev, cudaEvent_t* bev, cudaEvent_t* aev,
+                        const ChunkSchedule& chunks) {
   const int32_t V = p.V;
   int32_t* cnt = cb.cnt;
+  if (chunks.ev) cudaStreamWaitEvent(L.stream, chunks.ev[0], 0);  // the first chunk holds the prefix
   if (bev) cudaEventRecord(bev[0], L.stream);
   if (aev) cudaEventRecord(aev[0], L.stream);
   cudaMemsetAsync(fb.top, 0, sizeof(uint32_t) * (size_t)fb.ntop, L.stream);
@@ -796,12 +798,17 @@ void articulation_fused(const Launch& L, const CertPlan& p, const CertBufs& cb, 
     launch_fused<false, true>(L, a, grid, p.block);
   else
     launch_fused<false, false>(L, a, grid, p.block);
-  a.s = p.warm;
-  a.t = p.E;
-  if (vec)
-    launch_fused<true, true>(L, a, grid, p.block);
-  else
-    launch_fused<true, false>(L, a, grid, p.block);
+  const int K = chunks.ev ? chunks.K : 1;
+  for (int i = 0; i < K; i++) {  // the rest of the list, chunk by chunk behind a host copy
+    if (i > 0) cudaStreamWaitEvent(L.stream, chunks.ev[i], 0);
+    a.s = chunks.ev ? std::max<int64_t>(p.warm, chunks.C * i) : p.warm;
+    a.t = chunks.ev ? std::min<int64_t>(p.E, chunks.C * (i + 1)) : p.E;
+    if (a.t <= a.s) continue;
+    if (vec)
+      launch_fused<true, true>(L, a, grid, p.block);
+    else
+      launch_fused<true, false>(L, a, grid, p.block);
+  }
   if (bev) {
     cudaEventRecord(bev[3], L.stream);
     cudaEventRecord(bev[4], L.stream);

@@ -118,6 +118,14 @@ struct ApBufs {
   int64_t Vpad;
 };
 
+// An overlapped host copy: chunk i (edges [C*i, min(E, C*(i+1))) ) is on the device once ev[i]
+// has fired; ev null: the whole list is there already.
+struct ChunkSchedule {
+  cudaEvent_t* ev;
+  int64_t C;
+  int K;
+};
+
 // Buffers of the fused articulation path (blocks.cu).
 struct FusedBufs {
   uint32_t* keep;  // [nwords] one mark per edge of the list: walked on the final T
@@ -184,12 +192,14 @@ void articulation_stage(const Launch& L, const CertPlan& p, const FinalBufs& f, 
 // combined snapshot, one stream for the certificate and the classes, the final stage (bridges
 // to out_bridges, or scratch when null), the classes renamed onto the final T and the marked
 // edges walked, the points to out_points and their number (or the status) to *count_dev.
-// bev: the bridge path's 8 stage events, aev: the block pass's 5 (either may be null).
+// bev: the bridge path's 8 stage events, aev: the block pass's 5 (either may be null).  With a
+// chunk schedule the warm-up waits for the first chunk and the stream follows the copy.
 size_t fused_bytes(int64_t E);
 FusedBufs carve_fused(void* base, int64_t E);
 void articulation_fused(const Launch& L, const CertPlan& p, const CertBufs& cb, const FinalBufs& f, const ApBufs& b0,
                         const ApBufs& b1, const FusedBufs& fb, const int32_t* u, const int32_t* v, int32_t* out_points,
-                        int32_t* out_bridges, int64_t* count_dev, cudaEvent_t* bev, cudaEvent_t* aev);
+                        int32_t* out_bridges, int64_t* count_dev, cudaEvent_t* bev, cudaEvent_t* aev,
+                        const ChunkSchedule& chunks);
 
 inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
 inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
