@@ -1,7 +1,8 @@
-// stream.cuh -- the streaming loop shared by the certificate's forest pass and the block pass
-// of the articulation-point path: edges are read once with 16-byte loads, tested against a
-// 16-bit label snapshot in shared memory, and only the misses reach a slow path in global
-// memory.  Nothing here is visible through the C ABI.
+// stream.cuh -- the streaming loop shared by the certificate's forest pass, the block pass of
+// the articulation-point path and the fused pass that serves both: edges are read once with
+// 16-byte loads, tested against a snapshot in shared memory (16-bit labels or a bitmap), and
+// only the misses reach a slow path in global memory.  Nothing here is visible through the C
+// ABI.
 #pragma once
 
 #include "common.cuh"
