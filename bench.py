@@ -36,8 +36,8 @@ UNIT = "GE/s"
 #   forest pass, M = 1: 9.295 GB read + 7.2 MB written for 1,072,703,284 streamed edges
 #   block pass stream: 9.512 GB read + 11.0 MB written for 1,073,547,340 streamed edges
 TRAFFIC = {"certify_sha": "7e50d053b42e91d5", "bytes_per_edge": 8.6808}
-AP_TRAFFIC = {"blocks_sha": "941cd7d8c2be5caa", "bytes_per_edge": 8.8934}
-FUSED_TRAFFIC = {"blocks_sha": "941cd7d8c2be5caa", "bytes_per_edge": 8.6135}
+AP_TRAFFIC = {"blocks_sha": "1bb83ede0c0a1fe3", "bytes_per_edge": 8.8607}
+FUSED_TRAFFIC = {"blocks_sha": "1bb83ede0c0a1fe3", "bytes_per_edge": 8.5686}
 
 
 def peaks():
