@@ -303,3 +303,52 @@ def test_fused_enqueue_only(cuda_lib):
         assert c.last_config()["ap_fused"] == 1
         assert out[:n].cpu().numpy().tolist() == ref
         assert br[: 2 * nb].view(nb, 2).cpu().numpy().tolist() == refb
+
+
+def blocks_tree(rng, nblocks, size, deg):
+    """Random blocks (dense random graphs of `size` vertices and deg * size edges) hung on a random
+    tree of cut vertices: block k shares one vertex with an earlier block; plus pendant paths."""
+    us, vs = [], []
+    base = [0]
+    for k in range(nblocks):
+        lo = base[-1]
+        verts = np.arange(lo, lo + size)
+        if k:  # share one vertex with a random earlier block
+            j = int(rng.integers(0, k))
+            verts[0] = int(rng.integers(base[j], base[j] + size))
+        m = deg * size
+        us.append(verts[rng.integers(0, size, m)])
+        vs.append(verts[rng.integers(0, size, m)])
+        base.append(lo + size)
+    V = base[-1]
+    npend = int(rng.integers(0, 50))
+    for p in range(npend):  # a pendant path of 1-5 edges
+        L = int(rng.integers(1, 6))
+        path = np.concatenate([[int(rng.integers(0, V))], np.arange(V, V + L)])
+        us.append(path[:-1])
+        vs.append(path[1:])
+        V += L
+    u, v = np.concatenate(us), np.concatenate(vs)
+    perm = rng.permutation(V)
+    order = rng.permutation(len(u))
+    return perm[u][order].astype(np.int32), perm[v][order].astype(np.int32), V
+
+
+def test_fused_fuzz(cuda_lib):
+    """Seeded fuzz of the fused form on graph families dense enough to take it: trees of dense
+    blocks with pendant paths, and two clusters whose joining edges come late in the list."""
+    c = cuda_lib.Context(device="cuda:0")
+    rng = np.random.default_rng(56)
+    for t in range(24):
+        if t % 3 == 2:
+            n = int(rng.integers(300, 1500))
+            u, v, V = two_clusters(56000 + t, n, int(rng.integers(60, 200)) * n, int(rng.integers(1, 60)),
+                                   tail=bool(rng.integers(0, 2)), pendants=int(rng.integers(0, 20)))
+        else:
+            u, v, V = blocks_tree(rng, int(rng.integers(2, 40)), int(rng.integers(20, 400)), int(rng.integers(30, 120)))
+        ref = oracle.articulation_points(u, v, V).tolist()
+        refb = oracle.bridges(u, v, V).tolist()
+        pts, br = c.articulation_points(dev(u), dev(v), V, 0, with_bridges=True)
+        assert c.last_config()["ap_fused"] == 1, (t, V, len(u))
+        assert pts.cpu().numpy().tolist() == ref, (t, V, len(u))
+        assert br.cpu().numpy().tolist() == refb, (t, V, len(u))
