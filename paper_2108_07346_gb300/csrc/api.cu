@@ -565,7 +565,7 @@ int64_t bridges_rooted_forest(bridges_ctx* c, struct CUstream_st* stream, const 
       cudaMemcpyAsync(c->h_pinned + 1, k.fin.count, sizeof(int64_t), cudaMemcpyDeviceToHost, s) != cudaSuccess)
     return cuda_fail(cudaGetLastError());
   if (cudaStreamSynchronize(s) != cudaSuccess) return cuda_fail(cudaGetLastError());
-  return c->h_pinned[1] < 0 ? c->h_pinned[1] : BRIDGES_OK;
+  return c->h_pinned[1] < 0 ? c->h_pinned[1] : (int64_t)BRIDGES_OK;
 }
 
 int32_t bridges_ctx_stage_ms(const bridges_ctx* c, float* ms, int32_t n) {
