@@ -352,3 +352,28 @@ def test_fused_fuzz(cuda_lib):
         assert c.last_config()["ap_fused"] == 1, (t, V, len(u))
         assert pts.cpu().numpy().tolist() == ref, (t, V, len(u))
         assert br.cpu().numpy().tolist() == refb, (t, V, len(u))
+
+
+@pytest.mark.parametrize("where", ["prefix", "stream"])
+def test_fused_range_error(cuda_lib, where):
+    """An id outside [0, V) in the warm-up prefix or later in the list: ERANGE from the fused
+    form, and the context still answers the next call."""
+    c = cuda_lib.Context(device="cuda:0")
+    u, v, V = two_clusters(57000, 1000, 250000, 20, pendants=4)
+    bad = v.copy()
+    bad[100 if where == "prefix" else len(bad) - 10] = V + 5
+    with pytest.raises(cuda_lib.BridgesError) as ei:
+        c.articulation_points(dev(u), dev(bad), V, 0)
+    assert ei.value.code == -2
+    assert c.articulation_points(dev(u), dev(v), V, 0).cpu().numpy().tolist() == \
+        oracle.articulation_points(u, v, V).tolist()
+    assert c.last_config()["ap_fused"] == 1
+
+
+def test_fused_self_loops_only(cuda_lib):
+    """A list long enough for the fused form that holds only self-loops: no cut vertices."""
+    c = cuda_lib.Context(device="cuda:0")
+    V = 3000
+    a = np.random.default_rng(58).integers(0, V, 200000).astype(np.int32)
+    assert len(c.articulation_points(dev(a), dev(a), V, 0)) == 0
+    assert c.last_config()["ap_fused"] == 1
