@@ -10,8 +10,8 @@
 // bridge stage.  Nothing waits on another block, so there is no spin anywhere.
 //
 // The bridge stage is the same Euler-tour / preorder-range test as final.cu, on 16-bit arrays
-// with barriers between phases (list ranking four hops per round on packed successor / rank
-// words, subtree ranges of more than 32 entries tested by a whole warp), then a rank sort of
+// with barriers between phases (list ranking by a ruling set, subtree ranges of more than 32
+// entries tested by a whole warp), then a rank sort of
 // the packed (a << 12 | b) keys (bitonic above 1,024 bridges).  A graph's fixed cost is its barriers,
 // so the stage keeps their number low, and graphs of up to 2,048 vertices run two per block (and
 // of up to 1,024 four per block): the block splits into 512-thread (then 256-thread) groups with
@@ -34,22 +34,22 @@ constexpr int kHalfVmax = kVmax / 2;  // 2048: a half-block group's graph
 constexpr int kQuarterT = kT / 4;     // threads of a quarter-block group
 constexpr int kQuarterVmax = kVmax / 4;  // 1024: a quarter-block group's graph
 constexpr uint16_t kNone16 = 0xffff;
+constexpr int kRuleGap = 8;  // list ranking: a ruler every kRuleGap arcs (by index)
 
 constexpr int a16(int x) { return (x + 15) & ~15; }
 // Shared-memory layout for graphs of up to VM vertices (bytes, each region a multiple of 16),
 // in address order R0, R2, R1, R3, ... so that R0 and R2 (both free while the tour is ranked)
-// form one buffer of 8 VM bytes, as R7 and R8 do:
-//   R0  P1 (int32[V]); later the ranking's second buffer (with R2); later aoff + vbase (u16[V+1] each)
+// form one buffer of 8 VM bytes:
+//   R0  P1 (int32[V]); later each arc's ruler and place (with R2); later aoff + vbase (u16[V+1] each)
 //   R1  P2 (int32[V]); later root + cur (u16[V+2] each)
 //   R2  F list (u32[V]); later bridge keys (u32[V])
 //   R3  F' list (u32[V])
 //   R4  off (u16[V+2]); later chunk minima / maxima
 //   R5  dst (u16[2V]); later lo (int32[V])
 //   R6  twin (u16[2V]); later hi (int32[V])
-//   R7  succ (u16[2V]); with R8 the ranking's packed (successor, rank) words; later dflag /
-//       dscan (u16[2V+1])
+//   R7  succ (u16[2V]); later dflag / dscan (u16[2V+1])
 //   R8  rnk (u16[2V])
-//   R9  pre, sz, par (u16[V] each)
+//   R9  pre, sz, par (u16[V] each); earlier the rulers' two packed buffers (3 VM / 4 words each)
 template <int VM>
 struct Layout {
   static constexpr int kU16 = a16(2 * (VM + 16));  // a u16[V+2] array
@@ -463,50 +463,81 @@ __device__ int32_t s_bridges(const Grp<NT>& G, const Smem& S, int32_t V, int32_t
     S.twin[ib] = (uint16_t)ia;
   }
   G.sync();
-  // Euler-tour successors, cut at each root, packed with the rank so far: (succ | rank << 16)
-  uint32_t* pa = reinterpret_cast<uint32_t*>(S.succ);  // R7 + R8
-  uint32_t* pb = reinterpret_cast<uint32_t*>(S.P1);    // R0 + R2
+  // Euler-tour successors, cut at each root
+  uint16_t* succ = S.succ;  // R7
   for (int i = tid; i < narcs; i += NT) {
     const int32_t y = S.dst[i], t = S.twin[i];
-    uint32_t s;
+    uint16_t s;
     if (t + 1 < S.off[y + 1])
-      s = (uint32_t)(t + 1);
+      s = (uint16_t)(t + 1);
     else
       s = S.root[y] == y ? kNone16 : S.off[y];
-    pa[i] = s | (s == kNone16 ? 0u : 1u << 16);
+    succ[i] = s;
   }
+  if (tid == 0) *sh = 0;
   G.sync();
-  // list ranking by pointer jumping, four hops per round (shared-memory loads are cheap, the
-  // block barriers between rounds are not): ceil(log4 n) rounds.  Successor and rank share one
-  // 32-bit word, so a hop is one random load; the words are double-buffered in R7 + R8 and
-  // R0 + R2 (both free now: the roots are known and the adjacency is built), and the ranks end
-  // up unpacked in rnk.
+  // List ranking (rank = arcs after the arc in its tour) by a ruling set: every kRuleGap-th arc
+  // by index and the head of every tour (a root's first arc, which no arc points to) start a
+  // sublist that ends before the next ruler; one lane walks each sublist, recording for each arc
+  // its ruler and its place in the sublist; the rulers' own list is ranked by pointer jumping,
+  // four hops per round; then every arc subtracts its place from its ruler's count.  Random
+  // shared-memory loads bound this step, and this reads each arc about three times in all where
+  // pointer jumping over every arc reads it four times a round.
+  //   R0 + R2 (free now): per arc, (ruler | place << 16)
+  //   R9 (pre / sz / par, written later): two buffers of packed (next ruler | arcs << 16) words
+  //   R1's cur half (free now): the first arc of each extra ruler (heads off the kRuleGap grid)
+  // A forest with t trees has at most (2V - 2t) / kRuleGap + t + 1 <= 5V/8 + 1 rulers.
   {
-    int rounds = 0;
-    while ((1 << (2 * rounds)) < max(narcs, 1)) rounds++;
-    for (int r = 0; r < rounds; r++) {
-      for (int i = tid; i < narcs; i += NT) {
-        uint32_t w = pa[i];
-        uint32_t s = w & 0xffffu, acc = w >> 16;
-#pragma unroll
-        for (int h = 0; h < 3 && s != kNone16; h++) {
-          const uint32_t x = pa[s];
-          acc += x >> 16;
-          s = x & 0xffffu;
+    const int32_t nreg = (narcs + kRuleGap - 1) / kRuleGap;
+    for (int x = tid; x < V; x += NT)
+      if (S.root[x] == x && S.off[x + 1] > S.off[x] && S.off[x] % kRuleGap != 0)
+        S.cur[atomicAdd(sh, 1)] = S.off[x];
+    G.sync();
+    const int32_t nrul = nreg + *sh;
+    uint32_t* own = reinterpret_cast<uint32_t*>(S.P1);  // R0 + R2
+    uint32_t* ra = reinterpret_cast<uint32_t*>(S.pre);  // R9: 3 VM / 4 words each
+    uint32_t* rb = ra + 3 * VM / 4;
+    for (int k = tid; k < nrul; k += NT) {
+      uint32_t i = k < nreg ? (uint32_t)(k * kRuleGap) : S.cur[k - nreg];
+      uint32_t place = 0, next = kNone16;
+      for (int32_t step = 0; step < narcs; step++) {  // a tour is a path: a sublist has < narcs arcs
+        own[i] = (uint32_t)k | (place << 16);
+        place++;
+        const uint32_t s = succ[i];
+        if (s == kNone16) break;
+        if (s % kRuleGap == 0) {
+          next = s / kRuleGap;
+          break;
         }
-        pb[i] = s | (acc << 16);
+        i = s;
+      }
+      ra[k] = next | (place << 16);
+    }
+    G.sync();
+    int rounds = 0;
+    while ((1 << (2 * rounds)) < max(nrul, 1)) rounds++;
+    for (int r = 0; r < rounds; r++) {
+      for (int k = tid; k < nrul; k += NT) {
+        const uint32_t w = ra[k];
+        uint32_t nx = w & 0xffffu, acc = w >> 16;
+#pragma unroll
+        for (int h = 0; h < 3 && nx != kNone16; h++) {
+          const uint32_t x = ra[nx];
+          acc += x >> 16;
+          nx = x & 0xffffu;
+        }
+        rb[k] = nx | (acc << 16);
       }
       G.sync();
-      uint32_t* t = pa;
-      pa = pb;
-      pb = t;
+      uint32_t* t = ra;
+      ra = rb;
+      rb = t;
     }
-    if (pa == reinterpret_cast<uint32_t*>(S.succ)) {  // rnk lies inside R7 + R8: move them first
-      for (int i = tid; i < narcs; i += NT) pb[i] = pa[i];
-      G.sync();
-      pa = pb;
+    // ra[k] >> 16: the arcs from ruler k's first arc to the end of its tour
+    for (int i = tid; i < narcs; i += NT) {
+      const uint32_t w = own[i];
+      S.rnk[i] = (uint16_t)((ra[w & 0xffffu] >> 16) - (w >> 16) - 1);
     }
-    for (int i = tid; i < narcs; i += NT) S.rnk[i] = (uint16_t)(pa[i] >> 16);
     G.sync();
   }
   // per root: tour arcs (aoff) and tree vertices (vbase); P1 region is free now
