@@ -195,6 +195,15 @@ def ref_sample_per_step(args, budget_edges):
     return max(1_000_000, min(args.ref_sample, budget_edges // max(1, args.steps)))
 
 
+def workload_name(workload, g):
+    """The workload as both arms name it in `config`."""
+    if workload in ("large", "articulation"):
+        name = (f"large: ER(65536, p={g.spec.p}) core + 256 pendant trees + 128 two-edge vertices, "
+                f"seed {g.spec.seed}")
+        return name if workload == "large" else "articulation points of " + name
+    return workload
+
+
 def run_reference(args, world, rank):
     if rank != 0:
         return
@@ -217,7 +226,7 @@ def run_reference(args, world, rank):
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": tot / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "int32", "data": "synthetic",
-        "config": {"workload": args.workload, "V": g.V, "E": g.E, "sample_edges_per_step": n},
+        "config": {"workload": workload_name(args.workload, g), "V": g.V, "E": g.E, "sample_edges_per_step": n},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
@@ -242,7 +251,7 @@ def run_reference_ap(args, world):
         "impl": "reference", "metric": AP_METRIC, "value": value, "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": tot / args.steps * 1e3, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
-        "config": {"workload": "articulation points of large", "V": g.V, "E": g.E, "sample_edges_per_step": n},
+        "config": {"workload": workload_name("articulation", g), "V": g.V, "E": g.E, "sample_edges_per_step": n},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }), flush=True)
@@ -365,8 +374,7 @@ def run_native(args, world, rank, local):
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "int32", "data": "synthetic",
-            "config": {"workload": f"{args.workload}: ER(65536, p={g.spec.p}) core + 256 pendant trees + 128 "
-                                   f"two-edge vertices, seed {g.spec.seed}" if args.workload == "large" else args.workload,
+            "config": {"workload": workload_name(args.workload, g),
                        "V": V, "E": E, "M": cfg["M"], "fan_in": cfg["fan_in"],
                        "blocks_per_partition": cfg["blocks_per_partition"], "block": cfg["block"],
                        "warm_edges": cfg["warm_edges"], "l2": "inputs (8E bytes) larger than L2; no flush",
@@ -529,8 +537,7 @@ def run_articulation(args, world, rank, local):
             "metric": AP_METRIC, "value": whole_job_rate(E * args.steps, world, ms_total * 1e-3), "unit": UNIT,
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_total / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
-            "config": {"workload": f"articulation points of large: ER(65536, p={g.spec.p}) core + 256 pendant trees "
-                                   f"+ 128 two-edge vertices, seed {g.spec.seed}",
+            "config": {"workload": workload_name("articulation", g),
                        "V": V, "E": E, "M": cfg["M"], "warm_edges": cfg["warm_edges"],
                        "form": "one fused read of the list" if fused else "bridge path, then a second pass",
                        "block_pass_prefix_edges": cfg["ap_warm_edges"], "block_pass_blocks": cfg["ap_blocks"],
