@@ -636,13 +636,23 @@ def run_served(args, world, rank, local):
 
     import paper_2108_07346_gb300 as pb
 
+    import dataclasses
+
     dev = torch.device("cuda", local)
     torch.cuda.set_device(dev)
     rng = np.random.default_rng(4)
+    stress = args.served_variant == "stress"
     pool = []
-    for i in range(args.pool):
-        g = graphgen.generate(graphgen.workload_spec("served", 4, i))
+    # the stress variant: one ER(V, d) core per request (same V and d draws, same pendant paths,
+    # no clusters): about 63 M edges per request on average, up to about 1.3 G; its pool is kept
+    # to 24 graphs to bound host and device memory
+    for i in range(min(args.pool, 24) if stress else args.pool):
+        spec = graphgen.workload_spec("served", 4, i)
+        if stress:
+            spec = dataclasses.replace(spec, n_clusters=1, n_extra=0)
+        g = graphgen.generate(spec)
         pool.append((torch.from_numpy(np.array(g.u)).to(dev), torch.from_numpy(np.array(g.v)).to(dev), g.V, g.E))
+        del g
     N = args.requests
     gaps = rng.exponential(1.0 / args.rate, N)
     arrival = np.cumsum(gaps)
@@ -704,10 +714,15 @@ def run_served(args, world, rank, local):
         "metric": "served graphs/s with p50/p99 latency", "value": N / wall, "unit": "graphs/s", "n_gpus": 1,
         "steps": N, "warmup": len(pool), "ms_per_step": wall / N * 1e3, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "int32", "data": "synthetic",
-        "config": {"workload": f"served: Poisson arrivals {args.rate}/s, {N} requests over {len(pool)} resident graphs, "
-                               "V log-uniform [256, 65536], density U[0.05, 0.6], clusters of 512 with pendant "
-                               "paths and extra inter-cluster edges, seed 4",
-                   "budget_gb": args.budget_gb, "slots": args.slots, "mean_edges": edges / N},
+        "config": {"workload": (f"served{' (stress)' if stress else ''}: Poisson arrivals {args.rate}/s, {N} requests "
+                                f"over {len(pool)} resident graphs, V log-uniform [256, 65536], density U[0.05, 0.6], "
+                                + ("one ER(V, d) core per request with pendant paths" if stress else
+                                   "clusters of 512 with pendant paths and extra inter-cluster edges") + ", seed 4"),
+                   "variant": args.served_variant, "budget_gb": args.budget_gb, "slots": args.slots,
+                   "mean_edges": edges / N,
+                   "pool_edges": {"mean": float(np.mean([p[3] for p in pool])),
+                                  "p99": float(np.percentile([p[3] for p in pool], 99)),
+                                  "max": int(max(p[3] for p in pool))}},
         "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
                        "max": float(lat.max())},
         "served_GE_per_s": edges / wall / 1e9, "offered_per_s": args.rate, "server_stats": st,
@@ -732,6 +747,8 @@ def main():
     ap.add_argument("--slots", type=int, default=8, help="served: concurrent units of work")
     ap.add_argument("--budget-gb", type=float, default=40.0, help="served: device-memory budget")
     ap.add_argument("--plain", type=int, default=1000, help="served: plain calls timed for comparison")
+    ap.add_argument("--served-variant", choices=["primary", "stress"], default="primary",
+                    help="served: clusters of 512 per request (primary) or one ER core per request (stress)")
     ap.add_argument("--graphs", type=int, default=4096, help="graphs of the batched workload")
     ap.add_argument("--density", type=float, default=None, help="override the ER density (profiling)")
     ap.add_argument("--M", type=int, default=0, help="partitions (0: automatic)")
