@@ -612,6 +612,21 @@ def run_batched(args, world, rank, local):
     p1.record(stream)
     torch.cuda.synchronize()
     ms_plain = p0.elapsed_time(p1)
+    cpu = None
+    if not args.no_cpu:
+        # the oracle (Sec. 3 pipeline + Alg. 1 in C) on every graph, one graph per host core: the
+        # C calls release the GIL, so a thread pool runs them in parallel
+        import concurrent.futures
+
+        import oracle
+
+        cores = os.cpu_count() or 1
+        t0 = time.perf_counter()
+        with concurrent.futures.ThreadPoolExecutor(cores) as ex:
+            list(ex.map(lambda g: oracle.bridges(u[off[g]:off[g + 1]], v[off[g]:off[g + 1]], int(Vs[g]), 1), range(G)))
+        dt = time.perf_counter() - t0
+        cpu = {"value": G / dt, "unit": "graphs/s", "cores": cores, "kind": "oracle",
+               "sample": f"all {G} graphs, one per host thread ({dt:.1f} s)"}
     peak, kind = peaks()
     line = {
         "metric": "graphs/s (batched bridge queries)", "value": G / (ms * 1e-3), "unit": "graphs/s", "n_gpus": 1,
@@ -624,6 +639,7 @@ def run_batched(args, world, rank, local):
                      "frac": 8.0 * E / (ms * 1e-3) / 1e9 / peak, "peak_kind": kind},
         "plain_per_graph": {"value": G / (ms_plain * 1e-3), "unit": "graphs/s", "ms_total": ms_plain},
         "speedup_vs_plain": ms_plain / ms,
+        "cpu_baseline": cpu,
     }
     print(json.dumps(line), flush=True)
 
