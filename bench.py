@@ -24,6 +24,10 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 import numpy as np  # noqa: E402
+import warnings  # noqa: E402
+
+# the generator's arrays are read-only views of C memory; torch only reads them here
+warnings.filterwarnings("ignore", message="The given NumPy array is not writable")
 
 import graphgen  # noqa: E402
 

@@ -188,8 +188,8 @@ def test_from_forest_matches_oracle(ctx):
 def test_find_host_and_async(ctx, cuda_lib):
     g = graphgen.workload("small")
     ref = oracle.bridges(g.u, g.v, g.V, 16)
-    hu = torch.from_numpy(np.ascontiguousarray(g.u)).pin_memory()
-    hv = torch.from_numpy(np.ascontiguousarray(g.v)).pin_memory()
+    hu = torch.from_numpy(np.array(g.u)).pin_memory()
+    hv = torch.from_numpy(np.array(g.v)).pin_memory()
     assert ctx.find_host(hu, hv, g.V, 8).numpy().tolist() == ref.tolist()
     du, dv = dev_edges(g.u, g.v)
     cnt = torch.zeros(1, dtype=torch.int64, device="cuda:0")
