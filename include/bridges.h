@@ -73,9 +73,10 @@ typedef struct bridges_opts {
                             (snapshot right after the certificate's own edges) */
   int32_t warm_block;    /* threads per block of the forest pass's warm-up launch (the prefix certified
                             through the union-finds before the snapshot); 0: auto */
-  int32_t ap_fused;      /* bridges_articulation_points on device edges: 0 = auto (one read of the list
-                            for the certificate and the block pass when the plan is one partition
-                            with a 16-bit label snapshot), < 0 = always the two-pass form */
+  int32_t ap_fused;      /* bridges_articulation_points: 0 = auto (one read of the list for the
+                            certificate and the block pass when the plan is one partition with a
+                            16-bit label snapshot and the larger workspace of that form fits the
+                            context's budget or workspace), < 0 = always the two-pass form */
   int32_t reserved[3];
 } bridges_opts;
 
@@ -331,8 +332,10 @@ int64_t bridges_inc_certificate_size(const bridges_inc* inc);
  *   or read in place when opts.host_read is set and they are pinned and mapped); the cut
  *   vertices go to out_points_host (host, capacity max(V, 1)).  Synchronous; returns their
  *   number or a negative status.
- * bridges_articulation_workspace_bytes: workspace a context needs for this call (contexts made
- *   with bridges_ctx_create_ws must be at least this large).
+ * bridges_articulation_workspace_bytes: workspace a context needs for this call in the form it
+ *   would take (the fused form's, when it applies).  A context made with bridges_ctx_create_ws
+ *   (or limited by a budget) that holds less runs the two-pass form if that fits, else the call
+ *   returns BRIDGES_ENOMEM.
  * bridges_ctx_ap_stage_ms: on a profiling context, the stage times of the last call's block
  *   pass in ms: [0] warm-up (certificate edges + prefix), [1] snapshot, [2] stream,
  *   [3] marking and compaction, [4] the whole block pass; waits for them; returns how many were

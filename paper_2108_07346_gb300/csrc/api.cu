@@ -64,6 +64,14 @@ Carved carve(bridges_ctx* c, const CertPlan& p) {
 
 // Makes the workspace at least `need` bytes.  Waits for the context's previous work before
 // freeing an old, smaller workspace.
+// Whether ensure_ws(c, need) could succeed without exceeding a limit the caller set (a
+// workspace of its own, or a memory budget).
+bool ws_fits(const bridges_ctx* c, size_t need) {
+  if (need <= c->ws_bytes) return true;
+  if (c->user_ws) return false;
+  return !c->budget || need + c->stage_bytes <= c->budget;
+}
+
 int64_t ensure_ws(bridges_ctx* c, size_t need, cudaStream_t s) {
   if (need <= c->ws_bytes) return BRIDGES_OK;
   if (c->user_ws) return BRIDGES_ENOMEM;
@@ -1151,7 +1159,8 @@ static int64_t articulation_run(bridges_ctx* c, cudaStream_t s, const int32_t* u
   const CertPlan p0 = plan_for(c, E, V, M);
   const size_t ap_at = align_up(total_bytes(p0), 256);
   Launch L{s, &c->launches, c->num_sms, c->smem_optin};
-  if (fused_eligible(c, p0, E, V))
+  // the fused form when it applies and its larger workspace fits the caller's limits, else two passes
+  if (fused_eligible(c, p0, E, V) && ws_fits(c, fused_ws_bytes(p0, V)))
     return articulation_fused_run(c, s, L, p0, u, v, E, V, out_points, out_bridges, out_counts_device, hu, hv);
   int64_t rc = ensure_ws(c, ap_at + ap_bytes(V), s);
   if (rc) return rc;

@@ -142,19 +142,38 @@ def test_with_bridges_async_and_profile(cuda_lib):
 
 @pytest.mark.parametrize("M,fused", [(2, 0), (1, 1)])
 def test_user_workspace(cuda_lib, M, fused):
-    """A caller's workspace of exactly bridges_articulation_workspace_bytes suffices for either
-    form (the fused one for a single partition); one byte less is refused with ENOMEM."""
+    """A caller's workspace of exactly bridges_articulation_workspace_bytes suffices for the form
+    the call takes (the fused one for a single partition).  With less, a single-partition call
+    falls back to the two-pass form while that fits; below the two-pass need it is ENOMEM."""
     g = graphgen.workload("small")
     ref = oracle.articulation_points(g.u, g.v, g.V).tolist()
-    probe = cuda_lib.Context(device="cuda:0")
-    need = probe.articulation_workspace_bytes(g.E, g.V, M)
+    need = cuda_lib.Context(device="cuda:0").articulation_workspace_bytes(g.E, g.V, M)
     c = cuda_lib.Context(device="cuda:0", workspace_bytes=need)
     assert c.articulation_points(dev(g.u), dev(g.v), g.V, M).cpu().numpy().tolist() == ref
     assert c.last_config()["ap_fused"] == fused
-    small = cuda_lib.Context(device="cuda:0", workspace_bytes=need - 1)
+    two_pass = cuda_lib.Context(device="cuda:0", ap_fused=-1).articulation_workspace_bytes(g.E, g.V, M)
+    if fused:
+        assert two_pass < need
+        c = cuda_lib.Context(device="cuda:0", workspace_bytes=need - 1)
+        assert c.articulation_points(dev(g.u), dev(g.v), g.V, M).cpu().numpy().tolist() == ref
+        assert c.last_config()["ap_fused"] == 0
+    small = cuda_lib.Context(device="cuda:0", workspace_bytes=two_pass - 1)
     with pytest.raises(cuda_lib.BridgesError) as ei:
         small.articulation_points(dev(g.u), dev(g.v), g.V, M)
     assert ei.value.code == -3
+
+
+def test_budget_falls_back_to_two_passes(cuda_lib):
+    """A memory budget that holds the two-pass workspace but not the fused one: the call runs
+    two passes (same result) instead of failing."""
+    g = graphgen.workload("small")
+    ref = oracle.articulation_points(g.u, g.v, g.V).tolist()
+    two_pass = cuda_lib.Context(device="cuda:0", ap_fused=-1).articulation_workspace_bytes(g.E, g.V, 1)
+    fused = cuda_lib.Context(device="cuda:0").articulation_workspace_bytes(g.E, g.V, 1)
+    assert two_pass < fused
+    c = cuda_lib.Context(device="cuda:0", mem_budget=(two_pass + fused) // 2)
+    assert c.articulation_points(dev(g.u), dev(g.v), g.V, 1).cpu().numpy().tolist() == ref
+    assert c.last_config()["ap_fused"] == 0
 
 
 def test_host_entry(cuda_lib):
