@@ -10,7 +10,7 @@ pytestmark = pytest.mark.gpu
 
 
 def dev(a):
-    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.int32)).cuda()
+    return torch.from_numpy(np.array(a, dtype=np.int32)).cuda()
 
 
 def mixed_graphs():

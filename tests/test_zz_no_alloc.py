@@ -26,7 +26,7 @@ def pb():
 
 
 def _dev(a):
-    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.int32)).to("cuda:0")
+    return torch.from_numpy(np.array(a, dtype=np.int32)).to("cuda:0")
 
 
 def _noalloc_abi(pb, u, v, V, M):
