@@ -148,7 +148,9 @@ int64_t bridges_find_host(bridges_ctx* ctx, struct CUstream_st* stream, const in
  * (graphs with many edges are split into partitions whose certificates are merged by the block
  * that finishes last); the launch is a CUDA graph cached per capacity.  Larger graphs follow
  * through the single-graph path on the same stream.  Enqueue-only: returns BRIDGES_OK or a
- * host-detected error; synchronise the stream before reading the outputs.
+ * host-detected error; synchronise the stream before reading the outputs.  The call waits on the
+ * host only for the context's batch before last, and a batch starts on the device after the
+ * context's previous batch has finished, whichever stream that one ran on.
  */
 int64_t bridges_find_batched(bridges_ctx* ctx, struct CUstream_st* stream, const int32_t* edges_u,
                              const int32_t* edges_v, const int64_t* edge_off_host, const int32_t* V_host, int32_t G,

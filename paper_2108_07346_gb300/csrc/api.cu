@@ -391,10 +391,12 @@ void bridges_ctx_destroy(bridges_ctx* c) {
   if (!c->user_ws && c->ws) cudaFree(c->ws);
   if (c->stage) cudaFree(c->stage);
   if (c->h_pinned) cudaFreeHost(c->h_pinned);
-  if (c->b_exec) cudaGraphExecDestroy(c->b_exec);
+  for (int k = 0; k < 2; k++) {
+    if (c->b_exec[k]) cudaGraphExecDestroy(c->b_exec[k]);
+    if (c->bstage[k]) cudaFreeHost(c->bstage[k]);
+    if (c->b_done_ev[k]) cudaEventDestroy(c->b_done_ev[k]);
+  }
   if (c->bws) cudaFree(c->bws);
-  if (c->bstage) cudaFreeHost(c->bstage);
-  if (c->b_done_ev) cudaEventDestroy(c->b_done_ev);
   if (c->copy_stream) {
     cudaStreamDestroy(c->copy_stream);
     cudaEventDestroy(c->entry_ev);
@@ -662,51 +664,64 @@ int64_t next_pow2(int64_t x) {
   return p;
 }
 
-// (Re)creates the batched buffers and the captured CUDA graph for these capacities.
+// (Re)creates the batched buffers and the two captured CUDA graphs for these capacities.
 int64_t ensure_batched(bridges_ctx* c, cudaStream_t s, int64_t ntasks, int64_t G, int64_t slots) {
-  if (ntasks <= c->b_task_cap && G <= c->b_graph_cap && slots <= c->b_slot_cap && c->b_exec) return BRIDGES_OK;
+  if (ntasks <= c->b_task_cap && G <= c->b_graph_cap && slots <= c->b_slot_cap && c->b_exec[0] && c->b_exec[1])
+    return BRIDGES_OK;
   const int64_t tcap = next_pow2(std::max<int64_t>(ntasks, 64)), gcap = next_pow2(std::max<int64_t>(G, 64));
   const int64_t scap = next_pow2(std::max<int64_t>(slots, 1024));
   const BLayout L = blayout(tcap, gcap, scap);
   if (c->user_ws) return BRIDGES_ENOMEM;
   if (c->budget && L.total + c->ws_bytes + c->stage_bytes > c->budget) return BRIDGES_ENOMEM;
-  if (c->b_done_ev) cudaEventSynchronize(c->b_done_ev);
+  for (int k = 0; k < 2; k++)
+    if (c->b_done_ev[k]) cudaEventSynchronize(c->b_done_ev[k]);
   cudaStreamSynchronize(s);
-  if (c->b_exec) cudaGraphExecDestroy(c->b_exec);
-  c->b_exec = nullptr;
+  for (int k = 0; k < 2; k++) {
+    if (c->b_exec[k]) cudaGraphExecDestroy(c->b_exec[k]);
+    if (c->bstage[k]) cudaFreeHost(c->bstage[k]);
+    c->b_exec[k] = nullptr;
+    c->bstage[k] = nullptr;
+  }
   if (c->bws) cudaFree(c->bws);
-  if (c->bstage) cudaFreeHost(c->bstage);
   c->bws = nullptr;
-  c->bstage = nullptr;
-  if (cudaMalloc(&c->bws, L.total) != cudaSuccess || cudaMallocHost(&c->bstage, L.s_total) != cudaSuccess) {
+  if (cudaMalloc(&c->bws, L.total) != cudaSuccess || cudaMallocHost(&c->bstage[0], L.s_total) != cudaSuccess ||
+      cudaMallocHost(&c->bstage[1], L.s_total) != cudaSuccess) {
     cudaGetLastError();
     return BRIDGES_ENOMEM;
   }
-  if (!c->b_done_ev && cudaEventCreateWithFlags(&c->b_done_ev, cudaEventDisableTiming) != cudaSuccess)
-    return cuda_fail(cudaGetLastError());
+  for (int k = 0; k < 2; k++)
+    if (!c->b_done_ev[k] && cudaEventCreateWithFlags(&c->b_done_ev[k], cudaEventDisableTiming) != cudaSuccess)
+      return cuda_fail(cudaGetLastError());
   c->b_task_cap = tcap;
   c->b_graph_cap = gcap;
   c->b_slot_cap = scap;
   c->bws_bytes = L.total;
   c->bstage_bytes = L.s_total;
-  // capture: reset counters, upload descriptors from the pinned staging, run the kernel
+  c->b_next = 0;
+  // capture, once per staging copy: reset counters, upload descriptors from that copy, run the
+  // kernel
   char* d = static_cast<char*>(c->bws);
-  char* h = static_cast<char*>(c->bstage);
   cudaStream_t cs;
   if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess) return cuda_fail(cudaGetLastError());
-  cudaGraph_t graph;
-  bool ok = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
-  ok = ok && cudaMemsetAsync(d + L.queue, 0, 256, cs) == cudaSuccess;
-  ok = ok && cudaMemsetAsync(d + L.done, 0, L.slots - L.done, cs) == cudaSuccess;  // done and gerr
-  ok = ok && cudaMemcpyAsync(d, h, L.s_total, cudaMemcpyHostToDevice, cs) == cudaSuccess;  // args, ntasks, tasks
-  ok = ok && batched_launch(cs, reinterpret_cast<const BatchArgs*>(d + L.args), c->num_sms);
-  ok = (cudaStreamEndCapture(cs, &graph) == cudaSuccess) && ok;
-  if (ok) ok = cudaGraphInstantiate(&c->b_exec, graph, 0) == cudaSuccess;
-  cudaGraphDestroy(graph);
+  bool ok = true;
+  for (int k = 0; k < 2 && ok; k++) {
+    cudaGraph_t graph;
+    ok = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+    ok = ok && cudaMemsetAsync(d + L.queue, 0, 256, cs) == cudaSuccess;
+    ok = ok && cudaMemsetAsync(d + L.done, 0, L.slots - L.done, cs) == cudaSuccess;  // done and gerr
+    ok = ok && cudaMemcpyAsync(d, c->bstage[k], L.s_total, cudaMemcpyHostToDevice, cs) == cudaSuccess;
+    ok = ok && batched_launch(cs, reinterpret_cast<const BatchArgs*>(d + L.args), c->num_sms);
+    ok = (cudaStreamEndCapture(cs, &graph) == cudaSuccess) && ok;
+    if (ok) ok = cudaGraphInstantiate(&c->b_exec[k], graph, 0) == cudaSuccess;
+    cudaGraphDestroy(graph);
+  }
   cudaStreamDestroy(cs);
   if (!ok) {
     cudaGetLastError();
-    c->b_exec = nullptr;
+    for (int k = 0; k < 2; k++) {
+      if (c->b_exec[k]) cudaGraphExecDestroy(c->b_exec[k]);
+      c->b_exec[k] = nullptr;
+    }
     return BRIDGES_ECUDA;
   }
   return BRIDGES_OK;
@@ -752,11 +767,15 @@ int64_t launch_batch_tasks(bridges_ctx* c, cudaStream_t s, const std::vector<Bat
   Range range("bridges: batched launch");
   int64_t rc = ensure_batched(c, s, (int64_t)tasks.size(), G, slot_words);
   if (rc) return rc;
-  // the staging area may still feed the previous batch's upload
-  cudaEventSynchronize(c->b_done_ev);
+  // Two staging copies in turn: the host waits only for the batch before last (the last one to
+  // read this copy), so it fills the next batch while the previous one runs.  The device area is
+  // shared, so this batch also waits on the device for the previous one, whatever its stream.
+  const int k = c->b_next;
+  c->b_next ^= 1;
+  cudaEventSynchronize(c->b_done_ev[k]);
   const BLayout L = blayout(c->b_task_cap, c->b_graph_cap, c->b_slot_cap);
   char* d = static_cast<char*>(c->bws);
-  char* h = static_cast<char*>(c->bstage);
+  char* h = static_cast<char*>(c->bstage[k]);
   BatchArgs A{};
   A.tasks = reinterpret_cast<const BatchTask*>(d + L.tasks);
   A.d_ntasks = reinterpret_cast<const int32_t*>(d + L.ntasks);
@@ -784,8 +803,9 @@ int64_t launch_batch_tasks(bridges_ctx* c, cudaStream_t s, const std::vector<Bat
   const int32_t nt = (int32_t)tasks.size();
   std::memcpy(h + L.s_ntasks, &nt, sizeof(nt));
   std::memcpy(h + L.s_tasks, tasks.data(), sizeof(BatchTask) * tasks.size());
-  if (cudaGraphLaunch(c->b_exec, s) != cudaSuccess) return cuda_fail(cudaGetLastError());
-  if (cudaEventRecord(c->b_done_ev, s) != cudaSuccess) return cuda_fail(cudaGetLastError());
+  if (cudaStreamWaitEvent(s, c->b_done_ev[k ^ 1], 0) != cudaSuccess) return cuda_fail(cudaGetLastError());
+  if (cudaGraphLaunch(c->b_exec[k], s) != cudaSuccess) return cuda_fail(cudaGetLastError());
+  if (cudaEventRecord(c->b_done_ev[k], s) != cudaSuccess) return cuda_fail(cudaGetLastError());
   c->launches += 1;
   return BRIDGES_OK;
 }

@@ -38,15 +38,16 @@ struct bridges_ctx {
   int64_t ap_calls = 0;
   int64_t ap_resolved = 0;
   float ap_ms[kRing][5]{};
-  // batched path: device descriptors, pinned staging and a CUDA graph per capacity
+  // batched path: device descriptors; two pinned staging copies used in turn, each with the CUDA
+  // graph that uploads from it and the event of the last batch that read it
   void* bws = nullptr;          // device: BatchArgs | ntasks | queue | tasks[cap] | done[gcap] | gerr[gcap] | slots
   size_t bws_bytes = 0;
-  void* bstage = nullptr;        // pinned: BatchArgs | ntasks | tasks[cap]
+  void* bstage[2]{};             // pinned: BatchArgs | ntasks | tasks[cap]
   size_t bstage_bytes = 0;
   int64_t b_task_cap = 0, b_graph_cap = 0, b_slot_cap = 0;
-  cudaGraphExec_t b_exec = nullptr;
-  cudaStream_t b_exec_stream = nullptr;
-  cudaEvent_t b_done_ev = nullptr;
+  cudaGraphExec_t b_exec[2]{};
+  cudaEvent_t b_done_ev[2]{};
+  int b_next = 0;                // the staging copy the next batch fills
   int64_t b_split_edges = 0;     // partition graphs with more edges than this (0: automatic)
   // pipelined host input: a copy stream and one event per chunk copied
   static constexpr int kMaxChunks = 64;

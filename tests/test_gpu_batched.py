@@ -127,3 +127,33 @@ def test_rmat_graphs_all_group_sizes(ctx):
     res = run_batch(ctx, graphs)
     for (u, v, V), got in zip(graphs, res):
         assert got.tolist() == oracle.dfs_bridges(u, v, V).tolist()
+
+
+def test_back_to_back_batches_on_two_streams(ctx):
+    """Batches enqueued without a host wait, on one stream and alternating between two: each
+    batch's descriptors are uploaded while the one before may still run (two staging copies in
+    turn, the shared device area ordered by an event), and every graph of every batch must still
+    come out right."""
+    rng = np.random.default_rng(44)
+    batches = []
+    for b in range(6):
+        graphs = []
+        for t in range(24):
+            V = int(rng.choice([int(rng.integers(2, 300)), int(rng.integers(1100, 2048)), int(rng.integers(2100, 4096))]))
+            u, v = graphgen.random_multigraph(7000 + 100 * b + t, V, int(rng.integers(V, 6 * V)))
+            graphs.append((u, v, V))
+        u, v, off, Vs = concat(graphs)
+        batches.append((graphs, torch.from_numpy(u).cuda(), torch.from_numpy(v).cuda(), off, Vs))
+    torch.cuda.synchronize()
+    streams = [torch.cuda.Stream(), torch.cuda.Stream()]
+    results = []
+    for b, (graphs, du, dv, off, Vs) in enumerate(batches):
+        s = streams[[0, 1, 0, 0, 1, 1][b]]
+        results.append(ctx.find_batched(du, dv, off, Vs, stream=s, sync=False))
+    torch.cuda.synchronize()
+    for (graphs, *_), (out, counts, out_off) in zip(batches, results):
+        out = out.cpu().numpy()
+        counts = counts.cpu().numpy()
+        for g, (u, v, V) in enumerate(graphs):
+            n = int(counts[g])
+            assert out[out_off[g]: out_off[g] + 2 * n].reshape(n, 2).tolist() == oracle.dfs_bridges(u, v, V).tolist()
