@@ -10,7 +10,8 @@
 A plausible mistake in the oracle fails at least one of these: a dropped F' (Alg. 2) changes
 bridges on any cycle; a vertex-based parent skip (Alg. 1) makes a doubled edge a bridge; a
 ">=" for ">" in the low/disc test makes cycle edges bridges; a lost merge partner (Sec. 3)
-changes components; a wrong partition bound loses edges.
+changes components; a wrong partition bound loses edges.  test_oracle_mutants builds these
+mistakes and others into the oracle's C source and checks that a pin here rejects each one.
 """
 import itertools
 
