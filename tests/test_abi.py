@@ -67,3 +67,36 @@ def test_missing_library_fails_loudly(monkeypatch, tmp_path):
     monkeypatch.setattr(pb, "_lib", None)
     with pytest.raises(RuntimeError, match="libbridges.so not found"):
         pb.load(build_if_missing=False)
+
+
+# Entry points that report "nothing" as 0 rather than as an error status.
+_ZERO_WHEN_EMPTY = {"bridges_ctx_ap_stage_ms", "bridges_ctx_ap_stage_ms_history", "bridges_ctx_last_config",
+                    "bridges_ctx_launches", "bridges_ctx_stage_ms", "bridges_ctx_stage_ms_history",
+                    "bridges_server_stats", "bridges_workspace_bytes", "bridges_articulation_workspace_bytes"}
+# Creation calls, the status table, and the two calls without a handle, for which all-zero
+# arguments form a valid request rather than an error.
+_NOT_HANDLE_CALLS = {"bridges_ctx_create", "bridges_ctx_create_ws", "bridges_server_create", "bridges_inc_create",
+                     "bridges_status_string", "bridges_find", "bridges_find_noalloc"}
+
+
+def test_null_handles_are_rejected_without_touching_a_gpu():
+    """Every call on a context, server or incremental handle checks the handle before anything
+    else: a null handle (all other arguments zero) gives BRIDGES_EINVAL, or 0 where the call
+    reports a count or a size, and the destroy calls do nothing."""
+    import paper_2108_07346_gb300 as pb
+
+    lib = pb.load()
+    checked = 0
+    for name, (restype, argtypes) in sorted(pb._SIGS.items()):
+        if name in _NOT_HANDLE_CALLS:
+            continue
+        args = [None if t is ctypes.c_void_p or hasattr(t, "contents") else 0 for t in argtypes]
+        got = getattr(lib, name)(*args)
+        if restype is None:
+            assert got is None, name
+        elif name in _ZERO_WHEN_EMPTY:
+            assert got == 0, name
+        else:
+            assert got == -1, (name, got)
+        checked += 1
+    assert checked >= 30
