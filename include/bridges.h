@@ -77,7 +77,13 @@ typedef struct bridges_opts {
                             certificate and the block pass when the plan is one partition with a
                             16-bit label snapshot and the larger workspace of that form fits the
                             context's budget or workspace), < 0 = always the two-pass form */
-  int32_t reserved[3];
+  int32_t test_barrier_polls; /* for tests of the failure path; 0 in normal use.  > 0: a grid
+                                 barrier of the final stage gives up after this many polls
+                                 (~100 ns apart; default 2^22) with BRIDGES_ETIMEDOUT */
+  int32_t test_hold_polls;    /* for tests of the failure path; 0 in normal use.  > 0: the final
+                                 stage's last block sleeps this many ~100 ns polls before its first
+                                 barrier, so that a short barrier wait above gives up */
+  int32_t reserved[1];
 } bridges_opts;
 
 typedef struct bridges_ctx bridges_ctx;
@@ -250,9 +256,10 @@ int64_t bridges_rooted_forest(bridges_ctx* ctx, struct CUstream_st* stream, cons
  * block in the driver, or the process reserves all device memory up front.  This entry point
  * allocates nothing: every intermediate buffer lives in one fixed 8 MiB array of device memory
  * that is part of the library itself (each GPU that loads the library holds it until the process
- * exits).  That bounds the graph: about 24,000 vertices with M <= 2, or 16,384 vertices with
- * M <= 8 (the edge count is not limited by the array).  Larger graphs return BRIDGES_ENOMEM
- * without running anything.
+ * exits).  That bounds the graph: a call needs about 1.07 MB plus (150 + 30 M) bytes per vertex,
+ * so V may be at most 41,023 with M = 1 (M <= 0 picks 1), 35,135 with M = 2, 27,264 with M = 4
+ * and 18,848 with M = 8.  The edge count is not limited by the array.  Larger graphs return
+ * BRIDGES_ENOMEM without running anything.
  *
  *   edges_u, edges_v, E, V, M, out_bridges, out_count_device : as for bridges_find_ctx, on the
  *       current device; `stream` is the launch stream.  Synchronous (returns the count) when

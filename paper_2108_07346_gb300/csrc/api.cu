@@ -25,7 +25,9 @@ using namespace bridges;
 
 namespace {
 
-constexpr size_t kMiscBytes = 1024;  // status word, device counts of bridges_from_forest
+constexpr size_t kMiscBytes = 1024;  // status word, device counts of bridges_from_forest, spare output
+constexpr size_t kSpareAt = 512;     // the spare output slot: where a call that has no pairs or points
+                                     // to write (V <= 1, null output) points the stages
 
 // NVTX range for the duration of a host scope (what the host enqueues; a profiler correlates the
 // launches inside it).  Header-only NVTX: without an attached tool a push / pop is a no-op.
@@ -39,9 +41,19 @@ struct Range {
 struct Carved {
   int32_t* status;
   int32_t* counts;  // [2]
+  int32_t* spare;   // [2] device scratch for outputs the caller did not ask for
   CertBufs cert;
   FinalBufs fin;
 };
+
+// The launch context of a call on c: its stream, its launch counter and the final stage's test
+// knobs from the options (zero in normal use).
+Launch launch_for(bridges_ctx* c, cudaStream_t s) {
+  Launch L{s, &c->launches, c->num_sms, c->smem_optin};
+  L.bar_polls = c->opts.test_barrier_polls > 0 ? (unsigned)c->opts.test_barrier_polls : 0u;
+  L.hold_polls = c->opts.test_hold_polls > 0 ? c->opts.test_hold_polls : 0;
+  return L;
+}
 
 int64_t cuda_fail(cudaError_t e) {
   (void)e;
@@ -56,6 +68,7 @@ Carved carve(bridges_ctx* c, const CertPlan& p) {
   char* base = static_cast<char*>(c->ws);
   k.status = reinterpret_cast<int32_t*>(base);
   k.counts = reinterpret_cast<int32_t*>(base + 256);
+  k.spare = reinterpret_cast<int32_t*>(base + kSpareAt);
   k.cert = carve_cert(base + kMiscBytes, p);
   k.cert.status = k.status;
   k.fin = carve_final(base + kMiscBytes + align_up(cert_bytes(p), 256), p.V, k.status);
@@ -159,15 +172,17 @@ int init_ctx(bridges_ctx* c, int device, const bridges_opts* opts) {
   return 0;
 }
 
-// The whole path on device-resident edges.  Leaves the count on the device (fin.count).
+// The whole path on device-resident edges.  Leaves the count on the device (fin.count).  With
+// with_final false it stops after the certificate; otherwise the sorted pairs go to out, or to
+// the final stage's own dscan array (free by the time it sorts) when out is null.
 int64_t run_path(bridges_ctx* c, cudaStream_t s, const int32_t* u, const int32_t* v, int64_t E, int32_t V, int32_t M,
-                 int32_t* out, Carved* kout, CertPlan* pout) {
+                 int32_t* out, Carved* kout, CertPlan* pout, bool with_final = true) {
   Range range("bridges: certificate + final stage");
   CertPlan p = plan_for(c, E, V, M);
   int64_t rc = ensure_ws(c, total_bytes(p), s);
   if (rc != BRIDGES_OK) return rc;
   Carved k = carve(c, p);
-  Launch L{s, &c->launches, c->num_sms, c->smem_optin};
+  Launch L = launch_for(c, s);
   c->last_cfg[0] = p.M;
   c->last_cfg[1] = p.f;
   c->last_cfg[2] = p.G;
@@ -182,10 +197,10 @@ int64_t run_path(bridges_ctx* c, cudaStream_t s, const int32_t* u, const int32_t
     for (int i = 0; i < 4; i++) cudaEventRecord(ev[i], s);
   cert_merge(L, p, k.cert);
   if (ev) cudaEventRecord(ev[4], s);
-  if (out) {
+  if (with_final) {
     // job 0 holds the final certificate: F (tree) and F' (extra); its UF1 roots the trees
     final_stage(L, k.fin, V, k.cert.f1u, k.cert.f1v, k.cert.cnt + 0, V, k.cert.f2u, k.cert.f2v, k.cert.cnt + 1, V,
-                k.cert.P1, out);
+                k.cert.P1, out ? out : k.fin.dscan);
   }
   if (ev) {
     cudaEventRecord(ev[5], s);
@@ -314,7 +329,7 @@ int64_t run_path_host(bridges_ctx* c, cudaStream_t s, const int32_t* hu, const i
   int64_t rc = ensure_ws(c, total_bytes(p), s);
   if (rc != BRIDGES_OK) return rc;
   Carved k = carve(c, p);
-  Launch L{s, &c->launches, c->num_sms, c->smem_optin};
+  Launch L = launch_for(c, s);
   c->last_cfg[0] = p.M;
   c->last_cfg[1] = p.f;
   c->last_cfg[2] = p.G;
@@ -424,9 +439,8 @@ int64_t bridges_find_ctx(bridges_ctx* c, struct CUstream_st* stream, const int32
   if (V > (1 << 30)) return BRIDGES_EINVAL;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   if (cudaSetDevice(c->device) != cudaSuccess) return cuda_fail(cudaGetLastError());
-  int32_t dummy_out[1];
   Carved k{};
-  rc = run_path(c, s, u, v, E, V, M, out ? out : dummy_out, &k, nullptr);
+  rc = run_path(c, s, u, v, E, V, M, out, &k, nullptr);
   if (rc) return rc;
   if (out_count_device) {
     if (cudaMemcpyAsync(out_count_device, k.fin.count, sizeof(int64_t), cudaMemcpyDeviceToDevice, s) != cudaSuccess)
@@ -502,9 +516,9 @@ int64_t bridges_certificate(bridges_ctx* c, struct CUstream_st* stream, const in
   if (cudaSetDevice(c->device) != cudaSuccess) return cuda_fail(cudaGetLastError());
   Carved k{};
   CertPlan p{};
-  rc = run_path(c, s, u, v, E, V, M, nullptr, &k, &p);
+  rc = run_path(c, s, u, v, E, V, M, nullptr, &k, &p, false);
   if (rc) return rc;
-  if (V > 1) cert_export(Launch{s, &c->launches, c->num_sms, c->smem_optin}, p, k.cert, cu, cv, ct);
+  if (V > 1) cert_export(launch_for(c, s), p, k.cert, cu, cv, ct);
   // counts and status
   if (cudaMemcpyAsync(c->h_pinned, k.cert.cnt, 2 * sizeof(int32_t), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
       cudaMemcpyAsync(c->h_pinned + 1, k.status, sizeof(int32_t), cudaMemcpyDeviceToHost, s) != cudaSuccess)
@@ -530,7 +544,7 @@ int64_t bridges_from_forest(bridges_ctx* c, struct CUstream_st* stream, const in
   int64_t rc = ensure_ws(c, total_bytes(p), s);
   if (rc) return rc;
   Carved k = carve(c, p);
-  Launch L{s, &c->launches, c->num_sms, c->smem_optin};
+  Launch L = launch_for(c, s);
   int32_t* h = reinterpret_cast<int32_t*>(c->h_pinned);
   // the pinned scratch may still be read by an earlier copy on another stream: wait for it
   cudaStreamSynchronize(s);
@@ -538,8 +552,7 @@ int64_t bridges_from_forest(bridges_ctx* c, struct CUstream_st* stream, const in
   h[1] = (int32_t)n_extra;
   cudaMemsetAsync(k.status, 0, sizeof(int32_t), s);
   cudaMemcpyAsync(k.counts, h, 2 * sizeof(int32_t), cudaMemcpyHostToDevice, s);
-  int32_t dummy[1];
-  final_stage(L, k.fin, V, tu, tv, k.counts, n_tree, xu, xv, k.counts + 1, n_extra, nullptr, out ? out : dummy);
+  final_stage(L, k.fin, V, tu, tv, k.counts, n_tree, xu, xv, k.counts + 1, n_extra, nullptr, out ? out : k.spare);
   if (cudaGetLastError() != cudaSuccess) return BRIDGES_ECUDA;
   if (cudaMemcpyAsync(c->h_pinned + 1, k.fin.count, sizeof(int64_t), cudaMemcpyDeviceToHost, s) != cudaSuccess)
     return cuda_fail(cudaGetLastError());
@@ -558,7 +571,7 @@ int64_t bridges_rooted_forest(bridges_ctx* c, struct CUstream_st* stream, const 
   int64_t rc = ensure_ws(c, total_bytes(p), s);
   if (rc) return rc;
   Carved k = carve(c, p);
-  Launch L{s, &c->launches, c->num_sms, c->smem_optin};
+  Launch L = launch_for(c, s);
   int32_t* h = reinterpret_cast<int32_t*>(c->h_pinned);
   cudaStreamSynchronize(s);  // the pinned scratch may still be read by an earlier copy
   h[0] = (int32_t)n_tree;
@@ -819,8 +832,7 @@ int64_t default_split(const bridges_ctx* c, int64_t total_e) {
 int64_t run_single(bridges_ctx* c, cudaStream_t s, const int32_t* u, const int32_t* v, int64_t E, int32_t V, int32_t M,
                    int32_t* out, int64_t* count_dev) {
   Carved k{};
-  int32_t dummy[1];
-  int64_t rc = run_path(c, s, u, v, E, V, M, out ? out : dummy, &k, nullptr);
+  int64_t rc = run_path(c, s, u, v, E, V, M, out, &k, nullptr);
   if (rc) return rc;
   if (cudaMemcpyAsync(count_dev, k.fin.count, sizeof(int64_t), cudaMemcpyDeviceToDevice, s) != cudaSuccess)
     return cuda_fail(cudaGetLastError());
@@ -1050,15 +1062,9 @@ extern "C" int64_t bridges_two_edge_components(bridges_ctx* c, struct CUstream_s
   // the bridges go to the caller's buffer or to the (then unused) workspace key area
   Carved k{};
   CertPlan p{};
-  rc = run_path(c, s, u, v, E, V, M, out_bridges ? out_bridges : nullptr, &k, &p);
+  rc = run_path(c, s, u, v, E, V, M, out_bridges, &k, &p);
   if (rc) return rc;
-  Launch L{s, &c->launches, c->num_sms, c->smem_optin};
-  if (!out_bridges) {
-    // run_path skipped the final stage: run it with the bridges written to dscan, a 2V+1 array
-    // the final stage no longer reads by the time it sorts
-    final_stage(L, k.fin, V, k.cert.f1u, k.cert.f1v, k.cert.cnt + 0, V, k.cert.f2u, k.cert.f2v, k.cert.cnt + 1, V,
-                k.cert.P1, k.fin.dscan);
-  }
+  Launch L = launch_for(c, s);
   two_edge_components(L, k.fin, V, k.cert.f2u, k.cert.f2v, k.cert.cnt + 1, V, labels, k.fin.count);
   if (cudaMemcpyAsync(c->h_pinned, k.fin.count, sizeof(int64_t), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
       cudaStreamSynchronize(s) != cudaSuccess)
@@ -1114,6 +1120,7 @@ static int64_t articulation_fused_run(bridges_ctx* c, cudaStream_t s, const Laun
   int64_t rc = ensure_ws(c, fused_ws_bytes(p, V), s);
   if (rc) return rc;
   Carved k = carve(c, p);
+  if (!out_points) out_points = k.spare;  // V <= 1: no point is written
   char* ws = static_cast<char*>(c->ws);
   const ApBufs b0 = carve_ap(ws + ap_at, V);
   const ApBufs b1 = carve_ap(ws + ap_at + apb, V);
@@ -1174,11 +1181,9 @@ static int64_t articulation_fused_run(bridges_ctx* c, cudaStream_t s, const Laun
 static int64_t articulation_run(bridges_ctx* c, cudaStream_t s, const int32_t* u, const int32_t* v, int64_t E, int32_t V,
                          int32_t M, int32_t* out_points, int32_t* out_bridges, int64_t* out_counts_device,
                          const int32_t* hu, const int32_t* hv) {
-  int32_t dummy_out[1];
-  if (!out_points) out_points = dummy_out;  // V <= 1: nothing is written
   const CertPlan p0 = plan_for(c, E, V, M);
   const size_t ap_at = align_up(total_bytes(p0), 256);
-  Launch L{s, &c->launches, c->num_sms, c->smem_optin};
+  Launch L = launch_for(c, s);
   // the fused form when it applies and its larger workspace fits the caller's limits, else two passes
   if (fused_eligible(c, p0, E, V) && ws_fits(c, fused_ws_bytes(p0, V)))
     return articulation_fused_run(c, s, L, p0, u, v, E, V, out_points, out_bridges, out_counts_device, hu, hv);
@@ -1204,10 +1209,8 @@ static int64_t articulation_run(bridges_ctx* c, cudaStream_t s, const int32_t* u
   if (rc == 1) {
     rc = run_path(c, s, u, v, E, V, M, out_bridges, &k, nullptr);
     if (rc) return rc;
-    if (!out_bridges)
-      final_stage(L, k.fin, V, k.cert.f1u, k.cert.f1v, k.cert.cnt + 0, V, k.cert.f2u, k.cert.f2v, k.cert.cnt + 1, V,
-                  k.cert.P1, k.fin.dscan);
   }
+  if (!out_points) out_points = k.spare;  // V <= 1: no point is written
   Range range("bridges: articulation block pass");
   ApBufs b = carve_ap(static_cast<char*>(c->ws) + ap_at, V);
   // the block pass streams the whole list as one partition, its own warm-up before the snapshot
@@ -1339,8 +1342,7 @@ extern "C" int64_t bridges_inc_reset(bridges_inc* I, struct CUstream_st* stream,
   if (V > (1 << 30)) return BRIDGES_EINVAL;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   if (cudaSetDevice(I->ctx->device) != cudaSuccess) return cuda_fail(cudaGetLastError());
-  int32_t dummy[1];
-  rc = run_path(I->ctx, s, u, v, E, V, M, out_bridges ? out_bridges : dummy, &I->k, &I->p);
+  rc = run_path(I->ctx, s, u, v, E, V, M, out_bridges, &I->k, &I->p);
   if (rc) return rc;
   if (cudaMemcpyAsync(I->ctx->h_pinned, I->k.fin.count, sizeof(int64_t), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
       cudaStreamSynchronize(s) != cudaSuccess)
@@ -1357,14 +1359,13 @@ extern "C" int64_t bridges_inc_add(bridges_inc* I, struct CUstream_st* stream, c
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   bridges_ctx* c = I->ctx;
   if (cudaSetDevice(c->device) != cudaSuccess) return cuda_fail(cudaGetLastError());
-  Launch L{s, &c->launches, c->num_sms, c->smem_optin};
+  Launch L = launch_for(c, s);
   const Carved& k = I->k;
   const int32_t V = I->V;
   if (cudaMemsetAsync(k.status, 0, sizeof(int32_t), s) != cudaSuccess) return cuda_fail(cudaGetLastError());
   cert_offer(L, I->p, k.cert, yu, yv, n);
-  int32_t dummy[1];
   final_stage(L, k.fin, V, k.cert.f1u, k.cert.f1v, k.cert.cnt + 0, V, k.cert.f2u, k.cert.f2v, k.cert.cnt + 1, V,
-              k.cert.P1, out_bridges ? out_bridges : dummy);
+              k.cert.P1, out_bridges ? out_bridges : k.spare);
   if (cudaMemcpyAsync(c->h_pinned, k.fin.count, sizeof(int64_t), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
       cudaStreamSynchronize(s) != cudaSuccess)
     return cuda_fail(cudaGetLastError());
@@ -1376,7 +1377,7 @@ extern "C" int64_t bridges_inc_two_edge_components(bridges_inc* I, struct CUstre
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   bridges_ctx* c = I->ctx;
   if (cudaSetDevice(c->device) != cudaSuccess) return cuda_fail(cudaGetLastError());
-  Launch L{s, &c->launches, c->num_sms, c->smem_optin};
+  Launch L = launch_for(c, s);
   const Carved& k = I->k;
   two_edge_components(L, k.fin, I->V, k.cert.f2u, k.cert.f2v, k.cert.cnt + 1, I->V, labels, k.fin.count);
   if (cudaMemcpyAsync(c->h_pinned, k.fin.count, sizeof(int64_t), cudaMemcpyDeviceToHost, s) != cudaSuccess ||

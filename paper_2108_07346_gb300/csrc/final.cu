@@ -19,7 +19,8 @@
 //   superchunks in shared memory) -> bridge test -> sort of the packed (a<<k | b) keys (all-pairs
 //   rank for up to 16,384 bridges, else an in-kernel stable LSD radix sort).
 // Every wait in the barrier is bounded: on expiry the block records BRIDGES_ETIMEDOUT in the
-// status word and leaves the kernel, and the others follow at their next barrier.
+// status word and as the call's count, and leaves the kernel; the others follow at their next
+// barrier.
 #include <algorithm>
 
 #include "common.cuh"
@@ -57,6 +58,8 @@ struct FinArgs {
   int32_t* out;
   int kbits;
   int32_t sup_log;  // chunks per superchunk = kSuperChunks << sup_log
+  unsigned bar_polls;  // polls a barrier waits before it gives up
+  int32_t hold_polls;  // > 0: the last block sleeps this many ~100 ns polls before its first barrier
 };
 
 __device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
@@ -75,23 +78,27 @@ __device__ __forceinline__ unsigned atom_add_acq_rel(unsigned* p, unsigned v) {
   return old;
 }
 
-// Grid-wide barrier for a cooperative launch.  Returns false if the wait gave up (the status
-// word then holds BRIDGES_ETIMEDOUT and the caller must leave the kernel).  The block's writes
-// are ordered before its thread 0 by the block barrier; thread 0's arrival is an acquire-release
-// add (publishes them, and the last arriver acquires everyone's), and the release of the new
-// generation / the waiters' acquire loads carry them to every block.  No separate fences: about
-// 1.9 us per barrier against 2.4 us with fences around a relaxed add (measured, 152 blocks).
-__device__ __noinline__ bool grid_barrier(unsigned* count, unsigned* gen, int32_t* status) {
+// Grid-wide barrier for a cooperative launch.  Returns false if the wait gave up: the status
+// word then holds BRIDGES_ETIMEDOUT (or an earlier error) and the caller must leave the kernel.
+// Every other block then gives up at its next barrier, so the block that would write the count
+// after the last phase never gets there; the count is set to that first error here instead, so
+// that a caller never reads the count of an earlier call.  The block's writes are ordered before
+// its thread 0 by the block barrier; thread 0's arrival is an acquire-release add (publishes
+// them, and the last arriver acquires everyone's), and the release of the new generation / the
+// waiters' acquire loads carry them to every block.  No separate fences: about 1.9 us per
+// barrier against 2.4 us with fences around a relaxed add (measured, 152 blocks).
+__device__ __noinline__ bool grid_barrier(const FinalBufs& f, unsigned polls) {
   __shared__ int ok;
   __syncthreads();
   if (threadIdx.x == 0) {
     ok = 1;
-    const unsigned g = ld_acquire(gen);
-    if (atom_add_acq_rel(count, 1u) == gridDim.x - 1) {
-      atomicExch(count, 0u);  // ordered before the release below
-      st_release(gen, g + 1);
-    } else if (!bounded_poll([&] { return ld_acquire(gen) != g; }, kSpinCap)) {
-      set_status(status, BRIDGES_ETIMEDOUT_CODE);
+    const unsigned g = ld_acquire(f.bar_gen);
+    if (atom_add_acq_rel(f.bar_count, 1u) == gridDim.x - 1) {
+      atomicExch(f.bar_count, 0u);  // ordered before the release below
+      st_release(f.bar_gen, g + 1);
+    } else if (!bounded_poll([&] { return ld_acquire(f.bar_gen) != g; }, polls)) {
+      const int32_t first = atomicCAS(f.status, 0, BRIDGES_ETIMEDOUT_CODE);
+      *f.count = (int64_t)(first != 0 ? first : BRIDGES_ETIMEDOUT_CODE);
       ok = 0;
     }
   }
@@ -99,9 +106,9 @@ __device__ __noinline__ bool grid_barrier(unsigned* count, unsigned* gen, int32_
   return ok != 0;
 }
 
-#define BARRIER()                                                 \
-  do {                                                            \
-    if (!grid_barrier(f.bar_count, f.bar_gen, f.status)) return; \
+#define BARRIER()                            \
+  do {                                       \
+    if (!grid_barrier(f, A.bar_polls)) return; \
   } while (0)
 
 __device__ __forceinline__ int64_t gtid() { return (int64_t)blockIdx.x * blockDim.x + threadIdx.x; }
@@ -142,8 +149,8 @@ __device__ __forceinline__ int32_t block_excl(int32_t v, int32_t* red, int32_t* 
 
 // Exclusive scans of one or two int32 arrays of length n (in place allowed); out[n] = total.
 // Block b owns a contiguous range.  Contains one grid barrier; the caller adds the one after.
-__device__ bool grid_scan(const FinalBufs& f, const int32_t* in0, int32_t* out0, const int32_t* in1, int32_t* out1,
-                          int64_t n, int32_t* red) {
+__device__ bool grid_scan(const FinalBufs& f, unsigned polls, const int32_t* in0, int32_t* out0, const int32_t* in1,
+                          int32_t* out1, int64_t n, int32_t* red) {
   const int64_t per = (n + gridDim.x - 1) / gridDim.x;
   const int64_t lo = min(n, per * (int64_t)blockIdx.x), hi = min(n, lo + per);
   int32_t s0 = 0, s1 = 0;
@@ -157,7 +164,7 @@ __device__ bool grid_scan(const FinalBufs& f, const int32_t* in0, int32_t* out0,
     f.part[blockIdx.x] = s0;
     if (in1) f.part[gridDim.x + blockIdx.x] = s1;
   }
-  if (!grid_barrier(f.bar_count, f.bar_gen, f.status)) return false;
+  if (!grid_barrier(f, polls)) return false;
   int32_t c0 = 0, c1 = 0;
   for (int k = threadIdx.x; k < (int)blockIdx.x; k += blockDim.x) {
     c0 += f.part[k];
@@ -225,6 +232,11 @@ __global__ void __launch_bounds__(kThreads) final_kernel(FinArgs A) {
   const int32_t nx = min(*A.d_nx, A.cx);
   const int64_t narcs_cap = 2 * (int64_t)max(V, 1);
 
+  // a test knob: hold the last block back (a bounded sleep) so that the others' first barrier
+  // gives up; never set in normal use
+  if (A.hold_polls > 0 && blockIdx.x == gridDim.x - 1 && threadIdx.x == 0)
+    for (int32_t i = 0; i < A.hold_polls; i++) __nanosleep(100);
+
   // 0: clear
   for (int64_t i = gtid(); i < V; i += gstride()) {
     f.deg[i] = 0;
@@ -247,7 +259,7 @@ __global__ void __launch_bounds__(kThreads) final_kernel(FinArgs A) {
     atomicAdd(f.deg + b, 1);
   }
   BARRIER();
-  if (!grid_scan(f, f.deg, f.off, nullptr, nullptr, V, red)) return;
+  if (!grid_scan(f, A.bar_polls, f.deg, f.off, nullptr, nullptr, V, red)) return;
   BARRIER();
   const int32_t narcs = (int32_t)min((int64_t)f.off[V], narcs_cap);
 
@@ -322,7 +334,7 @@ __global__ void __launch_bounds__(kThreads) final_kernel(FinArgs A) {
     f.vbase[x] = nv;
   }
   BARRIER();
-  if (!grid_scan(f, f.aoff, f.aoff, f.vbase, f.vbase, V, red)) return;
+  if (!grid_scan(f, A.bar_polls, f.aoff, f.aoff, f.vbase, f.vbase, V, red)) return;
   BARRIER();
 
   // 6: tour positions; down arcs (parent -> child) come before their twins
@@ -346,7 +358,7 @@ __global__ void __launch_bounds__(kThreads) final_kernel(FinArgs A) {
     }
   }
   BARRIER();
-  if (!grid_scan(f, f.dflag, f.dscan, nullptr, nullptr, narcs, red)) return;
+  if (!grid_scan(f, A.bar_polls, f.dflag, f.dscan, nullptr, nullptr, narcs, red)) return;
   BARRIER();
 
   // 7: preorder numbers and subtree sizes; lo / hi start at the vertex itself
@@ -534,7 +546,7 @@ __global__ void __launch_bounds__(kThreads) final_kernel(FinArgs A) {
       __syncthreads();
       if (threadIdx.x < 256) f.hist[(int64_t)threadIdx.x * gridDim.x + blockIdx.x] = (int32_t)run[threadIdx.x];
       BARRIER();
-      if (!grid_scan(f, f.hist, f.hist, nullptr, nullptr, (int64_t)256 * gridDim.x, red)) return;
+      if (!grid_scan(f, A.bar_polls, f.hist, f.hist, nullptr, nullptr, (int64_t)256 * gridDim.x, red)) return;
       BARRIER();
       if (threadIdx.x < 256) {
         run[threadIdx.x] = (uint32_t)f.hist[(int64_t)threadIdx.x * gridDim.x + blockIdx.x];
@@ -750,6 +762,8 @@ void final_stage(const Launch& L, const FinalBufs& f, int32_t V, const int32_t* 
   int sl = 0;
   while (ceil_div(nchunks, (int64_t)kSuperChunks << sl) > kMaxSup) sl++;
   A.sup_log = sl;
+  A.bar_polls = L.bar_polls > 0 ? L.bar_polls : kSpinCap;
+  A.hold_polls = L.hold_polls;
   // one block per SM at most; small forests take fewer (a block per 256 vertices), which makes
   // every grid barrier cheaper and leaves SMs free for work on other streams (the server)
   const int64_t want = ceil_div(std::max(V, 1), 256);

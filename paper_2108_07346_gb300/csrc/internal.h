@@ -21,6 +21,10 @@ struct Launch {
   int64_t* launches;
   int num_sms;
   size_t smem_optin;  // max dynamic shared memory per block
+  // test knobs of the final stage (bridges_opts.test_barrier_polls / test_hold_polls); zero in
+  // normal use
+  unsigned bar_polls = 0;  // polls a grid barrier waits before it gives up (0: the default cap)
+  int32_t hold_polls = 0;  // > 0: its last block sleeps this many ~100 ns polls before the first barrier
 };
 
 // Per-call plan for the certificate stages (Sec. 3): M partitions ("jobs"), G blocks per job,

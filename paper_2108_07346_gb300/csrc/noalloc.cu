@@ -17,10 +17,13 @@ namespace {
 
 using namespace bridges;
 
-// 8 MiB: enough for about 24,000 vertices with M <= 2 partitions, or 16,384 vertices with
-// M <= 8.  Every GPU that loads the library holds this array until the process exits.
+// 8 MiB.  A call needs about 1.07 MB plus (150 + 30 M) bytes per vertex, so the largest graph
+// that fits has 41,023 vertices at M = 1 (the automatic choice), 35,135 at M = 2, 27,264 at
+// M = 4 and 18,848 at M = 8; the edge count does not enter.  Every GPU that loads the library
+// holds this array until the process exits.
 constexpr size_t kNoAllocScratchBytes = 8u << 20;
-constexpr size_t kMiscBytes = 1024;  // status word
+constexpr size_t kMiscBytes = 1024;  // status word at 0, the spare output slot at kSpareOut
+constexpr size_t kSpareOut = 512;    // output target of a call that writes no pairs (V <= 1)
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
 
@@ -29,11 +32,11 @@ struct DeviceSetup {
   void* scratch = nullptr;  // device address of g_noalloc_scratch on this device
   int num_sms = 0;
   size_t smem_optin = 0;
+  int64_t launches = 0;  // kernels launched on this device (calls on one device are serialised)
 };
 
 std::mutex g_setup_mu;
 DeviceSetup g_setup[64];
-int64_t g_launches = 0;
 
 // Once per device, with that device current: the device address of the scratch array.  In
 // host code the array's name only stands for a host-side shadow, so the address must come from
@@ -86,8 +89,10 @@ extern "C" int64_t bridges_find_noalloc(struct CUstream_st* stream, const int32_
   cb.status = status;
   FinalBufs fb = carve_final(base + kMiscBytes + cert, p.V, status);
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-  Launch L{s, &g_launches, S->num_sms, S->smem_optin};
-  int32_t dummy_out[1];
+  Launch L{s, &S->launches, S->num_sms, S->smem_optin};
+  // a graph of at most one vertex has no pairs to write; its output pointer may be null, so the
+  // stage gets a slot of the scratch array instead (a device address, never a host one)
+  int32_t* spare_out = reinterpret_cast<int32_t*>(base + kSpareOut);
 
   // The array keeps whatever the previous call left: the status word is cleared here, and every
   // other buffer that must start at zero is initialised by the stages themselves.
@@ -98,7 +103,7 @@ extern "C" int64_t bridges_find_noalloc(struct CUstream_st* stream, const int32_
   cert_init(L, p, cb);
   cert_leaves(L, p, cb, u, v, nullptr);
   cert_merge(L, p, cb);
-  final_stage(L, fb, V, cb.f1u, cb.f1v, cb.cnt + 0, V, cb.f2u, cb.f2v, cb.cnt + 1, V, cb.P1, out ? out : dummy_out);
+  final_stage(L, fb, V, cb.f1u, cb.f1v, cb.cnt + 0, V, cb.f2u, cb.f2v, cb.cnt + 1, V, cb.P1, out ? out : spare_out);
   if (cudaGetLastError() != cudaSuccess) return BRIDGES_ECUDA;
   if (out_count_device) {
     if (cudaMemcpyAsync(out_count_device, fb.count, sizeof(int64_t), cudaMemcpyDeviceToDevice, s) != cudaSuccess) {

@@ -5,6 +5,7 @@ import pytest
 import torch
 
 import graphgen
+import oracle
 
 pytestmark = pytest.mark.gpu
 
@@ -36,3 +37,29 @@ def test_errors_leave_context_usable(cuda_lib):
     with pytest.raises(cuda_lib.BridgesError) as ei:
         small.find(u, v2, 5)
     assert ei.value.code == -3
+
+
+def test_final_stage_barrier_timeout_leaves_a_usable_context(cuda_lib):
+    """The final stage's grid barrier gives up after its poll cap: one block is held back (a
+    bounded sleep, a test knob) while the others wait with a short cap.  The call then returns
+    BRIDGES_ETIMEDOUT -- not the count of the call before it -- and the same context, with the
+    knobs cleared, gives the exact result again (the barrier's count and generation are reset
+    for every call)."""
+    g = graphgen.workload("small")  # 2,088 vertices: a block per 256, so 9 blocks
+    u = torch.from_numpy(np.array(g.u)).cuda()
+    v = torch.from_numpy(np.array(g.v)).cuda()
+    ref = oracle.dfs_bridges(g.u, g.v, g.V).tolist()
+    ctx = cuda_lib.Context(device="cuda:0")
+    assert ctx.find(u, v, g.V, 1).cpu().numpy().tolist() == ref
+    ctx.set_opts(test_barrier_polls=1000, test_hold_polls=200_000)
+    for _ in range(2):
+        with pytest.raises(cuda_lib.BridgesError) as ei:
+            ctx.find(u, v, g.V, 1)
+        assert ei.value.code == -5
+    cnt = torch.zeros(1, dtype=torch.int64, device="cuda:0")
+    ctx.find(u, v, g.V, 1, count_device=cnt)  # the enqueue-only form: the status lands in the count
+    torch.cuda.synchronize()
+    assert int(cnt.item()) == -5
+    ctx.set_opts()
+    assert ctx.find(u, v, g.V, 1).cpu().numpy().tolist() == ref
+    assert ctx.find(u, v, g.V, 4).cpu().numpy().tolist() == ref

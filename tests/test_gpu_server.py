@@ -49,8 +49,8 @@ def test_mix_equals_alone(cuda_lib):
     st = srv.stats()
     assert st["completed"] == 2 * len(graphs) and st["batches"] >= 1 and st["singles"] >= 1
     assert st["max_in_flight"] >= 2
-    # the results are also the oracle's
-    for (u, v, V), ref in list(zip(graphs, alone))[::5]:
+    # every result is also the oracle's
+    for (u, v, V), ref in zip(graphs, alone):
         assert ref.tolist() == oracle.dfs_bridges(u, v, V).tolist()
     srv.close()
 
@@ -64,7 +64,7 @@ def test_arrivals_while_running(cuda_lib):
     ts = [srv.submit(dev(g.u), dev(g.v), g.V) for g in small]
     for g, t in zip(small, ts):
         got, _ = srv.wait(t)
-        assert {tuple(x) for x in g.planted.tolist()} <= {tuple(x) for x in got.cpu().numpy().tolist()}
+        assert got.cpu().numpy().tolist() == oracle.dfs_bridges(g.u, g.v, g.V).tolist()
     got, _ = srv.wait(tb)
     assert got.cpu().numpy().tolist() == big.planted.tolist()
     srv.close()
