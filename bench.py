@@ -5,8 +5,12 @@ Euler tour / range test / sort -- over the large dense workload: an ER(65,536, 0
 256 pendant trees and 128 two-edge vertices (about 1.07 G edges, 8.6 GB of int32 COO; seed 2).
 The inputs (8.6 GB) are larger than L2 (129 MB), so no flush is needed between steps.
 
-Prints one JSON line (rank 0).  ``--impl reference`` times the CPU oracle (the paper's
-pipeline, single-threaded C) on a bounded sample of the same workload instead.
+Prints one JSON line (rank 0).  On one GPU the default run adds two sub-objects measured after
+the large workload: ``batched`` (4,096 graphs per persistent launch) and ``served`` (100,000
+Poisson requests at 2,000/s, each a fresh graph generated on the device, against the
+continuous-batching server), each with its oracle comparison and plain per-graph calls beside it.
+``--impl reference`` times the CPU oracle (the paper's pipeline, single-threaded C) on a bounded
+sample of the large workload instead.
 """
 from __future__ import annotations
 
@@ -19,6 +23,7 @@ import subprocess
 import sys
 import tempfile
 import time
+import types
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
@@ -34,9 +39,9 @@ import graphgen  # noqa: E402
 METRIC = "input edges/s to exact bridge set"
 UNIT = "GE/s"
 
-# DRAM bytes (read + write) per streamed edge, from full-size single-pass ncu captures on the large
-# workload (profiles/launch_list_large_dense.md, profiles/block_pass_large_dense.md); each is valid
-# only for the kernel sources it was measured on (hash of those sources).
+# DRAM bytes (read + write) per streamed edge, from the ncu captures of the large workload's
+# streaming kernels; each is valid only for the kernel sources it was measured on (hash of those
+# sources).
 #   forest pass, M = 1: 9.295 GB read + 7.2 MB written for 1,072,703,284 streamed edges
 #   block pass stream: 9.512 GB read + 11.0 MB written for 1,073,547,340 streamed edges
 TRAFFIC = {"certify_sha": "7e50d053b42e91d5", "bytes_per_edge": 8.6808}
@@ -228,9 +233,9 @@ def cpu_oracle_parallel_rate(g, cores):
         ids = np.concatenate(list(ex.map(leaf, range(cores))))
     u1, v1 = g.u[ids], g.v[ids]
     keep, _ = oracle.certificate(u1, v1, g.V)
-    nb = len(oracle.dfs_bridges(u1[keep], v1[keep], g.V))
+    br = oracle.dfs_bridges(u1[keep], v1[keep], g.V)
     dt = time.perf_counter() - t
-    return E / dt / 1e9, dt, nb
+    return E / dt / 1e9, dt, br
 
 
 def ref_sample_per_step(args, budget_edges):
@@ -301,6 +306,93 @@ def run_reference_ap(args, world):
     }), flush=True)
 
 
+def run_sharded(args, world, rank, local):
+    """N ranks on one graph (strong scaling): rank r holds the contiguous shard r of the list, the
+    ranks merge certificates on the paper's schedule (Sec. 3 phases) and rank 0 finds the bridges
+    and broadcasts them.  Certificates travel through NCCL on device buffers (NVLS off), or with
+    --exchange gloo through host buffers (which also lets several ranks share one GPU for a test
+    with --same-device).  A step is one whole sharded call."""
+    import torch
+    import torch.distributed as dist
+
+    import paper_2108_07346_gb300 as pb
+    from paper_2108_07346_gb300.sharded import Certifier, shard_range, sharded_bridges
+
+    os.environ.setdefault("NCCL_NVLS_ENABLE", "0")
+    dev = torch.device("cuda", 0 if args.same_device else local)
+    torch.cuda.set_device(dev)
+    if args.exchange == "gloo":
+        dist.init_process_group("gloo")
+    else:
+        dist.init_process_group("nccl", device_id=dev)
+    spec = graphgen.Spec(**{**graphgen.asdict(graphgen.WORKLOADS[args.workload]),
+                            **({} if args.density is None else {"p": args.density})})
+    g = graphgen.generate_device(spec, dev)
+    E, V, planted = g.E, g.V, g.planted
+    lo, hi = shard_range(E, rank, world)
+    u, v = g.u[lo:hi].clone(), g.v[lo:hi].clone()
+    del g
+    torch.cuda.empty_cache()
+    ctx = pb.Context(device=dev)
+    cert = Certifier(ctx)
+    res = sharded_bridges(u, v, V, cert).cpu().numpy()
+    correct = bool(np.array_equal(res, planted))
+    for _ in range(args.warmup):
+        sharded_bridges(u, v, V, cert)
+    stream = torch.cuda.current_stream(dev)
+    dist.barrier()
+    torch.cuda.synchronize()
+    clocks = Clocks(dev.index)
+    clocks.start()
+    clocks.mark("t0")
+    l0 = ctx.launches()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        br = sharded_bridges(u, v, V, cert)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    dist.barrier()
+    clocks.mark("t1")
+    launches = ctx.launches() - l0
+    ms_total = reduce_max(e0.elapsed_time(e1), dev if args.exchange == "nccl" else None)
+    ck = clocks.stop()
+    timed_correct = bool(np.array_equal(br.cpu().numpy(), planted))
+    # end to end: each rank's shard from pinned host memory, copied in inside the timed region
+    hu, hv = u.cpu().pin_memory(), v.cpu().pin_memory()
+    ks = max(1, min(args.steps, args.e2e_steps))
+    dist.barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    nb = 0
+    for _ in range(ks):
+        du, dv = hu.to(dev, non_blocking=True), hv.to(dev, non_blocking=True)
+        nb = int(sharded_bridges(du, dv, V, cert).cpu().shape[0])
+    torch.cuda.synchronize()
+    dt = reduce_max(time.perf_counter() - t0, dev if args.exchange == "nccl" else None)
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": E * args.steps / (ms_total * 1e-3) / 1e9, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_total / args.steps,
+            "higher_is_better": True, "scaling": "strong", "vs_baseline": None, "dtype": "int32",
+            "data": "synthetic",
+            "config": {"workload": workload_name(args.workload, types.SimpleNamespace(spec=spec)),
+                       "V": V, "E": E, "parallelism": f"sharded x{world}: contiguous shards, certificates merged on "
+                                                     f"the paper's log2 N schedule, rank 0 final stage",
+                       "exchange": args.exchange, "same_device": bool(args.same_device),
+                       "bridges": int(br.shape[0]), "bridges_equal_planted": correct,
+                       "timed_output_equal_planted": timed_correct,
+                       "l2": "inputs (8E bytes) larger than L2; no flush"},
+            "clocks": ck, "gpu_launches": launches,
+            "e2e": {"value": E * ks / dt / 1e9, "unit": UNIT, "h2d_bytes_per_step": 8 * E,
+                    "d2h_bytes_per_step": 16 + 8 * nb, "steps": ks, "ms_per_step": dt / ks * 1e3},
+            "roofline": None, "cpu_baseline": None,
+        }
+        print(json.dumps(line), flush=True)
+    dist.destroy_process_group()
+
+
 def run_native(args, world, rank, local):
     import torch
 
@@ -338,8 +430,8 @@ def run_native(args, world, rank, local):
             del sctx
 
     # correctness of what is timed: the planted bridges are exact on this workload
-    res = ctx.find(du, dv, V, args.M)
-    correct = bool(res.shape[0] == len(g.planted) and np.array_equal(res.cpu().numpy(), g.planted))
+    res = ctx.find(du, dv, V, args.M).cpu().numpy()
+    correct = bool(res.shape[0] == len(g.planted) and np.array_equal(res, g.planted))
     for _ in range(args.warmup):
         ctx.find(du, dv, V, args.M, out=out, count_device=cnt, stream=stream)
     torch.cuda.synchronize()
@@ -365,6 +457,9 @@ def run_native(args, world, rank, local):
     ck = clocks.stop()
     ms_total = reduce_max(ms_total, dev)
     n_found = int(cnt.item())
+    # the last timed call's own output, read back after the timed region
+    timed_out = out[: 2 * max(n_found, 0)].view(-1, 2).cpu().numpy()
+    timed_correct = bool(n_found == len(g.planted) and np.array_equal(timed_out, g.planted))
     ms_step = ms_total / args.steps
     value = whole_job_rate(E * args.steps, world, ms_total * 1e-3)
 
@@ -413,12 +508,25 @@ def run_native(args, world, rank, local):
                "sample": f"Sec. 3 pipeline + Alg. 1 (single-threaded C) on the first {n} edges of the workload; "
                          f"{dt:.1f} s"}
         cores = os.cpu_count() or 1
-        prate, pdt, pnb = cpu_oracle_parallel_rate(g, cores)
+        prate, pdt, pbr = cpu_oracle_parallel_rate(g, cores)
         cpu_all = {"value": prate, "unit": UNIT, "cores": cores, "kind": "oracle",
                    "cpu": cpu_model(),
                    "sample": f"the whole graph: Alg. 2 on {cores} partitions in parallel, one merge, Alg. 1 "
                              f"(the oracle's C, one thread per partition); {pdt:.2f} s",
-                   "bridges_equal": pnb == n_found}
+                   "bridges_equal": bool(np.array_equal(pbr, timed_out))}
+
+    # the batched and served workloads on the same GPU, after the large one's buffers are gone
+    legs = {}
+    if rank == 0 and world == 1 and args.workload == "large":
+        del du, dv, ctx
+        torch.cuda.synchronize()
+        torch.cuda.empty_cache()
+        if not args.no_batched:
+            legs["batched"] = batched_leg(args, dev, with_cpu=not args.no_cpu)
+            torch.cuda.empty_cache()
+        if not args.no_served:
+            legs["served"] = served_leg(args, dev, with_cpu=not args.no_cpu)
+            torch.cuda.empty_cache()
 
     if rank == 0:
         line = {
@@ -431,6 +539,7 @@ def run_native(args, world, rank, local):
                        "warm_edges": cfg["warm_edges"], "l2": "inputs (8E bytes) larger than L2; no flush",
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
                        "bridges": n_found, "bridges_equal_planted": correct,
+                       "timed_output_equal_planted": timed_correct,
                        "autotuned_plan": plan, "stage_ms_by_M": sweep},
             "clocks": ck, "e2e": e2e, "gpu_launches": launches, "roofline": roof, "cpu_baseline": cpu,
             "cpu_baseline_all_cores": cpu_all,
@@ -439,6 +548,7 @@ def run_native(args, world, rank, local):
                 "max": max(h["total"] for h in hist), "calls": len(hist),
                 "note": "CUDA-event time of each of the last timed calls (stage events)"},
         }
+        line.update(legs)
         print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()
@@ -618,13 +728,17 @@ def make_batch(seed, count):
     return np.concatenate(us), np.concatenate(vs), off, np.array(Vs, np.int32), planted
 
 
-def run_batched(args, world, rank, local):
+def batched_leg(args, dev, with_cpu=True):
+    """The batched workload (4,096 graphs in one persistent launch per step) on device `dev`:
+    graphs/s, per-step latency, the last timed step's output against the oracle, one plain call
+    per graph for comparison.  Returns a dict (the standalone line's body)."""
+    import concurrent.futures
+
     import torch
 
+    import oracle
     import paper_2108_07346_gb300 as pb
 
-    dev = torch.device("cuda", local)
-    torch.cuda.set_device(dev)
     u, v, off, Vs, planted = make_batch(3, args.graphs)
     G, E = len(Vs), int(off[-1])
     du = torch.from_numpy(u).to(dev)
@@ -632,23 +746,25 @@ def run_batched(args, world, rank, local):
     ctx = pb.Context(device=dev)
     stream = torch.cuda.current_stream(dev)
     out, counts, out_off = ctx.find_batched(du, dv, off, Vs)
-    cnt = counts.cpu().numpy()
-    o = out.cpu().numpy()
-    correct = all(
-        {tuple(x) for x in planted[g].tolist()} <= {tuple(x) for x in o[out_off[g]:out_off[g] + 2 * cnt[g]].reshape(-1, 2).tolist()}
-        for g in range(G))
     for _ in range(args.warmup):
         ctx.find_batched(du, dv, off, Vs, out=out, counts=counts, sync=False)
     torch.cuda.synchronize()
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
+    steps = max(1, args.steps)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(steps + 1)]
     l0 = ctx.launches()
-    e0.record(stream)
-    for _ in range(args.steps):
+    ev[0].record(stream)
+    for i in range(steps):
         ctx.find_batched(du, dv, off, Vs, out=out, counts=counts, sync=False)
-    e1.record(stream)
+        ev[i + 1].record(stream)
     torch.cuda.synchronize()
-    ms = e0.elapsed_time(e1) / args.steps
+    launches = ctx.launches() - l0
+    step_ms = np.array([ev[i].elapsed_time(ev[i + 1]) for i in range(steps)])
+    ms = float(ev[0].elapsed_time(ev[steps])) / steps
+    # the last timed step's output, graph by graph
+    cnt = counts.cpu().numpy()
+    o = out.cpu().numpy()
+    got = [o[out_off[g]:out_off[g] + 2 * max(int(cnt[g]), 0)].reshape(-1, 2) for g in range(G)]
+    planted_ok = all({tuple(x) for x in planted[g].tolist()} <= {tuple(x) for x in got[g].tolist()} for g in range(G))
     # one plain call per graph, same GPU, same stream
     plain = pb.Context(device=dev)
     cnt_d = torch.zeros(1, dtype=torch.int64, device=dev)
@@ -665,168 +781,282 @@ def run_batched(args, world, rank, local):
     torch.cuda.synchronize()
     ms_plain = p0.elapsed_time(p1)
     cpu = None
-    if not args.no_cpu:
-        # the oracle (Sec. 3 pipeline + Alg. 1 in C) on every graph, one graph per host core: the
-        # C calls release the GIL, so a thread pool runs them in parallel
-        import concurrent.futures
-
-        import oracle
-
+    if with_cpu:
+        # the oracle (Sec. 3 pipeline + Alg. 1 in C) on every graph, one graph per host core (the C
+        # calls release the GIL); its bridges are compared with the timed step's, graph by graph
         cores = os.cpu_count() or 1
         t0 = time.perf_counter()
         with concurrent.futures.ThreadPoolExecutor(cores) as ex:
-            list(ex.map(lambda g: oracle.bridges(u[off[g]:off[g + 1]], v[off[g]:off[g + 1]], int(Vs[g]), 1), range(G)))
+            ref = list(ex.map(lambda g: oracle.bridges(u[off[g]:off[g + 1]], v[off[g]:off[g + 1]], int(Vs[g]), 1),
+                              range(G)))
         dt = time.perf_counter() - t0
+        equal = sum(int(np.array_equal(ref[g], got[g])) for g in range(G))
         cpu = {"value": G / dt, "unit": "graphs/s", "cores": cores, "kind": "oracle",
-               "sample": f"all {G} graphs, one per host thread ({dt:.1f} s)"}
+               "sample": f"all {G} graphs, one per host thread ({dt:.1f} s)",
+               "graphs_equal_to_timed_step": equal, "graphs": G}
     peak, kind = peaks()
-    line = {
-        "metric": "graphs/s (batched bridge queries)", "value": G / (ms * 1e-3), "unit": "graphs/s", "n_gpus": 1,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "int32", "data": "synthetic",
-        "config": {"workload": f"batched: {G} graphs, V log-uniform [64, 4096], density U[0.1, 0.9], seed 3",
-                   "E_total": E, "planted_subset_found": correct, "launches_per_step": (ctx.launches() - l0) / args.steps},
+    del du, dv, ctx, plain
+    return {
+        "metric": "graphs/s (batched bridge queries)", "value": G / (ms * 1e-3), "unit": "graphs/s",
+        "steps": steps, "warmup": args.warmup, "ms_per_step": ms,
+        "step_latency_ms": {"p50": float(np.percentile(step_ms, 50)), "p99": float(np.percentile(step_ms, 99)),
+                            "max": float(step_ms.max())},
+        "config": {"workload": f"batched: {G} graphs, V log-uniform [64, 4096], density U[0.1, 0.9], 1-32 planted "
+                               f"bridges each, seed 3", "graphs": G, "E_total": E,
+                   "planted_subset_found": planted_ok, "launches_per_step": launches / steps,
+                   "l2": "inputs (8E bytes, 4.3 GB) larger than L2; no flush"},
         "input_GE_per_s": E / (ms * 1e-3) / 1e9,
         "roofline": {"bound": "hbm", "achieved": 8.0 * E / (ms * 1e-3) / 1e9, "peak": peak, "unit": "GB/s",
-                     "frac": 8.0 * E / (ms * 1e-3) / 1e9 / peak, "peak_kind": kind},
-        "plain_per_graph": {"value": G / (ms_plain * 1e-3), "unit": "graphs/s", "ms_total": ms_plain},
+                     "frac": 8.0 * E / (ms * 1e-3) / 1e9 / peak, "peak_kind": kind,
+                     "kernel": "batched_kernel (whole step)"},
+        "plain_per_graph": {"value": G / (ms_plain * 1e-3), "unit": "graphs/s", "ms_total": ms_plain,
+                            "note": "one bridges_find_ctx call per graph on the same stream"},
         "speedup_vs_plain": ms_plain / ms,
         "cpu_baseline": cpu,
     }
-    print(json.dumps(line), flush=True)
 
 
-def run_served(args, world, rank, local):
-    """Poisson arrivals of bridge queries against the continuous-batching server."""
-    import threading
-
+def run_batched(args, world, rank, local):
     import torch
-
-    import paper_2108_07346_gb300 as pb
-
-    import dataclasses
 
     dev = torch.device("cuda", local)
     torch.cuda.set_device(dev)
-    rng = np.random.default_rng(4)
+    leg = batched_leg(args, dev, with_cpu=not args.no_cpu)
+    line = {"metric": leg.pop("metric"), "value": leg.pop("value"), "unit": leg.pop("unit"), "n_gpus": 1,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic"}
+    line.update(leg)
+    print(json.dumps(line), flush=True)
+
+
+class RequestStream:
+    """The served workload's requests, each a fresh seeded graph (workload_spec("served", 4, i)),
+    generated on the device by `threads` producer threads (request i by thread i mod threads, each
+    on its own stream), up to `ahead` requests (and `max_bytes` of edges) ahead of the consumer,
+    which takes them in order.  Generation time is ingest, reported apart."""
+
+    def __init__(self, dev, first, count, ahead=256, max_bytes=6 << 30, variant="primary", threads=4):
+        import threading
+
+        self.dev, self.first, self.count = dev, first, count
+        self.ahead, self.max_bytes = ahead, max_bytes
+        self.bytes = 0
+        self.ready = {}
+        self.next = first  # the next request the consumer takes
+        self.cv = threading.Condition()
+        self.gen_s = 0.0
+        self.error = None
+        self.variant = variant
+        self.threads = [threading.Thread(target=self._run, args=(k, threads), daemon=True) for k in range(threads)]
+        for t in self.threads:
+            t.start()
+
+    def spec(self, i):
+        import dataclasses
+
+        s = graphgen.workload_spec("served", 4, i)
+        return dataclasses.replace(s, n_clusters=1, n_extra=0) if self.variant == "stress" else s
+
+    def _run(self, k, n):
+        import torch
+
+        try:
+            st = torch.cuda.Stream(self.dev) if torch.device(self.dev).type == "cuda" else None
+            for i in range(self.first + k, self.first + self.count, n):
+                with self.cv:  # stay within `ahead` requests and `max_bytes` of the consumer
+                    while i - self.next >= self.ahead or (self.bytes > self.max_bytes and i > self.next):
+                        self.cv.wait()
+                t0 = time.perf_counter()
+                g = graphgen.generate_device(self.spec(i), self.dev, stream=st)
+                dt = time.perf_counter() - t0
+                with self.cv:
+                    self.gen_s += dt
+                    self.bytes += 8 * g.E
+                    self.ready[i] = g
+                    self.cv.notify_all()
+        except Exception as e:  # surfaced to the consumer
+            with self.cv:
+                self.error = e
+                self.cv.notify_all()
+
+    def qsize(self):
+        with self.cv:
+            return len(self.ready)
+
+    def get(self):
+        with self.cv:
+            while self.next not in self.ready:
+                if self.error is not None:
+                    raise RuntimeError(f"request generation failed: {self.error!r}")
+                self.cv.wait()
+            i = self.next
+            g = self.ready.pop(i)
+            self.next += 1
+            self.cv.notify_all()
+            return i, g
+
+    def release(self, g):
+        with self.cv:
+            self.bytes -= 8 * g.E
+            self.cv.notify_all()
+
+
+def served_leg(args, dev, with_cpu=True):
+    """The served workload as configured: args.requests Poisson arrivals (mean args.rate per s),
+    each a fresh seeded graph generated on the device, against the continuous-batching server
+    under a args.budget_gb device-memory budget; p50 / p99 latency (submit to completion), a
+    seeded 1% of the results against the oracle, and plain per-graph calls and the saturated
+    server on fresh requests for comparison.  Returns a dict."""
+    import concurrent.futures
+
+    import torch
+
+    import oracle
+    import paper_2108_07346_gb300 as pb
+
     stress = args.served_variant == "stress"
-    pool = []
-    # the stress variant: one ER(V, d) core per request (same V and d draws, same pendant paths,
-    # no clusters): about 63 M edges per request on average, up to about 1.3 G; its pool is kept
-    # to 24 graphs to bound host and device memory
-    for i in range(min(args.pool, 24) if stress else args.pool):
-        spec = graphgen.workload_spec("served", 4, i)
-        if stress:
-            spec = dataclasses.replace(spec, n_clusters=1, n_extra=0)
-        g = graphgen.generate(spec)
-        pool.append((torch.from_numpy(np.array(g.u)).to(dev), torch.from_numpy(np.array(g.v)).to(dev), g.V, g.E))
-        del g
     N = args.requests
-    gaps = rng.exponential(1.0 / args.rate, N)
-    arrival = np.cumsum(gaps)
-    ring = 256
-    vmax = max(p[2] for p in pool)
-    outs = [torch.empty(2 * vmax, dtype=torch.int32, device=dev) for _ in range(ring)]
+    rng = np.random.default_rng(4)
+    arrival = np.cumsum(rng.exponential(1.0 / args.rate, N))
+    vrng = np.random.default_rng(41)
+    check = set(int(i) for i in vrng.choice(N, max(1, N // 100), replace=False))
     srv = pb.Server(device=dev, mem_budget=int(args.budget_gb * (1 << 30)), max_slots=args.slots)
-    # warm-up: every pool graph once
-    for i, (u, v, V, E) in enumerate(pool):
-        srv.wait(srv.submit(u, v, V, out=outs[i % ring]))
-    tickets = [None] * N
+    # warm-up: a few requests past the measured range (kernels loaded, graphs captured)
+    warm = RequestStream(dev, N + 1_000_000, 32, variant=args.served_variant)
+    for _ in range(32):
+        _, g = warm.get()
+        srv.wait(srv.submit(g.u, g.v, g.V))
+        warm.release(g)
+    reqs = RequestStream(dev, 0, N, variant=args.served_variant)
+    ring = 256
+    live = [None] * ring  # (ticket, graph, out)
     lat = np.zeros(N)
+    late = np.zeros(N)
+    results = {}
     edges = 0
+    # the ingest of the first requests is not part of the arrival schedule
+    while reqs.qsize() < min(64, N) and reqs.error is None:
+        time.sleep(0.01)
+
+    def finish(j):
+        t, g, o = live[j % ring]
+        got, ms = srv.wait(t)
+        lat[j] = ms
+        if j in check:
+            results[j] = got.cpu().numpy()
+        reqs.release(g)
+        live[j % ring] = None
+
     t0 = time.perf_counter()
     for i in range(N):
-        j = i % ring
         if i >= ring:
-            res = srv.wait(tickets[i - ring])
-            lat[i - ring] = res[1]
+            finish(i - ring)
+        _, g = reqs.get()
         due = t0 + arrival[i]
         now = time.perf_counter()
         if due > now:
             time.sleep(due - now)
-        u, v, V, E = pool[i % len(pool)]
-        tickets[i] = srv.submit(u, v, V, out=outs[j])
-        edges += E
-    for i in range(max(0, N - ring), N):
-        lat[i] = srv.wait(tickets[i])[1]
+        late[i] = max(0.0, time.perf_counter() - due)
+        o = torch.empty(2 * max(g.V - 1, 1), dtype=torch.int32, device=dev)
+        live[i % ring] = (srv.submit(g.u, g.v, g.V, out=o), g, o)
+        edges += g.E
+    for j in range(max(0, N - ring), N):
+        finish(j)
     wall = time.perf_counter() - t0
+    gen_s = reqs.gen_s
     st = srv.stats()
-    # saturation: the same requests submitted as fast as the ring of outputs allows (no arrival
-    # gaps), so the server always has a backlog; its completion rate is its capacity
-    sat_n = min(N, args.plain * 4)
-    ts = time.perf_counter()
-    sat = [None] * sat_n
-    for i in range(sat_n):
-        if i >= ring:
-            srv.wait(sat[i - ring])
-        u, v, V, E = pool[i % len(pool)]
-        sat[i] = srv.submit(u, v, V, out=outs[i % ring])
-    for i in range(max(0, sat_n - ring), sat_n):
-        srv.wait(sat[i])
-    sat_s = time.perf_counter() - ts
-    # a seeded 1% of the requests and every request under 1 M edges, served once more: their
-    # bridges are compared with the oracle's in the cpu_baseline leg below
-    vrng = np.random.default_rng(41)
-    picks = sorted({int(i) % len(pool) for i in vrng.choice(N, max(1, N // 100), replace=False)} |
-                   {k for k, p in enumerate(pool) if p[3] < 1_000_000})
-    got = {}
-    for k in picks:
-        u, v, V, E = pool[k]
-        o = torch.empty(2 * max(V - 1, 1), dtype=torch.int32, device=dev)
-        got[k] = srv.wait(srv.submit(u, v, V, out=o))[0].cpu().numpy().tolist()
+    # saturation and plain calls on fresh requests past the measured range (same distribution):
+    # each chunk is generated first (nothing else on the GPU), then submitted back to back or
+    # called one by one, and only that part is timed
+    nsat = min(N, args.plain * 2)
+    chunk = 128
+
+    def gen_chunk(i0, n):
+        return [graphgen.generate_device(reqs.spec(i), dev) for i in range(i0, i0 + n)]
+
+    sat_s = 0.0
+    for c0 in range(0, nsat, chunk):
+        gs = gen_chunk(N + c0, min(chunk, nsat - c0))
+        torch.cuda.synchronize()
+        ts = time.perf_counter()
+        tk = [srv.submit(g.u, g.v, g.V) for g in gs]
+        for t in tk:
+            srv.wait(t)
+        sat_s += time.perf_counter() - ts
+        del gs, tk
     srv.close()
-    # one plain call per request, back to back, same requests
     ctx = pb.Context(device=dev)
     cnt = torch.zeros(1, dtype=torch.int64, device=dev)
-    for u, v, V, E in pool:
-        ctx.find(u, v, V, 0, out=outs[0], count_device=cnt)
-    torch.cuda.synchronize()
-    tp = time.perf_counter()
-    nplain = min(N, args.plain)
-    for i in range(nplain):
-        u, v, V, E = pool[i % len(pool)]
-        ctx.find(u, v, V, 0, out=outs[0], count_device=cnt)
-    torch.cuda.synchronize()
-    plain_s = time.perf_counter() - tp
+    outp = torch.empty(2 * 200_000, dtype=torch.int32, device=dev)
+    plain_s = 0.0
+    for c0 in range(0, args.plain, chunk):
+        gs = gen_chunk(N + nsat + c0, min(chunk, args.plain - c0))
+        if c0 == 0:
+            for g in gs[:8]:
+                ctx.find(g.u, g.v, g.V, 0, out=outp, count_device=cnt)
+        torch.cuda.synchronize()
+        tp = time.perf_counter()
+        for g in gs:
+            ctx.find(g.u, g.v, g.V, 0, out=outp, count_device=cnt)
+        torch.cuda.synchronize()
+        plain_s += time.perf_counter() - tp
+        del gs
     cpu = None
-    if not args.no_cpu:
-        # the oracle (Sec. 3 pipeline + Alg. 1 in C) on the sampled requests, one per host thread
-        # (the C calls release the GIL); its bridges must equal the server's
-        import concurrent.futures
-
-        import oracle
-
-        hosts = {k: (pool[k][0].cpu().numpy(), pool[k][1].cpu().numpy(), pool[k][2]) for k in picks}
+    if with_cpu:
+        # the oracle (Sec. 3 pipeline + Alg. 1 in C) on the seeded 1% of the requests, regenerated
+        # on the host, one per host thread (the C calls release the GIL); its bridges must equal
+        # what the server returned for them
         cores = os.cpu_count() or 1
+        picks = sorted(check)
         tc = time.perf_counter()
+
+        def one(i):
+            g = graphgen.generate(reqs.spec(i))
+            return oracle.bridges(g.u, g.v, g.V, 1), g.E
+
         with concurrent.futures.ThreadPoolExecutor(cores) as ex:
-            ref = dict(zip(picks, ex.map(lambda k: oracle.bridges(*hosts[k], 1).tolist(), picks)))
+            ref = dict(zip(picks, ex.map(one, picks)))
         dtc = time.perf_counter() - tc
         cpu = {"value": len(picks) / dtc, "unit": "graphs/s", "cores": cores, "kind": "oracle",
-               "sample": f"{len(picks)} requests: a seeded 1% plus every request under 1 M edges "
-                         f"({dtc:.1f} s)",
-               "equal_to_served": all(got[k] == ref[k] for k in picks)}
-    line = {
-        "metric": "served graphs/s with p50/p99 latency", "value": N / wall, "unit": "graphs/s", "n_gpus": 1,
-        "steps": N, "warmup": len(pool), "ms_per_step": wall / N * 1e3, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "int32", "data": "synthetic",
-        "config": {"workload": (f"served{' (stress)' if stress else ''}: Poisson arrivals {args.rate}/s, {N} requests "
-                                f"over {len(pool)} resident graphs, V log-uniform [256, 65536], density U[0.05, 0.6], "
+               "sample": f"a seeded 1% of the requests ({len(picks)} graphs, {sum(e for _, e in ref.values())} "
+                         f"edges), regenerated on the host; {dtc:.1f} s including generation",
+               "requests_equal_to_served": sum(int(np.array_equal(ref[i][0], results[i])) for i in picks),
+               "requests_checked": len(picks)}
+    del ctx
+    return {
+        "metric": "served graphs/s with p50/p99 latency", "value": N / wall, "unit": "graphs/s",
+        "requests": N, "ms_per_request": wall / N * 1e3,
+        "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
+                       "max": float(lat.max()), "from": "submit to completion, measured by the server"},
+        "config": {"workload": (f"served{' (stress)' if stress else ''}: Poisson arrivals {args.rate:g}/s, {N} "
+                                f"requests, each a fresh graph, V log-uniform [256, 65536], density U[0.05, 0.6], "
                                 + ("one ER(V, d) core per request with pendant paths" if stress else
                                    "clusters of 512 with pendant paths and extra inter-cluster edges") + ", seed 4"),
                    "variant": args.served_variant, "budget_gb": args.budget_gb, "slots": args.slots,
                    "mean_edges": edges / N,
-                   "pool_edges": {"mean": float(np.mean([p[3] for p in pool])),
-                                  "p99": float(np.percentile([p[3] for p in pool], 99)),
-                                  "max": int(max(p[3] for p in pool))}},
-        "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
-                       "max": float(lat.max())},
+                   "ingest": {"where": "generated on the device by 4 producer threads, ahead of arrival",
+                              "thread_s": gen_s, "per_request_thread_ms": gen_s / N * 1e3},
+                   "late_submits": {"over_1ms": int((late > 1e-3).sum()), "p99_ms": float(np.percentile(late, 99) * 1e3)}},
         "served_GE_per_s": edges / wall / 1e9, "offered_per_s": args.rate, "server_stats": st,
-        "plain_per_graph": {"value": nplain / plain_s, "unit": "graphs/s"},
-        "saturation": {"value": sat_n / sat_s, "unit": "graphs/s", "requests": sat_n,
-                       "note": "all requests submitted back to back (256 in flight at most)"},
+        "plain_per_graph": {"value": args.plain / plain_s, "unit": "graphs/s", "requests": args.plain,
+                            "note": "one bridges_find_ctx call per fresh request, back to back"},
+        "saturation": {"value": nsat / sat_s, "unit": "graphs/s", "requests": nsat,
+                       "note": f"fresh requests submitted {chunk} at a time back to back"},
+        "speedup_saturated_vs_plain": (nsat / sat_s) / (args.plain / plain_s),
         "cpu_baseline": cpu,
     }
+
+
+def run_served(args, world, rank, local):
+    """Poisson arrivals of bridge queries against the continuous-batching server."""
+    import torch
+
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    leg = served_leg(args, dev, with_cpu=not args.no_cpu)
+    line = {"metric": leg.pop("metric"), "value": leg.pop("value"), "unit": leg.pop("unit"), "n_gpus": 1,
+            "steps": leg["requests"], "warmup": 32, "ms_per_step": leg["ms_per_request"],
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic"}
+    line.update(leg)
     print(json.dumps(line), flush=True)
 
 
@@ -838,9 +1068,8 @@ def main():
     ap.add_argument("--impl", choices=["native", "reference"], default="native")
     ap.add_argument("--workload", choices=["large", "mid", "small", "batched", "served", "articulation"],
                     default="large")
-    ap.add_argument("--requests", type=int, default=4000, help="served: requests")
+    ap.add_argument("--requests", type=int, default=100_000, help="served: requests")
     ap.add_argument("--rate", type=float, default=2000.0, help="served: mean arrivals per second")
-    ap.add_argument("--pool", type=int, default=64, help="served: distinct resident graphs")
     ap.add_argument("--slots", type=int, default=8, help="served: concurrent units of work")
     ap.add_argument("--budget-gb", type=float, default=40.0, help="served: device-memory budget")
     ap.add_argument("--plain", type=int, default=1000, help="served: plain calls timed for comparison")
@@ -854,6 +1083,12 @@ def main():
     ap.add_argument("--no-sweep", action="store_true", help="skip the per-M stage timings")
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--exchange", choices=["nccl", "gloo"], default="nccl",
+                    help="N > 1: certificates through NCCL device buffers or gloo host buffers")
+    ap.add_argument("--same-device", action="store_true",
+                    help="N > 1 with gloo: every rank on cuda:0 (a test of the sharded path on one GPU)")
+    ap.add_argument("--no-batched", action="store_true", help="large workload: skip the batched leg")
+    ap.add_argument("--no-served", action="store_true", help="large workload: skip the served leg")
     ap.add_argument("--ap-two-pass", action="store_true",
                     help="articulation workload: the bridge path, then a second pass (not the fused read)")
     ap.add_argument("--cpu-sample", type=int, default=2_000_000_000, help="oracle sample (edges; whole graph)")
@@ -870,6 +1105,8 @@ def main():
         run_served(args, world, rank, local)
     elif args.workload == "articulation":
         run_articulation(args, world, rank, local)
+    elif world > 1:
+        run_sharded(args, world, rank, local)
     else:
         run_native(args, world, rank, local)
 

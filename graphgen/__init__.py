@@ -60,6 +60,50 @@ class _Graph(ctypes.Structure):
     ]
 
 
+class _Perm(ctypes.Structure):
+    _fields_ = [("add", ctypes.c_uint64 * 3), ("mul", ctypes.c_uint64 * 3), ("shift", ctypes.c_int),
+                ("mask", ctypes.c_uint64), ("n", ctypes.c_uint64)]
+
+
+class _Layout(ctypes.Structure):
+    _fields_ = [
+        ("s", _Spec),
+        ("Vc", ctypes.c_int64),
+        ("nc", ctypes.c_int64),
+        ("V", ctypes.c_int64),
+        ("n_struct", ctypes.c_int64),
+        ("thr", ctypes.c_uint64),
+        ("kER", ctypes.c_uint64),
+        ("su", ctypes.POINTER(ctypes.c_int32)),
+        ("sv", ctypes.POINTER(ctypes.c_int32)),
+        ("n_planted", ctypes.c_int64),
+        ("planted", ctypes.POINTER(ctypes.c_int32)),
+        ("rowcl", ctypes.POINTER(ctypes.c_int32)),
+        ("PV", _Perm),
+    ]
+
+
+_dev_lib = None
+
+
+def _load_dev():
+    global _dev_lib
+    if _dev_lib is None:
+        lib = _load()
+        lib.gg_layout_make.restype = ctypes.POINTER(_Layout)
+        lib.gg_layout_make.argtypes = [ctypes.POINTER(_Spec)]
+        lib.gg_layout_free.argtypes = [ctypes.POINTER(_Layout)]
+        dev = ctypes.CDLL(_build.build_dev())
+        dev.ggd_count.restype = ctypes.c_int
+        dev.ggd_count.argtypes = [ctypes.POINTER(_Layout), ctypes.c_void_p, ctypes.c_void_p,
+                                  ctypes.POINTER(ctypes.c_int64)]
+        dev.ggd_write.restype = ctypes.c_int
+        dev.ggd_write.argtypes = [ctypes.POINTER(_Layout), ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64,
+                                  ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
+        _dev_lib = dev
+    return _dev_lib
+
+
 def _load():
     global _lib
     if _lib is None:
@@ -169,6 +213,66 @@ def generate(spec: Spec) -> Graph:
         u = np.zeros(0, np.int32)
         v = np.zeros(0, np.int32)
     return Graph(u=u, v=v, V=V, planted=planted, spec=spec, n_er=int(g.n_er))
+
+
+@dataclass
+class DeviceGraph:
+    """A generated graph whose edge arrays are torch int32 tensors on a CUDA device."""
+
+    u: object
+    v: object
+    V: int
+    planted: np.ndarray
+    n_er: int = 0
+
+    @property
+    def E(self) -> int:
+        return int(self.u.shape[0])
+
+
+def generate_device(spec: Spec, device="cuda", stream=None) -> DeviceGraph:
+    """The graph of ``spec`` generated on a GPU, bit-identical to :func:`generate`.
+
+    The host draws the structural part (a few thousand edges); the device draws the
+    Erdos-Renyi pairs, counts them per row (one stream synchronisation to learn the edge count)
+    and writes every edge at its shuffled position.  Returns once the edges are written
+    (``stream`` is synchronised), so the tensors can be used on any stream."""
+    import torch
+
+    dev_lib = _load_dev()
+    lib = _load()
+    dev = torch.device(device)
+    cs = spec._c()
+    h = lib.gg_layout_make(ctypes.byref(cs))
+    if not h:
+        raise ValueError(f"invalid generator spec or out of memory: {spec}")
+    try:
+        L = h.contents
+        with torch.cuda.device(dev):
+            st = torch.cuda.current_stream(dev) if stream is None else stream
+            sh = ctypes.c_void_p(st.cuda_stream)
+            rowoff = torch.empty(int(L.Vc) + 1, dtype=torch.int64, device=dev)
+            n_er = ctypes.c_int64(0)
+            if dev_lib.ggd_count(h, sh, ctypes.c_void_p(rowoff.data_ptr()), ctypes.byref(n_er)) != 0:
+                raise RuntimeError("ggd_count failed")
+            ns = int(L.n_struct)
+            E = int(n_er.value) + ns
+            u = torch.empty(max(E, 1), dtype=torch.int32, device=dev)[:E]
+            v = torch.empty(max(E, 1), dtype=torch.int32, device=dev)[:E]
+            su = torch.from_numpy(np.ctypeslib.as_array(L.su, shape=(max(ns, 1),))[:ns].copy()).to(dev)
+            sv = torch.from_numpy(np.ctypeslib.as_array(L.sv, shape=(max(ns, 1),))[:ns].copy()).to(dev)
+            with torch.cuda.stream(st):
+                rc = dev_lib.ggd_write(h, sh, ctypes.c_void_p(rowoff.data_ptr()), n_er.value,
+                                       ctypes.c_void_p(su.data_ptr()), ctypes.c_void_p(sv.data_ptr()),
+                                       ctypes.c_void_p(u.data_ptr()), ctypes.c_void_p(v.data_ptr()))
+            if rc != 0:
+                raise RuntimeError("ggd_write failed")
+            st.synchronize()
+        npl = int(L.n_planted)
+        planted = np.ctypeslib.as_array(L.planted, shape=(max(npl, 1) * 2,))[: 2 * npl].reshape(npl, 2).copy()
+        return DeviceGraph(u=u, v=v, V=int(L.V), planted=planted, n_er=int(n_er.value))
+    finally:
+        lib.gg_layout_free(h)
 
 
 WORKLOADS = {

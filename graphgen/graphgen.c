@@ -24,6 +24,8 @@
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+
+#include "graphgen.h"
 #ifdef _OPENMP
 #include <omp.h>
 #endif
@@ -85,12 +87,7 @@ static double exp2_det(double x) {
  * Three rounds of (add key, multiply by an odd key, xor-shift right) on b = ceil(log2 n) bits;
  * each step is a bijection of [0, 2^b), so their composition is one.  Cycle walking maps it onto
  * [0, n) (Black & Rogaway 2002); since 2^b < 2n the expected walk is below two steps. */
-typedef struct {
-  uint64_t add[3], mul[3];
-  int shift;
-  uint64_t mask;
-  uint64_t n;
-} perm_t;
+typedef gg_perm perm_t;
 
 static void perm_init(perm_t* P, uint64_t n, uint64_t seed, uint64_t stream) {
   int b = 1;
@@ -121,34 +118,7 @@ static inline uint64_t perm_apply(const perm_t* P, uint64_t x) {
   return x;
 }
 
-/* ---------------- specification ---------------- */
-typedef struct {
-  uint64_t seed;
-  int32_t n_clusters;    /* >= 1; core vertices are split into near-equal clusters */
-  int32_t core_vertices; /* >= n_clusters */
-  double p;              /* Erdos-Renyi density inside every cluster */
-  int32_t n_pendant;     /* pendant vertices, one edge each to a random core vertex */
-  int32_t n_paths;       /* pendant paths hung from random core vertices */
-  int32_t path_min, path_max;
-  int32_t n_extra_pairs; /* pairs of edges joining the same random pair of distinct clusters */
-  int32_t n_extra;       /* single extra edges between random distinct clusters */
-  int32_t n_trees;       /* pendant random recursive trees, each hung by one edge */
-  int32_t tree_min, tree_max;
-  int32_t n_two_edge; /* vertices joined to two distinct random core vertices */
-  int32_t shuffle;    /* 1: random edge order */
-  int32_t relabel;    /* 1: random vertex ids */
-} gg_spec;
-
-typedef struct {
-  int64_t E;
-  int32_t V;
-  int64_t n_planted;
-  int32_t* u;
-  int32_t* v;
-  int32_t* planted; /* 2 * n_planted, (a<b) pairs sorted ascending */
-  int64_t n_er;     /* edges inside clusters */
-} gg_graph;
-
+/* ---------------- specification (gg_spec, gg_graph, gg_layout: graphgen.h) ---------------- */
 static inline int32_t cluster_start(const gg_spec* s, int64_t c) {
   return (int32_t)((c * (int64_t)s->core_vertices) / s->n_clusters);
 }
@@ -184,38 +154,32 @@ static int validate(const gg_spec* s) {
   return 0;
 }
 
-/* Generates the graph described by *s.  Returns NULL on invalid spec or out of memory. */
-gg_graph* gg_generate(const gg_spec* s_in) {
-  gg_spec S = *s_in;
-  const gg_spec* s = &S;
-  if (validate(s)) return NULL;
+/* Everything of the graph of *s except its Erdos-Renyi edges: the sizes, the structural edges
+ * (cluster tree, extra edges, pendant vertices, paths and trees, two-edge vertices) in raw ids,
+ * and the planted bridges after relabelling.  The ER edges depend on the cluster sizes only, so
+ * they can be drawn anywhere (host or device) from (kER, thr) and added in row order. */
+gg_layout* gg_layout_make(const gg_spec* s_in) {
+  gg_layout* L = (gg_layout*)calloc(1, sizeof(gg_layout));
+  if (!L) return NULL;
+  L->s = *s_in;
+  const gg_spec* s = &L->s;
+  if (validate(s)) {
+    free(L);
+    return NULL;
+  }
   const int64_t Vc = s->core_vertices;
   const int64_t nc = s->n_clusters;
-  const uint64_t thr = density_threshold(s->p);
-  const uint64_t kER = stream_key(s->seed, ST_ER);
-
-  /* ---- pass 1: ER edge count per core row ---- */
-  int64_t* rowoff = (int64_t*)malloc((size_t)(Vc + 1) * sizeof(int64_t));
+  L->Vc = Vc;
+  L->nc = nc;
+  L->thr = density_threshold(s->p);
+  L->kER = stream_key(s->seed, ST_ER);
   int32_t* rowcl = (int32_t*)malloc((size_t)Vc * sizeof(int32_t));
-  if (!rowoff || !rowcl) {
-    free(rowoff);
-    free(rowcl);
+  if (!rowcl) {
+    free(L);
     return NULL;
   }
   for (int64_t c = 0; c < nc; c++)
     for (int64_t a = cluster_start(s, c); a < cluster_start(s, c + 1); a++) rowcl[a] = (int32_t)c;
-
-#pragma omp parallel for schedule(dynamic, 16)
-  for (int64_t a = 0; a < Vc; a++) {
-    int64_t c = rowcl[a];
-    int64_t c0 = cluster_start(s, c), sz = cluster_start(s, c + 1) - c0;
-    int64_t la = a - c0, cnt = 0;
-    for (int64_t lb = la + 1; lb < sz; lb++) cnt += (draw(kER, er_ctr(c, sz, la, lb)) < thr);
-    rowoff[a + 1] = cnt;
-  }
-  rowoff[0] = 0;
-  for (int64_t a = 0; a < Vc; a++) rowoff[a + 1] += rowoff[a];
-  const int64_t n_er = rowoff[Vc];
 
   /* ---- structural edges (sequential stream) ---- */
   seq_rng R = {stream_key(s->seed, ST_STRUCT), 0};
@@ -235,12 +199,13 @@ gg_graph* gg_generate(const gg_spec* s_in) {
   const int64_t n_struct = n_ctree + 2LL * s->n_extra_pairs + s->n_extra + s->n_pendant + n_path_edges +
                            n_tree_edges + 2LL * s->n_two_edge;
   const int64_t V = Vc + s->n_pendant + n_path_edges + n_tree_edges + s->n_two_edge;
-  const int64_t E = n_er + n_struct;
+  L->V = V;
+  L->n_struct = n_struct;
   if (V > INT32_MAX) {
-    free(rowoff);
     free(rowcl);
     free(path_len);
     free(tree_sz);
+    free(L);
     return NULL;
   }
 
@@ -354,6 +319,88 @@ gg_graph* gg_generate(const gg_spec* s_in) {
   for (int64_t c = 1; c < nc; c++)
     if (!covered[c]) splanted[ctree_base + (c - 1)] = 1;
 
+  /* the vertex relabelling and the planted bridges in final ids */
+  perm_init(&L->PV, (uint64_t)(V > 0 ? V : 1), s->seed, ST_VPERM);
+  int64_t np = 0;
+  for (int64_t i = 0; i < n_struct; i++) np += splanted[i];
+  L->n_planted = np;
+  L->planted = (int32_t*)malloc(sizeof(int32_t) * (size_t)(2 * np + 2));
+  uint64_t* keys = (uint64_t*)malloc(sizeof(uint64_t) * (size_t)(np + 1));
+  int64_t q = 0;
+  for (int64_t i = 0; i < n_struct; i++) {
+    if (!splanted[i]) continue;
+    const int64_t ra = gg_relabel(L, su[i]), rb = gg_relabel(L, sv[i]);
+    const int64_t lo = ra < rb ? ra : rb, hi = ra < rb ? rb : ra;
+    keys[q++] = ((uint64_t)lo << 32) | (uint64_t)hi;
+  }
+  qsort(keys, (size_t)np, sizeof(uint64_t), cmp_u64);
+  for (int64_t i = 0; i < np; i++) {
+    L->planted[2 * i] = (int32_t)(keys[i] >> 32);
+    L->planted[2 * i + 1] = (int32_t)(keys[i] & 0xffffffffULL);
+  }
+  free(keys);
+  L->su = su;
+  L->sv = sv;
+  L->rowcl = rowcl;
+  free(path_len);
+  free(tree_sz);
+  free(splanted);
+  free(cpar);
+  free(cdepth);
+  free(covered);
+  return L;
+}
+
+void gg_layout_free(gg_layout* L) {
+  if (!L) return;
+  free(L->su);
+  free(L->sv);
+  free(L->planted);
+  free(L->rowcl);
+  free(L);
+}
+
+/* Final id of raw vertex x (the keyed bijection, or x itself without relabelling). */
+int64_t gg_relabel(const gg_layout* L, int64_t x) {
+  return L->s.relabel ? (int64_t)perm_apply(&L->PV, (uint64_t)x) : x;
+}
+
+/* The edge shuffle of a graph with E edges: the keyed bijection's parameters (perm_t). */
+void gg_edge_perm(const gg_layout* L, int64_t E, gg_perm* out) {
+  perm_init(out, (uint64_t)(E > 0 ? E : 1), L->s.seed, ST_EPERM);
+}
+
+/* Generates the graph described by *s.  Returns NULL on invalid spec or out of memory. */
+gg_graph* gg_generate(const gg_spec* s_in) {
+  gg_layout* L = gg_layout_make(s_in);
+  if (!L) return NULL;
+  const gg_spec* s = &L->s;
+  const int64_t Vc = L->Vc;
+  const uint64_t thr = L->thr;
+  const uint64_t kER = L->kER;
+  const int32_t* rowcl = L->rowcl;
+
+  /* ---- pass 1: ER edge count per core row ---- */
+  int64_t* rowoff = (int64_t*)malloc((size_t)(Vc + 1) * sizeof(int64_t));
+  if (!rowoff) {
+    gg_layout_free(L);
+    return NULL;
+  }
+#pragma omp parallel for schedule(dynamic, 16)
+  for (int64_t a = 0; a < Vc; a++) {
+    int64_t c = rowcl[a];
+    int64_t c0 = cluster_start(s, c), sz = cluster_start(s, c + 1) - c0;
+    int64_t la = a - c0, cnt = 0;
+    for (int64_t lb = la + 1; lb < sz; lb++) cnt += (draw(kER, er_ctr(c, sz, la, lb)) < thr);
+    rowoff[a + 1] = cnt;
+  }
+  rowoff[0] = 0;
+  for (int64_t a = 0; a < Vc; a++) rowoff[a + 1] += rowoff[a];
+  const int64_t n_er = rowoff[Vc];
+  const int64_t n_struct = L->n_struct;
+  const int64_t V = L->V;
+  const int64_t E = n_er + n_struct;
+
   /* ---- output with relabelling and shuffling ---- */
   gg_graph* g = (gg_graph*)calloc(1, sizeof(gg_graph));
   g->E = E;
@@ -361,21 +408,22 @@ gg_graph* gg_generate(const gg_spec* s_in) {
   g->n_er = n_er;
   g->u = (int32_t*)malloc(sizeof(int32_t) * (size_t)(E > 0 ? E : 1));
   g->v = (int32_t*)malloc(sizeof(int32_t) * (size_t)(E > 0 ? E : 1));
-  if (!g->u || !g->v) {
+  g->planted = (int32_t*)malloc(sizeof(int32_t) * (size_t)(2 * L->n_planted + 2));
+  if (!g->u || !g->v || !g->planted) {
     free(g->u);
     free(g->v);
+    free(g->planted);
     free(g);
     g = NULL;
     goto done;
   }
   {
-    perm_t PV, PE;
-    perm_init(&PV, (uint64_t)(V > 0 ? V : 1), s->seed, ST_VPERM);
-    perm_init(&PE, (uint64_t)(E > 0 ? E : 1), s->seed, ST_EPERM);
-    const int relabel = s->relabel, shuffle = s->shuffle;
+    perm_t PE;
+    gg_edge_perm(L, E, &PE);
+    const int shuffle = s->shuffle;
     int32_t* phi = (int32_t*)malloc(sizeof(int32_t) * (size_t)(V > 0 ? V : 1));
 #pragma omp parallel for schedule(static)
-    for (int64_t x = 0; x < V; x++) phi[x] = relabel ? (int32_t)perm_apply(&PV, (uint64_t)x) : (int32_t)x;
+    for (int64_t x = 0; x < V; x++) phi[x] = (int32_t)gg_relabel(L, x);
     int32_t* ou = g->u;
     int32_t* ov = g->v;
 #pragma omp parallel for schedule(dynamic, 16)
@@ -395,41 +443,22 @@ gg_graph* gg_generate(const gg_spec* s_in) {
         }
       }
     }
-    int64_t np = 0;
-    for (int64_t i = 0; i < n_struct; i++) np += splanted[i];
-    g->n_planted = np;
-    g->planted = (int32_t*)malloc(sizeof(int32_t) * (size_t)(2 * np + 2));
-    uint64_t* keys = (uint64_t*)malloc(sizeof(uint64_t) * (size_t)(np + 1));
-    int64_t q = 0;
     for (int64_t i = 0; i < n_struct; i++) {
-      int64_t ra = phi[su[i]];
-      int64_t rb = phi[sv[i]];
+      int64_t ra = phi[L->su[i]];
+      int64_t rb = phi[L->sv[i]];
       int64_t lo = ra < rb ? ra : rb, hi = ra < rb ? rb : ra;
       int64_t raw = n_er + i;
       int64_t at = shuffle ? (int64_t)perm_apply(&PE, (uint64_t)raw) : raw;
       ou[at] = (int32_t)lo;
       ov[at] = (int32_t)hi;
-      if (splanted[i]) keys[q++] = ((uint64_t)lo << 32) | (uint64_t)hi;
     }
-    qsort(keys, (size_t)np, sizeof(uint64_t), cmp_u64);
-    for (int64_t i = 0; i < np; i++) {
-      g->planted[2 * i] = (int32_t)(keys[i] >> 32);
-      g->planted[2 * i + 1] = (int32_t)(keys[i] & 0xffffffffULL);
-    }
-    free(keys);
+    g->n_planted = L->n_planted;
+    memcpy(g->planted, L->planted, sizeof(int32_t) * (size_t)(2 * L->n_planted));
     free(phi);
   }
 done:
   free(rowoff);
-  free(rowcl);
-  free(path_len);
-  free(tree_sz);
-  free(su);
-  free(sv);
-  free(splanted);
-  free(cpar);
-  free(cdepth);
-  free(covered);
+  gg_layout_free(L);
   return g;
 }
 

@@ -1,5 +1,7 @@
 """Host-side helpers of bench.py that need no GPU: the source hash that decides whether a
 stored DRAM-traffic figure still describes the kernel's code."""
+import pytest
+
 import bench
 
 
@@ -28,3 +30,39 @@ def test_stored_traffic_figures_name_their_sources():
     for table, key in ((bench.TRAFFIC, "certify_sha"), (bench.AP_TRAFFIC, "blocks_sha"),
                        (bench.FUSED_TRAFFIC, "blocks_sha")):
         assert len(table[key]) == 16 and table["bytes_per_edge"] > 8.0
+
+
+def test_request_stream_hands_out_requests_in_order(monkeypatch):
+    """The served bench's producer threads generate out of order; the consumer gets request
+    first, first + 1, ... and the byte budget is returned on release."""
+    import random
+    import time as _time
+    from types import SimpleNamespace
+
+    import graphgen
+
+    def fake(spec, dev, stream=None):
+        _time.sleep(random.random() * 0.002)
+        return SimpleNamespace(E=int(spec.core_vertices), seed=spec.seed)
+
+    monkeypatch.setattr(graphgen, "generate_device", fake)
+    rs = bench.RequestStream("cpu", 10, 200, ahead=16, max_bytes=1 << 40, threads=4)
+    got = []
+    for _ in range(200):
+        i, g = rs.get()
+        assert g.seed == graphgen.workload_spec("served", 4, i).seed
+        got.append(i)
+        rs.release(g)
+    assert got == list(range(10, 210)) and rs.bytes == 0 and rs.error is None
+
+
+def test_request_stream_reports_a_failed_generation(monkeypatch):
+    import graphgen
+
+    def boom(spec, dev, stream=None):
+        raise ValueError("no device")
+
+    monkeypatch.setattr(graphgen, "generate_device", boom)
+    rs = bench.RequestStream("cpu", 0, 8, threads=2)
+    with pytest.raises(RuntimeError, match="request generation failed"):
+        rs.get()

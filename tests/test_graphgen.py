@@ -62,3 +62,23 @@ def test_rmat_is_seeded_skewed_and_in_range():
     uu, vv = graphgen.rmat(5, 12, 60000, 0.25, 0.25, 0.25)
     d2 = np.bincount(np.concatenate([uu, vv]), minlength=4096)
     assert d2.max() < 3 * d2.mean()
+
+
+def test_layout_matches_generated_graph():
+    """The host layout (sizes, structural edges, planted bridges) that the device form of the
+    generator starts from is the generated graph's."""
+    import ctypes
+
+    lib = graphgen._load()
+    lib.gg_layout_make.restype = ctypes.POINTER(graphgen._Layout)
+    lib.gg_layout_make.argtypes = [ctypes.POINTER(graphgen._Spec)]
+    lib.gg_layout_free.argtypes = [ctypes.POINTER(graphgen._Layout)]
+    for spec in [graphgen.WORKLOADS["small"], graphgen.workload_spec("served", 4, 2),
+                 graphgen.workload_spec("batched", 3, 5)]:
+        g = graphgen.generate(spec)
+        h = lib.gg_layout_make(ctypes.byref(spec._c()))
+        L = h.contents
+        assert L.V == g.V and L.n_struct == g.E - g.n_er
+        pl = np.ctypeslib.as_array(L.planted, shape=(2 * L.n_planted,)).reshape(-1, 2)
+        assert np.array_equal(pl, g.planted)
+        lib.gg_layout_free(h)
