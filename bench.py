@@ -746,6 +746,22 @@ def batched_leg(args, dev, with_cpu=True):
     ctx = pb.Context(device=dev)
     stream = torch.cuda.current_stream(dev)
     out, counts, out_off = ctx.find_batched(du, dv, off, Vs)
+
+    def time_steps(n):
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(n):
+            ctx.find_batched(du, dv, off, Vs, out=out, counts=counts, sync=False)
+        b.record(stream)
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / n
+
+    # the automatic plan, then the plan the batched autotuner picks (both outside the timed region)
+    for _ in range(args.warmup):
+        ctx.find_batched(du, dv, off, Vs, out=out, counts=counts, sync=False)
+    auto_ms = time_steps(max(1, args.steps))
+    plan, tune_us = (None, None) if args.no_tune else ctx.batch_autotune(du, dv, off, Vs, reps=5)
     for _ in range(args.warmup):
         ctx.find_batched(du, dv, off, Vs, out=out, counts=counts, sync=False)
     torch.cuda.synchronize()
@@ -804,6 +820,7 @@ def batched_leg(args, dev, with_cpu=True):
         "config": {"workload": f"batched: {G} graphs, V log-uniform [64, 4096], density U[0.1, 0.9], 1-32 planted "
                                f"bridges each, seed 3", "graphs": G, "E_total": E,
                    "planted_subset_found": planted_ok, "launches_per_step": launches / steps,
+                   "tuned_plan": plan, "automatic_plan_ms_per_step": auto_ms,
                    "l2": "inputs (8E bytes, 4.3 GB) larger than L2; no flush"},
         "input_GE_per_s": E / (ms * 1e-3) / 1e9,
         "roofline": {"bound": "hbm", "achieved": 8.0 * E / (ms * 1e-3) / 1e9, "peak": peak, "unit": "GB/s",
@@ -830,15 +847,17 @@ def run_batched(args, world, rank, local):
 
 class RequestStream:
     """The served workload's requests, each a fresh seeded graph (workload_spec("served", 4, i)),
-    generated on the device by `threads` producer threads (request i by thread i mod threads, each
-    on its own stream), up to `ahead` requests (and `max_bytes` of edges) ahead of the consumer,
-    which takes them in order.  Generation time is ingest, reported apart."""
+    generated on the device in batches of `batch` consecutive requests (one batch per call of the
+    generator: two stream synchronisations per batch; 8 graphs, about 64 MB of edges, stay in L2
+    while the generator scatters them to their shuffled positions) by `threads` producer threads,
+    each on its own stream, up to `ahead` requests (and `max_bytes` of edges) ahead of the
+    consumer, which takes them in order.  Generation time is ingest, reported apart."""
 
-    def __init__(self, dev, first, count, ahead=256, max_bytes=6 << 30, variant="primary", threads=4):
+    def __init__(self, dev, first, count, ahead=512, max_bytes=6 << 30, variant="primary", threads=3, batch=8):
         import threading
 
         self.dev, self.first, self.count = dev, first, count
-        self.ahead, self.max_bytes = ahead, max_bytes
+        self.ahead, self.max_bytes, self.batch = ahead, max_bytes, batch
         self.bytes = 0
         self.ready = {}
         self.next = first  # the next request the consumer takes
@@ -861,17 +880,20 @@ class RequestStream:
 
         try:
             st = torch.cuda.Stream(self.dev) if torch.device(self.dev).type == "cuda" else None
-            for i in range(self.first + k, self.first + self.count, n):
+            end = self.first + self.count
+            for b0 in range(self.first + k * self.batch, end, n * self.batch):
+                b1 = min(end, b0 + self.batch)
                 with self.cv:  # stay within `ahead` requests and `max_bytes` of the consumer
-                    while i - self.next >= self.ahead or (self.bytes > self.max_bytes and i > self.next):
+                    while b1 - 1 - self.next >= self.ahead or (self.bytes > self.max_bytes and b0 > self.next):
                         self.cv.wait()
                 t0 = time.perf_counter()
-                g = graphgen.generate_device(self.spec(i), self.dev, stream=st)
+                gs = graphgen.generate_device_many([self.spec(i) for i in range(b0, b1)], self.dev, stream=st)
                 dt = time.perf_counter() - t0
                 with self.cv:
                     self.gen_s += dt
-                    self.bytes += 8 * g.E
-                    self.ready[i] = g
+                    for i, g in zip(range(b0, b1), gs):
+                        self.bytes += 8 * g.E
+                        self.ready[i] = g
                     self.cv.notify_all()
         except Exception as e:  # surfaced to the consumer
             with self.cv:
@@ -971,7 +993,7 @@ def served_leg(args, dev, with_cpu=True):
     chunk = 128
 
     def gen_chunk(i0, n):
-        return [graphgen.generate_device(reqs.spec(i), dev) for i in range(i0, i0 + n)]
+        return graphgen.generate_device_many([reqs.spec(i) for i in range(i0, i0 + n)], dev)
 
     sat_s = 0.0
     for c0 in range(0, nsat, chunk):
@@ -1033,7 +1055,8 @@ def served_leg(args, dev, with_cpu=True):
                                    "clusters of 512 with pendant paths and extra inter-cluster edges") + ", seed 4"),
                    "variant": args.served_variant, "budget_gb": args.budget_gb, "slots": args.slots,
                    "mean_edges": edges / N,
-                   "ingest": {"where": "generated on the device by 4 producer threads, ahead of arrival",
+                   "ingest": {"where": "generated on the device, 8 requests per generator call, by 3 producer "
+                                       "threads ahead of arrival",
                               "thread_s": gen_s, "per_request_thread_ms": gen_s / N * 1e3},
                    "late_submits": {"over_1ms": int((late > 1e-3).sum()), "p99_ms": float(np.percentile(late, 99) * 1e3)}},
         "served_GE_per_s": edges / wall / 1e9, "offered_per_s": args.rate, "server_stats": st,

@@ -100,6 +100,14 @@ def _load_dev():
         dev.ggd_write.restype = ctypes.c_int
         dev.ggd_write.argtypes = [ctypes.POINTER(_Layout), ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64,
                                   ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
+        LP = ctypes.POINTER(ctypes.POINTER(_Layout))
+        dev.ggd_count_many.restype = ctypes.c_int
+        dev.ggd_count_many.argtypes = [LP, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
+                                       ctypes.POINTER(ctypes.c_int64)]
+        dev.ggd_write_many.restype = ctypes.c_int
+        dev.ggd_write_many.argtypes = [LP, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
+                                       ctypes.POINTER(ctypes.c_int64), ctypes.c_void_p, ctypes.c_void_p,
+                                       ctypes.c_void_p]
         _dev_lib = dev
     return _dev_lib
 
@@ -273,6 +281,66 @@ def generate_device(spec: Spec, device="cuda", stream=None) -> DeviceGraph:
         return DeviceGraph(u=u, v=v, V=int(L.V), planted=planted, n_er=int(n_er.value))
     finally:
         lib.gg_layout_free(h)
+
+
+def generate_device_many(specs, device="cuda", stream=None):
+    """The graphs of ``specs`` generated on a GPU together (two stream synchronisations in all),
+    each bit-identical to :func:`generate`.  Their edge arrays are views of one device buffer."""
+    import torch
+
+    dev_lib = _load_dev()
+    lib = _load()
+    dev = torch.device(device)
+    K = len(specs)
+    if K == 0:
+        return []
+    handles = []
+    try:
+        for spec in specs:
+            cs = spec._c()
+            h = lib.gg_layout_make(ctypes.byref(cs))
+            if not h:
+                raise ValueError(f"invalid generator spec or out of memory: {spec}")
+            handles.append(h)
+        arr = (ctypes.POINTER(_Layout) * K)(*handles)
+        Ls = [h.contents for h in handles]
+        n_rows = sum(int(L.Vc) + 1 for L in Ls)
+        n_struct = [int(L.n_struct) for L in Ls]
+        with torch.cuda.device(dev):
+            st = torch.cuda.current_stream(dev) if stream is None else stream
+            sh = ctypes.c_void_p(st.cuda_stream)
+            rowoff = torch.empty(n_rows + K, dtype=torch.int64, device=dev)
+            n_er = (ctypes.c_int64 * K)()
+            if dev_lib.ggd_count_many(arr, K, sh, ctypes.c_void_p(rowoff.data_ptr()), n_er) != 0:
+                raise RuntimeError("ggd_count_many failed")
+            Es = [int(n_er[k]) + n_struct[k] for k in range(K)]
+            total = sum(Es)
+            ub = torch.empty(max(total, 1), dtype=torch.int32, device=dev)
+            vb = torch.empty(max(total, 1), dtype=torch.int32, device=dev)
+            parts = []
+            for k, L in enumerate(Ls):
+                if n_struct[k]:
+                    parts.append(np.ctypeslib.as_array(L.su, shape=(n_struct[k],)))
+                    parts.append(np.ctypeslib.as_array(L.sv, shape=(n_struct[k],)))
+            host = np.concatenate(parts) if parts else np.zeros(1, np.int32)
+            sb = torch.from_numpy(host).to(dev)
+            with torch.cuda.stream(st):
+                rc = dev_lib.ggd_write_many(arr, K, sh, ctypes.c_void_p(rowoff.data_ptr()), n_er,
+                                            ctypes.c_void_p(sb.data_ptr()), ctypes.c_void_p(ub.data_ptr()),
+                                            ctypes.c_void_p(vb.data_ptr()))
+            if rc != 0:
+                raise RuntimeError("ggd_write_many failed")
+        out, at = [], 0
+        for k, L in enumerate(Ls):
+            npl = int(L.n_planted)
+            planted = np.ctypeslib.as_array(L.planted, shape=(max(npl, 1) * 2,))[: 2 * npl].reshape(npl, 2).copy()
+            out.append(DeviceGraph(u=ub[at:at + Es[k]], v=vb[at:at + Es[k]], V=int(L.V), planted=planted,
+                                   n_er=int(n_er[k])))
+            at += Es[k]
+        return out
+    finally:
+        for h in handles:
+            lib.gg_layout_free(h)
 
 
 WORKLOADS = {

@@ -152,9 +152,11 @@ __global__ void struct_write_kernel(const int32_t* su, const int32_t* sv, int64_
 
 Er er_of(const gg_layout* L) { return Er{L->Vc, L->nc, L->thr, L->kER}; }
 
+// A grid for one warp per row: at most 1,024 blocks of 256 threads, so that a graph's rows never
+// queue more blocks than a few waves (work of higher priority sharing the GPU starts between them).
 int grid_for(int64_t warps) {
   const int64_t blocks = (warps * 32 + 255) / 256;
-  return (int)(blocks < 1 ? 1 : (blocks > 65536 ? 65536 : blocks));
+  return (int)(blocks < 1 ? 1 : (blocks > 1024 ? 1024 : blocks));
 }
 
 }  // namespace
@@ -192,6 +194,54 @@ int ggd_write(const gg_layout* L, cudaStream_t s, const int64_t* d_rowoff, int64
   if (A.Vc > 0) er_write_kernel<<<grid_for(A.Vc), 256, 0, s>>>(A, d_rowoff, O);
   if (L->n_struct > 0)
     struct_write_kernel<<<(int)((L->n_struct + 255) / 256), 256, 0, s>>>(d_su, d_sv, L->n_struct, n_er, O);
+  return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
+/* The same for K graphs at once, with one synchronisation: d_rowoff holds the K row-offset
+ * arrays one after the other (Vc_k + 1 entries each) followed by K more entries (the counts,
+ * gathered for one copy to the host); n_er (host, K) receives the ER edge counts.  Returns 0, or
+ * -1 on a CUDA error. */
+int ggd_count_many(const gg_layout* const* Ls, int K, cudaStream_t s, int64_t* d_rowoff, int64_t* n_er) {
+  int64_t at = 0;
+  for (int k = 0; k < K; k++) at += Ls[k]->Vc + 1;
+  int64_t* d_counts = d_rowoff + at;
+  at = 0;
+  for (int k = 0; k < K; k++) {
+    const Er A = er_of(Ls[k]);
+    if (cudaMemsetAsync(d_rowoff + at, 0, sizeof(int64_t), s) != cudaSuccess) return -1;
+    if (A.Vc > 0) {
+      er_count_kernel<<<grid_for(A.Vc), 256, 0, s>>>(A, d_rowoff + at);
+      scan_kernel<<<1, 1024, 0, s>>>(d_rowoff + at, A.Vc);
+    }
+    if (cudaMemcpyAsync(d_counts + k, d_rowoff + at + A.Vc, sizeof(int64_t), cudaMemcpyDeviceToDevice, s) !=
+        cudaSuccess)
+      return -1;
+    at += A.Vc + 1;
+  }
+  if (cudaMemcpyAsync(n_er, d_counts, sizeof(int64_t) * (size_t)K, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      cudaStreamSynchronize(s) != cudaSuccess)
+    return -1;
+  return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
+/* Writes the K graphs one after the other into (u, v) (graph k at edge offset sum_{j<k} E_j,
+ * E_j = n_er[j] + n_struct_j), given ggd_count_many's row offsets and counts; d_struct holds the
+ * structural edges on the device, graph after graph, each as its su then its sv (2 n_struct_k
+ * int32).  Synchronises the stream before returning.  Returns 0, or -1 on a CUDA error. */
+int ggd_write_many(const gg_layout* const* Ls, int K, cudaStream_t s, const int64_t* d_rowoff, const int64_t* n_er,
+                   const int32_t* d_struct, int32_t* u, int32_t* v) {
+  int64_t at_row = 0, at_edge = 0, at_struct = 0;
+  for (int k = 0; k < K; k++) {
+    const gg_layout* L = Ls[k];
+    const int64_t ns = L->n_struct;
+    const int32_t* su = d_struct + at_struct;
+    const int32_t* sv = su + ns;
+    if (ggd_write(L, s, d_rowoff + at_row, n_er[k], su, sv, u + at_edge, v + at_edge) != 0) return -1;
+    at_row += L->Vc + 1;
+    at_edge += n_er[k] + ns;
+    at_struct += 2 * ns;
+  }
+  if (cudaStreamSynchronize(s) != cudaSuccess) return -1;
   return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 

@@ -166,6 +166,50 @@ int64_t bridges_find_batched(bridges_ctx* ctx, struct CUstream_st* stream, const
  * max(2^20, total edges / (4 x SMs))).  Returns BRIDGES_OK or BRIDGES_EINVAL. */
 int32_t bridges_ctx_set_batch_split(bridges_ctx* ctx, int64_t split_edges);
 
+/* The plan of the batched form, per size bucket (what bridges_batch_autotune picks; a caller may
+ * also set one, e.g. from a cache of tuning results).  Graph g belongs to the first bucket b with
+ * V[g] <= vmax[b] (vmax increasing; graphs above the last vmax use the last bucket).  Per bucket:
+ *   group[b] : threads per graph -- 1024 (a whole block), 512 (half a block) or 256 (a quarter);
+ *              0 = the smallest group the graph fits (256 up to 1,024 vertices, 512 up to 2,048,
+ *              1024 above).  A group too small for a graph is raised to the smallest that fits.
+ *   split[b] : graphs with more edges than this are cut into ceil(E / split) contiguous
+ *              partitions (at most 64, Sec. 3's M per graph), each certified by a whole block;
+ *              the block that finishes a graph's last partition merges all of its partitions'
+ *              certificates in one step (merge fan-in = M: one merge level, since every
+ *              certificate is already in device memory); 0 = automatic (the context's
+ *              bridges_ctx_set_batch_split value, else about max(2^20, total edges / (4 x SMs))).
+ *   warm_per_v[b], warm_add[b] : each task certifies its first warm_per_v * V + warm_add edges one
+ *              by one before flattening its union-finds and streaming the rest; both 0 =
+ *              automatic (4V + 2048).
+ * n = 0 means the automatic plan for every graph.  Plans change only scheduling: results are
+ * identical under every plan. */
+#define BRIDGES_BATCH_BUCKETS 8
+typedef struct bridges_batch_plan {
+  int32_t n;
+  int32_t vmax[BRIDGES_BATCH_BUCKETS];
+  int32_t group[BRIDGES_BATCH_BUCKETS];
+  int32_t warm_per_v[BRIDGES_BATCH_BUCKETS];
+  int32_t warm_add[BRIDGES_BATCH_BUCKETS];
+  int64_t split[BRIDGES_BATCH_BUCKETS];
+} bridges_batch_plan;
+
+/* Sets / reads the context's batched plan.  BRIDGES_EINVAL for a malformed plan (n outside
+ * [0, 8], vmax not increasing, a group other than 0, 256, 512, 1024, a negative split or warm-up). */
+int32_t bridges_ctx_set_batch_plan(bridges_ctx* ctx, const bridges_batch_plan* plan);
+int32_t bridges_ctx_get_batch_plan(const bridges_ctx* ctx, bridges_batch_plan* plan);
+
+/* bridges_batch_autotune: tunes the batched plan on a caller's batch (arguments as for
+ * bridges_find_batched): buckets of vertex counts up to 256, 512, 1,024, 2,048 and 4,096, and,
+ * one bucket at a time (largest first, twice over), every group size the bucket's graphs fit,
+ * partition splits of 2^18 to 2^22 edges or automatic, and warm-up prefixes of 2V + 1024, 4V + 2048
+ * and 8V + 2048 edges, each timed over `reps` batched calls (CUDA events on `stream`).  Keeps the
+ * fastest plan in the context and copies it to *best (may be NULL); *best_us (may be NULL) gets
+ * its microseconds per batch.  Graphs above 4,096 vertices are not batched and not tuned.  Uses
+ * the context's batched buffers; returns BRIDGES_OK or an error (the plan is then unchanged). */
+int32_t bridges_batch_autotune(bridges_ctx* ctx, struct CUstream_st* stream, const int32_t* edges_u,
+                               const int32_t* edges_v, const int64_t* edge_off_host, const int32_t* V_host, int32_t G,
+                               int32_t reps, bridges_batch_plan* best, double* best_us);
+
 /* ---------------------------------------------------------------------------------------
  * Serving: a continuous-batching request loop on one GPU (thread-safe).
  *

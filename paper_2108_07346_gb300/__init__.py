@@ -60,6 +60,33 @@ class Opts(ctypes.Structure):
     ]
 
 
+class BatchPlan(ctypes.Structure):
+    """bridges_batch_plan: the batched form's per-bucket plan (see include/bridges.h)."""
+
+    _fields_ = [
+        ("n", ctypes.c_int32),
+        ("vmax", ctypes.c_int32 * 8),
+        ("group", ctypes.c_int32 * 8),
+        ("warm_per_v", ctypes.c_int32 * 8),
+        ("warm_add", ctypes.c_int32 * 8),
+        ("split", ctypes.c_int64 * 8),
+    ]
+
+    def buckets(self):
+        """The plan as a list of per-bucket dicts."""
+        return [{"vmax": self.vmax[b], "group": self.group[b], "split": self.split[b],
+                 "warm_per_v": self.warm_per_v[b], "warm_add": self.warm_add[b]} for b in range(self.n)]
+
+    @classmethod
+    def from_buckets(cls, buckets):
+        p = cls()
+        p.n = len(buckets)
+        for b, d in enumerate(buckets):
+            p.vmax[b], p.group[b], p.split[b] = d["vmax"], d["group"], d["split"]
+            p.warm_per_v[b], p.warm_add[b] = d["warm_per_v"], d["warm_add"]
+        return p
+
+
 _P = ctypes.c_void_p
 _I64 = ctypes.c_int64
 _I32 = ctypes.c_int32
@@ -83,6 +110,10 @@ _SIGS = {
     "bridges_find_noalloc": (_I64, [_P, _P, _P, _I64, _I32, _I32, _P, _P]),
     "bridges_find_batched": (_I64, [_P, _P, _P, _P, _P, _P, _I32, _P, _P]),
     "bridges_ctx_set_batch_split": (_I32, [_P, _I64]),
+    "bridges_ctx_set_batch_plan": (_I32, [_P, ctypes.POINTER(BatchPlan)]),
+    "bridges_ctx_get_batch_plan": (_I32, [_P, ctypes.POINTER(BatchPlan)]),
+    "bridges_batch_autotune": (_I32, [_P, _P, _P, _P, _P, _P, _I32, _I32, ctypes.POINTER(BatchPlan),
+                                      ctypes.POINTER(ctypes.c_double)]),
     "bridges_server_create": (_P, [ctypes.c_int, ctypes.c_size_t, _I32, _I32, ctypes.POINTER(Opts)]),
     "bridges_server_submit": (_I32, [_P, _P, ctypes.POINTER(ctypes.c_uint64)]),
     "bridges_server_poll": (_I32, [_P, ctypes.c_uint64, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_double)]),
@@ -387,6 +418,33 @@ class Context:
         k = self._lib.bridges_ctx_ap_stage_ms_history(self._h, buf, max_calls)
         names = ["warmup", "snapshot", "stream", "mark", "total"]
         return [{names[j]: float(buf[5 * i + j]) for j in range(5)} for i in range(k)]
+
+    def batch_autotune(self, u, v, edge_off, Vs, reps: int = 3, stream=None):
+        """bridges_batch_autotune on a batch (arguments as for find_batched); keeps the tuned plan
+        in the context and returns (per-bucket plan list, microseconds per batch)."""
+        import numpy as np
+
+        u, v = _dev_edges(u, v)
+        eo = np.ascontiguousarray(edge_off, dtype=np.int64)
+        vs = np.ascontiguousarray(Vs, dtype=np.int32)
+        G = int(vs.shape[0])
+        if eo.shape != (G + 1,):
+            raise ValueError("edge_off must have G+1 entries")
+        plan, us = BatchPlan(), ctypes.c_double(0)
+        _check(self._lib.bridges_batch_autotune(self._h, _stream(stream), _ptr(u), _ptr(v), eo.ctypes.data,
+                                                vs.ctypes.data, G, int(reps), ctypes.byref(plan), ctypes.byref(us)),
+               "bridges_batch_autotune")
+        return plan.buckets(), float(us.value)
+
+    def set_batch_plan(self, buckets):
+        """bridges_ctx_set_batch_plan from a per-bucket list (empty: the automatic plan)."""
+        _check(self._lib.bridges_ctx_set_batch_plan(self._h, ctypes.byref(BatchPlan.from_buckets(buckets))),
+               "bridges_ctx_set_batch_plan")
+
+    def get_batch_plan(self):
+        plan = BatchPlan()
+        _check(self._lib.bridges_ctx_get_batch_plan(self._h, ctypes.byref(plan)), "bridges_ctx_get_batch_plan")
+        return plan.buckets()
 
     def set_batch_split(self, split_edges: int):
         _check(self._lib.bridges_ctx_set_batch_split(self._h, int(split_edges)), "bridges_ctx_set_batch_split")

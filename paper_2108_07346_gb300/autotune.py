@@ -1,8 +1,9 @@
-"""Persistent cache of autotuning results (bridges_autotune) keyed by problem size and GPU.
+"""Persistent cache of autotuning results keyed by problem size and GPU (a small JSON file).
 
-Key: (round(log2 V), round(log2 E), number of SMs, device name).  A hit applies the cached plan
-to the context without timing anything; a miss runs bridges_autotune on the caller's input and
-stores the result.  The cache is a small JSON file.
+Single graphs (bridges_autotune): key (round(log2 V), round(log2 E), number of SMs, device
+name).  Batches (bridges_batch_autotune): one entry per size bucket of the batched plan, key
+("batch", the bucket's vertex bound, number of SMs, device name).  A hit applies the cached plan
+to the context without timing anything; a miss tunes on the caller's input and stores the result.
 """
 from __future__ import annotations
 
@@ -28,6 +29,42 @@ def _load(path):
         return {}
 
 
+def _store(path, cache):
+    os.makedirs(os.path.dirname(path) or ".", exist_ok=True)
+    tmp = path + ".tmp"
+    with open(tmp, "w") as f:
+        json.dump(cache, f, indent=1, sort_keys=True)
+    os.replace(tmp, path)
+
+
+BATCH_BUCKETS = (256, 512, 1024, 2048, 4096)  # the vertex bounds bridges_batch_autotune tunes
+
+
+def _batch_key(vmax: int, device) -> str:
+    p = torch.cuda.get_device_properties(device)
+    return f"batch:{vmax}:{p.multi_processor_count}:{p.name}"
+
+
+def tune_batched(ctx, u, v, edge_off, Vs, path: str = DEFAULT_PATH, reps: int = 3, refresh: bool = False):
+    """Applies the cached batched plan to `ctx` when every size bucket the batch's graphs fall in
+    is cached for this GPU; otherwise tunes on the batch (bridges_batch_autotune) and stores each
+    bucket.  Returns (per-bucket plan list, hit)."""
+    present = sorted({next((b for b in BATCH_BUCKETS if int(x) <= b), None) for x in Vs} - {None})
+    cache = _load(path)
+    keys = {b: _batch_key(b, ctx.device) for b in BATCH_BUCKETS}
+    if not refresh and present and all(keys[b] in cache for b in present):
+        plan = [dict(cache[keys[b]], vmax=b) if keys[b] in cache else
+                {"vmax": b, "group": 0, "split": 0, "warm_per_v": 0, "warm_add": 0} for b in BATCH_BUCKETS]
+        ctx.set_batch_plan(plan)
+        return plan, True
+    plan, us = ctx.batch_autotune(u, v, edge_off, Vs, reps=reps)
+    for d in plan:
+        if d["vmax"] in present:
+            cache[keys[d["vmax"]]] = {k: d[k] for k in ("group", "split", "warm_per_v", "warm_add")}
+    _store(path, cache)
+    return plan, False
+
+
 def tune(ctx, u, v, V: int, path: str = DEFAULT_PATH, reps: int = 3, refresh: bool = False):
     """Applies the cached plan for this size bucket to `ctx`, tuning (and caching) on a miss.
     Returns (plan dict, hit)."""
@@ -40,9 +77,5 @@ def tune(ctx, u, v, V: int, path: str = DEFAULT_PATH, reps: int = 3, refresh: bo
         return plan, True
     plan = ctx.autotune(u, v, V, reps=reps)
     cache[key] = plan
-    os.makedirs(os.path.dirname(path) or ".", exist_ok=True)
-    tmp = path + ".tmp"
-    with open(tmp, "w") as f:
-        json.dump(cache, f, indent=1, sort_keys=True)
-    os.replace(tmp, path)
+    _store(path, cache)
     return plan, False

@@ -744,14 +744,31 @@ int64_t ensure_batched(bridges_ctx* c, cudaStream_t s, int64_t ntasks, int64_t G
 
 namespace bridges {
 
-// Splits graphs with many edges into partitions (slot offsets filled in) and orders the tasks
-// largest first.  Returns the certificate slot words needed.
-int64_t plan_batch_tasks(std::vector<BatchTask>& graphs, int64_t split, std::vector<BatchTask>& tasks) {
+// The bucket of a graph with V vertices under plan P (-1: the automatic plan).
+static int batch_bucket(const bridges_batch_plan& P, int32_t V) {
+  if (P.n <= 0) return -1;
+  for (int b = 0; b < P.n; b++)
+    if (V <= P.vmax[b]) return b;
+  return P.n - 1;
+}
+
+// Applies the context's batched plan (see plan_batch_tasks in ctx.h).
+int64_t plan_batch_tasks(const bridges_ctx* c, std::vector<BatchTask>& graphs, int64_t total_e,
+                         std::vector<BatchTask>& tasks) {
+  const bridges_batch_plan& P = c->bplan;
+  const int64_t auto_split = default_split(c, total_e);
   int64_t slot = 0;
   tasks.clear();
   for (const BatchTask& g : graphs) {
+    const int b = batch_bucket(P, g.V);
+    const int64_t split = b >= 0 && P.split[b] > 0 ? P.split[b] : auto_split;
     const int64_t E = g.hi - g.lo;
     const int32_t np = (int32_t)std::min<int64_t>(64, std::max<int64_t>(1, (E + split - 1) / split));
+    // the plan's group, raised to the smallest one the task fits (class 0 is the largest group)
+    int cls = batch_min_class(g.V, np);
+    if (b >= 0 && P.group[b] > 0) cls = std::min(cls, P.group[b] >= 1024 ? 0 : (P.group[b] >= 512 ? 1 : 2));
+    int64_t warm = 4LL * g.V + 2048;  // measured on the batched workload against 2V + 1024, 8V + 2048, 16V + 2048
+    if (b >= 0 && (P.warm_per_v[b] > 0 || P.warm_add[b] > 0)) warm = (int64_t)P.warm_per_v[b] * g.V + P.warm_add[b];
     for (int32_t p = 0; p < np; p++) {
       BatchTask t = g;
       t.lo = g.lo + E * p / np;
@@ -759,6 +776,8 @@ int64_t plan_batch_tasks(std::vector<BatchTask>& graphs, int64_t split, std::vec
       t.slot = np > 1 ? slot + (int64_t)p * (2 + 2 * (int64_t)g.V) : 0;
       t.part = p;
       t.nparts = np;
+      t.cls = cls;
+      t.warm = warm;
       tasks.push_back(t);
     }
     if (np > 1) slot += (int64_t)np * (2 + 2 * (int64_t)g.V);
@@ -882,7 +901,7 @@ extern "C" int64_t bridges_find_batched(bridges_ctx* c, struct CUstream_st* stre
     t.V = Vs[g];
     graphs.push_back(t);
   }
-  const int64_t slots = plan_batch_tasks(graphs, default_split(c, total_e), tasks);
+  const int64_t slots = plan_batch_tasks(c, graphs, total_e, tasks);
   int64_t rc = launch_batch_tasks(c, s, tasks, (int32_t)graphs.size(), slots);
   if (rc) return rc;
   for (int32_t g : large) {
@@ -896,6 +915,119 @@ extern "C" int64_t bridges_find_batched(bridges_ctx* c, struct CUstream_st* stre
 extern "C" int32_t bridges_ctx_set_batch_split(bridges_ctx* c, int64_t split_edges) {
   if (!c || split_edges < 0) return BRIDGES_EINVAL;
   c->b_split_edges = split_edges;
+  return BRIDGES_OK;
+}
+
+extern "C" int32_t bridges_ctx_set_batch_plan(bridges_ctx* c, const bridges_batch_plan* P) {
+  if (!c || !P || P->n < 0 || P->n > BRIDGES_BATCH_BUCKETS) return BRIDGES_EINVAL;
+  for (int b = 0; b < P->n; b++) {
+    const int32_t g = P->group[b];
+    if ((b > 0 && P->vmax[b] <= P->vmax[b - 1]) || P->vmax[b] < 0 || (g != 0 && g != 256 && g != 512 && g != 1024) ||
+        P->split[b] < 0 || P->warm_per_v[b] < 0 || P->warm_add[b] < 0)
+      return BRIDGES_EINVAL;
+  }
+  c->bplan = *P;
+  return BRIDGES_OK;
+}
+
+extern "C" int32_t bridges_ctx_get_batch_plan(const bridges_ctx* c, bridges_batch_plan* P) {
+  if (!c || !P) return BRIDGES_EINVAL;
+  *P = c->bplan;
+  return BRIDGES_OK;
+}
+
+// Batched autotuner: coordinate descent over the buckets' group, split and warm-up choices,
+// each candidate timed over whole batched calls (a bucket's choices interact with the others'
+// only through the shared queue, so one bucket is changed at a time, largest first, twice over).
+extern "C" int32_t bridges_batch_autotune(bridges_ctx* c, struct CUstream_st* stream, const int32_t* u,
+                                          const int32_t* v, const int64_t* edge_off, const int32_t* Vs, int32_t G,
+                                          int32_t reps, bridges_batch_plan* best, double* best_us) {
+  if (!c || G <= 0 || !edge_off || !Vs) return BRIDGES_EINVAL;
+  int64_t total_out = 0;
+  for (int32_t g = 0; g < G; g++) {
+    if (Vs[g] < 0 || Vs[g] > (1 << 30) || edge_off[g] < 0 || edge_off[g + 1] < edge_off[g]) return BRIDGES_EINVAL;
+    total_out += 2 * (int64_t)std::max(Vs[g] - 1, 0);
+  }
+  if (edge_off[G] > 0 && (!u || !v)) return BRIDGES_EINVAL;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  if (cudaSetDevice(c->device) != cudaSuccess) return (int32_t)cuda_fail(cudaGetLastError());
+  if (reps <= 0) reps = 3;
+  int32_t* out = nullptr;
+  int64_t* cnt = nullptr;
+  if (cudaMalloc(&out, sizeof(int32_t) * (size_t)std::max<int64_t>(total_out, 1)) != cudaSuccess ||
+      cudaMalloc(&cnt, sizeof(int64_t) * (size_t)G) != cudaSuccess) {
+    cudaGetLastError();
+    if (out) cudaFree(out);
+    return BRIDGES_ENOMEM;
+  }
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  const bridges_batch_plan saved = c->bplan;
+  int32_t rc = BRIDGES_OK;
+  // time of one batched call under plan P (ms), or a negative value on error
+  auto time_plan = [&](const bridges_batch_plan& P) -> float {
+    c->bplan = P;
+    int64_t r = bridges_find_batched(c, stream, u, v, edge_off, Vs, G, out, cnt);  // untimed: first use
+    cudaEventRecord(e0, s);
+    for (int i = 0; i < reps && !r; i++) r = bridges_find_batched(c, stream, u, v, edge_off, Vs, G, out, cnt);
+    cudaEventRecord(e1, s);
+    if (r || cudaEventSynchronize(e1) != cudaSuccess) {
+      rc = r ? (int32_t)r : (int32_t)BRIDGES_ECUDA;
+      return -1.0f;
+    }
+    float ms = 0;
+    cudaEventElapsedTime(&ms, e0, e1);
+    return ms / reps;
+  };
+  bridges_batch_plan cur{};
+  const int32_t vmax[5] = {256, 512, 1024, 2048, kBatchVmax};
+  cur.n = 5;
+  for (int b = 0; b < 5; b++) cur.vmax[b] = vmax[b];
+  std::vector<int> present(5, 0);
+  for (int32_t g = 0; g < G; g++)
+    if (Vs[g] <= kBatchVmax) present[batch_bucket(cur, Vs[g])] = 1;
+  float best_ms = time_plan(cur);
+  for (int pass = 0; pass < 2 && rc == BRIDGES_OK; pass++) {
+    for (int b = 4; b >= 0 && rc == BRIDGES_OK; b--) {
+      if (!present[b]) continue;
+      auto consider = [&](const bridges_batch_plan& P) {
+        const float ms = time_plan(P);
+        if (ms >= 0 && ms < best_ms) {
+          best_ms = ms;
+          cur = P;
+        }
+      };
+      for (int32_t grp : {1024, 512, 256}) {  // groups the bucket's largest graph fits
+        if ((grp == 256 && vmax[b] > kBatchQuarterVmax) || (grp == 512 && vmax[b] > kBatchHalfVmax)) continue;
+        bridges_batch_plan P = cur;
+        P.group[b] = grp;
+        if (P.group[b] != cur.group[b]) consider(P);
+      }
+      for (int64_t sp : {(int64_t)0, (int64_t)1 << 18, (int64_t)1 << 19, (int64_t)1 << 20, (int64_t)1 << 21,
+                         (int64_t)1 << 22}) {
+        bridges_batch_plan P = cur;
+        P.split[b] = sp;
+        if (P.split[b] != cur.split[b]) consider(P);
+      }
+      const int32_t warms[3][2] = {{4, 2048}, {2, 1024}, {8, 2048}};
+      for (const auto& w : warms) {
+        bridges_batch_plan P = cur;
+        P.warm_per_v[b] = w[0];
+        P.warm_add[b] = w[1];
+        if (P.warm_per_v[b] != cur.warm_per_v[b] || P.warm_add[b] != cur.warm_add[b]) consider(P);
+      }
+    }
+  }
+  cudaStreamSynchronize(s);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaFree(out);
+  cudaFree(cnt);
+  c->bplan = rc ? saved : cur;
+  if (rc) return rc;
+  if (best) *best = cur;
+  if (best_us) *best_us = (double)best_ms * 1000.0;
   return BRIDGES_OK;
 }
 

@@ -404,9 +404,10 @@ __device__ __forceinline__ void s_certify_vec(const Grp<NT>& G, const Smem& S, c
 // and the rest streams through the vector loop.
 template <int NT, int VM>
 __device__ void s_certify_range(const Grp<NT>& G, const Smem& S, const int32_t* __restrict__ u, const int32_t* __restrict__ v,
-                                int64_t lo, int64_t hi, int32_t V, int32_t* n1, int32_t* n2, int32_t* err) {
-  // 4V + 2048: measured on the batched workload against 2V + 1024, 8V + 2048 and 16V + 2048
-  const int64_t warm = min(hi - lo, (int64_t)4 * V + 2048);
+                                int64_t lo, int64_t hi, int64_t warm_edges, int32_t V, int32_t* n1, int32_t* n2,
+                                int32_t* err) {
+  // the task's prefix (the host's plan: 4V + 2048 unless tuned)
+  const int64_t warm = min(hi - lo, max(warm_edges, (int64_t)0));
   s_certify_scalar(G, S, u, v, lo, lo + warm, V, n1, n2, err);
   lo += warm;
   if (lo >= hi) return;
@@ -736,7 +737,7 @@ __device__ void run_task(const BatchArgs& A, const BatchTask& T, const Smem& S, 
     gs.err = 0;
   }
   G.sync();
-  s_certify_range<NT, VM>(G, S, T.u, T.v, T.lo, T.hi, V, &gs.n1, &gs.n2, &gs.err);
+  s_certify_range<NT, VM>(G, S, T.u, T.v, T.lo, T.hi, T.warm, V, &gs.n1, &gs.n2, &gs.err);
   G.sync();
   int32_t nt = min(gs.n1, V), nx = min(gs.n2, V);
   if (T.nparts > 1) {

@@ -22,6 +22,9 @@ struct BatchTask {
   int32_t part;      // partition index within the graph
   int32_t nparts;    // partitions of the graph
   int32_t V;         // vertices of the graph
+  int32_t cls;       // group that runs it: 0 a whole block, 1 a half block, 2 a quarter block
+  int32_t pad;
+  int64_t warm;      // edges certified one by one before the union-finds are flattened
 };
 
 // Everything the kernel reads, in device memory so a captured CUDA graph stays valid when the
@@ -39,12 +42,16 @@ struct BatchArgs {
   int64_t slot_words;  // capacity of slots (u32)
 };
 
-// Which group a task needs: 0 a whole block (more than kBatchHalfVmax vertices, or a partition of
-// a graph: partitions merge through the slots), 1 a half block, 2 a quarter block.
-inline int batch_task_class(const BatchTask& t) {
-  if (t.V > kBatchHalfVmax || t.nparts > 1) return 0;
-  return t.V > kBatchQuarterVmax ? 1 : 2;
+// The smallest group a task fits: 0 a whole block (more than kBatchHalfVmax vertices, or a
+// partition of a graph: partitions merge through the slots), 1 a half block, 2 a quarter block.
+inline int batch_min_class(int32_t V, int32_t nparts) {
+  if (V > kBatchHalfVmax || nparts > 1) return 0;
+  return V > kBatchQuarterVmax ? 1 : 2;
 }
+
+// The group a planned task runs on (its cls, which the plan may set to a larger group than the
+// smallest it fits; never a smaller one).
+inline int batch_task_class(const BatchTask& t) { return t.cls; }
 
 size_t batched_smem_bytes();
 // Launches the persistent kernel (one block per SM) reading its arguments from *dev_args.

@@ -49,6 +49,7 @@ struct bridges_ctx {
   cudaEvent_t b_done_ev[2]{};
   int b_next = 0;                // the staging copy the next batch fills
   int64_t b_split_edges = 0;     // partition graphs with more edges than this (0: automatic)
+  bridges_batch_plan bplan{};    // per-bucket plan of the batched form (n = 0: automatic)
   // pipelined host input: a copy stream and one event per chunk copied
   static constexpr int kMaxChunks = 64;
   cudaStream_t copy_stream = nullptr;
@@ -58,9 +59,12 @@ struct bridges_ctx {
 
 namespace bridges {
 
-// Splits graphs (whole-graph tasks) with more than `split` edges into partitions, fills in the
-// certificate slots and orders the tasks largest first; returns the slot words needed.
-int64_t plan_batch_tasks(std::vector<BatchTask>& graphs, int64_t split, std::vector<BatchTask>& tasks);
+// Applies the context's batched plan to whole-graph tasks: splits graphs with many edges into
+// partitions (certificate slots filled in), picks each task's group and warm-up prefix, and
+// orders the tasks by group, largest first; returns the slot words needed.  total_e: the edges
+// of every graph of the batch (the automatic split depends on it).
+int64_t plan_batch_tasks(const bridges_ctx* c, std::vector<BatchTask>& graphs, int64_t total_e,
+                         std::vector<BatchTask>& tasks);
 // One persistent launch over `tasks` (G graphs) on stream s, through the context's CUDA graph.
 int64_t launch_batch_tasks(bridges_ctx* c, cudaStream_t s, const std::vector<BatchTask>& tasks, int32_t G,
                            int64_t slot_words);

@@ -120,7 +120,7 @@ void admit(bridges_server* S) {
       }
       if (graphs.empty()) return;  // only large requests wait, and the head does not fit yet
       sl.reserved = 0;
-      const int64_t slot_words = plan_batch_tasks(graphs, default_split(sl.ctx, total_e), tasks);
+      const int64_t slot_words = plan_batch_tasks(sl.ctx, graphs, total_e, tasks);
       rc = launch_batch_tasks(sl.ctx, sl.stream, tasks, (int32_t)graphs.size(), slot_words);
       S->stats[1]++;
     }
@@ -213,11 +213,19 @@ bridges_server* bridges_server_create(int device, size_t mem_budget_bytes, int32
     return nullptr;
   }
   S->slots.resize(max_slots);
+  // requests run at the device's highest stream priority: when other work of the process shares
+  // the GPU (ingest of the next requests, say), the block scheduler starts the requests' blocks
+  // first as SMs free up
+  int prio_low = 0, prio_high = 0;
+  if (cudaDeviceGetStreamPriorityRange(&prio_low, &prio_high) != cudaSuccess) {
+    cudaGetLastError();
+    prio_high = 0;
+  }
   bool ok = true;
   for (SrvSlot& sl : S->slots) {
     sl.ctx = bridges_ctx_create(device, 0, opts);
     ok = ok && sl.ctx;
-    ok = ok && cudaStreamCreateWithFlags(&sl.stream, cudaStreamNonBlocking) == cudaSuccess;
+    ok = ok && cudaStreamCreateWithPriority(&sl.stream, cudaStreamNonBlocking, prio_high) == cudaSuccess;
     ok = ok && cudaEventCreateWithFlags(&sl.ev, cudaEventDisableTiming) == cudaSuccess;
     ok = ok && cudaMalloc(&sl.d_counts, sizeof(int64_t) * (size_t)max_batch) == cudaSuccess;
     ok = ok && cudaMallocHost(&sl.h_counts, sizeof(int64_t) * (size_t)max_batch) == cudaSuccess;

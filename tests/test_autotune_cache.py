@@ -67,3 +67,45 @@ def test_unreadable_cache_counts_as_empty(tmp_path):
     plan, hit = autotune.tune(c, *edges(100), 50, path=str(path))
     assert not hit and c.tuned == 1
     assert list(json.load(open(path)).values()) == [plan]
+
+
+class StandInBatchContext:
+    device = "cuda:0"
+
+    def __init__(self):
+        self.tuned = 0
+        self.applied = None
+
+    def batch_autotune(self, u, v, edge_off, Vs, reps=3):
+        self.tuned += 1
+        plan = [{"vmax": b, "group": 1024 if b > 1024 else 512, "split": 1 << 20, "warm_per_v": 2,
+                 "warm_add": 1024 * self.tuned} for b in autotune.BATCH_BUCKETS]
+        return plan, 1234.0
+
+    def set_batch_plan(self, buckets):
+        self.applied = buckets
+
+
+def test_batched_plan_cached_per_bucket(tmp_path):
+    path = str(tmp_path / "cache.json")
+    u, v = edges(100)
+    ctx = StandInBatchContext()
+    plan, hit = autotune.tune_batched(ctx, u, v, [0, 50, 100], [300, 3000], path=path)
+    assert not hit and ctx.tuned == 1
+    stored = json.load(open(path))
+    # only the buckets the batch's graphs fall in (V = 300 -> 512, V = 3000 -> 4096) are stored
+    assert sorted(k.split(":")[1] for k in stored) == ["4096", "512"]
+    assert all(k.endswith(":152:stand-in GPU") and k.startswith("batch:") for k in stored)
+    # a batch within the cached buckets hits and applies the stored entries without tuning
+    ctx2 = StandInBatchContext()
+    plan2, hit2 = autotune.tune_batched(ctx2, u, v, [0, 100], [500], path=path)
+    assert hit2 and ctx2.tuned == 0
+    applied = {d["vmax"]: d for d in ctx2.applied}
+    assert applied[512]["warm_add"] == 1024 and applied[512]["group"] == 512
+    assert applied[256]["group"] == 0  # uncached buckets stay automatic
+    # a graph in an uncached bucket (V = 100 -> 256) misses and tunes again
+    plan3, hit3 = autotune.tune_batched(ctx2, u, v, [0, 50, 100], [100, 500], path=path)
+    assert not hit3 and ctx2.tuned == 1
+    # refresh tunes even when everything is cached
+    _, hit4 = autotune.tune_batched(ctx2, u, v, [0, 100], [500], path=path, refresh=True)
+    assert not hit4 and ctx2.tuned == 2

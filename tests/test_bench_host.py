@@ -41,12 +41,12 @@ def test_request_stream_hands_out_requests_in_order(monkeypatch):
 
     import graphgen
 
-    def fake(spec, dev, stream=None):
+    def fake(specs, dev, stream=None):
         _time.sleep(random.random() * 0.002)
-        return SimpleNamespace(E=int(spec.core_vertices), seed=spec.seed)
+        return [SimpleNamespace(E=int(spec.core_vertices), seed=spec.seed) for spec in specs]
 
-    monkeypatch.setattr(graphgen, "generate_device", fake)
-    rs = bench.RequestStream("cpu", 10, 200, ahead=16, max_bytes=1 << 40, threads=4)
+    monkeypatch.setattr(graphgen, "generate_device_many", fake)
+    rs = bench.RequestStream("cpu", 10, 200, ahead=16, max_bytes=1 << 40, threads=3, batch=5)
     got = []
     for _ in range(200):
         i, g = rs.get()
@@ -59,10 +59,10 @@ def test_request_stream_hands_out_requests_in_order(monkeypatch):
 def test_request_stream_reports_a_failed_generation(monkeypatch):
     import graphgen
 
-    def boom(spec, dev, stream=None):
+    def boom(specs, dev, stream=None):
         raise ValueError("no device")
 
-    monkeypatch.setattr(graphgen, "generate_device", boom)
+    monkeypatch.setattr(graphgen, "generate_device_many", boom)
     rs = bench.RequestStream("cpu", 0, 8, threads=2)
     with pytest.raises(RuntimeError, match="request generation failed"):
         rs.get()

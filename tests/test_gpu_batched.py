@@ -157,3 +157,46 @@ def test_back_to_back_batches_on_two_streams(ctx):
         for g, (u, v, V) in enumerate(graphs):
             n = int(counts[g])
             assert out[out_off[g]: out_off[g] + 2 * n].reshape(n, 2).tolist() == oracle.dfs_bridges(u, v, V).tolist()
+
+
+def _tuning_batch():
+    """Graphs of every size bucket: the batched workload's specs, a few dense graphs large
+    enough to be split into partitions under small split values, and sparse multigraphs."""
+    graphs = []
+    for i in range(160):
+        g = graphgen.generate(graphgen.workload_spec("batched", 13, i))
+        graphs.append((np.array(g.u), np.array(g.v), g.V))
+    for i, V in enumerate((3000, 4096)):
+        g = graphgen.generate(graphgen.Spec(seed=70 + i, n_clusters=2, core_vertices=V - 4, p=0.6, n_pendant=4))
+        graphs.append((np.array(g.u), np.array(g.v), g.V))
+    for t in range(20):
+        V = 40 + 97 * t
+        u, v = graphgen.random_multigraph(880 + t, V, 3 * V)
+        graphs.append((u, v, V))
+    return graphs
+
+
+def test_tuned_plan_gives_the_oracle_graph_by_graph(cuda_lib):
+    """bridges_batch_autotune changes scheduling only: under the tuned plan, and under a hand-set
+    plan that forces every choice away from the automatic one (whole blocks for small graphs,
+    partitions of 2^12 edges, the shortest warm-up), every graph's bridges equal the oracle's."""
+    graphs = _tuning_batch()
+    refs = [oracle.dfs_bridges(u, v, V).tolist() for u, v, V in graphs]
+    ctx = cuda_lib.Context(device="cuda:0")
+    u, v, off, Vs = concat(graphs)
+    plan, us = ctx.batch_autotune(torch.from_numpy(u).cuda(), torch.from_numpy(v).cuda(), off, Vs, reps=2)
+    assert us > 0 and [d["vmax"] for d in plan] == [256, 512, 1024, 2048, 4096]
+    assert ctx.get_batch_plan() == plan
+    for got, ref in zip(run_batch(ctx, graphs), refs):
+        assert got.tolist() == ref
+    forced = [{"vmax": b, "group": 1024, "split": 1 << 12, "warm_per_v": 1, "warm_add": 1}
+              for b in (256, 512, 1024, 2048, 4096)]
+    ctx.set_batch_plan(forced)
+    for got, ref in zip(run_batch(ctx, graphs), refs):
+        assert got.tolist() == ref
+    quarter = [{"vmax": 4096, "group": 256, "split": 0, "warm_per_v": 8, "warm_add": 2048}]  # raised where needed
+    ctx.set_batch_plan(quarter)
+    for got, ref in zip(run_batch(ctx, graphs), refs):
+        assert got.tolist() == ref
+    with pytest.raises(cuda_lib.BridgesError):
+        ctx.set_batch_plan([{"vmax": 4096, "group": 300, "split": 0, "warm_per_v": 0, "warm_add": 0}])

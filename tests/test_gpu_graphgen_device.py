@@ -32,3 +32,15 @@ def test_device_graph_equals_host_graph(name, spec):
     assert d.V == h.V and d.E == h.E and d.n_er == h.n_er
     assert np.array_equal(d.u.cpu().numpy(), h.u) and np.array_equal(d.v.cpu().numpy(), h.v)
     assert np.array_equal(d.planted, h.planted)
+
+
+def test_many_at_once_equal_host_graphs():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    specs_ = [s for _, s in specs()][3:]
+    many = graphgen.generate_device_many(specs_, "cuda:0")
+    for spec, d in zip(specs_, many):
+        h = graphgen.generate(spec)
+        assert d.V == h.V and d.E == h.E
+        assert np.array_equal(d.u.cpu().numpy(), h.u) and np.array_equal(d.v.cpu().numpy(), h.v)
+        assert np.array_equal(d.planted, h.planted)
