@@ -42,9 +42,13 @@ UNIT = "GE/s"
 # DRAM bytes (read + write) per streamed edge, from the ncu captures of the large workload's
 # streaming kernels; each is valid only for the kernel sources it was measured on (hash of those
 # sources).
-#   forest pass, M = 1: 9.295 GB read + 7.2 MB written for 1,072,703,284 streamed edges
+#   forest pass, M = 1, at density 1/8 (268 M edges, 2.1 GB: a capture of a few GB, scaled to a
+#   full launch by its streamed edges; 8.30 B per edge at density 1/16 as well):
+#   2.2191 GB read + 5.9 MB written for 267,444,294 streamed edges
 #   block pass stream: 9.512 GB read + 11.0 MB written for 1,073,547,340 streamed edges
-TRAFFIC = {"certify_sha": "7e50d053b42e91d5", "bytes_per_edge": 8.6808}
+TRAFFIC = {"certify_sha": "7e50d053b42e91d5", "bytes_per_edge": 8.3197,
+           "source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of the forest pass at density 1/8 "
+                     "(268 M edges), scaled to a full launch by its streamed edges"}
 AP_TRAFFIC = {"blocks_sha": "1bb83ede0c0a1fe3", "bytes_per_edge": 8.8607}
 FUSED_TRAFFIC = {"blocks_sha": "1bb83ede0c0a1fe3", "bytes_per_edge": 8.5686}
 
@@ -474,7 +478,8 @@ def run_native(args, world, rank, local):
         if TRAFFIC["certify_sha"] == certify_sha() and TRAFFIC["bytes_per_edge"]:
             traffic = TRAFFIC["bytes_per_edge"] * forest_edges
         roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": traffic, "kernel": "leaf_kernel<cache, vec> (partition forest pass)",
+                "traffic": traffic, "traffic_source": TRAFFIC["source"] if traffic else None,
+                "kernel": "leaf_kernel<cache, vec> (partition forest pass)",
                 "algorithmic_bytes": 8 * forest_edges, "peak_kind": peak_kind,
                 "frac_of_nominal_7900": achieved / 7900.0,
                 "stage_ms_mean": {k: statistics.mean(h[k] for h in hist) for k in hist[0]}}
