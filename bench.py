@@ -43,14 +43,17 @@ UNIT = "GE/s"
 # streaming kernels; each is valid only for the kernel sources it was measured on (hash of those
 # sources).
 #   forest pass, M = 1, at density 1/8 (268 M edges, 2.1 GB: a capture of a few GB, scaled to a
-#   full launch by its streamed edges; 8.30 B per edge at density 1/16 as well):
-#   2.2191 GB read + 5.9 MB written for 267,444,294 streamed edges
-#   block pass stream: 9.512 GB read + 11.0 MB written for 1,073,547,340 streamed edges
-TRAFFIC = {"certify_sha": "7e50d053b42e91d5", "bytes_per_edge": 8.3197,
+#   full launch by its streamed edges): 2.1402 GB read + 5.6 MB written for 267,444,294 streamed
+#   edges; block pass stream and fused stream (articulation points), the same density:
+#   2.1471 GB read + 7.5 MB written, and 2.1404 GB read + 0.4 MB written, for 267,444,294
+#   streamed edges each
+TRAFFIC = {"certify_sha": "955904b8335e32d4", "bytes_per_edge": 8.0231,
            "source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of the forest pass at density 1/8 "
                      "(268 M edges), scaled to a full launch by its streamed edges"}
-AP_TRAFFIC = {"blocks_sha": "1bb83ede0c0a1fe3", "bytes_per_edge": 8.8607}
-FUSED_TRAFFIC = {"blocks_sha": "1bb83ede0c0a1fe3", "bytes_per_edge": 8.5686}
+AP_TRAFFIC = {"blocks_sha": "4eb6347dc917184f", "bytes_per_edge": 8.0562,
+              "source": "ncu dram bytes of the block pass stream at density 1/8, scaled by streamed edges"}
+FUSED_TRAFFIC = {"blocks_sha": "4eb6347dc917184f", "bytes_per_edge": 8.0046,
+                 "source": "ncu dram bytes of the fused stream at density 1/8, scaled by streamed edges"}
 
 
 def peaks():
@@ -505,6 +508,21 @@ def run_native(args, world, rank, local):
         e2e = {"value": whole_job_rate(E * ks, world, dt), "unit": UNIT, "h2d_bytes_per_step": 8 * E,
                "d2h_bytes_per_step": 8 + 8 * nb, "steps": ks, "ms_per_step": dt / ks * 1e3}
         del ctx_h
+        # the same call with the kernels reading the pinned host buffers in place (opts.host_read):
+        # no device copy of the edges at all
+        ctx_r = pb.Context(device=dev, M=args.M, host_read=True)
+        ctx_r.find_host(hu, hv, V, args.M, out=hout)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(ks):
+            nr = ctx_r.find_host(hu, hv, V, args.M, out=hout).shape[0]
+        torch.cuda.synchronize()
+        dtr = reduce_max(time.perf_counter() - t0, dev)
+        e2e["in_place"] = {"value": whole_job_rate(E * ks, world, dtr), "unit": UNIT, "steps": ks,
+                           "ms_per_step": dtr / ks * 1e3, "bridges_equal_planted": nr == len(g.planted),
+                           "note": "kernels read the pinned, mapped host buffers over the host link "
+                                   "(opts.host_read); the device holds no copy of the edges"}
+        del ctx_r
 
     cpu = cpu_all = None
     if rank == 0 and world == 1 and not args.no_cpu:
@@ -644,10 +662,11 @@ def run_articulation(args, world, rank, local):
     kernels = {}
     fused = cfg.get("ap_fused", 0) == 1
     if fused and ap_hist and br_hist:
-        # one stream over all E edges: the warm-up prefix for the classes, the rest for both
+        # one read of the list: the warm-up prefix (its own launch), then the fused stream over the
+        # other E - warm edges for both the certificate and the classes
         fs_bpe = FUSED_TRAFFIC["bytes_per_edge"] if FUSED_TRAFFIC["blocks_sha"] == blocks_sha() else None
-        kernels = {"fused stream (ap_fused_kernel<forest, vec>)": (statistics.mean(h["stream"] for h in ap_hist), E,
-                                                                  fs_bpe)}
+        kernels = {"fused stream (ap_fused_kernel<forest, vec>)": (statistics.mean(h["stream"] for h in ap_hist),
+                                                                  E - (warm or 0), fs_bpe)}
     elif warm is not None and ap_warm is not None and ap_hist and br_hist:
         fe = E - cfg["M"] * warm
         se = E - ap_warm

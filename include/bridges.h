@@ -50,7 +50,8 @@ typedef enum bridges_status {
   BRIDGES_ETIMEDOUT = -5, /* a bounded device-side wait gave up */
   BRIDGES_EAGAIN = -6,    /* request can never fit the server's memory budget */
   BRIDGES_EBUSY = -7,     /* result not ready yet */
-  BRIDGES_EINTERNAL = -8  /* an internal capacity invariant failed (a bug) */
+  BRIDGES_EINTERNAL = -8, /* an internal capacity invariant failed (a bug) */
+  BRIDGES_ECANCELED = -9  /* a server request withdrawn by bridges_server_cancel */
 } bridges_status;
 
 /* Tuning options.  Zero-initialise and set what you need; zero / negative fields mean
@@ -246,6 +247,11 @@ int32_t bridges_server_poll(bridges_server* srv, uint64_t ticket, int64_t* count
 /* As poll, but waits up to timeout_ms; BRIDGES_ETIMEDOUT if the request is still not done. */
 int32_t bridges_server_wait(bridges_server* srv, uint64_t ticket, int64_t timeout_ms, int64_t* count,
                             double* latency_ms);
+/* Withdraws a request that is still queued (not yet launched): it completes at once with count
+ * BRIDGES_ECANCELED (poll / wait then release its ticket as for any request), and the caller may
+ * reuse its buffers right away.  BRIDGES_EBUSY if it is already running or done (it then completes
+ * normally); BRIDGES_EINVAL for an unknown or already released ticket. */
+int32_t bridges_server_cancel(bridges_server* srv, uint64_t ticket);
 /* [0] completed, [1] batched launches, [2] single-graph launches, [3] most requests in flight at
  * once, [4] failed launches, [5] queued now.  Returns the number of values written. */
 int32_t bridges_server_stats(bridges_server* srv, int64_t* vals, int32_t n);
@@ -409,7 +415,7 @@ int32_t bridges_ctx_ap_stage_ms_history(const bridges_ctx* ctx, float* ms, int32
 /* ---------------------------------------------------------------------------------------
  * Autotuning.
  * bridges_autotune: times candidate plans on the given device-resident input (M in
- * {1,2,4,8,16,32}, fan-in 2 or M, warm-up 0.6/0.8/1.2/2.0 x V ln V edges, block 1024 or 512; `reps`
+ * {1,2,4,8,16,32}, fan-in 2 or M, warm-up 0.6/0.8/1.2/2.0 x V ln V edges, block 1024, 768 or 512; `reps`
  * timed calls each, CUDA events on `stream`), then the warm-up launch's block size (128 to 1024)
  * for the winner, and keeps the fastest in the context's options (read them back whole with
  * bridges_ctx_get_opts).  best[0..4] receives M, fan-in, warm-up edges, block size and

@@ -33,6 +33,7 @@ STATUS = {
     -6: "BRIDGES_EAGAIN",
     -7: "BRIDGES_EBUSY",
     -8: "BRIDGES_EINTERNAL",
+    -9: "BRIDGES_ECANCELED",
 }
 
 
@@ -120,6 +121,7 @@ _SIGS = {
     "bridges_server_wait": (_I32, [_P, ctypes.c_uint64, _I64, ctypes.POINTER(ctypes.c_int64),
                                    ctypes.POINTER(ctypes.c_double)]),
     "bridges_server_stats": (_I32, [_P, ctypes.POINTER(ctypes.c_int64), _I32]),
+    "bridges_server_cancel": (_I32, [_P, ctypes.c_uint64]),
     "bridges_server_destroy": (None, [_P]),
     "bridges_autotune": (_I32, [_P, _P, _P, _P, _I64, _I32, _I32, ctypes.POINTER(ctypes.c_int64)]),
     "bridges_ctx_set_opts": (_I32, [_P, ctypes.POINTER(Opts)]),
@@ -531,6 +533,15 @@ class Server:
         cnt, lat = ctypes.c_int64(0), ctypes.c_double(0)
         rc = self._lib.bridges_server_wait(self._h, ticket, timeout_ms, ctypes.byref(cnt), ctypes.byref(lat))
         return self._result(ticket, rc, cnt, lat)
+
+    def cancel(self, ticket: int) -> bool:
+        """bridges_server_cancel: True if the queued request was withdrawn (its wait / poll then
+        raises BRIDGES_ECANCELED), False if it was already running or done."""
+        rc = int(self._lib.bridges_server_cancel(self._h, ticket))
+        if rc == -7:
+            return False
+        _check(rc, "bridges_server_cancel")
+        return True
 
     def stats(self):
         buf = (ctypes.c_int64 * 6)()

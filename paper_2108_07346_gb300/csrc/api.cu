@@ -633,6 +633,7 @@ const char* bridges_status_string(int32_t st) {
     case BRIDGES_EAGAIN: return "request can never fit the memory budget";
     case BRIDGES_EBUSY: return "result not ready";
     case BRIDGES_EINTERNAL: return "internal invariant failed";
+    case BRIDGES_ECANCELED: return "request canceled";
     default: return "unknown status";
   }
 }
@@ -1058,7 +1059,7 @@ extern "C" int32_t bridges_autotune(bridges_ctx* c, struct CUstream_st* stream, 
   int32_t rc = BRIDGES_OK;
   const int32_t Ms[] = {1, 2, 4, 8, 16, 32};
   const double warms[] = {0.6, 0.8, 1.2, 2.0};
-  const int32_t blocks[] = {1024, 512};
+  const int32_t blocks[] = {1024, 768, 512};
   for (int32_t M : Ms) {
     if (M > 1 && (int64_t)M > std::max<int64_t>(E, 1)) break;
     for (int32_t f : {2, M}) {

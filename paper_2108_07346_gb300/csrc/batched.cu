@@ -350,10 +350,13 @@ __device__ __forceinline__ void s_certify_vec(const Grp<NT>& G, const Smem& S, c
                               int64_t hi, int32_t V, int32_t* n1, int32_t* n2, int32_t* err) {
   constexpr int U = 4;
   if (lo >= hi) return;
-  const bool same = ((reinterpret_cast<uintptr_t>(u) ^ reinterpret_cast<uintptr_t>(v)) & 15) == 0;
+  // the vector body starts on a 128-byte line of both arrays when they share their offset within
+  // a line (a warp's 512 bytes of loads then touch four lines, not five), else on a 16-byte boundary
+  const uintptr_t d = reinterpret_cast<uintptr_t>(u) ^ reinterpret_cast<uintptr_t>(v);
+  const uintptr_t amask = (d & 127) == 0 ? 127 : 15;
   int64_t body = lo;
-  if (same) {
-    while (body < hi && (reinterpret_cast<uintptr_t>(u + body) & 15)) body++;
+  if ((d & 15) == 0) {
+    while (body < hi && (reinterpret_cast<uintptr_t>(u + body) & amask)) body++;
   } else {
     body = hi;
   }

@@ -103,7 +103,7 @@ __device__ __forceinline__ void offer_edge(const ApArgs& A, int32_t a, int32_t b
 }
 
 __device__ __noinline__ void cycle_misses(const ApArgs& A, uint32_t m, const int32_t* __restrict__ u,
-                                          const int32_t* __restrict__ v, int32_t base) {
+                                          const int32_t* __restrict__ v, int64_t base) {
   while (m) {
     const int bit = __ffs(m) - 1;
     m &= m - 1;
@@ -118,7 +118,7 @@ struct CycleSink {
   __device__ __forceinline__ void slot(bool need, int32_t a, int32_t b, int64_t) const {
     if (need) offer_edge(A, a, b);
   }
-  __device__ __forceinline__ void misses(uint32_t m, const int32_t* ub, const int32_t* vb, int32_t base) const {
+  __device__ __forceinline__ void misses(uint32_t m, const int32_t* ub, const int32_t* vb, int64_t base) const {
     cycle_misses(A, m, ub, vb, base);
   }
 };
@@ -220,12 +220,17 @@ __global__ void __launch_bounds__(1024, 1) ap_pass_kernel(PassArgs P) {
   if (threadIdx.x == 0) stop = *P.A.status;
   __syncthreads();
   if (stop) return;  // block-uniform: the stream below contains barriers
-  const int64_t n = P.t - P.s;
-  const int64_t s = P.s + n * blockIdx.x / gridDim.x, t = P.s + n * (blockIdx.x + 1) / gridDim.x;
   if (MODE == 1) load_labels(slab, P.lab, P.Vpad);
   if (MODE == 2) load_words(slab, P.lab, (P.Vb / 32 + 4) / 4);
   const CycleSink S{P.A};
-  stream_range<MODE, VEC, kUnroll>(S, P.u, P.v, s, t, MODE == 2 ? (uint32_t)P.Vb : (uint32_t)P.A.V, slab);
+  const uint32_t clampv = MODE == 2 ? (uint32_t)P.Vb : (uint32_t)P.A.V;
+  if (MODE != 0) {  // with a snapshot: the stream, in interleaved tiles
+    stream_range<MODE, VEC, kUnroll>(S, P.u, P.v, P.s, P.t, clampv, slab, blockIdx.x, gridDim.x);
+  } else {  // the prefix, a slice per block
+    const int64_t n = P.t - P.s;
+    const int64_t s = P.s + n * blockIdx.x / gridDim.x, t = P.s + n * (blockIdx.x + 1) / gridDim.x;
+    stream_range<MODE, VEC, kUnroll>(S, P.u, P.v, s, t, clampv, slab);
+  }
 }
 
 // ---- label snapshot: each vertex takes the largest class it belongs to ----
@@ -474,7 +479,7 @@ __device__ __forceinline__ void fused_edge(const FusedArgs& F, bool go, int32_t 
 
 template <bool FOREST>
 __device__ __noinline__ void fused_misses(const FusedArgs& F, uint32_t m, const int32_t* __restrict__ u,
-                                          const int32_t* __restrict__ v, int32_t base) {
+                                          const int32_t* __restrict__ v, int64_t base) {
   while (__any_sync(kFull, m != 0)) {
     int32_t a = 0, b = 0;
     int64_t e = 0;
@@ -497,7 +502,7 @@ struct FusedSink {
   __device__ __forceinline__ void slot(bool need, int32_t a, int32_t b, int64_t i) const {
     fused_edge<FOREST>(F, need && checked_edge(F.A, a, b), a, b, i);
   }
-  __device__ __forceinline__ void misses(uint32_t m, const int32_t* ub, const int32_t* vb, int32_t base) const {
+  __device__ __forceinline__ void misses(uint32_t m, const int32_t* ub, const int32_t* vb, int64_t base) const {
     fused_misses<FOREST>(F, m, ub, vb, base);
   }
 };
@@ -511,11 +516,15 @@ __global__ void __launch_bounds__(1024, 1) ap_fused_kernel(FusedArgs F) {
   if (threadIdx.x == 0) stop = *F.A.status;
   __syncthreads();
   if (stop) return;  // block-uniform: the stream below contains barriers
-  const int64_t n = F.t - F.s;
-  const int64_t s = F.s + n * blockIdx.x / gridDim.x, t = F.s + n * (blockIdx.x + 1) / gridDim.x;
   load_labels(slab, F.lab, F.Vpad);
   const FusedSink<FOREST> S{F};
-  stream_range<1, VEC, kUnroll>(S, F.u, F.v, s, t, (uint32_t)F.A.V, slab);
+  if (FOREST) {  // the stream after the prefix, in interleaved tiles
+    stream_range<1, VEC, kUnroll>(S, F.u, F.v, F.s, F.t, (uint32_t)F.A.V, slab, blockIdx.x, gridDim.x);
+  } else {  // the prefix, a slice per block
+    const int64_t n = F.t - F.s;
+    const int64_t s = F.s + n * blockIdx.x / gridDim.x, t = F.s + n * (blockIdx.x + 1) / gridDim.x;
+    stream_range<1, VEC, kUnroll>(S, F.u, F.v, s, t, (uint32_t)F.A.V, slab);
+  }
 }
 
 // The combined snapshot, in place over the certificate's F' labels: a vertex keeps its F' label

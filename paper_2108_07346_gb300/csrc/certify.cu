@@ -68,7 +68,7 @@ __device__ __forceinline__ void scalar_slot(const Job& J, bool valid, int32_t a,
 // Kept out of line so the streaming loop stays small; the edges are re-read (they are still in
 // L1/L2).
 __device__ __noinline__ void offer_misses(const Job& J, uint32_t m, const int32_t* __restrict__ u,
-                                          const int32_t* __restrict__ v, int32_t base, int32_t V, int32_t* status) {
+                                          const int32_t* __restrict__ v, int64_t base, int32_t V, int32_t* status) {
   while (__any_sync(kFull, m != 0)) {
     int32_t a = 0, b = 0;
     bool go = false;
@@ -94,7 +94,7 @@ struct ForestSink {
   __device__ __forceinline__ void slot(bool need, int32_t a, int32_t b, int64_t) const {
     settle(J, need && checked(a, b, V, status), a, b, V, status);
   }
-  __device__ __forceinline__ void misses(uint32_t m, const int32_t* ub, const int32_t* vb, int32_t base) const {
+  __device__ __forceinline__ void misses(uint32_t m, const int32_t* ub, const int32_t* vb, int64_t base) const {
     offer_misses(J, m, ub, vb, base, V, status);
   }
 };
@@ -116,7 +116,8 @@ struct LeafArgs {
 };
 
 // Forest pass over the partitions: block -> (job j = blockIdx / G, member m = blockIdx % G);
-// member m streams its share of job j's chunk [E j / M, E (j+1) / M) (Sec. 3 partition).
+// the job's G members share its chunk [E j / M, E (j+1) / M) (Sec. 3 partition): the warm-up
+// prefix in one slice per member, the cached pass in interleaved tiles.
 template <int MODE, bool VEC>
 __global__ void __launch_bounds__(1024, 1) leaf_kernel(LeafArgs A) {
   extern __shared__ __align__(16) uint16_t slab[];
@@ -129,13 +130,18 @@ __global__ void __launch_bounds__(1024, 1) leaf_kernel(LeafArgs A) {
     a = max(a, A.r0);
     z = max(a, min(z, A.r1));
   }
-  const int64_t n = z - a;
-  const int64_t s = a + n * m / A.G, t = a + n * (m + 1) / A.G;
   if (MODE == 1) load_labels(slab, A.b.lab + j * A.b.Vpad, A.b.Vpad);
   if (MODE == 2) load_words(slab, A.b.lab + j * A.b.Vpad, (A.Vb / 32 + 4) / 4);
   const Job J = job_of(A.b, A.V, j);
   const ForestSink S{J, A.V, A.b.status};
-  stream_range<MODE, VEC, kUnroll>(S, A.u, A.v, s, t, MODE == 2 ? (uint32_t)A.Vb : (uint32_t)A.V, slab);
+  const uint32_t clampv = MODE == 2 ? (uint32_t)A.Vb : (uint32_t)A.V;
+  if (A.mode == 1) {
+    stream_range<MODE, VEC, kUnroll>(S, A.u, A.v, a, z, clampv, slab, m, A.G);
+  } else {
+    const int64_t n = z - a;
+    const int64_t s = a + n * m / A.G, t = a + n * (m + 1) / A.G;
+    stream_range<MODE, VEC, kUnroll>(S, A.u, A.v, s, t, clampv, slab);
+  }
 }
 
 struct MergeArgs {

@@ -295,6 +295,24 @@ int32_t bridges_server_wait(bridges_server* S, uint64_t ticket, int64_t timeout_
   }
 }
 
+int32_t bridges_server_cancel(bridges_server* S, uint64_t ticket) {
+  if (!S) return BRIDGES_EINVAL;
+  {
+    std::lock_guard<std::mutex> lk(S->mu);
+    auto it = S->reqs.find(ticket);
+    if (it == S->reqs.end()) return BRIDGES_EINVAL;
+    SrvReq& q = it->second;
+    if (q.state != 0) return BRIDGES_EBUSY;  // launched (or done): it completes normally
+    auto qt = std::find(S->queue.begin(), S->queue.end(), ticket);
+    if (qt != S->queue.end()) S->queue.erase(qt);
+    q.state = 2;
+    q.count = BRIDGES_ECANCELED;
+    q.t_done = now_s();
+  }
+  S->cv_done.notify_all();
+  return BRIDGES_OK;
+}
+
 int32_t bridges_server_stats(bridges_server* S, int64_t* vals, int32_t n) {
   if (!S || !vals) return 0;
   std::lock_guard<std::mutex> lk(S->mu);

@@ -129,3 +129,35 @@ def test_client_threads_and_an_abandoned_ticket(cuda_lib):
         time.sleep(0.01)
     assert srv.stats()["completed"] == len(dgraphs) + 1 and srv.stats()["failures"] == 0
     srv.close()
+
+
+def test_cancel_withdraws_queued_requests(cuda_lib):
+    """With one slot busy on a large graph, requests queued behind it can be withdrawn: their wait
+    raises BRIDGES_ECANCELED, the others complete with the oracle's bridges, and a request that
+    already runs cannot be withdrawn."""
+    big = graphgen.workload("mid")
+    small = [graphgen.generate(graphgen.workload_spec("batched", 9, i)) for i in range(12)]
+    srv = cuda_lib.Server(device="cuda:0", max_slots=1)
+    tb = srv.submit(dev(big.u), dev(big.v), big.V)
+    ts = [srv.submit(dev(g.u), dev(g.v), g.V) for g in small]
+    cancelled = [srv.cancel(t) for t in ts[::2]]
+    assert any(cancelled)
+    for k, (g, t) in enumerate(zip(small, ts)):
+        if k % 2 == 0 and cancelled[k // 2]:
+            with pytest.raises(cuda_lib.BridgesError) as ei:
+                srv.wait(t)
+            assert ei.value.code == -9
+        else:
+            got, _ = srv.wait(t)
+            assert got.cpu().numpy().tolist() == oracle.dfs_bridges(g.u, g.v, g.V).tolist()
+    got, _ = srv.wait(tb)
+    assert got.cpu().numpy().tolist() == big.planted.tolist()
+    t = srv.submit(dev(big.u), dev(big.v), big.V)
+    import time
+
+    time.sleep(0.05)  # long enough for an idle scheduler to launch it
+    assert srv.cancel(t) is False
+    assert srv.wait(t)[0].cpu().numpy().tolist() == big.planted.tolist()
+    with pytest.raises(cuda_lib.BridgesError):
+        srv.cancel(t)  # released
+    srv.close()
