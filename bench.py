@@ -43,16 +43,16 @@ UNIT = "GE/s"
 # streaming kernels; each is valid only for the kernel sources it was measured on (hash of those
 # sources).
 #   forest pass, M = 1, at density 1/8 (268 M edges, 2.1 GB: a capture of a few GB, scaled to a
-#   full launch by its streamed edges): 2.1402 GB read + 5.6 MB written for 267,444,294 streamed
+#   full launch by its streamed edges): 2.1402 GB read + 5.5 MB written for 267,444,294 streamed
 #   edges; block pass stream and fused stream (articulation points), the same density:
-#   2.1471 GB read + 7.5 MB written, and 2.1404 GB read + 0.4 MB written, for 267,444,294
+#   2.1471 GB read + 7.6 MB written, and 2.1402 GB read + 0.4 MB written, for 267,444,294
 #   streamed edges each
-TRAFFIC = {"certify_sha": "955904b8335e32d4", "bytes_per_edge": 8.0231,
+TRAFFIC = {"certify_sha": "4075a6058190271e", "bytes_per_edge": 8.0229,
            "source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of the forest pass at density 1/8 "
                      "(268 M edges), scaled to a full launch by its streamed edges"}
-AP_TRAFFIC = {"blocks_sha": "4eb6347dc917184f", "bytes_per_edge": 8.0562,
+AP_TRAFFIC = {"blocks_sha": "ed26c4b0ffd195fe", "bytes_per_edge": 8.0566,
               "source": "ncu dram bytes of the block pass stream at density 1/8, scaled by streamed edges"}
-FUSED_TRAFFIC = {"blocks_sha": "4eb6347dc917184f", "bytes_per_edge": 8.0046,
+FUSED_TRAFFIC = {"blocks_sha": "ed26c4b0ffd195fe", "bytes_per_edge": 8.0040,
                  "source": "ncu dram bytes of the fused stream at density 1/8, scaled by streamed edges"}
 
 

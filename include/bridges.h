@@ -415,13 +415,12 @@ int32_t bridges_ctx_ap_stage_ms_history(const bridges_ctx* ctx, float* ms, int32
 /* ---------------------------------------------------------------------------------------
  * Autotuning.
  * bridges_autotune: times candidate plans on the given device-resident input (M in
- * {1,2,4,8,16,32}, fan-in 2 or M, warm-up 0.6/0.8/1.2/2.0 x V ln V edges, block 1024, 768 or 512; `reps`
- * timed calls each, CUDA events on `stream`), then the warm-up launch's block size (128 to 1024)
- * for the winner, and keeps the fastest in the context's options (read them back whole with
- * bridges_ctx_get_opts).  best[0..4] receives M, fan-in, warm-up edges, block size and
- * microseconds per call.  Uses
- * a little scratch memory of its own (the output buffers).  Returns BRIDGES_OK or an error (the
- * options are then unchanged).
+ * {1,2,4,8,16,32}, fan-in 2 or M, warm-up 0.3/0.45/0.6/0.8/1.2/2.0 x V ln V edges, block 1024,
+ * 768 or 512; `reps` timed calls each, CUDA events on `stream`), then the warm-up launch's block
+ * size (128 to 1024) for the winner, and keeps the fastest in the context's options (read them
+ * back whole with bridges_ctx_get_opts).  best[0..4] receives M, fan-in, warm-up edges, block
+ * size and microseconds per call.  Uses a little scratch memory of its own (the output buffers).
+ * Returns BRIDGES_OK or an error (the options are then unchanged).
  * bridges_ctx_set_opts: replaces the context's tuning options (e.g. from a cache of tuning
  * results); the profiling flag stays as created.
  * bridges_ctx_get_opts: copies the context's current options to *opts.

@@ -1058,7 +1058,7 @@ extern "C" int32_t bridges_autotune(bridges_ctx* c, struct CUstream_st* stream, 
   bridges_opts best_o = saved;
   int32_t rc = BRIDGES_OK;
   const int32_t Ms[] = {1, 2, 4, 8, 16, 32};
-  const double warms[] = {0.6, 0.8, 1.2, 2.0};
+  const double warms[] = {0.3, 0.45, 0.6, 0.8, 1.2, 2.0};
   const int32_t blocks[] = {1024, 768, 512};
   for (int32_t M : Ms) {
     if (M > 1 && (int64_t)M > std::max<int64_t>(E, 1)) break;

@@ -224,9 +224,9 @@ __global__ void __launch_bounds__(1024, 1) ap_pass_kernel(PassArgs P) {
   if (MODE == 2) load_words(slab, P.lab, (P.Vb / 32 + 4) / 4);
   const CycleSink S{P.A};
   const uint32_t clampv = MODE == 2 ? (uint32_t)P.Vb : (uint32_t)P.A.V;
-  if (MODE != 0) {  // with a snapshot: the stream, in interleaved tiles
+  if (MODE != 0 && use_tiles(P.s, P.t, gridDim.x, blockDim.x, kUnroll)) {  // the stream, interleaved tiles
     stream_range<MODE, VEC, kUnroll>(S, P.u, P.v, P.s, P.t, clampv, slab, blockIdx.x, gridDim.x);
-  } else {  // the prefix, a slice per block
+  } else {  // the prefix (or a short list), a slice per block
     const int64_t n = P.t - P.s;
     const int64_t s = P.s + n * blockIdx.x / gridDim.x, t = P.s + n * (blockIdx.x + 1) / gridDim.x;
     stream_range<MODE, VEC, kUnroll>(S, P.u, P.v, s, t, clampv, slab);
@@ -518,9 +518,9 @@ __global__ void __launch_bounds__(1024, 1) ap_fused_kernel(FusedArgs F) {
   if (stop) return;  // block-uniform: the stream below contains barriers
   load_labels(slab, F.lab, F.Vpad);
   const FusedSink<FOREST> S{F};
-  if (FOREST) {  // the stream after the prefix, in interleaved tiles
+  if (FOREST && use_tiles(F.s, F.t, gridDim.x, blockDim.x, kUnroll)) {  // the stream after the prefix, in tiles
     stream_range<1, VEC, kUnroll>(S, F.u, F.v, F.s, F.t, (uint32_t)F.A.V, slab, blockIdx.x, gridDim.x);
-  } else {  // the prefix, a slice per block
+  } else {  // the prefix (or a short list), a slice per block
     const int64_t n = F.t - F.s;
     const int64_t s = F.s + n * blockIdx.x / gridDim.x, t = F.s + n * (blockIdx.x + 1) / gridDim.x;
     stream_range<1, VEC, kUnroll>(S, F.u, F.v, s, t, (uint32_t)F.A.V, slab);

@@ -117,7 +117,8 @@ struct LeafArgs {
 
 // Forest pass over the partitions: block -> (job j = blockIdx / G, member m = blockIdx % G);
 // the job's G members share its chunk [E j / M, E (j+1) / M) (Sec. 3 partition): the warm-up
-// prefix in one slice per member, the cached pass in interleaved tiles.
+// prefix in one slice per member, the cached pass in interleaved tiles when the chunk is long
+// enough (use_tiles), else in slices too.
 template <int MODE, bool VEC>
 __global__ void __launch_bounds__(1024, 1) leaf_kernel(LeafArgs A) {
   extern __shared__ __align__(16) uint16_t slab[];
@@ -135,7 +136,7 @@ __global__ void __launch_bounds__(1024, 1) leaf_kernel(LeafArgs A) {
   const Job J = job_of(A.b, A.V, j);
   const ForestSink S{J, A.V, A.b.status};
   const uint32_t clampv = MODE == 2 ? (uint32_t)A.Vb : (uint32_t)A.V;
-  if (A.mode == 1) {
+  if (A.mode == 1 && use_tiles(a, z, A.G, blockDim.x, kUnroll)) {
     stream_range<MODE, VEC, kUnroll>(S, A.u, A.v, a, z, clampv, slab, m, A.G);
   } else {
     const int64_t n = z - a;

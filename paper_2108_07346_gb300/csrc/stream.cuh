@@ -137,6 +137,14 @@ __device__ __forceinline__ void stream_range(const Sink& S, const int32_t* __res
   }
 }
 
+// Whether `members` blocks of nt threads share [s, t) in interleaved tiles (true) or take one
+// slice each (false): tiles only when every block gets at least 16 of them -- a tile is 4U edges
+// per thread, so on a short list tiles would leave blocks idle (a 1 M-edge list has 61 tiles of
+// 16,384 edges for 152 blocks).
+__device__ __forceinline__ bool use_tiles(int64_t s, int64_t t, int64_t members, int nt, int U) {
+  return members > 1 && t - s >= 16 * members * (int64_t)nt * 4 * U;
+}
+
 // Edge index of bit `bit` of a miss mask (see stream_range).
 __device__ __forceinline__ int64_t miss_edge(int bit, int64_t base) {
   return 4 * (base + (int64_t)(bit >> 2) * blockDim.x + threadIdx.x) + (bit & 3);
