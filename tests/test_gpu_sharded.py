@@ -1,5 +1,5 @@
-"""The sharded form on the GPU: two ranks (two processes, both on cuda:0) certify their halves of
-the list with the library's kernels, exchange certificates over a host-staged gloo channel on the
+"""The sharded form on the GPU: ranks (processes, all on cuda:0) certify their shards of the
+list with the library's kernels, exchange certificates over a host-staged gloo channel on the
 paper's merge schedule (Sec. 3 phases), and rank 0 finds the bridges of X_0.  No kernel of one
 process waits for the other: every exchange is a host-side send and receive between launches.
 The bridges must equal the oracle's on the whole list, bit for bit."""
@@ -57,14 +57,14 @@ def _worker(rank, world, port, kind, q):
         q.put((rank, repr(e), -1))
 
 
-@pytest.mark.parametrize("kind", ["mid", pytest.param("dense300m", marks=pytest.mark.slow)])
-def test_two_ranks_on_one_gpu_match_the_oracle(kind):
+@pytest.mark.parametrize("kind,world", [("mid", 2), ("mid", 3), pytest.param("dense300m", 2, marks=pytest.mark.slow)])
+def test_ranks_on_one_gpu_match_the_oracle(kind, world):
+    """Two ranks (one merge phase) and three (two phases, the second with an odd rank out)."""
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
     import graphgen
     import oracle
 
-    world = 2
     ctx = mp.get_context("spawn")
     q = ctx.Queue()
     port = _free_port()
