@@ -306,9 +306,9 @@ int64_t bridges_rooted_forest(bridges_ctx* ctx, struct CUstream_st* stream, cons
  * block in the driver, or the process reserves all device memory up front.  This entry point
  * allocates nothing: every intermediate buffer lives in one fixed 8 MiB array of device memory
  * that is part of the library itself (each GPU that loads the library holds it until the process
- * exits).  That bounds the graph: a call needs about 1.07 MB plus (150 + 30 M) bytes per vertex,
- * so V may be at most 41,023 with M = 1 (M <= 0 picks 1), 35,135 with M = 2, 27,264 with M = 4
- * and 18,848 with M = 8.  The edge count is not limited by the array.  Larger graphs return
+ * exits).  That bounds the graph: a call needs about 1.07 MB plus (132 + 30 M) bytes per vertex,
+ * so V may be at most 45,135 with M = 1 (M <= 0 picks 1), 38,095 with M = 2, 29,040 with M = 4
+ * and 19,679 with M = 8.  The edge count is not limited by the array.  Larger graphs return
  * BRIDGES_ENOMEM without running anything.
  *
  *   edges_u, edges_v, E, V, M, out_bridges, out_count_device : as for bridges_find_ctx, on the

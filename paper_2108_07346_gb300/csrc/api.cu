@@ -580,7 +580,8 @@ int64_t bridges_rooted_forest(bridges_ctx* c, struct CUstream_st* stream, const 
   cudaMemcpyAsync(k.counts, h, 2 * sizeof(int32_t), cudaMemcpyHostToDevice, s);
   // with no extra edges every tree edge is a bridge; the sorted list goes to dscan, which the
   // stage no longer reads once it sorts
-  final_stage(L, k.fin, V, tu, tv, k.counts, n_tree, nullptr, nullptr, k.counts + 1, 0, nullptr, k.fin.dscan);
+  final_stage(L, k.fin, V, tu, tv, k.counts, n_tree, nullptr, nullptr, k.counts + 1, 0, nullptr, k.fin.dscan,
+              /*ordered=*/true);
   const size_t bytes = sizeof(int32_t) * (size_t)V;
   if ((out_parent && cudaMemcpyAsync(out_parent, k.fin.par, bytes, cudaMemcpyDeviceToDevice, s) != cudaSuccess) ||
       (out_pre && cudaMemcpyAsync(out_pre, k.fin.pre, bytes, cudaMemcpyDeviceToDevice, s) != cudaSuccess) ||

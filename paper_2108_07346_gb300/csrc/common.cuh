@@ -79,10 +79,13 @@ __device__ __forceinline__ int32_t uf_find_static(int32_t* P, int32_t x) {
 // Walks up from both ends comparing PARENTS, not roots: equal parents prove a common set, so in
 // the dense phase, where nearly every vertex points straight at its root, a rejection costs two
 // loads and never touches the root's own entry (which every block would otherwise hammer).  The
-// end with the larger parent moves up (path halving).  When that end is itself a root x, the
-// other end is walked to its root r < x and x is hooked under r: members of a set are >= its
-// root, so r is not in x's set and the CAS joins two different sets, and hooking root under
-// root keeps the trees shallow while they are still growing.
+// end with the larger parent moves up (path halving); a grandparent equal to the other end's
+// parent also proves a common set.  When the end with the larger parent is a root x (or its
+// parent px is one), it is hooked under the other end's parent py < x: members of a set are >=
+// its root, so py is not in x's set and the CAS joins two different sets.  Hooking under py
+// rather than under py's root spares the walk to that root, whose entry every vertex joining
+// the giant component would otherwise read -- one L2 line for all blocks while the forests grow
+// (large workload, 150 k-edge prefix: 0.136 ms with root-under-root hooking, 0.090 ms so).
 __device__ __forceinline__ bool uf_link(int32_t* P, int32_t a, int32_t b) {
   int32_t x = a, y = b;
   while (true) {
@@ -98,12 +101,19 @@ __device__ __forceinline__ bool uf_link(int32_t* P, int32_t a, int32_t b) {
     }
     // now px > py
     if (px == x) {
-      const int32_t ry = uf_find(P, py);  // ry <= py < x
-      if (atomicCAS(P + x, x, ry) == x) return true;
+      if (atomicCAS(P + x, x, py) == x) return true;  // py < x lies in y's set
       continue;  // x was hooked meanwhile: re-read its parent
     }
     const int32_t g = ld_relaxed(P + px);
-    if (g != px) st_relaxed(P + x, g);  // path halving
+    if (g == py) {  // x's grandparent is y's parent: one set (halve x's path on the way out)
+      st_relaxed(P + x, g);
+      return false;
+    }
+    if (g == px) {              // px is a root: hook it without reading its entry again
+      if (atomicCAS(P + px, px, py) == px) return true;
+      continue;
+    }
+    st_relaxed(P + x, g);  // path halving
     x = g;
   }
 }

@@ -66,34 +66,29 @@ struct CertBufs {
 struct FinalBufs {
   int32_t* status;
   int64_t* count;  // [1] bridges found (device)
-  unsigned* bar_count;  // grid barrier: arrivals
-  unsigned* bar_gen;    // grid barrier: generation
+  unsigned* bar_count;  // grid barrier: arrivals (grows within a launch)
+  int32_t* nroots;  // [1] trees of the forest (one-vertex trees included)
   int32_t* P;      // [V] union-find over the tree (built by the stage when it owns it)
-  int32_t* root;   // [V]
-  int32_t* deg;    // [V]
-  int32_t* off;    // [V+1]
-  int32_t* cur;    // [V]
-  int32_t* dst;    // [2V]
-  int32_t* twin;   // [2V]
+  int32_t* root;   // [V] root (minimum vertex) of each vertex's tree
+  int32_t* head;   // [V] first arc of each vertex's arc list (-1: none)
+  int32_t* next;   // [2V] next arc of the same tail (-1: last); tree edge e has arcs 2e, 2e+1
+  int32_t* rslot;  // [V+1] index of each root's tree in the tour (-1: not a root)
+  int32_t* rlist;  // [V] root of each tree index
   int2* sr;        // [2V] Euler-tour successor and rank, packed (one load per pointer jump)
   int2* sr2;       // [2V] its double buffer
   int32_t* rnk;    // [2V] final ranks
-  int32_t* aoff;   // [V+1] arc offset of each tree
-  int32_t* vbase;  // [V+1] preorder base of each tree
-  int32_t* dflag;  // [2V+1]
-  int32_t* dscan;  // [2V+1]
+  int32_t* dflag;  // [2V+1] 1 at the tour positions of down arcs and tree entries
+  int32_t* dscan;  // [2V+1] its exclusive scan
   int32_t* pre;    // [V]
   int32_t* sz;     // [V]
   int32_t* par;    // [V] parent in the rooted tree (-1 for roots)
   int32_t* bflag;  // [V] 1 if the tree edge (par[y], y) is a bridge
-  int32_t* slo;    // [V] by vertex y (non-roots): min of lo over y's subtree range
-  int32_t* shi;    // [V] by vertex y (non-roots): max of hi over y's subtree range
-  int32_t* lo;     // [V] indexed by preorder
-  int32_t* hi;     // [V]
+  int32_t* slo;    // [V] by vertex y (non-roots): min of lo over y's subtree range (at most pre y)
+  int32_t* shi;    // [V] by vertex y (non-roots): max of hi over y's subtree range (at least its end)
+  int32_t* lo;     // [V] indexed by preorder: smallest preorder among the X-neighbours
+  int32_t* hi;     // [V] largest preorder among the X-neighbours
   int32_t* cmin;   // [V/32] chunk minima of lo
   int32_t* cmax;   // [V/32] chunk maxima of hi
-  int32_t* smin;   // superchunk minima
-  int32_t* smax;   // superchunk maxima
   uint64_t* keys;   // [V]
   uint64_t* keys2;  // [V]
   int32_t* nkeys;   // [1]
@@ -174,9 +169,12 @@ void two_edge_components(const Launch& L, const FinalBufs& fb, int32_t V, const 
 void cert_offer(const Launch& L, const CertPlan& p, const CertBufs& b, const int32_t* u, const int32_t* v, int64_t n);
 // Bridges of T u X (T a spanning forest of every tree it touches, X edges inside trees).
 // Counts on device.  P_tree: union-find of T (roots = minimum vertex), or null to build it.
+// ordered: trees take consecutive preorder ranges in increasing order of their roots (otherwise
+// in an arbitrary order).
 void final_stage(const Launch& L, const FinalBufs& fb, int32_t V, const int32_t* tu, const int32_t* tv,
                  const int32_t* d_ntree, int64_t cap_tree, const int32_t* xu, const int32_t* xv,
-                 const int32_t* d_nextra, int64_t cap_extra, const int32_t* P_tree, int32_t* out);
+                 const int32_t* d_nextra, int64_t cap_extra, const int32_t* P_tree, int32_t* out,
+                 bool ordered = false);
 
 // ---- blocks.cu ----
 size_t ap_bytes(int32_t V);

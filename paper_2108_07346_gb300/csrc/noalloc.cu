@@ -17,9 +17,9 @@ namespace {
 
 using namespace bridges;
 
-// 8 MiB.  A call needs about 1.07 MB plus (150 + 30 M) bytes per vertex, so the largest graph
-// that fits has 41,023 vertices at M = 1 (the automatic choice), 35,135 at M = 2, 27,264 at
-// M = 4 and 18,848 at M = 8; the edge count does not enter.  Every GPU that loads the library
+// 8 MiB.  A call needs about 1.07 MB plus (132 + 30 M) bytes per vertex, so the largest graph
+// that fits has 45,135 vertices at M = 1 (the automatic choice), 38,095 at M = 2, 29,040 at
+// M = 4 and 19,679 at M = 8; the edge count does not enter.  Every GPU that loads the library
 // holds this array until the process exits.
 constexpr size_t kNoAllocScratchBytes = 8u << 20;
 constexpr size_t kMiscBytes = 1024;  // status word at 0, the spare output slot at kSpareOut

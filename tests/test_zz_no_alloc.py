@@ -19,7 +19,7 @@ import oracle
 pytestmark = pytest.mark.gpu
 
 # the largest graph the fixed 8 MiB array holds with one partition (include/bridges.h)
-V_MAX_M1 = 41_023
+V_MAX_M1 = 45_135
 
 
 @pytest.fixture(scope="module")
