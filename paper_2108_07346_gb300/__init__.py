@@ -497,6 +497,8 @@ class Server:
         o = Opts()
         o.warm_edges = opts.get("warm_edges", -1)
         o.M = opts.get("M", 0)
+        o.test_barrier_polls = int(opts.get("test_barrier_polls", 0))
+        o.test_hold_polls = int(opts.get("test_hold_polls", 0))
         h = self._lib.bridges_server_create(dev.index, int(mem_budget), max_slots, max_batch, ctypes.byref(o))
         if not h:
             raise BridgesError(-4, "bridges_server_create")

@@ -49,14 +49,14 @@ static_assert(kSuperChunks == 32, "superchunk indexes are taken by shifts of 5 +
 constexpr int kMaxSup = 1024;        // superchunks covered by the shared-memory table
 constexpr int kSupLevels = 11;       // log2(kMaxSup) + 1
 constexpr int64_t kRankMax = 16384;  // up to this many bridges: slice sort + merge ranking
-constexpr int kSlice = 1024;         // keys per block slice at most (a power of two)
+constexpr int kSortSlice = 256;      // keys per sorted slice at most (the small-n sort)
 constexpr unsigned kSpinCap = 1u << 22;
 constexpr int kHopsLog = 2;  // pointer-jumping hops per round: 4 (8 was slower: longer load chains)
 constexpr int kHops = 1 << kHopsLog;
 constexpr int kMaxBlocks = 1024;
 constexpr int kScanItems = 8;  // consecutive elements per thread in a grid-scan tile
 constexpr size_t kSmemTables = sizeof(int32_t) * 2 * kSupLevels * kMaxSup;
-constexpr size_t kSmemSort = sizeof(uint64_t) * (kRankMax + kMaxBlocks) + sizeof(int32_t) * kSlice;
+constexpr size_t kSmemSort = sizeof(uint64_t) * (kRankMax + kMaxBlocks);
 
 struct FinArgs {
   FinalBufs f;
@@ -352,7 +352,7 @@ __global__ void __launch_bounds__(kThreads) final_kernel(FinArgs A) {
   for (int64_t x = gspread(); x < V; x += gstride()) {
     f.head[x] = -1;
     f.rslot[x] = -1;
-    f.pre[x] = -1;
+    f.slo[x] = -1;
     f.lo[x] = INT32_MAX;
     f.hi[x] = INT32_MIN;
     if (own) f.P[x] = (int32_t)x;
@@ -533,7 +533,7 @@ __global__ void __launch_bounds__(kThreads) final_kernel(FinArgs A) {
       f.dflag[g] = down ? 1 : 0;
       if (down) {
         f.par[y] = x;
-        f.pre[y] = (int32_t)g;  // tour position of y's down arc; turned into a preorder number below
+        f.slo[y] = (int32_t)g;  // tour position of y's down arc (slo serves as scratch until the test)
         f.sz[y] = (ri - rt + 1) / 2;
       }
     } else {
@@ -546,7 +546,7 @@ __global__ void __launch_bounds__(kThreads) final_kernel(FinArgs A) {
       const int32_t root = f.rlist[k];
       f.dflag[g] = 1;
       f.par[root] = -1;
-      f.pre[root] = (int32_t)g;
+      f.slo[root] = (int32_t)g;
       f.sz[root] = (ri - rn - 1) / 2 + 1;  // the tree's ri - rn - 1 arcs, two per edge
     }
   }
@@ -554,36 +554,37 @@ __global__ void __launch_bounds__(kThreads) final_kernel(FinArgs A) {
   if (!grid_scan(f, A.bar_polls, &bar_epoch, f.dflag, f.dscan, nullptr, nullptr, N, red)) return;
   BARRIER();
 
-  // 5: preorder numbers: the down arcs and entries before the vertex's own
-  for (int64_t x = gspread(); x < V; x += gstride()) {
-    const int32_t g = f.pre[x];
-    int32_t p = (g >= 0 && g < N) ? f.dscan[g] : -1;
-    if (p < 0 || p >= V) {  // only if the tree input was not a forest
-      set_status(f.status, BRIDGES_EINTERNAL_CODE);
-      p = 0;
+  // 5: preorder numbers (the down arcs and entries before the vertex's own tour position), and in
+  //    the same pass lo / hi over the extra edges, per element and per chunk, from the same scan.
+  //    An edge between the vertices numbered p < q has exactly one end in a range [l, r) iff
+  //    either p lies in it and q >= r (seen as hi[p] >= r) or q lies in it and p < l (seen as
+  //    lo[q] < l); q can never fall below a range holding p, nor p above a range holding q.  So
+  //    the edge lowers lo[q] to p and raises hi[p] to q only: two element and two chunk atomics.
+  {
+    auto preorder = [&](int32_t x) {
+      const int32_t g = f.slo[x];
+      const int32_t p = (g >= 0 && g < N) ? f.dscan[g] : -1;
+      if (p < 0 || p >= V) {  // only if the tree input was not a forest
+        set_status(f.status, BRIDGES_EINTERNAL_CODE);
+        return 0;
+      }
+      return p;
+    };
+    for (int64_t x = gspread(); x < V; x += gstride()) f.pre[x] = preorder((int32_t)x);
+    for (int64_t e = gspread(); e < nx; e += gstride()) {
+      const int32_t a = A.xu[e], b = A.xv[e];
+      if ((uint32_t)a >= (uint32_t)V || (uint32_t)b >= (uint32_t)V) {
+        set_status(f.status, BRIDGES_ERANGE_CODE);
+        continue;
+      }
+      if (a == b) continue;
+      const int32_t pa = preorder(a), pb = preorder(b);
+      const int32_t p = min(pa, pb), q = max(pa, pb);
+      atomicMin(f.lo + q, p);
+      atomicMax(f.hi + p, q);
+      atomicMin(f.cmin + q / kChunk, p);
+      atomicMax(f.cmax + p / kChunk, q);
     }
-    f.pre[x] = p;
-  }
-  BARRIER();
-
-  // 6: lo / hi over the extra edges, per element and per chunk.  An edge between the vertices
-  //    numbered p < q has exactly one end in a range [l, r) iff either p lies in it and q >= r
-  //    (seen as hi[p] >= r) or q lies in it and p < l (seen as lo[q] < l); q can never fall below
-  //    a range holding p, nor p above a range holding q.  So the edge lowers lo[q] to p and
-  //    raises hi[p] to q only: two element and two chunk atomics per edge.
-  for (int64_t e = gspread(); e < nx; e += gstride()) {
-    const int32_t a = A.xu[e], b = A.xv[e];
-    if ((uint32_t)a >= (uint32_t)V || (uint32_t)b >= (uint32_t)V) {
-      set_status(f.status, BRIDGES_ERANGE_CODE);
-      continue;
-    }
-    if (a == b) continue;
-    const int32_t pa = f.pre[a], pb = f.pre[b];
-    const int32_t p = min(pa, pb), q = max(pa, pb);
-    atomicMin(f.lo + q, p);
-    atomicMax(f.hi + p, q);
-    atomicMin(f.cmin + q / kChunk, p);
-    atomicMax(f.cmax + p / kChunk, q);
   }
   BARRIER();
 
@@ -794,51 +795,48 @@ __global__ void __launch_bounds__(kThreads) final_kernel(FinArgs A) {
   const int32_t n = min(*f.nkeys, cap);
   const uint64_t mask = (1ULL << A.kbits) - 1;
   const int64_t per = (n + gridDim.x - 1) / gridDim.x;
-  if (n <= kRankMax && per <= kSlice) {
-    // each block sorts its slice [b per, (b+1) per) (the rank of a key among the slice's keys,
-    // all pairs in shared memory); then each key's rank is the number of smaller keys in every
-    // sorted slice, by binary search (keys are unique)
+  if (n <= kRankMax) {
+    // the keys in slices of at most kSortSlice: block b sorts slices b, b + gridDim, ... (each
+    // key's rank among the slice's keys, all pairs in shared memory); then every block ranks its
+    // share of the keys against every sorted slice by binary search (keys are unique), a warp
+    // per key with its lanes over the slices -- few slices keep the searches few
     uint64_t* S = reinterpret_cast<uint64_t*>(sm);
-    const int32_t per32 = (int32_t)per, n32 = n;
-    const int32_t s0 = min(n32, per32 * (int32_t)blockIdx.x), m = min(n32, s0 + per32) - s0;
-    for (int i = threadIdx.x; i < m; i += blockDim.x) S[i] = f.keys[s0 + i];
-    __syncthreads();
-    for (int q = threadIdx.x; q < m; q += blockDim.x) {
-      const uint64_t key = S[q];
-      int32_t r = 0;
-      for (int j = 0; j < m; j++) r += S[j] < key;  // every lane reads the same word
-      f.keys2[s0 + r] = key;
+    const int32_t n32 = n;
+    const int32_t nsl = (n32 + kSortSlice - 1) / kSortSlice;
+    const int32_t ps = nsl > 0 ? (n32 + nsl - 1) / nsl : 0;  // slice length
+    for (int32_t b = blockIdx.x; b < nsl; b += gridDim.x) {  // small grids take several slices
+      const int32_t s0 = ps * b, m = min(n32, s0 + ps) - s0;
+      for (int i = threadIdx.x; i < m; i += blockDim.x) S[i] = f.keys[s0 + i];
+      __syncthreads();
+      for (int q = threadIdx.x; q < m; q += blockDim.x) {
+        const uint64_t key = S[q];
+        int32_t r = 0;
+        for (int j = 0; j < m; j++) r += S[j] < key;  // every lane reads the same word
+        f.keys2[s0 + r] = key;
+      }
+      __syncthreads();
     }
     BARRIER();
     // slice b at S + b * sp: an odd stride (in 8-byte words) puts the same position of 16
-    // consecutive slices in 16 different bank pairs, so a warp whose lanes search 32 slices for
-    // one key reads without bank conflicts at least at the first probe
-    const int32_t nslices = per32 > 0 ? (n32 + per32 - 1) / per32 : 0;
-    const int32_t sp = per32 | 1;
-    int32_t* rank = reinterpret_cast<int32_t*>(S + kRankMax + kMaxBlocks);
+    // consecutive slices in 16 different bank pairs
+    const int32_t sp = ps | 1;
     for (int32_t i = threadIdx.x; i < n32; i += blockDim.x) {
-      const int32_t b = i / per32;
-      S[b * sp + (i - b * per32)] = f.keys2[i];
+      const int32_t b = i / ps;
+      S[b * sp + (i - b * ps)] = f.keys2[i];
     }
     __syncthreads();
-    const uint64_t* own = S + (int64_t)blockIdx.x * sp;
-    {
-      const int lane = threadIdx.x & 31;
-      for (int q = threadIdx.x >> 5; q < m; q += kWarps) {  // a warp per key, its lanes over the slices
-        const uint64_t key = own[q];
-        int32_t c = 0;
-        for (int32_t b = lane; b < nslices; b += 32)
-          c += b == (int32_t)blockIdx.x ? q : lower_rank(S + b * sp, min(n32, (b + 1) * per32) - b * per32, key);
-        for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(kFull, c, o);
-        if (lane == 0) rank[q] = c;
+    const int32_t k0 = min(n32, (int32_t)per * (int32_t)blockIdx.x), k1 = min(n32, k0 + (int32_t)per);
+    const int lane = threadIdx.x & 31;
+    for (int32_t i = k0 + (threadIdx.x >> 5); i < k1; i += kWarps) {  // a warp per key
+      const int32_t bi = i / ps;
+      const uint64_t key = S[bi * sp + (i - bi * ps)];
+      int32_t c = 0;
+      for (int32_t b = lane; b < nsl; b += 32) c += lower_rank(S + b * sp, min(n32, (b + 1) * ps) - b * ps, key);
+      for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(kFull, c, o);
+      if (lane == 0) {
+        A.out[2 * (int64_t)c] = (int32_t)(key >> A.kbits);
+        A.out[2 * (int64_t)c + 1] = (int32_t)(key & mask);
       }
-    }
-    __syncthreads();
-    for (int q = threadIdx.x; q < m; q += blockDim.x) {
-      const uint64_t key = own[q];
-      const int64_t at = rank[q];
-      A.out[2 * at] = (int32_t)(key >> A.kbits);
-      A.out[2 * at + 1] = (int32_t)(key & mask);
     }
   } else {
     const int passes = (2 * A.kbits + 7) / 8;

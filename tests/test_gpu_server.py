@@ -134,12 +134,16 @@ def test_client_threads_and_an_abandoned_ticket(cuda_lib):
 def test_cancel_withdraws_queued_requests(cuda_lib):
     """With one slot busy on a large graph, requests queued behind it can be withdrawn: their wait
     raises BRIDGES_ECANCELED, the others complete with the oracle's bridges, and a request that
-    already runs cannot be withdrawn."""
+    already runs cannot be withdrawn.  The slot stays busy for a known time: the test knob that
+    holds one block of the final stage back (a bounded sleep of about 30 ms per large request)
+    keeps the queue from draining before the cancels, however fast the GPU runs the graph."""
     big = graphgen.workload("mid")
     small = [graphgen.generate(graphgen.workload_spec("batched", 9, i)) for i in range(12)]
-    srv = cuda_lib.Server(device="cuda:0", max_slots=1)
-    tb = srv.submit(dev(big.u), dev(big.v), big.V)
-    ts = [srv.submit(dev(g.u), dev(g.v), g.V) for g in small]
+    srv = cuda_lib.Server(device="cuda:0", max_slots=1, test_hold_polls=300_000)
+    bu, bv = dev(big.u), dev(big.v)
+    su = [(dev(g.u), dev(g.v)) for g in small]
+    tb = srv.submit(bu, bv, big.V)
+    ts = [srv.submit(u, v, g.V) for (u, v), g in zip(su, small)]
     cancelled = [srv.cancel(t) for t in ts[::2]]
     assert any(cancelled)
     for k, (g, t) in enumerate(zip(small, ts)):
