@@ -247,6 +247,7 @@ struct RangeArrays {
   const int32_t* cwl;  // window of 2^k chunks (k >= 1) at cwl + (k - 1) * nch: min of the minima
   const int32_t* cwh;  // max of the maxima, the same
   int64_t nch;
+  int kc;  // chunk window levels 1..kc exist
 };
 
 // min of lo and max of hi over the preorder range [l, r), 0 <= l < r: a range inside one chunk
@@ -289,7 +290,11 @@ __device__ __forceinline__ void range_minmax(const FinalBufs& f, const RangeArra
       mx = max(mx, f.cmax[c0]);
       return;
     }
-    const int k = 63 - __clzll(n);  // 1 <= k < cslog, and 2^k <= n < the chunk count
+    // the n whole chunks lie in one superchunk and the range's end chunks are not among them,
+    // so n <= 2^cslog and n < the chunk count; kc is the largest level below both bounds, so two
+    // windows of 2^k chunks, k = min(floor(log2 n), kc), cover them (a whole superchunk, n =
+    // 2^cslog, takes k = kc = cslog - 1)
+    const int k = min(63 - __clzll(n), R.kc);
     const int32_t* wl = R.cwl + (int64_t)(k - 1) * R.nch;
     const int32_t* wh = R.cwh + (int64_t)(k - 1) * R.nch;
     mn = min(mn, min(wl[c0], wl[c1 - (1LL << k)]));
@@ -604,7 +609,7 @@ __global__ void __launch_bounds__(kThreads) final_kernel(FinArgs A) {
   const RangeArrays R{f.dflag,      f.dflag + V,  f.dscan,           f.dscan + V,      f.rnk,
                       sr32,         sr32 + 2 * V, f.rnk + V,         sr32 + V,         sr32 + 3 * V,
                       cp32,         cp32 + nchunks, cp32 + 2 * nchunks, cp32 + 3 * nchunks, cp32 + 4 * nchunks,
-                      cp32 + (4 + (int64_t)kc) * nchunks, nchunks};
+                      cp32 + (4 + (int64_t)kc) * nchunks, nchunks, kc};
   {
     int32_t* epl = const_cast<int32_t*>(R.epl);
     int32_t* esl = const_cast<int32_t*>(R.esl);

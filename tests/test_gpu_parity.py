@@ -185,6 +185,23 @@ def test_from_forest_matches_oracle(ctx):
         assert got.tolist() == oracle.dfs_bridges(g.u, g.v, g.V).tolist()
 
 
+@pytest.mark.parametrize("V", [2060, 3090, 33_812, 70_000, 1_230_860])
+def test_from_forest_path_ranges(ctx, V):
+    """The final stage on the path 0-1-...-(V-1) given as the forest: its preorder is the vertex
+    order whatever order the arcs come in, so vertex y's subtree is the range [y, V) and every
+    start of a range ending at V is queried.  V is chosen one chunk past a superchunk (32 chunks
+    of 32 preorder numbers; 64 chunks above about a million vertices), so for y in the chunk
+    before that superchunk the range's whole chunks fill it exactly.  Random extra edges close
+    cycles over the path; the bridges are the path edges no cycle covers."""
+    rng = np.random.default_rng(V)
+    tu = np.arange(V - 1, dtype=np.int32)
+    tv = tu + 1
+    a, b = rng.integers(0, V, 40), rng.integers(0, V, 40)
+    xu, xv = a[a != b].astype(np.int32), b[a != b].astype(np.int32)
+    got = ctx.from_forest(*dev_edges(tu, tv), *dev_edges(xu, xv), V).cpu().numpy()
+    assert got.tolist() == oracle.dfs_bridges(np.concatenate([tu, xu]), np.concatenate([tv, xv]), V).tolist()
+
+
 def test_find_host_and_async(ctx, cuda_lib):
     g = graphgen.workload("small")
     ref = oracle.bridges(g.u, g.v, g.V, 16)
