@@ -47,12 +47,12 @@ UNIT = "GE/s"
 #   edges; block pass stream and fused stream (articulation points), the same density:
 #   2.1471 GB read + 7.6 MB written, and 2.1402 GB read + 0.4 MB written, for 267,444,294
 #   streamed edges each
-TRAFFIC = {"certify_sha": "4075a6058190271e", "bytes_per_edge": 8.0229,
+TRAFFIC = {"certify_sha": "245b7bcea88905d1", "bytes_per_edge": 8.0245,
            "source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of the forest pass at density 1/8 "
                      "(268 M edges), scaled to a full launch by its streamed edges"}
-AP_TRAFFIC = {"blocks_sha": "ed26c4b0ffd195fe", "bytes_per_edge": 8.0566,
+AP_TRAFFIC = {"blocks_sha": "461b023b22eb6faa", "bytes_per_edge": 8.0566,
               "source": "ncu dram bytes of the block pass stream at density 1/8, scaled by streamed edges"}
-FUSED_TRAFFIC = {"blocks_sha": "ed26c4b0ffd195fe", "bytes_per_edge": 8.0040,
+FUSED_TRAFFIC = {"blocks_sha": "461b023b22eb6faa", "bytes_per_edge": 8.0040,
                  "source": "ncu dram bytes of the fused stream at density 1/8, scaled by streamed edges"}
 
 
@@ -789,7 +789,7 @@ def make_batch(seed, count):
 
 
 def batched_leg(args, dev, with_cpu=True):
-    """The batched workload (4,096 graphs in one persistent launch per step) on device `dev`:
+    """The batched workload (4,096 graphs, two persistent launches per step) on device `dev`:
     graphs/s, per-step latency, the last timed step's output against the oracle, one plain call
     per graph for comparison.  Returns a dict (the standalone line's body)."""
     import concurrent.futures
@@ -885,7 +885,7 @@ def batched_leg(args, dev, with_cpu=True):
         "input_GE_per_s": E / (ms * 1e-3) / 1e9,
         "roofline": {"bound": "hbm", "achieved": 8.0 * E / (ms * 1e-3) / 1e9, "peak": peak, "unit": "GB/s",
                      "frac": 8.0 * E / (ms * 1e-3) / 1e9 / peak, "peak_kind": kind,
-                     "kernel": "batched_kernel (whole step)"},
+                     "kernel": "certify_kernel + bridge_kernel (whole step)"},
         "plain_per_graph": {"value": G / (ms_plain * 1e-3), "unit": "graphs/s", "ms_total": ms_plain,
                             "note": "one bridges_find_ctx call per graph on the same stream"},
         "speedup_vs_plain": ms_plain / ms,
