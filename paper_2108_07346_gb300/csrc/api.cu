@@ -645,8 +645,8 @@ namespace {
 
 // Layout of the batched workspace for the given capacities (bytes from the start).
 struct BLayout {
-  size_t args, ntasks, queue, tasks, done, gerr, slots, total;
-  size_t s_args, s_ntasks, s_tasks, s_total;  // pinned staging
+  size_t args, ntasks, queue, tasks, corder, gerr, slots, total;
+  size_t s_args, s_ntasks, s_tasks, s_corder, s_total;  // pinned staging
 };
 
 BLayout blayout(int64_t task_cap, int64_t graph_cap, int64_t slot_cap) {
@@ -660,11 +660,11 @@ BLayout blayout(int64_t task_cap, int64_t graph_cap, int64_t slot_cap) {
   o += 256;
   L.tasks = L.s_tasks = o;
   o += align_up(sizeof(BatchTask) * (size_t)task_cap, 256);
+  L.corder = L.s_corder = o;
+  o += align_up(sizeof(int32_t) * (size_t)task_cap, 256);
   L.s_total = o;
   L.queue = o;
   o += 256;
-  L.done = o;
-  o += align_up(sizeof(int32_t) * (size_t)graph_cap, 256);
   L.gerr = o;
   o += align_up(sizeof(int32_t) * (size_t)graph_cap, 256);
   L.slots = o;
@@ -723,7 +723,7 @@ int64_t ensure_batched(bridges_ctx* c, cudaStream_t s, int64_t ntasks, int64_t G
     cudaGraph_t graph;
     ok = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
     ok = ok && cudaMemsetAsync(d + L.queue, 0, 256, cs) == cudaSuccess;
-    ok = ok && cudaMemsetAsync(d + L.done, 0, L.slots - L.done, cs) == cudaSuccess;  // done and gerr
+    ok = ok && cudaMemsetAsync(d + L.gerr, 0, L.slots - L.gerr, cs) == cudaSuccess;
     ok = ok && cudaMemcpyAsync(d, c->bstage[k], L.s_total, cudaMemcpyHostToDevice, cs) == cudaSuccess;
     ok = ok && batched_launch(cs, reinterpret_cast<const BatchArgs*>(d + L.args), c->num_sms);
     ok = (cudaStreamEndCapture(cs, &graph) == cudaSuccess) && ok;
@@ -775,14 +775,14 @@ int64_t plan_batch_tasks(const bridges_ctx* c, std::vector<BatchTask>& graphs, i
       BatchTask t = g;
       t.lo = g.lo + E * p / np;
       t.hi = g.lo + E * (p + 1) / np;
-      t.slot = np > 1 ? slot + (int64_t)p * (2 + 2 * (int64_t)g.V) : 0;
+      t.slot = slot + (int64_t)p * batch_slot_words(g.V);  // every task's certificate gets a slot
       t.part = p;
       t.nparts = np;
       t.cls = cls;
       t.warm = warm;
       tasks.push_back(t);
     }
-    if (np > 1) slot += (int64_t)np * (2 + 2 * (int64_t)g.V);
+    slot += (int64_t)np * batch_slot_words(g.V);
   }
   // whole-block tasks first, then the ones for half and for quarter blocks; largest first in each
   std::stable_sort(tasks.begin(), tasks.end(), [](const BatchTask& x, const BatchTask& y) {
@@ -793,8 +793,8 @@ int64_t plan_batch_tasks(const bridges_ctx* c, std::vector<BatchTask>& graphs, i
   return slot;
 }
 
-// Enqueues one persistent launch over `tasks` (G graphs) on stream s, through the context's
-// cached CUDA graph.
+// Enqueues the two persistent launches over `tasks` (G graphs: certification, then the bridge
+// stages) on stream s, through the context's cached CUDA graph.
 int64_t launch_batch_tasks(bridges_ctx* c, cudaStream_t s, const std::vector<BatchTask>& tasks, int32_t G,
                            int64_t slot_words) {
   if (tasks.empty()) return BRIDGES_OK;
@@ -812,9 +812,9 @@ int64_t launch_batch_tasks(bridges_ctx* c, cudaStream_t s, const std::vector<Bat
   char* h = static_cast<char*>(c->bstage[k]);
   BatchArgs A{};
   A.tasks = reinterpret_cast<const BatchTask*>(d + L.tasks);
+  A.corder = reinterpret_cast<const int32_t*>(d + L.corder);
   A.d_ntasks = reinterpret_cast<const int32_t*>(d + L.ntasks);
   A.queue = reinterpret_cast<int32_t*>(d + L.queue);
-  A.done = reinterpret_cast<int32_t*>(d + L.done);
   A.gerr = reinterpret_cast<int32_t*>(d + L.gerr);
   A.slots = reinterpret_cast<uint32_t*>(d + L.slots);
   A.G = G;
@@ -832,15 +832,23 @@ int64_t launch_batch_tasks(bridges_ctx* c, cudaStream_t s, const std::vector<Bat
     }
   A.nbig = nbig;
   A.nmid = nmid;
+  // certification order: most edges first
+  std::vector<int32_t>& order = c->b_order;
+  order.resize(n);
+  for (int32_t i = 0; i < n; i++) order[i] = i;
+  std::stable_sort(order.begin(), order.end(), [&](int32_t x, int32_t y) {
+    return tasks[x].hi - tasks[x].lo > tasks[y].hi - tasks[y].lo;
+  });
   A.slot_words = c->b_slot_cap;
   std::memcpy(h + L.s_args, &A, sizeof(A));
   const int32_t nt = (int32_t)tasks.size();
   std::memcpy(h + L.s_ntasks, &nt, sizeof(nt));
   std::memcpy(h + L.s_tasks, tasks.data(), sizeof(BatchTask) * tasks.size());
+  std::memcpy(h + L.s_corder, order.data(), sizeof(int32_t) * tasks.size());
   if (cudaStreamWaitEvent(s, c->b_done_ev[k ^ 1], 0) != cudaSuccess) return cuda_fail(cudaGetLastError());
   if (cudaGraphLaunch(c->b_exec[k], s) != cudaSuccess) return cuda_fail(cudaGetLastError());
   if (cudaEventRecord(c->b_done_ev[k], s) != cudaSuccess) return cuda_fail(cudaGetLastError());
-  c->launches += 1;
+  c->launches += 2;
   return BRIDGES_OK;
 }
 

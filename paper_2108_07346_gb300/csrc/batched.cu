@@ -1,22 +1,24 @@
-// batched.cu -- many small graphs in one persistent launch.
+// batched.cu -- many small graphs in two persistent launches.
 //
-// Each block repeatedly takes a task from an atomic queue.  A task is a whole graph (V <= 4096)
-// or one partition of a large one (Sec. 3: the edge list split into contiguous sets).  The block
-// certifies the task's edges with two concurrent union-finds in SHARED memory (Alg. 2: F, then F'
-// from the edges F rejects), so a graph never touches global memory except to read its edges.
-// A single-task graph then runs the whole bridge stage in shared memory; a partitioned graph
-// writes its certificate to a global slot, and the block that finishes the graph's LAST
-// partition merges all of them (Sec. 3 merge, fan-in = number of partitions) and runs the
-// bridge stage.  Nothing waits on another block, so there is no spin anywhere.
+// Certification (certify_kernel): four 256-thread groups per block take tasks from an atomic
+// queue.  A task is a whole graph (V <= 4096) or one partition of its edge list (Sec. 3: the edges
+// split into contiguous sets).  The group certifies the task's edges with two concurrent
+// union-finds in SHARED memory (Alg. 2: F, then F' from the edges F rejects) and appends the
+// winners to the task's slot in global memory, so it holds only the union-finds (8 bytes per
+// vertex) and four graphs share an SM: while one runs its warm-up prefix edge by edge (latency
+// bound), the others stream their edges.
 //
-// The bridge stage is the same Euler-tour / preorder-range test as final.cu, on 16-bit arrays
-// with barriers between phases (list ranking by a ruling set, subtree ranges of more than 32
-// entries tested by a whole warp), then a rank sort of
-// the packed (a << 12 | b) keys (bitonic above 1,024 bridges).  A graph's fixed cost is its barriers,
-// so the stage keeps their number low, and graphs of up to 2,048 vertices run two per block (and
-// of up to 1,024 four per block): the block splits into 512-thread (then 256-thread) groups with
-// their own share of shared memory and their own named barrier, so that one graph's barrier
-// waits overlap with the others' work.
+// Bridges (bridge_kernel): per graph, a group offers the F then F' edges of every one of the
+// graph's slots to fresh union-finds in shared memory (for one slot this rebuilds the same two
+// forests; for several it is the Sec. 3 merge with fan-in = the number of partitions) and runs the
+// bridge stage.  The stage is the same Euler-tour / preorder-range test as final.cu, on 16-bit
+// arrays with barriers between phases (list ranking by a ruling set, subtree ranges of more than
+// 32 entries tested by a whole warp), then a rank sort of the packed (a << 12 | b) keys (bitonic
+// above 1,024 bridges).  A graph's fixed cost is its barriers, so graphs of up to 2,048 vertices
+// run two per block (and of up to 1,024 four per block): the block splits into 512-thread (then
+// 256-thread) groups with their own share of shared memory and their own named barrier, so that
+// one graph's barrier waits overlap with the others' work.  Nothing waits on another block, so
+// there is no spin anywhere.
 #include <algorithm>
 
 #include "../../include/bridges.h"
@@ -159,7 +161,8 @@ __device__ __forceinline__ uint16_t inc16(uint16_t* a, int i) {
 }
 
 // Concurrent union-find in shared memory: the algorithm of uf_link (common.cuh) -- parents are
-// compared first, a root is hooked under a smaller vertex, P[x] <= x always.
+// compared first (a grandparent equal to the other end's parent also proves one set), a root is
+// hooked under the other end's parent, a smaller vertex, so P[x] <= x always.
 __device__ __forceinline__ bool s_link(int32_t* P, int32_t a, int32_t b) {
   volatile int32_t* VP = P;
   int32_t x = a, y = b;
@@ -175,16 +178,19 @@ __device__ __forceinline__ bool s_link(int32_t* P, int32_t a, int32_t b) {
       py = t;
     }
     if (px == x) {
-      int32_t r = py, q = VP[r];  // hook under the other side's root (shallow trees)
-      while (q != r) {
-        r = q;
-        q = VP[r];
-      }
-      if (atomicCAS(P + x, x, r) == x) return true;
+      if (atomicCAS(P + x, x, py) == x) return true;
       continue;
     }
     const int32_t g = VP[px];
-    if (g != px) VP[x] = g;
+    if (g == py) {
+      VP[x] = g;
+      return false;
+    }
+    if (g == px) {
+      if (atomicCAS(P + px, px, py) == px) return true;
+      continue;
+    }
+    VP[x] = g;
     x = g;
   }
 }
@@ -304,10 +310,14 @@ template <int NT>
 __device__ void s_certify_scalar(const Grp<NT>& G, const Smem& S, const int32_t* __restrict__ u, const int32_t* __restrict__ v,
                                  int64_t lo, int64_t hi, int32_t V, int32_t* n1, int32_t* n2, int32_t* err) {
   volatile int32_t* P2 = S.P2;
-  for (int64_t t0 = lo; t0 < hi; t0 += NT) {
-    const int64_t i = t0 + G.tid;
+  // the next step's edge is loaded before this step's union-find work, so the load's latency
+  // overlaps it instead of adding to every step
+  int64_t i = lo + G.tid;
+  int32_t a = i < hi ? __ldcs(u + i) : 0, b = i < hi ? __ldcs(v + i) : 0;
+  for (int64_t t0 = lo; t0 < hi; t0 += NT, i += NT) {
     const bool valid = i < hi;
-    const int32_t a = valid ? __ldcs(u + i) : 0, b = valid ? __ldcs(v + i) : 0;
+    const int64_t j = i + NT;
+    const int32_t na = j < hi ? __ldcs(u + j) : 0, nb = j < hi ? __ldcs(v + j) : 0;
     bool need = valid;
     if (need && ((uint32_t)a >= (uint32_t)V || (uint32_t)b >= (uint32_t)V)) {
       *err = BRIDGES_ERANGE;
@@ -315,6 +325,8 @@ __device__ void s_certify_scalar(const Grp<NT>& G, const Smem& S, const int32_t*
     }
     if (need && (a == b || P2[a] == P2[b])) need = false;
     s_settle(S, need, a, b, n1, n2, V);
+    a = na;
+    b = nb;
   }
 }
 
@@ -419,14 +431,14 @@ __device__ void s_certify_range(const Grp<NT>& G, const Smem& S, const int32_t* 
   s_certify_vec<NT, VM>(G, S, u, v, lo, hi, V, n1, n2, err);
 }
 
-// Certifies packed edges (a | b << 16) of a global list.
+// Certifies packed edges (a | b << 16) of a list in shared memory.
 template <int NT>
 __device__ void s_certify_packed(const Grp<NT>& G, const Smem& S, const uint32_t* e, int32_t n, int32_t V, int32_t* n1, int32_t* n2) {
   volatile int32_t* P2 = S.P2;
   for (int32_t t0 = 0; t0 < n; t0 += NT) {
     const int32_t i = t0 + G.tid;
     const bool valid = i < n;
-    const uint32_t x = valid ? __ldcg(e + i) : 0;
+    const uint32_t x = valid ? e[i] : 0;
     const int32_t a = (int32_t)(x & 0xffff), b = (int32_t)(x >> 16);
     const bool need = valid && a != b && P2[a] != P2[b];
     s_settle(S, need, a, b, n1, n2, V);
@@ -714,22 +726,38 @@ __device__ int32_t s_bridges(const Grp<NT>& G, const Smem& S, int32_t V, int32_t
   return n;
 }
 
-// One task -- a whole graph, or one partition of a large graph -- by a group of NT threads whose
-// graphs have at most VM vertices.
-template <int NT, int VM>
-__device__ void run_task(const BatchArgs& A, const BatchTask& T, const Smem& S, const Grp<NT>& G, GroupShared& gs) {
+constexpr int kAT = 256;               // threads of a certification group
+constexpr int kAGroups = kT / kAT;     // certification groups per block
+constexpr int kABytes = 8 * kVmax;     // a certification group's union-finds (P1, P2)
+
+// The certificate slot of task T (batch_slot_words).
+__device__ __forceinline__ uint32_t* task_slot(const BatchArgs& A, const BatchTask& T) { return A.slots + T.slot; }
+
+// Whether T's descriptor can be used (a malformed one is skipped, never used to index memory).
+__device__ __forceinline__ bool task_ok(const BatchArgs& A, const BatchTask& T) {
+  const int64_t stride = batch_slot_words(T.V);
+  return T.V >= 0 && T.V <= kVmax && T.lo >= 0 && T.hi >= T.lo && T.g >= 0 && T.g < A.G && T.nparts >= 1 &&
+         T.part >= 0 && T.part < T.nparts && T.count && (T.V <= 1 || T.out) && T.slot >= (int64_t)T.part * stride &&
+         T.slot + (int64_t)(T.nparts - T.part) * stride <= A.slot_words;
+}
+
+// Certifies task T by group G of NT threads (shared memory: the two union-finds); the winners go
+// to T's slot.
+template <int NT>
+__device__ void certify_task(const BatchArgs& A, const BatchTask& T, char* smem, const Grp<NT>& G,
+                             GroupShared& gs) {
   const int tid = G.tid;
-  const int32_t V = T.V;
-  // a malformed descriptor is skipped, never used to index shared memory; partitioned graphs
-  // (which merge through the slots) only run on whole blocks
-  const int64_t stride = 2 + 2 * (int64_t)V;
-  if (V < 0 || V > VM || T.lo < 0 || T.hi < T.lo || T.g < 0 || T.g >= A.G || T.nparts < 1 || T.part < 0 ||
-      T.part >= T.nparts || !T.count || (V > 1 && !T.out) || (T.nparts > 1 && NT != kT) ||
-      (T.nparts > 1 &&
-       (T.slot < (int64_t)T.part * stride || T.slot + (int64_t)(T.nparts - T.part) * stride > A.slot_words))) {
-    if (tid == 0 && T.count) *T.count = BRIDGES_EINTERNAL;
+  if (!task_ok(A, T)) {
+    if (tid == 0 && T.g >= 0 && T.g < A.G) atomicExch(A.gerr + T.g, BRIDGES_EINTERNAL);
     return;
   }
+  const int32_t V = T.V;
+  uint32_t* slot = task_slot(A, T);
+  Smem S{};
+  S.P1 = reinterpret_cast<int32_t*>(smem);
+  S.P2 = S.P1 + kVmax;
+  S.F1 = slot + 2;      // global: winners are appended straight to the slot
+  S.F2 = slot + 2 + V;
   for (int x = tid; x < V; x += NT) {
     S.P1[x] = x;
     S.P2[x] = x;
@@ -740,46 +768,78 @@ __device__ void run_task(const BatchArgs& A, const BatchTask& T, const Smem& S, 
     gs.err = 0;
   }
   G.sync();
-  s_certify_range<NT, VM>(G, S, T.u, T.v, T.lo, T.hi, T.warm, V, &gs.n1, &gs.n2, &gs.err);
+  s_certify_range<NT, kVmax>(G, S, T.u, T.v, T.lo, T.hi, T.warm, V, &gs.n1, &gs.n2, &gs.err);
+  if (T.nparts == 1) {  // the graph's one task: its F trees' roots too, so the bridge stage needs no union-find
+    s_flatten(G, S.P1, V);
+    uint16_t* roots = reinterpret_cast<uint16_t*>(slot + 2 + 2 * (int64_t)V);
+    for (int x = tid; x < V; x += NT) roots[x] = (uint16_t)S.P1[x];
+  }
   G.sync();
-  int32_t nt = min(gs.n1, V), nx = min(gs.n2, V);
-  if (T.nparts > 1) {
-    // publish this partition's certificate; the last partition of the graph merges
-    uint32_t* slot = A.slots + T.slot;
-    for (int i = tid; i < nt; i += NT) slot[2 + i] = S.F1[i];
-    for (int i = tid; i < nx; i += NT) slot[2 + nt + i] = S.F2[i];
+  if (tid == 0) {
+    slot[0] = (uint32_t)min(gs.n1, V);
+    slot[1] = (uint32_t)min(gs.n2, V);
+    if (gs.err) atomicExch(A.gerr + T.g, gs.err);
+  }
+}
+
+// Bridges of the graph whose first task is T (later partitions are skipped): its slots' F and F'
+// edges offered to fresh union-finds (one slot: the same two forests again; several: the Sec. 3
+// merge), then the bridge stage, by a group of NT threads whose graphs have at most VM vertices.
+template <int NT, int VM>
+__device__ void bridge_task(const BatchArgs& A, const BatchTask& T, const Smem& S, const Grp<NT>& G, GroupShared& gs) {
+  const int tid = G.tid;
+  if (T.part != 0) return;
+  if (!task_ok(A, T) || T.V > VM) {
+    if (tid == 0 && T.count) *T.count = BRIDGES_EINTERNAL;
+    return;
+  }
+  const int32_t V = T.V;
+  const int64_t stride = batch_slot_words(V);
+  if (tid == 0) {
+    gs.n1 = 0;
+    gs.n2 = 0;
+    gs.err = ld_relaxed(A.gerr + T.g);
+  }
+  if (T.nparts == 1) {
+    // one task: its F and F' are the graph's certificate as they stand, and the roots of the F
+    // trees come with them (P1 then holds each vertex's root: the stage's root walk is one step)
+    const uint32_t* sp = task_slot(A, T);
+    const int32_t nf = min((int32_t)__ldcg(sp), V), nx = min((int32_t)__ldcg(sp + 1), V);
+    const uint16_t* roots = reinterpret_cast<const uint16_t*>(sp + 2 + 2 * (int64_t)V);
+#pragma unroll 4
+    for (int32_t i = tid; i < nf; i += NT) S.F1[i] = __ldcg(sp + 2 + i);
+#pragma unroll 4
+    for (int32_t i = tid; i < nx; i += NT) S.F2[i] = __ldcg(sp + 2 + V + i);
+#pragma unroll 4
+    for (int32_t x = tid; x < V; x += NT) S.P1[x] = min((int32_t)__ldcg(roots + x), V - 1);
     if (tid == 0) {
-      slot[0] = (uint32_t)nt;
-      slot[1] = (uint32_t)nx;
-      if (gs.err) atomicExch(A.gerr + T.g, gs.err);
+      gs.n1 = nf;
+      gs.n2 = nx;
     }
-    __threadfence();
     G.sync();
-    if (tid == 0) gs.flag = atomicAdd(A.done + T.g, 1) == T.nparts - 1;
-    G.sync();
-    if (!gs.flag) return;
-    __threadfence();
-    // merge: certify the union of every partition's certificate (this one included)
+  } else {
+    // several tasks: the Sec. 3 merge -- every slot's F, then F', offered to fresh union-finds;
+    // each slot is first copied to shared memory (the dst / twin region, 2 VM words, free until
+    // the bridge stage) with all of a thread's loads in flight
     for (int x = tid; x < V; x += NT) {
       S.P1[x] = x;
       S.P2[x] = x;
     }
-    if (tid == 0) {
-      gs.n1 = 0;
-      gs.n2 = 0;
-      const int32_t e = ld_relaxed(A.gerr + T.g);
-      if (e) gs.err = e;
-    }
     G.sync();
+    uint32_t* stage = reinterpret_cast<uint32_t*>(S.dst);
     for (int p = 0; p < T.nparts; p++) {
-      const uint32_t* sp = A.slots + T.slot - (int64_t)T.part * stride + (int64_t)p * stride;
-      const int32_t pn = (int32_t)(__ldcg(sp) + __ldcg(sp + 1));
-      s_certify_packed(G, S, sp + 2, min(pn, 2 * V), V, &gs.n1, &gs.n2);
+      const uint32_t* sp = task_slot(A, T) + (int64_t)p * stride;
+      const int32_t nf = min((int32_t)__ldcg(sp), V), nx = min((int32_t)__ldcg(sp + 1), V);
+#pragma unroll 8
+      for (int32_t i = tid; i < nf; i += NT) stage[i] = __ldcg(sp + 2 + i);
+#pragma unroll 8
+      for (int32_t i = tid; i < nx; i += NT) stage[nf + i] = __ldcg(sp + 2 + V + i);
+      G.sync();
+      s_certify_packed(G, S, stage, nf + nx, V, &gs.n1, &gs.n2);  // F first, then F'
       G.sync();
     }
-    nt = min(gs.n1, V);
-    nx = min(gs.n2, V);
   }
+  const int32_t nt = min(gs.n1, V), nx = min(gs.n2, V);
   if (gs.err) {
     G.sync();  // every thread has read gs.err before the next task resets it
     if (tid == 0) *T.count = gs.err;
@@ -789,7 +849,7 @@ __device__ void run_task(const BatchArgs& A, const BatchTask& T, const Smem& S, 
   if (tid == 0) *T.count = nb;
 }
 
-// Takes tasks first + 0, 1, ... from `queue` until `last` and runs them on group G.
+// Takes tasks first + 0, 1, ... from `queue` until `last` and runs their bridge stage on group G.
 template <int NT, int VM>
 __device__ void run_queue(const BatchArgs& A, char* smem, const Grp<NT>& G, GroupShared& gs, int32_t* queue,
                           int32_t first, int32_t last) {
@@ -800,17 +860,46 @@ __device__ void run_queue(const BatchArgs& A, char* smem, const Grp<NT>& G, Grou
     G.sync();
     const int32_t t = gs.task;
     if (t >= last) break;
-    run_task<NT, VM>(A, A.tasks[t], S, G, gs);
+    bridge_task<NT, VM>(A, A.tasks[t], S, G, gs);
   }
 }
 
-// Persistent: whole-block tasks first (graphs above kHalfVmax vertices and the partitions of
-// large graphs); then the block splits into two independent half-block groups, each with half
-// the shared memory and its own named barrier, for graphs of up to kHalfVmax vertices; when a
+// Takes tasks from `queue` (first + 0, 1, ... until `last`) and certifies them on group G.
+template <int NT>
+__device__ void certify_queue(const BatchArgs& A, char* smem, const Grp<NT>& G, GroupShared& gs, int32_t* queue,
+                              int32_t first, int32_t last) {
+  while (true) {
+    G.sync();
+    if (G.tid == 0) gs.task = first + atomicAdd(queue, 1);
+    G.sync();
+    const int32_t t = gs.task;
+    if (t >= last) break;
+    certify_task<NT>(A, A.tasks[A.corder[t]], smem, G, gs);
+  }
+}
+
+// Persistent certification: four 256-thread groups per block (named barriers 1-4), each with a
+// quarter of the shared memory, take the tasks in corder (most edges first, so that the longest
+// lists start early); one group's warm-up prefix (edge by edge, latency bound) overlaps the other
+// groups' streams.  (Whole blocks for the long tasks were measured slower: a block alone on its
+// SM has no other group's stream to hide its own prefix behind.)
+__global__ void __launch_bounds__(kT, 1) certify_kernel(const BatchArgs* __restrict__ dA) {
+  const BatchArgs A = *dA;
+  extern __shared__ __align__(16) char smem_raw[];
+  __shared__ GroupShared gs[kAGroups];
+  const int32_t ntasks = *A.d_ntasks;
+  const int k = (int)threadIdx.x / kAT;
+  certify_queue<kAT>(A, smem_raw + k * kABytes, Grp<kAT>{(int)threadIdx.x % kAT, 1 + k}, gs[k], A.queue + 3, 0,
+                     ntasks);
+}
+
+// Persistent bridge stages: whole-block tasks first (graphs above kHalfVmax vertices and
+// partitioned graphs); then the block splits into two independent half-block groups, each with
+// half the shared memory and its own named barrier, for graphs of up to kHalfVmax vertices; when a
 // half runs out of those it splits again into two quarter-block groups for graphs of up to
 // kQuarterVmax.  A small graph's cost is mostly its barriers, and this overlaps up to four of
 // them on one SM.  No barrier spans groups after the first split.
-__global__ void __launch_bounds__(kT, 1) batched_kernel(const BatchArgs* __restrict__ dA) {
+__global__ void __launch_bounds__(kT, 1) bridge_kernel(const BatchArgs* __restrict__ dA) {
   const BatchArgs A = *dA;
   extern __shared__ __align__(16) char smem_raw[];
   __shared__ GroupShared gs[6];  // [0] the block, then [h] each half, then [2 + 2h + q] each quarter
@@ -835,10 +924,12 @@ __global__ void __launch_bounds__(kT, 1) batched_kernel(const BatchArgs* __restr
 size_t batched_smem_bytes() { return (size_t)kSmem; }
 
 bool batched_launch(cudaStream_t s, const BatchArgs* dev_args, int num_sms) {
-  // function attributes are per device: set on every launch (a host-side call; the launch is
+  // function attributes are per device: set on every launch (a host-side call; the launches are
   // usually replayed from a CUDA graph anyway)
-  cudaFuncSetAttribute(batched_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem);
-  batched_kernel<<<num_sms, kT, kSmem, s>>>(dev_args);
+  cudaFuncSetAttribute(certify_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kAGroups * kABytes);
+  cudaFuncSetAttribute(bridge_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem);
+  certify_kernel<<<num_sms, kT, kAGroups * kABytes, s>>>(dev_args);
+  bridge_kernel<<<num_sms, kT, kSmem, s>>>(dev_args);
   return cudaGetLastError() == cudaSuccess;
 }
 

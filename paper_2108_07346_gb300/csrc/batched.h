@@ -17,8 +17,8 @@ struct BatchTask {
   int64_t lo, hi;    // edge range of this task in u / v
   int32_t* out;      // the graph's output pairs
   int64_t* count;    // the graph's count (or negative status)
-  int64_t slot;      // u32 offset of this partition's certificate slot (nparts > 1)
-  int32_t g;         // graph index within the launch (done / gerr counters)
+  int64_t slot;      // u32 offset of this task's certificate slot (batch_slot_words(V); a graph's are consecutive)
+  int32_t g;         // graph index within the launch (its gerr word)
   int32_t part;      // partition index within the graph
   int32_t nparts;    // partitions of the graph
   int32_t V;         // vertices of the graph
@@ -31,19 +31,19 @@ struct BatchTask {
 // caller's pointers change between calls.
 struct BatchArgs {
   const BatchTask* tasks;
+  const int32_t* corder;  // certification order: task indices, most edges first
   const int32_t* d_ntasks;
-  int32_t* queue;    // next task (atomic)
-  int32_t* done;     // per graph: partitions finished
+  int32_t* queue;    // next task (atomic): [0..2] bridge stages by group size, [3] certification
   int32_t* gerr;     // per graph: first error of any partition
-  uint32_t* slots;   // certificates of partitions
+  uint32_t* slots;   // the tasks' certificates
   int32_t G;           // graphs (bounds the graph index of every task)
-  int32_t nbig;        // tasks [0, nbig) run on whole blocks,
+  int32_t nbig;        // bridge stages: tasks [0, nbig) run on whole blocks,
   int32_t nmid;        // [nbig, nbig + nmid) on half-block groups, the rest on quarter-block groups
   int64_t slot_words;  // capacity of slots (u32)
 };
 
 // The smallest group a task fits: 0 a whole block (more than kBatchHalfVmax vertices, or a
-// partition of a graph: partitions merge through the slots), 1 a half block, 2 a quarter block.
+// partition of a graph: partitions merge from the slots), 1 a half block, 2 a quarter block.
 inline int batch_min_class(int32_t V, int32_t nparts) {
   if (V > kBatchHalfVmax || nparts > 1) return 0;
   return V > kBatchQuarterVmax ? 1 : 2;
@@ -53,8 +53,13 @@ inline int batch_min_class(int32_t V, int32_t nparts) {
 // smallest it fits; never a smaller one).
 inline int batch_task_class(const BatchTask& t) { return t.cls; }
 
+// Words of a task's certificate slot: [nF, nF', F (V words), F' (V words), the root of each
+// vertex's F tree (V u16, written for a graph of one task)].  A graph's slots are consecutive.
+__host__ __device__ inline int64_t batch_slot_words(int32_t V) { return 2 + 2 * (int64_t)V + ((int64_t)V + 1) / 2; }
+
 size_t batched_smem_bytes();
-// Launches the persistent kernel (one block per SM) reading its arguments from *dev_args.
+// Launches the two persistent kernels (one block per SM each: certification, then the bridge
+// stages) reading their arguments from *dev_args.
 bool batched_launch(cudaStream_t s, const BatchArgs* dev_args, int num_sms);
 
 }  // namespace bridges

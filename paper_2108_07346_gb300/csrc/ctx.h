@@ -40,11 +40,12 @@ struct bridges_ctx {
   float ap_ms[kRing][5]{};
   // batched path: device descriptors; two pinned staging copies used in turn, each with the CUDA
   // graph that uploads from it and the event of the last batch that read it
-  void* bws = nullptr;          // device: BatchArgs | ntasks | queue | tasks[cap] | done[gcap] | gerr[gcap] | slots
+  void* bws = nullptr;          // device: BatchArgs | ntasks | tasks[cap] | corder[cap] | queue | gerr[gcap] | slots
   size_t bws_bytes = 0;
-  void* bstage[2]{};             // pinned: BatchArgs | ntasks | tasks[cap]
+  void* bstage[2]{};             // pinned: BatchArgs | ntasks | tasks[cap] | corder[cap]
   size_t bstage_bytes = 0;
   int64_t b_task_cap = 0, b_graph_cap = 0, b_slot_cap = 0;
+  std::vector<int32_t> b_order;  // the last batch's certification order (host scratch)
   cudaGraphExec_t b_exec[2]{};
   cudaEvent_t b_done_ev[2]{};
   int b_next = 0;                // the staging copy the next batch fills
