@@ -839,6 +839,10 @@ int64_t launch_batch_tasks(bridges_ctx* c, cudaStream_t s, const std::vector<Bat
   std::stable_sort(order.begin(), order.end(), [&](int32_t x, int32_t y) {
     return tasks[x].hi - tasks[x].lo > tasks[y].hi - tasks[y].lo;
   });
+  // the tail of small tasks that one group per SM takes from the back
+  int32_t nback = 0;
+  while (nback < n && tasks[order[n - 1 - nback]].hi - tasks[order[n - 1 - nback]].lo <= c->b_back_edges) nback++;
+  A.nback = nback;
   A.slot_words = c->b_slot_cap;
   std::memcpy(h + L.s_args, &A, sizeof(A));
   const int32_t nt = (int32_t)tasks.size();

@@ -1,24 +1,26 @@
 // batched.cu -- many small graphs in two persistent launches.
 //
-// Certification (certify_kernel): four 256-thread groups per block take tasks from an atomic
-// queue.  A task is a whole graph (V <= 4096) or one partition of its edge list (Sec. 3: the edges
-// split into contiguous sets).  The group certifies the task's edges with two concurrent
-// union-finds in SHARED memory (Alg. 2: F, then F' from the edges F rejects) and appends the
-// winners to the task's slot in global memory, so it holds only the union-finds (8 bytes per
-// vertex) and four graphs share an SM: while one runs its warm-up prefix edge by edge (latency
-// bound), the others stream their edges.
+// Certification (certify_kernel): four 256-thread groups per block take tasks from a queue with
+// two ends (most edges first; one group per block starts with the fewest).  A task is a whole
+// graph (V <= 4096) or one partition of its edge list (Sec. 3: the edges split into contiguous
+// sets).  The group certifies the task's edges with two concurrent union-finds in SHARED memory
+// (Alg. 2: F, then F' from the edges F rejects) and appends the winners to the task's slot in
+// global memory, so it holds only the union-finds (8 bytes per vertex) and four graphs share an
+// SM: while one runs its warm-up prefix edge by edge (latency bound), the others stream their
+// edges.  A graph of up to 1,024 vertices (one task) is certified straight into the bridge
+// stage's shared-memory layout and its bridge stage runs right there, beside the other groups'
+// streams.
 //
-// Bridges (bridge_kernel): per graph, a group offers the F then F' edges of every one of the
-// graph's slots to fresh union-finds in shared memory (for one slot this rebuilds the same two
-// forests; for several it is the Sec. 3 merge with fan-in = the number of partitions) and runs the
-// bridge stage.  The stage is the same Euler-tour / preorder-range test as final.cu, on 16-bit
-// arrays with barriers between phases (list ranking by a ruling set, subtree ranges of more than
-// 32 entries tested by a whole warp), then a rank sort of the packed (a << 12 | b) keys (bitonic
-// above 1,024 bridges).  A graph's fixed cost is its barriers, so graphs of up to 2,048 vertices
-// run two per block (and of up to 1,024 four per block): the block splits into 512-thread (then
-// 256-thread) groups with their own share of shared memory and their own named barrier, so that
-// one graph's barrier waits overlap with the others' work.  Nothing waits on another block, so
-// there is no spin anywhere.
+// Bridges (bridge_kernel), for the larger graphs: per graph, a group copies its certificate from
+// its slot (one task) or offers the F then F' edges of every one of the graph's slots to fresh
+// union-finds in shared memory (several: the Sec. 3 merge with fan-in = the number of partitions)
+// and runs the bridge stage.  The stage is the same Euler-tour / preorder-range test as final.cu,
+// on 16-bit arrays with barriers between phases (list ranking by a ruling set, subtree ranges
+// from shuffle windows and chunk extrema), then a rank sort of the packed (a << 12 | b) keys
+// (bitonic above the group's thread count).  A graph's fixed cost is its barriers, so graphs of
+// up to 2,048 vertices run two per block: the block splits into 512-thread groups with their own
+// half of shared memory and their own named barrier, so that one graph's barrier waits overlap
+// with the other's work.  Nothing waits on another block, so there is no spin anywhere.
 #include <algorithm>
 
 #include "../../include/bridges.h"
@@ -40,17 +42,17 @@ constexpr int kRuleGap = 8;  // list ranking: a ruler every kRuleGap arcs (by in
 
 constexpr int a16(int x) { return (x + 15) & ~15; }
 // Shared-memory layout for graphs of up to VM vertices (bytes, each region a multiple of 16),
-// in address order R0, R2, R1, R3, ... so that R0 and R2 (both free while the tour is ranked)
-// form one buffer of 8 VM bytes:
-//   R0  P1 (int32[V]); later each arc's ruler and place (with R2); later aoff + vbase (u16[V+1] each)
+// in address order R0, R2, R1, R3, ...:
+//   R0  P1 (int32[V]); later each arc's ruler (u16[2V]); later aoff + vbase (u16[V+1] each);
+//       later the chunk tables of the range test
 //   R1  P2 (int32[V]); later root + cur (u16[V+2] each)
 //   R2  F list (u32[V]); later bridge keys (u32[V])
 //   R3  F' list (u32[V])
-//   R4  off (u16[V+2]); later chunk minima / maxima
-//   R5  dst (u16[2V]); later lo (int32[V])
-//   R6  twin (u16[2V]); later hi (int32[V])
-//   R7  succ (u16[2V]); later dflag / dscan (u16[2V+1])
-//   R8  rnk (u16[2V])
+//   R4  chunk minima / maxima (int32[V/32] each)
+//   R5  head (int32[V]); later lo (int32[V]); before the stage, with R6, a merge's staging copy
+//   R6  next (u16[2V]); later each arc's place in its sublist; later hi (int32[V])
+//   R7  succ (u16[2V]); later dflag / dscan (u16[2V+1]); later in-chunk prefix extrema (u16[V] x 2)
+//   R8  rnk (u16[2V]); later the vertex at each preorder position
 //   R9  pre, sz, par (u16[V] each); earlier the rulers' two packed buffers (3 VM / 4 words each)
 template <int VM>
 struct Layout {
@@ -59,7 +61,7 @@ struct Layout {
   static constexpr int R1 = R0;
   static constexpr int R2 = 4 * VM;
   static constexpr int R3 = 4 * VM;
-  static constexpr int R4 = kU16 > VM / 4 ? kU16 : VM / 4;
+  static constexpr int R4 = VM / 4;
   static constexpr int R5 = 4 * VM;
   static constexpr int R6 = 4 * VM;
   static constexpr int R7 = a16(2 * (2 * VM + 8));
@@ -82,9 +84,10 @@ struct Smem {
   uint16_t* root;
   uint16_t* cur;
   uint32_t* keys;
-  uint16_t* off;
+  int32_t* chunk;
   uint16_t* dst;
-  uint16_t* twin;
+  int32_t* head;
+  uint16_t* next;
   int32_t* lo;
   int32_t* hi;
   uint16_t* succ;
@@ -113,12 +116,13 @@ __device__ Smem carve_smem(char* base) {
   c += L::R1;
   s.F2 = reinterpret_cast<uint32_t*>(c);
   c += L::R3;
-  s.off = reinterpret_cast<uint16_t*>(c);
+  s.chunk = reinterpret_cast<int32_t*>(c);
   c += L::R4;
   s.dst = reinterpret_cast<uint16_t*>(c);
+  s.head = reinterpret_cast<int32_t*>(c);
   s.lo = reinterpret_cast<int32_t*>(c);
   c += L::R5;
-  s.twin = reinterpret_cast<uint16_t*>(c);
+  s.next = reinterpret_cast<uint16_t*>(c);
   s.hi = reinterpret_cast<int32_t*>(c);
   c += L::R6;
   s.succ = reinterpret_cast<uint16_t*>(c);
@@ -152,13 +156,6 @@ struct GroupShared {
   int32_t red_b[kT / 32];
   int32_t task, n1, n2, err, flag, sh;
 };
-
-// 16-bit counters packed two to a 32-bit word (shared-memory atomics are 32-bit).
-__device__ __forceinline__ uint16_t inc16(uint16_t* a, int i) {
-  uint32_t* w = reinterpret_cast<uint32_t*>(a + (i & ~1));
-  const int sh = 16 * (i & 1);
-  return (uint16_t)(atomicAdd(w, 1u << sh) >> sh);
-}
 
 // Concurrent union-find in shared memory: the algorithm of uf_link (common.cuh) -- parents are
 // compared first (a grandparent equal to the other end's parent also proves one set), a root is
@@ -450,7 +447,7 @@ template <int NT, int VM>
 __device__ int32_t s_bridges(const Grp<NT>& G, const Smem& S, int32_t V, int32_t nt, int32_t nx, int32_t* out,
                              int32_t* red, int32_t* red_b, int32_t* sh) {
   const int tid = G.tid;
-  // roots (minimum vertex of each tree), degrees
+  // roots (minimum vertex of each tree)
   for (int x = tid; x < V; x += NT) {
     int32_t r = x, p = S.P1[x];
     while (p != r) {
@@ -458,36 +455,26 @@ __device__ int32_t s_bridges(const Grp<NT>& G, const Smem& S, int32_t V, int32_t
       p = S.P1[r];
     }
     S.root[x] = (uint16_t)r;  // P2 region: F' union-find no longer needed
+    S.head[x] = -1;
   }
-  for (int x = tid; x <= V + 1; x += NT) S.off[x] = 0;
-  for (int x = tid; x < V + 2; x += NT) S.cur[x] = 0;
   G.sync();
+  // arcs 2e (a -> b) and 2e + 1 (b -> a) of tree edge e = F1[e] = (a, b): each vertex's outgoing
+  // arcs in a list (head, next) built by one atomic exchange per arc
+  const int32_t narcs = 2 * nt;
   for (int e = tid; e < nt; e += NT) {
     const uint32_t p = S.F1[e];
-    inc16(S.off, (int)(p & 0xffff));
-    inc16(S.off, (int)(p >> 16));
+    S.next[2 * e] = (uint16_t)atomicExch(S.head + (p & 0xffff), 2 * e);
+    S.next[2 * e + 1] = (uint16_t)atomicExch(S.head + (p >> 16), 2 * e + 1);
   }
   G.sync();
-  const int32_t narcs = block_scan16(G, S.off, V + 1, red);  // off[V] = narcs
-  for (int e = tid; e < nt; e += NT) {
-    const uint32_t p = S.F1[e];
-    const int32_t a = (int32_t)(p & 0xffff), b = (int32_t)(p >> 16);
-    const int32_t ia = S.off[a] + inc16(S.cur, a), ib = S.off[b] + inc16(S.cur, b);
-    S.dst[ia] = (uint16_t)b;
-    S.dst[ib] = (uint16_t)a;
-    S.twin[ia] = (uint16_t)ib;
-    S.twin[ib] = (uint16_t)ia;
-  }
-  G.sync();
-  // Euler-tour successors, cut at each root
+  // Euler-tour successors, cut at each root: after arc i into y comes the arc that follows i's
+  // twin (y's arc back) in y's list, wrapping to its first arc except at the root
   uint16_t* succ = S.succ;  // R7
   for (int i = tid; i < narcs; i += NT) {
-    const int32_t y = S.dst[i], t = S.twin[i];
-    uint16_t s;
-    if (t + 1 < S.off[y + 1])
-      s = (uint16_t)(t + 1);
-    else
-      s = S.root[y] == y ? kNone16 : S.off[y];
+    const uint32_t p = S.F1[i >> 1];
+    const int32_t y = (int32_t)((i & 1) ? (p & 0xffff) : (p >> 16));
+    uint16_t s = S.next[i ^ 1];
+    if (s == kNone16 && S.root[y] != y) s = (uint16_t)S.head[y];
     succ[i] = s;
   }
   if (tid == 0) *sh = 0;
@@ -499,25 +486,28 @@ __device__ int32_t s_bridges(const Grp<NT>& G, const Smem& S, int32_t V, int32_t
   // four hops per round; then every arc subtracts its place from its ruler's count.  Random
   // shared-memory loads bound this step, and this reads each arc about three times in all where
   // pointer jumping over every arc reads it four times a round.
-  //   R0 + R2 (free now): per arc, (ruler | place << 16)
+  //   R0 (free now) and R6 (next, free now): per arc, its ruler and its place (u16 each)
   //   R9 (pre / sz / par, written later): two buffers of packed (next ruler | arcs << 16) words
   //   R1's cur half (free now): the first arc of each extra ruler (heads off the kRuleGap grid)
   // A forest with t trees has at most (2V - 2t) / kRuleGap + t + 1 <= 5V/8 + 1 rulers.
   {
     const int32_t nreg = (narcs + kRuleGap - 1) / kRuleGap;
-    for (int x = tid; x < V; x += NT)
-      if (S.root[x] == x && S.off[x + 1] > S.off[x] && S.off[x] % kRuleGap != 0)
-        S.cur[atomicAdd(sh, 1)] = S.off[x];
+    for (int x = tid; x < V; x += NT) {
+      const int32_t h = S.head[x];
+      if (S.root[x] == x && h >= 0 && h % kRuleGap != 0) S.cur[atomicAdd(sh, 1)] = (uint16_t)h;
+    }
     G.sync();
     const int32_t nrul = nreg + *sh;
-    uint32_t* own = reinterpret_cast<uint32_t*>(S.P1);  // R0 + R2
+    uint16_t* oruler = reinterpret_cast<uint16_t*>(S.P1);  // R0
+    uint16_t* oplace = S.next;                             // R6
     uint32_t* ra = reinterpret_cast<uint32_t*>(S.pre);  // R9: 3 VM / 4 words each
     uint32_t* rb = ra + 3 * VM / 4;
     for (int k = tid; k < nrul; k += NT) {
       uint32_t i = k < nreg ? (uint32_t)(k * kRuleGap) : S.cur[k - nreg];
       uint32_t place = 0, next = kNone16;
       for (int32_t step = 0; step < narcs; step++) {  // a tour is a path: a sublist has < narcs arcs
-        own[i] = (uint32_t)k | (place << 16);
+        oruler[i] = (uint16_t)k;
+        oplace[i] = (uint16_t)place;
         place++;
         const uint32_t s = succ[i];
         if (s == kNone16) break;
@@ -550,36 +540,43 @@ __device__ int32_t s_bridges(const Grp<NT>& G, const Smem& S, int32_t V, int32_t
       rb = t;
     }
     // ra[k] >> 16: the arcs from ruler k's first arc to the end of its tour
-    for (int i = tid; i < narcs; i += NT) {
-      const uint32_t w = own[i];
-      S.rnk[i] = (uint16_t)((ra[w & 0xffffu] >> 16) - (w >> 16) - 1);
-    }
+    for (int i = tid; i < narcs; i += NT) S.rnk[i] = (uint16_t)((ra[oruler[i]] >> 16) - oplace[i] - 1);
     G.sync();
   }
   // per root: tour arcs (aoff) and tree vertices (vbase); P1 region is free now
-  for (int x = tid; x <= V; x += NT) {
-    uint16_t L = 0, nv = 0;
-    if (x < V && S.root[x] == x) {
-      L = S.off[x + 1] > S.off[x] ? (uint16_t)(S.rnk[S.off[x]] + 1) : 0;
-      nv = (uint16_t)(L / 2 + 1);
+  if (nt == V - 1) {
+    // one spanning tree, whose root is vertex 0 (the minimum of its set): its tour takes every
+    // arc and its vertices every preorder number, and no other entry is read
+    if (tid == 0) {
+      S.aoff[0] = 0;
+      S.aoff[1] = (uint16_t)narcs;
+      S.vbase[0] = 0;
     }
-    S.aoff[x] = L;
-    S.vbase[x] = nv;
+  } else {
+    for (int x = tid; x <= V; x += NT) {
+      uint16_t L = 0, nv = 0;
+      if (x < V && S.root[x] == x) {
+        L = S.head[x] >= 0 ? (uint16_t)(S.rnk[S.head[x]] + 1) : 0;
+        nv = (uint16_t)(L / 2 + 1);
+      }
+      S.aoff[x] = L;
+      S.vbase[x] = nv;
+    }
+    G.sync();
+    block_scan16_pair(G, S.aoff, S.vbase, V + 1, red, red_b);
   }
-  G.sync();
-  block_scan16_pair(G, S.aoff, S.vbase, V + 1, red, red_b);
   // tour positions; down arcs (dflag reuses succ, free after ranking)
   for (int i = tid; i <= narcs; i += NT) S.dflag[i] = 0;
   G.sync();
   for (int i = tid; i < narcs; i += NT) {
-    const int32_t x = S.dst[S.twin[i]];
-    const int32_t r = S.root[x];
-    const int32_t L = S.rnk[S.off[r]] + 1;
-    const int32_t ri = S.rnk[i], rt = S.rnk[S.twin[i]];
-    const int32_t g = S.aoff[r] + L - 1 - ri;
+    const uint32_t pe = S.F1[i >> 1];
+    const int32_t a = (int32_t)(pe & 0xffff), b = (int32_t)(pe >> 16);
+    const int32_t x = (i & 1) ? b : a, y = (i & 1) ? a : b;  // arc i: x -> y
+    const int32_t ri = S.rnk[i], rt = S.rnk[i ^ 1];
+    // the tour of x's root r fills positions [aoff[r], aoff[r + 1]); arc i is ri arcs from its end
+    const int32_t g = S.aoff[S.root[x] + 1] - 1 - ri;
     if (g < 0 || g >= narcs) continue;
     if (ri > rt) {
-      const int32_t y = S.dst[i];
       S.dflag[g] = 1;
       S.par[y] = (uint16_t)x;
       S.pre[y] = (uint16_t)g;
@@ -600,12 +597,11 @@ __device__ int32_t s_bridges(const Grp<NT>& G, const Smem& S, int32_t V, int32_t
       const int32_t g = S.pre[x], a0 = S.aoff[r];
       p = (g < narcs && a0 < narcs) ? S.vbase[r] + 1 + S.dflag[g] - S.dflag[a0] : 0;
     }
-    S.pre[x] = (uint16_t)min(max(p, 0), V - 1);
-  }
-  G.sync();
-  for (int x = tid; x < V; x += NT) {
-    S.lo[S.pre[x]] = S.pre[x];
-    S.hi[S.pre[x]] = S.pre[x];
+    const int32_t q = min(max(p, 0), V - 1);
+    S.pre[x] = (uint16_t)q;
+    S.rnk[q] = (uint16_t)x;  // the vertex at each preorder position (rnk is free now)
+    S.lo[q] = q;
+    S.hi[q] = q;
   }
   G.sync();
   for (int e = tid; e < nx; e += NT) {
@@ -619,67 +615,143 @@ __device__ int32_t s_bridges(const Grp<NT>& G, const Smem& S, int32_t V, int32_t
     atomicMax(S.hi + pb, pa);
   }
   G.sync();
-  // chunk (32) minima / maxima kept in the off region, free now
-  int32_t* cmin = reinterpret_cast<int32_t*>(S.off);
+  // per chunk of 32 preorder positions: the in-chunk prefix minima of lo and maxima of hi (u16, in
+  // the dflag region, free now) and the chunk's minimum / maximum
+  uint16_t* plo = S.dflag;
+  uint16_t* phi = S.dflag + VM;
+  int32_t* cmin = S.chunk;
   int32_t* cmax = cmin + VM / 32;
   const int nch = (V + 31) / 32;
-  for (int c = tid >> 5; c < nch; c += (NT / 32)) {
-    const int i = c * 32 + (tid & 31);
+  const int lane = tid & 31;
+  for (int c = tid >> 5; c < nch; c += (NT / 32)) {  // warp-uniform
+    const int i = c * 32 + lane;
     int32_t mn = i < V ? S.lo[i] : INT32_MAX, mx = i < V ? S.hi[i] : INT32_MIN;
-    for (int o = 16; o > 0; o >>= 1) {
-      mn = min(mn, __shfl_xor_sync(kFull, mn, o));
-      mx = max(mx, __shfl_xor_sync(kFull, mx, o));
+    for (int o = 1; o < 32; o <<= 1) {
+      const int32_t a = __shfl_up_sync(kFull, mn, o), b = __shfl_up_sync(kFull, mx, o);
+      if (lane >= o) mn = min(mn, a), mx = max(mx, b);
     }
-    if ((tid & 31) == 0) {
+    if (i < V) {
+      plo[i] = (uint16_t)mn;
+      phi[i] = (uint16_t)mx;
+    }
+    if (lane == 31) {
       cmin[c] = mn;
       cmax[c] = mx;
     }
   }
   if (tid == 0) *sh = 0;
   G.sync();
-  // test every tree edge (par(y), y); keys reuse the F region.  A subtree range of up to 32
-  // entries is scanned by its own lane; a larger one (the vertices near a root) by the whole
-  // warp, one chunk minimum per lane, so no lane scans V / 32 chunks alone (32 measured faster
-  // than 64 and 96 on the batched workload).
-  const int lane = tid & 31;
-  for (int y0 = 0; y0 < V; y0 += NT) {  // group-uniform: every lane of a warp takes part
-    const int y = y0 + tid;
-    const bool live = y < V && S.par[y] != kNone16;
-    int32_t l = 0, r = 0;
-    if (live) {
-      l = S.pre[y];
-      r = min(V, l + max((int32_t)S.sz[y], 1));
-    }
-    const bool big = live && r - l > 32;
-    int32_t mn = INT32_MAX, mx = INT32_MIN;
-    if (live && !big) {
-      const int32_t cl = (l + 31) / 32, cr = r / 32;
-      if (cl >= cr) {
-        for (int i = l; i < r; i++) mn = min(mn, S.lo[i]), mx = max(mx, S.hi[i]);
-      } else {
-        for (int i = l; i < cl * 32; i++) mn = min(mn, S.lo[i]), mx = max(mx, S.hi[i]);
-        for (int c = cl; c < cr; c++) mn = min(mn, cmin[c]), mx = max(mx, cmax[c]);
-        for (int i = cr * 32; i < r; i++) mn = min(mn, S.lo[i]), mx = max(mx, S.hi[i]);
+  // superchunks of 32 chunks, a warp each: the extrema of windows of 2^j chunks (j < 6, cut at
+  // the superchunk's end), the in-superchunk prefix and suffix extrema and each superchunk's
+  // extrema (int32, in the P1 region, free now), so that any run of whole chunks is a few loads
+  constexpr int NC = VM / 32;
+  static_assert((16 * NC + 2 * (NC / 32 + 1)) * 4 <= Layout<VM>::R0, "the chunk tables fit the P1 region");
+  int32_t* wcl = S.P1;           // [6][NC] window minima of lo
+  int32_t* wch = wcl + 6 * NC;   // [6][NC] window maxima of hi
+  int32_t* pcl = wch + 6 * NC;   // in-superchunk prefix
+  int32_t* pch = pcl + NC;
+  int32_t* scl = pch + NC;       // in-superchunk suffix
+  int32_t* sch = scl + NC;
+  int32_t* sml = sch + NC;       // [NC / 32 + 1] superchunk extrema
+  int32_t* smh = sml + NC / 32 + 1;
+  const int nsc = (nch + 31) / 32;
+  if ((tid >> 5) < nsc) {  // warp-uniform
+    const int w = tid >> 5, c = w * 32 + lane;
+    const int32_t a0 = c < nch ? cmin[c] : INT32_MAX, b0 = c < nch ? cmax[c] : INT32_MIN;
+    int32_t wa = a0, wb = b0;
+#pragma unroll
+    for (int j = 0; j < 6; j++) {
+      if (c < nch) {
+        wcl[j * NC + c] = wa;
+        wch[j * NC + c] = wb;
+      }
+      if (j < 5) {
+        const int o = 1 << j;
+        const int32_t ta = __shfl_down_sync(kFull, wa, o), tb = __shfl_down_sync(kFull, wb, o);
+        if (lane + o < 32) wa = min(wa, ta), wb = max(wb, tb);
       }
     }
-    unsigned todo = __ballot_sync(kFull, big);
-    while (todo) {
-      const int src = __ffs(todo) - 1;
-      todo &= todo - 1;
-      const int32_t L = __shfl_sync(kFull, l, src), R = __shfl_sync(kFull, r, src);
-      const int32_t cl = (L + 31) / 32, cr = R / 32;  // cl <= cr: the range holds a multiple of 32
-      int32_t a = INT32_MAX, b = INT32_MIN;
-      if (L + lane < cl * 32) a = S.lo[L + lane], b = S.hi[L + lane];
-      if (cr * 32 + lane < R) a = min(a, S.lo[cr * 32 + lane]), b = max(b, S.hi[cr * 32 + lane]);
-      for (int c = cl + lane; c < cr; c += 32) a = min(a, cmin[c]), b = max(b, cmax[c]);
-      a = __reduce_min_sync(kFull, a);
-      b = __reduce_max_sync(kFull, b);
-      if (lane == src) mn = a, mx = b;
+    int32_t pa = a0, pb = b0, sa = a0, sb = b0;
+    for (int o = 1; o < 32; o <<= 1) {
+      const int32_t x1 = __shfl_up_sync(kFull, pa, o), x2 = __shfl_up_sync(kFull, pb, o);
+      const int32_t y1 = __shfl_down_sync(kFull, sa, o), y2 = __shfl_down_sync(kFull, sb, o);
+      if (lane >= o) pa = min(pa, x1), pb = max(pb, x2);
+      if (lane + o < 32) sa = min(sa, y1), sb = max(sb, y2);
     }
-    if (live && mn >= l && mx < r) {
-      const uint32_t a = (uint32_t)min(y, (int)S.par[y]), b = (uint32_t)max(y, (int)S.par[y]);
-      const int32_t k = atomicAdd(sh, 1);
-      if (k < V) S.keys[k] = (a << 12) | b;
+    if (c < nch) {
+      pcl[c] = pa;
+      pch[c] = pb;
+      scl[c] = sa;
+      sch[c] = sb;
+    }
+    if (lane == 31) {
+      sml[w] = pa;
+      smh[w] = pb;
+    }
+  }
+  G.sync();
+  // test every tree edge (par(y), y), whose subtree holds the preorder positions [p, p + sz(y)),
+  // p = pre(y): a warp takes a chunk of 32 positions, a lane one position.  The subtree's part in
+  // the chunk, [p, e), is covered by two power-of-two windows, [p, p + 2^k) and [e - 2^k, e),
+  // whose extrema the warp builds and exchanges by shuffles; past the chunk come the whole
+  // chunks (two windows within a superchunk, else a suffix, a prefix and the superchunks between)
+  // and the last chunk's prefix.
+  const uint16_t* vtx = S.rnk;
+  for (int c = tid >> 5; c < nch; c += (NT / 32)) {  // warp-uniform
+    const int32_t p = c * 32 + lane;
+    int32_t wa[6], wb[6];  // extrema of [p, p + 2^j), cut at the chunk's end
+    wa[0] = p < V ? S.lo[p] : INT32_MAX;
+    wb[0] = p < V ? S.hi[p] : INT32_MIN;
+#pragma unroll
+    for (int j = 1; j < 6; j++) {
+      const int o = 1 << (j - 1);
+      const int32_t a = __shfl_down_sync(kFull, wa[j - 1], o), b = __shfl_down_sync(kFull, wb[j - 1], o);
+      wa[j] = lane + o < 32 ? min(wa[j - 1], a) : wa[j - 1];
+      wb[j] = lane + o < 32 ? max(wb[j - 1], b) : wb[j - 1];
+    }
+    int32_t y = 0, py = kNone16, r = p;
+    if (p < V) {
+      y = min((int32_t)vtx[p], V - 1);
+      py = S.par[y];
+      r = min(V, p + max((int32_t)S.sz[y], 1));
+    }
+    const bool live = p < V && py != kNone16;
+    const int32_t e = min(r, c * 32 + 32);
+    const int32_t len = max(e - p, 1);  // lane + len <= 32
+    const int k = 31 - __clz(len);
+    int32_t mn = INT32_MAX, mx = INT32_MIN;
+#pragma unroll
+    for (int j = 0; j < 6; j++) {
+      const int src = min(max(lane + len - (1 << j), 0), 31);
+      const int32_t a = __shfl_sync(kFull, wa[j], src), b = __shfl_sync(kFull, wb[j], src);
+      if (k == j) {
+        mn = min(wa[j], a);
+        mx = max(wb[j], b);
+      }
+    }
+    // past the chunk: whole chunks [c + 1, cr), then chunk cr's prefix up to r - 1
+    if (live && r > e) {
+      const int32_t cl = c + 1, cr = (r - 1) >> 5;
+      mn = min(mn, (int32_t)plo[r - 1]);
+      mx = max(mx, (int32_t)phi[r - 1]);
+      if (cl < cr) {
+        const int32_t s0 = cl >> 5, s1 = (cr - 1) >> 5;
+        if (s0 == s1) {
+          const int j = 31 - __clz(cr - cl);
+          const int32_t c2 = cr - (1 << j);
+          mn = min(mn, min(wcl[j * NC + cl], wcl[j * NC + c2]));
+          mx = max(mx, max(wch[j * NC + cl], wch[j * NC + c2]));
+        } else {
+          mn = min(mn, min(scl[cl], pcl[cr - 1]));
+          mx = max(mx, max(sch[cl], pch[cr - 1]));
+          for (int32_t q = s0 + 1; q < s1; q++) mn = min(mn, sml[q]), mx = max(mx, smh[q]);
+        }
+      }
+    }
+    if (live && mn >= p && mx < r) {
+      const uint32_t a = (uint32_t)min(y, py), b = (uint32_t)max(y, py);
+      const int32_t kk = atomicAdd(sh, 1);
+      if (kk < V) S.keys[kk] = (a << 12) | b;
     }
   }
   G.sync();
@@ -728,7 +800,11 @@ __device__ int32_t s_bridges(const Grp<NT>& G, const Smem& S, int32_t V, int32_t
 
 constexpr int kAT = 256;               // threads of a certification group
 constexpr int kAGroups = kT / kAT;     // certification groups per block
-constexpr int kABytes = 8 * kVmax;     // a certification group's union-finds (P1, P2)
+static_assert(kAT == kQuarterT, "a certification group runs the quarter-class bridge stages");
+// a certification group's shared memory: the union-finds (P1, P2) of a graph of up to kVmax
+// vertices, or the whole bridge-stage layout of a quarter-class graph
+constexpr int kABytes = cmax(8 * kVmax, Layout<kQuarterVmax>::kBytes);
+static_assert(kABytes % 16 == 0, "group regions stay 16-byte aligned");
 
 // The certificate slot of task T (batch_slot_words).
 __device__ __forceinline__ uint32_t* task_slot(const BatchArgs& A, const BatchTask& T) { return A.slots + T.slot; }
@@ -752,6 +828,36 @@ __device__ void certify_task(const BatchArgs& A, const BatchTask& T, char* smem,
     return;
   }
   const int32_t V = T.V;
+  if (T.cls == 2) {
+    if (V > kQuarterVmax || T.nparts != 1) {  // not a quarter-class task: never run past the layout
+      if (tid == 0) *T.count = BRIDGES_EINTERNAL;
+      return;
+    }
+    // a quarter-class graph (one task, at most kQuarterVmax vertices): certified straight into the
+    // bridge stage's shared-memory layout, then its bridge stage runs here, beside the other
+    // groups' streams, instead of in bridge_kernel
+    const Smem S = carve_smem<kQuarterVmax>(smem);
+    for (int x = tid; x < V; x += NT) {
+      S.P1[x] = x;
+      S.P2[x] = x;
+    }
+    if (tid == 0) {
+      gs.n1 = 0;
+      gs.n2 = 0;
+      gs.err = 0;
+    }
+    G.sync();
+    s_certify_range<NT, kQuarterVmax>(G, S, T.u, T.v, T.lo, T.hi, T.warm, V, &gs.n1, &gs.n2, &gs.err);
+    G.sync();
+    const int32_t nt = min(gs.n1, V), nx = min(gs.n2, V), err = gs.err;
+    if (err) {
+      if (tid == 0) *T.count = err;
+      return;
+    }
+    const int32_t nb = s_bridges<NT, kQuarterVmax>(G, S, V, nt, nx, T.out, gs.red, gs.red_b, &gs.sh);
+    if (tid == 0) *T.count = nb;
+    return;
+  }
   uint32_t* slot = task_slot(A, T);
   Smem S{};
   S.P1 = reinterpret_cast<int32_t*>(smem);
@@ -782,13 +888,32 @@ __device__ void certify_task(const BatchArgs& A, const BatchTask& T, char* smem,
   }
 }
 
+// Copies words [0, n) of src (global) to dst(i) (shared memory) with eight loads per thread in
+// flight before their stores: a plain copy loop waits for one load per round.
+template <int NT, class Dst>
+__device__ __forceinline__ void copy_in(const uint32_t* __restrict__ src, int32_t n, int tid, Dst dst) {
+  for (int32_t base = 0; base < n; base += 8 * NT) {
+    uint32_t r[8];
+#pragma unroll
+    for (int k = 0; k < 8; k++) {
+      const int32_t i = base + k * NT + tid;
+      r[k] = i < n ? __ldcg(src + i) : 0u;
+    }
+#pragma unroll
+    for (int k = 0; k < 8; k++) {
+      const int32_t i = base + k * NT + tid;
+      if (i < n) dst(i, r[k]);
+    }
+  }
+}
+
 // Bridges of the graph whose first task is T (later partitions are skipped): its slots' F and F'
 // edges offered to fresh union-finds (one slot: the same two forests again; several: the Sec. 3
 // merge), then the bridge stage, by a group of NT threads whose graphs have at most VM vertices.
 template <int NT, int VM>
 __device__ void bridge_task(const BatchArgs& A, const BatchTask& T, const Smem& S, const Grp<NT>& G, GroupShared& gs) {
   const int tid = G.tid;
-  if (T.part != 0) return;
+  if (T.part != 0 || T.cls == 2) return;  // quarter-class graphs are finished by certify_kernel
   if (!task_ok(A, T) || T.V > VM) {
     if (tid == 0 && T.count) *T.count = BRIDGES_EINTERNAL;
     return;
@@ -805,13 +930,17 @@ __device__ void bridge_task(const BatchArgs& A, const BatchTask& T, const Smem& 
     // trees come with them (P1 then holds each vertex's root: the stage's root walk is one step)
     const uint32_t* sp = task_slot(A, T);
     const int32_t nf = min((int32_t)__ldcg(sp), V), nx = min((int32_t)__ldcg(sp + 1), V);
-    const uint16_t* roots = reinterpret_cast<const uint16_t*>(sp + 2 + 2 * (int64_t)V);
-#pragma unroll 4
-    for (int32_t i = tid; i < nf; i += NT) S.F1[i] = __ldcg(sp + 2 + i);
-#pragma unroll 4
-    for (int32_t i = tid; i < nx; i += NT) S.F2[i] = __ldcg(sp + 2 + V + i);
-#pragma unroll 4
-    for (int32_t x = tid; x < V; x += NT) S.P1[x] = min((int32_t)__ldcg(roots + x), V - 1);
+    copy_in<NT>(sp + 2, 2 * V, tid, [&](int32_t i, uint32_t w) {  // the F and F' regions
+      if (i < V) {
+        if (i < nf) S.F1[i] = w;
+      } else if (i - V < nx) {
+        S.F2[i - V] = w;
+      }
+    });
+    copy_in<NT>(sp + 2 + 2 * V, (V + 1) / 2, tid, [&](int32_t i, uint32_t w) {  // two 16-bit roots a word
+      if (2 * i < V) S.P1[2 * i] = min((int32_t)(w & 0xffffu), V - 1);
+      if (2 * i + 1 < V) S.P1[2 * i + 1] = min((int32_t)(w >> 16), V - 1);
+    });
     if (tid == 0) {
       gs.n1 = nf;
       gs.n2 = nx;
@@ -820,7 +949,7 @@ __device__ void bridge_task(const BatchArgs& A, const BatchTask& T, const Smem& 
   } else {
     // several tasks: the Sec. 3 merge -- every slot's F, then F', offered to fresh union-finds;
     // each slot is first copied to shared memory (the dst / twin region, 2 VM words, free until
-    // the bridge stage) with all of a thread's loads in flight
+    // the bridge stage)
     for (int x = tid; x < V; x += NT) {
       S.P1[x] = x;
       S.P2[x] = x;
@@ -830,10 +959,13 @@ __device__ void bridge_task(const BatchArgs& A, const BatchTask& T, const Smem& 
     for (int p = 0; p < T.nparts; p++) {
       const uint32_t* sp = task_slot(A, T) + (int64_t)p * stride;
       const int32_t nf = min((int32_t)__ldcg(sp), V), nx = min((int32_t)__ldcg(sp + 1), V);
-#pragma unroll 8
-      for (int32_t i = tid; i < nf; i += NT) stage[i] = __ldcg(sp + 2 + i);
-#pragma unroll 8
-      for (int32_t i = tid; i < nx; i += NT) stage[nf + i] = __ldcg(sp + 2 + V + i);
+      copy_in<NT>(sp + 2, 2 * V, tid, [&](int32_t i, uint32_t w) {  // F then F', packed together
+        if (i < V) {
+          if (i < nf) stage[i] = w;
+        } else if (i - V < nx) {
+          stage[nf + i - V] = w;
+        }
+      });
       G.sync();
       s_certify_packed(G, S, stage, nf + nx, V, &gs.n1, &gs.n2);  // F first, then F'
       G.sync();
@@ -864,16 +996,36 @@ __device__ void run_queue(const BatchArgs& A, char* smem, const Grp<NT>& G, Grou
   }
 }
 
-// Takes tasks from `queue` (first + 0, 1, ... until `last`) and certifies them on group G.
+// Claims the next position of corder, or -1 when none is left.  One 64-bit word counts the claims
+// at both ends (the front's in the low half, the back's in the high half), so one atomic add
+// sees both: a front claim f succeeds while f + min(b, nback) < n, a back claim b while b < nback
+// and f + b < n (task n - 1 - b).  No position is claimed twice, and none is missed: after a back
+// claim fails, every later one fails too and its group claims from the front.
+__device__ __noinline__ int32_t claim_task(unsigned long long* q, int32_t n, int32_t nback, bool& back) {
+  if (back) {
+    const unsigned long long old = atomicAdd(q, 1ull << 32);
+    const int64_t f = (int64_t)(old & 0xffffffffull), b = (int64_t)(old >> 32);
+    if (b < nback && f + b < n) return (int32_t)(n - 1 - b);
+    back = false;
+  }
+  const unsigned long long old = atomicAdd(q, 1ull);
+  const int64_t f = (int64_t)(old & 0xffffffffull), b = (int64_t)(old >> 32);
+  return f + min(b, (int64_t)nback) < n ? (int32_t)f : -1;
+}
+
+// Certifies tasks on group G in corder: most edges first, or, for a back group, the fewest edges
+// first while the last nback tasks last, then from the front.
 template <int NT>
-__device__ void certify_queue(const BatchArgs& A, char* smem, const Grp<NT>& G, GroupShared& gs, int32_t* queue,
-                              int32_t first, int32_t last) {
+__device__ void certify_queue(const BatchArgs& A, char* smem, const Grp<NT>& G, GroupShared& gs, bool back,
+                              int32_t ntasks) {
+  unsigned long long* q = reinterpret_cast<unsigned long long*>(A.queue + 4);
+  const int32_t nback = min(max(A.nback, 0), ntasks);
   while (true) {
     G.sync();
-    if (G.tid == 0) gs.task = first + atomicAdd(queue, 1);
+    if (G.tid == 0) gs.task = claim_task(q, ntasks, nback, back);
     G.sync();
     const int32_t t = gs.task;
-    if (t >= last) break;
+    if (t < 0) break;
     certify_task<NT>(A, A.tasks[A.corder[t]], smem, G, gs);
   }
 }
@@ -881,28 +1033,30 @@ __device__ void certify_queue(const BatchArgs& A, char* smem, const Grp<NT>& G, 
 // Persistent certification: four 256-thread groups per block (named barriers 1-4), each with a
 // quarter of the shared memory, take the tasks in corder (most edges first, so that the longest
 // lists start early); one group's warm-up prefix (edge by edge, latency bound) overlaps the other
-// groups' streams.  (Whole blocks for the long tasks were measured slower: a block alone on its
-// SM has no other group's stream to hide its own prefix behind.)
+// groups' streams.  The last group of each block starts from the back of corder: the smallest
+// graphs are almost all prefix, and taken last they would leave HBM idle at the end of the
+// launch; taken beside the long streams they are hidden.  (Whole blocks for the long tasks were
+// measured slower: a block alone on its SM has no other group's stream to hide its own prefix
+// behind.)
 __global__ void __launch_bounds__(kT, 1) certify_kernel(const BatchArgs* __restrict__ dA) {
   const BatchArgs A = *dA;
   extern __shared__ __align__(16) char smem_raw[];
   __shared__ GroupShared gs[kAGroups];
   const int32_t ntasks = *A.d_ntasks;
   const int k = (int)threadIdx.x / kAT;
-  certify_queue<kAT>(A, smem_raw + k * kABytes, Grp<kAT>{(int)threadIdx.x % kAT, 1 + k}, gs[k], A.queue + 3, 0,
-                     ntasks);
+  certify_queue<kAT>(A, smem_raw + k * kABytes, Grp<kAT>{(int)threadIdx.x % kAT, 1 + k}, gs[k],
+                     k == kAGroups - 1, ntasks);
 }
 
 // Persistent bridge stages: whole-block tasks first (graphs above kHalfVmax vertices and
 // partitioned graphs); then the block splits into two independent half-block groups, each with
-// half the shared memory and its own named barrier, for graphs of up to kHalfVmax vertices; when a
-// half runs out of those it splits again into two quarter-block groups for graphs of up to
-// kQuarterVmax.  A small graph's cost is mostly its barriers, and this overlaps up to four of
-// them on one SM.  No barrier spans groups after the first split.
+// half the shared memory and its own named barrier, for graphs of up to kHalfVmax vertices.  A
+// small graph's cost is mostly its barriers, and this overlaps two of them on one SM.  No barrier
+// spans groups after the split.  (Quarter-class graphs were finished by certify_kernel.)
 __global__ void __launch_bounds__(kT, 1) bridge_kernel(const BatchArgs* __restrict__ dA) {
   const BatchArgs A = *dA;
   extern __shared__ __align__(16) char smem_raw[];
-  __shared__ GroupShared gs[6];  // [0] the block, then [h] each half, then [2 + 2h + q] each quarter
+  __shared__ GroupShared gs[3];  // [0] the block, then [1 + h] each half
   const int32_t ntasks = *A.d_ntasks;
   const int32_t nbig = min(max(A.nbig, 0), ntasks);
   const int32_t nmid = min(max(A.nmid, 0), ntasks - nbig);
@@ -911,12 +1065,7 @@ __global__ void __launch_bounds__(kT, 1) bridge_kernel(const BatchArgs* __restri
   const int h = (int)threadIdx.x / kHalfT;
   char* half = smem_raw + h * kHalfBytes;
   const Grp<kHalfT> gh{(int)threadIdx.x % kHalfT, 1 + h};
-  run_queue<kHalfT, kHalfVmax>(A, half, gh, gs[h], A.queue + 1, nbig, nbig + nmid);
-  gh.sync();  // the quarters reuse this half's shared memory
-  const int q = ((int)threadIdx.x % kHalfT) / kQuarterT;
-  run_queue<kQuarterT, kQuarterVmax>(A, half + q * Layout<kQuarterVmax>::kBytes,
-                                     Grp<kQuarterT>{(int)threadIdx.x % kQuarterT, 3 + 2 * h + q}, gs[2 + 2 * h + q],
-                                     A.queue + 2, nbig + nmid, ntasks);
+  run_queue<kHalfT, kHalfVmax>(A, half, gh, gs[1 + h], A.queue + 1, nbig, nbig + nmid);
 }
 
 }  // namespace

@@ -8,7 +8,7 @@ namespace bridges {
 
 constexpr int kBatchVmax = 4096;  // graphs up to this many vertices are handled in shared memory
 constexpr int kBatchHalfVmax = kBatchVmax / 2;     // ... up to this many, two per block
-constexpr int kBatchQuarterVmax = kBatchVmax / 4;  // ... up to this many, four per block
+constexpr int kBatchQuarterVmax = kBatchVmax / 4;  // ... up to this many, by a certification group
 
 // One unit of work: a whole graph (nparts == 1) or partition `part` of it.
 struct BatchTask {
@@ -22,7 +22,8 @@ struct BatchTask {
   int32_t part;      // partition index within the graph
   int32_t nparts;    // partitions of the graph
   int32_t V;         // vertices of the graph
-  int32_t cls;       // group that runs it: 0 a whole block, 1 a half block, 2 a quarter block
+  int32_t cls;       // group that runs its bridge stage: 0 a whole block, 1 a half block, 2 the
+                     // quarter-block group that certified it (in certify_kernel)
   int32_t pad;
   int64_t warm;      // edges certified one by one before the union-finds are flattened
 };
@@ -33,17 +34,21 @@ struct BatchArgs {
   const BatchTask* tasks;
   const int32_t* corder;  // certification order: task indices, most edges first
   const int32_t* d_ntasks;
-  int32_t* queue;    // next task (atomic): [0..2] bridge stages by group size, [3] certification
+  int32_t* queue;    // next task (atomic): [0..1] bridge stages by group size; words [4, 5] the
+                     // certification claims (front count low, back count high, one 64-bit word)
   int32_t* gerr;     // per graph: first error of any partition
   uint32_t* slots;   // the tasks' certificates
   int32_t G;           // graphs (bounds the graph index of every task)
   int32_t nbig;        // bridge stages: tasks [0, nbig) run on whole blocks,
-  int32_t nmid;        // [nbig, nbig + nmid) on half-block groups, the rest on quarter-block groups
+  int32_t nmid;        // [nbig, nbig + nmid) on half-block groups; the rest were finished by certify_kernel
+  int32_t nback;       // certification: the last nback tasks of corder may be claimed from the back
+  int32_t pad;
   int64_t slot_words;  // capacity of slots (u32)
 };
 
 // The smallest group a task fits: 0 a whole block (more than kBatchHalfVmax vertices, or a
-// partition of a graph: partitions merge from the slots), 1 a half block, 2 a quarter block.
+// partition of a graph: partitions merge from the slots), 1 a half block, 2 the certification
+// group (a quarter block).
 inline int batch_min_class(int32_t V, int32_t nparts) {
   if (V > kBatchHalfVmax || nparts > 1) return 0;
   return V > kBatchQuarterVmax ? 1 : 2;

@@ -50,6 +50,7 @@ struct bridges_ctx {
   cudaEvent_t b_done_ev[2]{};
   int b_next = 0;                // the staging copy the next batch fills
   int64_t b_split_edges = 0;     // partition graphs with more edges than this (0: automatic)
+  int64_t b_back_edges = 16384;  // certification: tasks of at most this many edges may be taken from the back
   bridges_batch_plan bplan{};    // per-bucket plan of the batched form (n = 0: automatic)
   // pipelined host input: a copy stream and one event per chunk copied
   static constexpr int kMaxChunks = 64;
