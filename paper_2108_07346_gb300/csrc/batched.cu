@@ -875,10 +875,18 @@ __device__ void certify_task(const BatchArgs& A, const BatchTask& T, char* smem,
   }
   G.sync();
   s_certify_range<NT, kVmax>(G, S, T.u, T.v, T.lo, T.hi, T.warm, V, &gs.n1, &gs.n2, &gs.err);
-  if (T.nparts == 1) {  // the graph's one task: its F trees' roots too, so the bridge stage needs no union-find
+  if (T.part == 0) {
+    // the graph's first task: the roots of its F trees (and, when more tasks follow, of its F'
+    // trees), so that the bridge stage starts from this task's union-finds as they stand and
+    // offers only the other tasks' edges
     s_flatten(G, S.P1, V);
-    uint16_t* roots = reinterpret_cast<uint16_t*>(slot + 2 + 2 * (int64_t)V);
-    for (int x = tid; x < V; x += NT) roots[x] = (uint16_t)S.P1[x];
+    if (T.nparts > 1) s_flatten(G, S.P2, V);
+    uint16_t* roots1 = reinterpret_cast<uint16_t*>(slot + 2 + 2 * (int64_t)V);
+    uint16_t* roots2 = reinterpret_cast<uint16_t*>(slot + 2 + 2 * (int64_t)V + (V + 1) / 2);
+    for (int x = tid; x < V; x += NT) {
+      roots1[x] = (uint16_t)S.P1[x];
+      if (T.nparts > 1) roots2[x] = (uint16_t)S.P2[x];
+    }
   }
   G.sync();
   if (tid == 0) {
@@ -925,51 +933,46 @@ __device__ void bridge_task(const BatchArgs& A, const BatchTask& T, const Smem& 
     gs.n2 = 0;
     gs.err = ld_relaxed(A.gerr + T.g);
   }
-  if (T.nparts == 1) {
-    // one task: its F and F' are the graph's certificate as they stand, and the roots of the F
-    // trees come with them (P1 then holds each vertex's root: the stage's root walk is one step)
-    const uint32_t* sp = task_slot(A, T);
-    const int32_t nf = min((int32_t)__ldcg(sp), V), nx = min((int32_t)__ldcg(sp + 1), V);
-    copy_in<NT>(sp + 2, 2 * V, tid, [&](int32_t i, uint32_t w) {  // the F and F' regions
+  // the first task's F and F' as they stand, with the roots of their trees (P1 and P2 then hold
+  // each vertex's root: offering those lists again to fresh union-finds would rebuild exactly
+  // these forests).  For one task that is the graph's certificate.
+  const uint32_t* sp = task_slot(A, T);
+  const int32_t nf = min((int32_t)__ldcg(sp), V), nx0 = min((int32_t)__ldcg(sp + 1), V);
+  copy_in<NT>(sp + 2, 2 * V, tid, [&](int32_t i, uint32_t w) {  // the F and F' regions
+    if (i < V) {
+      if (i < nf) S.F1[i] = w;
+    } else if (i - V < nx0) {
+      S.F2[i - V] = w;
+    }
+  });
+  const int32_t rw = (V + 1) / 2;  // words of a roots array (two 16-bit roots a word)
+  copy_in<NT>(sp + 2 + 2 * V, T.nparts > 1 ? 2 * rw : rw, tid, [&](int32_t i, uint32_t w) {
+    int32_t* P = i < rw ? S.P1 : S.P2;
+    const int32_t x = 2 * (i < rw ? i : i - rw);
+    if (x < V) P[x] = min((int32_t)(w & 0xffffu), V - 1);
+    if (x + 1 < V) P[x + 1] = min((int32_t)(w >> 16), V - 1);
+  });
+  if (tid == 0) {
+    gs.n1 = nf;
+    gs.n2 = nx0;
+  }
+  G.sync();
+  // the other tasks: the Sec. 3 merge -- each slot's F, then F', offered to the union-finds; each
+  // slot is first copied to shared memory (the dst region, 2 VM words, free until the bridge stage)
+  uint32_t* stage = reinterpret_cast<uint32_t*>(S.dst);
+  for (int p = 1; p < T.nparts; p++) {
+    const uint32_t* pp = sp + (int64_t)p * stride;
+    const int32_t mf = min((int32_t)__ldcg(pp), V), mx = min((int32_t)__ldcg(pp + 1), V);
+    copy_in<NT>(pp + 2, 2 * V, tid, [&](int32_t i, uint32_t w) {  // F then F', packed together
       if (i < V) {
-        if (i < nf) S.F1[i] = w;
-      } else if (i - V < nx) {
-        S.F2[i - V] = w;
+        if (i < mf) stage[i] = w;
+      } else if (i - V < mx) {
+        stage[mf + i - V] = w;
       }
     });
-    copy_in<NT>(sp + 2 + 2 * V, (V + 1) / 2, tid, [&](int32_t i, uint32_t w) {  // two 16-bit roots a word
-      if (2 * i < V) S.P1[2 * i] = min((int32_t)(w & 0xffffu), V - 1);
-      if (2 * i + 1 < V) S.P1[2 * i + 1] = min((int32_t)(w >> 16), V - 1);
-    });
-    if (tid == 0) {
-      gs.n1 = nf;
-      gs.n2 = nx;
-    }
     G.sync();
-  } else {
-    // several tasks: the Sec. 3 merge -- every slot's F, then F', offered to fresh union-finds;
-    // each slot is first copied to shared memory (the dst / twin region, 2 VM words, free until
-    // the bridge stage)
-    for (int x = tid; x < V; x += NT) {
-      S.P1[x] = x;
-      S.P2[x] = x;
-    }
+    s_certify_packed(G, S, stage, mf + mx, V, &gs.n1, &gs.n2);  // F first, then F'
     G.sync();
-    uint32_t* stage = reinterpret_cast<uint32_t*>(S.dst);
-    for (int p = 0; p < T.nparts; p++) {
-      const uint32_t* sp = task_slot(A, T) + (int64_t)p * stride;
-      const int32_t nf = min((int32_t)__ldcg(sp), V), nx = min((int32_t)__ldcg(sp + 1), V);
-      copy_in<NT>(sp + 2, 2 * V, tid, [&](int32_t i, uint32_t w) {  // F then F', packed together
-        if (i < V) {
-          if (i < nf) stage[i] = w;
-        } else if (i - V < nx) {
-          stage[nf + i - V] = w;
-        }
-      });
-      G.sync();
-      s_certify_packed(G, S, stage, nf + nx, V, &gs.n1, &gs.n2);  // F first, then F'
-      G.sync();
-    }
   }
   const int32_t nt = min(gs.n1, V), nx = min(gs.n2, V);
   if (gs.err) {

@@ -59,8 +59,10 @@ inline int batch_min_class(int32_t V, int32_t nparts) {
 inline int batch_task_class(const BatchTask& t) { return t.cls; }
 
 // Words of a task's certificate slot: [nF, nF', F (V words), F' (V words), the root of each
-// vertex's F tree (V u16, written for a graph of one task)].  A graph's slots are consecutive.
-__host__ __device__ inline int64_t batch_slot_words(int32_t V) { return 2 + 2 * (int64_t)V + ((int64_t)V + 1) / 2; }
+// vertex's F tree (V u16, padded to a word), the root of each vertex's F' tree (likewise)]; the
+// roots are written by a graph's first task (the F' roots only when more tasks follow).  A
+// graph's slots are consecutive.
+__host__ __device__ inline int64_t batch_slot_words(int32_t V) { return 2 + 2 * (int64_t)V + 2 * (((int64_t)V + 1) / 2); }
 
 size_t batched_smem_bytes();
 // Launches the two persistent kernels (one block per SM each: certification, then the bridge
