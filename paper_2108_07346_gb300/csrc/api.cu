@@ -1001,13 +1001,17 @@ extern "C" int32_t bridges_batch_autotune(bridges_ctx* c, struct CUstream_st* st
   std::vector<int> present(5, 0);
   for (int32_t g = 0; g < G; g++)
     if (Vs[g] <= kBatchVmax) present[batch_bucket(cur, Vs[g])] = 1;
+  const bridges_batch_plan automatic = cur;
   float best_ms = time_plan(cur);
+  // a change is kept only when it is faster by more than the timing noise of a few calls: the
+  // minimum over many noisy candidates otherwise drifts to a plan that is merely lucky
+  constexpr float kMargin = 0.995f;
   for (int pass = 0; pass < 2 && rc == BRIDGES_OK; pass++) {
     for (int b = 4; b >= 0 && rc == BRIDGES_OK; b--) {
       if (!present[b]) continue;
       auto consider = [&](const bridges_batch_plan& P) {
         const float ms = time_plan(P);
-        if (ms >= 0 && ms < best_ms) {
+        if (ms >= 0 && ms < best_ms * kMargin) {
           best_ms = ms;
           cur = P;
         }
@@ -1030,6 +1034,32 @@ extern "C" int32_t bridges_batch_autotune(bridges_ctx* c, struct CUstream_st* st
         P.warm_per_v[b] = w[0];
         P.warm_add[b] = w[1];
         if (P.warm_per_v[b] != cur.warm_per_v[b] || P.warm_add[b] != cur.warm_add[b]) consider(P);
+      }
+    }
+  }
+  // the search's plan against the automatic one, timed in turn over more calls: the automatic
+  // plan stays unless the other is faster beyond the margin
+  auto same_plan = [](const bridges_batch_plan& x, const bridges_batch_plan& y) {
+    if (x.n != y.n) return false;
+    for (int b = 0; b < x.n && b < BRIDGES_BATCH_BUCKETS; b++)
+      if (x.vmax[b] != y.vmax[b] || x.group[b] != y.group[b] || x.split[b] != y.split[b] ||
+          x.warm_per_v[b] != y.warm_per_v[b] || x.warm_add[b] != y.warm_add[b])
+        return false;
+    return true;
+  };
+  if (rc == BRIDGES_OK && !same_plan(cur, automatic)) {
+    float t_cur = 0, t_auto = 0;
+    for (int k = 0; k < 3 && rc == BRIDGES_OK; k++) {
+      const float a = time_plan(automatic), b = time_plan(cur);
+      t_auto += a;
+      t_cur += b;
+    }
+    if (rc == BRIDGES_OK) {
+      if (t_cur < t_auto * kMargin) {
+        best_ms = t_cur / 3;
+      } else {
+        cur = automatic;
+        best_ms = t_auto / 3;
       }
     }
   }
