@@ -163,22 +163,25 @@ int64_t bridges_find_batched(bridges_ctx* ctx, struct CUstream_st* stream, const
                              const int32_t* edges_v, const int64_t* edge_off_host, const int32_t* V_host, int32_t G,
                              int32_t* out_bridges, int64_t* out_counts_device);
 
-/* Edge count above which a batched graph is split into partitions (0: automatic, about
- * max(2^20, total edges / (4 x SMs))).  Returns BRIDGES_OK or BRIDGES_EINVAL. */
+/* Edge count above which a batched graph is split into partitions (0: automatic, the batch's
+ * edges / (3 x SMs) clamped to [2^17, 2^20]).  Returns BRIDGES_OK or BRIDGES_EINVAL. */
 int32_t bridges_ctx_set_batch_split(bridges_ctx* ctx, int64_t split_edges);
 
 /* The plan of the batched form, per size bucket (what bridges_batch_autotune picks; a caller may
  * also set one, e.g. from a cache of tuning results).  Graph g belongs to the first bucket b with
  * V[g] <= vmax[b] (vmax increasing; graphs above the last vmax use the last bucket).  Per bucket:
- *   group[b] : threads per graph -- 1024 (a whole block), 512 (half a block) or 256 (a quarter);
- *              0 = the smallest group the graph fits (256 up to 1,024 vertices, 512 up to 2,048,
- *              1024 above).  A group too small for a graph is raised to the smallest that fits.
+ *   group[b] : threads of the group that runs a graph's bridge stage -- 1024 (a whole block), 512
+ *              (half a block) or 256 (the certification group itself, which runs the stage of a
+ *              one-partition graph of up to 1,024 vertices right after certifying it); 0 = the
+ *              smallest group the graph fits (256 up to 1,024 vertices, 512 up to 2,048, 1024
+ *              above).  A group too small for a graph is raised to the smallest that fits.
  *   split[b] : graphs with more edges than this are cut into ceil(E / split) contiguous
- *              partitions (at most 64, Sec. 3's M per graph), each certified by a whole block;
- *              the block that finishes a graph's last partition merges all of its partitions'
- *              certificates in one step (merge fan-in = M: one merge level, since every
- *              certificate is already in device memory); 0 = automatic (the context's
- *              bridges_ctx_set_batch_split value, else about max(2^20, total edges / (4 x SMs))).
+ *              partitions (at most 64, Sec. 3's M per graph), each certified by a 256-thread
+ *              group; the bridge stage starts from the first partition's two forests and offers
+ *              the other partitions' F and F' edges (merge fan-in = M: one merge level, since
+ *              every certificate is already in device memory); 0 = automatic (the context's
+ *              bridges_ctx_set_batch_split value, else the batch's edges / (3 x SMs) clamped to
+ *              [2^17, 2^20]).
  *   warm_per_v[b], warm_add[b] : each task certifies its first warm_per_v * V + warm_add edges one
  *              by one before flattening its union-finds and streaming the rest; both 0 =
  *              automatic (4V + 2048).

@@ -856,9 +856,14 @@ int64_t launch_batch_tasks(bridges_ctx* c, cudaStream_t s, const std::vector<Bat
   return BRIDGES_OK;
 }
 
+// The automatic split: the batch's edges over three certification groups per SM (there are
+// four), no task above 2^20 edges and none below 2^17 (every task pays its own warm-up prefix).
+// A small batch then cuts its large graphs finer, so that the launch does not wait on its one
+// longest graph (512 graphs of the batched workload: 0.30 ms against 0.50 with 2^20 alone);
+// the 4,096-graph batch keeps 2^20 (0.881 M edges a task with four groups per SM was 2% slower).
 int64_t default_split(const bridges_ctx* c, int64_t total_e) {
-  return c->b_split_edges > 0 ? c->b_split_edges
-                              : std::max<int64_t>(1 << 20, total_e / std::max(1, c->num_sms * 4));
+  if (c->b_split_edges > 0) return c->b_split_edges;
+  return std::min<int64_t>(1 << 20, std::max<int64_t>(1 << 17, total_e / std::max(1, c->num_sms * 3)));
 }
 
 // The single-graph path on a context, count copied to count_dev (device).
