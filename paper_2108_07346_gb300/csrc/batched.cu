@@ -938,42 +938,56 @@ __device__ void bridge_task(const BatchArgs& A, const BatchTask& T, const Smem& 
   // these forests).  For one task that is the graph's certificate.
   const uint32_t* sp = task_slot(A, T);
   const int32_t nf = min((int32_t)__ldcg(sp), V), nx0 = min((int32_t)__ldcg(sp + 1), V);
-  copy_in<NT>(sp + 2, 2 * V, tid, [&](int32_t i, uint32_t w) {  // the F and F' regions
+  const int32_t rw = (V + 1) / 2;  // words of a roots array (two 16-bit roots a word)
+  // one copy of the F region, the F' region and the roots array(s), which follow each other
+  copy_in<NT>(sp + 2, 2 * V + (T.nparts > 1 ? 2 * rw : rw), tid, [&](int32_t i, uint32_t w) {
     if (i < V) {
       if (i < nf) S.F1[i] = w;
-    } else if (i - V < nx0) {
-      S.F2[i - V] = w;
+    } else if (i < 2 * V) {
+      if (i - V < nx0) S.F2[i - V] = w;
+    } else {
+      const int32_t j = i - 2 * V;
+      int32_t* P = j < rw ? S.P1 : S.P2;
+      const int32_t x = 2 * (j < rw ? j : j - rw);
+      if (x < V) P[x] = min((int32_t)(w & 0xffffu), V - 1);
+      if (x + 1 < V) P[x + 1] = min((int32_t)(w >> 16), V - 1);
     }
-  });
-  const int32_t rw = (V + 1) / 2;  // words of a roots array (two 16-bit roots a word)
-  copy_in<NT>(sp + 2 + 2 * V, T.nparts > 1 ? 2 * rw : rw, tid, [&](int32_t i, uint32_t w) {
-    int32_t* P = i < rw ? S.P1 : S.P2;
-    const int32_t x = 2 * (i < rw ? i : i - rw);
-    if (x < V) P[x] = min((int32_t)(w & 0xffffu), V - 1);
-    if (x + 1 < V) P[x + 1] = min((int32_t)(w >> 16), V - 1);
   });
   if (tid == 0) {
     gs.n1 = nf;
     gs.n2 = nx0;
   }
   G.sync();
-  // the other tasks: the Sec. 3 merge -- each slot's F, then F', offered to the union-finds; each
-  // slot is first copied to shared memory (the dst region, 2 VM words, free until the bridge stage)
+  // the other tasks: the Sec. 3 merge -- each slot's F and F' edges offered to the union-finds.
+  // Each slot is read with all of a thread's loads in flight and filtered on the way: an edge
+  // whose ends already have the same F' parent is joined in both forests (F' components lie
+  // inside F components, and sets only grow), so only the others are staged in shared memory
+  // (the dst region, 2 VM words, free until the bridge stage) and offered, in any order (every
+  // order leaves F a spanning forest of the offered edges and F' one of the rest).
   uint32_t* stage = reinterpret_cast<uint32_t*>(S.dst);
+  volatile int32_t* P2v = S.P2;
+  // two staging counters used in turn (red_b is free until the bridge stage): slot p counts in
+  // cnt[p & 1], and cnt[(p + 1) & 1], last read in slot p - 1's pass, is reset after the barrier
+  // that ends that pass
+  int32_t* cnt = gs.red_b;
+  if (tid == 0) {
+    cnt[0] = 0;
+    cnt[1] = 0;
+  }
   for (int p = 1; p < T.nparts; p++) {
     const uint32_t* pp = sp + (int64_t)p * stride;
     const int32_t mf = min((int32_t)__ldcg(pp), V), mx = min((int32_t)__ldcg(pp + 1), V);
-    copy_in<NT>(pp + 2, 2 * V, tid, [&](int32_t i, uint32_t w) {  // F then F', packed together
-      if (i < V) {
-        if (i < mf) stage[i] = w;
-      } else if (i - V < mx) {
-        stage[mf + i - V] = w;
-      }
+    G.sync();  // the previous slot's edges are settled: the stage is free
+    if (tid == 0) cnt[(p + 1) & 1] = 0;
+    copy_in<NT>(pp + 2, 2 * V, tid, [&](int32_t i, uint32_t w) {
+      if (i < V ? i >= mf : i - V >= mx) return;
+      const int32_t a = (int32_t)(w & 0xffff), b = (int32_t)(w >> 16);
+      if (a < V && b < V && a != b && P2v[a] != P2v[b]) stage[atomicAdd(cnt + (p & 1), 1)] = w;
     });
     G.sync();
-    s_certify_packed(G, S, stage, mf + mx, V, &gs.n1, &gs.n2);  // F first, then F'
-    G.sync();
+    s_certify_packed(G, S, stage, min(cnt[p & 1], 2 * V), V, &gs.n1, &gs.n2);
   }
+  G.sync();
   const int32_t nt = min(gs.n1, V), nx = min(gs.n2, V);
   if (gs.err) {
     G.sync();  // every thread has read gs.err before the next task resets it

@@ -83,6 +83,28 @@ def test_split_partitions_and_large_graphs(ctx, cuda_lib):
             assert got.tolist() == oracle.dfs_bridges(u, v, V).tolist()
 
 
+def test_small_batch_automatic_split(cuda_lib):
+    """A small batch of large dense graphs: the automatic split (the batch's edges over three
+    certification groups per SM, at least 2^17 edges) cuts each graph into many partitions whose
+    certificates the bridge stage merges; every graph equals the oracle.  The same graphs with the
+    split left at 2^20 (set explicitly) take fewer partitions and must give the same lists."""
+    graphs = []
+    for i, (V, p) in enumerate([(4000, 0.45), (3500, 0.6), (3900, 0.3), (2600, 0.8)]):
+        g = graphgen.generate(graphgen.Spec(seed=900 + i, n_clusters=1, core_vertices=V - 40, p=p,
+                                            n_pendant=6, n_paths=3, path_min=2, path_max=6))
+        assert len(g.u) > 4 * (1 << 17)  # several partitions each at the automatic split
+        graphs.append((g.u, g.v, g.V, g.planted))
+    auto = cuda_lib.Context(device="cuda:0")
+    fixed = cuda_lib.Context(device="cuda:0")
+    fixed.set_batch_split(1 << 20)
+    ref = [oracle.dfs_bridges(u, v, V).tolist() for u, v, V, _ in graphs]
+    for c in (auto, fixed):
+        res = run_batch(c, [(u, v, V) for u, v, V, _ in graphs])
+        for (u, v, V, planted), got, r in zip(graphs, res, ref):
+            assert got.tolist() == r
+            assert {tuple(x) for x in planted.tolist()} <= {tuple(x) for x in got.tolist()}
+
+
 def test_errors_are_per_graph(ctx):
     good = graphgen.random_multigraph(7, 20, 30)
     bad = (np.array([0, 1], np.int32), np.array([1, 50], np.int32), 10)
