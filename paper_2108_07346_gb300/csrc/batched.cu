@@ -817,8 +817,10 @@ __device__ __forceinline__ bool task_ok(const BatchArgs& A, const BatchTask& T) 
          T.slot + (int64_t)(T.nparts - T.part) * stride <= A.slot_words;
 }
 
-// Certifies task T by group G of NT threads (shared memory: the two union-finds); the winners go
-// to T's slot.
+// Certifies task T by group G of NT threads.  A quarter-class graph (one task, at most
+// kQuarterVmax vertices) is certified into the bridge stage's layout in the group's shared memory
+// and finished here; any other task keeps only its two union-finds in shared memory and appends
+// its winners to its slot (the graph's first task also leaves the roots of its forests there).
 template <int NT>
 __device__ void certify_task(const BatchArgs& A, const BatchTask& T, char* smem, const Grp<NT>& G,
                              GroupShared& gs) {
