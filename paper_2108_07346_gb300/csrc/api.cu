@@ -172,11 +172,28 @@ int init_ctx(bridges_ctx* c, int device, const bridges_opts* opts) {
   return 0;
 }
 
+// The final stage of a call that wants only the sorted bridges and their count (none of the
+// rooted forest's arrays): a graph of 2..kBatchVmax vertices runs it on one block in shared
+// memory (small_final_launch: block barriers only, against the grid stage's 19 grid barriers),
+// a larger one on the grid.  The grid barrier's test knobs keep the grid form.
+void final_bridges(const Launch& L, const Carved& k, int32_t V, int32_t* out) {
+  if (V >= 2 && V <= kBatchVmax && L.bar_polls == 0 && L.hold_polls == 0) {
+    const SmallFinalArgs a{V, k.cert.P1, k.cert.f1u, k.cert.f1v, k.cert.cnt + 0, k.cert.f2u, k.cert.f2v,
+                           k.cert.cnt + 1, k.fin.status, k.fin.count, out};
+    small_final_launch(L.stream, a);  // a launch error is caught by the caller's error check
+    *L.launches += 1;
+    return;
+  }
+  final_stage(L, k.fin, V, k.cert.f1u, k.cert.f1v, k.cert.cnt + 0, V, k.cert.f2u, k.cert.f2v, k.cert.cnt + 1, V,
+              k.cert.P1, out);
+}
+
 // The whole path on device-resident edges.  Leaves the count on the device (fin.count).  With
 // with_final false it stops after the certificate; otherwise the sorted pairs go to out, or to
-// the final stage's own dscan array (free by the time it sorts) when out is null.
+// the final stage's own dscan array (free by the time it sorts) when out is null.  With
+// bridges_only the caller reads nothing of the final stage but the pairs and the count.
 int64_t run_path(bridges_ctx* c, cudaStream_t s, const int32_t* u, const int32_t* v, int64_t E, int32_t V, int32_t M,
-                 int32_t* out, Carved* kout, CertPlan* pout, bool with_final = true) {
+                 int32_t* out, Carved* kout, CertPlan* pout, bool with_final = true, bool bridges_only = false) {
   Range range("bridges: certificate + final stage");
   CertPlan p = plan_for(c, E, V, M);
   int64_t rc = ensure_ws(c, total_bytes(p), s);
@@ -199,8 +216,11 @@ int64_t run_path(bridges_ctx* c, cudaStream_t s, const int32_t* u, const int32_t
   if (ev) cudaEventRecord(ev[4], s);
   if (with_final) {
     // job 0 holds the final certificate: F (tree) and F' (extra); its UF1 roots the trees
-    final_stage(L, k.fin, V, k.cert.f1u, k.cert.f1v, k.cert.cnt + 0, V, k.cert.f2u, k.cert.f2v, k.cert.cnt + 1, V,
-                k.cert.P1, out ? out : k.fin.dscan);
+    if (bridges_only)
+      final_bridges(L, k, V, out ? out : k.fin.dscan);
+    else
+      final_stage(L, k.fin, V, k.cert.f1u, k.cert.f1v, k.cert.cnt + 0, V, k.cert.f2u, k.cert.f2v, k.cert.cnt + 1,
+                  V, k.cert.P1, out ? out : k.fin.dscan);
   }
   if (ev) {
     cudaEventRecord(ev[5], s);
@@ -319,7 +339,7 @@ static int64_t issue_chunks(bridges_ctx* c, cudaStream_t s, const int32_t* hu, c
 }
 
 int64_t run_path_host(bridges_ctx* c, cudaStream_t s, const int32_t* hu, const int32_t* hv, int32_t* du, int32_t* dv,
-                      int64_t E, int32_t V, int32_t M, int32_t* out, Carved* kout) {
+                      int64_t E, int32_t V, int32_t M, int32_t* out, Carved* kout, bool bridges_only) {
   Range range("bridges: pipelined host input");
   const CertPlan p = plan_for(c, E, V, M);
   if (p.M != 1 || !p.cache) return 1;
@@ -354,8 +374,11 @@ int64_t run_path_host(bridges_ctx* c, cudaStream_t s, const int32_t* hu, const i
   if (ev) cudaEventRecord(ev[3], s);
   cert_merge(L, p, k.cert);
   if (ev) cudaEventRecord(ev[4], s);
-  final_stage(L, k.fin, V, k.cert.f1u, k.cert.f1v, k.cert.cnt + 0, V, k.cert.f2u, k.cert.f2v, k.cert.cnt + 1, V,
-              k.cert.P1, out);
+  if (bridges_only)
+    final_bridges(L, k, V, out);
+  else
+    final_stage(L, k.fin, V, k.cert.f1u, k.cert.f1v, k.cert.cnt + 0, V, k.cert.f2u, k.cert.f2v, k.cert.cnt + 1, V,
+                k.cert.P1, out);
   if (ev) {
     cudaEventRecord(ev[5], s);
     cudaEventRecord(ev[6], s);
@@ -440,7 +463,7 @@ int64_t bridges_find_ctx(bridges_ctx* c, struct CUstream_st* stream, const int32
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   if (cudaSetDevice(c->device) != cudaSuccess) return cuda_fail(cudaGetLastError());
   Carved k{};
-  rc = run_path(c, s, u, v, E, V, M, out, &k, nullptr);
+  rc = run_path(c, s, u, v, E, V, M, out, &k, nullptr, true, true);
   if (rc) return rc;
   if (out_count_device) {
     if (cudaMemcpyAsync(out_count_device, k.fin.count, sizeof(int64_t), cudaMemcpyDeviceToDevice, s) != cudaSuccess)
@@ -482,7 +505,7 @@ int64_t bridges_find_host(bridges_ctx* c, struct CUstream_st* stream, const int3
   Carved k{};
   rc = 1;
   if (deferred)  // copies not issued yet: overlap them with the forest pass if the plan allows
-    rc = run_path_host(c, s, hu, hv, const_cast<int32_t*>(ru), const_cast<int32_t*>(rv), E, V, M, dout, &k);
+    rc = run_path_host(c, s, hu, hv, const_cast<int32_t*>(ru), const_cast<int32_t*>(rv), E, V, M, dout, &k, true);
   if (rc < 0) return rc;
   if (rc == 1) {
     if (deferred && E > 0 &&
@@ -491,7 +514,7 @@ int64_t bridges_find_host(bridges_ctx* c, struct CUstream_st* stream, const int3
          cudaMemcpyAsync(const_cast<int32_t*>(rv), hv, sizeof(int32_t) * (size_t)E, cudaMemcpyHostToDevice, s) !=
              cudaSuccess))
       return cuda_fail(cudaGetLastError());
-    rc = run_path(c, s, ru, rv, E, V, M, dout, &k, nullptr);
+    rc = run_path(c, s, ru, rv, E, V, M, dout, &k, nullptr, true, true);
     if (rc) return rc;
   }
   if (cudaMemcpyAsync(c->h_pinned, k.fin.count, sizeof(int64_t), cudaMemcpyDeviceToHost, s) != cudaSuccess)
@@ -870,7 +893,7 @@ int64_t default_split(const bridges_ctx* c, int64_t total_e) {
 int64_t run_single(bridges_ctx* c, cudaStream_t s, const int32_t* u, const int32_t* v, int64_t E, int32_t V, int32_t M,
                    int32_t* out, int64_t* count_dev) {
   Carved k{};
-  int64_t rc = run_path(c, s, u, v, E, V, M, out, &k, nullptr);
+  int64_t rc = run_path(c, s, u, v, E, V, M, out, &k, nullptr, true, true);
   if (rc) return rc;
   if (cudaMemcpyAsync(count_dev, k.fin.count, sizeof(int64_t), cudaMemcpyDeviceToDevice, s) != cudaSuccess)
     return cuda_fail(cudaGetLastError());
@@ -1125,13 +1148,13 @@ extern "C" int32_t bridges_autotune(bridges_ctx* c, struct CUstream_st* stream, 
           // one untimed run (workspace growth, first-touch), then reps timed runs
           int64_t r = BRIDGES_OK;
           Carved k{};
-          r = run_path(c, s, u, v, E, V, 0, out, &k, nullptr);
+          r = run_path(c, s, u, v, E, V, 0, out, &k, nullptr, true, true);
           if (r) {
             rc = (int32_t)r;
             break;
           }
           cudaEventRecord(e0, s);
-          for (int i = 0; i < reps && !r; i++) r = run_path(c, s, u, v, E, V, 0, out, &k, nullptr);
+          for (int i = 0; i < reps && !r; i++) r = run_path(c, s, u, v, E, V, 0, out, &k, nullptr, true, true);
           cudaEventRecord(e1, s);
           if (r || cudaEventSynchronize(e1) != cudaSuccess) {
             rc = r ? (int32_t)r : (int32_t)BRIDGES_ECUDA;
@@ -1159,9 +1182,9 @@ extern "C" int32_t bridges_autotune(bridges_ctx* c, struct CUstream_st* stream, 
     o.profile = 0;
     c->opts = o;
     Carved k{};
-    int64_t r = run_path(c, s, u, v, E, V, 0, out, &k, nullptr);
+    int64_t r = run_path(c, s, u, v, E, V, 0, out, &k, nullptr, true, true);
     cudaEventRecord(e0, s);
-    for (int i = 0; i < reps && !r; i++) r = run_path(c, s, u, v, E, V, 0, out, &k, nullptr);
+    for (int i = 0; i < reps && !r; i++) r = run_path(c, s, u, v, E, V, 0, out, &k, nullptr, true, true);
     cudaEventRecord(e1, s);
     if (r || cudaEventSynchronize(e1) != cudaSuccess) {
       rc = r ? (int32_t)r : (int32_t)BRIDGES_ECUDA;
@@ -1378,7 +1401,7 @@ static int64_t articulation_run(bridges_ctx* c, cudaStream_t s, const int32_t* u
     // free by the time the final stage sorts
     const Carved k0 = carve(c, p0);
     rc = run_path_host(c, s, hu, hv, const_cast<int32_t*>(u), const_cast<int32_t*>(v), E, V, M,
-                       out_bridges ? out_bridges : k0.fin.dscan, &k);
+                       out_bridges ? out_bridges : k0.fin.dscan, &k, false);
     if (rc < 0) return rc;
     if (rc == 1 && E > 0 &&
         (cudaMemcpyAsync(const_cast<int32_t*>(u), hu, sizeof(int32_t) * (size_t)E, cudaMemcpyHostToDevice, s) !=

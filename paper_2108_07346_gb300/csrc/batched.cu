@@ -1087,9 +1087,56 @@ __global__ void __launch_bounds__(kT, 1) bridge_kernel(const BatchArgs* __restri
   run_queue<kHalfT, kHalfVmax>(A, half, gh, gs[1 + h], A.queue + 1, nbig, nbig + nmid);
 }
 
+// The bridge stage of one graph of 2..kVmax vertices on one block, in place of the grid-wide
+// final stage when only the sorted bridges and their count are wanted: the final certificate (F
+// and F' in global memory) is packed into the shared-memory layout, F's union-find copied as it
+// stands (its roots root the trees), and s_bridges runs with block barriers only -- no grid
+// barrier, no cooperative launch.
+__global__ void __launch_bounds__(kT, 1) small_final_kernel(const SmallFinalArgs A) {
+  extern __shared__ __align__(16) char smem_raw[];
+  __shared__ GroupShared gs;
+  const Smem S = carve_smem<kVmax>(smem_raw);
+  const Grp<kT> G{(int)threadIdx.x, 0};
+  const int tid = (int)threadIdx.x;
+  const int32_t V = min(max(A.V, 0), kVmax);
+  const int32_t nt = min(max(ld_relaxed(A.d_nt), 0), max(V - 1, 0));
+  const int32_t nx = min(max(ld_relaxed(A.d_nx), 0), V);
+  for (int x = tid; x < V; x += kT) {
+    const int32_t p = __ldcg(A.P + x);
+    S.P1[x] = (p >= 0 && p <= x) ? p : x;
+  }
+  int bad = 0;  // a certificate edge out of range (never expected: its edges passed the range test)
+  for (int e = tid; e < nt; e += kT) {
+    const int32_t a = __ldcg(A.tu + e), b = __ldcg(A.tv + e);
+    bad |= (uint32_t)a >= (uint32_t)V || (uint32_t)b >= (uint32_t)V;
+    S.F1[e] = (uint32_t)(a & 0xffff) | ((uint32_t)(b & 0xffff) << 16);
+  }
+  for (int e = tid; e < nx; e += kT) {
+    const int32_t a = __ldcg(A.xu + e), b = __ldcg(A.xv + e);
+    bad |= (uint32_t)a >= (uint32_t)V || (uint32_t)b >= (uint32_t)V;
+    S.F2[e] = (uint32_t)(a & 0xffff) | ((uint32_t)(b & 0xffff) << 16);
+  }
+  const bool any_bad = __syncthreads_or(bad) != 0;
+  int32_t st = ld_relaxed(A.status);  // the same value for every thread: no stage writes it now
+  if (st == 0 && any_bad) st = BRIDGES_EINTERNAL;
+  if (st != 0) {
+    if (tid == 0) *A.count = st;
+    return;
+  }
+  const int32_t nb = s_bridges<kT, kVmax>(G, S, V, nt, nx, A.out, gs.red, gs.red_b, &gs.sh);
+  if (tid == 0) *A.count = nb;
+}
+
 }  // namespace
 
 size_t batched_smem_bytes() { return (size_t)kSmem; }
+
+bool small_final_launch(cudaStream_t s, const SmallFinalArgs& a) {
+  if (a.V < 2 || a.V > kVmax) return false;
+  cudaFuncSetAttribute(small_final_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, Layout<kVmax>::kBytes);
+  small_final_kernel<<<1, kT, Layout<kVmax>::kBytes, s>>>(a);
+  return cudaPeekAtLastError() == cudaSuccess;
+}
 
 bool batched_launch(cudaStream_t s, const BatchArgs* dev_args, int num_sms) {
   // function attributes are per device: set on every launch (a host-side call; the launches are

@@ -64,7 +64,25 @@ inline int batch_task_class(const BatchTask& t) { return t.cls; }
 // graph's slots are consecutive.
 __host__ __device__ inline int64_t batch_slot_words(int32_t V) { return 2 + 2 * (int64_t)V + 2 * (((int64_t)V + 1) / 2); }
 
+// One graph's final stage on one block (small_final_launch): the final certificate as the forest
+// pass and the merge tree leave it in global memory, for a graph of 2..kBatchVmax vertices.
+struct SmallFinalArgs {
+  int32_t V;
+  const int32_t* P;     // F's union-find (P[x] <= x; a root is its set's minimum vertex)
+  const int32_t* tu;    // F: tree edges, *d_nt of them
+  const int32_t* tv;
+  const int32_t* d_nt;
+  const int32_t* xu;    // F': the other certificate edges, *d_nx of them
+  const int32_t* xv;
+  const int32_t* d_nx;
+  const int32_t* status;  // the call's status word (0, or the first error of an earlier stage)
+  int64_t* count;       // receives the bridge count, or the status when it is set
+  int32_t* out;         // receives the sorted (a, b) pairs, capacity 2 (V - 1)
+};
+
 size_t batched_smem_bytes();
+// Launches the one-block final stage (bridges and count only) on stream s.
+bool small_final_launch(cudaStream_t s, const SmallFinalArgs& a);
 // Launches the two persistent kernels (one block per SM each: certification, then the bridge
 // stages) reading their arguments from *dev_args.
 bool batched_launch(cudaStream_t s, const BatchArgs* dev_args, int num_sms);
