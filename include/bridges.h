@@ -173,7 +173,7 @@ int32_t bridges_ctx_set_batch_split(bridges_ctx* ctx, int64_t split_edges);
  *   group[b] : threads of the group that runs a graph's bridge stage -- 1024 (a whole block), 512
  *              (half a block) or 256 (the certification group itself, which runs the stage of a
  *              one-partition graph of up to 1,024 vertices right after certifying it); 0 = the
- *              smallest group the graph fits (256 up to 1,024 vertices, 512 up to 2,048, 1024
+ *              smallest group the graph fits (256 up to 1,024 vertices, 512 up to 3,008, 1024
  *              above).  A group too small for a graph is raised to the smallest that fits.
  *   split[b] : graphs with more edges than this are cut into ceil(E / split) contiguous
  *              partitions (at most 64, Sec. 3's M per graph), each certified by a 256-thread

@@ -18,7 +18,7 @@
 // on 16-bit arrays with barriers between phases (list ranking by a ruling set, subtree ranges
 // from shuffle windows and chunk extrema), then a rank sort of the packed (a << 12 | b) keys
 // (bitonic above the group's thread count).  A graph's fixed cost is its barriers, so graphs of
-// up to 2,048 vertices run two per block: the block splits into 512-thread groups with their own
+// up to 3,008 vertices run two per block: the block splits into 512-thread groups with their own
 // half of shared memory and their own named barrier, so that one graph's barrier waits overlap
 // with the other's work.  Nothing waits on another block, so there is no spin anywhere.
 #include <algorithm>
@@ -34,7 +34,7 @@ namespace {
 constexpr int kT = 1024;           // threads per block
 constexpr int kVmax = kBatchVmax;  // 4096: a whole block's graph
 constexpr int kHalfT = kT / 2;     // threads of a half-block group
-constexpr int kHalfVmax = kVmax / 2;  // 2048: a half-block group's graph
+constexpr int kHalfVmax = kBatchHalfVmax;  // 3008: a half-block group's graph
 constexpr int kQuarterT = kT / 4;     // threads of a quarter-block group
 constexpr int kQuarterVmax = kVmax / 4;  // 1024: a quarter-block group's graph
 constexpr uint16_t kNone16 = 0xffff;
@@ -70,9 +70,11 @@ struct Layout {
   static constexpr int kBytes = R0 + R1 + R2 + R3 + R4 + R5 + R6 + R7 + R8 + R9;
 };
 constexpr int cmax(int a, int b) { return a > b ? a : b; }
-// a half block's share holds one half-group layout or two quarter-group layouts
-constexpr int kHalfBytes = cmax(Layout<kHalfVmax>::kBytes, 2 * Layout<kQuarterVmax>::kBytes);
+// a half block's share holds one half-group layout
+constexpr int kHalfBytes = Layout<kHalfVmax>::kBytes;
 constexpr int kSmem = cmax(Layout<kVmax>::kBytes, 2 * kHalfBytes);
+static_assert(kHalfVmax % 32 == 0 && kHalfBytes % 16 == 0, "half layouts: whole chunks, 16-byte regions");
+static_assert(kSmem + 2048 <= 227 * 1024, "the bridge kernel's shared memory (with its static part) fits a block");
 
 struct Smem {
   int32_t* P1;
@@ -769,9 +771,22 @@ __device__ int32_t s_bridges(const Grp<NT>& G, const Smem& S, int32_t V, int32_t
     G.sync();
     return n;
   }
-  // bitonic sort of n keys (padded to a power of two with ~0)
   int np = 1;
   while (np < n) np <<= 1;
+  if (np > VM) {
+    // more keys than the threads and a power of two above the key array's capacity: every thread
+    // ranks several keys against all n (keys are unique)
+    for (int i = tid; i < n; i += NT) {
+      const uint32_t mine = S.keys[i];
+      int32_t rank = 0;
+      for (int j = 0; j < n; j++) rank += S.keys[j] < mine;
+      out[2 * rank] = (int32_t)(mine >> 12);
+      out[2 * rank + 1] = (int32_t)(mine & 0xfff);
+    }
+    G.sync();
+    return n;
+  }
+  // bitonic sort of n keys (padded to a power of two with ~0)
   for (int i = n + tid; i < np; i += NT) S.keys[i] = 0xffffffffu;
   G.sync();
   for (int k = 2; k <= np; k <<= 1) {

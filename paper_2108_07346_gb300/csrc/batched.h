@@ -7,7 +7,9 @@
 namespace bridges {
 
 constexpr int kBatchVmax = 4096;  // graphs up to this many vertices are handled in shared memory
-constexpr int kBatchHalfVmax = kBatchVmax / 2;     // ... up to this many, two per block
+// ... up to this many, two per block: the largest size whose bridge-stage layout fits twice in a
+// block's shared memory (2 x 115,200 bytes)
+constexpr int kBatchHalfVmax = 3008;
 constexpr int kBatchQuarterVmax = kBatchVmax / 4;  // ... up to this many, by a certification group
 
 // One unit of work: a whole graph (nparts == 1) or partition `part` of it.
