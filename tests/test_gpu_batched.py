@@ -105,6 +105,25 @@ def test_small_batch_automatic_split(cuda_lib):
             assert {tuple(x) for x in planted.tolist()} <= {tuple(x) for x in got.tolist()}
 
 
+def test_many_bridges_at_the_class_limits(ctx):
+    """Trees and paths (every edge a bridge) at the group-size limits: 2,000 vertices (a half
+    block, bitonic sort), 2,900 and 3,008 (a half block, more keys than its threads and a power of
+    two above its key array: the several-keys-per-thread rank sort), 3,009 (a whole block), and a
+    sparse multigraph of 2,950 vertices with many components."""
+    rng = np.random.default_rng(5)
+    graphs = []
+    for n in (2000, 2900, 3008, 3009):
+        par = (rng.random(n - 1) * np.arange(1, n)).astype(np.int32)
+        graphs.append((par, np.arange(1, n, dtype=np.int32), n))
+        pu = np.arange(n - 1, dtype=np.int32)
+        graphs.append((pu, pu + 1, n))
+    u, v = graphgen.random_multigraph(4242, 2950, 2600)
+    graphs.append((u, v, 2950))
+    res = run_batch(ctx, graphs)
+    for (u, v, V), got in zip(graphs, res):
+        assert got.tolist() == oracle.dfs_bridges(u, v, V).tolist()
+
+
 def test_errors_are_per_graph(ctx):
     good = graphgen.random_multigraph(7, 20, 30)
     bad = (np.array([0, 1], np.int32), np.array([1, 50], np.int32), 10)
