@@ -36,7 +36,7 @@ constexpr int kVmax = kBatchVmax;  // 4096: a whole block's graph
 constexpr int kHalfT = kT / 2;     // threads of a half-block group
 constexpr int kHalfVmax = kBatchHalfVmax;  // 3008: a half-block group's graph
 constexpr int kQuarterT = kT / 4;     // threads of a quarter-block group
-constexpr int kQuarterVmax = kVmax / 4;  // 1024: a quarter-block group's graph
+constexpr int kQuarterVmax = kBatchQuarterVmax;  // 1024: a quarter-block (certification) group's graph
 constexpr uint16_t kNone16 = 0xffff;
 constexpr int kRuleGap = 8;  // list ranking: a ruler every kRuleGap arcs (by index)
 
@@ -139,7 +139,8 @@ __device__ Smem carve_smem(char* base) {
 }
 
 // A group of NT threads (whole block, a half or a quarter) working on one task: its thread index
-// and its barrier (0 = the block's; 1, 2 = the halves' and 3 to 6 = the quarters' named ones).
+// and its barrier (0 = the block's; named barriers 1, 2 for the bridge kernel's halves and 1 to 4
+// for the certification groups, the quarters).
 template <int NT>
 struct Grp {
   int tid;
