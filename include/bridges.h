@@ -84,7 +84,11 @@ typedef struct bridges_opts {
   int32_t test_hold_polls;    /* for tests of the failure path; 0 in normal use.  > 0: the final
                                  stage's last block sleeps this many ~100 ns polls before its first
                                  barrier, so that a short barrier wait above gives up */
-  int32_t reserved[1];
+  int32_t test_fail_alloc;    /* for tests of the failure path; 0 in normal use.  n > 0: the n-th
+                                 device allocation of the context's own buffers (workspace,
+                                 host-call staging, batched descriptors) after the options were
+                                 set fails as on a full device: that call returns BRIDGES_ENOMEM,
+                                 and the context stays usable (a later call allocates again) */
 } bridges_opts;
 
 typedef struct bridges_ctx bridges_ctx;

@@ -57,7 +57,7 @@ class Opts(ctypes.Structure):
         ("ap_fused", ctypes.c_int32),
         ("test_barrier_polls", ctypes.c_int32),
         ("test_hold_polls", ctypes.c_int32),
-        ("reserved", ctypes.c_int32 * 1),
+        ("test_fail_alloc", ctypes.c_int32),
     ]
 
 
@@ -337,16 +337,17 @@ class Context:
         """bridges_ctx_get_opts: the context's current options as a dict."""
         o = Opts()
         _check(self._lib.bridges_ctx_get_opts(self._h, ctypes.byref(o)), "bridges_ctx_get_opts")
-        return {name: getattr(o, name) for name, _ in Opts._fields_ if name != "reserved"}
+        return {name: getattr(o, name) for name, _ in Opts._fields_}
 
     def set_opts(self, M=0, fan_in=0, block=0, ctas_per_sm=0, warm_edges=-1, host_read=False, warm_block=0,
-                 ap_warm_edges=0, ap_fused=0, test_barrier_polls=0, test_hold_polls=0):
+                 ap_warm_edges=0, ap_fused=0, test_barrier_polls=0, test_hold_polls=0, test_fail_alloc=0):
         o = Opts()
         o.M, o.fan_in, o.block, o.ctas_per_sm, o.warm_edges = M, fan_in, block, ctas_per_sm, warm_edges
         o.host_read = int(bool(host_read))
         o.warm_block, o.ap_warm_edges = int(warm_block), int(ap_warm_edges)
         o.ap_fused = int(ap_fused)
         o.test_barrier_polls, o.test_hold_polls = int(test_barrier_polls), int(test_hold_polls)
+        o.test_fail_alloc = int(test_fail_alloc)
         _check(self._lib.bridges_ctx_set_opts(self._h, ctypes.byref(o)), "bridges_ctx_set_opts")
 
     def wait_value(self, flag, value: int, max_polls: int, stream=None) -> int:

@@ -85,6 +85,17 @@ bool ws_fits(const bridges_ctx* c, size_t need) {
   return !c->budget || need + c->stage_bytes <= c->budget;
 }
 
+// A device allocation of one of the context's own buffers.  With opts.test_fail_alloc = n > 0 the
+// n-th of them since the options were set fails as cudaMalloc does on a full device (a test of the
+// failure path; never set in normal use).
+cudaError_t ctx_malloc(bridges_ctx* c, void** p, size_t bytes) {
+  if (++c->allocs == c->opts.test_fail_alloc && c->opts.test_fail_alloc > 0) {
+    *p = nullptr;
+    return cudaErrorMemoryAllocation;
+  }
+  return cudaMalloc(p, bytes);
+}
+
 int64_t ensure_ws(bridges_ctx* c, size_t need, cudaStream_t s) {
   if (need <= c->ws_bytes) return BRIDGES_OK;
   if (c->user_ws) return BRIDGES_ENOMEM;
@@ -98,7 +109,7 @@ int64_t ensure_ws(bridges_ctx* c, size_t need, cudaStream_t s) {
   }
   size_t bytes = align_up(need + need / 8, 1 << 20);
   if (c->budget) bytes = std::min(bytes, c->budget - c->stage_bytes);
-  if (cudaMalloc(&c->ws, bytes) != cudaSuccess) {
+  if (ctx_malloc(c, &c->ws, bytes) != cudaSuccess) {
     cudaGetLastError();
     c->ws = nullptr;
     return BRIDGES_ENOMEM;
@@ -275,7 +286,7 @@ int64_t stage_host_edges(bridges_ctx* c, cudaStream_t s, const int32_t* hu, cons
       c->stage = nullptr;
       c->stage_bytes = 0;
     }
-    if (cudaMalloc(&c->stage, need) != cudaSuccess) {
+    if (ctx_malloc(c, reinterpret_cast<void**>(&c->stage), need) != cudaSuccess) {
       cudaGetLastError();
       return BRIDGES_ENOMEM;
     }
@@ -722,7 +733,7 @@ int64_t ensure_batched(bridges_ctx* c, cudaStream_t s, int64_t ntasks, int64_t G
   }
   if (c->bws) cudaFree(c->bws);
   c->bws = nullptr;
-  if (cudaMalloc(&c->bws, L.total) != cudaSuccess || cudaMallocHost(&c->bstage[0], L.s_total) != cudaSuccess ||
+  if (ctx_malloc(c, &c->bws, L.total) != cudaSuccess || cudaMallocHost(&c->bstage[0], L.s_total) != cudaSuccess ||
       cudaMallocHost(&c->bstage[1], L.s_total) != cudaSuccess) {
     cudaGetLastError();
     return BRIDGES_ENOMEM;
@@ -1225,6 +1236,7 @@ extern "C" int32_t bridges_ctx_set_opts(bridges_ctx* c, const bridges_opts* o) {
   const int32_t prof = c->opts.profile;
   c->opts = *o;
   c->opts.profile = prof;  // event slots exist only if created with profiling
+  c->allocs = 0;           // opts.test_fail_alloc counts from here
   return BRIDGES_OK;
 }
 

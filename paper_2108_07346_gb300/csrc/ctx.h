@@ -24,6 +24,7 @@ struct bridges_ctx {
   int num_sms = 0;
   size_t smem_optin = 0;
   int64_t launches = 0;
+  int64_t allocs = 0;  // device allocations of the context's own buffers since its options were set
   // profiling: a ring of kRing event sets, one per call; slot = call index % kRing
   static constexpr int kRing = 32;
   cudaEvent_t ev[kRing][8]{};

@@ -3,6 +3,8 @@ import ctypes
 import glob
 import os
 import re
+import shutil
+import subprocess
 
 import pytest
 
@@ -100,3 +102,30 @@ def test_null_handles_are_rejected_without_touching_a_gpu():
             assert got == -1, (name, got)
         checked += 1
     assert checked >= 30
+
+
+@pytest.mark.skipif(not shutil.which("gcc"), reason="needs gcc")
+def test_binding_structs_match_the_header(tmp_path):
+    """Every struct the binding passes by pointer has the header's size and field offsets, as a C
+    compiler lays them out (a field added, dropped or retyped on one side only would shift the
+    rest)."""
+    import paper_2108_07346_gb300 as pb
+
+    pairs = [("bridges_opts", pb.Opts), ("bridges_batch_plan", pb.BatchPlan), ("bridges_request", pb.Request)]
+    lines = ['#include <stdio.h>', '#include <stddef.h>', f'#include "{os.path.join(ROOT, "include", "bridges.h")}"',
+             "int main(void) {"]
+    for cname, cls in pairs:
+        lines.append(f'  printf("{cname} size %zu\\n", sizeof({cname}));')
+        for fname, _ in cls._fields_:
+            lines.append(f'  printf("{cname} {fname} %zu\\n", offsetof({cname}, {fname}));')
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-std=c99", "-o", str(exe), str(src)], check=True)
+    got = dict(l.rsplit(" ", 1) for l in subprocess.run([str(exe)], check=True, capture_output=True,
+                                                         text=True).stdout.splitlines())
+    for cname, cls in pairs:
+        assert int(got[f"{cname} size"]) == ctypes.sizeof(cls), cname
+        for fname, _ in cls._fields_:
+            assert int(got[f"{cname} {fname}"]) == getattr(cls, fname).offset, (cname, fname)

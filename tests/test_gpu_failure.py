@@ -63,3 +63,49 @@ def test_final_stage_barrier_timeout_leaves_a_usable_context(cuda_lib):
     ctx.set_opts()
     assert ctx.find(u, v, g.V, 1).cpu().numpy().tolist() == ref
     assert ctx.find(u, v, g.V, 4).cpu().numpy().tolist() == ref
+
+
+def test_injected_allocation_failure_leaves_the_context_usable(cuda_lib):
+    """A device allocation that fails (injected with opts.test_fail_alloc: the n-th allocation of
+    the context's own buffers fails as on a full device) makes that call return ENOMEM; the next
+    call on the same context allocates again and gives the exact result.  Covers the workspace of
+    the device-buffer path, the staging and the workspace of the host-buffer path, and the
+    batched descriptors."""
+    g = graphgen.workload("small")
+    u = torch.from_numpy(np.array(g.u)).cuda()
+    v = torch.from_numpy(np.array(g.v)).cuda()
+    ref = oracle.dfs_bridges(g.u, g.v, g.V).tolist()
+
+    ctx = cuda_lib.Context(device="cuda:0")
+    ctx.set_opts(test_fail_alloc=1)  # the workspace
+    with pytest.raises(cuda_lib.BridgesError) as ei:
+        ctx.find(u, v, g.V, 2)
+    assert ei.value.code == -3
+    assert ctx.find(u, v, g.V, 2).cpu().numpy().tolist() == ref
+
+    hu = torch.from_numpy(np.array(g.u)).pin_memory()
+    hv = torch.from_numpy(np.array(g.v)).pin_memory()
+    for n in (1, 2):  # the host-buffer path's staging, then its workspace
+        hctx = cuda_lib.Context(device="cuda:0")
+        hctx.set_opts(test_fail_alloc=n)
+        with pytest.raises(cuda_lib.BridgesError) as ei:
+            hctx.find_host(hu, hv, g.V, 2)
+        assert ei.value.code == -3
+        assert hctx.find_host(hu, hv, g.V, 2).numpy().tolist() == ref
+
+    graphs = [graphgen.generate(graphgen.workload_spec("batched", 3, i)) for i in range(3)]
+    bu = torch.from_numpy(np.concatenate([x.u for x in graphs]).astype(np.int32)).cuda()
+    bv = torch.from_numpy(np.concatenate([x.v for x in graphs]).astype(np.int32)).cuda()
+    off = np.concatenate([[0], np.cumsum([x.E for x in graphs])]).astype(np.int64)
+    Vs = np.array([x.V for x in graphs], np.int32)
+    bctx = cuda_lib.Context(device="cuda:0")
+    bctx.set_opts(test_fail_alloc=1)  # the batched descriptors
+    with pytest.raises(cuda_lib.BridgesError) as ei:
+        bctx.find_batched(bu, bv, off, Vs)
+    assert ei.value.code == -3
+    out, counts, out_off = bctx.find_batched(bu, bv, off, Vs)
+    out, counts = out.cpu().numpy(), counts.cpu().numpy()
+    for k, x in enumerate(graphs):
+        n = int(counts[k])
+        assert out[out_off[k]: out_off[k] + 2 * n].reshape(n, 2).tolist() == \
+            oracle.dfs_bridges(x.u, x.v, x.V).tolist()
