@@ -1,5 +1,8 @@
 """Host-side helpers of bench.py that need no GPU: the source hash that decides whether a
-stored DRAM-traffic figure still describes the kernel's code."""
+stored DRAM-traffic figure still describes the kernel's code, the served bench's request stream and the
+reference arm's JSON line."""
+import os
+
 import pytest
 
 import bench
@@ -66,3 +69,24 @@ def test_request_stream_reports_a_failed_generation(monkeypatch):
     rs = bench.RequestStream("cpu", 0, 8, threads=2)
     with pytest.raises(RuntimeError, match="request generation failed"):
         rs.get()
+
+
+def test_reference_arm_prints_one_contract_line():
+    """`bench.py --impl reference` runs the oracle on the host cores (no GPU needed) and prints one
+    JSON line with the keys both arms share, its own CPU baseline and a zero-copy e2e figure."""
+    import json
+    import subprocess
+    import sys
+
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    r = subprocess.run([sys.executable, "bench.py", "--impl", "reference", "--workload", "small", "--steps", "2",
+                        "--warmup", "1"], cwd=root, capture_output=True, text=True, timeout=300, check=True)
+    lines = [l for l in r.stdout.splitlines() if l.startswith("{")]
+    assert len(lines) == 1, r.stdout
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference" and d["unit"] == "GE/s" and d["higher_is_better"] is True
+    assert d["value"] > 0 and d["steps"] == 2 and d["warmup"] == 1 and d["n_gpus"] == 1
+    assert d["config"]["workload"] == "small" and d["config"]["sample_edges_per_step"] == d["config"]["E"]
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] == 1
+    assert d["cpu_baseline"]["value"] == d["value"]
+    assert d["e2e"] == {"value": d["value"], "unit": "GE/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
