@@ -14,6 +14,11 @@ sent through ``torch.distributed`` point to point (device buffers with NCCL, hos
 gloo).  No kernel reads another rank's memory.  Each step of the computation runs in the
 library's kernels through the ``Certifier`` it is given; this module only schedules them and moves
 the certificates.
+
+A rank that dies or stops sending surfaces on the rank waiting for it as an exception from the
+exchange, never as an endless wait: with gloo at once when the connection closes, else once the
+process group's timeout (the ``timeout`` of ``init_process_group``) expires; the caller decides
+whether to rerun the call on the surviving ranks.
 """
 from __future__ import annotations
 

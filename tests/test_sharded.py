@@ -114,3 +114,50 @@ def test_gloo_ranks_reach_the_oracle_pipeline(world, kind):
     assert all(r[1] is None for r in res[1:])  # only rank 0 keeps a certificate
     ref = oracle.dfs_bridges(u, v, V).tolist()
     assert all(r[2] == ref for r in res)  # every rank gets the bridges of the whole list
+
+
+
+def _worker_lost_peer(rank, world, port, mode, q):
+    """Rank 1 joins the group and then never sends: it dies ("dead": the machine is gone) or hangs
+    ("silent").  Rank 0, waiting for rank 1's certificate, must get an error from the exchange --
+    at once for a closed connection, else after the group's timeout -- instead of waiting forever."""
+    import datetime
+    import time
+
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    sys.path.insert(0, ROOT)
+    from paper_2108_07346_gb300.sharded import shard_range, sharded_bridges
+
+    dist.init_process_group("gloo", rank=rank, world_size=world, timeout=datetime.timedelta(seconds=5))
+    if rank == 1:
+        if mode == "silent":
+            time.sleep(12)  # past rank 0's 5 s wait
+        os._exit(3)  # no clean-up, no message
+    u, v, V = _graph("small")
+    lo, hi = shard_range(len(u), rank, world)
+    t0 = time.monotonic()
+    try:
+        sharded_bridges(torch.from_numpy(u[lo:hi].copy()), torch.from_numpy(v[lo:hi].copy()), V, OracleCertifier())
+        q.put((rank, "no error", time.monotonic() - t0))
+    except Exception as e:  # the exchange reports the lost peer
+        q.put((rank, type(e).__name__, time.monotonic() - t0))
+    q.close()
+    q.join_thread()  # flush the result before leaving without tearing the group down
+    os._exit(0)
+
+
+@pytest.mark.parametrize("mode", ["dead", "silent"])
+def test_a_lost_rank_surfaces_as_an_error_not_a_hang(mode):
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_worker_lost_peer, args=(r, 2, port, mode, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    rank, what, waited = q.get(timeout=120)
+    for p in procs:
+        p.join(timeout=60)
+    assert rank == 0 and what == "RuntimeError", what
+    assert waited < (2 if mode == "dead" else 11)  # the group's timeout is 5 s
+    assert procs[0].exitcode == 0 and procs[1].exitcode == 3
