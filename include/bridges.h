@@ -226,7 +226,10 @@ int32_t bridges_batch_autotune(bridges_ctx* ctx, struct CUstream_st* stream, con
  * up to max_slots units of work in flight, each on its own stream and workspace, so requests
  * overlap on the device.  Queued small graphs (V <= 4096) are gathered into one batched launch
  * (as bridges_find_batched); a large graph runs the single-graph path once its workspace fits
- * in what mem_budget_bytes has left.  Requests arriving while others run are admitted as slots
+ * in what mem_budget_bytes has left.  The budget counts the workspaces of the single-graph
+ * requests running at the time; a slot keeps the workspace it grew to, and batched buffers are
+ * not counted, so the memory held can exceed the budget by up to (max_slots - 1) times the
+ * largest workspace admitted, plus the batched buffers.  Requests arriving while others run are admitted as slots
  * and memory free up.  Results are exact and identical to a call on the graph alone.
  */
 typedef struct bridges_request {
