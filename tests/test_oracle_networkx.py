@@ -87,3 +87,35 @@ def test_components_and_two_edge_components_match_networkx():
         assert c2 == len(ref2), (k, V, p)
         for comp in ref2:
             assert set(lab2[list(comp)].tolist()) == {min(comp)}
+
+
+def test_rooted_forest_matches_networkx_dfs():
+    """oracle.rooted_forest (Alg. 1's numbering of a spanning forest: trees rooted at their minimum
+    vertex and searched in root order, siblings by increasing id, one global counter) equals
+    networkx's depth-first preorder, predecessors and subtree sizes, with each vertex's neighbours
+    inserted in increasing order."""
+    rng = np.random.default_rng(7346)
+    for k in range(60):
+        V = int(rng.integers(1, 400))
+        # a random forest: vertex x > 0 hangs under a random earlier vertex unless it starts a tree
+        perm = rng.permutation(V)
+        edges = [(int(perm[x]), int(perm[rng.integers(0, x)])) for x in range(1, V) if rng.random() < 0.9]
+        tu = np.array([a for a, _ in edges], np.int32)
+        tv = np.array([b for _, b in edges], np.int32)
+        parent, pre, size = oracle.rooted_forest(tu, tv, V)
+        G = nx.Graph()
+        G.add_nodes_from(range(V))
+        G.add_edges_from(sorted((min(a, b), max(a, b)) for a, b in edges))  # neighbours in id order
+        order, ref_parent, ref_size = [], np.full(V, -1), np.zeros(V, int)
+        for r in sorted(min(c) for c in nx.connected_components(G)):
+            order += list(nx.dfs_preorder_nodes(G, r))
+            for y, x in nx.dfs_predecessors(G, r).items():
+                ref_parent[y] = x
+            T = nx.dfs_tree(G, r)
+            for x in T:
+                ref_size[x] = len(nx.descendants(T, x)) + 1
+        ref_pre = np.empty(V, int)
+        ref_pre[np.array(order, int)] = np.arange(V)
+        assert pre.tolist() == ref_pre.tolist(), k
+        assert parent.tolist() == ref_parent.tolist(), k
+        assert size.tolist() == ref_size.tolist(), k
