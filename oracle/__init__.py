@@ -8,8 +8,9 @@ count ``V`` and returns bridges as an (n, 2) int32 array of (a < b) pairs sorted
 See ``oracle.c`` for the passage of the paper each function follows.
 
 Parity status: every function here is pinned by the ``-m "not gpu"`` tests (hand-derived
-fixtures, closed forms, brute force, planted bridges and certificate invariants); none is
-"parity unpinned".
+fixtures, closed forms, brute force, planted bridges, certificate invariants and, where networkx
+is installed, that library's independent routines on random simple graphs); none is "parity
+unpinned".
 """
 from __future__ import annotations
 
