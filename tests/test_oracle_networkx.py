@@ -119,3 +119,34 @@ def test_rooted_forest_matches_networkx_dfs():
         assert pre.tolist() == ref_pre.tolist(), k
         assert parent.tolist() == ref_parent.tolist(), k
         assert size.tolist() == ref_size.tolist(), k
+
+
+def _nx_of(g):
+    G = nx.Graph()
+    G.add_nodes_from(range(g.V))
+    G.add_edges_from(zip(np.asarray(g.u).tolist(), np.asarray(g.v).tolist()))
+    assert G.number_of_edges() == g.E  # no parallel edges or loops: networkx sees the same graph
+    return G
+
+
+def test_generated_workloads_match_networkx():
+    """The seeded workloads: networkx's bridges equal the oracle's (Sec. 3 pipeline) and contain
+    every planted bridge; on the small workload they are exactly the planted set."""
+    import graphgen
+
+    g = graphgen.workload("small")
+    ref = _nx_bridges(_nx_of(g))
+    assert ref == [tuple(x) for x in g.planted.tolist()]
+    assert [tuple(x) for x in oracle.bridges(g.u, g.v, g.V, 16).tolist()] == ref
+    specs = [graphgen.workload_spec("batched", 3, i) for i in range(24)] + \
+        [graphgen.workload_spec("served", 4, i) for i in range(3)]
+    checked = 0
+    for spec in specs:
+        g = graphgen.generate(spec)
+        if g.E > 400_000:
+            continue
+        ref = _nx_bridges(_nx_of(g))
+        assert [tuple(x) for x in oracle.bridges(g.u, g.v, g.V, 4).tolist()] == ref
+        assert set(map(tuple, g.planted.tolist())) <= set(ref)
+        checked += 1
+    assert checked >= 20
