@@ -20,9 +20,6 @@
 
 using namespace bridges;
 
-
-
-
 namespace {
 
 constexpr size_t kMiscBytes = 1024;  // status word, device counts of bridges_from_forest, spare output
@@ -75,8 +72,6 @@ Carved carve(bridges_ctx* c, const CertPlan& p) {
   return k;
 }
 
-// Makes the workspace at least `need` bytes.  Waits for the context's previous work before
-// freeing an old, smaller workspace.
 // Whether ensure_ws(c, need) could succeed without exceeding a limit the caller set (a
 // workspace of its own, or a memory budget).
 bool ws_fits(const bridges_ctx* c, size_t need) {
@@ -96,6 +91,8 @@ cudaError_t ctx_malloc(bridges_ctx* c, void** p, size_t bytes) {
   return cudaMalloc(p, bytes);
 }
 
+// Makes the workspace at least `need` bytes.  Waits for the context's previous work before
+// freeing an old, smaller workspace.
 int64_t ensure_ws(bridges_ctx* c, size_t need, cudaStream_t s) {
   if (need <= c->ws_bytes) return BRIDGES_OK;
   if (c->user_ws) return BRIDGES_ENOMEM;
