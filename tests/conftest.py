@@ -27,6 +27,17 @@ def load_golden(name):
     return edges[:, 0].copy(), edges[:, 1].copy(), V, exp
 
 
+def load_golden_cuts(name):
+    """The fixture's hand-derived cut vertices (its optional `cuts k` section after the bridges),
+    as a sorted int32 array, or None if the fixture has none."""
+    lines = [ln.strip() for ln in open(os.path.join(GOLDEN, name)) if ln.strip() and not ln.startswith("#")]
+    at = [i for i, ln in enumerate(lines) if ln.split()[0] == "cuts"]
+    if not at:
+        return None
+    k = int(lines[at[0]].split()[1])
+    return np.array([int(ln) for ln in lines[at[0] + 1:at[0] + 1 + k]], dtype=np.int32)
+
+
 def golden_names():
     return sorted(f for f in os.listdir(GOLDEN) if f.endswith(".txt"))
 

@@ -11,7 +11,7 @@ import torch
 
 import graphgen
 import oracle
-from conftest import golden_names, load_golden
+from conftest import golden_names, load_golden, load_golden_cuts
 
 pytestmark = pytest.mark.gpu
 
@@ -33,7 +33,9 @@ def gpu_points(ctx, u, v, V, M=0):
 @pytest.mark.parametrize("M", [1, 3])
 def test_golden(ctx, name, M):
     u, v, V, _ = load_golden(name)
-    assert gpu_points(ctx, u, v, V, M).tolist() == oracle.brute_articulation(u, v, V).tolist()
+    got = gpu_points(ctx, u, v, V, M).tolist()
+    assert got == oracle.brute_articulation(u, v, V).tolist()
+    assert got == load_golden_cuts(name).tolist()  # the fixture's hand-derived cut vertices
 
 
 def test_random_multigraphs_against_definition(ctx):

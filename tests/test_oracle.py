@@ -20,7 +20,7 @@ import pytest
 
 import graphgen
 import oracle
-from conftest import golden_names, load_golden
+from conftest import golden_names, load_golden, load_golden_cuts
 
 ALL_METHODS = {
     "dfs": lambda u, v, V: oracle.dfs_bridges(u, v, V),
@@ -45,6 +45,18 @@ def test_golden(name, method):
     u, v, V, exp = load_golden(name)
     got = ALL_METHODS[method](u, v, V)
     assert got.tolist() == exp.tolist()
+
+
+@pytest.mark.parametrize("name", golden_names())
+def test_golden_cut_vertices(name):
+    """The fixtures' hand-derived cut vertices: Tarjan's low/disc test, the definition (brute
+    force) and the block-certificate restatement all give exactly them."""
+    u, v, V, _ = load_golden(name)
+    exp = load_golden_cuts(name)
+    assert exp is not None, "every fixture carries its cut vertices"
+    assert oracle.articulation_points(u, v, V).tolist() == exp.tolist()
+    assert oracle.brute_articulation(u, v, V).tolist() == exp.tolist()
+    assert sorted(oracle.block_certificate(u, v, V)[2].tolist()) == exp.tolist()
 
 
 def _random_tree(rng, n):

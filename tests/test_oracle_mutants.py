@@ -64,6 +64,7 @@ def pins():
     methods = sorted(T.ALL_METHODS)
     return [
         ("golden fixtures", lambda: [T.test_golden(n, m) for n in golden_names() for m in methods]),
+        ("golden cut vertices", lambda: [T.test_golden_cut_vertices(n) for n in golden_names()]),
         ("closed forms", lambda: [T.test_closed_forms(m) for m in methods]),
         ("random multigraphs, three methods", T.test_random_multigraphs_agree),
         ("sparse trees plus edges", T.test_sparse_random_trees_plus_edges),
