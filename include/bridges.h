@@ -155,10 +155,12 @@ int64_t bridges_find_host(bridges_ctx* ctx, struct CUstream_st* stream, const in
  *                      sum over h < g of 2*max(V[h]-1, 0).
  *   out_counts_device: device, G int64; graph g's bridge count, or a negative status for that
  *                      graph alone (e.g. BRIDGES_ERANGE).
- * Graphs with V <= 4096 are certified and solved entirely in shared memory, one block per graph
- * (graphs with many edges are split into partitions whose certificates are merged by the block
- * that finishes last); the launch is a CUDA graph cached per capacity.  Larger graphs follow
- * through the single-graph path on the same stream.  Enqueue-only: returns BRIDGES_OK or a
+ * Graphs with V <= 4096 are certified and solved in shared memory by two persistent kernels,
+ * replayed as one CUDA graph cached per capacity: the first certifies every task (a graph, or a
+ * partition of a graph with many edges) on a 256-thread group and finishes graphs of up to 1,024
+ * vertices in place; the second runs the larger graphs' bridge stages (the partitions'
+ * certificates merged there), two graphs per block up to 3,008 vertices, else one.  Larger graphs
+ * follow through the single-graph path on the same stream.  Enqueue-only: returns BRIDGES_OK or a
  * host-detected error; synchronise the stream before reading the outputs.  The call waits on the
  * host only for the context's batch before last, and a batch starts on the device after the
  * context's previous batch has finished, whichever stream that one ran on.
@@ -210,9 +212,11 @@ int32_t bridges_ctx_get_batch_plan(const bridges_ctx* ctx, bridges_batch_plan* p
  * bridges_find_batched): buckets of vertex counts up to 256, 512, 1,024, 2,048 and 4,096, and,
  * one bucket at a time (largest first, twice over), every group size the bucket's graphs fit,
  * partition splits of 2^18 to 2^22 edges or automatic, and warm-up prefixes of 2V + 1024, 4V + 2048
- * and 8V + 2048 edges, each timed over `reps` batched calls (CUDA events on `stream`).  Keeps the
- * fastest plan in the context and copies it to *best (may be NULL); *best_us (may be NULL) gets
- * its microseconds per batch.  Graphs above 4,096 vertices are not batched and not tuned.  Uses
+ * and 8V + 2048 edges, each timed over `reps` batched calls (CUDA events on `stream`).  A change
+ * is kept only when it is at least 0.5% faster (the timing noise of a few calls), and the plan
+ * found is then timed against the automatic plan, in turn, three more times: the automatic plan
+ * stays unless beaten by the same margin.  The plan kept goes to the context and to *best (may be
+ * NULL); *best_us (may be NULL) gets its microseconds per batch.  Graphs above 4,096 vertices are not batched and not tuned.  Uses
  * the context's batched buffers; returns BRIDGES_OK or an error (the plan is then unchanged). */
 int32_t bridges_batch_autotune(bridges_ctx* ctx, struct CUstream_st* stream, const int32_t* edges_u,
                                const int32_t* edges_v, const int64_t* edge_off_host, const int32_t* V_host, int32_t G,
@@ -229,8 +233,8 @@ int32_t bridges_batch_autotune(bridges_ctx* ctx, struct CUstream_st* stream, con
  * in what mem_budget_bytes has left.  The budget counts the workspaces of the single-graph
  * requests running at the time; a slot keeps the workspace it grew to, and batched buffers are
  * not counted, so the memory held can exceed the budget by up to (max_slots - 1) times the
- * largest workspace admitted, plus the batched buffers.  Requests arriving while others run are admitted as slots
- * and memory free up.  Results are exact and identical to a call on the graph alone.
+ * largest workspace admitted, plus the batched buffers.  Requests arriving while others run are
+ * admitted as slots and memory free up.  Results are exact and identical to a call on the graph alone.
  */
 typedef struct bridges_request {
   const int32_t* edges_u; /* device, E int32 */
