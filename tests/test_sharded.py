@@ -93,7 +93,7 @@ def _worker(rank, world, port, kind, q):
         dist.destroy_process_group()
 
 
-@pytest.mark.parametrize("world,kind", [(2, "small"), (3, "small"), (3, "multigraph"), (4, "multigraph")])
+@pytest.mark.parametrize("world,kind", [(2, "small"), (3, "small"), (3, "multigraph"), (4, "multigraph"), (5, "small")])
 def test_gloo_ranks_reach_the_oracle_pipeline(world, kind):
     import oracle
 
